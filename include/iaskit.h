@@ -1,0 +1,148 @@
+/*
+ * iaskit.h - C ABI of the GB300 INV-ASKIT library (libiaskit.so).
+ *
+ * INV-ASKIT (Yu, March, Xiao, Biros, arXiv 1602.01376) factorizes lambda*I + K~,
+ * where K~ = D + UV is ASKIT's hierarchical approximation of the Gaussian kernel
+ * matrix K_ij = exp(-||x_i - x_j||^2 / (2 h^2)) (Sec. I, eq. gaussian; Sec. II-A,
+ * II-B), and then solves (lambda*I + K~) w = u in O(N log N) (Sec. II-C, Alg.
+ * "Factorize" and Alg. "Solve").  The calls follow the paper's problem statement
+ * (Sec. II-C, first paragraph): given the points, the bandwidth h, the
+ * regularization lambda, the leaf size m and the skeleton budget, build the tree,
+ * K~ and its factorization; then apply (lambda*I + K~)^{-1} to right-hand sides.
+ *
+ * Conventions shared by every call
+ *  - Every step runs on the current CUDA device in this library's kernels; there
+ *    is no CPU fallback.  If no device is usable the call returns IASKIT_ERR_CUDA.
+ *  - All int-returning calls return IASKIT_OK (0) or a negative error code and
+ *    never abort; iaskit_last_error() describes the last failure.
+ *  - Matrices are column-major FP64.  Points are row-major: point i occupies
+ *    points[i*d .. i*d + d - 1].  Right-hand sides and solutions are N x nrhs
+ *    column-major in the ORIGINAL point order (the tree permutation is internal).
+ *  - One implicit factorization is held by the library.  It is owned by the
+ *    library until iaskit_free() or the next iaskit_factor*; the library never
+ *    keeps a caller pointer after a call returns.
+ *  - Calls are synchronous: they return after the device work they enqueued has
+ *    finished.  Work is enqueued on the stream set by iaskit_set_stream (default:
+ *    the legacy default stream).
+ *  - Not thread-safe: serialize calls from several host threads.
+ */
+#ifndef IASKIT_H
+#define IASKIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define IASKIT_OK 0
+#define IASKIT_ERR_ARG (-1)           /* invalid argument (sizes, h <= 0, lambda < 0, ...) */
+#define IASKIT_ERR_INPUT (-2)         /* non-finite point or right-hand-side entry */
+#define IASKIT_ERR_NOMEM (-3)         /* device allocation failed or memory cap exceeded */
+#define IASKIT_ERR_SINGULAR (-4)      /* exact zero pivot in a leaf LU or a reduced system */
+#define IASKIT_ERR_NOT_FACTORED (-5)  /* solve/apply before a successful factor */
+#define IASKIT_ERR_NOT_CONVERGED (-6) /* iterative refinement hit its sweep cap */
+#define IASKIT_ERR_TIMEOUT (-7)       /* a bounded device-side wait expired */
+#define IASKIT_ERR_CUDA (-8)          /* CUDA runtime error; see iaskit_last_error() */
+#define IASKIT_ERR_UNSUPPORTED (-9)   /* valid request outside what this build supports */
+
+/*
+ * Build the tree, the kNN lists, the skeletons (ASKIT, Sec. II-B) and the
+ * INV-ASKIT factorization (Sec. II-C, Alg. "Factorize") for N points in d
+ * dimensions.
+ *   points   HOST pointer, N*d doubles, row-major; copied to the device.
+ *   N >= 2, d >= 1, h > 0, lambda >= 0, leaf_m >= 2 (leaf size m: the tree has
+ *            L = min{l : ceil(N/2^l) <= m} levels below the root, Sec. II-A),
+ *   s_max >= 1 (skeleton budget per node),
+ *   tol      > 0: adaptive rank, the smallest s with |R_ss| <= tol*|R_00| in the
+ *            column-pivoted QR of the sampled block (Sec. II-B "chosen adaptively");
+ *            <= 0: fixed rank s = min(s_max, columns, sampled rows).
+ * Errors: IASKIT_ERR_ARG, _INPUT (non-finite point), _NOMEM, _SINGULAR, _CUDA.
+ * On error the previous factorization is released.
+ */
+int iaskit_factor(const double* points, int64_t N, int d, double h, double lambda,
+                  int leaf_m, int s_max, double tol);
+
+/* As iaskit_factor with a DEVICE pointer (caller-owned, e.g. a torch tensor). */
+int iaskit_factor_device(const double* d_points, int64_t N, int d, double h, double lambda,
+                         int leaf_m, int s_max, double tol);
+
+/*
+ * Solve (lambda*I + K~) w = u in place (Sec. II-C, Alg. "Solve").
+ *   rhs      HOST pointer, N x nrhs column-major, original point order; on return
+ *            it holds w.  nrhs >= 1.
+ * With the option "refine" > 0 the solve iterates w += Solve(u - (lambda I + K~) w)
+ * with the FP64 hierarchical operator until ||r||/||u|| <= "refine_tol" for every
+ * column or "refine" sweeps were spent (then IASKIT_ERR_NOT_CONVERGED, w holds the
+ * last iterate).
+ * Errors: IASKIT_ERR_NOT_FACTORED, _ARG, _INPUT, _NOT_CONVERGED, _NOMEM, _CUDA.
+ */
+int iaskit_solve(double* rhs, int nrhs);
+
+/* As iaskit_solve with a DEVICE pointer (N x nrhs, column-major, ld = N). */
+int iaskit_solve_device(double* d_rhs, int nrhs);
+
+/*
+ * u = (lambda*I + K~) w by the FP64 hierarchical MatVec (Sec. II-B, "Skeletonize"
+ * lines that depend on w, then "Evaluate" with the separation i not in alpha).
+ *   w, u     HOST pointers, N x nrhs column-major, original point order; u is
+ *            overwritten.  The pointers may not alias.
+ * Errors: IASKIT_ERR_NOT_FACTORED, _ARG, _NOMEM, _CUDA.
+ */
+int iaskit_apply(const double* w, double* u, int nrhs);
+
+/* As iaskit_apply with DEVICE pointers. */
+int iaskit_apply_device(const double* d_w, double* d_u, int nrhs);
+
+/*
+ * Options (set before iaskit_factor* unless noted):
+ *   "kappa"        neighbours per point for sampling (default 16)
+ *   "samp_factor"  sampled rows per node = samp_factor * s_max, capped at N - |node| (2)
+ *   "seed"         seed of the uniform-fill random stream (0)
+ *   "refine"       max refinement sweeps in iaskit_solve* (0 = plain solve) [any time]
+ *   "refine_tol"   relative residual target of refinement (1e-10) [any time]
+ *   "mem_cap_gb"   refuse factorizations whose device footprint exceeds this (0 = none)
+ * Errors: IASKIT_ERR_ARG for an unknown key or an invalid value.
+ */
+int iaskit_set_option(const char* key, double value);
+int iaskit_get_option(const char* key, double* value);
+
+/* Stream for all later work (a cudaStream_t passed as void*; NULL = default). */
+int iaskit_set_stream(void* cuda_stream);
+
+/*
+ * JSON with timings per phase (ms), the rank profile, algorithmic flop and byte
+ * counts and the last refinement history.  Writes at most len bytes including the
+ * terminating NUL; returns the full length needed (>= 0) or a negative error.
+ */
+int iaskit_stats(char* json_buf, size_t len);
+
+/* Human-readable description of the last error (static storage, never NULL). */
+const char* iaskit_last_error(void);
+
+/* Release the factorization and all device memory held by the library. */
+void iaskit_free(void);
+
+/*
+ * Introspection of the current factorization (tests compare these with the
+ * oracle).  Node (l, i) has heap id 2^l + i, l = 0 .. depth.  All outputs are HOST
+ * buffers.  Errors: IASKIT_ERR_NOT_FACTORED, _ARG (bad node or short buffer).
+ */
+int iaskit_depth(void);                                 /* L, or a negative error */
+int iaskit_get_perm(int32_t* perm);                     /* N: perm[pos] = original index */
+int iaskit_get_knn(int32_t* knn, int kappa_cap);        /* N x kappa row-major, original ids */
+int iaskit_get_ranks(int32_t* ranks, int count);        /* per heap id (count = 2^(L+1)); root = 0 */
+/* Skeletons of node (l, i) as permuted positions in pivot order; returns s or error. */
+int iaskit_get_skeleton(int level, int index, int32_t* skel, int cap);
+/* Sampled rows of node (l, i) as ascending permuted positions; returns the count. */
+int iaskit_get_samples(int level, int index, int32_t* samp, int cap);
+/* Nested P of node (l, i): s x n_cols column-major; returns n_cols. */
+int iaskit_get_P(int level, int index, double* P, int64_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IASKIT_H */

@@ -1,0 +1,236 @@
+"""Python binding of libiaskit.so (INV-ASKIT on one GB300, arXiv 1602.01376).
+
+Argument marshalling only: every step of the factorization and the solve runs in
+the library's CUDA kernels.  Host arrays are numpy; device arrays are torch CUDA
+tensors (used only as device memory).  There is no CPU fallback: if the shared
+library cannot be loaded, every call raises.
+
+Function names follow the C ABI in include/iaskit.h.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libiaskit.so")
+
+IASKIT_OK = 0
+ERRORS = {
+    -1: "IASKIT_ERR_ARG",
+    -2: "IASKIT_ERR_INPUT",
+    -3: "IASKIT_ERR_NOMEM",
+    -4: "IASKIT_ERR_SINGULAR",
+    -5: "IASKIT_ERR_NOT_FACTORED",
+    -6: "IASKIT_ERR_NOT_CONVERGED",
+    -7: "IASKIT_ERR_TIMEOUT",
+    -8: "IASKIT_ERR_CUDA",
+    -9: "IASKIT_ERR_UNSUPPORTED",
+}
+EXPORTS = [
+    "iaskit_factor", "iaskit_factor_device", "iaskit_solve", "iaskit_solve_device",
+    "iaskit_apply", "iaskit_apply_device", "iaskit_set_option", "iaskit_get_option",
+    "iaskit_set_stream", "iaskit_stats", "iaskit_last_error", "iaskit_free", "iaskit_depth",
+    "iaskit_get_perm", "iaskit_get_knn", "iaskit_get_ranks", "iaskit_get_skeleton",
+    "iaskit_get_samples", "iaskit_get_P",
+]
+
+
+class IaskitError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_c_int32_p = ctypes.POINTER(ctypes.c_int32)
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libiaskit.so (build it first with ``paper_1602_01376_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run paper_1602_01376_gb300.build.build() first")
+    lib = ctypes.CDLL(path)
+    i64, i32, dbl, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    sig = {
+        "iaskit_factor": ([vp, i64, i32, dbl, dbl, i32, i32, dbl], i32),
+        "iaskit_factor_device": ([vp, i64, i32, dbl, dbl, i32, i32, dbl], i32),
+        "iaskit_solve": ([vp, i32], i32),
+        "iaskit_solve_device": ([vp, i32], i32),
+        "iaskit_apply": ([vp, vp, i32], i32),
+        "iaskit_apply_device": ([vp, vp, i32], i32),
+        "iaskit_set_option": ([ctypes.c_char_p, dbl], i32),
+        "iaskit_get_option": ([ctypes.c_char_p, _c_double_p], i32),
+        "iaskit_set_stream": ([vp], i32),
+        "iaskit_stats": ([ctypes.c_char_p, ctypes.c_size_t], i32),
+        "iaskit_last_error": ([], ctypes.c_char_p),
+        "iaskit_free": ([], None),
+        "iaskit_depth": ([], i32),
+        "iaskit_get_perm": ([vp], i32),
+        "iaskit_get_knn": ([vp, i32], i32),
+        "iaskit_get_ranks": ([vp, i32], i32),
+        "iaskit_get_skeleton": ([i32, i32, vp, i32], i32),
+        "iaskit_get_samples": ([i32, i32, vp, i32], i32),
+        "iaskit_get_P": ([i32, i32, vp, i64], i32),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise IaskitError(rc, _lib.iaskit_last_error().decode())
+    return rc
+
+
+def _host_f64(a, order="C") -> np.ndarray:
+    return np.require(np.asarray(a, dtype=np.float64), requirements=[order[0], "A", "W"])
+
+
+def _dev_ptr(t) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError("expected a CUDA float64 torch tensor")
+    return t.data_ptr()
+
+
+# ------------------------------------------------------------------ public calls
+def iaskit_factor(points, h: float, lam: float, leaf_m: int, s_max: int, tol: float) -> None:
+    """Factorize lambda I + K~ for host points (N x d float64)."""
+    lib = load()
+    X = _host_f64(points, "C")
+    N, d = X.shape
+    _check(lib.iaskit_factor(X.ctypes.data, N, d, h, lam, leaf_m, s_max, tol))
+
+
+def iaskit_factor_device(points, h: float, lam: float, leaf_m: int, s_max: int, tol: float) -> None:
+    """Factorize from a CUDA float64 tensor of shape (N, d), row-major contiguous."""
+    lib = load()
+    if not points.is_contiguous():
+        raise ValueError("points must be contiguous")
+    N, d = points.shape
+    _check(lib.iaskit_factor_device(_dev_ptr(points), N, d, h, lam, leaf_m, s_max, tol))
+
+
+def iaskit_solve(rhs) -> np.ndarray:
+    """w = (lambda I + K~)^{-1} u for host u (N,) or (N, nrhs); returns a new array."""
+    lib = load()
+    u = np.asarray(rhs, dtype=np.float64)
+    vec = u.ndim == 1
+    U = np.array(u.reshape(u.shape[0], -1), dtype=np.float64, order="F", copy=True)
+    _check(lib.iaskit_solve(U.ctypes.data, U.shape[1]))
+    return U[:, 0] if vec else U
+
+
+def iaskit_solve_device(rhs) -> None:
+    """In place on a CUDA float64 tensor laid out N x nrhs column-major (i.e. the
+    tensor is (nrhs, N) contiguous, or (N,) for one right-hand side)."""
+    lib = load()
+    if not rhs.is_contiguous():
+        raise ValueError("rhs must be contiguous")
+    nrhs = 1 if rhs.dim() == 1 else rhs.shape[0]
+    _check(lib.iaskit_solve_device(_dev_ptr(rhs), nrhs))
+
+
+def iaskit_apply(w) -> np.ndarray:
+    """u = (lambda I + K~) w by the FP64 hierarchical MatVec (host arrays)."""
+    lib = load()
+    x = np.asarray(w, dtype=np.float64)
+    vec = x.ndim == 1
+    W = np.array(x.reshape(x.shape[0], -1), dtype=np.float64, order="F", copy=True)
+    U = np.empty_like(W, order="F")
+    _check(lib.iaskit_apply(W.ctypes.data, U.ctypes.data, W.shape[1]))
+    return U[:, 0] if vec else U
+
+
+def iaskit_apply_device(w, u) -> None:
+    lib = load()
+    nrhs = 1 if w.dim() == 1 else w.shape[0]
+    _check(lib.iaskit_apply_device(_dev_ptr(w), _dev_ptr(u), nrhs))
+
+
+def iaskit_set_option(key: str, value: float) -> None:
+    _check(load().iaskit_set_option(key.encode(), float(value)))
+
+
+def iaskit_get_option(key: str) -> float:
+    v = ctypes.c_double()
+    _check(load().iaskit_get_option(key.encode(), ctypes.byref(v)))
+    return v.value
+
+
+def iaskit_set_stream(stream) -> None:
+    """Accepts a torch.cuda.Stream, an int handle, or None for the default stream."""
+    handle = 0 if stream is None else getattr(stream, "cuda_stream", stream)
+    _check(load().iaskit_set_stream(ctypes.c_void_p(handle)))
+
+
+def iaskit_stats() -> dict:
+    lib = load()
+    n = lib.iaskit_stats(None, 0)
+    buf = ctypes.create_string_buffer(n + 16)
+    lib.iaskit_stats(buf, len(buf))
+    return json.loads(buf.value.decode())
+
+
+def iaskit_last_error() -> str:
+    return load().iaskit_last_error().decode()
+
+
+def iaskit_free() -> None:
+    load().iaskit_free()
+
+
+def iaskit_depth() -> int:
+    return _check(load().iaskit_depth())
+
+
+def iaskit_get_perm(N: int) -> np.ndarray:
+    out = np.empty(N, dtype=np.int32)
+    _check(load().iaskit_get_perm(out.ctypes.data))
+    return out
+
+
+def iaskit_get_knn(N: int, kappa: int) -> np.ndarray:
+    out = np.empty((N, kappa), dtype=np.int32)
+    _check(load().iaskit_get_knn(out.ctypes.data, kappa))
+    return out
+
+
+def iaskit_get_ranks() -> np.ndarray:
+    L = iaskit_depth()
+    out = np.empty(2 << L, dtype=np.int32)
+    _check(load().iaskit_get_ranks(out.ctypes.data, out.size))
+    return out
+
+
+def iaskit_get_skeleton(level: int, index: int, cap: int = 4096) -> np.ndarray:
+    out = np.empty(cap, dtype=np.int32)
+    s = _check(load().iaskit_get_skeleton(level, index, out.ctypes.data, cap))
+    return out[:s].copy()
+
+
+def iaskit_get_samples(level: int, index: int, cap: int = 1 << 16) -> np.ndarray:
+    out = np.empty(cap, dtype=np.int32)
+    n = _check(load().iaskit_get_samples(level, index, out.ctypes.data, cap))
+    return out[:n].copy()
+
+
+def iaskit_get_P(level: int, index: int, s: int, cap: int = 1 << 22) -> np.ndarray:
+    out = np.empty(cap, dtype=np.float64)
+    nc = _check(load().iaskit_get_P(level, index, out.ctypes.data, cap))
+    return out[: s * nc].reshape(nc, s).T.copy()

@@ -1,0 +1,275 @@
+// Brute-force kNN lists (the nearest-neighbour input of ASKIT, Sec. II-B).
+//
+// The lists are defined on the FP64 squared distance sum_k (x_k - y_k)^2 with the
+// coordinates summed in order and every operation rounded (no FMA), ties broken by
+// the lower index.  The search runs in three steps:
+//   1. FP32 prefilter: every query keeps its KP smallest FP32 squared distances
+//      (FMA accumulation) over all points, in registers;
+//   2. exact re-rank: the KP candidates get their FP64 distances, sorted by
+//      (distance, index); the first kappa form the list.  A rounding bound proves
+//      that no excluded point can come before the kappa-th: with |x| <= M for all
+//      coordinates, u = 2^-24 and e = 4.01 u M, every FP32 difference is within e of
+//      the exact one, so ||t|| >= sqrt(S32 / (1 + gamma_d)) - sqrt(d) e for the exact
+//      difference vector t and the FP32 sum S32 (gamma_d = d u / (1 - d u)); every
+//      excluded point has S32 >= the largest kept FP32 value;
+//   3. queries whose bound fails (near-ties at the cut) are redone by an exact FP64
+//      scan over all points.
+#include <cfloat>
+#include <climits>
+
+#include "kernels.cuh"
+
+namespace iaskit {
+
+namespace {
+
+constexpr int KNN_THREADS = 128;
+constexpr int KNN_TILE = 128;
+
+__global__ void to_float_kernel(const double* X, float* X32, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) X32[i] = (float)X[i];
+}
+
+__global__ void maxabs_kernel(const double* X, size_t n, unsigned long long* out) {
+  double m = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    m = fmax(m, fabs(X[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// One thread per query.  D: padded dimension (coordinates >= d are zero on both
+// sides, which adds exact zeros to the FP32 sums).  KP: kept candidates.
+template <int D, int KP>
+__global__ void __launch_bounds__(KNN_THREADS) knn_prefilter_kernel(const float* X32, int N, int d,
+                                                                    float* cand_d, int* cand_i) {
+  __shared__ float tile[KNN_TILE][D];
+  const int i = blockIdx.x * KNN_THREADS + threadIdx.x;
+  const bool active = i < N;
+  float q[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) q[k] = (active && k < d) ? X32[(size_t)i * d + k] : 0.0f;
+  float bd[KP];
+  int bi[KP];
+#pragma unroll
+  for (int t = 0; t < KP; ++t) {
+    bd[t] = FLT_MAX;
+    bi[t] = INT_MAX;
+  }
+  for (int j0 = 0; j0 < N; j0 += KNN_TILE) {
+    const int nt = min(KNN_TILE, N - j0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < KNN_TILE * D; e += KNN_THREADS) {
+      int r = e / D, k = e % D;
+      tile[r][k] = (r < nt && k < d) ? X32[(size_t)(j0 + r) * d + k] : 0.0f;
+    }
+    __syncthreads();
+    if (!active) continue;
+    for (int r = 0; r < nt; ++r) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        float df = q[k] - tile[r][k];
+        acc = fmaf(df, df, acc);
+      }
+      const int j = j0 + r;
+      if (acc <= bd[KP - 1] && j != i) {
+        float cv = acc;
+        int cj = j;
+#pragma unroll
+        for (int t = 0; t < KP; ++t) {
+          bool less = cv < bd[t] || (cv == bd[t] && cj < bi[t]);
+          float tv = less ? bd[t] : cv;
+          int tj = less ? bi[t] : cj;
+          bd[t] = less ? cv : bd[t];
+          bi[t] = less ? cj : bi[t];
+          cv = tv;
+          cj = tj;
+        }
+      }
+    }
+  }
+  if (active) {
+#pragma unroll
+    for (int t = 0; t < KP; ++t) {
+      cand_d[(size_t)i * KP + t] = bd[t];
+      cand_i[(size_t)i * KP + t] = bi[t];
+    }
+  }
+}
+
+// Exact FP64 squared distance in coordinate order, no contraction.
+__device__ __forceinline__ double exact_sqdist(const double* a, const double* b, int d) {
+  double acc = 0.0;
+  for (int k = 0; k < d; ++k) {
+    double df = __dsub_rn(a[k], b[k]);
+    acc = __dadd_rn(acc, __dmul_rn(df, df));
+  }
+  return acc;
+}
+
+__device__ __forceinline__ bool pair_less(double a, int ia, double b, int ib) {
+  return a < b || (a == b && ia < ib);
+}
+
+template <int KP>
+__global__ void knn_rerank_kernel(const double* X, int N, int d, int kappa, const float* cand_d,
+                                  const int* cand_i, const unsigned long long* maxabs_bits,
+                                  int* knn, int* flagged, int* nflagged) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double dd[KP];
+  int ii[KP];
+  const double* xi = X + (size_t)i * d;
+  const int nc = min(KP, N - 1);
+  for (int t = 0; t < nc; ++t) {
+    int j = cand_i[(size_t)i * KP + t];
+    if (j < 0 || j >= N) {  // an FP32 distance overflowed: redo this query exactly
+      int slot = atomicAdd(nflagged, 1);
+      flagged[slot] = i;
+      return;
+    }
+    ii[t] = j;
+    dd[t] = exact_sqdist(xi, X + (size_t)j * d, d);
+  }
+  for (int a = 1; a < nc; ++a) {  // insertion sort by (distance, index)
+    double v = dd[a];
+    int j = ii[a];
+    int b = a - 1;
+    while (b >= 0 && pair_less(v, j, dd[b], ii[b])) {
+      dd[b + 1] = dd[b];
+      ii[b + 1] = ii[b];
+      --b;
+    }
+    dd[b + 1] = v;
+    ii[b + 1] = j;
+  }
+  for (int t = 0; t < kappa; ++t) knn[(size_t)i * kappa + t] = ii[t];
+  if (N - 1 <= KP) return;  // every other point was a candidate
+  const double M = __longlong_as_double((long long)*maxabs_bits);
+  const double u = 5.9604644775390625e-08;  // 2^-24
+  const double e = 4.01 * u * M;
+  const double gam = d * u / (1.0 - d * u);
+  const double Dkept = (double)cand_d[(size_t)i * KP + KP - 1];
+  const double r_lo = sqrt(Dkept / (1.0 + gam)) * (1.0 - 1e-15) - sqrt((double)d) * e;
+  const bool ok = r_lo > 0.0 && r_lo * r_lo * (1.0 - 1e-12) > dd[kappa - 1];
+  if (!ok) {
+    int slot = atomicAdd(nflagged, 1);
+    flagged[slot] = i;
+  }
+}
+
+// Exact scan for one flagged query per block: every thread keeps a sorted top-kappa
+// list of its strided share of the points, then kappa rounds of a block-wide argmin
+// over the list heads merge them.
+constexpr int FB_THREADS = 128;
+constexpr int FB_MAXK = 64;
+__global__ void knn_fallback_kernel(const double* X, int N, int d, int kappa, const int* flagged,
+                                    int* knn) {
+  __shared__ double sd[FB_THREADS];
+  __shared__ int si[FB_THREADS];
+  __shared__ int st[FB_THREADS];
+  __shared__ int chosen[FB_MAXK];
+  const int i = flagged[blockIdx.x];
+  const double* xi = X + (size_t)i * d;
+  double ld[FB_MAXK];
+  int li[FB_MAXK];
+  for (int t = 0; t < kappa; ++t) {
+    ld[t] = DBL_MAX;
+    li[t] = INT_MAX;
+  }
+  for (int j = threadIdx.x; j < N; j += FB_THREADS) {
+    if (j == i) continue;
+    double v = exact_sqdist(xi, X + (size_t)j * d, d);
+    if (!pair_less(v, j, ld[kappa - 1], li[kappa - 1])) continue;
+    int b = kappa - 1;
+    while (b > 0 && pair_less(v, j, ld[b - 1], li[b - 1])) {
+      ld[b] = ld[b - 1];
+      li[b] = li[b - 1];
+      --b;
+    }
+    ld[b] = v;
+    li[b] = j;
+  }
+  int head = 0;
+  for (int t = 0; t < kappa; ++t) {
+    sd[threadIdx.x] = head < kappa ? ld[head] : DBL_MAX;
+    si[threadIdx.x] = head < kappa ? li[head] : INT_MAX;
+    st[threadIdx.x] = threadIdx.x;
+    __syncthreads();
+    for (int s = FB_THREADS / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s && pair_less(sd[threadIdx.x + s], si[threadIdx.x + s], sd[threadIdx.x],
+                                       si[threadIdx.x])) {
+        sd[threadIdx.x] = sd[threadIdx.x + s];
+        si[threadIdx.x] = si[threadIdx.x + s];
+        st[threadIdx.x] = st[threadIdx.x + s];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) chosen[t] = si[0];
+    if (threadIdx.x == st[0]) ++head;
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < kappa; t += FB_THREADS) knn[(size_t)i * kappa + t] = chosen[t];
+}
+
+template <int D, int KP>
+void launch_prefilter(const float* X32, int N, int d, float* cd, int* ci, cudaStream_t st) {
+  knn_prefilter_kernel<D, KP><<<ceil_div(N, KNN_THREADS), KNN_THREADS, 0, st>>>(X32, N, d, cd, ci);
+  IA_LAUNCH_CHECK();
+}
+
+template <int KP>
+void prefilter_dispatch(const float* X32, int N, int d, float* cd, int* ci, cudaStream_t st) {
+  if (d <= 8) launch_prefilter<8, KP>(X32, N, d, cd, ci, st);
+  else if (d <= 16) launch_prefilter<16, KP>(X32, N, d, cd, ci, st);
+  else if (d <= 32) launch_prefilter<32, KP>(X32, N, d, cd, ci, st);
+  else if (d <= 64) launch_prefilter<64, KP>(X32, N, d, cd, ci, st);
+  else throw Error(IASKIT_ERR_UNSUPPORTED, "kNN supports d <= 64");
+}
+
+}  // namespace
+
+int knn_bruteforce(const double* X, int N, int d, int kappa, int* knn, KnnScratch& s,
+                   cudaStream_t st) {
+  if (kappa < 1 || kappa > N - 1) throw Error(IASKIT_ERR_ARG, "kappa must be in [1, N-1]");
+  if (kappa > FB_MAXK - 16) throw Error(IASKIT_ERR_UNSUPPORTED, "kappa > 48");
+  const size_t nd = (size_t)N * d;
+  float* X32 = s.x32.ensure_n<float>(nd);
+  to_float_kernel<<<ceil_div(nd, 256), 256, 0, st>>>(X, X32, nd);
+  IA_LAUNCH_CHECK();
+  unsigned long long* mx = s.maxabs.ensure_n<unsigned long long>(1);
+  IA_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st));
+  maxabs_kernel<<<304, 256, 0, st>>>(X, nd, mx);
+  IA_LAUNCH_CHECK();
+  int* flagged = s.flagged.ensure_n<int>(N);
+  int* nfl = s.counter.ensure_n<int>(1);
+  IA_CUDA(cudaMemsetAsync(nfl, 0, sizeof(int), st));
+  const bool wide = kappa + 8 > 32;
+  const int KP = wide ? 64 : 32;
+  float* cd = s.cand_d.ensure_n<float>((size_t)N * KP);
+  int* ci = s.cand_i.ensure_n<int>((size_t)N * KP);
+  if (wide) {
+    prefilter_dispatch<64>(X32, N, d, cd, ci, st);
+    knn_rerank_kernel<64><<<ceil_div(N, 128), 128, 0, st>>>(X, N, d, kappa, cd, ci, mx, knn,
+                                                            flagged, nfl);
+  } else {
+    prefilter_dispatch<32>(X32, N, d, cd, ci, st);
+    knn_rerank_kernel<32><<<ceil_div(N, 128), 128, 0, st>>>(X, N, d, kappa, cd, ci, mx, knn,
+                                                            flagged, nfl);
+  }
+  IA_LAUNCH_CHECK();
+  int nf = 0;
+  d2h(&nf, nfl, 1, st);
+  IA_CUDA(cudaStreamSynchronize(st));
+  if (nf > 0) {
+    knn_fallback_kernel<<<nf, FB_THREADS, 0, st>>>(X, N, d, kappa, flagged, knn);
+    IA_LAUNCH_CHECK();
+  }
+  return nf;
+}
+
+}  // namespace iaskit

@@ -1,0 +1,59 @@
+// Per-kernel-class timing with CUDA events and a count of kernel launches.
+//
+// When enabled (option "profile"), every launcher brackets its kernel with a pair
+// of events on the launching stream; the pairs are resolved after the next stream
+// synchronization of an API call and summed per class.  The launch counter counts
+// every kernel launch of the library, enabled or not.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+namespace iaskit {
+
+enum ProfKind {
+  PK_TREE = 0,
+  PK_KNN,
+  PK_SAMPLE,
+  PK_KBLOCK,
+  PK_CPQR,
+  PK_ASSEMBLE_P,
+  PK_GETRF,
+  PK_GETRS,
+  PK_GEMM,
+  PK_MATVEC,
+  PK_MISC,
+  PK_COUNT
+};
+
+const char* prof_name(int kind);
+
+struct Profiler {
+  bool enabled = false;
+  double ms[PK_COUNT] = {};
+  long long calls[PK_COUNT] = {};
+  double flops[PK_COUNT] = {};
+  long long launches = 0;
+  struct Pending {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get_event();
+  void resolve();  // call after the stream has been synchronized
+  void reset();
+};
+
+Profiler& prof();
+
+// RAII bracket of one launch: records start/stop events when profiling is enabled.
+struct ProfScope {
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t b = nullptr;
+  ProfScope(int k, cudaStream_t s);
+  ~ProfScope();
+};
+
+}  // namespace iaskit
