@@ -1,0 +1,315 @@
+"""Benchmark of the INV-ASKIT hot path on GB300: factorization + solve per step.
+
+One step = iaskit_factor (tree, kNN, sampling, skeletonization, leaf LU, W and Z
+for every level) followed by iaskit_solve of the workload's right-hand sides.
+The metric is right-hand sides solved per second with the factorization counted
+in every step (RHS/s); the JSON line also carries the factor time and the
+solve-only rate.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload C2]
+
+--impl reference times the FP64 CPU oracle (the baseline) on a bounded sample of
+the same workload.  Under torchrun with N > 1 every rank factors its own copy of
+the workload (independent replicas, weak scaling); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from workloads import make_points, make_rhs, workload  # noqa: E402
+
+METRIC = "factor s + RHS solves/s at N=4M,d=8: chosen form vs FP64 plain, resid<=1e-10"
+UNIT = "RHS/s (factor+solve per step)"
+SM_COUNT = 152
+FP64_FMA_PER_CLK_PER_SM = 2          # GB300: FP64 pipe width per SM and clock
+CPU_SAMPLE_N = 4096                  # oracle sample: same generator and parameters, smaller N
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- CPU oracle leg
+def oracle_step(w, N_sample: int, nrhs: int) -> float:
+    """One factor + solve of the oracle on a sample of the workload; returns seconds."""
+    import oracle
+    ws = w.scaled(N_sample)
+    X = make_points(ws)
+    u = make_rhs(ws, nrhs=nrhs)
+    t0 = time.perf_counter()
+    _, _, _, F = oracle.build_all(X, ws.h, ws.lam, ws.m, ws.s_max, ws.tol, kappa=ws.kappa,
+                                  samp_factor=ws.samp_factor)
+    oracle.solve(F, u)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline_subprocess(wname: str, N_sample: int, nrhs: int, steps: int) -> dict:
+    """Runs the oracle single-threaded in a child process (BLAS pinned to one thread)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"from workloads import workload; w = workload({wname!r}); "
+            f"ts = [bench.oracle_step(w, {N_sample}, {nrhs}) for _ in range({steps})]; "
+            f"print(json.dumps(ts))")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True)
+    if r.returncode != 0:
+        return {"error": r.stderr[-400:]}
+    ts = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"times": ts}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    nrhs = w.nrhs
+    res = cpu_baseline_subprocess(w.name, CPU_SAMPLE_N, nrhs, args.warmup + args.steps)
+    if "error" in res:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + res["error"][-200:]}))
+        return 0
+    ts = res["times"][args.warmup:]
+    total = float(sum(ts))
+    value = nrhs * len(ts) / total
+    sample = (f"oracle factor+solve of N={CPU_SAMPLE_N} points of the {w.name} generator with "
+              f"the same h, lambda, m, s_max, tol and {nrhs} RHS per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(ts),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_of(w),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def config_of(w):
+    return {"workload": f"{w.name}: N={w.N}, d={w.d}, {w.kind}", "N": w.N, "d": w.d, "h": w.h,
+            "lambda": w.lam, "leaf_m": w.m, "s_max": w.s_max, "tol": w.tol, "nrhs": w.nrhs,
+            "kappa": w.kappa, "path": "plain FP64",
+            "l2": "inputs and working set larger than L2 (no flush needed)"}
+
+
+# ------------------------------------------------------------------- GPU leg
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="C2")
+    ap.add_argument("--N", type=int, default=None, help="override N (testing only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = workload(args.workload, N=args.N)
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import paper_1602_01376_gb300 as ia
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    ia.load()
+    ia.iaskit_set_stream(None)                     # legacy default stream = torch's default
+    X = torch.from_numpy(make_points(w)).cuda()
+    U0 = torch.from_numpy(np.ascontiguousarray(make_rhs(w).T)).cuda()   # (nrhs, N): N x nrhs col-major
+    U = torch.empty_like(U0)
+    args_f = (w.h, w.lam, w.m, w.s_max, w.tol)
+
+    def step():
+        ia.iaskit_factor_device(X, *args_f)
+        U.copy_(U0)
+        ia.iaskit_solve_device(U)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # residual of the last warm-up solve against the FP64 hierarchical operator
+    AU = torch.empty_like(U)
+    ia.iaskit_apply_device(U, AU)
+    resid = float(((U0 - AU).norm(dim=1) / U0.norm(dim=1)).max())
+
+    ia.iaskit_set_option("profile", 1)
+    launches0 = ia.iaskit_stats()["launches"]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            step()
+        ev1.record()
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    stats = ia.iaskit_stats()
+    ia.iaskit_set_option("profile", 0)
+    launches = stats["launches"] - launches0
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * w.nrhs * args.steps / (ms / 1e3)
+    factor_ms = stats["ms"]["factor"]
+    solve_ms = stats["ms"]["solve"]
+
+    # end to end through the host API: pinned host inputs in, solution out
+    Xh = torch.from_numpy(make_points(w)).pin_memory()
+    U_src = torch.from_numpy(np.ascontiguousarray(make_rhs(w).T))       # (nrhs, N)
+    Uh = torch.empty((w.nrhs, w.N), dtype=torch.float64).pin_memory()
+    Uh.copy_(U_src)
+    Xh_np, Uh_view = Xh.numpy(), Uh.numpy()
+    lib = ia.load()
+    e2e_steps = max(1, min(args.steps, 2))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rc = lib.iaskit_factor(Xh_np.ctypes.data, w.N, w.d, *args_f)
+        if rc != 0:
+            raise RuntimeError(ia.iaskit_last_error())
+        rc = lib.iaskit_solve(Uh_view.ctypes.data, w.nrhs)
+        if rc != 0:
+            raise RuntimeError(ia.iaskit_last_error())
+        Uh.copy_(U_src)                            # restore the right-hand sides
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * w.nrhs * e2e_steps / e2e_s
+
+    if rank != 0:
+        return 0
+    pk, src = peaks()
+    # dominant kernel class by device time inside the timed region
+    kern = stats["kernels"]
+    top = max(kern, key=lambda k: kern[k]["ms"])
+    clocks = clk.summary()
+    roof = None
+    if kern[top]["flops"] > 0 and kern[top]["ms"] > 0:
+        achieved = kern[top]["flops"] / (kern[top]["ms"] / 1e3) / 1e12      # TFLOP/s
+        peak = SM_COUNT * FP64_FMA_PER_CLK_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": top,
+                "peak_source": f"derived: {SM_COUNT} SMs x {FP64_FMA_PER_CLK_PER_SM} FP64 FMA/clk x "
+                               f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({src} clock)",
+                "launches": kern[top]["calls"], "ms_total": kern[top]["ms"]}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(w),
+        "factor_s": factor_ms / 1e3, "solve_rhs_per_s": w.nrhs / (solve_ms / 1e3),
+        "residual": resid, "gpu_launches": launches, "clocks": clocks, "roofline": roof,
+        "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in kern.items() if v["ms"] > 0},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": 8 * w.N * (w.d + w.nrhs), "d2h_bytes_per_step": 8 * w.N * w.nrhs},
+    }
+    if not args.no_cpu_baseline:
+        res = cpu_baseline_subprocess(w.name, CPU_SAMPLE_N, w.nrhs, 1)
+        if "times" in res:
+            t = res["times"][0]
+            line["cpu_baseline"] = {
+                "value": w.nrhs / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"one oracle factor+solve of N={CPU_SAMPLE_N} points of the {w.name} "
+                          f"generator, same parameters, {w.nrhs} RHS ({t:.1f} s)"}
+        else:
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": "failed: " + res.get("error", "")[-200:]}
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

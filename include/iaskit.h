@@ -104,6 +104,8 @@ int iaskit_apply_device(const double* d_w, double* d_u, int nrhs);
  *   "refine"       max refinement sweeps in iaskit_solve* (0 = plain solve) [any time]
  *   "refine_tol"   relative residual target of refinement (1e-10) [any time]
  *   "mem_cap_gb"   refuse factorizations whose device footprint exceeds this (0 = none)
+ *   "profile"      1: time every kernel class with CUDA events (reported by iaskit_stats)
+ *                  and reset the counters; 0: stop timing [any time]
  * Errors: IASKIT_ERR_ARG for an unknown key or an invalid value.
  */
 int iaskit_set_option(const char* key, double value);

@@ -492,6 +492,7 @@ void kernel_blocks(const double* Xp, int d, double h, const KDesc* descs_dev, in
                    int64_t max_entries, cudaStream_t st) {
   if (ndesc <= 0) return;
   dim3 grid(grid_for(max_entries, 256, 4096), std::min(ndesc, 65535));
+  ProfScope _ps(PK_KBLOCK, st);
   kernel_blocks_kernel<<<grid, 256, 0, st>>>(Xp, d, -1.0 / (2.0 * h * h), descs_dev, ndesc);
   IA_LAUNCH_CHECK();
 }
@@ -503,6 +504,7 @@ void cpqr_id(const CpqrDesc* descs_dev, int ndesc, int max_rows, int max_cols, i
   if (smem > 220 * 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "ID block too large for one CTA");
   if (smem > 48 * 1024)
     IA_CUDA(cudaFuncSetAttribute(cpqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ProfScope _ps(PK_CPQR, st);
   cpqr_kernel<<<ndesc, QR_THREADS, smem, st>>>(descs_dev, s_max, tol);
   IA_LAUNCH_CHECK();
 }
@@ -510,6 +512,7 @@ void cpqr_id(const CpqrDesc* descs_dev, int ndesc, int max_rows, int max_cols, i
 void assemble_P(const PDesc* descs_dev, int ndesc, int max_cols, cudaStream_t st) {
   if (ndesc <= 0) return;
   dim3 grid(grid_for((int64_t)max_cols * 64, 256, 1024), ndesc);
+  ProfScope _ps(PK_ASSEMBLE_P, st);
   assemble_P_kernel<<<grid, 256, 0, st>>>(descs_dev, ndesc);
   IA_LAUNCH_CHECK();
 }
@@ -517,6 +520,7 @@ void assemble_P(const PDesc* descs_dev, int ndesc, int max_cols, cudaStream_t st
 void getrf_batched(const LuDesc* descs_dev, int ndesc, int max_n, int* dev_status, cudaStream_t st) {
   if (ndesc <= 0) return;
   (void)max_n;
+  ProfScope _ps(PK_GETRF, st);
   getrf_kernel<<<ndesc, LU_THREADS, 0, st>>>(descs_dev, dev_status);
   IA_LAUNCH_CHECK();
 }
@@ -530,12 +534,14 @@ void getrs_batched(const LuSolveDesc* descs_dev, int ndesc, int max_n, int max_c
   if (smem > 48 * 1024)
     IA_CUDA(cudaFuncSetAttribute(getrs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(ndesc, ceil_div(max_cols, cc));
+  ProfScope _ps(PK_GETRS, st);
   getrs_kernel<<<grid, RS_THREADS, smem, st>>>(descs_dev, cc);
   IA_LAUNCH_CHECK();
 }
 
 void gemm_grouped(const GemmDesc* descs_dev, const GemmTile* tiles_dev, int ntiles, cudaStream_t st) {
   if (ntiles <= 0) return;
+  ProfScope _ps(PK_GEMM, st);
   gemm_kernel<<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
   IA_LAUNCH_CHECK();
 }
@@ -543,6 +549,7 @@ void gemm_grouped(const GemmDesc* descs_dev, const GemmTile* tiles_dev, int ntil
 void copy_batched(const CopyDesc* descs_dev, int ndesc, int64_t max_entries, cudaStream_t st) {
   if (ndesc <= 0) return;
   dim3 grid(grid_for(max_entries, 256, 1024), std::min(ndesc, 65535));
+  ProfScope _ps(PK_MISC, st);
   copy_kernel<<<grid, 256, 0, st>>>(descs_dev, ndesc);
   IA_LAUNCH_CHECK();
 }
@@ -550,12 +557,14 @@ void copy_batched(const CopyDesc* descs_dev, int ndesc, int64_t max_entries, cud
 void form_Z(const ZDesc* descs_dev, int ndesc, int64_t max_entries, cudaStream_t st) {
   if (ndesc <= 0) return;
   dim3 grid(grid_for(max_entries, 256, 1024), std::min(ndesc, 65535));
+  ProfScope _ps(PK_MISC, st);
   form_Z_kernel<<<grid, 256, 0, st>>>(descs_dev, ndesc);
   IA_LAUNCH_CHECK();
 }
 
 void permute_rows(const double* in, int ldi, double* out, int ldo, const int* perm, int N,
                   int ncols, bool scatter, cudaStream_t st) {
+  ProfScope _ps(PK_MISC, st);
   permute_rows_kernel<<<grid_for((int64_t)N * ncols, 256, 8192), 256, 0, st>>>(in, ldi, out, ldo,
                                                                                perm, N, ncols,
                                                                                scatter);
@@ -570,12 +579,14 @@ void kernel_matvec(const double* Xp, int d, double h, int nrhs, const KMatvecDes
     IA_CUDA(cudaFuncSetAttribute(kernel_matvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
   dim3 grid(ceil_div(max_rows, MV_THREADS), ndesc);
+  ProfScope _ps(PK_MATVEC, st);
   kernel_matvec_kernel<<<grid, MV_THREADS, smem, st>>>(Xp, d, -1.0 / (2.0 * h * h), nrhs, descs_dev);
   IA_LAUNCH_CHECK();
 }
 
 void check_finite(const double* x, int64_t n, int* dev_status, cudaStream_t st) {
   if (n <= 0) return;
+  ProfScope _ps(PK_MISC, st);
   check_finite_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(x, n, dev_status);
   IA_LAUNCH_CHECK();
 }

@@ -235,6 +235,7 @@ void prefilter_dispatch(const float* X32, int N, int d, float* cd, int* ci, cuda
 
 int knn_bruteforce(const double* X, int N, int d, int kappa, int* knn, KnnScratch& s,
                    cudaStream_t st) {
+  ProfScope _ps(PK_KNN, st);
   if (kappa < 1 || kappa > N - 1) throw Error(IASKIT_ERR_ARG, "kappa must be in [1, N-1]");
   if (kappa > FB_MAXK - 16) throw Error(IASKIT_ERR_UNSUPPORTED, "kappa > 48");
   const size_t nd = (size_t)N * d;

@@ -181,6 +181,7 @@ __global__ void select_fill_kernel(const uint32_t* cand_sorted, const int* node_
 
 void knn_to_positions(const int* knn, const int* perm, const int* iperm, int N, int kappa,
                       int* knn_pos, cudaStream_t st) {
+  ProfScope _ps(PK_SAMPLE, st);
   size_t n = (size_t)N * kappa;
   knn_pos_kernel<<<ceil_div(n, 256), 256, 0, st>>>(knn, perm, iperm, N, kappa, knn_pos);
   IA_LAUNCH_CHECK();
@@ -189,6 +190,7 @@ void knn_to_positions(const int* knn, const int* perm, const int* iperm, int N, 
 void sample_level(const int* knn_pos, int N, int kappa, int level, const int* off_dev,
                   const std::vector<int>& off_host, int samp_cap, const int* samp_off_dev,
                   uint64_t seed, int* samp, int* dev_status, SampleScratch& s, cudaStream_t st) {
+  ProfScope _ps(PK_SAMPLE, st);
   const int nn = 1 << level;
   const size_t n = (size_t)N * kappa;
   const int pos_bits = bit_length((uint64_t)N);   // 2^pos_bits > N: the sentinel is no position

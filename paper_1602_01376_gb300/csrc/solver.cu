@@ -140,6 +140,22 @@ class Solver {
     if (v & DEV_OVERFLOW) throw Error(IASKIT_ERR_UNSUPPORTED, "internal bound exceeded");
   }
 
+  static double gemm_flops(const std::vector<GemmDesc>& g) {
+    double f = 0;
+    for (const GemmDesc& d : g) f += 2.0 * d.M * (double)d.N * d.K;
+    return f;
+  }
+  static double getrs_flops(const std::vector<LuSolveDesc>& v) {
+    double f = 0;
+    for (const LuSolveDesc& d : v) f += 2.0 * d.n * (double)d.n * d.ncols;
+    return f;
+  }
+  static double getrf_flops(const std::vector<LuDesc>& v) {
+    double f = 0;
+    for (const LuDesc& d : v) f += 2.0 / 3.0 * d.n * (double)d.n * d.n;
+    return f;
+  }
+
   static void add_gemm(std::vector<GemmDesc>& g, std::vector<GemmTile>& t, const double* A, int lda,
                        const double* B, int ldb, double* C, int ldc, int M, int Ncol, int K,
                        double alpha, double beta) {
@@ -155,6 +171,7 @@ class Solver {
     arena.clear();
     size_t og = arena.push(g), ot = arena.push(t);
     char* base = upload_arena();
+    prof().flops[PK_GEMM] += gemm_flops(g);
     gemm_grouped((const GemmDesc*)(base + og), (const GemmTile*)(base + ot), (int)t.size(), st);
   }
 
@@ -211,6 +228,7 @@ class Solver {
       arena.clear();
       size_t o = arena.push(ds);
       char* base = upload_arena();
+      prof().flops[PK_GETRS] += getrs_flops(ds);
       getrs_batched((const LuSolveDesc*)(base + o), (int)ds.size(), m_max, max_nc, st);
     }
     if (r == L) {
@@ -289,6 +307,8 @@ class Solver {
       size_t ocp = arena.push(cp), ozs = arena.push(zs), og1 = arena.push(g1), ot1 = arena.push(t1),
              og2 = arena.push(g2), ot2 = arena.push(t2);
       char* base = upload_arena();
+      prof().flops[PK_GETRS] += getrs_flops(zs);
+      prof().flops[PK_GEMM] += gemm_flops(g1) + gemm_flops(g2);
       copy_batched((const CopyDesc*)(base + ocp), (int)cp.size(), max_cp, st);
       getrs_batched((const LuSolveDesc*)(base + ozs), (int)zs.size(), max_n2, max_nc, st);
       gemm_grouped((const GemmDesc*)(base + og1), (const GemmTile*)(base + ot1), (int)t1.size(), st);
@@ -380,6 +400,7 @@ class Solver {
     raise_status(read_status_and_clear());
     stats.t_factor_levels = now_ms() - t4;
     stats.t_factor = now_ms() - t0;
+    prof().resolve();
     factored = true;
   }
 
@@ -528,6 +549,7 @@ class Solver {
     size_t ok = arena.push(kd), ol = arena.push(ld);
     char* base = upload_arena();
     kernel_blocks(Xp.as<double>(), d, h, (const KDesc*)(base + ok), nl, (int64_t)m_max * m_max, st);
+    prof().flops[PK_GETRF] += getrf_flops(ld);
     getrf_batched((const LuDesc*)(base + ol), nl, m_max, status.as<int>(), st);
     stats.bytes_LU = tot * 8;
   }
@@ -625,6 +647,7 @@ class Solver {
       size_t oz = arena.push(zd), ol = arena.push(ld);
       base = upload_arena();
       form_Z((const ZDesc*)(base + oz), nn, max_z, st);
+      prof().flops[PK_GETRF] += getrf_flops(ld);
       getrf_batched((const LuDesc*)(base + ol), nn, max_n, status.as<int>(), st);
     }
   }
@@ -644,6 +667,7 @@ class Solver {
       refine_solve(rhs, nrhs);
     }
     IA_CUDA(cudaStreamSynchronize(st));
+    prof().resolve();
     stats.t_solve = now_ms() - t0;
   }
 
@@ -765,6 +789,7 @@ class Solver {
     }
     permute_rows(Up, N, u, N, perm.as<int>(), N, nrhs, true, st);
     IA_CUDA(cudaStreamSynchronize(st));
+    prof().resolve();
     stats.t_apply = now_ms() - t0;
   }
   void scale_copy(const double* x, double* y, double a, size_t n);
@@ -953,6 +978,11 @@ int iaskit_set_option(const char* key, double value) {
     } else if (k == "mem_cap_gb") {
       if (!(value >= 0)) throw Error(IASKIT_ERR_ARG, "invalid mem_cap_gb");
       o.mem_cap_gb = value;
+    } else if (k == "profile") {
+      int v = as_int(0, 1);
+      IA_CUDA(cudaStreamSynchronize(S().st));
+      prof().reset();
+      prof().enabled = v != 0;
     } else throw Error(IASKIT_ERR_ARG, "unknown option " + k);
   });
 }
@@ -968,6 +998,7 @@ int iaskit_get_option(const char* key, double* value) {
     else if (k == "refine") *value = o.refine;
     else if (k == "refine_tol") *value = o.refine_tol;
     else if (k == "mem_cap_gb") *value = o.mem_cap_gb;
+    else if (k == "profile") *value = prof().enabled ? 1 : 0;
     else throw Error(IASKIT_ERR_ARG, "unknown option " + k);
   });
 }
@@ -997,7 +1028,15 @@ int iaskit_stats(char* buf, size_t len) {
     snprintf(tmp, sizeof tmp, "%s%.6g", i ? "," : "", s.stats.refine_hist[i]);
     j += tmp;
   }
-  j += "],\"mean_rank_per_level\":[";
+  j += "],\"launches\":";
+  j += std::to_string(prof().launches);
+  j += ",\"kernels\":{";
+  for (int k = 0; k < PK_COUNT; ++k) {
+    snprintf(tmp, sizeof tmp, "%s\"%s\":{\"ms\":%.4f,\"calls\":%lld,\"flops\":%.6g}", k ? "," : "",
+             prof_name(k), prof().ms[k], prof().calls[k], prof().flops[k]);
+    j += tmp;
+  }
+  j += "},\"mean_rank_per_level\":[";
   for (int l = 1; l <= s.L && s.factored; ++l) {
     double tot = 0;
     for (int i = 0; i < (1 << l); ++i) tot += s.nd[(1 << l) + i].s;

@@ -157,6 +157,7 @@ int bit_length(uint64_t v) {
 
 void build_tree(const double* X, int N, int d, int L, const std::vector<std::vector<int>>& level_off,
                 int* perm, int* split_dim, TreeScratch& s, cudaStream_t st) {
+  ProfScope _ps(PK_TREE, st);
   const int T = 256;
   iota_kernel<<<ceil_div(N, T), T, 0, st>>>(perm, N);
   IA_LAUNCH_CHECK();
@@ -228,6 +229,7 @@ void build_tree(const double* X, int N, int d, int L, const std::vector<std::vec
 
 void permute_points(const double* X, const int* perm, int N, int d, int* iperm, double* Xp,
                     cudaStream_t st) {
+  ProfScope _ps(PK_TREE, st);
   const size_t n = (size_t)N * d;
   permute_points_kernel<<<ceil_div(n, 256), 256, 0, st>>>(X, perm, N, d, iperm, Xp);
   IA_LAUNCH_CHECK();
