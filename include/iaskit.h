@@ -143,6 +143,29 @@ int iaskit_get_samples(int level, int index, int32_t* samp, int cap);
 /* Nested P of node (l, i): s x n_cols column-major; returns n_cols. */
 int iaskit_get_P(int level, int index, double* P, int64_t cap);
 
+/*
+ * The kNN lists of iaskit_factor (same order, same ties, bit for bit) for callers
+ * that must not allocate device memory: for example a serving process whose
+ * device memory is entirely handed out by its own pool allocator, or a caller
+ * that cannot accept the device-wide synchronization that cudaMalloc/cudaFree may
+ * imply.  The paper has no counterpart; this is a library convenience.
+ *   d_points  DEVICE pointer, N x d row-major FP64 (caller-owned).
+ *   d_knn     DEVICE pointer, N x kappa row-major int32 output (original indices).
+ *   cuda_stream  stream to run on (NULL = default stream); the call returns after
+ *             the work has finished.
+ * Limits: 2 <= N <= 32768, 1 <= d <= 64, N*d <= 1048576, 1 <= kappa <= min(24, N-1);
+ * anything larger returns IASKIT_ERR_ARG with the limit in iaskit_last_error().
+ * Scratch: one static device array of about 12.1 MiB, which every GPU that loads
+ * this library holds until the process exits.  The call makes no device
+ * allocation.  Its first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) once; make that first call before any stream capture.
+ * All calls share the array, so calls that overlap on the GPU (other streams or
+ * threads) race; serialize them.
+ * Errors: IASKIT_ERR_ARG, _UNSUPPORTED, _CUDA.
+ */
+int iaskit_knn_noalloc(const double* d_points, int64_t N, int d, int kappa, int32_t* d_knn,
+                       void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

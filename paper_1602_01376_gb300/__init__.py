@@ -36,7 +36,7 @@ EXPORTS = [
     "iaskit_apply", "iaskit_apply_device", "iaskit_set_option", "iaskit_get_option",
     "iaskit_set_stream", "iaskit_stats", "iaskit_last_error", "iaskit_free", "iaskit_depth",
     "iaskit_get_perm", "iaskit_get_knn", "iaskit_get_ranks", "iaskit_get_skeleton",
-    "iaskit_get_samples", "iaskit_get_P",
+    "iaskit_get_samples", "iaskit_get_P", "iaskit_knn_noalloc",
 ]
 
 
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "iaskit_get_skeleton": ([i32, i32, vp, i32], i32),
         "iaskit_get_samples": ([i32, i32, vp, i32], i32),
         "iaskit_get_P": ([i32, i32, vp, i64], i32),
+        "iaskit_knn_noalloc": ([vp, i64, i32, i32, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -234,3 +235,21 @@ def iaskit_get_P(level: int, index: int, s: int, cap: int = 1 << 22) -> np.ndarr
     out = np.empty(cap, dtype=np.float64)
     nc = _check(load().iaskit_get_P(level, index, out.ctypes.data, cap))
     return out[: s * nc].reshape(nc, s).T.copy()
+
+
+def iaskit_knn_noalloc(points, kappa: int, out, stream=None) -> None:
+    """kNN lists into a caller-provided device buffer, with no device allocation.
+
+    points: CUDA float64 tensor (N, d), contiguous; out: CUDA int32 tensor (N, kappa),
+    contiguous.  For callers that cannot allocate device memory (see iaskit.h).
+    """
+    import torch
+    lib = load()
+    if not points.is_contiguous() or not out.is_contiguous():
+        raise ValueError("points and out must be contiguous")
+    if out.dtype != torch.int32 or not out.is_cuda:
+        raise TypeError("out must be a CUDA int32 tensor")
+    N, d = points.shape
+    handle = 0 if stream is None else getattr(stream, "cuda_stream", stream)
+    _check(lib.iaskit_knn_noalloc(_dev_ptr(points), N, d, kappa, out.data_ptr(),
+                                  ctypes.c_void_p(handle)))

@@ -274,3 +274,100 @@ int knn_bruteforce(const double* X, int N, int d, int kappa, int* knn, KnnScratc
 }
 
 }  // namespace iaskit
+
+// ---------------------------------------------------------------------------
+// kNN without device allocation (iaskit_knn_noalloc in include/iaskit.h).
+//
+// Its scratch lives in one file-scope device array that every GPU loading this
+// library holds until the process exits.  Host code must not pass the array's
+// name to a kernel (on the host it is only a stand-in symbol); the device address
+// is looked up once per device with cudaGetSymbolAddress and cached.
+namespace iaskit {
+namespace {
+
+constexpr int64_t NA_MAX_N = 32768;             // points
+constexpr int64_t NA_MAX_ND = int64_t(1) << 20;  // N * d coordinates
+constexpr int NA_KP = 32;                        // candidates kept per query (kappa <= 24)
+constexpr size_t NA_X32 = 0;
+constexpr size_t NA_CD = NA_X32 + sizeof(float) * NA_MAX_ND;
+constexpr size_t NA_CI = NA_CD + sizeof(float) * NA_MAX_N * NA_KP;
+constexpr size_t NA_FLAGGED = NA_CI + sizeof(int) * NA_MAX_N * NA_KP;
+constexpr size_t NA_COUNTER = NA_FLAGGED + sizeof(int) * NA_MAX_N;
+constexpr size_t NA_MAXABS = NA_COUNTER + 256;
+constexpr size_t NA_BYTES = NA_MAXABS + 256;   // about 12.1 MiB
+
+__device__ __align__(256) unsigned char g_knn_noalloc_scratch[NA_BYTES];
+
+constexpr int NA_MAX_DEVICES = 64;
+void* g_knn_noalloc_base[NA_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device (looked up once).
+unsigned char* noalloc_scratch() {
+  int dev = 0;
+  IA_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NA_MAX_DEVICES) throw Error(IASKIT_ERR_UNSUPPORTED, "device ordinal >= 64");
+  if (!g_knn_noalloc_base[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_knn_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      throw Error(IASKIT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_knn_noalloc_base[dev] = p;
+  }
+  return static_cast<unsigned char*>(g_knn_noalloc_base[dev]);
+}
+
+void knn_noalloc(const double* X, int N, int d, int kappa, int* knn, cudaStream_t st) {
+  unsigned char* base = noalloc_scratch();
+  float* X32 = reinterpret_cast<float*>(base + NA_X32);
+  float* cd = reinterpret_cast<float*>(base + NA_CD);
+  int* ci = reinterpret_cast<int*>(base + NA_CI);
+  int* flagged = reinterpret_cast<int*>(base + NA_FLAGGED);
+  int* nfl = reinterpret_cast<int*>(base + NA_COUNTER);
+  unsigned long long* mx = reinterpret_cast<unsigned long long*>(base + NA_MAXABS);
+  const size_t nd = (size_t)N * d;
+  // the array keeps the previous call's contents: clear what must start at zero
+  IA_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st));
+  IA_CUDA(cudaMemsetAsync(nfl, 0, sizeof(int), st));
+  to_float_kernel<<<ceil_div(nd, 256), 256, 0, st>>>(X, X32, nd);
+  IA_LAUNCH_CHECK();
+  maxabs_kernel<<<304, 256, 0, st>>>(X, nd, mx);
+  IA_LAUNCH_CHECK();
+  prefilter_dispatch<NA_KP>(X32, N, d, cd, ci, st);
+  knn_rerank_kernel<NA_KP><<<ceil_div(N, 128), 128, 0, st>>>(X, N, d, kappa, cd, ci, mx, knn,
+                                                              flagged, nfl);
+  IA_LAUNCH_CHECK();
+  int nf = 0;
+  IA_CUDA(cudaMemcpyAsync(&nf, nfl, sizeof(int), cudaMemcpyDeviceToHost, st));
+  IA_CUDA(cudaStreamSynchronize(st));
+  if (nf > 0) {
+    knn_fallback_kernel<<<nf, FB_THREADS, 0, st>>>(X, N, d, kappa, flagged, knn);
+    IA_LAUNCH_CHECK();
+  }
+  IA_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace
+
+int report_error(int code, const std::string& msg);
+
+}  // namespace iaskit
+
+extern "C" int iaskit_knn_noalloc(const double* d_points, int64_t N, int d, int kappa,
+                                  int32_t* d_knn, void* cuda_stream) {
+  using namespace iaskit;
+  try {
+    if (!d_points || !d_knn) return report_error(IASKIT_ERR_ARG, "null pointer");
+    if (N < 2 || d < 1) return report_error(IASKIT_ERR_ARG, "need N >= 2 and d >= 1");
+    if (N > NA_MAX_N)
+      return report_error(IASKIT_ERR_ARG, "N exceeds the no-allocation limit of 32768 points");
+    if (d > 64) return report_error(IASKIT_ERR_ARG, "d exceeds the no-allocation limit of 64");
+    if (N * (int64_t)d > NA_MAX_ND)
+      return report_error(IASKIT_ERR_ARG, "N*d exceeds the no-allocation limit of 1048576");
+    if (kappa < 1 || kappa > 24 || kappa > N - 1)
+      return report_error(IASKIT_ERR_ARG, "kappa must be in [1, min(24, N-1)]");
+    knn_noalloc(d_points, (int)N, d, kappa, d_knn, (cudaStream_t)cuda_stream);
+    return IASKIT_OK;
+  } catch (const Error& e) {
+    return report_error(e.code, e.what());
+  }
+}

@@ -891,6 +891,10 @@ int check_node(int level, int index) {
 }
 
 }  // namespace
+
+// Records a failure for iaskit_last_error() and returns its code.
+int report_error(int code, const std::string& msg) { return fail(code, msg); }
+
 }  // namespace iaskit
 
 using namespace iaskit;
