@@ -1,4 +1,5 @@
-// Batched dense kernels of the factorization (FP64).
+// Batched dense kernels of the factorization, templated on the scalar type T
+// (double: plain FP64 path; float: mixed-precision form).
 //
 //  * kernel_blocks   Gaussian kernel blocks from coordinates (Sec. I, eq. gaussian):
 //                    sampled blocks K(samples, columns), leaf blocks lambda I + K_aa
@@ -6,13 +7,16 @@
 //  * cpqr_id         column-pivoted Householder QR of a sampled block and the
 //                    interpolative decomposition T = R11^{-1} R12 (Sec. II-B; GEQP3 and
 //                    GELS in Sec. II-C).  Trailing column norms are recomputed from the
-//                    updated block at every step; pivot ties go to the lowest column.
+//                    updated block at every step, accumulated in FP64; pivot ties go to
+//                    the lowest column.
 //  * getrf / getrs   LU with partial pivoting (ties to the lowest row) and the
-//                    corresponding solve (GETRF / GETRS of Alg. "Factorize"/"Solve").
+//                    corresponding solve (GETRF / GETRS of Alg. "Factorize"/"Solve"),
+//                    both blocked by 32 so that most of the work is a register-tiled
+//                    product.
 //  * gemm_grouped    C <- alpha A B + beta C over many independent small problems, the
 //                    products of eqs. innerid and blocksmw.
-// FP64 runs at about 2 FMA per clock per SM on this part, so these kernels are bound
-// by the FP64 pipe; they keep it fed with many independent blocks.
+// In FP64 these kernels are bound by the FP64 pipe (2 FMA per clock per SM on this
+// part); they keep it fed with many independent blocks.
 #include <cfloat>
 #include <climits>
 
@@ -22,11 +26,20 @@ namespace iaskit {
 
 namespace {
 
+template <typename T>
+__device__ __forceinline__ T kexp(T x);
+template <>
+__device__ __forceinline__ double kexp<double>(double x) { return exp(x); }
+template <>
+__device__ __forceinline__ float kexp<float>(float x) { return expf(x); }
+
 // ------------------------------------------------------------ kernel blocks
+template <typename T>
 __global__ void kernel_blocks_kernel(const double* Xp, int d, double neg_inv_2h2,
-                                     const KDesc* descs, int ndesc) {
+                                     const KDescT<T>* descs, int ndesc) {
+  const T scale = (T)neg_inv_2h2;
   for (int q = blockIdx.y; q < ndesc; q += gridDim.y) {
-    const KDesc D = descs[q];
+    const KDescT<T> D = descs[q];
     const int64_t total = (int64_t)D.nrows * D.ncols;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -35,13 +48,13 @@ __global__ void kernel_blocks_kernel(const double* Xp, int d, double neg_inv_2h2
       const int c = D.colsA ? (j < D.nA ? D.colsA[j] : D.colsB[j - D.nA]) : D.col0 + j;
       const double* xr = Xp + (size_t)r * d;
       const double* xc = Xp + (size_t)c * d;
-      double d2 = 0.0;
+      T d2 = 0;
       for (int k = 0; k < d; ++k) {
-        double t = xr[k] - xc[k];
+        T t = (T)xr[k] - (T)xc[k];
         d2 = fma(t, t, d2);
       }
-      double v = exp(d2 * neg_inv_2h2);
-      if (r == c) v += D.diag;
+      T v = kexp<T>(d2 * scale);
+      if (r == c) v += (T)D.diag;
       D.out[(size_t)i + (size_t)j * D.ld] = v;
     }
   }
@@ -61,8 +74,8 @@ __device__ void block_argmax(double& v, int& idx, double* rv, int* ri) {
   }
   __syncthreads();
   if (warp == 0) {
-    v = lane < QR_WARPS ? rv[lane] : -1.0;
-    idx = lane < QR_WARPS ? ri[lane] : INT_MAX;
+    v = lane < (int)(blockDim.x >> 5) ? rv[lane] : -1.0;
+    idx = lane < (int)(blockDim.x >> 5) ? ri[lane] : INT_MAX;
     warp_argmax(v, idx);
     if (lane == 0) {
       rv[0] = v;
@@ -90,24 +103,32 @@ __device__ double block_sum(double v, double* rv) {
   return v;
 }
 
-// One block per node.  Dynamic shared memory: norms (ncols doubles), v (nrows
-// doubles), piv (ncols ints).
-__global__ void __launch_bounds__(QR_THREADS) cpqr_kernel(const CpqrDesc* descs, int s_max,
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One block per node.  Dynamic shared memory: norms (ncols doubles), v (nrows T),
+// piv (ncols ints).
+template <typename T>
+__global__ void __launch_bounds__(QR_THREADS) cpqr_kernel(const CpqrDescT<T>* descs, int s_max,
                                                           double tol) {
   extern __shared__ double shq[];
   __shared__ double rv[QR_WARPS];
   __shared__ int ri[QR_WARPS];
-  const CpqrDesc D = descs[blockIdx.x];
-  double* A = D.A;
+  const CpqrDescT<T> D = descs[blockIdx.x];
+  T* A = D.A;
   const int ld = D.ld, nr = D.nrows, nc = D.ncols;
   double* norms = shq;
-  double* v = shq + nc;
-  int* piv = (int*)(shq + nc + nr);
+  T* v = reinterpret_cast<T*>(shq + nc);
+  int* piv = reinterpret_cast<int*>(shq + nc + nr);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j = warp; j < nc; j += QR_WARPS) {
     double s = 0.0;
     for (int i = lane; i < nr; i += 32) {
-      double a = A[(size_t)i + (size_t)j * ld];
+      double a = (double)A[(size_t)i + (size_t)j * ld];
       s = fma(a, a, s);
     }
     s = warp_sum(s);
@@ -134,7 +155,7 @@ __global__ void __launch_bounds__(QR_THREADS) cpqr_kernel(const CpqrDesc* descs,
     const int p = bi;
     if (p != k) {
       for (int i = threadIdx.x; i < nr; i += QR_THREADS) {
-        double t = A[(size_t)i + (size_t)k * ld];
+        T t = A[(size_t)i + (size_t)k * ld];
         A[(size_t)i + (size_t)k * ld] = A[(size_t)i + (size_t)p * ld];
         A[(size_t)i + (size_t)p * ld] = t;
       }
@@ -150,32 +171,35 @@ __global__ void __launch_bounds__(QR_THREADS) cpqr_kernel(const CpqrDesc* descs,
     __syncthreads();
     for (int i = k + threadIdx.x; i < nr; i += QR_THREADS) v[i - k] = A[(size_t)i + (size_t)k * ld];
     __syncthreads();
-    const double x0 = v[0];
+    const double x0 = (double)v[0];
     const double alpha = x0 >= 0.0 ? -nu : nu;
     double part = 0.0;
-    for (int i = 1 + threadIdx.x; i < nr - k; i += QR_THREADS) part = fma(v[i], v[i], part);
+    for (int i = 1 + threadIdx.x; i < nr - k; i += QR_THREADS) {
+      double vi = (double)v[i];
+      part = fma(vi, vi, part);
+    }
     const double v0 = x0 - alpha;
     const double vv = block_sum(part, rv) + v0 * v0;
-    if (threadIdx.x == 0) v[0] = v0;
+    if (threadIdx.x == 0) v[0] = (T)v0;
     __syncthreads();
-    const double beta = vv > 0.0 ? 2.0 / vv : 0.0;
+    const T beta = vv > 0.0 ? (T)(2.0 / vv) : (T)0;
     for (int j = k + 1 + warp; j < nc; j += QR_WARPS) {
-      double* col = A + (size_t)j * ld;
-      double dot = 0.0;
+      T* col = A + (size_t)j * ld;
+      T dot = 0;
       for (int i = k + lane; i < nr; i += 32) dot = fma(v[i - k], col[i], dot);
-      dot = warp_sum(dot);
-      const double f = beta * dot;
+      dot = warp_sum_t<T>(dot);
+      const T f = beta * dot;
       double nrm = 0.0;
       for (int i = k + lane; i < nr; i += 32) {
-        double a = col[i] - f * v[i - k];
+        T a = col[i] - f * v[i - k];
         col[i] = a;
-        if (i > k) nrm = fma(a, a, nrm);
+        if (i > k) nrm = fma((double)a, (double)a, nrm);
       }
       nrm = warp_sum(nrm);
       if (lane == 0) norms[j] = nrm;
     }
     for (int i = k + threadIdx.x; i < nr; i += QR_THREADS)
-      A[(size_t)i + (size_t)k * ld] = (i == k) ? alpha : 0.0;
+      A[(size_t)i + (size_t)k * ld] = (i == k) ? (T)alpha : (T)0;
     s = k + 1;
     __syncthreads();
   }
@@ -183,10 +207,10 @@ __global__ void __launch_bounds__(QR_THREADS) cpqr_kernel(const CpqrDesc* descs,
   // entry of R11 gives a zero row of T.
   const int nt = nc - s;
   for (int kk = s - 1; kk >= 0 && nt > 0; --kk) {
-    const double rkk = A[(size_t)kk + (size_t)kk * ld];
+    const T rkk = A[(size_t)kk + (size_t)kk * ld];
     for (int j = threadIdx.x; j < nt; j += QR_THREADS) {
-      double* a = &A[(size_t)kk + (size_t)(s + j) * ld];
-      *a = (rkk == 0.0) ? 0.0 : *a / rkk;
+      T* a = &A[(size_t)kk + (size_t)(s + j) * ld];
+      *a = (rkk == (T)0) ? (T)0 : *a / rkk;
     }
     __syncthreads();
     const int64_t items = (int64_t)kk * nt;
@@ -200,14 +224,16 @@ __global__ void __launch_bounds__(QR_THREADS) cpqr_kernel(const CpqrDesc* descs,
   if (threadIdx.x == 0) *D.rank = s;
 }
 
-__global__ void assemble_P_kernel(const PDesc* descs, int ndesc) {
-  const PDesc D = descs[blockIdx.y];
+template <typename T>
+__global__ void assemble_P_kernel(const PDescT<T>* descs, int ndesc) {
+  const PDescT<T> D = descs[blockIdx.y];
   const int64_t total = (int64_t)D.s * D.ncols;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(e % D.s), jj = (int)(e / D.s);
     const int col = D.piv[jj];
-    const double val = jj < D.s ? (r == jj ? 1.0 : 0.0) : D.A[(size_t)r + (size_t)jj * D.ld];
+    const double val =
+        jj < D.s ? (r == jj ? 1.0 : 0.0) : (double)D.A[(size_t)r + (size_t)jj * D.ld];
     D.P[(size_t)r + (size_t)col * D.s] = val;
     if (r == 0 && jj < D.s)
       D.skel[jj] = D.colsA ? (col < D.nA ? D.colsA[col] : D.colsB[col - D.nA]) : D.col0 + col;
@@ -215,113 +241,228 @@ __global__ void assemble_P_kernel(const PDesc* descs, int ndesc) {
 }
 
 // ---------------------------------------------------------------- LU (GETRF)
+// Blocked right-looking LU with partial pivoting, one CTA per matrix:
+//   for each panel of NB columns: factor the panel column by column (pivot search
+//   over the whole remaining column, swaps inside the panel), apply the panel's
+//   row swaps to the other columns, U12 = L11^{-1} A12, and A22 -= L21 U12 as a
+//   tiled product.  The row swaps touch whole rows, as LAPACK's GETRF stores them.
 constexpr int LU_THREADS = 256;
+constexpr int LU_NB = 32;
+constexpr int LU_TM = 64;  // trailing-update tile (rows)
+constexpr int LU_TN = 64;  // trailing-update tile (cols)
 
-__global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDesc* descs, int* status) {
+template <typename T>
+__global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* descs, int* status) {
   __shared__ double rv[LU_THREADS / 32];
   __shared__ int ri[LU_THREADS / 32];
-  const LuDesc D = descs[blockIdx.x];
-  double* A = D.A;
+  __shared__ T L11[LU_NB][LU_NB + 1];
+  __shared__ T As[LU_NB][LU_TM + 1];
+  __shared__ T Bs[LU_NB][LU_TN + 1];
+  const LuDescT<T> D = descs[blockIdx.x];
+  T* A = D.A;
   const int n = D.n, ld = D.ld;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = 0; k < n; ++k) {
-    double best = -1.0;
-    int bi = INT_MAX;
-    for (int i = k + threadIdx.x; i < n; i += LU_THREADS)
-      argmax_merge(best, bi, fabs(A[(size_t)i + (size_t)k * ld]), i);
-    warp_argmax(best, bi);
-    __syncthreads();
-    if (lane == 0) {
-      rv[warp] = best;
-      ri[warp] = bi;
+  const int tid = threadIdx.x;
+  auto at = [&](int i, int j) -> T& { return A[(size_t)i + (size_t)j * ld]; };
+  for (int k0 = 0; k0 < n; k0 += LU_NB) {
+    const int nb = min(LU_NB, n - k0);
+    // 1. panel factorization
+    for (int j = 0; j < nb; ++j) {
+      const int k = k0 + j;
+      double best = -1.0;
+      int bi = INT_MAX;
+      for (int i = k + tid; i < n; i += LU_THREADS) argmax_merge(best, bi, fabs((double)at(i, k)), i);
+      block_argmax(best, bi, rv, ri);
+      const int p = bi;
+      if (tid == 0) D.ipiv[k] = p;
+      if (p != k && tid < nb) {
+        T t = at(k, k0 + tid);
+        at(k, k0 + tid) = at(p, k0 + tid);
+        at(p, k0 + tid) = t;
+      }
+      __syncthreads();
+      const T piv = at(k, k);
+      if (piv == (T)0) {
+        if (tid == 0) atomicOr(status, DEV_SINGULAR);
+        continue;
+      }
+      for (int i = k + 1 + tid; i < n; i += LU_THREADS) at(i, k) /= piv;
+      __syncthreads();
+      const int rows = n - k - 1, cols = k0 + nb - k - 1;
+      for (int t = tid; t < rows * cols; t += LU_THREADS) {
+        const int i = k + 1 + t % rows, c = k + 1 + t / rows;
+        at(i, c) -= at(i, k) * at(k, c);
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    if (warp == 0) {
-      best = lane < LU_THREADS / 32 ? rv[lane] : -1.0;
-      bi = lane < LU_THREADS / 32 ? ri[lane] : INT_MAX;
-      warp_argmax(best, bi);
-      if (lane == 0) {
-        rv[0] = best;
-        ri[0] = bi;
+    // 2. the panel's row swaps on the columns outside the panel
+    for (int c = tid; c < n; c += LU_THREADS) {
+      if (c >= k0 && c < k0 + nb) continue;
+      for (int j = 0; j < nb; ++j) {
+        const int p = D.ipiv[k0 + j];
+        if (p != k0 + j) {
+          T t = at(k0 + j, c);
+          at(k0 + j, c) = at(p, c);
+          at(p, c) = t;
+        }
       }
     }
     __syncthreads();
-    const int p = ri[0];
-    if (threadIdx.x == 0) D.ipiv[k] = p;
-    if (p != k)
-      for (int j = threadIdx.x; j < n; j += LU_THREADS) {
-        double t = A[(size_t)k + (size_t)j * ld];
-        A[(size_t)k + (size_t)j * ld] = A[(size_t)p + (size_t)j * ld];
-        A[(size_t)p + (size_t)j * ld] = t;
+    const int c0 = k0 + nb;
+    if (c0 >= n) break;
+    // 3. U12 = L11^{-1} A12 (unit lower), one thread per column
+    for (int t = tid; t < nb * nb; t += LU_THREADS) L11[t % nb][t / nb] = at(k0 + t % nb, k0 + t / nb);
+    __syncthreads();
+    for (int c = c0 + tid; c < n; c += LU_THREADS) {
+      T x[LU_NB];
+#pragma unroll
+      for (int r = 0; r < LU_NB; ++r) x[r] = r < nb ? at(k0 + r, c) : (T)0;
+#pragma unroll
+      for (int r = 1; r < LU_NB; ++r) {
+        T acc = x[r];
+#pragma unroll
+        for (int q = 0; q < LU_NB; ++q)
+          if (q < r) acc -= L11[r][q] * x[q];
+        x[r] = acc;
       }
-    __syncthreads();
-    const double piv = A[(size_t)k + (size_t)k * ld];
-    if (piv == 0.0) {
-      if (threadIdx.x == 0) atomicOr(status, DEV_SINGULAR);
-      continue;
-    }
-    for (int i = k + 1 + threadIdx.x; i < n; i += LU_THREADS) A[(size_t)i + (size_t)k * ld] /= piv;
-    __syncthreads();
-    const int m = n - k - 1;
-    const int64_t items = (int64_t)m * m;
-    for (int64_t t = threadIdx.x; t < items; t += LU_THREADS) {
-      const int i = k + 1 + (int)(t % m), j = k + 1 + (int)(t / m);
-      A[(size_t)i + (size_t)j * ld] -= A[(size_t)i + (size_t)k * ld] * A[(size_t)k + (size_t)j * ld];
+#pragma unroll
+      for (int r = 0; r < LU_NB; ++r)
+        if (r < nb) at(k0 + r, c) = x[r];
     }
     __syncthreads();
+    // 4. A22 -= L21 U12, tiles of LU_TM x LU_TN, 4 x 4 per thread
+    const int m2 = n - c0;
+    const int tx = tid & 15, ty = tid >> 4;
+    for (int tm = 0; tm < m2; tm += LU_TM)
+      for (int tn = 0; tn < m2; tn += LU_TN) {
+        for (int e = tid; e < LU_NB * LU_TM; e += LU_THREADS) {
+          const int r = e % LU_TM, q = e / LU_TM;
+          As[q][r] = (q < nb && tm + r < m2) ? at(c0 + tm + r, k0 + q) : (T)0;
+        }
+        for (int e = tid; e < LU_NB * LU_TN; e += LU_THREADS) {
+          const int q = e % LU_NB, cc = e / LU_NB;
+          Bs[q][cc] = (q < nb && tn + cc < m2) ? at(k0 + q, c0 + tn + cc) : (T)0;
+        }
+        __syncthreads();
+        T acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+#pragma unroll 8
+        for (int q = 0; q < LU_NB; ++q) {
+          T av[4], bv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) av[a] = As[q][tx + 16 * a];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) bv[b] = Bs[q][ty + 16 * b];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int r = tm + tx + 16 * a, cc = tn + ty + 16 * b;
+            if (r < m2 && cc < m2) at(c0 + r, c0 + cc) -= acc[a][b];
+          }
+        __syncthreads();
+      }
   }
 }
 
 // ---------------------------------------------------------------- GETRS
+// Grid (descriptor, chunk of RS_NC right-hand sides).  The chunk lives in shared
+// memory; rows are processed in blocks of 32: a warp solves the 32 x 32 diagonal
+// block for one column with shuffles, then all threads update the rows below
+// (forward) or above (backward) with a register-tiled product.
 constexpr int RS_THREADS = 256;
 
-// Grid: (descriptor, column chunk).  Dynamic shared memory: n * cc doubles.
-__global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDesc* descs, int cc) {
-  extern __shared__ double X[];
-  const LuSolveDesc D = descs[blockIdx.x];
-  const int c0 = blockIdx.y * cc;
+template <typename T, int NC>
+__global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>* descs) {
+  extern __shared__ __align__(16) unsigned char rs_sh[];
+  T* X = reinterpret_cast<T*>(rs_sh);  // n x NC, column-major, ld n
+  const LuSolveDescT<T> D = descs[blockIdx.x];
+  const int c0 = blockIdx.y * NC;
   if (c0 >= D.ncols) return;
-  const int nc = min(cc, D.ncols - c0);
+  const int nc = min(NC, D.ncols - c0);
   const int n = D.n;
-  const double* LU = D.LU;
+  const T* LU = D.LU;
   const int ld = D.ldlu;
-  for (int64_t t = threadIdx.x; t < (int64_t)n * nc; t += RS_THREADS) {
-    const int i = (int)(t % n), c = (int)(t / n);
-    X[(size_t)c * n + i] = D.B[(size_t)i + (size_t)(c0 + c) * D.ldb];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int t = tid; t < n * NC; t += RS_THREADS) {
+    const int i = t % n, c = t / n;
+    X[(size_t)c * n + i] = c < nc ? D.B[(size_t)i + (size_t)(c0 + c) * D.ldb] : (T)0;
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < nc; c += RS_THREADS) {
-    double* x = X + (size_t)c * n;
+  if (tid < nc) {
+    T* x = X + (size_t)tid * n;
     for (int k = 0; k < n; ++k) {
       const int p = D.ipiv[k];
       if (p != k) {
-        double t = x[k];
+        T t = x[k];
         x[k] = x[p];
         x[p] = t;
       }
     }
   }
   __syncthreads();
-  for (int k = 0; k < n - 1; ++k) {  // unit lower triangle
-    const int m = n - k - 1;
-    for (int t = threadIdx.x; t < m * nc; t += RS_THREADS) {
-      const int i = k + 1 + t % m, c = t / m;
-      X[(size_t)c * n + i] -= LU[(size_t)i + (size_t)k * ld] * X[(size_t)c * n + k];
+  // forward substitution with the unit lower triangle
+  for (int b0 = 0; b0 < n; b0 += 32) {
+    const int bs = min(32, n - b0);
+    for (int c = warp; c < nc; c += RS_THREADS / 32) {
+      T x = lane < bs ? X[(size_t)c * n + b0 + lane] : (T)0;
+      for (int k = 0; k < bs - 1; ++k) {
+        const T xk = __shfl_sync(0xffffffffu, x, k);
+        if (lane > k && lane < bs) x -= LU[(size_t)(b0 + lane) + (size_t)(b0 + k) * ld] * xk;
+      }
+      if (lane < bs) X[(size_t)c * n + b0 + lane] = x;
+    }
+    __syncthreads();
+    for (int r = b0 + bs + tid; r < n; r += RS_THREADS) {
+      T acc[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] = 0;
+      for (int k = 0; k < bs; ++k) {
+        const T l = LU[(size_t)r + (size_t)(b0 + k) * ld];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = fma(l, X[(size_t)c * n + b0 + k], acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) X[(size_t)c * n + r] -= acc[c];
     }
     __syncthreads();
   }
-  for (int k = n - 1; k >= 0; --k) {  // upper triangle
-    const double ukk = LU[(size_t)k + (size_t)k * ld];
-    for (int c = threadIdx.x; c < nc; c += RS_THREADS) X[(size_t)c * n + k] /= ukk;
+  // backward substitution with the upper triangle
+  for (int b1 = n; b1 > 0; b1 -= 32) {
+    const int b0 = max(0, b1 - 32), bs = b1 - b0;
+    for (int c = warp; c < nc; c += RS_THREADS / 32) {
+      T x = lane < bs ? X[(size_t)c * n + b0 + lane] : (T)0;
+      for (int k = bs - 1; k >= 0; --k) {
+        if (lane == k) x /= LU[(size_t)(b0 + k) + (size_t)(b0 + k) * ld];
+        const T xk = __shfl_sync(0xffffffffu, x, k);
+        if (lane < k) x -= LU[(size_t)(b0 + lane) + (size_t)(b0 + k) * ld] * xk;
+      }
+      if (lane < bs) X[(size_t)c * n + b0 + lane] = x;
+    }
     __syncthreads();
-    for (int t = threadIdx.x; t < k * nc; t += RS_THREADS) {
-      const int i = t % k, c = t / k;
-      X[(size_t)c * n + i] -= LU[(size_t)i + (size_t)k * ld] * X[(size_t)c * n + k];
+    for (int r = tid; r < b0; r += RS_THREADS) {
+      T acc[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] = 0;
+      for (int k = 0; k < bs; ++k) {
+        const T u = LU[(size_t)r + (size_t)(b0 + k) * ld];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] = fma(u, X[(size_t)c * n + b0 + k], acc[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) X[(size_t)c * n + r] -= acc[c];
     }
     __syncthreads();
   }
-  for (int64_t t = threadIdx.x; t < (int64_t)n * nc; t += RS_THREADS) {
-    const int i = (int)(t % n), c = (int)(t / n);
+  for (int t = tid; t < n * nc; t += RS_THREADS) {
+    const int i = t % n, c = t / n;
     D.B[(size_t)i + (size_t)(c0 + c) * D.ldb] = X[(size_t)c * n + i];
   }
 }
@@ -331,34 +472,35 @@ constexpr int GT = 64;   // tile
 constexpr int GK = 16;   // k step
 constexpr int G_THREADS = 256;
 
-__global__ void __launch_bounds__(G_THREADS) gemm_kernel(const GemmDesc* descs,
+template <typename T>
+__global__ void __launch_bounds__(G_THREADS) gemm_kernel(const GemmDescT<T>* descs,
                                                          const GemmTile* tiles) {
-  __shared__ double As[GK][GT + 1];
-  __shared__ double Bs[GK][GT + 1];
-  const GemmTile T = tiles[blockIdx.x];
-  const GemmDesc D = descs[T.desc];
-  const int m0 = T.tm * GT, n0 = T.tn * GT;
+  __shared__ T As[GK][GT + 1];
+  __shared__ T Bs[GK][GT + 1];
+  const GemmTile Tl = tiles[blockIdx.x];
+  const GemmDescT<T> D = descs[Tl.desc];
+  const int m0 = Tl.tm * GT, n0 = Tl.tn * GT;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
   for (int k0 = 0; k0 < D.K; k0 += GK) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int e = threadIdx.x + r * G_THREADS;  // 0 .. 1023
       const int am = e % GT, ak = e / GT;         // A tile: 64 rows x 16 k
       const int gm = m0 + am, gk = k0 + ak;
-      As[ak][am] = (gm < D.M && gk < D.K) ? D.A[(size_t)gm + (size_t)gk * D.lda] : 0.0;
+      As[ak][am] = (gm < D.M && gk < D.K) ? D.A[(size_t)gm + (size_t)gk * D.lda] : (T)0;
       const int bk = e % GK, bn = e / GK;         // B tile: 16 k x 64 cols
       const int gk2 = k0 + bk, gn = n0 + bn;
-      Bs[bk][bn] = (gk2 < D.K && gn < D.N) ? D.B[(size_t)gk2 + (size_t)gn * D.ldb] : 0.0;
+      Bs[bk][bn] = (gk2 < D.K && gn < D.N) ? D.B[(size_t)gk2 + (size_t)gn * D.ldb] : (T)0;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      double a[4], b[4];
+      T a[4], b[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         a[r] = As[kk][tx + 16 * r];
@@ -371,22 +513,24 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(const GemmDesc* descs,
     }
     __syncthreads();
   }
+  const T alpha = (T)D.alpha, beta = (T)D.beta;
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int gm = m0 + tx + 16 * r, gn = n0 + ty + 16 * c;
       if (gm < D.M && gn < D.N) {
-        double* cp = D.C + (size_t)gm + (size_t)gn * D.ldc;
-        *cp = D.beta == 0.0 ? D.alpha * acc[r][c] : D.alpha * acc[r][c] + D.beta * *cp;
+        T* cp = D.C + (size_t)gm + (size_t)gn * D.ldc;
+        *cp = D.beta == 0.0 ? alpha * acc[r][c] : alpha * acc[r][c] + beta * *cp;
       }
     }
 }
 
 // ---------------------------------------------------------------- small helpers
-__global__ void copy_kernel(const CopyDesc* descs, int ndesc) {
+template <typename T>
+__global__ void copy_kernel(const CopyDescT<T>* descs, int ndesc) {
   for (int q = blockIdx.y; q < ndesc; q += gridDim.y) {
-    const CopyDesc D = descs[q];
+    const CopyDescT<T> D = descs[q];
     const int64_t total = (int64_t)D.rows * D.cols;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -396,17 +540,18 @@ __global__ void copy_kernel(const CopyDesc* descs, int ndesc) {
   }
 }
 
-__global__ void form_Z_kernel(const ZDesc* descs, int ndesc) {
+template <typename T>
+__global__ void form_Z_kernel(const ZDescT<T>* descs, int ndesc) {
   for (int q = blockIdx.y; q < ndesc; q += gridDim.y) {
-    const ZDesc D = descs[q];
+    const ZDescT<T> D = descs[q];
     const int n = D.sl + D.sr;
     const int64_t total = (int64_t)n * n;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
       const int i = (int)(e % n), j = (int)(e / n);
-      double v;
-      if (i < D.sl && j < D.sl) v = (i == j) ? 1.0 : 0.0;
-      else if (i >= D.sl && j >= D.sl) v = (i == j) ? 1.0 : 0.0;
+      T v;
+      if (i < D.sl && j < D.sl) v = (i == j) ? (T)1 : (T)0;
+      else if (i >= D.sl && j >= D.sl) v = (i == j) ? (T)1 : (T)0;
       else if (i < D.sl) v = D.Cl[(size_t)i + (size_t)(j - D.sl) * D.sl];
       else v = D.Cr[(size_t)(i - D.sl) + (size_t)j * D.sr];
       D.Z[(size_t)i + (size_t)j * n] = v;
@@ -414,8 +559,9 @@ __global__ void form_Z_kernel(const ZDesc* descs, int ndesc) {
   }
 }
 
-__global__ void permute_rows_kernel(const double* in, int ldi, double* out, int ldo,
-                                    const int* perm, int N, int ncols, bool scatter) {
+template <typename T>
+__global__ void permute_rows_kernel(const T* in, int ldi, T* out, int ldo, const int* perm, int N,
+                                    int ncols, bool scatter) {
   const int64_t total = (int64_t)N * ncols;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -423,6 +569,17 @@ __global__ void permute_rows_kernel(const double* in, int ldi, double* out, int 
     if (scatter) out[(size_t)perm[p] + (size_t)c * ldo] = in[(size_t)p + (size_t)c * ldi];
     else out[(size_t)p + (size_t)c * ldo] = in[(size_t)perm[p] + (size_t)c * ldi];
   }
+}
+
+__global__ void d2f_kernel(const double* in, float* out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+__global__ void f2d_kernel(const float* in, double* out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
 }
 
 // u_rows += K(x_rows, x_cols) y, one thread per target row, up to MV_R right-hand
@@ -486,88 +643,125 @@ unsigned grid_for(int64_t work, int threads, unsigned cap = 65535u) {
   return (unsigned)std::min<int64_t>(b, cap);
 }
 
-}  // namespace
-
-void kernel_blocks(const double* Xp, int d, double h, const KDesc* descs_dev, int ndesc,
-                   int64_t max_entries, cudaStream_t st) {
-  if (ndesc <= 0) return;
-  dim3 grid(grid_for(max_entries, 256, 4096), std::min(ndesc, 65535));
-  ProfScope _ps(PK_KBLOCK, st);
-  kernel_blocks_kernel<<<grid, 256, 0, st>>>(Xp, d, -1.0 / (2.0 * h * h), descs_dev, ndesc);
+template <typename T, int NC>
+void launch_getrs(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int max_cols,
+                  cudaStream_t st) {
+  const size_t smem = (size_t)max_n * NC * sizeof(T);
+  if (smem > 220 * 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "LU block too large");
+  if (smem > 48 * 1024)
+    IA_CUDA(cudaFuncSetAttribute(getrs_kernel<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  dim3 grid(ndesc, ceil_div(max_cols, NC));
+  getrs_kernel<T, NC><<<grid, RS_THREADS, smem, st>>>(descs_dev);
   IA_LAUNCH_CHECK();
 }
 
-void cpqr_id(const CpqrDesc* descs_dev, int ndesc, int max_rows, int max_cols, int s_max,
+}  // namespace
+
+template <typename T>
+void kernel_blocks(const double* Xp, int d, double h, const KDescT<T>* descs_dev, int ndesc,
+                   int64_t max_entries, cudaStream_t st) {
+  if (ndesc <= 0) return;
+  ProfScope _ps(pk_of<T>(PK_KBLOCK), st);
+  dim3 grid(grid_for(max_entries, 256, 4096), std::min(ndesc, 65535));
+  kernel_blocks_kernel<T><<<grid, 256, 0, st>>>(Xp, d, -1.0 / (2.0 * h * h), descs_dev, ndesc);
+  IA_LAUNCH_CHECK();
+}
+
+template <typename T>
+void cpqr_id(const CpqrDescT<T>* descs_dev, int ndesc, int max_rows, int max_cols, int s_max,
              double tol, cudaStream_t st) {
   if (ndesc <= 0) return;
   const size_t smem = (size_t)(2 * max_cols + max_rows) * sizeof(double);
   if (smem > 220 * 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "ID block too large for one CTA");
   if (smem > 48 * 1024)
-    IA_CUDA(cudaFuncSetAttribute(cpqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ProfScope _ps(PK_CPQR, st);
-  cpqr_kernel<<<ndesc, QR_THREADS, smem, st>>>(descs_dev, s_max, tol);
+    IA_CUDA(cudaFuncSetAttribute(cpqr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ProfScope _ps(pk_of<T>(PK_CPQR), st);
+  cpqr_kernel<T><<<ndesc, QR_THREADS, smem, st>>>(descs_dev, s_max, tol);
   IA_LAUNCH_CHECK();
 }
 
-void assemble_P(const PDesc* descs_dev, int ndesc, int max_cols, cudaStream_t st) {
+template <typename T>
+void assemble_P(const PDescT<T>* descs_dev, int ndesc, int max_cols, cudaStream_t st) {
   if (ndesc <= 0) return;
-  dim3 grid(grid_for((int64_t)max_cols * 64, 256, 1024), ndesc);
   ProfScope _ps(PK_ASSEMBLE_P, st);
-  assemble_P_kernel<<<grid, 256, 0, st>>>(descs_dev, ndesc);
+  dim3 grid(grid_for((int64_t)max_cols * 64, 256, 1024), ndesc);
+  assemble_P_kernel<T><<<grid, 256, 0, st>>>(descs_dev, ndesc);
   IA_LAUNCH_CHECK();
 }
 
-void getrf_batched(const LuDesc* descs_dev, int ndesc, int max_n, int* dev_status, cudaStream_t st) {
+template <typename T>
+void getrf_batched(const LuDescT<T>* descs_dev, int ndesc, int max_n, int* dev_status,
+                   cudaStream_t st) {
   if (ndesc <= 0) return;
   (void)max_n;
-  ProfScope _ps(PK_GETRF, st);
-  getrf_kernel<<<ndesc, LU_THREADS, 0, st>>>(descs_dev, dev_status);
+  ProfScope _ps(pk_of<T>(PK_GETRF), st);
+  getrf_kernel<T><<<ndesc, LU_THREADS, 0, st>>>(descs_dev, dev_status);
   IA_LAUNCH_CHECK();
 }
 
-void getrs_batched(const LuSolveDesc* descs_dev, int ndesc, int max_n, int max_cols,
+template <typename T>
+void getrs_batched(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int max_cols,
                    cudaStream_t st) {
   if (ndesc <= 0 || max_cols <= 0) return;
-  int cc = std::max(1, std::min(max_cols, (int)(16384 / std::max(1, max_n))));
-  const size_t smem = (size_t)max_n * cc * sizeof(double);
-  if (smem > 220 * 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "LU block too large");
-  if (smem > 48 * 1024)
-    IA_CUDA(cudaFuncSetAttribute(getrs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid(ndesc, ceil_div(max_cols, cc));
-  ProfScope _ps(PK_GETRS, st);
-  getrs_kernel<<<grid, RS_THREADS, smem, st>>>(descs_dev, cc);
-  IA_LAUNCH_CHECK();
+  ProfScope _ps(pk_of<T>(PK_GETRS), st);
+  // chunk width: 16 columns while the chunk stays small enough for 3 blocks per SM
+  if (max_cols >= 16 && (size_t)max_n * 16 * sizeof(T) <= 72 * 1024)
+    launch_getrs<T, 16>(descs_dev, ndesc, max_n, max_cols, st);
+  else if (max_cols >= 8 && (size_t)max_n * 8 * sizeof(T) <= 144 * 1024)
+    launch_getrs<T, 8>(descs_dev, ndesc, max_n, max_cols, st);
+  else if (max_cols >= 4)
+    launch_getrs<T, 4>(descs_dev, ndesc, max_n, max_cols, st);
+  else
+    launch_getrs<T, 1>(descs_dev, ndesc, max_n, max_cols, st);
 }
 
-void gemm_grouped(const GemmDesc* descs_dev, const GemmTile* tiles_dev, int ntiles, cudaStream_t st) {
+template <typename T>
+void gemm_grouped(const GemmDescT<T>* descs_dev, const GemmTile* tiles_dev, int ntiles,
+                  cudaStream_t st) {
   if (ntiles <= 0) return;
-  ProfScope _ps(PK_GEMM, st);
-  gemm_kernel<<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
+  ProfScope _ps(pk_of<T>(PK_GEMM), st);
+  gemm_kernel<T><<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
   IA_LAUNCH_CHECK();
 }
 
-void copy_batched(const CopyDesc* descs_dev, int ndesc, int64_t max_entries, cudaStream_t st) {
+template <typename T>
+void copy_batched(const CopyDescT<T>* descs_dev, int ndesc, int64_t max_entries, cudaStream_t st) {
   if (ndesc <= 0) return;
-  dim3 grid(grid_for(max_entries, 256, 1024), std::min(ndesc, 65535));
   ProfScope _ps(PK_MISC, st);
-  copy_kernel<<<grid, 256, 0, st>>>(descs_dev, ndesc);
+  dim3 grid(grid_for(max_entries, 256, 1024), std::min(ndesc, 65535));
+  copy_kernel<T><<<grid, 256, 0, st>>>(descs_dev, ndesc);
   IA_LAUNCH_CHECK();
 }
 
-void form_Z(const ZDesc* descs_dev, int ndesc, int64_t max_entries, cudaStream_t st) {
+template <typename T>
+void form_Z(const ZDescT<T>* descs_dev, int ndesc, int64_t max_entries, cudaStream_t st) {
   if (ndesc <= 0) return;
-  dim3 grid(grid_for(max_entries, 256, 1024), std::min(ndesc, 65535));
   ProfScope _ps(PK_MISC, st);
-  form_Z_kernel<<<grid, 256, 0, st>>>(descs_dev, ndesc);
+  dim3 grid(grid_for(max_entries, 256, 1024), std::min(ndesc, 65535));
+  form_Z_kernel<T><<<grid, 256, 0, st>>>(descs_dev, ndesc);
   IA_LAUNCH_CHECK();
 }
 
-void permute_rows(const double* in, int ldi, double* out, int ldo, const int* perm, int N,
-                  int ncols, bool scatter, cudaStream_t st) {
+template <typename T>
+void permute_rows(const T* in, int ldi, T* out, int ldo, const int* perm, int N, int ncols,
+                  bool scatter, cudaStream_t st) {
   ProfScope _ps(PK_MISC, st);
-  permute_rows_kernel<<<grid_for((int64_t)N * ncols, 256, 8192), 256, 0, st>>>(in, ldi, out, ldo,
-                                                                               perm, N, ncols,
-                                                                               scatter);
+  permute_rows_kernel<T><<<grid_for((int64_t)N * ncols, 256, 8192), 256, 0, st>>>(
+      in, ldi, out, ldo, perm, N, ncols, scatter);
+  IA_LAUNCH_CHECK();
+}
+
+void convert_d2f(const double* in, float* out, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  ProfScope _ps(PK_MISC, st);
+  d2f_kernel<<<grid_for(n, 256, 8192), 256, 0, st>>>(in, out, n);
+  IA_LAUNCH_CHECK();
+}
+void convert_f2d(const float* in, double* out, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  ProfScope _ps(PK_MISC, st);
+  f2d_kernel<<<grid_for(n, 256, 8192), 256, 0, st>>>(in, out, n);
   IA_LAUNCH_CHECK();
 }
 
@@ -578,8 +772,8 @@ void kernel_matvec(const double* Xp, int d, double h, int nrhs, const KMatvecDes
   if (smem > 48 * 1024)
     IA_CUDA(cudaFuncSetAttribute(kernel_matvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
-  dim3 grid(ceil_div(max_rows, MV_THREADS), ndesc);
   ProfScope _ps(PK_MATVEC, st);
+  dim3 grid(ceil_div(max_rows, MV_THREADS), ndesc);
   kernel_matvec_kernel<<<grid, MV_THREADS, smem, st>>>(Xp, d, -1.0 / (2.0 * h * h), nrhs, descs_dev);
   IA_LAUNCH_CHECK();
 }
@@ -590,5 +784,20 @@ void check_finite(const double* x, int64_t n, int* dev_status, cudaStream_t st) 
   check_finite_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(x, n, dev_status);
   IA_LAUNCH_CHECK();
 }
+
+#define IASKIT_INSTANTIATE(T)                                                                    \
+  template void kernel_blocks<T>(const double*, int, double, const KDescT<T>*, int, int64_t,      \
+                                 cudaStream_t);                                                  \
+  template void cpqr_id<T>(const CpqrDescT<T>*, int, int, int, int, double, cudaStream_t);        \
+  template void assemble_P<T>(const PDescT<T>*, int, int, cudaStream_t);                          \
+  template void getrf_batched<T>(const LuDescT<T>*, int, int, int*, cudaStream_t);                \
+  template void getrs_batched<T>(const LuSolveDescT<T>*, int, int, int, cudaStream_t);            \
+  template void gemm_grouped<T>(const GemmDescT<T>*, const GemmTile*, int, cudaStream_t);         \
+  template void copy_batched<T>(const CopyDescT<T>*, int, int64_t, cudaStream_t);                 \
+  template void form_Z<T>(const ZDescT<T>*, int, int64_t, cudaStream_t);                          \
+  template void permute_rows<T>(const T*, int, T*, int, const int*, int, int, bool, cudaStream_t);
+IASKIT_INSTANTIATE(double)
+IASKIT_INSTANTIATE(float)
+#undef IASKIT_INSTANTIATE
 
 }  // namespace iaskit

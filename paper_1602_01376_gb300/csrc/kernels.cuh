@@ -68,37 +68,47 @@ void sample_level(const int* knn_pos, int N, int kappa, int level, const int* of
                   uint64_t seed, int* samp, int* dev_status, SampleScratch& s, cudaStream_t st);
 
 // ------------------------------------------------------- dense batched kernels
+// All dense kernels are templated on the storage/arithmetic type T (double for
+// the plain FP64 path, float for the mixed-precision form).
+
 // Kernel block K(x_rows, x_cols) (+ diag where the row and column positions agree),
 // column-major into out.  Rows: rows ? rows[i] : row0 + i.  Columns: colsA ?
 // (j < nA ? colsA[j] : colsB[j - nA]) : col0 + j.  Points are positions in Xp.
-struct KDesc {
+// T = double evaluates in FP64; T = float evaluates distances and exp in FP32.
+template <typename T>
+struct KDescT {
   const int* rows;
   const int* colsA;
   const int* colsB;
-  double* out;
+  T* out;
   int row0, nrows, col0, nA, ncols, ld;
   double diag;
 };
-void kernel_blocks(const double* Xp, int d, double h, const KDesc* descs_dev, int ndesc,
+template <typename T>
+void kernel_blocks(const double* Xp, int d, double h, const KDescT<T>* descs_dev, int ndesc,
                    int64_t max_entries_per_desc, cudaStream_t st);
 
 // Column-pivoted Householder QR + interpolative decomposition of each block.
 // A (nrows x ncols, ld) is overwritten: its first s rows hold, in pivoted column
 // order, R11 and T = R11^{-1} R12 in place of R12.  piv receives the column
-// permutation; rank[0] receives s.
-struct CpqrDesc {
-  double* A;
+// permutation; rank[0] receives s.  Column norms are accumulated in FP64 for both
+// T, so pivot decisions are taken in FP64.
+template <typename T>
+struct CpqrDescT {
+  T* A;
   int* piv;
   int* rank;
   int ld, nrows, ncols;
 };
-void cpqr_id(const CpqrDesc* descs_dev, int ndesc, int max_rows, int max_cols, int s_max,
+template <typename T>
+void cpqr_id(const CpqrDescT<T>* descs_dev, int ndesc, int max_rows, int max_cols, int s_max,
              double tol, cudaStream_t st);
 
-// Builds P (s x ncols, ld = s) from a cpqr_id result and the skeleton list
-// skel[k] = cols[piv[k]] with cols as in KDesc (colsA/colsB/col0).
-struct PDesc {
-  const double* A;  // cpqr output (ld)
+// Builds P (s x ncols, ld = s, FP64) from a cpqr_id result and the skeleton list
+// skel[k] = cols[piv[k]] with cols as in KDescT (colsA/colsB/col0).
+template <typename T>
+struct PDescT {
+  const T* A;  // cpqr output (ld)
   const int* piv;
   const int* colsA;
   const int* colsB;
@@ -106,32 +116,39 @@ struct PDesc {
   int* skel;
   int ld, ncols, s, nA, col0;
 };
-void assemble_P(const PDesc* descs_dev, int ndesc, int max_cols, cudaStream_t st);
+template <typename T>
+void assemble_P(const PDescT<T>* descs_dev, int ndesc, int max_cols, cudaStream_t st);
 
-// LU with partial pivoting (ties to the lowest row) of each n x n block in place.
-struct LuDesc {
-  double* A;
+// LU with partial pivoting (ties to the lowest row) of each n x n block in place,
+// blocked (panel width 32, register-tiled trailing update), one CTA per matrix.
+template <typename T>
+struct LuDescT {
+  T* A;
   int* ipiv;
   int n, ld;
 };
-void getrf_batched(const LuDesc* descs_dev, int ndesc, int max_n, int* dev_status,
+template <typename T>
+void getrf_batched(const LuDescT<T>* descs_dev, int ndesc, int max_n, int* dev_status,
                    cudaStream_t st);
 
 // B <- A^{-1} B from getrf output, for each descriptor; B is n x ncols (ldb).
-struct LuSolveDesc {
-  const double* LU;
+template <typename T>
+struct LuSolveDescT {
+  const T* LU;
   const int* ipiv;
-  double* B;
+  T* B;
   int n, ldlu, ldb, ncols;
 };
-void getrs_batched(const LuSolveDesc* descs_dev, int ndesc, int max_n, int max_cols,
+template <typename T>
+void getrs_batched(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int max_cols,
                    cudaStream_t st);
 
 // C <- alpha * A * B + beta * C (column-major, no transposes) for each descriptor.
-struct GemmDesc {
-  const double* A;
-  const double* B;
-  double* C;
+template <typename T>
+struct GemmDescT {
+  const T* A;
+  const T* B;
+  T* C;
   int M, N, K, lda, ldb, ldc;
   double alpha, beta;
 };
@@ -139,30 +156,49 @@ struct GemmDesc {
 struct GemmTile {
   int desc, tm, tn;
 };
-void gemm_grouped(const GemmDesc* descs_dev, const GemmTile* tiles_dev, int ntiles,
+template <typename T>
+void gemm_grouped(const GemmDescT<T>* descs_dev, const GemmTile* tiles_dev, int ntiles,
                   cudaStream_t st);
 
 // dst (rows x cols, ldd) <- src (rows x cols, lds), batched.
-struct CopyDesc {
-  const double* src;
-  double* dst;
+template <typename T>
+struct CopyDescT {
+  const T* src;
+  T* dst;
   int rows, cols, lds, ldd;
 };
-void copy_batched(const CopyDesc* descs_dev, int ndesc, int64_t max_entries, cudaStream_t st);
+template <typename T>
+void copy_batched(const CopyDescT<T>* descs_dev, int ndesc, int64_t max_entries, cudaStream_t st);
 
 // Z'' = [[I, C_l], [C_r, I]] of size (s_l + s_r), ld = s_l + s_r.
-struct ZDesc {
-  const double* Cl;  // s_l x s_r, ld s_l
-  const double* Cr;  // s_r x s_l, ld s_r
-  double* Z;
+template <typename T>
+struct ZDescT {
+  const T* Cl;  // s_l x s_r, ld s_l
+  const T* Cr;  // s_r x s_l, ld s_r
+  T* Z;
   int sl, sr;
 };
-void form_Z(const ZDesc* descs_dev, int ndesc, int64_t max_entries, cudaStream_t st);
+template <typename T>
+void form_Z(const ZDescT<T>* descs_dev, int ndesc, int64_t max_entries, cudaStream_t st);
+
+using KDesc = KDescT<double>;
+using CpqrDesc = CpqrDescT<double>;
+using PDesc = PDescT<double>;
+using LuDesc = LuDescT<double>;
+using LuSolveDesc = LuSolveDescT<double>;
+using GemmDesc = GemmDescT<double>;
+using CopyDesc = CopyDescT<double>;
+using ZDesc = ZDescT<double>;
+
+// Elementwise conversions between FP64 and FP32 buffers.
+void convert_d2f(const double* in, float* out, int64_t n, cudaStream_t st);
+void convert_f2d(const float* in, double* out, int64_t n, cudaStream_t st);
 
 // Row permutation of an N x ncols column-major block: out[p] = in[perm[p]] (gather)
 // or out[perm[p]] = in[p] (scatter).
-void permute_rows(const double* in, int ldi, double* out, int ldo, const int* perm, int N,
-                  int ncols, bool scatter, cudaStream_t st);
+template <typename T>
+void permute_rows(const T* in, int ldi, T* out, int ldo, const int* perm, int N, int ncols,
+                  bool scatter, cudaStream_t st);
 
 // u_rows += K(x_rows, x_cols) * y for each descriptor, kernel values recomputed in
 // FP64.  y is ncols x nrhs (ldy), u is nrows x nrhs (ldu) with rows starting at row0.

@@ -23,8 +23,27 @@ enum ProfKind {
   PK_GEMM,
   PK_MATVEC,
   PK_MISC,
+  PK_KBLOCK32,   // FP32 variants of the dense kernels (mixed-precision form)
+  PK_CPQR32,
+  PK_GETRF32,
+  PK_GETRS32,
+  PK_GEMM32,
   PK_COUNT
 };
+
+// The FP32 class of a dense kernel class when T is float.
+template <typename T>
+inline int pk_of(int kind) {
+  if (sizeof(T) != 4) return kind;
+  switch (kind) {
+    case PK_KBLOCK: return PK_KBLOCK32;
+    case PK_CPQR: return PK_CPQR32;
+    case PK_GETRF: return PK_GETRF32;
+    case PK_GETRS: return PK_GETRS32;
+    case PK_GEMM: return PK_GEMM32;
+    default: return kind;
+  }
+}
 
 const char* prof_name(int kind);
 
