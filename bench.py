@@ -59,6 +59,8 @@ class ClockSampler:
         self.lines = []
 
     def __enter__(self):
+        if self.gpu < 0:
+            return self
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -166,6 +168,19 @@ def config_of(w):
 
 
 # ------------------------------------------------------------------- GPU leg
+FP32_LANES_PER_SM = 128              # GB300: FP32 FMA lanes per SM
+PEAK_CLASS = {                       # kernel classes whose arithmetic is FP32
+    "kernel_blocks_f32", "cpqr_id_f32", "getrf_f32", "getrs_f32", "gemm_f32"}
+
+
+def alu_peak_tflops(kernel: str, sm_mhz: float) -> tuple:
+    if kernel in PEAK_CLASS:
+        return (SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12,
+                f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 FMA/clk x {sm_mhz:.0f} MHz")
+    return (SM_COUNT * FP64_FMA_PER_CLK_PER_SM * 2 * sm_mhz * 1e6 / 1e12,
+            f"derived: {SM_COUNT} SMs x {FP64_FMA_PER_CLK_PER_SM} FP64 FMA/clk x {sm_mhz:.0f} MHz")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -173,6 +188,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="C2")
+    ap.add_argument("--form", choices=["mixed", "fp64"], default="mixed",
+                    help="form timed for the headline value (mixed = the chosen form)")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other form")
     ap.add_argument("--N", type=int, default=None, help="override N (testing only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -196,6 +214,13 @@ def main():
         if dist is not None:
             dist.barrier()
 
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
     ia.load()
     ia.iaskit_set_stream(None)                     # legacy default stream = torch's default
     X = torch.from_numpy(make_points(w)).cuda()
@@ -203,42 +228,47 @@ def main():
     U = torch.empty_like(U0)
     args_f = (w.h, w.lam, w.m, w.s_max, w.tol)
 
+    def set_form(form):
+        ia.iaskit_set_option("precision", 1 if form == "mixed" else 0)
+        ia.iaskit_set_option("refine", 50 if form == "mixed" else 0)
+        ia.iaskit_set_option("refine_tol", 1e-10)
+
     def step():
         ia.iaskit_factor_device(X, *args_f)
         U.copy_(U0)
         ia.iaskit_solve_device(U)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    # residual of the last warm-up solve against the FP64 hierarchical operator
-    AU = torch.empty_like(U)
-    ia.iaskit_apply_device(U, AU)
-    resid = float(((U0 - AU).norm(dim=1) / U0.norm(dim=1)).max())
-
-    ia.iaskit_set_option("profile", 1)
-    launches0 = ia.iaskit_stats()["launches"]
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        ev0.record()
-        for _ in range(args.steps):
+    def measure(form, sample_clocks):
+        set_form(form)
+        for _ in range(args.warmup):
             step()
-        ev1.record()
         torch.cuda.synchronize()
-    barrier()
-    ms = ev0.elapsed_time(ev1)
-    stats = ia.iaskit_stats()
-    ia.iaskit_set_option("profile", 0)
-    launches = stats["launches"] - launches0
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * w.nrhs * args.steps / (ms / 1e3)
-    factor_ms = stats["ms"]["factor"]
-    solve_ms = stats["ms"]["solve"]
+        AU = torch.empty_like(U)
+        ia.iaskit_apply_device(U, AU)             # residual against the FP64 operator
+        resid = float(((U0 - AU).norm(dim=1) / U0.norm(dim=1)).max())
+        ia.iaskit_set_option("profile", 1)
+        launches0 = ia.iaskit_stats()["launches"]
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local if sample_clocks else -1) as clk:
+            ev0.record()
+            for _ in range(args.steps):
+                step()
+            ev1.record()
+            torch.cuda.synchronize()
+        barrier()
+        ms = max_over_ranks(ev0.elapsed_time(ev1))
+        stats = ia.iaskit_stats()
+        ia.iaskit_set_option("profile", 0)
+        return {"ms": ms, "stats": stats, "resid": resid, "clocks": clk.summary(),
+                "launches": stats["launches"] - launches0}
+
+    chosen = measure(args.form, True)
+    other_form = "fp64" if args.form == "mixed" else "mixed"
+    other = None if args.no_compare else measure(other_form, False)
+    set_form(args.form)
+    value = world * w.nrhs * args.steps / (chosen["ms"] / 1e3)
 
     # end to end through the host API: pinned host inputs in, solution out
     Xh = torch.from_numpy(make_points(w)).pin_memory()
@@ -260,40 +290,50 @@ def main():
             raise RuntimeError(ia.iaskit_last_error())
         Uh.copy_(U_src)                            # restore the right-hand sides
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e_value = world * w.nrhs * e2e_steps / e2e_s
 
     if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
         return 0
     pk, src = peaks()
-    # dominant kernel class by device time inside the timed region
-    kern = stats["kernels"]
+    kern = chosen["stats"]["kernels"]
     top = max(kern, key=lambda k: kern[k]["ms"])
-    clocks = clk.summary()
+    clocks = chosen["clocks"]
     roof = None
     if kern[top]["flops"] > 0 and kern[top]["ms"] > 0:
         achieved = kern[top]["flops"] / (kern[top]["ms"] / 1e3) / 1e12      # TFLOP/s
-        peak = SM_COUNT * FP64_FMA_PER_CLK_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        peak, how = alu_peak_tflops(top, pk.get("sm_max_mhz", 2070.0))
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "kernel": top,
-                "peak_source": f"derived: {SM_COUNT} SMs x {FP64_FMA_PER_CLK_PER_SM} FP64 FMA/clk x "
-                               f"{pk.get('sm_max_mhz', 2070.0):.0f} MHz ({src} clock)",
+                "peak_source": f"{how} ({src} max clock)",
                 "launches": kern[top]["calls"], "ms_total": kern[top]["ms"]}
+    st = chosen["stats"]
+    cfg = config_of(w)
+    cfg["path"] = ("mixed: FP32 factorization, FP64 pivots and operator, refined to 1e-10"
+                   if args.form == "mixed" else "plain FP64")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": config_of(w),
-        "factor_s": factor_ms / 1e3, "solve_rhs_per_s": w.nrhs / (solve_ms / 1e3),
-        "residual": resid, "gpu_launches": launches, "clocks": clocks, "roofline": roof,
-        "kernel_ms_per_step": {k: v["ms"] / args.steps for k, v in kern.items() if v["ms"] > 0},
+        "warmup": args.warmup, "ms_per_step": chosen["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.form == "mixed" else "f64", "data": "synthetic",
+        "config": cfg,
+        "factor_s": st["ms"]["factor"] / 1e3, "solve_rhs_per_s": w.nrhs / (st["ms"]["solve"] / 1e3),
+        "residual": chosen["resid"], "refine_sweeps": st.get("refine_sweeps"),
+        "gpu_launches": chosen["launches"], "clocks": clocks, "roofline": roof,
+        "kernel_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in kern.items() if v["ms"] > 0},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * w.N * (w.d + w.nrhs), "d2h_bytes_per_step": 8 * w.N * w.nrhs},
     }
+    if other is not None:
+        so = other["stats"]
+        line["compare_" + other_form] = {
+            "value": world * w.nrhs * args.steps / (other["ms"] / 1e3),
+            "ms_per_step": other["ms"] / args.steps, "factor_s": so["ms"]["factor"] / 1e3,
+            "solve_rhs_per_s": w.nrhs / (so["ms"]["solve"] / 1e3), "residual": other["resid"],
+            "kernel_ms_per_step": {k: round(v["ms"] / args.steps, 3)
+                                   for k, v in so["kernels"].items() if v["ms"] > 0}}
     if not args.no_cpu_baseline:
         res = cpu_baseline_subprocess(w.name, CPU_SAMPLE_N, w.nrhs, 1)
         if "times" in res:

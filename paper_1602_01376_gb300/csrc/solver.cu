@@ -20,12 +20,21 @@
 // The reduced system is stored with blocks in the order [a~ part; b~ part]:
 // Z'' = [[I, C_a], [C_b, I]] acting on [y2; y1] with right side [t_a; t_b]; it is
 // the paper's [[I, C_b], [C_a, I]] with both block rows and block columns swapped.
+//
+// Two precisions:
+//  * plain: everything in FP64;
+//  * mixed: the factorization (sampled blocks, CPQR updates, leaf LU, W, C, Z) in
+//    FP32 with FP64 pivot norms in the CPQR; the operator lambda I + K~ is kept in
+//    FP64 (leaf blocks and U blocks evaluated once in FP64 and stored, P in FP64),
+//    and the solve refines w += Solve32(u - (lambda I + K~) w) until the relative
+//    residual of every column is below the target.  K~ is the one defined by the
+//    skeletons and P this factorization chose, so the FP32 factorization is an
+//    approximate inverse of exactly the operator the residual uses.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
-#include <cstdarg>
 #include <memory>
-#include <mutex>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -52,6 +61,8 @@ struct Arena {
   void clear() { host.clear(); }
 };
 
+enum Precision { PREC_FP64 = 0, PREC_MIXED = 1 };
+
 struct Options {
   int kappa = 16;
   int samp_factor = 2;
@@ -59,6 +70,7 @@ struct Options {
   int refine = 0;
   double refine_tol = 1e-10;
   double mem_cap_gb = 0.0;
+  int precision = PREC_FP64;
 };
 
 struct Node {
@@ -74,20 +86,50 @@ struct Stats {
   double t_tree = 0, t_knn = 0, t_skel = 0, t_leaf_lu = 0, t_factor_levels = 0, t_factor = 0;
   double t_solve = 0, t_apply = 0;
   int knn_fallback = 0;
-  double flops_W = 0, flops_solve = 0;
-  int64_t bytes_W = 0, bytes_LU = 0, bytes_P = 0;
+  int64_t bytes_W = 0, bytes_LU = 0, bytes_P = 0, bytes_operator = 0;
   std::vector<double> refine_hist;
   int refine_sweeps = 0;
 };
 
+template <typename T>
 struct RootBlock {
   int uid;
-  double* V;
+  T* V;
   int ld;
   int nc;
-  double* t_out;  // P_c v_c destination when the caller needs it (may be null)
+  T* t_out;  // P_c v_c destination when the caller needs it (may be null)
   int t_ld;
 };
+
+template <typename T>
+double gemm_flops(const std::vector<GemmDescT<T>>& g) {
+  double f = 0;
+  for (const auto& d : g) f += 2.0 * d.M * (double)d.N * d.K;
+  return f;
+}
+template <typename T>
+double getrs_flops(const std::vector<LuSolveDescT<T>>& v) {
+  double f = 0;
+  for (const auto& d : v) f += 2.0 * d.n * (double)d.n * d.ncols;
+  return f;
+}
+template <typename T>
+double getrf_flops(const std::vector<LuDescT<T>>& v) {
+  double f = 0;
+  for (const auto& d : v) f += 2.0 / 3.0 * d.n * (double)d.n * d.n;
+  return f;
+}
+template <typename T>
+void add_gemm(std::vector<GemmDescT<T>>& g, std::vector<GemmTile>& t, const T* A, int lda,
+              const T* B, int ldb, T* C, int ldc, int M, int Ncol, int K, double alpha,
+              double beta) {
+  if (M <= 0 || Ncol <= 0) return;
+  GemmDescT<T> D{A, B, C, M, Ncol, K, lda, ldb, ldc, alpha, beta};
+  int idx = (int)g.size();
+  g.push_back(D);
+  for (int tn = 0; tn < (Ncol + 63) / 64; ++tn)
+    for (int tm = 0; tm < (M + 63) / 64; ++tm) t.push_back(GemmTile{idx, tm, tn});
+}
 
 class Solver {
  public:
@@ -95,26 +137,43 @@ class Solver {
   Options opt;
   Stats stats;
   bool factored = false;
+  int prec = PREC_FP64;  // precision of the current factorization
   int N = 0, d = 0, L = 0, m_max = 0, s_max = 0, kappa = 0;
   double h = 0, lam = 0, tol = 0;
   std::vector<std::vector<int>> level_off;
   std::vector<Node> nd;  // heap ids 1 .. 2^(L+1) - 1
-  DevBuf X, Xp, perm, iperm, split_dim, knn, knn_pos, samp, ranks, skel, piv_ws, A_ws, LU, LUpiv,
-      Wb, Zb, Zpiv, Cb, status, arena_dev, level_off_dev, samp_off_dev, tbuf, vbuf, ubuf, rbuf,
-      wt, io, cpqr_rank, normbuf;
-  std::vector<std::unique_ptr<DevBuf>> Pl;  // nested P per level
+  DevBuf X, Xp, perm, iperm, split_dim, knn, knn_pos, samp, ranks, skel, piv_ws, A_ws, status,
+      arena_dev, level_off_dev, tbuf, vbuf, vbuf32, ubuf, rbuf, wt, io, normbuf;
+  // factorization storage: FP64 (plain) and FP32 (mixed)
+  DevBuf LU, LUpiv, Wb, Zb, Zpiv, Cb, LU32, Wb32, Zb32, Cb32, tbuf32;
+  // FP64 operator blocks kept by the mixed form: leaf blocks lambda I + K_aa and U blocks
+  DevBuf Kleaf, Ustore;
+  std::vector<std::unique_ptr<DevBuf>> Pl, Pl32;  // nested P per level (FP64; FP32 copy)
   TreeScratch tree_s;
   KnnScratch knn_s;
   SampleScratch samp_s;
   Arena arena;
 
   int uid(int l, int i) const { return (1 << l) + i; }
-  bool is_leaf_uid(int u) const { return u >= (1 << L); }
   int level_of(int u) const {
     int l = 0;
     while ((2 << l) <= u) ++l;
     return l;
   }
+
+  // typed views of the factorization storage
+  template <typename T>
+  T* luP() { return std::is_same<T, float>::value ? (T*)LU32.p : (T*)LU.p; }
+  template <typename T>
+  T* wP() { return std::is_same<T, float>::value ? (T*)Wb32.p : (T*)Wb.p; }
+  template <typename T>
+  T* zP() { return std::is_same<T, float>::value ? (T*)Zb32.p : (T*)Zb.p; }
+  template <typename T>
+  T* cP() { return std::is_same<T, float>::value ? (T*)Cb32.p : (T*)Cb.p; }
+  template <typename T>
+  T* pP(int l) { return std::is_same<T, float>::value ? (T*)Pl32[l]->p : (T*)Pl[l]->p; }
+  template <typename T>
+  DevBuf& tB() { return std::is_same<T, float>::value ? tbuf32 : tbuf; }
 
   // ---------------------------------------------------------------- helpers
   char* upload_arena() {
@@ -139,50 +198,25 @@ class Solver {
     if (v & DEV_TIMEOUT) throw Error(IASKIT_ERR_TIMEOUT, "bounded device wait expired");
     if (v & DEV_OVERFLOW) throw Error(IASKIT_ERR_UNSUPPORTED, "internal bound exceeded");
   }
-
-  static double gemm_flops(const std::vector<GemmDesc>& g) {
-    double f = 0;
-    for (const GemmDesc& d : g) f += 2.0 * d.M * (double)d.N * d.K;
-    return f;
-  }
-  static double getrs_flops(const std::vector<LuSolveDesc>& v) {
-    double f = 0;
-    for (const LuSolveDesc& d : v) f += 2.0 * d.n * (double)d.n * d.ncols;
-    return f;
-  }
-  static double getrf_flops(const std::vector<LuDesc>& v) {
-    double f = 0;
-    for (const LuDesc& d : v) f += 2.0 / 3.0 * d.n * (double)d.n * d.n;
-    return f;
-  }
-
-  static void add_gemm(std::vector<GemmDesc>& g, std::vector<GemmTile>& t, const double* A, int lda,
-                       const double* B, int ldb, double* C, int ldc, int M, int Ncol, int K,
-                       double alpha, double beta) {
-    if (M <= 0 || Ncol <= 0) return;
-    GemmDesc D{A, B, C, M, Ncol, K, lda, ldb, ldc, alpha, beta};
-    int idx = (int)g.size();
-    g.push_back(D);
-    for (int tn = 0; tn < (Ncol + 63) / 64; ++tn)
-      for (int tm = 0; tm < (M + 63) / 64; ++tm) t.push_back(GemmTile{idx, tm, tn});
-  }
-  void run_gemms(const std::vector<GemmDesc>& g, const std::vector<GemmTile>& t) {
+  template <typename T>
+  void run_gemms(const std::vector<GemmDescT<T>>& g, const std::vector<GemmTile>& t) {
     if (t.empty()) return;
     arena.clear();
     size_t og = arena.push(g), ot = arena.push(t);
     char* base = upload_arena();
-    prof().flops[PK_GEMM] += gemm_flops(g);
-    gemm_grouped((const GemmDesc*)(base + og), (const GemmTile*)(base + ot), (int)t.size(), st);
+    prof().flops[pk_of<T>(PK_GEMM)] += gemm_flops(g);
+    gemm_grouped((const GemmDescT<T>*)(base + og), (const GemmTile*)(base + ot), (int)t.size(), st);
   }
 
   // ------------------------------------------------------------- forest solve
   // Applies (lambda I + K~_cc)^{-1} to the block of every root c at level r, in
-  // place.  Writes P_c v_c to roots[].t_out when given.
-  void forest_solve(int r, const std::vector<RootBlock>& roots) {
+  // place, with the factorization stored in precision T.  Writes P_c v_c to
+  // roots[].t_out when given.
+  template <typename T>
+  void forest_solve(int r, const std::vector<RootBlock<T>>& roots) {
     const bool need_t = !roots.empty() && roots[0].t_out != nullptr;
-    // per node: root index
     std::vector<int> root_of(nd.size(), -1);
-    std::vector<double*> Vp(nd.size(), nullptr);
+    std::vector<T*> Vp(nd.size(), nullptr);
     int max_nc = 0;
     for (size_t q = 0; q < roots.size(); ++q) {
       max_nc = std::max(max_nc, roots[q].nc);
@@ -207,38 +241,38 @@ class Solver {
         Toff[u] = tsz;
         tsz += 2 * (int64_t)n2 * roots[root_of[u]].nc;
       }
-    double* T = tbuf.ensure_n<double>(std::max<int64_t>(tsz, 1));
-    auto Tp = [&](int u) { return T + Toff[u]; };
+    T* Tb = tB<T>().template ensure_n<T>(std::max<int64_t>(tsz, 1));
+    auto Tp = [&](int u) { return Tb + Toff[u]; };
     auto Yp = [&](int u) {
       int n2 = nd[2 * u].s + nd[2 * u + 1].s;
-      return T + Toff[u] + (int64_t)n2 * roots[root_of[u]].nc;
+      return Tb + Toff[u] + (int64_t)n2 * roots[root_of[u]].nc;
     };
     auto ldV = [&](int u) { return roots[root_of[u]].ld; };
     auto ncV = [&](int u) { return roots[root_of[u]].nc; };
 
     // 1. leaf LU solves
     {
-      std::vector<LuSolveDesc> ds;
+      std::vector<LuSolveDescT<T>> ds;
       for (int i = 0; i < (1 << L); ++i) {
         int u = uid(L, i);
         if (root_of[u] < 0) continue;
-        ds.push_back(LuSolveDesc{LU.as<double>() + nd[u].LU_off, LUpiv.as<int>() + (int64_t)i * m_max,
-                                 Vp[u], nd[u].size, nd[u].size, ldV(u), ncV(u)});
+        ds.push_back(LuSolveDescT<T>{luP<T>() + nd[u].LU_off, LUpiv.as<int>() + (int64_t)i * m_max,
+                                     Vp[u], nd[u].size, nd[u].size, ldV(u), ncV(u)});
       }
       arena.clear();
       size_t o = arena.push(ds);
       char* base = upload_arena();
-      prof().flops[PK_GETRS] += getrs_flops(ds);
-      getrs_batched((const LuSolveDesc*)(base + o), (int)ds.size(), m_max, max_nc, st);
+      prof().flops[pk_of<T>(PK_GETRS)] += getrs_flops(ds);
+      getrs_batched((const LuSolveDescT<T>*)(base + o), (int)ds.size(), m_max, max_nc, st);
     }
     if (r == L) {
       if (need_t) {
-        std::vector<GemmDesc> g;
+        std::vector<GemmDescT<T>> g;
         std::vector<GemmTile> t;
-        for (const RootBlock& rb : roots) {
+        for (const auto& rb : roots) {
           const Node& c = nd[rb.uid];
-          add_gemm(g, t, Pl[L]->as<double>() + c.P_off, c.s, rb.V, rb.ld, rb.t_out, rb.t_ld, c.s,
-                   rb.nc, c.size, 1.0, 0.0);
+          add_gemm<T>(g, t, pP<T>(L) + c.P_off, c.s, rb.V, rb.ld, rb.t_out, rb.t_ld, c.s, rb.nc,
+                      c.size, 1.0, 0.0);
         }
         run_gemms(g, t);
       }
@@ -246,7 +280,7 @@ class Solver {
     }
     // 2. leaf t = P v into the parent's T
     {
-      std::vector<GemmDesc> g;
+      std::vector<GemmDescT<T>> g;
       std::vector<GemmTile> t;
       for (int i = 0; i < (1 << L); ++i) {
         int u = uid(L, i);
@@ -254,16 +288,16 @@ class Solver {
         int par = u >> 1;
         int n2 = nd[2 * par].s + nd[2 * par + 1].s;
         int rowoff = (u & 1) ? nd[2 * par].s : 0;
-        add_gemm(g, t, Pl[L]->as<double>() + nd[u].P_off, nd[u].s, Vp[u], ldV(u), Tp(par) + rowoff,
-                 n2, nd[u].s, ncV(u), nd[u].size, 1.0, 0.0);
+        add_gemm<T>(g, t, pP<T>(L) + nd[u].P_off, nd[u].s, Vp[u], ldV(u), Tp(par) + rowoff, n2,
+                    nd[u].s, ncV(u), nd[u].size, 1.0, 0.0);
       }
       run_gemms(g, t);
     }
     // 3. levels L-1 .. r
     for (int j = L - 1; j >= r; --j) {
-      std::vector<CopyDesc> cp;
-      std::vector<LuSolveDesc> zs;
-      std::vector<GemmDesc> g1, g2;
+      std::vector<CopyDescT<T>> cp;
+      std::vector<LuSolveDescT<T>> zs;
+      std::vector<GemmDescT<T>> g1, g2;
       std::vector<GemmTile> t1, t2;
       int64_t max_cp = 0;
       int max_n2 = 0;
@@ -274,21 +308,21 @@ class Solver {
         int sa = nd[a].s, sc = nd[c].s, n2 = sa + sc, nc = ncV(b);
         max_n2 = std::max(max_n2, n2);
         max_cp = std::max<int64_t>(max_cp, (int64_t)n2 * nc);
-        cp.push_back(CopyDesc{Tp(b), Yp(b), n2, nc, n2, n2});
-        zs.push_back(LuSolveDesc{Zb.as<double>() + nd[b].Z_off, Zpiv.as<int>() + nd[b].Zpiv_off,
-                                 Yp(b), n2, n2, n2, nc});
-        const double* W = Wb.as<double>();
+        cp.push_back(CopyDescT<T>{Tp(b), Yp(b), n2, nc, n2, n2});
+        zs.push_back(LuSolveDescT<T>{zP<T>() + nd[b].Z_off, Zpiv.as<int>() + nd[b].Zpiv_off, Yp(b),
+                                     n2, n2, n2, nc});
+        const T* W = wP<T>();
         // v_a -= W_{a c~} y1 (y1 = Y[sa : n2]);  v_c -= W_{c a~} y2 (y2 = Y[0 : sa])
-        add_gemm(g1, t1, W + nd[a].W_off, nd[a].size, Yp(b) + sa, n2, Vp[a], ldV(b), nd[a].size, nc,
-                 sc, -1.0, 1.0);
-        add_gemm(g1, t1, W + nd[c].W_off, nd[c].size, Yp(b), n2, Vp[c], ldV(b), nd[c].size, nc, sa,
-                 -1.0, 1.0);
+        add_gemm<T>(g1, t1, W + nd[a].W_off, nd[a].size, Yp(b) + sa, n2, Vp[a], ldV(b), nd[a].size,
+                    nc, sc, -1.0, 1.0);
+        add_gemm<T>(g1, t1, W + nd[c].W_off, nd[c].size, Yp(b), n2, Vp[c], ldV(b), nd[c].size, nc,
+                    sa, -1.0, 1.0);
         const bool carry = (j > r) || need_t;
         if (carry) {
-          const double* C = Cb.as<double>();
-          add_gemm(g1, t1, C + nd[b].CL_off, sa, Yp(b) + sa, n2, Tp(b), n2, sa, nc, sc, -1.0, 1.0);
-          add_gemm(g1, t1, C + nd[b].CR_off, sc, Yp(b), n2, Tp(b) + sa, n2, sc, nc, sa, -1.0, 1.0);
-          double* dst;
+          const T* C = cP<T>();
+          add_gemm<T>(g1, t1, C + nd[b].CL_off, sa, Yp(b) + sa, n2, Tp(b), n2, sa, nc, sc, -1.0, 1.0);
+          add_gemm<T>(g1, t1, C + nd[b].CR_off, sc, Yp(b), n2, Tp(b) + sa, n2, sc, nc, sa, -1.0, 1.0);
+          T* dst;
           int ldd;
           if (j > r) {
             int par = b >> 1;
@@ -299,20 +333,20 @@ class Solver {
             dst = roots[root_of[b]].t_out;
             ldd = roots[root_of[b]].t_ld;
           }
-          add_gemm(g2, t2, Pl[j]->as<double>() + nd[b].P_off, nd[b].s, Tp(b), n2, dst, ldd, nd[b].s,
-                   nc, n2, 1.0, 0.0);
+          add_gemm<T>(g2, t2, pP<T>(j) + nd[b].P_off, nd[b].s, Tp(b), n2, dst, ldd, nd[b].s, nc, n2,
+                      1.0, 0.0);
         }
       }
       arena.clear();
       size_t ocp = arena.push(cp), ozs = arena.push(zs), og1 = arena.push(g1), ot1 = arena.push(t1),
              og2 = arena.push(g2), ot2 = arena.push(t2);
       char* base = upload_arena();
-      prof().flops[PK_GETRS] += getrs_flops(zs);
-      prof().flops[PK_GEMM] += gemm_flops(g1) + gemm_flops(g2);
-      copy_batched((const CopyDesc*)(base + ocp), (int)cp.size(), max_cp, st);
-      getrs_batched((const LuSolveDesc*)(base + ozs), (int)zs.size(), max_n2, max_nc, st);
-      gemm_grouped((const GemmDesc*)(base + og1), (const GemmTile*)(base + ot1), (int)t1.size(), st);
-      gemm_grouped((const GemmDesc*)(base + og2), (const GemmTile*)(base + ot2), (int)t2.size(), st);
+      prof().flops[pk_of<T>(PK_GETRS)] += getrs_flops(zs);
+      prof().flops[pk_of<T>(PK_GEMM)] += gemm_flops(g1) + gemm_flops(g2);
+      copy_batched((const CopyDescT<T>*)(base + ocp), (int)cp.size(), max_cp, st);
+      getrs_batched((const LuSolveDescT<T>*)(base + ozs), (int)zs.size(), max_n2, max_nc, st);
+      gemm_grouped((const GemmDescT<T>*)(base + og1), (const GemmTile*)(base + ot1), (int)t1.size(), st);
+      gemm_grouped((const GemmDescT<T>*)(base + og2), (const GemmTile*)(base + ot2), (int)t2.size(), st);
     }
   }
 
@@ -334,6 +368,7 @@ class Solver {
     lam = lam_;
     s_max = s_max_;
     tol = tol_;
+    prec = opt.precision;
     kappa = std::min(opt.kappa, N - 1);
     const double t0 = now_ms();
     // tree shape (data independent)
@@ -381,13 +416,20 @@ class Solver {
     const double t1 = now_ms();
     stats.t_tree = t1 - t0;
 
+    Pl.clear();
+    Pl32.clear();
+    for (int l = 0; l <= L; ++l) {
+      Pl.emplace_back(new DevBuf());
+      Pl32.emplace_back(new DevBuf());
+    }
     if (L > 0) {
       // a2: kNN
       stats.knn_fallback = knn_bruteforce(Xd, N, d, kappa, knn.ensure_n<int>((size_t)N * kappa), knn_s, st);
       IA_CUDA(cudaStreamSynchronize(st));
       const double t2 = now_ms();
       stats.t_knn = t2 - t1;
-      skeletonize();
+      if (prec == PREC_MIXED) skeletonize<float>();
+      else skeletonize<double>();
       IA_CUDA(cudaStreamSynchronize(st));
       stats.t_skel = now_ms() - t2;
     }
@@ -396,7 +438,8 @@ class Solver {
     raise_status(read_status_and_clear());
     const double t4 = now_ms();
     stats.t_leaf_lu = t4 - t3;
-    factor_levels();
+    if (prec == PREC_MIXED) factor_levels<float>();
+    else factor_levels<double>();
     raise_status(read_status_and_clear());
     stats.t_factor_levels = now_ms() - t4;
     stats.t_factor = now_ms() - t0;
@@ -404,7 +447,9 @@ class Solver {
     factored = true;
   }
 
-  // a3 + a4 + a5: skeletons, levels L .. 1
+  // a3 + a4 + a5: skeletons, levels L .. 1; TS is the precision of the sampled
+  // blocks and of the Householder updates (pivot norms are FP64 in both).
+  template <typename TS>
   void skeletonize() {
     int* kp = knn_pos.ensure_n<int>((size_t)N * kappa);
     knn_to_positions(knn.as<int>(), perm.as<int>(), iperm.as<int>(), N, kappa, kp, st);
@@ -421,8 +466,6 @@ class Solver {
     int* rk = ranks.ensure_n<int>(nd.size());
     IA_CUDA(cudaMemsetAsync(rk, 0, nd.size() * sizeof(int), st));
     int* sk = skel.ensure_n<int>(nd.size() * (size_t)s_max);
-    Pl.clear();
-    for (int l = 0; l <= L; ++l) Pl.emplace_back(new DevBuf());
     for (int l = L; l >= 1; --l) {
       const int nn = 1 << l;
       // sampling
@@ -448,14 +491,14 @@ class Solver {
         max_r = std::max(max_r, n.nsamp);
         max_c = std::max(max_c, n.ncols);
       }
-      double* A = A_ws.ensure_n<double>(asz);
+      TS* A = A_ws.ensure_n<TS>(asz);
       int* pv = piv_ws.ensure_n<int>(pvsz);
-      std::vector<KDesc> kd(nn);
-      std::vector<CpqrDesc> qd(nn);
+      std::vector<KDescT<TS>> kd(nn);
+      std::vector<CpqrDescT<TS>> qd(nn);
       for (int i = 0; i < nn; ++i) {
         const int u = uid(l, i);
         Node& n = nd[u];
-        KDesc k{};
+        KDescT<TS> k{};
         k.rows = sp + n.samp_off;
         k.nrows = n.nsamp;
         k.out = A + aoff[i];
@@ -470,13 +513,13 @@ class Solver {
           k.colsB = sk + (size_t)(2 * u + 1) * s_max;
         }
         kd[i] = k;
-        qd[i] = CpqrDesc{A + aoff[i], pv + poff[i], rk + u, n.nsamp, n.nsamp, n.ncols};
+        qd[i] = CpqrDescT<TS>{A + aoff[i], pv + poff[i], rk + u, n.nsamp, n.nsamp, n.ncols};
       }
       arena.clear();
       size_t ok = arena.push(kd), oq = arena.push(qd);
       char* base = upload_arena();
-      kernel_blocks(Xp.as<double>(), d, h, (const KDesc*)(base + ok), nn, max_e, st);
-      cpqr_id((const CpqrDesc*)(base + oq), nn, max_r, max_c, s_max, tol, st);
+      kernel_blocks<TS>(Xp.as<double>(), d, h, (const KDescT<TS>*)(base + ok), nn, max_e, st);
+      cpqr_id<TS>((const CpqrDescT<TS>*)(base + oq), nn, max_r, max_c, s_max, tol, st);
       // ranks of this level
       std::vector<int> rh(nn);
       d2h(rh.data(), rk + uid(l, 0), nn, st);
@@ -490,11 +533,11 @@ class Solver {
         psz += (int64_t)n.s * n.ncols;
       }
       double* P = Pl[l]->ensure_n<double>(psz);
-      std::vector<PDesc> pd(nn);
+      std::vector<PDescT<TS>> pd(nn);
       for (int i = 0; i < nn; ++i) {
         const int u = uid(l, i);
         Node& n = nd[u];
-        PDesc p{};
+        PDescT<TS> p{};
         p.A = A + aoff[i];
         p.piv = pv + poff[i];
         p.P = P + n.P_off;
@@ -514,12 +557,14 @@ class Solver {
       arena.clear();
       size_t op = arena.push(pd);
       base = upload_arena();
-      assemble_P((const PDesc*)(base + op), nn, max_c, st);
+      assemble_P<TS>((const PDescT<TS>*)(base + op), nn, max_c, st);
+      if (prec == PREC_MIXED) convert_d2f(P, Pl32[l]->ensure_n<float>(psz), psz, st);
       stats.bytes_P += psz * 8;
     }
   }
 
-  // a4 + a6: leaf LU of lambda I + K_aa
+  // a4 + a6: leaf LU of lambda I + K_aa.  Mixed: the FP64 blocks are kept for the
+  // operator and their FP32 rounding is factored.
   void leaf_lu() {
     const int nl = 1 << L;
     int64_t tot = 0;
@@ -528,10 +573,10 @@ class Solver {
       n.LU_off = tot;
       tot += (int64_t)n.size * n.size;
     }
-    double* lu = LU.ensure_n<double>(tot);
+    const bool mixed = prec == PREC_MIXED;
+    double* blocks = mixed ? Kleaf.ensure_n<double>(tot) : LU.ensure_n<double>(tot);
     int* lp = LUpiv.ensure_n<int>((size_t)nl * m_max);
     std::vector<KDesc> kd(nl);
-    std::vector<LuDesc> ld(nl);
     for (int i = 0; i < nl; ++i) {
       const Node& n = nd[uid(L, i)];
       KDesc k{};
@@ -539,24 +584,51 @@ class Solver {
       k.nrows = n.size;
       k.col0 = n.off;
       k.ncols = n.size;
-      k.out = lu + n.LU_off;
+      k.out = blocks + n.LU_off;
       k.ld = n.size;
       k.diag = lam;
       kd[i] = k;
-      ld[i] = LuDesc{lu + n.LU_off, lp + (int64_t)i * m_max, n.size, n.size};
     }
     arena.clear();
-    size_t ok = arena.push(kd), ol = arena.push(ld);
+    size_t ok = arena.push(kd);
     char* base = upload_arena();
-    kernel_blocks(Xp.as<double>(), d, h, (const KDesc*)(base + ok), nl, (int64_t)m_max * m_max, st);
-    prof().flops[PK_GETRF] += getrf_flops(ld);
-    getrf_batched((const LuDesc*)(base + ol), nl, m_max, status.as<int>(), st);
-    stats.bytes_LU = tot * 8;
+    kernel_blocks<double>(Xp.as<double>(), d, h, (const KDesc*)(base + ok), nl,
+                          (int64_t)m_max * m_max, st);
+    if (mixed) {
+      float* lu = LU32.ensure_n<float>(tot);
+      convert_d2f(blocks, lu, tot, st);
+      std::vector<LuDescT<float>> ld(nl);
+      for (int i = 0; i < nl; ++i) {
+        const Node& n = nd[uid(L, i)];
+        ld[i] = LuDescT<float>{lu + n.LU_off, lp + (int64_t)i * m_max, n.size, n.size};
+      }
+      arena.clear();
+      size_t ol = arena.push(ld);
+      base = upload_arena();
+      prof().flops[PK_GETRF32] += getrf_flops(ld);
+      getrf_batched<float>((const LuDescT<float>*)(base + ol), nl, m_max, status.as<int>(), st);
+      stats.bytes_operator += tot * 8;
+      stats.bytes_LU = tot * 4;
+    } else {
+      std::vector<LuDesc> ld(nl);
+      for (int i = 0; i < nl; ++i) {
+        const Node& n = nd[uid(L, i)];
+        ld[i] = LuDesc{blocks + n.LU_off, lp + (int64_t)i * m_max, n.size, n.size};
+      }
+      arena.clear();
+      size_t ol = arena.push(ld);
+      base = upload_arena();
+      prof().flops[PK_GETRF] += getrf_flops(ld);
+      getrf_batched<double>((const LuDesc*)(base + ol), nl, m_max, status.as<int>(), st);
+      stats.bytes_LU = tot * 8;
+    }
   }
 
-  // a7 + a8: W and Z, levels L-1 .. 0
+  // a7 + a8: W and Z, levels L-1 .. 0, factorization stored in precision T
+  template <typename T>
   void factor_levels() {
     if (L == 0) return;
+    const bool mixed = std::is_same<T, float>::value;
     int64_t wsz = 0, zsz = 0, zp = 0, csz = 0;
     for (int l = 1; l <= L; ++l)
       for (int i = 0; i < (1 << l); ++i) {
@@ -579,19 +651,22 @@ class Solver {
         n.CR_off = csz;
         csz += (int64_t)sb * sa;
       }
-    if (opt.mem_cap_gb > 0 && (double)(wsz + zsz + csz) * 8 > opt.mem_cap_gb * 1e9)
+    const double bytes = (double)(wsz + zsz + csz) * sizeof(T) + (mixed ? (double)wsz * 8 : 0.0);
+    if (opt.mem_cap_gb > 0 && bytes > opt.mem_cap_gb * 1e9)
       throw Error(IASKIT_ERR_NOMEM, "factorization exceeds mem_cap_gb");
-    double* W = Wb.ensure_n<double>(wsz);
-    Zb.ensure_n<double>(zsz);
+    T* W = (mixed ? Wb32 : Wb).template ensure_n<T>(wsz);
+    double* U64 = mixed ? Ustore.ensure_n<double>(wsz) : (double*)W;
+    (mixed ? Zb32 : Zb).template ensure_n<T>(zsz);
     Zpiv.ensure_n<int>(zp);
-    Cb.ensure_n<double>(csz);
-    stats.bytes_W = wsz * 8;
+    (mixed ? Cb32 : Cb).template ensure_n<T>(csz);
+    stats.bytes_W = wsz * (int64_t)sizeof(T);
+    if (mixed) stats.bytes_operator += wsz * 8;
     int* sk = skel.as<int>();
     for (int l = L - 1; l >= 0; --l) {
       const int nn = 1 << l;
-      // U blocks of the children of every node of level l
+      // U blocks of the children of every node of level l (FP64)
       std::vector<KDesc> kd;
-      int64_t max_e = 0;
+      int64_t max_e = 0, lo = INT64_MAX, hi = 0;
       for (int i = 0; i < 2 * nn; ++i) {
         int c = uid(l + 1, i);
         const Node& n = nd[c];
@@ -601,54 +676,50 @@ class Solver {
         k.colsA = sk + (size_t)(c ^ 1) * s_max;
         k.nA = nd[c ^ 1].s;
         k.ncols = nd[c ^ 1].s;
-        k.out = W + n.W_off;
+        k.out = U64 + n.W_off;
         k.ld = n.size;
         k.diag = 0.0;
         kd.push_back(k);
         max_e = std::max<int64_t>(max_e, (int64_t)n.size * k.ncols);
+        lo = std::min<int64_t>(lo, n.W_off);
+        hi = std::max<int64_t>(hi, n.W_off + (int64_t)n.size * k.ncols);
       }
       arena.clear();
       size_t ok = arena.push(kd);
       char* base = upload_arena();
-      kernel_blocks(Xp.as<double>(), d, h, (const KDesc*)(base + ok), (int)kd.size(), max_e, st);
+      kernel_blocks<double>(Xp.as<double>(), d, h, (const KDesc*)(base + ok), (int)kd.size(), max_e, st);
+      if (mixed) convert_d2f(U64 + lo, (float*)W + lo, hi - lo, st);
       // W = Solve(child, U) for all children at once; C blocks come back as P_c W_c
-      std::vector<RootBlock> rb;
+      std::vector<RootBlock<T>> rb;
+      T* C = cP<T>();
       for (int i = 0; i < 2 * nn; ++i) {
         int c = uid(l + 1, i);
         int par = c >> 1;
         const Node& n = nd[c];
-        double* tout;
-        int tld;
-        if ((c & 1) == 0) {  // left child: C_l = P_l W_{l r~}, s_l x s_r
-          tout = Cb.as<double>() + nd[par].CL_off;
-          tld = n.s;
-        } else {             // right child: C_r = P_r W_{r l~}, s_r x s_l
-          tout = Cb.as<double>() + nd[par].CR_off;
-          tld = n.s;
-        }
-        rb.push_back(RootBlock{c, W + n.W_off, n.size, nd[c ^ 1].s, tout, tld});
+        // left child: C_l = P_l W_{l r~} (s_l x s_r); right child: C_r = P_r W_{r l~}
+        T* tout = C + ((c & 1) == 0 ? nd[par].CL_off : nd[par].CR_off);
+        rb.push_back(RootBlock<T>{c, W + n.W_off, n.size, nd[c ^ 1].s, tout, n.s});
       }
-      forest_solve(l + 1, rb);
+      forest_solve<T>(l + 1, rb);
       // reduced systems Z'' = [[I, C_l], [C_r, I]] and their LU
-      std::vector<ZDesc> zd;
-      std::vector<LuDesc> ld;
+      std::vector<ZDescT<T>> zd;
+      std::vector<LuDescT<T>> ld;
       int64_t max_z = 0;
       int max_n = 0;
       for (int i = 0; i < nn; ++i) {
         int u = uid(l, i);
         int sa = nd[2 * u].s, sb = nd[2 * u + 1].s;
-        zd.push_back(ZDesc{Cb.as<double>() + nd[u].CL_off, Cb.as<double>() + nd[u].CR_off,
-                           Zb.as<double>() + nd[u].Z_off, sa, sb});
-        ld.push_back(LuDesc{Zb.as<double>() + nd[u].Z_off, Zpiv.as<int>() + nd[u].Zpiv_off, sa + sb, sa + sb});
+        zd.push_back(ZDescT<T>{C + nd[u].CL_off, C + nd[u].CR_off, zP<T>() + nd[u].Z_off, sa, sb});
+        ld.push_back(LuDescT<T>{zP<T>() + nd[u].Z_off, Zpiv.as<int>() + nd[u].Zpiv_off, sa + sb, sa + sb});
         max_z = std::max<int64_t>(max_z, (int64_t)(sa + sb) * (sa + sb));
         max_n = std::max(max_n, sa + sb);
       }
       arena.clear();
       size_t oz = arena.push(zd), ol = arena.push(ld);
       base = upload_arena();
-      form_Z((const ZDesc*)(base + oz), nn, max_z, st);
-      prof().flops[PK_GETRF] += getrf_flops(ld);
-      getrf_batched((const LuDesc*)(base + ol), nn, max_n, status.as<int>(), st);
+      form_Z<T>((const ZDescT<T>*)(base + oz), nn, max_z, st);
+      prof().flops[pk_of<T>(PK_GETRF)] += getrf_flops(ld);
+      getrf_batched<T>((const LuDescT<T>*)(base + ol), nn, max_n, status.as<int>(), st);
     }
   }
 
@@ -661,26 +732,38 @@ class Solver {
     raise_status(read_status_and_clear());
     stats.refine_hist.clear();
     stats.refine_sweeps = 0;
-    if (opt.refine <= 0) {
+    const int sweeps = opt.refine > 0 ? opt.refine : (prec == PREC_MIXED ? 50 : 0);
+    if (sweeps <= 0) {
       plain_solve(rhs, nrhs, rhs);
     } else {
-      refine_solve(rhs, nrhs);
+      refine_solve(rhs, nrhs, sweeps);
     }
     IA_CUDA(cudaStreamSynchronize(st));
     prof().resolve();
     stats.t_solve = now_ms() - t0;
   }
 
-  // out <- (lambda I + K~)^{-1} in  (ORIGINAL order, N x nrhs, ld N); may alias
+  // out <- (lambda I + K~)^{-1} in with the stored factorization (ORIGINAL order,
+  // N x nrhs, ld N); in and out may alias.
   void plain_solve(const double* in, int nrhs, double* out) {
-    double* V = vbuf.ensure_n<double>((size_t)N * nrhs);
-    permute_rows(in, N, V, N, perm.as<int>(), N, nrhs, false, st);
-    std::vector<RootBlock> rb{RootBlock{1, V, N, nrhs, nullptr, 0}};
-    forest_solve(0, rb);
-    permute_rows(V, N, out, N, perm.as<int>(), N, nrhs, true, st);
+    const size_t n = (size_t)N * nrhs;
+    double* V = vbuf.ensure_n<double>(n);
+    permute_rows<double>(in, N, V, N, perm.as<int>(), N, nrhs, false, st);
+    if (prec == PREC_MIXED) {
+      float* V32 = vbuf32.ensure_n<float>(n);
+      convert_d2f(V, V32, (int64_t)n, st);
+      std::vector<RootBlock<float>> rb{RootBlock<float>{1, V32, N, nrhs, nullptr, 0}};
+      forest_solve<float>(0, rb);
+      convert_f2d(V32, V, (int64_t)n, st);
+    } else {
+      std::vector<RootBlock<double>> rb{RootBlock<double>{1, V, N, nrhs, nullptr, 0}};
+      forest_solve<double>(0, rb);
+    }
+    permute_rows<double>(V, N, out, N, perm.as<int>(), N, nrhs, true, st);
   }
 
-  void refine_solve(double* rhs, int nrhs) {
+  // Iterative refinement against the FP64 operator: w <- w + Solve(u - A w).
+  void refine_solve(double* rhs, int nrhs, int sweeps) {
     const size_t n = (size_t)N * nrhs;
     double* u = rbuf.ensure_n<double>(2 * n);  // u copy, residual
     double* r = u + n;
@@ -688,43 +771,46 @@ class Solver {
     std::vector<double> un(nrhs), rn(nrhs);
     column_norms(u, nrhs, un);
     plain_solve(u, nrhs, rhs);
-    for (int it = 0; it < opt.refine; ++it) {
+    auto worst_residual = [&]() {
       apply_device(rhs, r, nrhs);        // r = A w
       axpby(u, r, n);                    // r = u - A w
       column_norms(r, nrhs, rn);
       double worst = 0;
       for (int c = 0; c < nrhs; ++c) worst = std::max(worst, un[c] > 0 ? rn[c] / un[c] : rn[c]);
       stats.refine_hist.push_back(worst);
-      if (worst <= opt.refine_tol) return;
+      return worst;
+    };
+    for (int it = 0; it < sweeps; ++it) {
+      if (worst_residual() <= opt.refine_tol) return;
       plain_solve(r, nrhs, r);           // delta
       add_inplace(rhs, r, n);            // w += delta
       stats.refine_sweeps = it + 1;
     }
-    apply_device(rhs, r, nrhs);
-    axpby(u, r, n);
-    column_norms(r, nrhs, rn);
-    double worst = 0;
-    for (int c = 0; c < nrhs; ++c) worst = std::max(worst, un[c] > 0 ? rn[c] / un[c] : rn[c]);
-    stats.refine_hist.push_back(worst);
-    if (worst > opt.refine_tol) throw Error(IASKIT_ERR_NOT_CONVERGED, "refinement did not converge");
+    if (worst_residual() > opt.refine_tol)
+      throw Error(IASKIT_ERR_NOT_CONVERGED, "refinement did not converge");
   }
 
   void column_norms(const double* x, int nrhs, std::vector<double>& out);
   void axpby(const double* u, double* r, size_t n);
   void add_inplace(double* w, const double* dlt, size_t n);
+  void scale_copy(const double* x, double* y, double a, size_t n);
 
   // ------------------------------------------------------- hierarchical apply
-  // u = (lambda I + K~) w, ORIGINAL order, device pointers
+  // u = (lambda I + K~) w, ORIGINAL order, device pointers.  Skeletonize (w~ = P w
+  // up the tree) then Evaluate (u_c += K_{c s~} w~_s for the sibling s of every
+  // node c, and the leaf blocks).  The plain form recomputes the kernel entries in
+  // FP64; the mixed form multiplies the FP64 blocks it stored.
   void apply_device(const double* w, double* u, int nrhs) {
     if (!factored) throw Error(IASKIT_ERR_NOT_FACTORED, "no factorization");
     if (nrhs < 1) throw Error(IASKIT_ERR_ARG, "bad nrhs");
     const double t0 = now_ms();
+    const bool stored = prec == PREC_MIXED;
     const size_t n = (size_t)N * nrhs;
     double* Wp = ubuf.ensure_n<double>(2 * n);
     double* Up = Wp + n;
-    permute_rows(w, N, Wp, N, perm.as<int>(), N, nrhs, false, st);
-    scale_copy(Wp, Up, lam, n);
-    // upward pass: wt of every internal node holds [w~_a; w~_b]
+    permute_rows<double>(w, N, Wp, N, perm.as<int>(), N, nrhs, false, st);
+    if (stored) IA_CUDA(cudaMemsetAsync(Up, 0, n * sizeof(double), st));
+    else scale_copy(Wp, Up, lam, n);
     std::vector<int64_t> woff(nd.size(), 0);
     int64_t tot = 0;
     for (int l = 0; l < L; ++l)
@@ -735,14 +821,18 @@ class Solver {
       }
     double* WT = wt.ensure_n<double>(std::max<int64_t>(tot, 1));
     auto n2 = [&](int u_) { return nd[2 * u_].s + nd[2 * u_ + 1].s; };
+    auto wsib = [&](int c) {  // w~ of the sibling of c, inside the parent's [w~_a; w~_b]
+      int par = c >> 1, sib = c ^ 1;
+      return WT + woff[par] + ((sib & 1) ? nd[2 * par].s : 0);
+    };
     if (L > 0) {
       std::vector<GemmDesc> g;
       std::vector<GemmTile> t;
       for (int i = 0; i < (1 << L); ++i) {
         int u_ = uid(L, i), par = u_ >> 1;
-        add_gemm(g, t, Pl[L]->as<double>() + nd[u_].P_off, nd[u_].s, Wp + nd[u_].off, N,
-                 WT + woff[par] + ((u_ & 1) ? nd[2 * par].s : 0), n2(par), nd[u_].s, nrhs,
-                 nd[u_].size, 1.0, 0.0);
+        add_gemm<double>(g, t, Pl[L]->as<double>() + nd[u_].P_off, nd[u_].s, Wp + nd[u_].off, N,
+                         WT + woff[par] + ((u_ & 1) ? nd[2 * par].s : 0), n2(par), nd[u_].s, nrhs,
+                         nd[u_].size, 1.0, 0.0);
       }
       run_gemms(g, t);
       for (int l = L - 1; l >= 1; --l) {
@@ -750,9 +840,9 @@ class Solver {
         t.clear();
         for (int i = 0; i < (1 << l); ++i) {
           int u_ = uid(l, i), par = u_ >> 1;
-          add_gemm(g, t, Pl[l]->as<double>() + nd[u_].P_off, nd[u_].s, WT + woff[u_], n2(u_),
-                   WT + woff[par] + ((u_ & 1) ? nd[2 * par].s : 0), n2(par), nd[u_].s, nrhs,
-                   n2(u_), 1.0, 0.0);
+          add_gemm<double>(g, t, Pl[l]->as<double>() + nd[u_].P_off, nd[u_].s, WT + woff[u_],
+                           n2(u_), WT + woff[par] + ((u_ & 1) ? nd[2 * par].s : 0), n2(par),
+                           nd[u_].s, nrhs, n2(u_), 1.0, 0.0);
         }
         run_gemms(g, t);
       }
@@ -760,47 +850,56 @@ class Solver {
     // Evaluate: one launch per level keeps the rows written by a launch disjoint
     int* sk = skel.as<int>();
     for (int l = 1; l <= L + 1; ++l) {
-      std::vector<KMatvecDesc> md;
-      int max_rows = 0;
-      if (l <= L) {
-        for (int i = 0; i < (1 << l); ++i) {
-          int c = uid(l, i), par = c >> 1, sib = c ^ 1;
-          const double* y = WT + woff[par] + ((sib & 1) ? nd[2 * par].s : 0);
-          md.push_back(KMatvecDesc{sk + (size_t)sib * s_max, y, Up + nd[c].off, nd[c].off,
-                                   nd[c].size, 0, nd[sib].s, n2(par), N});
-          max_rows = std::max(max_rows, nd[c].size);
+      const bool leaves = l == L + 1;
+      const int lev = leaves ? L : l;
+      if (stored) {
+        std::vector<GemmDesc> g;
+        std::vector<GemmTile> t;
+        for (int i = 0; i < (1 << lev); ++i) {
+          int c = uid(lev, i);
+          if (leaves)
+            add_gemm<double>(g, t, Kleaf.as<double>() + nd[c].LU_off, nd[c].size, Wp + nd[c].off, N,
+                             Up + nd[c].off, N, nd[c].size, nrhs, nd[c].size, 1.0, 1.0);
+          else
+            add_gemm<double>(g, t, Ustore.as<double>() + nd[c].W_off, nd[c].size, wsib(c),
+                             n2(c >> 1), Up + nd[c].off, N, nd[c].size, nrhs, nd[c ^ 1].s, 1.0, 1.0);
         }
+        run_gemms(g, t);
       } else {
-        for (int i = 0; i < (1 << L); ++i) {
-          int c = uid(L, i);
-          md.push_back(KMatvecDesc{nullptr, Wp + nd[c].off, Up + nd[c].off, nd[c].off, nd[c].size,
-                                   nd[c].off, nd[c].size, N, N});
+        std::vector<KMatvecDesc> md;
+        int max_rows = 0;
+        for (int i = 0; i < (1 << lev); ++i) {
+          int c = uid(lev, i);
+          if (leaves)
+            md.push_back(KMatvecDesc{nullptr, Wp + nd[c].off, Up + nd[c].off, nd[c].off, nd[c].size,
+                                     nd[c].off, nd[c].size, N, N});
+          else
+            md.push_back(KMatvecDesc{sk + (size_t)(c ^ 1) * s_max, wsib(c), Up + nd[c].off, nd[c].off,
+                                     nd[c].size, 0, nd[c ^ 1].s, n2(c >> 1), N});
           max_rows = std::max(max_rows, nd[c].size);
         }
+        arena.clear();
+        size_t om = arena.push(md);
+        char* base = upload_arena();
+        kernel_matvec(Xp.as<double>(), d, h, nrhs, (const KMatvecDesc*)(base + om), (int)md.size(),
+                      max_rows, st);
       }
-      arena.clear();
-      size_t om = arena.push(md);
-      char* base = upload_arena();
-      kernel_matvec(Xp.as<double>(), d, h, nrhs, (const KMatvecDesc*)(base + om), (int)md.size(),
-                    max_rows, st);
     }
-    if (L == 0) {
-      // single leaf: the loop above ran the leaf pass at l = 1 = L + 1
-    }
-    permute_rows(Up, N, u, N, perm.as<int>(), N, nrhs, true, st);
+    permute_rows<double>(Up, N, u, N, perm.as<int>(), N, nrhs, true, st);
     IA_CUDA(cudaStreamSynchronize(st));
     prof().resolve();
     stats.t_apply = now_ms() - t0;
   }
-  void scale_copy(const double* x, double* y, double a, size_t n);
 
   void release() {
     factored = false;
     DevBuf* all[] = {&X, &Xp, &perm, &iperm, &split_dim, &knn, &knn_pos, &samp, &ranks, &skel,
-                     &piv_ws, &A_ws, &LU, &LUpiv, &Wb, &Zb, &Zpiv, &Cb, &arena_dev, &level_off_dev,
-                     &samp_off_dev, &tbuf, &vbuf, &ubuf, &rbuf, &wt, &io, &cpqr_rank, &normbuf};
+                     &piv_ws, &A_ws, &status, &arena_dev, &level_off_dev, &tbuf, &vbuf, &vbuf32,
+                     &ubuf, &rbuf, &wt, &io, &normbuf, &LU, &LUpiv, &Wb, &Zb, &Zpiv, &Cb, &LU32,
+                     &Wb32, &Zb32, &Cb32, &tbuf32, &Kleaf, &Ustore};
     for (DevBuf* b : all) b->release();
     Pl.clear();
+    Pl32.clear();
     tree_s.release();
     knn_s.release();
     samp_s.release();
@@ -836,21 +935,27 @@ __global__ void colnorm_kernel(const double* x, int N, double* out) {
 
 void Solver::column_norms(const double* x, int nrhs, std::vector<double>& out) {
   double* dn = normbuf.ensure_n<double>(nrhs);
-  colnorm_kernel<<<nrhs, 256, 0, st>>>(x, N, dn);
-  IA_LAUNCH_CHECK();
+  {
+    ProfScope _ps(PK_MISC, st);
+    colnorm_kernel<<<nrhs, 256, 0, st>>>(x, N, dn);
+    IA_LAUNCH_CHECK();
+  }
   out.resize(nrhs);
   d2h(out.data(), dn, nrhs, st);
   IA_CUDA(cudaStreamSynchronize(st));
 }
 void Solver::axpby(const double* u, double* r, size_t n) {
+  ProfScope _ps(PK_MISC, st);
   axpby_kernel<<<std::min<size_t>(ceil_div(n, 256), 8192), 256, 0, st>>>(u, r, n);
   IA_LAUNCH_CHECK();
 }
 void Solver::add_inplace(double* w, const double* dl, size_t n) {
+  ProfScope _ps(PK_MISC, st);
   add_kernel<<<std::min<size_t>(ceil_div(n, 256), 8192), 256, 0, st>>>(w, dl, n);
   IA_LAUNCH_CHECK();
 }
 void Solver::scale_copy(const double* x, double* y, double a, size_t n) {
+  ProfScope _ps(PK_MISC, st);
   scale_kernel<<<std::min<size_t>(ceil_div(n, 256), 8192), 256, 0, st>>>(x, y, a, n);
   IA_LAUNCH_CHECK();
 }
@@ -982,6 +1087,8 @@ int iaskit_set_option(const char* key, double value) {
     } else if (k == "mem_cap_gb") {
       if (!(value >= 0)) throw Error(IASKIT_ERR_ARG, "invalid mem_cap_gb");
       o.mem_cap_gb = value;
+    } else if (k == "precision") {
+      o.precision = as_int(0, 1);
     } else if (k == "profile") {
       int v = as_int(0, 1);
       IA_CUDA(cudaStreamSynchronize(S().st));
@@ -1003,6 +1110,7 @@ int iaskit_get_option(const char* key, double* value) {
     else if (k == "refine_tol") *value = o.refine_tol;
     else if (k == "mem_cap_gb") *value = o.mem_cap_gb;
     else if (k == "profile") *value = prof().enabled ? 1 : 0;
+    else if (k == "precision") *value = o.precision;
     else throw Error(IASKIT_ERR_ARG, "unknown option " + k);
   });
 }
@@ -1020,11 +1128,12 @@ int iaskit_stats(char* buf, size_t len) {
            "\"N\":%d,\"d\":%d,\"L\":%d,\"factored\":%s,\"ms\":{\"tree\":%.3f,\"knn\":%.3f,"
            "\"skeletonize\":%.3f,\"leaf_lu\":%.3f,\"factor_levels\":%.3f,\"factor\":%.3f,"
            "\"solve\":%.3f,\"apply\":%.3f},\"knn_fallback\":%d,\"bytes\":{\"W\":%lld,\"LU\":%lld,"
-           "\"P\":%lld},\"flops_W\":%.6g,\"refine_sweeps\":%d,",
+           "\"P\":%lld,\"operator\":%lld},\"precision\":\"%s\",\"refine_sweeps\":%d,",
            s.N, s.d, s.L, s.factored ? "true" : "false", s.stats.t_tree, s.stats.t_knn,
            s.stats.t_skel, s.stats.t_leaf_lu, s.stats.t_factor_levels, s.stats.t_factor,
            s.stats.t_solve, s.stats.t_apply, s.stats.knn_fallback, (long long)s.stats.bytes_W,
-           (long long)s.stats.bytes_LU, (long long)s.stats.bytes_P, s.stats.flops_W,
+           (long long)s.stats.bytes_LU, (long long)s.stats.bytes_P,
+           (long long)s.stats.bytes_operator, s.prec == PREC_MIXED ? "mixed" : "fp64",
            s.stats.refine_sweeps);
   j += tmp;
   j += "\"refine_history\":[";

@@ -1,0 +1,105 @@
+"""Mixed-precision form: FP32 factorization refined against the FP64 operator.
+
+The mixed form chooses its own skeletons and P (FP32 Householder updates, FP64
+pivot norms), so its K~ can differ slightly from the FP64 path's.  The checks:
+
+* the GPU's FP64 operator of that K~ equals the oracle's hierarchical MatVec built
+  from the same skeletons and P (1e-10);
+* the refined solution reaches a relative residual <= 1e-10 against that operator,
+  evaluated by the oracle;
+* its error against the plain FP64 oracle solution is reported and bounded.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.askit import Skeletons
+from workloads import make_points, make_rhs, workload
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_skeletons(ia, X, tree, h):
+    """An oracle Skeletons object holding the GPU's skeletons and nested P."""
+    sk = Skeletons(tree=tree, Xp=np.asarray(X)[tree.perm], h=h)
+    ranks = ia.iaskit_get_ranks()
+    for l in range(1, tree.L + 1):
+        for i in range(1 << l):
+            s = int(ranks[(1 << l) + i])
+            sk.skel[(l, i)] = ia.iaskit_get_skeleton(l, i).astype(np.int64)
+            sk.P[(l, i)] = ia.iaskit_get_P(l, i, s)
+    return sk
+
+
+CASES = {
+    "c1": ("C1", 4096, 0.5, 1.0, 64, 32, 0.0, 2),
+    "gmm54": ("C2", 3000, 1.0, 1e-2, 64, 24, 1e-5, 3),
+    "ragged_small_lambda": ("C1", 2500, 0.3, 1e-3, 40, 20, 1e-7, 2),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def mixed_case(request, gpu_lib):
+    ia = gpu_lib
+    wname, N, h, lam, m, s_max, tol, nrhs = CASES[request.param]
+    w = workload(wname, N=N)
+    X = make_points(w)
+    u = make_rhs(w, N=N, nrhs=nrhs)
+    ia.iaskit_set_option("precision", 1)
+    try:
+        ia.iaskit_factor(X, h, lam, m, s_max, tol)
+        w_mixed = ia.iaskit_solve(u)
+        stats = ia.iaskit_stats()
+        tree = oracle.build_tree(X, m)
+        sk = _gpu_skeletons(ia, X, tree, h)
+        probe = np.random.default_rng(5).standard_normal((N, 2))
+        Au_gpu = ia.iaskit_apply(probe)
+    finally:
+        ia.iaskit_set_option("precision", 0)
+    return dict(X=X, u=u, w=w_mixed, sk=sk, lam=lam, stats=stats, probe=probe, Au=Au_gpu,
+                params=(h, lam, m, s_max, tol))
+
+
+def test_mixed_operator_matches_oracle_matvec(mixed_case):
+    c = mixed_case
+    ref = oracle.invaskit.apply_operator(c["sk"], c["lam"], c["probe"])
+    err = np.linalg.norm(c["Au"] - ref) / np.linalg.norm(ref)
+    assert err < 1e-10, err
+
+
+def test_mixed_refined_residual(mixed_case):
+    c = mixed_case
+    assert c["stats"]["precision"] == "mixed"
+    rho = oracle.residual(c["sk"], c["lam"], c["w"], c["u"])
+    assert rho <= 1e-10, (rho, c["stats"]["refine_history"])
+    assert c["stats"]["refine_history"][-1] <= 1e-10
+
+
+def test_mixed_error_against_fp64_oracle(mixed_case):
+    c = mixed_case
+    h, lam, m, s_max, tol = c["params"]
+    _, _, _, F = oracle.build_all(c["X"], h, lam, m, s_max, tol)
+    w64 = oracle.solve(F, c["u"])
+    err = np.linalg.norm(c["w"] - w64) / np.linalg.norm(w64)
+    print(f"mixed vs FP64 oracle: relative error {err:.3e}")
+    assert err < 1e-2
+
+
+def test_mixed_plain_solve_without_refinement_is_fp32_accurate(gpu_lib):
+    ia = gpu_lib
+    w = workload("C1", N=2048)
+    X, u = make_points(w), make_rhs(w, N=2048)
+    ia.iaskit_set_option("precision", 1)
+    ia.iaskit_set_option("refine", 1)
+    try:
+        ia.iaskit_factor(X, w.h, w.lam, w.m, w.s_max, w.tol)
+        with pytest.raises(ia.IaskitError) as e:
+            ia.iaskit_set_option("refine_tol", 1e-300)
+            ia.iaskit_solve(u)
+        assert e.value.name == "IASKIT_ERR_NOT_CONVERGED"
+        hist = ia.iaskit_stats()["refine_history"]
+        assert len(hist) == 2 and hist[1] < hist[0] < 1e-4
+    finally:
+        ia.iaskit_set_option("refine", 0)
+        ia.iaskit_set_option("refine_tol", 1e-10)
+        ia.iaskit_set_option("precision", 0)
