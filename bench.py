@@ -170,7 +170,7 @@ def config_of(w):
 # ------------------------------------------------------------------- GPU leg
 FP32_LANES_PER_SM = 128              # GB300: FP32 FMA lanes per SM
 PEAK_CLASS = {                       # kernel classes whose arithmetic is FP32
-    "kernel_blocks_f32", "cpqr_id_f32", "getrf_f32", "getrs_f32", "gemm_f32"}
+    "kernel_blocks_f32", "cpqr_id_f32", "getrf_f32", "getrs_f32", "gemm_f32", "knn"}
 
 
 def alu_peak_tflops(kernel: str, sm_mhz: float) -> tuple:
@@ -321,6 +321,7 @@ def main():
         "config": cfg,
         "factor_s": st["ms"]["factor"] / 1e3, "solve_rhs_per_s": w.nrhs / (st["ms"]["solve"] / 1e3),
         "residual": chosen["resid"], "refine_sweeps": st.get("refine_sweeps"),
+        "knn_exact_fallback_rows": st.get("knn_fallback"),
         "gpu_launches": chosen["launches"], "clocks": clocks, "roofline": roof,
         "kernel_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in kern.items() if v["ms"] > 0},
         "e2e": {"value": e2e_value, "unit": UNIT,

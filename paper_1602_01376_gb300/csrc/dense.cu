@@ -63,6 +63,7 @@ __global__ void kernel_blocks_kernel(const double* Xp, int d, double neg_inv_2h2
 // ----------------------------------------------------------------- CPQR / ID
 constexpr int QR_THREADS = 256;
 constexpr int QR_WARPS = QR_THREADS / 32;
+constexpr int QR_RPL = 32;  // rows per lane held in registers (columns of up to 1024 rows)
 
 __device__ void block_argmax(double& v, int& idx, double* rv, int* ri) {
   warp_argmax(v, idx);
@@ -111,7 +112,10 @@ __device__ __forceinline__ T warp_sum_t(T v) {
 }
 
 // One block per node.  Dynamic shared memory: norms (ncols doubles), v (nrows T),
-// piv (ncols ints).
+// piv (ncols ints).  Column norms: every lane accumulates its share of a column in
+// Acc (the storage type), the 32 partial sums are combined in FP64 and compared in
+// FP64.  For T = double this is FP64 throughout; for T = float each partial sum
+// covers at most nrows / 32 squares.
 template <typename T>
 __global__ void __launch_bounds__(QR_THREADS) cpqr_kernel(const CpqrDescT<T>* descs, int s_max,
                                                           double tol) {
@@ -126,12 +130,12 @@ __global__ void __launch_bounds__(QR_THREADS) cpqr_kernel(const CpqrDescT<T>* de
   int* piv = reinterpret_cast<int*>(shq + nc + nr);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j = warp; j < nc; j += QR_WARPS) {
-    double s = 0.0;
+    T part = 0;
     for (int i = lane; i < nr; i += 32) {
-      double a = (double)A[(size_t)i + (size_t)j * ld];
-      s = fma(a, a, s);
+      T a = A[(size_t)i + (size_t)j * ld];
+      part = fma(a, a, part);
     }
-    s = warp_sum(s);
+    double s = warp_sum((double)part);
     if (lane == 0) {
       norms[j] = s;
       piv[j] = j;
@@ -183,20 +187,47 @@ __global__ void __launch_bounds__(QR_THREADS) cpqr_kernel(const CpqrDescT<T>* de
     if (threadIdx.x == 0) v[0] = (T)v0;
     __syncthreads();
     const T beta = vv > 0.0 ? (T)(2.0 / vv) : (T)0;
+    const int tcount = (nr - k + 31) / 32;  // rows per lane of the trailing column
     for (int j = k + 1 + warp; j < nc; j += QR_WARPS) {
       T* col = A + (size_t)j * ld;
       T dot = 0;
-      for (int i = k + lane; i < nr; i += 32) dot = fma(v[i - k], col[i], dot);
-      dot = warp_sum_t<T>(dot);
-      const T f = beta * dot;
-      double nrm = 0.0;
-      for (int i = k + lane; i < nr; i += 32) {
-        T a = col[i] - f * v[i - k];
-        col[i] = a;
-        if (i > k) nrm = fma((double)a, (double)a, nrm);
+      if (sizeof(T) == 4 && tcount <= QR_RPL) {
+        // FP32: the warp keeps the column in registers between the dot product and the
+        // update (FP64 is bound by its arithmetic pipe and keeps the two-pass form)
+        T x[QR_RPL];
+#pragma unroll
+        for (int t = 0; t < QR_RPL; ++t) {
+          const int i = k + lane + 32 * t;
+          x[t] = (t < tcount && i < nr) ? col[i] : (T)0;
+          if (t < tcount && i < nr) dot = fma(v[i - k], x[t], dot);
+        }
+        dot = warp_sum_t<T>(dot);
+        const T f = beta * dot;
+        T part = 0;
+#pragma unroll
+        for (int t = 0; t < QR_RPL; ++t) {
+          const int i = k + lane + 32 * t;
+          if (t < tcount && i < nr) {
+            T a = x[t] - f * v[i - k];
+            col[i] = a;
+            if (i > k) part = fma(a, a, part);
+          }
+        }
+        const double nrm = warp_sum((double)part);
+        if (lane == 0) norms[j] = nrm;
+      } else {
+        for (int i = k + lane; i < nr; i += 32) dot = fma(v[i - k], col[i], dot);
+        dot = warp_sum_t<T>(dot);
+        const T f = beta * dot;
+        T part = 0;
+        for (int i = k + lane; i < nr; i += 32) {
+          T a = col[i] - f * v[i - k];
+          col[i] = a;
+          if (i > k) part = fma(a, a, part);
+        }
+        const double nrm = warp_sum((double)part);
+        if (lane == 0) norms[j] = nrm;
       }
-      nrm = warp_sum(nrm);
-      if (lane == 0) norms[j] = nrm;
     }
     for (int i = k + threadIdx.x; i < nr; i += QR_THREADS)
       A[(size_t)i + (size_t)k * ld] = (i == k) ? (T)alpha : (T)0;
@@ -373,8 +404,9 @@ __global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* des
 }
 
 // ---------------------------------------------------------------- GETRS
-// Grid (descriptor, chunk of RS_NC right-hand sides).  The chunk lives in shared
-// memory; rows are processed in blocks of 32: a warp solves the 32 x 32 diagonal
+// Grid (chunk of NC right-hand sides, descriptor): the chunks of one matrix are
+// neighbours in launch order, so its LU factors are read from L2 after the first.
+// The chunk lives in shared memory; rows are processed in blocks of 32: a warp solves the 32 x 32 diagonal
 // block for one column with shuffles, then all threads update the rows below
 // (forward) or above (backward) with a register-tiled product.
 constexpr int RS_THREADS = 256;
@@ -383,8 +415,8 @@ template <typename T, int NC>
 __global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>* descs) {
   extern __shared__ __align__(16) unsigned char rs_sh[];
   T* X = reinterpret_cast<T*>(rs_sh);  // n x NC, column-major, ld n
-  const LuSolveDescT<T> D = descs[blockIdx.x];
-  const int c0 = blockIdx.y * NC;
+  const LuSolveDescT<T> D = descs[blockIdx.y];
+  const int c0 = blockIdx.x * NC;
   if (c0 >= D.ncols) return;
   const int nc = min(NC, D.ncols - c0);
   const int n = D.n;
@@ -468,19 +500,22 @@ __global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>
 }
 
 // ---------------------------------------------------------------- GEMM
-constexpr int GT = 64;   // tile
 constexpr int GK = 16;   // k step
 constexpr int G_THREADS = 256;
 
-template <typename T>
+// Tile TM x TN, 256 threads, 4 x 4 outputs per thread: (64, 64) for general
+// problems, (256, 16) when every problem of the launch has at most 16 columns.
+template <typename T, int TM, int TN>
 __global__ void __launch_bounds__(G_THREADS) gemm_kernel(const GemmDescT<T>* descs,
                                                          const GemmTile* tiles) {
-  __shared__ T As[GK][GT + 1];
-  __shared__ T Bs[GK][GT + 1];
+  constexpr int TX = TM / 4, TY = TN / 4;
+  static_assert(TX * TY == G_THREADS, "tile must map to 256 threads");
+  __shared__ T As[GK][TM + 1];
+  __shared__ T Bs[GK][TN + 1];
   const GemmTile Tl = tiles[blockIdx.x];
   const GemmDescT<T> D = descs[Tl.desc];
-  const int m0 = Tl.tm * GT, n0 = Tl.tn * GT;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m0 = Tl.tm * TM, n0 = Tl.tn * TN;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -488,14 +523,20 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(const GemmDescT<T>* des
     for (int b = 0; b < 4; ++b) acc[a][b] = 0;
   for (int k0 = 0; k0 < D.K; k0 += GK) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int e = threadIdx.x + r * G_THREADS;  // 0 .. 1023
-      const int am = e % GT, ak = e / GT;         // A tile: 64 rows x 16 k
+    for (int r = 0; r < TM * GK / G_THREADS; ++r) {
+      const int e = threadIdx.x + r * G_THREADS;
+      const int am = e % TM, ak = e / TM;         // A tile: TM rows x 16 k
       const int gm = m0 + am, gk = k0 + ak;
       As[ak][am] = (gm < D.M && gk < D.K) ? D.A[(size_t)gm + (size_t)gk * D.lda] : (T)0;
-      const int bk = e % GK, bn = e / GK;         // B tile: 16 k x 64 cols
-      const int gk2 = k0 + bk, gn = n0 + bn;
-      Bs[bk][bn] = (gk2 < D.K && gn < D.N) ? D.B[(size_t)gk2 + (size_t)gn * D.ldb] : (T)0;
+    }
+#pragma unroll
+    for (int r = 0; r < (TN * GK + G_THREADS - 1) / G_THREADS; ++r) {
+      const int e = threadIdx.x + r * G_THREADS;
+      if (e < TN * GK) {
+        const int bk = e % GK, bn = e / GK;       // B tile: 16 k x TN cols
+        const int gk2 = k0 + bk, gn = n0 + bn;
+        Bs[bk][bn] = (gk2 < D.K && gn < D.N) ? D.B[(size_t)gk2 + (size_t)gn * D.ldb] : (T)0;
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -503,8 +544,8 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(const GemmDescT<T>* des
       T a[4], b[4];
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        a[r] = As[kk][tx + 16 * r];
-        b[r] = Bs[kk][ty + 16 * r];
+        a[r] = As[kk][tx + TX * r];
+        b[r] = Bs[kk][ty + TY * r];
       }
 #pragma unroll
       for (int r = 0; r < 4; ++r)
@@ -518,7 +559,7 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(const GemmDescT<T>* des
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int gm = m0 + tx + 16 * r, gn = n0 + ty + 16 * c;
+      const int gm = m0 + tx + TX * r, gn = n0 + ty + TY * c;
       if (gm < D.M && gn < D.N) {
         T* cp = D.C + (size_t)gm + (size_t)gn * D.ldc;
         *cp = D.beta == 0.0 ? alpha * acc[r][c] : alpha * acc[r][c] + beta * *cp;
@@ -651,7 +692,8 @@ void launch_getrs(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int ma
   if (smem > 48 * 1024)
     IA_CUDA(cudaFuncSetAttribute(getrs_kernel<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
-  dim3 grid(ndesc, ceil_div(max_cols, NC));
+  if (ndesc > 65535) throw Error(IASKIT_ERR_UNSUPPORTED, "more than 65535 LU solves in one launch");
+  dim3 grid(ceil_div(max_cols, NC), ndesc);
   getrs_kernel<T, NC><<<grid, RS_THREADS, smem, st>>>(descs_dev);
   IA_LAUNCH_CHECK();
 }
@@ -718,10 +760,13 @@ void getrs_batched(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int m
 
 template <typename T>
 void gemm_grouped(const GemmDescT<T>* descs_dev, const GemmTile* tiles_dev, int ntiles,
-                  cudaStream_t st) {
+                  GemmShape shape, cudaStream_t st) {
   if (ntiles <= 0) return;
   ProfScope _ps(pk_of<T>(PK_GEMM), st);
-  gemm_kernel<T><<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
+  if (shape == GEMM_SKINNY)
+    gemm_kernel<T, 256, 16><<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
+  else
+    gemm_kernel<T, 64, 64><<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
   IA_LAUNCH_CHECK();
 }
 
@@ -792,7 +837,8 @@ void check_finite(const double* x, int64_t n, int* dev_status, cudaStream_t st) 
   template void assemble_P<T>(const PDescT<T>*, int, int, cudaStream_t);                          \
   template void getrf_batched<T>(const LuDescT<T>*, int, int, int*, cudaStream_t);                \
   template void getrs_batched<T>(const LuSolveDescT<T>*, int, int, int, cudaStream_t);            \
-  template void gemm_grouped<T>(const GemmDescT<T>*, const GemmTile*, int, cudaStream_t);         \
+  template void gemm_grouped<T>(const GemmDescT<T>*, const GemmTile*, int, GemmShape,             \
+                                cudaStream_t);                                                   \
   template void copy_batched<T>(const CopyDescT<T>*, int, int64_t, cudaStream_t);                 \
   template void form_Z<T>(const ZDescT<T>*, int, int64_t, cudaStream_t);                          \
   template void permute_rows<T>(const T*, int, T*, int, const int*, int, int, bool, cudaStream_t);

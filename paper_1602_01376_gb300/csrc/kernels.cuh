@@ -152,13 +152,17 @@ struct GemmDescT {
   int M, N, K, lda, ldb, ldc;
   double alpha, beta;
 };
-// Work items (descriptor index, tile row, tile column) of 64 x 64 tiles.
+// Work items (descriptor index, tile row, tile column).  Tile shape: 64 x 64
+// (GEMM_SQUARE) or 256 x 16 (GEMM_SKINNY, every problem with N <= 16).
 struct GemmTile {
   int desc, tm, tn;
 };
+enum GemmShape { GEMM_SQUARE = 0, GEMM_SKINNY = 1 };
+inline int gemm_tile_m(GemmShape s) { return s == GEMM_SKINNY ? 256 : 64; }
+inline int gemm_tile_n(GemmShape s) { return s == GEMM_SKINNY ? 16 : 64; }
 template <typename T>
 void gemm_grouped(const GemmDescT<T>* descs_dev, const GemmTile* tiles_dev, int ntiles,
-                  cudaStream_t st);
+                  GemmShape shape, cudaStream_t st);
 
 // dst (rows x cols, ldd) <- src (rows x cols, lds), batched.
 template <typename T>

@@ -23,8 +23,6 @@ namespace iaskit {
 
 namespace {
 
-constexpr int KNN_THREADS = 128;
-constexpr int KNN_TILE = 128;
 
 __global__ void to_float_kernel(const double* X, float* X32, size_t n) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -41,17 +39,31 @@ __global__ void maxabs_kernel(const double* X, size_t n, unsigned long long* out
   if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
-// One thread per query.  D: padded dimension (coordinates >= d are zero on both
-// sides, which adds exact zeros to the FP32 sums).  KP: kept candidates.
+// FP32 prefilter.  A block owns KT_QB = 256 queries (one per thread for the
+// selection) and streams the points in tiles of KT_RB = 32:
+//   phase 1: every thread computes 8 queries x 4 points of the tile's squared
+//            distances, sum_k fma(q_k - r_k, q_k - r_k, acc) in coordinate order
+//            (coordinates d..D-1 are zero on both sides and add exact zeros), into
+//            shared memory;
+//   phase 2: every thread scans its query's row and updates its register list.
+// 8 x 4 keeps the kernel at two resident blocks per SM, so one block's selection
+// and barriers overlap the other's arithmetic.
+constexpr int KT_QB = 256;
+constexpr int KT_RB = 32;
 template <int D, int KP>
-__global__ void __launch_bounds__(KNN_THREADS) knn_prefilter_kernel(const float* X32, int N, int d,
-                                                                    float* cand_d, int* cand_i) {
-  __shared__ float tile[KNN_TILE][D];
-  const int i = blockIdx.x * KNN_THREADS + threadIdx.x;
-  const bool active = i < N;
-  float q[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) q[k] = (active && k < d) ? X32[(size_t)i * d + k] : 0.0f;
+__global__ void __launch_bounds__(KT_QB) knn_prefilter_tiled_kernel(const float* X32, int N, int d,
+                                                                   float* cand_d, int* cand_i) {
+  extern __shared__ float kt_sh[];
+  float* Qs = kt_sh;                      // [D][KT_QB]
+  float* Rs = Qs + D * KT_QB;             // [D][KT_RB]
+  float* Dt = Rs + D * KT_RB;             // [KT_QB][KT_RB + 1]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int q0 = blockIdx.x * KT_QB;
+  for (int e = tid; e < D * KT_QB; e += KT_QB) {
+    const int i = e / D, k = e % D;
+    Qs[k * KT_QB + i] = (q0 + i < N && k < d) ? X32[(size_t)(q0 + i) * d + k] : 0.0f;
+  }
+  const int my_q = q0 + tid;
   float bd[KP];
   int bi[KP];
 #pragma unroll
@@ -59,44 +71,65 @@ __global__ void __launch_bounds__(KNN_THREADS) knn_prefilter_kernel(const float*
     bd[t] = FLT_MAX;
     bi[t] = INT_MAX;
   }
-  for (int j0 = 0; j0 < N; j0 += KNN_TILE) {
-    const int nt = min(KNN_TILE, N - j0);
+  for (int r0 = 0; r0 < N; r0 += KT_RB) {
+    const int nt = min(KT_RB, N - r0);
     __syncthreads();
-    for (int e = threadIdx.x; e < KNN_TILE * D; e += KNN_THREADS) {
-      int r = e / D, k = e % D;
-      tile[r][k] = (r < nt && k < d) ? X32[(size_t)(j0 + r) * d + k] : 0.0f;
+    for (int e = tid; e < D * KT_RB; e += KT_QB) {
+      const int j = e / D, k = e % D;
+      Rs[k * KT_RB + j] = (j < nt && k < d) ? X32[(size_t)(r0 + j) * d + k] : 0.0f;
     }
     __syncthreads();
-    if (!active) continue;
-    for (int r = 0; r < nt; ++r) {
-      float acc = 0.0f;
+    float acc[8][4];
 #pragma unroll
-      for (int k = 0; k < D; ++k) {
-        float df = q[k] - tile[r][k];
-        acc = fmaf(df, df, acc);
-      }
-      const int j = j0 + r;
-      if (acc <= bd[KP - 1] && j != i) {
-        float cv = acc;
-        int cj = j;
+    for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int t = 0; t < KP; ++t) {
-          bool less = cv < bd[t] || (cv == bd[t] && cj < bi[t]);
-          float tv = less ? bd[t] : cv;
-          int tj = less ? bi[t] : cj;
-          bd[t] = less ? cv : bd[t];
-          bi[t] = less ? cj : bi[t];
-          cv = tv;
-          cj = tj;
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
+#pragma unroll 4
+    for (int k = 0; k < D; ++k) {
+      float qa[8], rb[4];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) qa[a] = Qs[k * KT_QB + lane + 32 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) rb[b] = Rs[k * KT_RB + warp * 4 + b];
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          float df = qa[a] - rb[b];
+          acc[a][b] = fmaf(df, df, acc[a][b]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) Dt[(lane + 32 * a) * (KT_RB + 1) + warp * 4 + b] = acc[a][b];
+    __syncthreads();
+    if (my_q < N) {
+      for (int j = 0; j < nt; ++j) {
+        const float v = Dt[tid * (KT_RB + 1) + j];
+        const int ref = r0 + j;
+        if (v <= bd[KP - 1] && ref != my_q) {
+          float cv = v;
+          int cj = ref;
+#pragma unroll
+          for (int t = 0; t < KP; ++t) {
+            bool less = cv < bd[t] || (cv == bd[t] && cj < bi[t]);
+            float tv = less ? bd[t] : cv;
+            int tj = less ? bi[t] : cj;
+            bd[t] = less ? cv : bd[t];
+            bi[t] = less ? cj : bi[t];
+            cv = tv;
+            cj = tj;
+          }
         }
       }
     }
   }
-  if (active) {
+  if (my_q < N) {
 #pragma unroll
     for (int t = 0; t < KP; ++t) {
-      cand_d[(size_t)i * KP + t] = bd[t];
-      cand_i[(size_t)i * KP + t] = bi[t];
+      cand_d[(size_t)my_q * KP + t] = bd[t];
+      cand_i[(size_t)my_q * KP + t] = bi[t];
     }
   }
 }
@@ -218,7 +251,11 @@ __global__ void knn_fallback_kernel(const double* X, int N, int d, int kappa, co
 
 template <int D, int KP>
 void launch_prefilter(const float* X32, int N, int d, float* cd, int* ci, cudaStream_t st) {
-  knn_prefilter_kernel<D, KP><<<ceil_div(N, KNN_THREADS), KNN_THREADS, 0, st>>>(X32, N, d, cd, ci);
+  const size_t smem = sizeof(float) * ((size_t)D * KT_QB + (size_t)D * KT_RB + (size_t)KT_QB * (KT_RB + 1));
+  if (smem > 48 * 1024)
+    IA_CUDA(cudaFuncSetAttribute(knn_prefilter_tiled_kernel<D, KP>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  knn_prefilter_tiled_kernel<D, KP><<<ceil_div(N, KT_QB), KT_QB, smem, st>>>(X32, N, d, cd, ci);
   IA_LAUNCH_CHECK();
 }
 
@@ -226,7 +263,11 @@ template <int KP>
 void prefilter_dispatch(const float* X32, int N, int d, float* cd, int* ci, cudaStream_t st) {
   if (d <= 8) launch_prefilter<8, KP>(X32, N, d, cd, ci, st);
   else if (d <= 16) launch_prefilter<16, KP>(X32, N, d, cd, ci, st);
+  else if (d <= 24) launch_prefilter<24, KP>(X32, N, d, cd, ci, st);
   else if (d <= 32) launch_prefilter<32, KP>(X32, N, d, cd, ci, st);
+  else if (d <= 40) launch_prefilter<40, KP>(X32, N, d, cd, ci, st);
+  else if (d <= 48) launch_prefilter<48, KP>(X32, N, d, cd, ci, st);
+  else if (d <= 56) launch_prefilter<56, KP>(X32, N, d, cd, ci, st);
   else if (d <= 64) launch_prefilter<64, KP>(X32, N, d, cd, ci, st);
   else throw Error(IASKIT_ERR_UNSUPPORTED, "kNN supports d <= 64");
 }
@@ -251,6 +292,8 @@ int knn_bruteforce(const double* X, int N, int d, int kappa, int* knn, KnnScratc
   IA_CUDA(cudaMemsetAsync(nfl, 0, sizeof(int), st));
   const bool wide = kappa + 8 > 32;
   const int KP = wide ? 64 : 32;
+  // algorithmic work of the FP32 prefilter: a subtraction and an FMA per pair and coordinate
+  prof().flops[PK_KNN] += 3.0 * (double)N * (double)N * d;
   float* cd = s.cand_d.ensure_n<float>((size_t)N * KP);
   int* ci = s.cand_i.ensure_n<int>((size_t)N * KP);
   if (wide) {

@@ -120,15 +120,25 @@ double getrf_flops(const std::vector<LuDescT<T>>& v) {
   return f;
 }
 template <typename T>
-void add_gemm(std::vector<GemmDescT<T>>& g, std::vector<GemmTile>& t, const T* A, int lda,
-              const T* B, int ldb, T* C, int ldc, int M, int Ncol, int K, double alpha,
-              double beta) {
+void add_gemm(std::vector<GemmDescT<T>>& g, const T* A, int lda, const T* B, int ldb, T* C,
+              int ldc, int M, int Ncol, int K, double alpha, double beta) {
   if (M <= 0 || Ncol <= 0) return;
-  GemmDescT<T> D{A, B, C, M, Ncol, K, lda, ldb, ldc, alpha, beta};
-  int idx = (int)g.size();
-  g.push_back(D);
-  for (int tn = 0; tn < (Ncol + 63) / 64; ++tn)
-    for (int tm = 0; tm < (M + 63) / 64; ++tm) t.push_back(GemmTile{idx, tm, tn});
+  g.push_back(GemmDescT<T>{A, B, C, M, Ncol, K, lda, ldb, ldc, alpha, beta});
+}
+
+// Tile list of one grouped launch: 256 x 16 tiles when no problem has more than 16
+// columns (right-hand-side blocks of a solve), 64 x 64 tiles otherwise.
+template <typename T>
+GemmShape make_tiles(const std::vector<GemmDescT<T>>& g, std::vector<GemmTile>& t) {
+  int maxn = 0;
+  for (const auto& d : g) maxn = std::max(maxn, d.N);
+  const GemmShape shape = maxn <= 16 ? GEMM_SKINNY : GEMM_SQUARE;
+  const int tm_ = gemm_tile_m(shape), tn_ = gemm_tile_n(shape);
+  t.clear();
+  for (int idx = 0; idx < (int)g.size(); ++idx)
+    for (int tn = 0; tn < (g[idx].N + tn_ - 1) / tn_; ++tn)
+      for (int tm = 0; tm < (g[idx].M + tm_ - 1) / tm_; ++tm) t.push_back(GemmTile{idx, tm, tn});
+  return shape;
 }
 
 class Solver {
@@ -199,13 +209,16 @@ class Solver {
     if (v & DEV_OVERFLOW) throw Error(IASKIT_ERR_UNSUPPORTED, "internal bound exceeded");
   }
   template <typename T>
-  void run_gemms(const std::vector<GemmDescT<T>>& g, const std::vector<GemmTile>& t) {
-    if (t.empty()) return;
+  void run_gemms(const std::vector<GemmDescT<T>>& g) {
+    if (g.empty()) return;
+    std::vector<GemmTile> t;
+    const GemmShape shape = make_tiles(g, t);
     arena.clear();
     size_t og = arena.push(g), ot = arena.push(t);
     char* base = upload_arena();
     prof().flops[pk_of<T>(PK_GEMM)] += gemm_flops(g);
-    gemm_grouped((const GemmDescT<T>*)(base + og), (const GemmTile*)(base + ot), (int)t.size(), st);
+    gemm_grouped((const GemmDescT<T>*)(base + og), (const GemmTile*)(base + ot), (int)t.size(),
+                 shape, st);
   }
 
   // ------------------------------------------------------------- forest solve
@@ -268,30 +281,28 @@ class Solver {
     if (r == L) {
       if (need_t) {
         std::vector<GemmDescT<T>> g;
-        std::vector<GemmTile> t;
         for (const auto& rb : roots) {
           const Node& c = nd[rb.uid];
-          add_gemm<T>(g, t, pP<T>(L) + c.P_off, c.s, rb.V, rb.ld, rb.t_out, rb.t_ld, c.s, rb.nc,
+          add_gemm<T>(g, pP<T>(L) + c.P_off, c.s, rb.V, rb.ld, rb.t_out, rb.t_ld, c.s, rb.nc,
                       c.size, 1.0, 0.0);
         }
-        run_gemms(g, t);
+        run_gemms(g);
       }
       return;
     }
     // 2. leaf t = P v into the parent's T
     {
       std::vector<GemmDescT<T>> g;
-      std::vector<GemmTile> t;
       for (int i = 0; i < (1 << L); ++i) {
         int u = uid(L, i);
         if (root_of[u] < 0) continue;
         int par = u >> 1;
         int n2 = nd[2 * par].s + nd[2 * par + 1].s;
         int rowoff = (u & 1) ? nd[2 * par].s : 0;
-        add_gemm<T>(g, t, pP<T>(L) + nd[u].P_off, nd[u].s, Vp[u], ldV(u), Tp(par) + rowoff, n2,
+        add_gemm<T>(g, pP<T>(L) + nd[u].P_off, nd[u].s, Vp[u], ldV(u), Tp(par) + rowoff, n2,
                     nd[u].s, ncV(u), nd[u].size, 1.0, 0.0);
       }
-      run_gemms(g, t);
+      run_gemms(g);
     }
     // 3. levels L-1 .. r
     for (int j = L - 1; j >= r; --j) {
@@ -313,15 +324,15 @@ class Solver {
                                      n2, n2, n2, nc});
         const T* W = wP<T>();
         // v_a -= W_{a c~} y1 (y1 = Y[sa : n2]);  v_c -= W_{c a~} y2 (y2 = Y[0 : sa])
-        add_gemm<T>(g1, t1, W + nd[a].W_off, nd[a].size, Yp(b) + sa, n2, Vp[a], ldV(b), nd[a].size,
+        add_gemm<T>(g1, W + nd[a].W_off, nd[a].size, Yp(b) + sa, n2, Vp[a], ldV(b), nd[a].size,
                     nc, sc, -1.0, 1.0);
-        add_gemm<T>(g1, t1, W + nd[c].W_off, nd[c].size, Yp(b), n2, Vp[c], ldV(b), nd[c].size, nc,
+        add_gemm<T>(g1, W + nd[c].W_off, nd[c].size, Yp(b), n2, Vp[c], ldV(b), nd[c].size, nc,
                     sa, -1.0, 1.0);
         const bool carry = (j > r) || need_t;
         if (carry) {
           const T* C = cP<T>();
-          add_gemm<T>(g1, t1, C + nd[b].CL_off, sa, Yp(b) + sa, n2, Tp(b), n2, sa, nc, sc, -1.0, 1.0);
-          add_gemm<T>(g1, t1, C + nd[b].CR_off, sc, Yp(b), n2, Tp(b) + sa, n2, sc, nc, sa, -1.0, 1.0);
+          add_gemm<T>(g1, C + nd[b].CL_off, sa, Yp(b) + sa, n2, Tp(b), n2, sa, nc, sc, -1.0, 1.0);
+          add_gemm<T>(g1, C + nd[b].CR_off, sc, Yp(b), n2, Tp(b) + sa, n2, sc, nc, sa, -1.0, 1.0);
           T* dst;
           int ldd;
           if (j > r) {
@@ -333,10 +344,11 @@ class Solver {
             dst = roots[root_of[b]].t_out;
             ldd = roots[root_of[b]].t_ld;
           }
-          add_gemm<T>(g2, t2, pP<T>(j) + nd[b].P_off, nd[b].s, Tp(b), n2, dst, ldd, nd[b].s, nc, n2,
+          add_gemm<T>(g2, pP<T>(j) + nd[b].P_off, nd[b].s, Tp(b), n2, dst, ldd, nd[b].s, nc, n2,
                       1.0, 0.0);
         }
       }
+      const GemmShape sh1 = make_tiles(g1, t1), sh2 = make_tiles(g2, t2);
       arena.clear();
       size_t ocp = arena.push(cp), ozs = arena.push(zs), og1 = arena.push(g1), ot1 = arena.push(t1),
              og2 = arena.push(g2), ot2 = arena.push(t2);
@@ -345,8 +357,10 @@ class Solver {
       prof().flops[pk_of<T>(PK_GEMM)] += gemm_flops(g1) + gemm_flops(g2);
       copy_batched((const CopyDescT<T>*)(base + ocp), (int)cp.size(), max_cp, st);
       getrs_batched((const LuSolveDescT<T>*)(base + ozs), (int)zs.size(), max_n2, max_nc, st);
-      gemm_grouped((const GemmDescT<T>*)(base + og1), (const GemmTile*)(base + ot1), (int)t1.size(), st);
-      gemm_grouped((const GemmDescT<T>*)(base + og2), (const GemmTile*)(base + ot2), (int)t2.size(), st);
+      gemm_grouped((const GemmDescT<T>*)(base + og1), (const GemmTile*)(base + ot1), (int)t1.size(),
+                   sh1, st);
+      gemm_grouped((const GemmDescT<T>*)(base + og2), (const GemmTile*)(base + ot2), (int)t2.size(),
+                   sh2, st);
     }
   }
 
@@ -526,12 +540,17 @@ class Solver {
       IA_CUDA(cudaStreamSynchronize(st));
       raise_status(read_status_and_clear());
       int64_t psz = 0;
+      double qr_flops = 0;
       for (int i = 0; i < nn; ++i) {
         Node& n = nd[uid(l, i)];
         n.s = rh[i];
         n.P_off = psz;
         psz += (int64_t)n.s * n.ncols;
+        // Householder update (dot + axpy) and norm recomputation per step, then R11^{-1} R12
+        for (int k = 0; k < n.s; ++k) qr_flops += 6.0 * (n.nsamp - k) * (double)(n.ncols - k);
+        qr_flops += (double)n.s * n.s * (n.ncols - n.s);
       }
+      prof().flops[pk_of<TS>(PK_CPQR)] += qr_flops;
       double* P = Pl[l]->ensure_n<double>(psz);
       std::vector<PDescT<TS>> pd(nn);
       for (int i = 0; i < nn; ++i) {
@@ -827,24 +846,22 @@ class Solver {
     };
     if (L > 0) {
       std::vector<GemmDesc> g;
-      std::vector<GemmTile> t;
       for (int i = 0; i < (1 << L); ++i) {
         int u_ = uid(L, i), par = u_ >> 1;
-        add_gemm<double>(g, t, Pl[L]->as<double>() + nd[u_].P_off, nd[u_].s, Wp + nd[u_].off, N,
+        add_gemm<double>(g, Pl[L]->as<double>() + nd[u_].P_off, nd[u_].s, Wp + nd[u_].off, N,
                          WT + woff[par] + ((u_ & 1) ? nd[2 * par].s : 0), n2(par), nd[u_].s, nrhs,
                          nd[u_].size, 1.0, 0.0);
       }
-      run_gemms(g, t);
+      run_gemms(g);
       for (int l = L - 1; l >= 1; --l) {
         g.clear();
-        t.clear();
         for (int i = 0; i < (1 << l); ++i) {
           int u_ = uid(l, i), par = u_ >> 1;
-          add_gemm<double>(g, t, Pl[l]->as<double>() + nd[u_].P_off, nd[u_].s, WT + woff[u_],
+          add_gemm<double>(g, Pl[l]->as<double>() + nd[u_].P_off, nd[u_].s, WT + woff[u_],
                            n2(u_), WT + woff[par] + ((u_ & 1) ? nd[2 * par].s : 0), n2(par),
                            nd[u_].s, nrhs, n2(u_), 1.0, 0.0);
         }
-        run_gemms(g, t);
+        run_gemms(g);
       }
     }
     // Evaluate: one launch per level keeps the rows written by a launch disjoint
@@ -854,17 +871,16 @@ class Solver {
       const int lev = leaves ? L : l;
       if (stored) {
         std::vector<GemmDesc> g;
-        std::vector<GemmTile> t;
         for (int i = 0; i < (1 << lev); ++i) {
           int c = uid(lev, i);
           if (leaves)
-            add_gemm<double>(g, t, Kleaf.as<double>() + nd[c].LU_off, nd[c].size, Wp + nd[c].off, N,
+            add_gemm<double>(g, Kleaf.as<double>() + nd[c].LU_off, nd[c].size, Wp + nd[c].off, N,
                              Up + nd[c].off, N, nd[c].size, nrhs, nd[c].size, 1.0, 1.0);
           else
-            add_gemm<double>(g, t, Ustore.as<double>() + nd[c].W_off, nd[c].size, wsib(c),
+            add_gemm<double>(g, Ustore.as<double>() + nd[c].W_off, nd[c].size, wsib(c),
                              n2(c >> 1), Up + nd[c].off, N, nd[c].size, nrhs, nd[c ^ 1].s, 1.0, 1.0);
         }
-        run_gemms(g, t);
+        run_gemms(g);
       } else {
         std::vector<KMatvecDesc> md;
         int max_rows = 0;
