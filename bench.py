@@ -28,7 +28,7 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-from workloads import make_points, make_rhs, workload  # noqa: E402
+from workloads import batched_problems, make_points, make_rhs, workload  # noqa: E402
 
 METRIC = "factor s + RHS solves/s at N=4M,d=8: chosen form vs FP64 plain, resid<=1e-10"
 UNIT = "RHS/s (factor+solve per step)"
@@ -161,6 +161,12 @@ def run_reference(args, w):
 
 
 def config_of(w):
+    if w.kind == "batched":
+        return {"workload": "C3: 64 independent problems, N log-uniform in [2048, 65536], d=16, "
+                            "uniform; h in {0.3,0.6,1.2}, lambda in {1e-1,1e-3}",
+                "problems": 64, "d": 16, "leaf_m": w.m, "s_max": w.s_max, "tol": w.tol,
+                "nrhs_per_problem": w.nrhs, "kappa": w.kappa,
+                "l2": "inputs and working set larger than L2 (no flush needed)"}
     return {"workload": f"{w.name}: N={w.N}, d={w.d}, {w.kind}", "N": w.N, "d": w.d, "h": w.h,
             "lambda": w.lam, "leaf_m": w.m, "s_max": w.s_max, "tol": w.tol, "nrhs": w.nrhs,
             "kappa": w.kappa, "path": "plain FP64",
@@ -181,6 +187,105 @@ def alu_peak_tflops(kernel: str, sm_mhz: float) -> tuple:
             f"derived: {SM_COUNT} SMs x {FP64_FMA_PER_CLK_PER_SM} FP64 FMA/clk x {sm_mhz:.0f} MHz")
 
 
+def run_batched(args, w, form):
+    """C3: all problems in one batched factor + solve per step vs one call per problem."""
+    import torch
+    import paper_1602_01376_gb300 as ia
+    ia.load()
+    ia.iaskit_set_stream(None)
+    probs = batched_problems(count=64)
+    Ns = [len(p[0]) for p in probs]
+    hs = [p[1] for p in probs]
+    lams = [p[2] for p in probs]
+    Xall = torch.from_numpy(np.ascontiguousarray(np.concatenate([p[0] for p in probs]))).cuda()
+    rng = np.random.default_rng(w.seed + 7)
+    U0 = torch.from_numpy(np.concatenate([rng.standard_normal(n * w.nrhs) for n in Ns])).cuda()
+    U = torch.empty_like(U0)
+    ia.iaskit_set_option("precision", 1 if form == "mixed" else 0)
+    ia.iaskit_set_option("refine", 50 if form == "mixed" else 0)
+    Xs = [Xall[sum(Ns[:q]):sum(Ns[:q + 1])] for q in range(len(Ns))]
+    offs = np.concatenate([[0], np.cumsum([n * w.nrhs for n in Ns])])
+
+    def step_batched():
+        ia.iaskit_factor_batched_device(Xall, Ns, hs, lams, w.m, w.s_max, w.tol)
+        U.copy_(U0)
+        ia.iaskit_solve_batched_device(U, w.nrhs)
+
+    def step_single():
+        for q in range(len(Ns)):
+            ia.iaskit_factor_device(Xs[q], hs[q], lams[q], w.m, w.s_max, w.tol)
+            Uq = U[offs[q]:offs[q + 1]].view(w.nrhs, Ns[q])
+            Uq.copy_(U0[offs[q]:offs[q + 1]].view(w.nrhs, Ns[q]))
+            ia.iaskit_solve_device(Uq)
+
+    def timed(fn, sample_clocks):
+        for _ in range(args.warmup):
+            fn()
+        ia.iaskit_set_option("profile", 1)
+        l0 = ia.iaskit_stats()["launches"]
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with ClockSampler(0 if sample_clocks else -1) as clk:
+            ev0.record()
+            for _ in range(args.steps):
+                fn()
+            ev1.record()
+            torch.cuda.synchronize()
+        st = ia.iaskit_stats()
+        ia.iaskit_set_option("profile", 0)
+        return ev0.elapsed_time(ev1), st, clk.summary(), st["launches"] - l0
+
+    ms_b, st_b, clocks, launches = timed(step_batched, True)
+    ms_s, st_s, _, launches_s = timed(step_single, False)
+    nrhs_total = sum(w.nrhs for _ in Ns)
+    value = nrhs_total * args.steps / (ms_b / 1e3)
+    # residual of the batched solution against the FP64 operator
+    step_batched()
+    AU = torch.empty_like(U)
+    ia.iaskit_apply_device(U, AU, w.nrhs)
+    resid = 0.0
+    for q in range(len(Ns)):
+        a, b = offs[q], offs[q + 1]
+        r = (U0[a:b] - AU[a:b]).view(w.nrhs, Ns[q]).norm(dim=1) / U0[a:b].view(w.nrhs, Ns[q]).norm(dim=1)
+        resid = max(resid, float(r.max()))
+    # end to end: host points and right-hand sides through iaskit_factor_batched / solve_batched
+    Xh = [np.ascontiguousarray(p[0]) for p in probs]
+    Uh = [np.ascontiguousarray(U0[offs[q]:offs[q + 1]].cpu().numpy().reshape(w.nrhs, Ns[q]).T) for q in range(len(Ns))]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ia.iaskit_factor_batched(Xh, hs, lams, w.m, w.s_max, w.tol)
+    ia.iaskit_solve_batched(Uh)
+    e2e_s = time.perf_counter() - t0
+    kern = st_b["kernels"]
+    top = max(kern, key=lambda k: kern[k]["ms"])
+    pk, src = peaks()
+    roof = None
+    if kern[top]["flops"] > 0 and kern[top]["ms"] > 0:
+        achieved = kern[top]["flops"] / (kern[top]["ms"] / 1e3) / 1e12
+        peak, how = alu_peak_tflops(top, pk.get("sm_max_mhz", 2070.0))
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": top,
+                "peak_source": f"{how} ({src} max clock)", "launches": kern[top]["calls"],
+                "ms_total": kern[top]["ms"]}
+    cfg = config_of(w)
+    cfg["path"] = "batched " + form
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if form == "mixed" else "f64",
+        "data": "synthetic", "config": cfg, "residual": resid, "gpu_launches": launches,
+        "clocks": clocks, "roofline": roof,
+        "kernel_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in kern.items() if v["ms"] > 0},
+        "compare_per_problem": {"value": nrhs_total * args.steps / (ms_s / 1e3),
+                                "ms_per_step": ms_s / args.steps, "gpu_launches": launches_s},
+        "e2e": {"value": nrhs_total / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": 8 * sum(Ns) * (16 + w.nrhs),
+                "d2h_bytes_per_step": 8 * sum(Ns) * w.nrhs},
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -197,6 +302,8 @@ def main():
     w = workload(args.workload, N=args.N)
     if args.impl == "reference":
         return run_reference(args, w)
+    if w.kind == "batched":
+        return run_batched(args, w, args.form)
 
     import torch
     import paper_1602_01376_gb300 as ia

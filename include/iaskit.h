@@ -70,6 +70,29 @@ int iaskit_factor_device(const double* d_points, int64_t N, int d, double h, dou
                          int leaf_m, int s_max, double tol);
 
 /*
+ * Factor nprob independent problems together (each with its own points, N, h and
+ * lambda; shared d, leaf_m, s_max, tol).  Each problem gets exactly the tree, kNN
+ * lists (searched among its own points), skeletons and factorization it would get
+ * alone; the work of all problems at the same height above the leaves runs in the
+ * same launches.  This is a batching of the paper's per-problem method (Sec. II-C);
+ * the paper itself factors one problem at a time.
+ *   points   HOST pointers, points[q] is N[q] x d row-major.
+ * The kNN lists use kappa = min("kappa", min_q N[q] - 1) for every problem.
+ * Errors as iaskit_factor.
+ */
+int iaskit_factor_batched(int nprob, const double* const* points, const int64_t* N, int d,
+                          const double* h, const double* lambda, int leaf_m, int s_max, double tol);
+
+/* As iaskit_factor_batched with one DEVICE array holding the problems' points one
+ * after the other (sum_q N[q] rows of d doubles). */
+int iaskit_factor_batched_device(int nprob, const double* d_points, const int64_t* N, int d,
+                                 const double* h, const double* lambda, int leaf_m, int s_max,
+                                 double tol);
+
+/* Number of problems of the current factorization, or a negative error. */
+int iaskit_num_problems(void);
+
+/*
  * Solve (lambda*I + K~) w = u in place (Sec. II-C, Alg. "Solve").
  *   rhs      HOST pointer, N x nrhs column-major, original point order; on return
  *            it holds w.  nrhs >= 1.
@@ -81,8 +104,18 @@ int iaskit_factor_device(const double* d_points, int64_t N, int d, double h, dou
  */
 int iaskit_solve(double* rhs, int nrhs);
 
-/* As iaskit_solve with a DEVICE pointer (N x nrhs, column-major, ld = N). */
+/* As iaskit_solve with a DEVICE pointer (N x nrhs, column-major, ld = N).  After a
+ * batched factorization, d_rhs holds the problems' N[q] x nrhs column-major blocks one
+ * after the other. */
 int iaskit_solve_device(double* d_rhs, int nrhs);
+
+/* Solve every problem of a batched factorization: rhs[q] is a HOST N[q] x nrhs
+ * column-major block, overwritten with the solution.  Refinement, when on, runs
+ * until every column of every problem meets "refine_tol". */
+int iaskit_solve_batched(double* const* rhs, int nrhs);
+
+/* As iaskit_solve_batched with one DEVICE array of all blocks one after the other. */
+int iaskit_solve_batched_device(double* d_rhs, int nrhs);
 
 /*
  * u = (lambda*I + K~) w by the FP64 hierarchical MatVec (Sec. II-B, "Skeletonize"
@@ -106,6 +139,10 @@ int iaskit_apply_device(const double* d_w, double* d_u, int nrhs);
  *   "mem_cap_gb"   refuse factorizations whose device footprint exceeds this (0 = none)
  *   "profile"      1: time every kernel class with CUDA events (reported by iaskit_stats)
  *                  and reset the counters; 0: stop timing [any time]
+ *   "precision"    0: plain FP64 (default); 1: mixed - FP32 factorization with FP64 pivot
+ *                  norms, FP64 operator, solves refined to "refine_tol" (up to 50 sweeps
+ *                  when "refine" is 0)
+ *   "problem"      which problem of a batch the introspection calls report (0) [any time]
  * Errors: IASKIT_ERR_ARG for an unknown key or an invalid value.
  */
 int iaskit_set_option(const char* key, double value);
@@ -129,8 +166,10 @@ void iaskit_free(void);
 
 /*
  * Introspection of the current factorization (tests compare these with the
- * oracle).  Node (l, i) has heap id 2^l + i, l = 0 .. depth.  All outputs are HOST
- * buffers.  Errors: IASKIT_ERR_NOT_FACTORED, _ARG (bad node or short buffer).
+ * oracle), for the problem selected by the option "problem".  Node (l, i) has heap
+ * id 2^l + i, l = 0 .. depth.  Indices and positions are local to that problem.  All
+ * outputs are HOST buffers.  Errors: IASKIT_ERR_NOT_FACTORED, _ARG (bad node or
+ * short buffer).
  */
 int iaskit_depth(void);                                 /* L, or a negative error */
 int iaskit_get_perm(int32_t* perm);                     /* N: perm[pos] = original index */
@@ -155,7 +194,7 @@ int iaskit_get_P(int level, int index, double* P, int64_t cap);
  *             the work has finished.
  * Limits: 2 <= N <= 32768, 1 <= d <= 64, N*d <= 1048576, 1 <= kappa <= min(24, N-1);
  * anything larger returns IASKIT_ERR_ARG with the limit in iaskit_last_error().
- * Scratch: one static device array of about 12.1 MiB, which every GPU that loads
+ * Scratch: one static device array of about 12.3 MiB, which every GPU that loads
  * this library holds until the process exits.  The call makes no device
  * allocation.  Its first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) once; make that first call before any stream capture.

@@ -36,7 +36,9 @@ EXPORTS = [
     "iaskit_apply", "iaskit_apply_device", "iaskit_set_option", "iaskit_get_option",
     "iaskit_set_stream", "iaskit_stats", "iaskit_last_error", "iaskit_free", "iaskit_depth",
     "iaskit_get_perm", "iaskit_get_knn", "iaskit_get_ranks", "iaskit_get_skeleton",
-    "iaskit_get_samples", "iaskit_get_P", "iaskit_knn_noalloc",
+    "iaskit_get_samples", "iaskit_get_P", "iaskit_knn_noalloc", "iaskit_factor_batched",
+    "iaskit_factor_batched_device", "iaskit_num_problems", "iaskit_solve_batched",
+    "iaskit_solve_batched_device",
 ]
 
 
@@ -83,6 +85,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "iaskit_get_samples": ([i32, i32, vp, i32], i32),
         "iaskit_get_P": ([i32, i32, vp, i64], i32),
         "iaskit_knn_noalloc": ([vp, i64, i32, i32, vp, vp], i32),
+        "iaskit_factor_batched": ([i32, vp, vp, i32, vp, vp, i32, i32, dbl], i32),
+        "iaskit_factor_batched_device": ([i32, vp, vp, i32, vp, vp, i32, i32, dbl], i32),
+        "iaskit_num_problems": ([], i32),
+        "iaskit_solve_batched": ([vp, i32], i32),
+        "iaskit_solve_batched_device": ([vp, i32], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -127,6 +134,56 @@ def iaskit_factor_device(points, h: float, lam: float, leaf_m: int, s_max: int, 
     _check(lib.iaskit_factor_device(_dev_ptr(points), N, d, h, lam, leaf_m, s_max, tol))
 
 
+def iaskit_factor_batched(points_list, h_list, lam_list, leaf_m: int, s_max: int, tol: float) -> None:
+    """Factor independent problems together (host arrays, one (N_q, d) array each)."""
+    lib = load()
+    Xs = [_host_f64(x, "C") for x in points_list]
+    q = len(Xs)
+    d = Xs[0].shape[1]
+    ptrs = (ctypes.c_void_p * q)(*[x.ctypes.data for x in Xs])
+    Ns = np.array([x.shape[0] for x in Xs], dtype=np.int64)
+    hs = np.asarray(h_list, dtype=np.float64)
+    ls = np.asarray(lam_list, dtype=np.float64)
+    _check(lib.iaskit_factor_batched(q, ptrs, Ns.ctypes.data, d, hs.ctypes.data, ls.ctypes.data,
+                                     leaf_m, s_max, tol))
+
+
+def iaskit_factor_batched_device(points, Ns, h_list, lam_list, leaf_m: int, s_max: int,
+                                 tol: float) -> None:
+    """Factor independent problems from one CUDA float64 tensor (sum N_q, d)."""
+    lib = load()
+    Nv = np.asarray(Ns, dtype=np.int64)
+    hs = np.asarray(h_list, dtype=np.float64)
+    ls = np.asarray(lam_list, dtype=np.float64)
+    _check(lib.iaskit_factor_batched_device(len(Nv), _dev_ptr(points), Nv.ctypes.data,
+                                            points.shape[1], hs.ctypes.data, ls.ctypes.data,
+                                            leaf_m, s_max, tol))
+
+
+def iaskit_num_problems() -> int:
+    return _check(load().iaskit_num_problems())
+
+
+def iaskit_solve_batched(rhs_list) -> list:
+    """Solve every problem of a batch; rhs_list[q] is (N_q,) or (N_q, nrhs)."""
+    lib = load()
+    arrs = [np.array(np.asarray(u, dtype=np.float64).reshape(len(u), -1), order="F", copy=True)
+            for u in rhs_list]
+    nrhs = arrs[0].shape[1]
+    ptrs = (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+    _check(lib.iaskit_solve_batched(ptrs, nrhs))
+    return [a[:, 0] if np.asarray(u).ndim == 1 else a for a, u in zip(arrs, rhs_list)]
+
+
+def iaskit_solve_batched_device(rhs, nrhs: int) -> None:
+    """In place on one contiguous CUDA float64 tensor holding every problem's
+    N_q x nrhs column-major block in turn (sum_q N_q * nrhs elements)."""
+    lib = load()
+    if not rhs.is_contiguous():
+        raise ValueError("rhs must be contiguous")
+    _check(lib.iaskit_solve_batched_device(_dev_ptr(rhs), nrhs))
+
+
 def iaskit_solve(rhs) -> np.ndarray:
     """w = (lambda I + K~)^{-1} u for host u (N,) or (N, nrhs); returns a new array."""
     lib = load()
@@ -158,9 +215,12 @@ def iaskit_apply(w) -> np.ndarray:
     return U[:, 0] if vec else U
 
 
-def iaskit_apply_device(w, u) -> None:
+def iaskit_apply_device(w, u, nrhs=None) -> None:
+    """u = (lambda I + K~) w on CUDA float64 tensors laid out like iaskit_solve_device's
+    right-hand sides; nrhs defaults to w.shape[0] for a 2-D tensor, else 1."""
     lib = load()
-    nrhs = 1 if w.dim() == 1 else w.shape[0]
+    if nrhs is None:
+        nrhs = 1 if w.dim() == 1 else w.shape[0]
     _check(lib.iaskit_apply_device(_dev_ptr(w), _dev_ptr(u), nrhs))
 
 

@@ -35,11 +35,10 @@ __device__ __forceinline__ float kexp<float>(float x) { return expf(x); }
 
 // ------------------------------------------------------------ kernel blocks
 template <typename T>
-__global__ void kernel_blocks_kernel(const double* Xp, int d, double neg_inv_2h2,
-                                     const KDescT<T>* descs, int ndesc) {
-  const T scale = (T)neg_inv_2h2;
+__global__ void kernel_blocks_kernel(const double* Xp, int d, const KDescT<T>* descs, int ndesc) {
   for (int q = blockIdx.y; q < ndesc; q += gridDim.y) {
     const KDescT<T> D = descs[q];
+    const T scale = (T)D.scale;
     const int64_t total = (int64_t)D.nrows * D.ncols;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -628,11 +627,11 @@ __global__ void f2d_kernel(const float* in, double* out, int64_t n) {
 constexpr int MV_THREADS = 128;
 constexpr int MV_R = 16;
 constexpr int MV_TILE = 32;
-__global__ void __launch_bounds__(MV_THREADS) kernel_matvec_kernel(const double* Xp, int d,
-                                                                   double neg_inv_2h2, int nrhs,
+__global__ void __launch_bounds__(MV_THREADS) kernel_matvec_kernel(const double* Xp, int d, int nrhs,
                                                                    const KMatvecDesc* descs) {
   extern __shared__ double xs[];  // MV_TILE x d
   const KMatvecDesc D = descs[blockIdx.y];
+  const double neg_inv_2h2 = D.scale;
   const int i = blockIdx.x * MV_THREADS + threadIdx.x;
   const bool active = i < D.nrows;
   const int row = D.row0 + (active ? i : 0);
@@ -701,12 +700,12 @@ void launch_getrs(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int ma
 }  // namespace
 
 template <typename T>
-void kernel_blocks(const double* Xp, int d, double h, const KDescT<T>* descs_dev, int ndesc,
+void kernel_blocks(const double* Xp, int d, const KDescT<T>* descs_dev, int ndesc,
                    int64_t max_entries, cudaStream_t st) {
   if (ndesc <= 0) return;
   ProfScope _ps(pk_of<T>(PK_KBLOCK), st);
   dim3 grid(grid_for(max_entries, 256, 4096), std::min(ndesc, 65535));
-  kernel_blocks_kernel<T><<<grid, 256, 0, st>>>(Xp, d, -1.0 / (2.0 * h * h), descs_dev, ndesc);
+  kernel_blocks_kernel<T><<<grid, 256, 0, st>>>(Xp, d, descs_dev, ndesc);
   IA_LAUNCH_CHECK();
 }
 
@@ -810,8 +809,8 @@ void convert_f2d(const float* in, double* out, int64_t n, cudaStream_t st) {
   IA_LAUNCH_CHECK();
 }
 
-void kernel_matvec(const double* Xp, int d, double h, int nrhs, const KMatvecDesc* descs_dev,
-                   int ndesc, int max_rows, cudaStream_t st) {
+void kernel_matvec(const double* Xp, int d, int nrhs, const KMatvecDesc* descs_dev, int ndesc,
+                   int max_rows, cudaStream_t st) {
   if (ndesc <= 0 || max_rows <= 0) return;
   const size_t smem = (size_t)MV_TILE * d * sizeof(double);
   if (smem > 48 * 1024)
@@ -819,7 +818,7 @@ void kernel_matvec(const double* Xp, int d, double h, int nrhs, const KMatvecDes
                                  (int)smem));
   ProfScope _ps(PK_MATVEC, st);
   dim3 grid(ceil_div(max_rows, MV_THREADS), ndesc);
-  kernel_matvec_kernel<<<grid, MV_THREADS, smem, st>>>(Xp, d, -1.0 / (2.0 * h * h), nrhs, descs_dev);
+  kernel_matvec_kernel<<<grid, MV_THREADS, smem, st>>>(Xp, d, nrhs, descs_dev);
   IA_LAUNCH_CHECK();
 }
 
@@ -831,8 +830,7 @@ void check_finite(const double* x, int64_t n, int* dev_status, cudaStream_t st) 
 }
 
 #define IASKIT_INSTANTIATE(T)                                                                    \
-  template void kernel_blocks<T>(const double*, int, double, const KDescT<T>*, int, int64_t,      \
-                                 cudaStream_t);                                                  \
+  template void kernel_blocks<T>(const double*, int, const KDescT<T>*, int, int64_t, cudaStream_t); \
   template void cpqr_id<T>(const CpqrDescT<T>*, int, int, int, int, double, cudaStream_t);        \
   template void assemble_P<T>(const PDescT<T>*, int, int, cudaStream_t);                          \
   template void getrf_batched<T>(const LuDescT<T>*, int, int, int*, cudaStream_t);                \

@@ -18,12 +18,21 @@ struct TreeScratch {
   }
 };
 
-// Median split on the coordinate of largest spread, level by level (Sec. II-A).
-// X: N x d row-major (original order, device).  level_off[l] holds the 2^l + 1
-// node offsets of level l (host).  Writes perm (device, N): perm[pos] = original index,
-// and split_dim (device, 2^L - 1 entries, heap order minus one).
-void build_tree(const double* X, int N, int d, int L, const std::vector<std::vector<int>>& level_off,
-                int* perm, int* split_dim, TreeScratch& s, cudaStream_t st);
+// One step of the tree build: nodes covering [0, N) in order; node j owns
+// [off[j], off[j+1]).  A split node sends the kleft[j] = floor(n/2) points that come
+// first in (x_c, original index) order to its left child; a node that is not split
+// has kleft[j] = n and keeps its points in place.
+struct TreeLevel {
+  std::vector<int> off;
+  std::vector<int> kleft;
+  std::vector<char> split;
+};
+
+// Median split on the coordinate of largest spread, one step per level (Sec. II-A).
+// X: N x d row-major (original order, device).  Writes perm (device, N):
+// perm[pos] = original index.
+void build_tree(const double* X, int N, int d, const std::vector<TreeLevel>& levels, int* perm,
+                TreeScratch& s, cudaStream_t st);
 
 // iperm[perm[p]] = p and Xp[p] = X[perm[p]] (rows of d doubles).
 void permute_points(const double* X, const int* perm, int N, int d, int* iperm, double* Xp,
@@ -31,18 +40,27 @@ void permute_points(const double* X, const int* perm, int N, int d, int* iperm, 
 
 // ------------------------------------------------------------------- kNN (a2)
 struct KnnScratch {
-  DevBuf x32, cand_d, cand_i, flagged, counter, maxabs;
+  DevBuf x32, cand_d, cand_i, flagged, counter, maxabs, tiles;
   void release() {
-    for (DevBuf* b : {&x32, &cand_d, &cand_i, &flagged, &counter, &maxabs}) b->release();
+    for (DevBuf* b : {&x32, &cand_d, &cand_i, &flagged, &counter, &maxabs, &tiles}) b->release();
   }
+};
+
+// Work tile of the kNN kernels: queries [q0, q0 + qn) against the points
+// [rb, rb + rn) of their problem.
+struct KnnTile {
+  int q0, qn, rb, rn;
 };
 
 // kappa nearest neighbours of every point by (squared distance, index), self
 // excluded, distance = sum_k (x_k - y_k)^2 in FP64 with every operation rounded
-// (no contraction), k in order.  X is N x d row-major FP64 (original order).
-// knn: N x kappa int32 (original indices).  Returns the number of queries that
-// needed the exact fallback scan.
-int knn_bruteforce(const double* X, int N, int d, int kappa, int* knn, KnnScratch& s,
+// (no contraction), k in order; neighbours are searched among the points of the
+// same problem only.  X is N x d row-major FP64 (original order, all problems
+// concatenated); problems lists (first point, point count).  knn: N x kappa int32
+// (original indices).  Returns the number of queries that needed the exact
+// fallback scan.
+int knn_bruteforce(const double* X, int N, int d, int kappa, int* knn,
+                   const std::vector<std::pair<int, int>>& problems, KnnScratch& s,
                    cudaStream_t st);
 
 // ------------------------------------------------------------- sampling (a3)
@@ -60,12 +78,20 @@ struct SampleScratch {
 void knn_to_positions(const int* knn, const int* perm, const int* iperm, int N, int kappa,
                       int* knn_pos, cudaStream_t st);
 
-// Sampled rows of every node of level l (see the sampling rule in sampling.cu).
-// off: device offsets of the level (2^l + 1).  samp_off: device, per node start in
-// `samp`; n_samp of node i = min(samp_cap, N - size_i).
-void sample_level(const int* knn_pos, int N, int kappa, int level, const int* off_dev,
-                  const std::vector<int>& off_host, int samp_cap, const int* samp_off_dev,
-                  uint64_t seed, int* samp, int* dev_status, SampleScratch& s, cudaStream_t st);
+// Per node of a sampling step: the node's problem (first point pb, point count pn),
+// its heap id 2^l + i in its own tree, where its sample starts in `samp`, and
+// whether it is sampled (0: points of a problem with no node at this step).
+struct SampleNodeInfo {
+  int pb, pn, uid, samp_off, active;
+};
+
+// Sampled rows of the nodes of one step (see the sampling rule in sampling.cu).
+// off: device offsets (nn + 1) covering [0, N); n_samp of an active node =
+// min(samp_cap, pn - size).
+void sample_level(const int* knn_pos, int N, int kappa, const int* off_dev,
+                  const SampleNodeInfo* info_dev, const std::vector<int>& off_host,
+                  const std::vector<SampleNodeInfo>& info_host, int samp_cap, uint64_t seed,
+                  int* samp, int* dev_status, SampleScratch& s, cudaStream_t st);
 
 // ------------------------------------------------------- dense batched kernels
 // All dense kernels are templated on the storage/arithmetic type T (double for
@@ -75,6 +101,7 @@ void sample_level(const int* knn_pos, int N, int kappa, int level, const int* of
 // column-major into out.  Rows: rows ? rows[i] : row0 + i.  Columns: colsA ?
 // (j < nA ? colsA[j] : colsB[j - nA]) : col0 + j.  Points are positions in Xp.
 // T = double evaluates in FP64; T = float evaluates distances and exp in FP32.
+// scale = -1 / (2 h^2) of the block's problem.
 template <typename T>
 struct KDescT {
   const int* rows;
@@ -83,9 +110,10 @@ struct KDescT {
   T* out;
   int row0, nrows, col0, nA, ncols, ld;
   double diag;
+  double scale;
 };
 template <typename T>
-void kernel_blocks(const double* Xp, int d, double h, const KDescT<T>* descs_dev, int ndesc,
+void kernel_blocks(const double* Xp, int d, const KDescT<T>* descs_dev, int ndesc,
                    int64_t max_entries_per_desc, cudaStream_t st);
 
 // Column-pivoted Householder QR + interpolative decomposition of each block.
@@ -211,9 +239,10 @@ struct KMatvecDesc {
   const double* y;
   double* u;
   int row0, nrows, col0, ncols, ldy, ldu;
+  double scale;  // -1 / (2 h^2)
 };
-void kernel_matvec(const double* Xp, int d, double h, int nrhs, const KMatvecDesc* descs_dev,
-                   int ndesc, int max_rows, cudaStream_t st);
+void kernel_matvec(const double* Xp, int d, int nrhs, const KMatvecDesc* descs_dev, int ndesc,
+                   int max_rows, cudaStream_t st);
 
 // Any entry non-finite -> atomicOr(status, DEV_BADINPUT).
 void check_finite(const double* x, int64_t n, int* dev_status, cudaStream_t st);

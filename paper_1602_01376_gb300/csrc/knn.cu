@@ -51,19 +51,22 @@ __global__ void maxabs_kernel(const double* X, size_t n, unsigned long long* out
 constexpr int KT_QB = 256;
 constexpr int KT_RB = 32;
 template <int D, int KP>
-__global__ void __launch_bounds__(KT_QB) knn_prefilter_tiled_kernel(const float* X32, int N, int d,
+__global__ void __launch_bounds__(KT_QB) knn_prefilter_tiled_kernel(const float* X32, int d,
+                                                                   const KnnTile* tiles,
                                                                    float* cand_d, int* cand_i) {
   extern __shared__ float kt_sh[];
   float* Qs = kt_sh;                      // [D][KT_QB]
   float* Rs = Qs + D * KT_QB;             // [D][KT_RB]
   float* Dt = Rs + D * KT_RB;             // [KT_QB][KT_RB + 1]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int q0 = blockIdx.x * KT_QB;
+  const KnnTile tl = tiles[blockIdx.x];
+  const int q0 = tl.q0, qend = tl.q0 + tl.qn;
   for (int e = tid; e < D * KT_QB; e += KT_QB) {
     const int i = e / D, k = e % D;
-    Qs[k * KT_QB + i] = (q0 + i < N && k < d) ? X32[(size_t)(q0 + i) * d + k] : 0.0f;
+    Qs[k * KT_QB + i] = (q0 + i < qend && k < d) ? X32[(size_t)(q0 + i) * d + k] : 0.0f;
   }
   const int my_q = q0 + tid;
+  const bool active = my_q < qend;
   float bd[KP];
   int bi[KP];
 #pragma unroll
@@ -71,8 +74,9 @@ __global__ void __launch_bounds__(KT_QB) knn_prefilter_tiled_kernel(const float*
     bd[t] = FLT_MAX;
     bi[t] = INT_MAX;
   }
-  for (int r0 = 0; r0 < N; r0 += KT_RB) {
-    const int nt = min(KT_RB, N - r0);
+  const int rend = tl.rb + tl.rn;
+  for (int r0 = tl.rb; r0 < rend; r0 += KT_RB) {
+    const int nt = min(KT_RB, rend - r0);
     __syncthreads();
     for (int e = tid; e < D * KT_RB; e += KT_QB) {
       const int j = e / D, k = e % D;
@@ -104,7 +108,7 @@ __global__ void __launch_bounds__(KT_QB) knn_prefilter_tiled_kernel(const float*
 #pragma unroll
       for (int b = 0; b < 4; ++b) Dt[(lane + 32 * a) * (KT_RB + 1) + warp * 4 + b] = acc[a][b];
     __syncthreads();
-    if (my_q < N) {
+    if (active) {
       for (int j = 0; j < nt; ++j) {
         const float v = Dt[tid * (KT_RB + 1) + j];
         const int ref = r0 + j;
@@ -125,7 +129,7 @@ __global__ void __launch_bounds__(KT_QB) knn_prefilter_tiled_kernel(const float*
       }
     }
   }
-  if (my_q < N) {
+  if (active) {
 #pragma unroll
     for (int t = 0; t < KP; ++t) {
       cand_d[(size_t)my_q * KP + t] = bd[t];
@@ -148,21 +152,25 @@ __device__ __forceinline__ bool pair_less(double a, int ia, double b, int ib) {
   return a < b || (a == b && ia < ib);
 }
 
+// One block of KT_QB threads per work tile, one thread per query.
 template <int KP>
-__global__ void knn_rerank_kernel(const double* X, int N, int d, int kappa, const float* cand_d,
-                                  const int* cand_i, const unsigned long long* maxabs_bits,
-                                  int* knn, int* flagged, int* nflagged) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+__global__ void knn_rerank_kernel(const double* X, int d, int kappa, const KnnTile* tiles,
+                                  const float* cand_d, const int* cand_i,
+                                  const unsigned long long* maxabs_bits, int* knn, int2* flagged,
+                                  int* nflagged) {
+  const KnnTile tl = tiles[blockIdx.x];
+  if ((int)threadIdx.x >= tl.qn) return;
+  const int i = tl.q0 + threadIdx.x;
+  const int N = tl.rn, rb = tl.rb;
   double dd[KP];
   int ii[KP];
   const double* xi = X + (size_t)i * d;
   const int nc = min(KP, N - 1);
   for (int t = 0; t < nc; ++t) {
     int j = cand_i[(size_t)i * KP + t];
-    if (j < 0 || j >= N) {  // an FP32 distance overflowed: redo this query exactly
+    if (j < rb || j >= rb + N) {  // an FP32 distance overflowed: redo this query exactly
       int slot = atomicAdd(nflagged, 1);
-      flagged[slot] = i;
+      flagged[slot] = make_int2(i, blockIdx.x);
       return;
     }
     ii[t] = j;
@@ -191,7 +199,7 @@ __global__ void knn_rerank_kernel(const double* X, int N, int d, int kappa, cons
   const bool ok = r_lo > 0.0 && r_lo * r_lo * (1.0 - 1e-12) > dd[kappa - 1];
   if (!ok) {
     int slot = atomicAdd(nflagged, 1);
-    flagged[slot] = i;
+    flagged[slot] = make_int2(i, blockIdx.x);
   }
 }
 
@@ -200,13 +208,15 @@ __global__ void knn_rerank_kernel(const double* X, int N, int d, int kappa, cons
 // over the list heads merge them.
 constexpr int FB_THREADS = 128;
 constexpr int FB_MAXK = 64;
-__global__ void knn_fallback_kernel(const double* X, int N, int d, int kappa, const int* flagged,
-                                    int* knn) {
+__global__ void knn_fallback_kernel(const double* X, int d, int kappa, const KnnTile* tiles,
+                                    const int2* flagged, int* knn) {
   __shared__ double sd[FB_THREADS];
   __shared__ int si[FB_THREADS];
   __shared__ int st[FB_THREADS];
   __shared__ int chosen[FB_MAXK];
-  const int i = flagged[blockIdx.x];
+  const int i = flagged[blockIdx.x].x;
+  const KnnTile tl = tiles[flagged[blockIdx.x].y];
+  const int r_begin = tl.rb, r_end = tl.rb + tl.rn;
   const double* xi = X + (size_t)i * d;
   double ld[FB_MAXK];
   int li[FB_MAXK];
@@ -214,7 +224,7 @@ __global__ void knn_fallback_kernel(const double* X, int N, int d, int kappa, co
     ld[t] = DBL_MAX;
     li[t] = INT_MAX;
   }
-  for (int j = threadIdx.x; j < N; j += FB_THREADS) {
+  for (int j = r_begin + threadIdx.x; j < r_end; j += FB_THREADS) {
     if (j == i) continue;
     double v = exact_sqdist(xi, X + (size_t)j * d, d);
     if (!pair_less(v, j, ld[kappa - 1], li[kappa - 1])) continue;
@@ -250,34 +260,47 @@ __global__ void knn_fallback_kernel(const double* X, int N, int d, int kappa, co
 }
 
 template <int D, int KP>
-void launch_prefilter(const float* X32, int N, int d, float* cd, int* ci, cudaStream_t st) {
+void launch_prefilter(const float* X32, int d, const KnnTile* tiles, int ntiles, float* cd, int* ci,
+                      cudaStream_t st) {
   const size_t smem = sizeof(float) * ((size_t)D * KT_QB + (size_t)D * KT_RB + (size_t)KT_QB * (KT_RB + 1));
   if (smem > 48 * 1024)
     IA_CUDA(cudaFuncSetAttribute(knn_prefilter_tiled_kernel<D, KP>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  knn_prefilter_tiled_kernel<D, KP><<<ceil_div(N, KT_QB), KT_QB, smem, st>>>(X32, N, d, cd, ci);
+  knn_prefilter_tiled_kernel<D, KP><<<ntiles, KT_QB, smem, st>>>(X32, d, tiles, cd, ci);
   IA_LAUNCH_CHECK();
 }
 
 template <int KP>
-void prefilter_dispatch(const float* X32, int N, int d, float* cd, int* ci, cudaStream_t st) {
-  if (d <= 8) launch_prefilter<8, KP>(X32, N, d, cd, ci, st);
-  else if (d <= 16) launch_prefilter<16, KP>(X32, N, d, cd, ci, st);
-  else if (d <= 24) launch_prefilter<24, KP>(X32, N, d, cd, ci, st);
-  else if (d <= 32) launch_prefilter<32, KP>(X32, N, d, cd, ci, st);
-  else if (d <= 40) launch_prefilter<40, KP>(X32, N, d, cd, ci, st);
-  else if (d <= 48) launch_prefilter<48, KP>(X32, N, d, cd, ci, st);
-  else if (d <= 56) launch_prefilter<56, KP>(X32, N, d, cd, ci, st);
-  else if (d <= 64) launch_prefilter<64, KP>(X32, N, d, cd, ci, st);
+void prefilter_dispatch(const float* X32, int d, const KnnTile* tl, int nt, float* cd, int* ci,
+                        cudaStream_t st) {
+  if (d <= 8) launch_prefilter<8, KP>(X32, d, tl, nt, cd, ci, st);
+  else if (d <= 16) launch_prefilter<16, KP>(X32, d, tl, nt, cd, ci, st);
+  else if (d <= 24) launch_prefilter<24, KP>(X32, d, tl, nt, cd, ci, st);
+  else if (d <= 32) launch_prefilter<32, KP>(X32, d, tl, nt, cd, ci, st);
+  else if (d <= 40) launch_prefilter<40, KP>(X32, d, tl, nt, cd, ci, st);
+  else if (d <= 48) launch_prefilter<48, KP>(X32, d, tl, nt, cd, ci, st);
+  else if (d <= 56) launch_prefilter<56, KP>(X32, d, tl, nt, cd, ci, st);
+  else if (d <= 64) launch_prefilter<64, KP>(X32, d, tl, nt, cd, ci, st);
   else throw Error(IASKIT_ERR_UNSUPPORTED, "kNN supports d <= 64");
 }
 
 }  // namespace
 
-int knn_bruteforce(const double* X, int N, int d, int kappa, int* knn, KnnScratch& s,
+std::vector<KnnTile> knn_tiles(const std::vector<std::pair<int, int>>& problems) {
+  std::vector<KnnTile> t;
+  for (const auto& pr : problems)
+    for (int q = 0; q < pr.second; q += KT_QB)
+      t.push_back(KnnTile{pr.first + q, std::min(KT_QB, pr.second - q), pr.first, pr.second});
+  return t;
+}
+
+int knn_bruteforce(const double* X, int N, int d, int kappa, int* knn,
+                   const std::vector<std::pair<int, int>>& problems, KnnScratch& s,
                    cudaStream_t st) {
   ProfScope _ps(PK_KNN, st);
-  if (kappa < 1 || kappa > N - 1) throw Error(IASKIT_ERR_ARG, "kappa must be in [1, N-1]");
+  int min_n = N;
+  for (const auto& pr : problems) min_n = std::min(min_n, pr.second);
+  if (kappa < 1 || kappa > min_n - 1) throw Error(IASKIT_ERR_ARG, "kappa must be in [1, N-1]");
   if (kappa > FB_MAXK - 16) throw Error(IASKIT_ERR_UNSUPPORTED, "kappa > 48");
   const size_t nd = (size_t)N * d;
   float* X32 = s.x32.ensure_n<float>(nd);
@@ -287,30 +310,32 @@ int knn_bruteforce(const double* X, int N, int d, int kappa, int* knn, KnnScratc
   IA_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st));
   maxabs_kernel<<<304, 256, 0, st>>>(X, nd, mx);
   IA_LAUNCH_CHECK();
-  int* flagged = s.flagged.ensure_n<int>(N);
+  int2* flagged = s.flagged.ensure_n<int2>(N);
   int* nfl = s.counter.ensure_n<int>(1);
   IA_CUDA(cudaMemsetAsync(nfl, 0, sizeof(int), st));
+  const std::vector<KnnTile> tiles = knn_tiles(problems);
+  KnnTile* dt = s.tiles.ensure_n<KnnTile>(tiles.size());
+  h2d(dt, tiles.data(), tiles.size(), st);
+  const int nt = (int)tiles.size();
   const bool wide = kappa + 8 > 32;
   const int KP = wide ? 64 : 32;
   // algorithmic work of the FP32 prefilter: a subtraction and an FMA per pair and coordinate
-  prof().flops[PK_KNN] += 3.0 * (double)N * (double)N * d;
+  for (const auto& pr : problems) prof().flops[PK_KNN] += 3.0 * (double)pr.second * pr.second * d;
   float* cd = s.cand_d.ensure_n<float>((size_t)N * KP);
   int* ci = s.cand_i.ensure_n<int>((size_t)N * KP);
   if (wide) {
-    prefilter_dispatch<64>(X32, N, d, cd, ci, st);
-    knn_rerank_kernel<64><<<ceil_div(N, 128), 128, 0, st>>>(X, N, d, kappa, cd, ci, mx, knn,
-                                                            flagged, nfl);
+    prefilter_dispatch<64>(X32, d, dt, nt, cd, ci, st);
+    knn_rerank_kernel<64><<<nt, KT_QB, 0, st>>>(X, d, kappa, dt, cd, ci, mx, knn, flagged, nfl);
   } else {
-    prefilter_dispatch<32>(X32, N, d, cd, ci, st);
-    knn_rerank_kernel<32><<<ceil_div(N, 128), 128, 0, st>>>(X, N, d, kappa, cd, ci, mx, knn,
-                                                            flagged, nfl);
+    prefilter_dispatch<32>(X32, d, dt, nt, cd, ci, st);
+    knn_rerank_kernel<32><<<nt, KT_QB, 0, st>>>(X, d, kappa, dt, cd, ci, mx, knn, flagged, nfl);
   }
   IA_LAUNCH_CHECK();
   int nf = 0;
   d2h(&nf, nfl, 1, st);
   IA_CUDA(cudaStreamSynchronize(st));
   if (nf > 0) {
-    knn_fallback_kernel<<<nf, FB_THREADS, 0, st>>>(X, N, d, kappa, flagged, knn);
+    knn_fallback_kernel<<<nf, FB_THREADS, 0, st>>>(X, d, kappa, dt, flagged, knn);
     IA_LAUNCH_CHECK();
   }
   return nf;
@@ -335,9 +360,10 @@ constexpr size_t NA_X32 = 0;
 constexpr size_t NA_CD = NA_X32 + sizeof(float) * NA_MAX_ND;
 constexpr size_t NA_CI = NA_CD + sizeof(float) * NA_MAX_N * NA_KP;
 constexpr size_t NA_FLAGGED = NA_CI + sizeof(int) * NA_MAX_N * NA_KP;
-constexpr size_t NA_COUNTER = NA_FLAGGED + sizeof(int) * NA_MAX_N;
+constexpr size_t NA_TILES = NA_FLAGGED + sizeof(int2) * NA_MAX_N;
+constexpr size_t NA_COUNTER = NA_TILES + sizeof(KnnTile) * (NA_MAX_N / KT_QB);
 constexpr size_t NA_MAXABS = NA_COUNTER + 256;
-constexpr size_t NA_BYTES = NA_MAXABS + 256;   // about 12.1 MiB
+constexpr size_t NA_BYTES = NA_MAXABS + 256;   // about 12.3 MiB
 
 __device__ __align__(256) unsigned char g_knn_noalloc_scratch[NA_BYTES];
 
@@ -364,10 +390,13 @@ void knn_noalloc(const double* X, int N, int d, int kappa, int* knn, cudaStream_
   float* X32 = reinterpret_cast<float*>(base + NA_X32);
   float* cd = reinterpret_cast<float*>(base + NA_CD);
   int* ci = reinterpret_cast<int*>(base + NA_CI);
-  int* flagged = reinterpret_cast<int*>(base + NA_FLAGGED);
+  int2* flagged = reinterpret_cast<int2*>(base + NA_FLAGGED);
+  KnnTile* dt = reinterpret_cast<KnnTile*>(base + NA_TILES);
   int* nfl = reinterpret_cast<int*>(base + NA_COUNTER);
   unsigned long long* mx = reinterpret_cast<unsigned long long*>(base + NA_MAXABS);
   const size_t nd = (size_t)N * d;
+  const std::vector<KnnTile> tiles = knn_tiles({{0, N}});
+  const int nt = (int)tiles.size();
   // the array keeps the previous call's contents: clear what must start at zero
   IA_CUDA(cudaMemsetAsync(mx, 0, sizeof(unsigned long long), st));
   IA_CUDA(cudaMemsetAsync(nfl, 0, sizeof(int), st));
@@ -375,15 +404,15 @@ void knn_noalloc(const double* X, int N, int d, int kappa, int* knn, cudaStream_
   IA_LAUNCH_CHECK();
   maxabs_kernel<<<304, 256, 0, st>>>(X, nd, mx);
   IA_LAUNCH_CHECK();
-  prefilter_dispatch<NA_KP>(X32, N, d, cd, ci, st);
-  knn_rerank_kernel<NA_KP><<<ceil_div(N, 128), 128, 0, st>>>(X, N, d, kappa, cd, ci, mx, knn,
-                                                              flagged, nfl);
+  IA_CUDA(cudaMemcpyAsync(dt, tiles.data(), nt * sizeof(KnnTile), cudaMemcpyHostToDevice, st));
+  prefilter_dispatch<NA_KP>(X32, d, dt, nt, cd, ci, st);
+  knn_rerank_kernel<NA_KP><<<nt, KT_QB, 0, st>>>(X, d, kappa, dt, cd, ci, mx, knn, flagged, nfl);
   IA_LAUNCH_CHECK();
   int nf = 0;
   IA_CUDA(cudaMemcpyAsync(&nf, nfl, sizeof(int), cudaMemcpyDeviceToHost, st));
   IA_CUDA(cudaStreamSynchronize(st));
   if (nf > 0) {
-    knn_fallback_kernel<<<nf, FB_THREADS, 0, st>>>(X, N, d, kappa, flagged, knn);
+    knn_fallback_kernel<<<nf, FB_THREADS, 0, st>>>(X, d, kappa, dt, flagged, knn);
     IA_LAUNCH_CHECK();
   }
   IA_CUDA(cudaStreamSynchronize(st));

@@ -12,7 +12,11 @@
 //      maps to position j (j < o) or j + n; positions already taken are skipped;
 //      when n_samp = N - n the sample is the whole complement;
 //   4. the sample is returned in ascending position order.
-// Device plan per level: one radix sort of (node, candidate) keys over all N*kappa
+// Several independent problems are sampled together: a step's node list covers
+// all points; nodes of problems that have no node at this step only pass through.
+// Positions, complements and streams are per problem, so every node gets exactly
+// the sample it would get alone.
+// Device plan per step: one radix sort of (node, candidate) keys over all N*kappa
 // entries gives the hit counts as run lengths; a second stable radix sort by
 // (node, hits descending) puts each node's best candidates first (the first sort
 // left equal hits in ascending position); one block per node then fills and sorts.
@@ -52,14 +56,15 @@ __global__ void knn_pos_kernel(const int* knn, const int* perm, const int* iperm
   knn_pos[t] = iperm[knn[(size_t)perm[p] * kappa + k]];
 }
 
-__global__ void cand_keys_kernel(const int* knn_pos, int N, int kappa, const int* off, int nnodes,
-                                 int pos_bits, uint64_t sentinel, uint64_t* keys) {
+__global__ void cand_keys_kernel(const int* knn_pos, int N, int kappa, const int* off,
+                                 const SampleNodeInfo* info, int nnodes, int pos_bits,
+                                 uint64_t sentinel, uint64_t* keys) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)N * kappa) return;
   int p = (int)(t / kappa);
   int node = node_of(off, nnodes, p);
   int c = knn_pos[t];
-  bool outside = c < off[node] || c >= off[node + 1];
+  bool outside = info[node].active && (c < off[node] || c >= off[node + 1]);
   keys[t] = outside ? (((uint64_t)node << pos_bits) | (uint64_t)c) : sentinel;
 }
 
@@ -103,21 +108,24 @@ __global__ void rank_keys_kernel(const int* run_start, const int* run_end, const
 // of 4 * cap_pow2 ints.
 constexpr int SEL_THREADS = 256;
 __global__ void select_fill_kernel(const uint32_t* cand_sorted, const int* node_start,
-                                   const int* node_cnt, const int* off, int N, int level,
-                                   int samp_cap, const int* samp_off, uint64_t seed,
+                                   const int* node_cnt, const int* off,
+                                   const SampleNodeInfo* info, int samp_cap, uint64_t seed,
                                    int cap_pow2, int* samp, int* status) {
   extern __shared__ int sh[];
   int* arr = sh;
   int* hset = sh + cap_pow2;
   const int hsize = 4 * cap_pow2;
   const int node = blockIdx.x;
-  const int o = off[node], n = off[node + 1] - o;
-  const int comp = N - n;
+  const SampleNodeInfo inf = info[node];
+  if (!inf.active) return;
+  const int pb = inf.pb;                              // first point of the node's problem
+  const int o = off[node] - pb, n = off[node + 1] - off[node];   // o: offset inside the problem
+  const int comp = inf.pn - n;
   const int ns = min(samp_cap, comp);
-  int* out = samp + samp_off[node];
+  int* out = samp + inf.samp_off;
   if (ns <= 0) return;
   if (ns == comp) {  // the whole complement, already ascending
-    for (int t = threadIdx.x; t < comp; t += SEL_THREADS) out[t] = t < o ? t : t + n;
+    for (int t = threadIdx.x; t < comp; t += SEL_THREADS) out[t] = pb + (t < o ? t : t + n);
     return;
   }
   const int nc = min(ns, node_cnt[node]);
@@ -140,7 +148,7 @@ __global__ void select_fill_kernel(const uint32_t* cand_sorted, const int* node_
     };
     for (int t = 0; t < nc; ++t) insert(arr[t]);
     int have = nc;
-    const uint64_t uid = (1ull << level) + (uint64_t)node;
+    const uint64_t uid = (uint64_t)inf.uid;
     const uint64_t s0 = splitmix64(splitmix64(seed) ^ uid);
     const uint64_t limit = 64ull * (uint64_t)comp + 4096ull;
     uint64_t q = 0;
@@ -151,7 +159,7 @@ __global__ void select_fill_kernel(const uint32_t* cand_sorted, const int* node_
       }
       uint64_t r = splitmix64(s0 + q * 0x9E3779B97F4A7C15ull);
       int j = (int)(r % (uint64_t)comp);
-      int pos = j < o ? j : j + n;
+      int pos = pb + (j < o ? j : j + n);
       if (insert(pos)) arr[have++] = pos;
       ++q;
     }
@@ -187,19 +195,22 @@ void knn_to_positions(const int* knn, const int* perm, const int* iperm, int N, 
   IA_LAUNCH_CHECK();
 }
 
-void sample_level(const int* knn_pos, int N, int kappa, int level, const int* off_dev,
-                  const std::vector<int>& off_host, int samp_cap, const int* samp_off_dev,
-                  uint64_t seed, int* samp, int* dev_status, SampleScratch& s, cudaStream_t st) {
+void sample_level(const int* knn_pos, int N, int kappa, const int* off_dev,
+                  const SampleNodeInfo* info_dev, const std::vector<int>& off_host,
+                  const std::vector<SampleNodeInfo>& info_host, int samp_cap, uint64_t seed,
+                  int* samp, int* dev_status, SampleScratch& s, cudaStream_t st) {
   ProfScope _ps(PK_SAMPLE, st);
-  const int nn = 1 << level;
+  const int nn = (int)info_host.size();
   const size_t n = (size_t)N * kappa;
+  int node_bits = 0;
+  while ((1 << node_bits) < nn) ++node_bits;
   const int pos_bits = bit_length((uint64_t)N);   // 2^pos_bits > N: the sentinel is no position
-  const int key_bits = level + pos_bits;
+  const int key_bits = node_bits + pos_bits;
   if (key_bits > 62) throw Error(IASKIT_ERR_UNSUPPORTED, "sampling key exceeds 62 bits");
   const uint64_t sentinel = (1ull << key_bits) - 1;
   uint64_t* keys = s.keys.ensure_n<uint64_t>(n);
-  cand_keys_kernel<<<ceil_div(n, 256), 256, 0, st>>>(knn_pos, N, kappa, off_dev, nn, pos_bits,
-                                                     sentinel, keys);
+  cand_keys_kernel<<<ceil_div(n, 256), 256, 0, st>>>(knn_pos, N, kappa, off_dev, info_dev, nn,
+                                                     pos_bits, sentinel, keys);
   IA_LAUNCH_CHECK();
   radix_sort_u64(keys, nullptr, n, key_bits, s.alt_keys, s.alt_vals, s.hist, s.scan_tmp, st);
   int* heads = s.flags.ensure_n<int>(n);
@@ -220,22 +231,23 @@ void sample_level(const int* knn_pos, int N, int kappa, int level, const int* of
   IA_CUDA(cudaMemsetAsync(node_cnt, 0, (nn + 1) * sizeof(int), st));
   uint64_t* keys2 = s.keys2.ensure_n<uint64_t>(nruns + 1);
   uint32_t* vals2 = s.vals2.ensure_n<uint32_t>(nruns + 1);
+  const int cnt_bits = pos_bits;  // a candidate is hit at most once per point of the node
   if (nruns > 0) {
     runs_kernel<<<ceil_div(n, 256), 256, 0, st>>>(keys, n, sentinel, heads, idx, run_start,
                                                   run_end, run_key);
     IA_LAUNCH_CHECK();
-    const int cnt_bits = pos_bits;  // a candidate is hit at most once per point of the node
     rank_keys_kernel<<<ceil_div(nruns, 256), 256, 0, st>>>(run_start, run_end, run_key, nruns,
                                                            pos_bits, cnt_bits, keys2, vals2,
                                                            node_cnt);
     IA_LAUNCH_CHECK();
-    radix_sort_u64(keys2, vals2, nruns, level + cnt_bits, s.alt_keys, s.alt_vals, s.hist,
+    radix_sort_u64(keys2, vals2, nruns, node_bits + cnt_bits, s.alt_keys, s.alt_vals, s.hist,
                    s.scan_tmp, st);
   }
   exclusive_scan_i32(node_cnt, node_start, nn, s.scan_tmp, st);
   int maxns = 0;
   for (int i = 0; i < nn; ++i)
-    maxns = std::max(maxns, std::min(samp_cap, N - (off_host[i + 1] - off_host[i])));
+    if (info_host[i].active)
+      maxns = std::max(maxns, std::min(samp_cap, info_host[i].pn - (off_host[i + 1] - off_host[i])));
   int cap_pow2 = 1;
   while (cap_pow2 < maxns) cap_pow2 <<= 1;
   const size_t smem = (size_t)5 * cap_pow2 * sizeof(int);
@@ -243,9 +255,8 @@ void sample_level(const int* knn_pos, int N, int kappa, int level, const int* of
   if (smem > 48 * 1024)
     IA_CUDA(cudaFuncSetAttribute(select_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
-  select_fill_kernel<<<nn, SEL_THREADS, smem, st>>>(vals2, node_start, node_cnt, off_dev, N, level,
-                                                    samp_cap, samp_off_dev, seed, cap_pow2, samp,
-                                                    dev_status);
+  select_fill_kernel<<<nn, SEL_THREADS, smem, st>>>(vals2, node_start, node_cnt, off_dev, info_dev,
+                                                    samp_cap, seed, cap_pow2, samp, dev_status);
   IA_LAUNCH_CHECK();
 }
 

@@ -2,11 +2,16 @@
 //
 // Factorization (Sec. II-C, Alg. "Factorize", run bottom-up with loops over levels
 // as the paper's implementation does):
-//   tree -> kNN -> skeletonize levels L..1 (sample, kernel block, CPQR/ID, nested P)
-//   -> leaf LU of lambda I + K_aa -> for l = L-1 .. 0: U blocks K_{l r~}, K_{r l~} of
-//   every node of level l, W = Solve(child subtree, U) for all of them at once (a
-//   "forest solve" rooted at level l+1), reduced systems Z and their LU.
-// Solve (Alg. "Solve"): a forest solve rooted at level 0.
+//   tree -> kNN -> skeletonize bottom-up (sample, kernel block, CPQR/ID, nested P)
+//   -> leaf LU of lambda I + K_aa -> for every node above the leaves, bottom-up:
+//   U blocks K_{l r~}, K_{r l~}, W = Solve(child subtree, U) for all children at once
+//   (a "forest solve"), reduced systems Z and their LU.
+// Solve (Alg. "Solve"): a forest solve rooted at the roots.
+//
+// Many independent problems (each with its own points, h and lambda) are factored
+// together: their points are concatenated, every node has a global id, and every
+// step is one launch over the nodes of all problems at the same height above the
+// leaves.  A single problem is the batch of one.
 //
 // The forest solve applies Solve to the blocks of a set of subtrees at once.  At a
 // node beta with children a, b it needs V v = [P_{b~ b} v_b; P_{a~ a} v_a] (eq.
@@ -24,7 +29,7 @@
 // Two precisions:
 //  * plain: everything in FP64;
 //  * mixed: the factorization (sampled blocks, CPQR updates, leaf LU, W, C, Z) in
-//    FP32 with FP64 pivot norms in the CPQR; the operator lambda I + K~ is kept in
+//    FP32 with pivot norms compared in FP64; the operator lambda I + K~ is kept in
 //    FP64 (leaf blocks and U blocks evaluated once in FP64 and stored, P in FP64),
 //    and the solve refines w += Solve32(u - (lambda I + K~) w) until the relative
 //    residual of every column is below the target.  K~ is the one defined by the
@@ -71,13 +76,23 @@ struct Options {
   double refine_tol = 1e-10;
   double mem_cap_gb = 0.0;
   int precision = PREC_FP64;
+  int problem = 0;  // problem the introspection calls refer to
+};
+
+struct Prob {
+  int N = 0, L = 0, m_max = 0;
+  double h = 0, lam = 0, scale = 0;  // scale = -1 / (2 h^2)
+  int pbase = 0;                     // first global position (and original index)
+  int nbase = 0;                     // global id of heap id 0: gid = nbase + uid
 };
 
 struct Node {
-  int off = 0, size = 0;
-  int s = 0;          // rank (skeleton count); 0 for the root
-  int ncols = 0;      // ID columns: size (leaf) or s_l + s_r
+  int prob = 0, uid = 0, level = 0;
+  int off = 0, size = 0;  // global position range
+  int s = 0;              // rank (skeleton count); 0 for a root
+  int ncols = 0;          // ID columns: size (leaf) or s_l + s_r
   int nsamp = 0;
+  int leaf = -1;          // global leaf index (leaves only)
   int64_t samp_off = 0, P_off = 0, W_off = 0, LU_off = 0, Z_off = 0, Zpiv_off = 0, CL_off = 0,
           CR_off = 0;
 };
@@ -93,7 +108,7 @@ struct Stats {
 
 template <typename T>
 struct RootBlock {
-  int uid;
+  int gid;
   T* V;
   int ld;
   int nc;
@@ -141,6 +156,65 @@ GemmShape make_tiles(const std::vector<GemmDescT<T>>& g, std::vector<GemmTile>& 
   return shape;
 }
 
+// Per problem block of an N_p x nrhs right-hand side inside the concatenated layout.
+struct BlockDesc {
+  int64_t base;  // element offset of the block (pbase * nrhs)
+  int n;         // N_p
+  double a;      // per-problem scalar
+};
+
+__global__ void gather_rows_kernel(const double* in, double* out, const int* perm, const int* pid,
+                                   const BlockDesc* blocks, int Ntot, int nrhs, bool scatter) {
+  const int64_t total = (int64_t)Ntot * nrhs;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e % Ntot), c = (int)(e / Ntot);
+    const BlockDesc b = blocks[pid[p]];
+    const int pb = (int)(b.base / nrhs);
+    const int64_t dst = b.base + (int64_t)(p - pb) + (int64_t)c * b.n;
+    const int64_t src = b.base + (int64_t)(perm[p] - pb) + (int64_t)c * b.n;
+    if (scatter) out[src] = in[dst];
+    else out[dst] = in[src];
+  }
+}
+__global__ void scale_blocks_kernel(const double* x, double* y, const BlockDesc* blocks, int nrhs) {
+  const BlockDesc b = blocks[blockIdx.y];
+  const int64_t n = (int64_t)b.n * nrhs;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[b.base + i] = b.a * x[b.base + i];
+}
+__global__ void axpby_kernel(const double* u, double* r, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    r[i] = u[i] - r[i];
+}
+__global__ void add_kernel(double* w, const double* dl, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    w[i] += dl[i];
+}
+// One block per (column, problem): the 2-norm of that column of that problem's block.
+__global__ void colnorm_kernel(const double* x, const BlockDesc* blocks, int nrhs, double* out) {
+  __shared__ double red[32];
+  const int c = blockIdx.x, q = blockIdx.y;
+  const BlockDesc b = blocks[q];
+  const double* col = x + b.base + (int64_t)c * b.n;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < b.n; i += blockDim.x) s = fma(col[i], col[i], s);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    s = warp_sum(s);
+    if (threadIdx.x == 0) out[(size_t)q * nrhs + c] = sqrt(s);
+  }
+}
+
+unsigned grid_cap(int64_t work, unsigned cap) {
+  int64_t b = (work + 255) / 256;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, cap));
+}
+
 class Solver {
  public:
   cudaStream_t st = nullptr;
@@ -148,28 +222,35 @@ class Solver {
   Stats stats;
   bool factored = false;
   int prec = PREC_FP64;  // precision of the current factorization
-  int N = 0, d = 0, L = 0, m_max = 0, s_max = 0, kappa = 0;
-  double h = 0, lam = 0, tol = 0;
-  std::vector<std::vector<int>> level_off;
-  std::vector<Node> nd;  // heap ids 1 .. 2^(L+1) - 1
-  DevBuf X, Xp, perm, iperm, split_dim, knn, knn_pos, samp, ranks, skel, piv_ws, A_ws, status,
-      arena_dev, level_off_dev, tbuf, vbuf, vbuf32, ubuf, rbuf, wt, io, normbuf;
+  int Ntot = 0, d = 0, s_max = 0, kappa = 0, m_max = 0, Hmax = 0, nleaves = 0;
+  double tol = 0;
+  std::vector<Prob> pr;
+  std::vector<Node> nd;                       // global ids; unused slot at each nbase
+  std::vector<std::vector<int>> by_height;    // gids of each height (0 = leaves), roots included
+  DevBuf X, Xp, perm, iperm, pid, knn, knn_pos, samp, ranks, skel, piv_ws, A_ws, status,
+      arena_dev, step_dev, tbuf, vbuf, vbuf32, ubuf, rbuf, wt, io, normbuf, blocks_dev;
   // factorization storage: FP64 (plain) and FP32 (mixed)
   DevBuf LU, LUpiv, Wb, Zb, Zpiv, Cb, LU32, Wb32, Zb32, Cb32, tbuf32;
   // FP64 operator blocks kept by the mixed form: leaf blocks lambda I + K_aa and U blocks
   DevBuf Kleaf, Ustore;
-  std::vector<std::unique_ptr<DevBuf>> Pl, Pl32;  // nested P per level (FP64; FP32 copy)
+  DevBuf Pd, Pf;  // nested P of every node: FP64, and its FP32 copy (mixed)
   TreeScratch tree_s;
   KnnScratch knn_s;
   SampleScratch samp_s;
   Arena arena;
 
-  int uid(int l, int i) const { return (1 << l) + i; }
-  int level_of(int u) const {
-    int l = 0;
-    while ((2 << l) <= u) ++l;
-    return l;
-  }
+  // ------------------------------------------------------------ tree helpers
+  int left(int g) const { return pr[nd[g].prob].nbase + 2 * nd[g].uid; }
+  int right(int g) const { return left(g) + 1; }
+  int parent(int g) const { return pr[nd[g].prob].nbase + (nd[g].uid >> 1); }
+  int sibling(int g) const { return pr[nd[g].prob].nbase + (nd[g].uid ^ 1); }
+  bool is_root(int g) const { return nd[g].uid == 1; }
+  bool is_leaf(int g) const { return nd[g].level == pr[nd[g].prob].L; }
+  int height(int g) const { return pr[nd[g].prob].L - nd[g].level; }
+  int n2(int g) const { return nd[left(g)].s + nd[right(g)].s; }  // reduced-system size
+  // row offset of child c's skeletons inside the parent's [t_a; t_b]
+  int rowoff(int c) const { return (nd[c].uid & 1) ? nd[sibling(c)].s : 0; }
+  double scale_of(int g) const { return pr[nd[g].prob].scale; }
 
   // typed views of the factorization storage
   template <typename T>
@@ -181,7 +262,7 @@ class Solver {
   template <typename T>
   T* cP() { return std::is_same<T, float>::value ? (T*)Cb32.p : (T*)Cb.p; }
   template <typename T>
-  T* pP(int l) { return std::is_same<T, float>::value ? (T*)Pl32[l]->p : (T*)Pl[l]->p; }
+  T* pP() { return std::is_same<T, float>::value ? (T*)Pf.p : (T*)Pd.p; }
   template <typename T>
   DevBuf& tB() { return std::is_same<T, float>::value ? tbuf32 : tbuf; }
 
@@ -220,134 +301,134 @@ class Solver {
     gemm_grouped((const GemmDescT<T>*)(base + og), (const GemmTile*)(base + ot), (int)t.size(),
                  shape, st);
   }
+  // per-problem blocks of an nrhs-column right-hand side (uploaded to blocks_dev)
+  const BlockDesc* upload_blocks(int nrhs, bool lam_scalar) {
+    std::vector<BlockDesc> b(pr.size());
+    for (size_t q = 0; q < pr.size(); ++q)
+      b[q] = BlockDesc{(int64_t)pr[q].pbase * nrhs, pr[q].N, lam_scalar ? pr[q].lam : 0.0};
+    BlockDesc* dv = blocks_dev.ensure_n<BlockDesc>(b.size());
+    h2d(dv, b.data(), b.size(), st);
+    return dv;
+  }
+  void gather(const double* in, double* out, int nrhs, const BlockDesc* blocks, bool scatter) {
+    ProfScope _ps(PK_MISC, st);
+    gather_rows_kernel<<<grid_cap((int64_t)Ntot * nrhs, 8192), 256, 0, st>>>(
+        in, out, perm.as<int>(), pid.as<int>(), blocks, Ntot, nrhs, scatter);
+    IA_LAUNCH_CHECK();
+  }
 
   // ------------------------------------------------------------- forest solve
-  // Applies (lambda I + K~_cc)^{-1} to the block of every root c at level r, in
-  // place, with the factorization stored in precision T.  Writes P_c v_c to
-  // roots[].t_out when given.
+  // Applies (lambda I + K~_cc)^{-1} to the block of every root c, in place, with the
+  // factorization stored in precision T.  Writes P_c v_c to roots[].t_out when given.
   template <typename T>
-  void forest_solve(int r, const std::vector<RootBlock<T>>& roots) {
+  void forest_solve(const std::vector<RootBlock<T>>& roots) {
     const bool need_t = !roots.empty() && roots[0].t_out != nullptr;
     std::vector<int> root_of(nd.size(), -1);
     std::vector<T*> Vp(nd.size(), nullptr);
-    int max_nc = 0;
+    int max_nc = 0, top = 0;
     for (size_t q = 0; q < roots.size(); ++q) {
       max_nc = std::max(max_nc, roots[q].nc);
-      const int c = roots[q].uid;
-      const int lc = level_of(c);
-      for (int l = lc; l <= L; ++l) {
-        int first = c << (l - lc), cnt = 1 << (l - lc);
-        for (int u = first; u < first + cnt; ++u) {
-          root_of[u] = (int)q;
-          Vp[u] = roots[q].V + (nd[u].off - nd[c].off);
+      const int c = roots[q].gid;
+      top = std::max(top, height(c));
+      std::vector<int> stack{c};
+      while (!stack.empty()) {
+        int u = stack.back();
+        stack.pop_back();
+        root_of[u] = (int)q;
+        Vp[u] = roots[q].V + (nd[u].off - nd[c].off);
+        if (!is_leaf(u)) {
+          stack.push_back(left(u));
+          stack.push_back(right(u));
         }
       }
     }
     // T and Y scratch for internal forest nodes
     std::vector<int64_t> Toff(nd.size(), -1);
     int64_t tsz = 0;
-    for (int l = r; l < L; ++l)
-      for (int i = 0; i < (1 << l); ++i) {
-        int u = uid(l, i);
+    for (int hh = 1; hh <= top; ++hh)
+      for (int u : by_height[hh]) {
         if (root_of[u] < 0) continue;
-        int n2 = nd[2 * u].s + nd[2 * u + 1].s;
         Toff[u] = tsz;
-        tsz += 2 * (int64_t)n2 * roots[root_of[u]].nc;
+        tsz += 2 * (int64_t)n2(u) * roots[root_of[u]].nc;
       }
     T* Tb = tB<T>().template ensure_n<T>(std::max<int64_t>(tsz, 1));
     auto Tp = [&](int u) { return Tb + Toff[u]; };
-    auto Yp = [&](int u) {
-      int n2 = nd[2 * u].s + nd[2 * u + 1].s;
-      return Tb + Toff[u] + (int64_t)n2 * roots[root_of[u]].nc;
-    };
+    auto Yp = [&](int u) { return Tb + Toff[u] + (int64_t)n2(u) * roots[root_of[u]].nc; };
     auto ldV = [&](int u) { return roots[root_of[u]].ld; };
     auto ncV = [&](int u) { return roots[root_of[u]].nc; };
+    // where node u's carried t goes: its parent's T, or the root's output
+    auto tdst = [&](int u, T*& dst, int& ldd) {
+      if (roots[root_of[u]].gid == u) {
+        dst = roots[root_of[u]].t_out;
+        ldd = roots[root_of[u]].t_ld;
+      } else {
+        const int par = parent(u);
+        dst = Tp(par) + rowoff(u);
+        ldd = n2(par);
+      }
+    };
 
-    // 1. leaf LU solves
+    // 1. leaf LU solves; leaf t = P v
     {
       std::vector<LuSolveDescT<T>> ds;
-      for (int i = 0; i < (1 << L); ++i) {
-        int u = uid(L, i);
+      std::vector<GemmDescT<T>> g;
+      for (int u : by_height[0]) {
         if (root_of[u] < 0) continue;
-        ds.push_back(LuSolveDescT<T>{luP<T>() + nd[u].LU_off, LUpiv.as<int>() + (int64_t)i * m_max,
-                                     Vp[u], nd[u].size, nd[u].size, ldV(u), ncV(u)});
+        ds.push_back(LuSolveDescT<T>{luP<T>() + nd[u].LU_off,
+                                     LUpiv.as<int>() + (int64_t)nd[u].leaf * m_max, Vp[u],
+                                     nd[u].size, nd[u].size, ldV(u), ncV(u)});
+        const bool top_root = roots[root_of[u]].gid == u;
+        if (!top_root || need_t) {
+          T* dst;
+          int ldd;
+          tdst(u, dst, ldd);
+          add_gemm<T>(g, pP<T>() + nd[u].P_off, nd[u].s, Vp[u], ldV(u), dst, ldd, nd[u].s, ncV(u),
+                      nd[u].size, 1.0, 0.0);
+        }
       }
       arena.clear();
       size_t o = arena.push(ds);
       char* base = upload_arena();
       prof().flops[pk_of<T>(PK_GETRS)] += getrs_flops(ds);
       getrs_batched((const LuSolveDescT<T>*)(base + o), (int)ds.size(), m_max, max_nc, st);
-    }
-    if (r == L) {
-      if (need_t) {
-        std::vector<GemmDescT<T>> g;
-        for (const auto& rb : roots) {
-          const Node& c = nd[rb.uid];
-          add_gemm<T>(g, pP<T>(L) + c.P_off, c.s, rb.V, rb.ld, rb.t_out, rb.t_ld, c.s, rb.nc,
-                      c.size, 1.0, 0.0);
-        }
-        run_gemms(g);
-      }
-      return;
-    }
-    // 2. leaf t = P v into the parent's T
-    {
-      std::vector<GemmDescT<T>> g;
-      for (int i = 0; i < (1 << L); ++i) {
-        int u = uid(L, i);
-        if (root_of[u] < 0) continue;
-        int par = u >> 1;
-        int n2 = nd[2 * par].s + nd[2 * par + 1].s;
-        int rowoff = (u & 1) ? nd[2 * par].s : 0;
-        add_gemm<T>(g, pP<T>(L) + nd[u].P_off, nd[u].s, Vp[u], ldV(u), Tp(par) + rowoff, n2,
-                    nd[u].s, ncV(u), nd[u].size, 1.0, 0.0);
-      }
       run_gemms(g);
     }
-    // 3. levels L-1 .. r
-    for (int j = L - 1; j >= r; --j) {
+    // 2. heights 1 .. top
+    for (int hh = 1; hh <= top; ++hh) {
       std::vector<CopyDescT<T>> cp;
       std::vector<LuSolveDescT<T>> zs;
       std::vector<GemmDescT<T>> g1, g2;
-      std::vector<GemmTile> t1, t2;
       int64_t max_cp = 0;
       int max_n2 = 0;
-      for (int i = 0; i < (1 << j); ++i) {
-        int b = uid(j, i);
+      for (int b : by_height[hh]) {
         if (root_of[b] < 0) continue;
-        int a = 2 * b, c = 2 * b + 1;  // children: a left, c right
-        int sa = nd[a].s, sc = nd[c].s, n2 = sa + sc, nc = ncV(b);
-        max_n2 = std::max(max_n2, n2);
-        max_cp = std::max<int64_t>(max_cp, (int64_t)n2 * nc);
-        cp.push_back(CopyDescT<T>{Tp(b), Yp(b), n2, nc, n2, n2});
+        const int a = left(b), c = right(b);  // children: a left, c right
+        const int sa = nd[a].s, sc = nd[c].s, nb2 = sa + sc, nc = ncV(b);
+        max_n2 = std::max(max_n2, nb2);
+        max_cp = std::max<int64_t>(max_cp, (int64_t)nb2 * nc);
+        cp.push_back(CopyDescT<T>{Tp(b), Yp(b), nb2, nc, nb2, nb2});
         zs.push_back(LuSolveDescT<T>{zP<T>() + nd[b].Z_off, Zpiv.as<int>() + nd[b].Zpiv_off, Yp(b),
-                                     n2, n2, n2, nc});
+                                     nb2, nb2, nb2, nc});
         const T* W = wP<T>();
-        // v_a -= W_{a c~} y1 (y1 = Y[sa : n2]);  v_c -= W_{c a~} y2 (y2 = Y[0 : sa])
-        add_gemm<T>(g1, W + nd[a].W_off, nd[a].size, Yp(b) + sa, n2, Vp[a], ldV(b), nd[a].size,
-                    nc, sc, -1.0, 1.0);
-        add_gemm<T>(g1, W + nd[c].W_off, nd[c].size, Yp(b), n2, Vp[c], ldV(b), nd[c].size, nc,
-                    sa, -1.0, 1.0);
-        const bool carry = (j > r) || need_t;
-        if (carry) {
+        // v_a -= W_{a c~} y1 (y1 = Y[sa : nb2]);  v_c -= W_{c a~} y2 (y2 = Y[0 : sa])
+        add_gemm<T>(g1, W + nd[a].W_off, nd[a].size, Yp(b) + sa, nb2, Vp[a], ldV(b), nd[a].size, nc,
+                    sc, -1.0, 1.0);
+        add_gemm<T>(g1, W + nd[c].W_off, nd[c].size, Yp(b), nb2, Vp[c], ldV(b), nd[c].size, nc, sa,
+                    -1.0, 1.0);
+        const bool top_root = roots[root_of[b]].gid == b;
+        if (!top_root || need_t) {
           const T* C = cP<T>();
-          add_gemm<T>(g1, C + nd[b].CL_off, sa, Yp(b) + sa, n2, Tp(b), n2, sa, nc, sc, -1.0, 1.0);
-          add_gemm<T>(g1, C + nd[b].CR_off, sc, Yp(b), n2, Tp(b) + sa, n2, sc, nc, sa, -1.0, 1.0);
+          add_gemm<T>(g1, C + nd[b].CL_off, sa, Yp(b) + sa, nb2, Tp(b), nb2, sa, nc, sc, -1.0, 1.0);
+          add_gemm<T>(g1, C + nd[b].CR_off, sc, Yp(b), nb2, Tp(b) + sa, nb2, sc, nc, sa, -1.0, 1.0);
           T* dst;
           int ldd;
-          if (j > r) {
-            int par = b >> 1;
-            int pn2 = nd[2 * par].s + nd[2 * par + 1].s;
-            dst = Tp(par) + ((b & 1) ? nd[2 * par].s : 0);
-            ldd = pn2;
-          } else {
-            dst = roots[root_of[b]].t_out;
-            ldd = roots[root_of[b]].t_ld;
-          }
-          add_gemm<T>(g2, pP<T>(j) + nd[b].P_off, nd[b].s, Tp(b), n2, dst, ldd, nd[b].s, nc, n2,
-                      1.0, 0.0);
+          tdst(b, dst, ldd);
+          add_gemm<T>(g2, pP<T>() + nd[b].P_off, nd[b].s, Tp(b), nb2, dst, ldd, nd[b].s, nc, nb2, 1.0,
+                      0.0);
         }
       }
+      if (cp.empty()) continue;
+      std::vector<GemmTile> t1, t2;
       const GemmShape sh1 = make_tiles(g1, t1), sh2 = make_tiles(g2, t2);
       arena.clear();
       size_t ocp = arena.push(cp), ozs = arena.push(zs), og1 = arena.push(g1), ot1 = arena.push(t1),
@@ -365,80 +446,154 @@ class Solver {
   }
 
   // ------------------------------------------------------------- factorization
-  void factor(const double* points, bool on_device, int64_t N_, int d_, double h_, double lam_,
-              int leaf_m, int s_max_, double tol_) {
+  struct ProbIn {
+    const double* X;
+    int64_t N;
+    double h, lam;
+  };
+
+  void factor(const std::vector<ProbIn>& in, bool on_device, bool concatenated, int d_, int leaf_m,
+              int s_max_, double tol_) {
     factored = false;
-    if (N_ < 2 || N_ > (int64_t)1 << 30) throw Error(IASKIT_ERR_ARG, "N must be in [2, 2^30]");
+    if (in.empty()) throw Error(IASKIT_ERR_ARG, "no problem");
     if (d_ < 1) throw Error(IASKIT_ERR_ARG, "d must be >= 1");
-    if (!(h_ > 0.0) || !std::isfinite(h_)) throw Error(IASKIT_ERR_ARG, "h must be > 0");
-    if (!(lam_ >= 0.0) || !std::isfinite(lam_)) throw Error(IASKIT_ERR_ARG, "lambda must be >= 0");
     if (leaf_m < 2) throw Error(IASKIT_ERR_ARG, "leaf_m must be >= 2");
     if (s_max_ < 1) throw Error(IASKIT_ERR_ARG, "s_max must be >= 1");
-    if (!points) throw Error(IASKIT_ERR_ARG, "points is null");
+    int64_t total = 0;
+    for (size_t q = 0; q < in.size(); ++q) {
+      const ProbIn& p = in[q];
+      if (p.N < 2) throw Error(IASKIT_ERR_ARG, "N must be >= 2");
+      if (!(p.h > 0.0) || !std::isfinite(p.h)) throw Error(IASKIT_ERR_ARG, "h must be > 0");
+      if (!(p.lam >= 0.0) || !std::isfinite(p.lam)) throw Error(IASKIT_ERR_ARG, "lambda must be >= 0");
+      if (!p.X && (!concatenated || q == 0)) throw Error(IASKIT_ERR_ARG, "points is null");
+      total += p.N;
+    }
+    if (total > ((int64_t)1 << 30)) throw Error(IASKIT_ERR_ARG, "more than 2^30 points");
     stats = Stats{};
-    N = (int)N_;
+    Ntot = (int)total;
     d = d_;
-    h = h_;
-    lam = lam_;
     s_max = s_max_;
     tol = tol_;
     prec = opt.precision;
-    kappa = std::min(opt.kappa, N - 1);
     const double t0 = now_ms();
-    // tree shape (data independent)
-    L = 0;
-    while ((N + (1 << L) - 1) / (1 << L) > leaf_m) ++L;
-    if (L > 24) throw Error(IASKIT_ERR_UNSUPPORTED, "tree deeper than 24 levels");
-    level_off.assign(L + 1, {});
-    nd.assign((size_t)2 << L, Node{});
-    nd[1].off = 0;
-    nd[1].size = N;
-    for (int l = 0; l < L; ++l)
-      for (int i = 0; i < (1 << l); ++i) {
-        Node& p = nd[uid(l, i)];
-        Node& a = nd[2 * uid(l, i)];
-        Node& b = nd[2 * uid(l, i) + 1];
-        a.off = p.off;
-        a.size = p.size / 2;
-        b.off = p.off + a.size;
-        b.size = p.size - a.size;
-      }
-    for (int l = 0; l <= L; ++l) {
-      level_off[l].resize((1 << l) + 1);
-      for (int i = 0; i < (1 << l); ++i) level_off[l][i] = nd[uid(l, i)].off;
-      level_off[l][1 << l] = N;
+    // problems and tree shapes (data independent)
+    pr.assign(in.size(), Prob{});
+    int pbase = 0, nbase = 0, min_n = Ntot;
+    Hmax = 0;
+    for (size_t q = 0; q < in.size(); ++q) {
+      Prob& P = pr[q];
+      P.N = (int)in[q].N;
+      P.h = in[q].h;
+      P.lam = in[q].lam;
+      P.scale = -1.0 / (2.0 * P.h * P.h);
+      P.pbase = pbase;
+      P.nbase = nbase;
+      P.L = 0;
+      while ((P.N + (1 << P.L) - 1) / (1 << P.L) > leaf_m) ++P.L;
+      if (P.L > 24) throw Error(IASKIT_ERR_UNSUPPORTED, "tree deeper than 24 levels");
+      pbase += P.N;
+      nbase += 2 << P.L;
+      min_n = std::min(min_n, P.N);
+      Hmax = std::max(Hmax, P.L);
     }
+    kappa = std::min(opt.kappa, min_n - 1);
+    nd.assign((size_t)nbase, Node{});
+    by_height.assign(Hmax + 1, {});
     m_max = 0;
-    for (int i = 0; i < (1 << L); ++i) m_max = std::max(m_max, nd[uid(L, i)].size);
+    nleaves = 0;
+    for (size_t q = 0; q < pr.size(); ++q) {
+      Prob& P = pr[q];
+      Node& root = nd[P.nbase + 1];
+      root.prob = (int)q;
+      root.uid = 1;
+      root.level = 0;
+      root.off = P.pbase;
+      root.size = P.N;
+      for (int l = 0; l < P.L; ++l)
+        for (int i = 0; i < (1 << l); ++i) {
+          const int u = (1 << l) + i;
+          const Node& p = nd[P.nbase + u];
+          Node& a = nd[P.nbase + 2 * u];
+          Node& b = nd[P.nbase + 2 * u + 1];
+          a.prob = b.prob = (int)q;
+          a.uid = 2 * u;
+          b.uid = 2 * u + 1;
+          a.level = b.level = l + 1;
+          a.off = p.off;
+          a.size = p.size / 2;
+          b.off = p.off + a.size;
+          b.size = p.size - a.size;
+        }
+      P.m_max = 0;
+      for (int i = 0; i < (1 << P.L); ++i) P.m_max = std::max(P.m_max, nd[P.nbase + (1 << P.L) + i].size);
+      m_max = std::max(m_max, P.m_max);
+    }
+    for (int hh = 0; hh <= Hmax; ++hh)
+      for (size_t q = 0; q < pr.size(); ++q) {
+        const int l = pr[q].L - hh;
+        if (l < 0) continue;
+        for (int i = 0; i < (1 << l); ++i) by_height[hh].push_back(pr[q].nbase + (1 << l) + i);
+      }
+    for (int g : by_height[0]) nd[g].leaf = nleaves++;
     if (m_max > 1536) throw Error(IASKIT_ERR_UNSUPPORTED, "leaf size above 1536");
-    if (2 * s_max > 1536 && L > 0) throw Error(IASKIT_ERR_UNSUPPORTED, "s_max above 768");
+    if (2 * s_max > 1536 && Hmax > 0) throw Error(IASKIT_ERR_UNSUPPORTED, "s_max above 768");
 
     status.ensure_n<int>(1);
     IA_CUDA(cudaMemsetAsync(status.as<int>(), 0, sizeof(int), st));
-    double* Xd = X.ensure_n<double>((size_t)N * d);
-    IA_CUDA(cudaMemcpyAsync(Xd, points, (size_t)N * d * sizeof(double),
-                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-    check_finite(Xd, (int64_t)N * d, status.as<int>(), st);
+    double* Xd = X.ensure_n<double>((size_t)Ntot * d);
+    if (concatenated) {
+      IA_CUDA(cudaMemcpyAsync(Xd, in[0].X, (size_t)Ntot * d * sizeof(double),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    } else {
+      for (size_t q = 0; q < pr.size(); ++q)
+        IA_CUDA(cudaMemcpyAsync(Xd + (size_t)pr[q].pbase * d, in[q].X, (size_t)pr[q].N * d * sizeof(double),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    }
+    check_finite(Xd, (int64_t)Ntot * d, status.as<int>(), st);
     raise_status(read_status_and_clear());
+    {
+      std::vector<int> hp(Ntot);
+      for (size_t q = 0; q < pr.size(); ++q)
+        std::fill(hp.begin() + pr[q].pbase, hp.begin() + pr[q].pbase + pr[q].N, (int)q);
+      int* dp = pid.ensure_n<int>(Ntot);
+      h2d(dp, hp.data(), hp.size(), st);
+      IA_CUDA(cudaStreamSynchronize(st));
+    }
 
-    // a1: tree
-    int* pm = perm.ensure_n<int>(N);
-    build_tree(Xd, N, d, L, level_off, pm, split_dim.ensure_n<int>((size_t)1 << std::max(L, 1)),
-               tree_s, st);
-    permute_points(Xd, pm, N, d, iperm.ensure_n<int>(N), Xp.ensure_n<double>((size_t)N * d), st);
+    // a1: tree, one step per level from the root; finished problems pass through
+    std::vector<TreeLevel> levels(Hmax);
+    for (int l = 0; l < Hmax; ++l) {
+      TreeLevel& lv = levels[l];
+      for (size_t q = 0; q < pr.size(); ++q) {
+        const Prob& P = pr[q];
+        if (l < P.L) {
+          for (int i = 0; i < (1 << l); ++i) {
+            const Node& n = nd[P.nbase + (1 << l) + i];
+            lv.off.push_back(n.off);
+            lv.kleft.push_back(n.size / 2);
+            lv.split.push_back(1);
+          }
+        } else {
+          lv.off.push_back(P.pbase);
+          lv.kleft.push_back(P.N);
+          lv.split.push_back(0);
+        }
+      }
+      lv.off.push_back(Ntot);
+    }
+    int* pm = perm.ensure_n<int>(Ntot);
+    build_tree(Xd, Ntot, d, levels, pm, tree_s, st);
+    permute_points(Xd, pm, Ntot, d, iperm.ensure_n<int>(Ntot), Xp.ensure_n<double>((size_t)Ntot * d), st);
     IA_CUDA(cudaStreamSynchronize(st));
     const double t1 = now_ms();
     stats.t_tree = t1 - t0;
 
-    Pl.clear();
-    Pl32.clear();
-    for (int l = 0; l <= L; ++l) {
-      Pl.emplace_back(new DevBuf());
-      Pl32.emplace_back(new DevBuf());
-    }
-    if (L > 0) {
-      // a2: kNN
-      stats.knn_fallback = knn_bruteforce(Xd, N, d, kappa, knn.ensure_n<int>((size_t)N * kappa), knn_s, st);
+    if (Hmax > 0) {
+      // a2: kNN inside every problem
+      std::vector<std::pair<int, int>> probs;
+      for (const Prob& P : pr) probs.emplace_back(P.pbase, P.N);
+      stats.knn_fallback =
+          knn_bruteforce(Xd, Ntot, d, kappa, knn.ensure_n<int>((size_t)Ntot * kappa), probs, knn_s, st);
       IA_CUDA(cudaStreamSynchronize(st));
       const double t2 = now_ms();
       stats.t_knn = t2 - t1;
@@ -461,42 +616,68 @@ class Solver {
     factored = true;
   }
 
-  // a3 + a4 + a5: skeletons, levels L .. 1; TS is the precision of the sampled
-  // blocks and of the Householder updates (pivot norms are FP64 in both).
+  // a3 + a4 + a5: skeletons, heights 0 .. Hmax-1 (roots excluded); TS is the
+  // precision of the sampled blocks and of the Householder updates.
   template <typename TS>
   void skeletonize() {
-    int* kp = knn_pos.ensure_n<int>((size_t)N * kappa);
-    knn_to_positions(knn.as<int>(), perm.as<int>(), iperm.as<int>(), N, kappa, kp, st);
+    int* kp = knn_pos.ensure_n<int>((size_t)Ntot * kappa);
+    knn_to_positions(knn.as<int>(), perm.as<int>(), iperm.as<int>(), Ntot, kappa, kp, st);
     const int samp_cap = opt.samp_factor * s_max;
     int64_t tot = 0;
-    for (int l = 1; l <= L; ++l)
-      for (int i = 0; i < (1 << l); ++i) {
-        Node& n = nd[uid(l, i)];
-        n.nsamp = std::min(samp_cap, N - n.size);
+    for (int hh = 0; hh <= Hmax; ++hh)
+      for (int g : by_height[hh]) {
+        if (is_root(g)) continue;
+        Node& n = nd[g];
+        n.nsamp = std::min(samp_cap, pr[n.prob].N - n.size);
         n.samp_off = tot;
         tot += n.nsamp;
       }
-    int* sp = samp.ensure_n<int>(tot);
+    int* sp = samp.ensure_n<int>(std::max<int64_t>(tot, 1));
     int* rk = ranks.ensure_n<int>(nd.size());
     IA_CUDA(cudaMemsetAsync(rk, 0, nd.size() * sizeof(int), st));
     int* sk = skel.ensure_n<int>(nd.size() * (size_t)s_max);
-    for (int l = L; l >= 1; --l) {
-      const int nn = 1 << l;
-      // sampling
-      std::vector<int> so(nn);
-      for (int i = 0; i < nn; ++i) so[i] = (int)nd[uid(l, i)].samp_off;
-      int* od = level_off_dev.ensure_n<int>(nn + 1 + nn);
-      h2d(od, level_off[l].data(), nn + 1, st);
-      h2d(od + nn + 1, so.data(), nn, st);
-      sample_level(kp, N, kappa, l, od, level_off[l], samp_cap, od + nn + 1, opt.seed, sp,
-                   status.as<int>(), samp_s, st);
+    int64_t p_total = 0;
+    for (int hh = 0; hh < Hmax; ++hh) {
+      std::vector<int> nodes;
+      for (int g : by_height[hh])
+        if (!is_root(g)) nodes.push_back(g);
+      if (nodes.empty()) continue;
+      // sampling step: node list covering all points (problems without a node here pass)
+      std::vector<int> off;
+      std::vector<SampleNodeInfo> info;
+      {
+        size_t k = 0;
+        for (size_t q = 0; q < pr.size(); ++q) {
+          const Prob& P = pr[q];
+          const int l = P.L - hh;
+          if (l >= 1) {
+            for (int i = 0; i < (1 << l); ++i) {
+              const Node& n = nd[nodes[k++]];
+              off.push_back(n.off);
+              info.push_back(SampleNodeInfo{P.pbase, P.N, n.uid, (int)n.samp_off, 1});
+            }
+          } else {
+            off.push_back(P.pbase);
+            info.push_back(SampleNodeInfo{P.pbase, P.N, 0, 0, 0});
+          }
+        }
+        off.push_back(Ntot);
+      }
+      const int nn = (int)info.size();
+      int* od = step_dev.ensure_n<int>(nn + 1 + (int64_t)nn * (sizeof(SampleNodeInfo) / sizeof(int)));
+      h2d(od, off.data(), nn + 1, st);
+      SampleNodeInfo* id = reinterpret_cast<SampleNodeInfo*>(od + nn + 1);
+      h2d(id, info.data(), info.size(), st);
+      sample_level(kp, Ntot, kappa, od, id, off, info, samp_cap, opt.seed, sp, status.as<int>(),
+                   samp_s, st);
       // sampled blocks
+      const int nk = (int)nodes.size();
       int64_t asz = 0, pvsz = 0, max_e = 0;
       int max_r = 0, max_c = 0;
-      std::vector<int64_t> aoff(nn), poff(nn);
-      for (int i = 0; i < nn; ++i) {
-        Node& n = nd[uid(l, i)];
-        n.ncols = (l == L) ? n.size : nd[2 * uid(l, i)].s + nd[2 * uid(l, i) + 1].s;
+      std::vector<int64_t> aoff(nk), poff(nk);
+      for (int i = 0; i < nk; ++i) {
+        Node& n = nd[nodes[i]];
+        n.ncols = is_leaf(nodes[i]) ? n.size : n2(nodes[i]);
         aoff[i] = asz;
         poff[i] = pvsz;
         asz += (int64_t)n.nsamp * n.ncols;
@@ -507,11 +688,11 @@ class Solver {
       }
       TS* A = A_ws.ensure_n<TS>(asz);
       int* pv = piv_ws.ensure_n<int>(pvsz);
-      std::vector<KDescT<TS>> kd(nn);
-      std::vector<CpqrDescT<TS>> qd(nn);
-      for (int i = 0; i < nn; ++i) {
-        const int u = uid(l, i);
-        Node& n = nd[u];
+      std::vector<KDescT<TS>> kd(nk);
+      std::vector<CpqrDescT<TS>> qd(nk);
+      for (int i = 0; i < nk; ++i) {
+        const int g = nodes[i];
+        Node& n = nd[g];
         KDescT<TS> k{};
         k.rows = sp + n.samp_off;
         k.nrows = n.nsamp;
@@ -519,85 +700,98 @@ class Solver {
         k.ld = n.nsamp;
         k.ncols = n.ncols;
         k.diag = 0.0;
-        if (l == L) {
+        k.scale = scale_of(g);
+        if (is_leaf(g)) {
           k.col0 = n.off;
         } else {
-          k.colsA = sk + (size_t)(2 * u) * s_max;
-          k.nA = nd[2 * u].s;
-          k.colsB = sk + (size_t)(2 * u + 1) * s_max;
+          k.colsA = sk + (size_t)left(g) * s_max;
+          k.nA = nd[left(g)].s;
+          k.colsB = sk + (size_t)right(g) * s_max;
         }
         kd[i] = k;
-        qd[i] = CpqrDescT<TS>{A + aoff[i], pv + poff[i], rk + u, n.nsamp, n.nsamp, n.ncols};
+        qd[i] = CpqrDescT<TS>{A + aoff[i], pv + poff[i], rk + g, n.nsamp, n.nsamp, n.ncols};
       }
       arena.clear();
       size_t ok = arena.push(kd), oq = arena.push(qd);
       char* base = upload_arena();
-      kernel_blocks<TS>(Xp.as<double>(), d, h, (const KDescT<TS>*)(base + ok), nn, max_e, st);
-      cpqr_id<TS>((const CpqrDescT<TS>*)(base + oq), nn, max_r, max_c, s_max, tol, st);
-      // ranks of this level
-      std::vector<int> rh(nn);
-      d2h(rh.data(), rk + uid(l, 0), nn, st);
+      kernel_blocks<TS>(Xp.as<double>(), d, (const KDescT<TS>*)(base + ok), nk, max_e, st);
+      cpqr_id<TS>((const CpqrDescT<TS>*)(base + oq), nk, max_r, max_c, s_max, tol, st);
+      // ranks of this height
+      std::vector<int> rall(nd.size());
+      d2h(rall.data(), rk, nd.size(), st);
       IA_CUDA(cudaStreamSynchronize(st));
       raise_status(read_status_and_clear());
       int64_t psz = 0;
       double qr_flops = 0;
-      for (int i = 0; i < nn; ++i) {
-        Node& n = nd[uid(l, i)];
-        n.s = rh[i];
-        n.P_off = psz;
+      for (int i = 0; i < nk; ++i) {
+        Node& n = nd[nodes[i]];
+        n.s = rall[nodes[i]];
+        n.P_off = p_total + psz;
         psz += (int64_t)n.s * n.ncols;
         // Householder update (dot + axpy) and norm recomputation per step, then R11^{-1} R12
         for (int k = 0; k < n.s; ++k) qr_flops += 6.0 * (n.nsamp - k) * (double)(n.ncols - k);
         qr_flops += (double)n.s * n.s * (n.ncols - n.s);
       }
       prof().flops[pk_of<TS>(PK_CPQR)] += qr_flops;
-      double* P = Pl[l]->ensure_n<double>(psz);
-      std::vector<PDescT<TS>> pd(nn);
-      for (int i = 0; i < nn; ++i) {
-        const int u = uid(l, i);
-        Node& n = nd[u];
+      // P storage grows by height; earlier heights are copied along when it grows
+      if ((p_total + psz) * (int64_t)sizeof(double) > (int64_t)Pd.bytes) {
+        DevBuf tmp;
+        double* t = tmp.ensure_n<double>(std::max<int64_t>(p_total, 1));
+        if (p_total)
+          IA_CUDA(cudaMemcpyAsync(t, Pd.as<double>(), p_total * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        IA_CUDA(cudaStreamSynchronize(st));
+        Pd.ensure_n<double>(2 * (p_total + psz));
+        if (p_total)
+          IA_CUDA(cudaMemcpyAsync(Pd.as<double>(), t, p_total * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        IA_CUDA(cudaStreamSynchronize(st));
+      }
+      double* P = Pd.as<double>();
+      std::vector<PDescT<TS>> pd(nk);
+      for (int i = 0; i < nk; ++i) {
+        const int g = nodes[i];
+        Node& n = nd[g];
         PDescT<TS> p{};
         p.A = A + aoff[i];
         p.piv = pv + poff[i];
         p.P = P + n.P_off;
-        p.skel = sk + (size_t)u * s_max;
+        p.skel = sk + (size_t)g * s_max;
         p.ld = n.nsamp;
         p.ncols = n.ncols;
         p.s = n.s;
-        if (l == L) {
+        if (is_leaf(g)) {
           p.col0 = n.off;
         } else {
-          p.colsA = sk + (size_t)(2 * u) * s_max;
-          p.nA = nd[2 * u].s;
-          p.colsB = sk + (size_t)(2 * u + 1) * s_max;
+          p.colsA = sk + (size_t)left(g) * s_max;
+          p.nA = nd[left(g)].s;
+          p.colsB = sk + (size_t)right(g) * s_max;
         }
         pd[i] = p;
       }
       arena.clear();
       size_t op = arena.push(pd);
       base = upload_arena();
-      assemble_P<TS>((const PDescT<TS>*)(base + op), nn, max_c, st);
-      if (prec == PREC_MIXED) convert_d2f(P, Pl32[l]->ensure_n<float>(psz), psz, st);
+      assemble_P<TS>((const PDescT<TS>*)(base + op), nk, max_c, st);
+      p_total += psz;
       stats.bytes_P += psz * 8;
     }
+    if (prec == PREC_MIXED && p_total > 0) convert_d2f(Pd.as<double>(), Pf.ensure_n<float>(p_total), p_total, st);
   }
 
   // a4 + a6: leaf LU of lambda I + K_aa.  Mixed: the FP64 blocks are kept for the
   // operator and their FP32 rounding is factored.
   void leaf_lu() {
-    const int nl = 1 << L;
     int64_t tot = 0;
-    for (int i = 0; i < nl; ++i) {
-      Node& n = nd[uid(L, i)];
+    for (int g : by_height[0]) {
+      Node& n = nd[g];
       n.LU_off = tot;
       tot += (int64_t)n.size * n.size;
     }
     const bool mixed = prec == PREC_MIXED;
     double* blocks = mixed ? Kleaf.ensure_n<double>(tot) : LU.ensure_n<double>(tot);
-    int* lp = LUpiv.ensure_n<int>((size_t)nl * m_max);
-    std::vector<KDesc> kd(nl);
-    for (int i = 0; i < nl; ++i) {
-      const Node& n = nd[uid(L, i)];
+    int* lp = LUpiv.ensure_n<int>((size_t)nleaves * m_max);
+    std::vector<KDesc> kd;
+    for (int g : by_height[0]) {
+      const Node& n = nd[g];
       KDesc k{};
       k.row0 = n.off;
       k.nrows = n.size;
@@ -605,21 +799,22 @@ class Solver {
       k.ncols = n.size;
       k.out = blocks + n.LU_off;
       k.ld = n.size;
-      k.diag = lam;
-      kd[i] = k;
+      k.diag = pr[n.prob].lam;
+      k.scale = scale_of(g);
+      kd.push_back(k);
     }
+    const int nl = (int)kd.size();
     arena.clear();
     size_t ok = arena.push(kd);
     char* base = upload_arena();
-    kernel_blocks<double>(Xp.as<double>(), d, h, (const KDesc*)(base + ok), nl,
-                          (int64_t)m_max * m_max, st);
+    kernel_blocks<double>(Xp.as<double>(), d, (const KDesc*)(base + ok), nl, (int64_t)m_max * m_max, st);
     if (mixed) {
       float* lu = LU32.ensure_n<float>(tot);
       convert_d2f(blocks, lu, tot, st);
-      std::vector<LuDescT<float>> ld(nl);
-      for (int i = 0; i < nl; ++i) {
-        const Node& n = nd[uid(L, i)];
-        ld[i] = LuDescT<float>{lu + n.LU_off, lp + (int64_t)i * m_max, n.size, n.size};
+      std::vector<LuDescT<float>> ld;
+      for (int g : by_height[0]) {
+        const Node& n = nd[g];
+        ld.push_back(LuDescT<float>{lu + n.LU_off, lp + (int64_t)n.leaf * m_max, n.size, n.size});
       }
       arena.clear();
       size_t ol = arena.push(ld);
@@ -629,10 +824,10 @@ class Solver {
       stats.bytes_operator += tot * 8;
       stats.bytes_LU = tot * 4;
     } else {
-      std::vector<LuDesc> ld(nl);
-      for (int i = 0; i < nl; ++i) {
-        const Node& n = nd[uid(L, i)];
-        ld[i] = LuDesc{blocks + n.LU_off, lp + (int64_t)i * m_max, n.size, n.size};
+      std::vector<LuDesc> ld;
+      for (int g : by_height[0]) {
+        const Node& n = nd[g];
+        ld.push_back(LuDesc{blocks + n.LU_off, lp + (int64_t)n.leaf * m_max, n.size, n.size});
       }
       arena.clear();
       size_t ol = arena.push(ld);
@@ -643,24 +838,23 @@ class Solver {
     }
   }
 
-  // a7 + a8: W and Z, levels L-1 .. 0, factorization stored in precision T
+  // a7 + a8: W and Z, heights 1 .. Hmax, factorization stored in precision T
   template <typename T>
   void factor_levels() {
-    if (L == 0) return;
+    if (Hmax == 0) return;
     const bool mixed = std::is_same<T, float>::value;
     int64_t wsz = 0, zsz = 0, zp = 0, csz = 0;
-    for (int l = 1; l <= L; ++l)
-      for (int i = 0; i < (1 << l); ++i) {
-        int u = uid(l, i);
-        Node& n = nd[u];
+    for (int hh = 0; hh < Hmax; ++hh)
+      for (int g : by_height[hh]) {
+        if (is_root(g)) continue;
+        Node& n = nd[g];
         n.W_off = wsz;
-        wsz += (int64_t)n.size * nd[u ^ 1].s;
+        wsz += (int64_t)n.size * nd[sibling(g)].s;
       }
-    for (int l = 0; l < L; ++l)
-      for (int i = 0; i < (1 << l); ++i) {
-        int u = uid(l, i);
-        Node& n = nd[u];
-        int sa = nd[2 * u].s, sb = nd[2 * u + 1].s;
+    for (int hh = 1; hh <= Hmax; ++hh)
+      for (int g : by_height[hh]) {
+        Node& n = nd[g];
+        const int sa = nd[left(g)].s, sb = nd[right(g)].s;
         n.Z_off = zsz;
         zsz += (int64_t)(sa + sb) * (sa + sb);
         n.Zpiv_off = zp;
@@ -673,81 +867,78 @@ class Solver {
     const double bytes = (double)(wsz + zsz + csz) * sizeof(T) + (mixed ? (double)wsz * 8 : 0.0);
     if (opt.mem_cap_gb > 0 && bytes > opt.mem_cap_gb * 1e9)
       throw Error(IASKIT_ERR_NOMEM, "factorization exceeds mem_cap_gb");
-    T* W = (mixed ? Wb32 : Wb).template ensure_n<T>(wsz);
-    double* U64 = mixed ? Ustore.ensure_n<double>(wsz) : (double*)W;
-    (mixed ? Zb32 : Zb).template ensure_n<T>(zsz);
-    Zpiv.ensure_n<int>(zp);
-    (mixed ? Cb32 : Cb).template ensure_n<T>(csz);
+    T* W = (mixed ? Wb32 : Wb).template ensure_n<T>(std::max<int64_t>(wsz, 1));
+    double* U64 = mixed ? Ustore.ensure_n<double>(std::max<int64_t>(wsz, 1)) : (double*)W;
+    (mixed ? Zb32 : Zb).template ensure_n<T>(std::max<int64_t>(zsz, 1));
+    Zpiv.ensure_n<int>(std::max<int64_t>(zp, 1));
+    (mixed ? Cb32 : Cb).template ensure_n<T>(std::max<int64_t>(csz, 1));
     stats.bytes_W = wsz * (int64_t)sizeof(T);
     if (mixed) stats.bytes_operator += wsz * 8;
     int* sk = skel.as<int>();
-    for (int l = L - 1; l >= 0; --l) {
-      const int nn = 1 << l;
-      // U blocks of the children of every node of level l (FP64)
+    T* C = cP<T>();
+    for (int hh = 1; hh <= Hmax; ++hh) {
+      const std::vector<int>& nodes = by_height[hh];
+      // U blocks of the children of every node of this height (FP64)
       std::vector<KDesc> kd;
       int64_t max_e = 0, lo = INT64_MAX, hi = 0;
-      for (int i = 0; i < 2 * nn; ++i) {
-        int c = uid(l + 1, i);
-        const Node& n = nd[c];
-        KDesc k{};
-        k.row0 = n.off;
-        k.nrows = n.size;
-        k.colsA = sk + (size_t)(c ^ 1) * s_max;
-        k.nA = nd[c ^ 1].s;
-        k.ncols = nd[c ^ 1].s;
-        k.out = U64 + n.W_off;
-        k.ld = n.size;
-        k.diag = 0.0;
-        kd.push_back(k);
-        max_e = std::max<int64_t>(max_e, (int64_t)n.size * k.ncols);
-        lo = std::min<int64_t>(lo, n.W_off);
-        hi = std::max<int64_t>(hi, n.W_off + (int64_t)n.size * k.ncols);
-      }
+      std::vector<RootBlock<T>> rb;
+      for (int g : nodes)
+        for (int c : {left(g), right(g)}) {
+          const Node& n = nd[c];
+          const int sib = sibling(c);
+          KDesc k{};
+          k.row0 = n.off;
+          k.nrows = n.size;
+          k.colsA = sk + (size_t)sib * s_max;
+          k.nA = nd[sib].s;
+          k.ncols = nd[sib].s;
+          k.out = U64 + n.W_off;
+          k.ld = n.size;
+          k.diag = 0.0;
+          k.scale = scale_of(c);
+          kd.push_back(k);
+          max_e = std::max<int64_t>(max_e, (int64_t)n.size * k.ncols);
+          lo = std::min<int64_t>(lo, n.W_off);
+          hi = std::max<int64_t>(hi, n.W_off + (int64_t)n.size * k.ncols);
+          // left child: C_l = P_l W_{l r~} (s_l x s_r); right child: C_r = P_r W_{r l~}
+          T* tout = C + ((n.uid & 1) == 0 ? nd[g].CL_off : nd[g].CR_off);
+          rb.push_back(RootBlock<T>{c, W + n.W_off, n.size, nd[sib].s, tout, n.s});
+        }
       arena.clear();
       size_t ok = arena.push(kd);
       char* base = upload_arena();
-      kernel_blocks<double>(Xp.as<double>(), d, h, (const KDesc*)(base + ok), (int)kd.size(), max_e, st);
-      if (mixed) convert_d2f(U64 + lo, (float*)W + lo, hi - lo, st);
+      kernel_blocks<double>(Xp.as<double>(), d, (const KDesc*)(base + ok), (int)kd.size(), max_e, st);
+      if (mixed && hi > lo) convert_d2f(U64 + lo, (float*)W + lo, hi - lo, st);
       // W = Solve(child, U) for all children at once; C blocks come back as P_c W_c
-      std::vector<RootBlock<T>> rb;
-      T* C = cP<T>();
-      for (int i = 0; i < 2 * nn; ++i) {
-        int c = uid(l + 1, i);
-        int par = c >> 1;
-        const Node& n = nd[c];
-        // left child: C_l = P_l W_{l r~} (s_l x s_r); right child: C_r = P_r W_{r l~}
-        T* tout = C + ((c & 1) == 0 ? nd[par].CL_off : nd[par].CR_off);
-        rb.push_back(RootBlock<T>{c, W + n.W_off, n.size, nd[c ^ 1].s, tout, n.s});
-      }
-      forest_solve<T>(l + 1, rb);
+      forest_solve<T>(rb);
       // reduced systems Z'' = [[I, C_l], [C_r, I]] and their LU
       std::vector<ZDescT<T>> zd;
       std::vector<LuDescT<T>> ld;
       int64_t max_z = 0;
       int max_n = 0;
-      for (int i = 0; i < nn; ++i) {
-        int u = uid(l, i);
-        int sa = nd[2 * u].s, sb = nd[2 * u + 1].s;
-        zd.push_back(ZDescT<T>{C + nd[u].CL_off, C + nd[u].CR_off, zP<T>() + nd[u].Z_off, sa, sb});
-        ld.push_back(LuDescT<T>{zP<T>() + nd[u].Z_off, Zpiv.as<int>() + nd[u].Zpiv_off, sa + sb, sa + sb});
+      for (int g : nodes) {
+        const int sa = nd[left(g)].s, sb = nd[right(g)].s;
+        zd.push_back(ZDescT<T>{C + nd[g].CL_off, C + nd[g].CR_off, zP<T>() + nd[g].Z_off, sa, sb});
+        ld.push_back(LuDescT<T>{zP<T>() + nd[g].Z_off, Zpiv.as<int>() + nd[g].Zpiv_off, sa + sb, sa + sb});
         max_z = std::max<int64_t>(max_z, (int64_t)(sa + sb) * (sa + sb));
         max_n = std::max(max_n, sa + sb);
       }
       arena.clear();
       size_t oz = arena.push(zd), ol = arena.push(ld);
       base = upload_arena();
-      form_Z<T>((const ZDescT<T>*)(base + oz), nn, max_z, st);
+      form_Z<T>((const ZDescT<T>*)(base + oz), (int)zd.size(), max_z, st);
       prof().flops[pk_of<T>(PK_GETRF)] += getrf_flops(ld);
-      getrf_batched<T>((const LuDescT<T>*)(base + ol), nn, max_n, status.as<int>(), st);
+      getrf_batched<T>((const LuDescT<T>*)(base + ol), (int)ld.size(), max_n, status.as<int>(), st);
     }
   }
 
   // ------------------------------------------------------------------ solve
+  // rhs: all problems' N_p x nrhs blocks, one after the other (ORIGINAL order), device
   void solve_device(double* rhs, int nrhs) {
     if (!factored) throw Error(IASKIT_ERR_NOT_FACTORED, "no factorization");
-    if (nrhs < 1 || (int64_t)N * nrhs > ((int64_t)1 << 31)) throw Error(IASKIT_ERR_ARG, "bad nrhs");
+    if (nrhs < 1 || (int64_t)Ntot * nrhs > ((int64_t)1 << 31)) throw Error(IASKIT_ERR_ARG, "bad nrhs");
     const double t0 = now_ms();
-    check_finite(rhs, (int64_t)N * nrhs, status.as<int>(), st);
+    check_finite(rhs, (int64_t)Ntot * nrhs, status.as<int>(), st);
     raise_status(read_status_and_clear());
     stats.refine_hist.clear();
     stats.refine_sweeps = 0;
@@ -762,32 +953,36 @@ class Solver {
     stats.t_solve = now_ms() - t0;
   }
 
-  // out <- (lambda I + K~)^{-1} in with the stored factorization (ORIGINAL order,
-  // N x nrhs, ld N); in and out may alias.
+  // out <- (lambda I + K~)^{-1} in with the stored factorization; in and out may alias.
   void plain_solve(const double* in, int nrhs, double* out) {
-    const size_t n = (size_t)N * nrhs;
+    const size_t n = (size_t)Ntot * nrhs;
+    const BlockDesc* blocks = upload_blocks(nrhs, false);
     double* V = vbuf.ensure_n<double>(n);
-    permute_rows<double>(in, N, V, N, perm.as<int>(), N, nrhs, false, st);
+    gather(in, V, nrhs, blocks, false);
     if (prec == PREC_MIXED) {
       float* V32 = vbuf32.ensure_n<float>(n);
       convert_d2f(V, V32, (int64_t)n, st);
-      std::vector<RootBlock<float>> rb{RootBlock<float>{1, V32, N, nrhs, nullptr, 0}};
-      forest_solve<float>(0, rb);
+      std::vector<RootBlock<float>> rb;
+      for (const Prob& P : pr)
+        rb.push_back(RootBlock<float>{P.nbase + 1, V32 + (size_t)P.pbase * nrhs, P.N, nrhs, nullptr, 0});
+      forest_solve<float>(rb);
       convert_f2d(V32, V, (int64_t)n, st);
     } else {
-      std::vector<RootBlock<double>> rb{RootBlock<double>{1, V, N, nrhs, nullptr, 0}};
-      forest_solve<double>(0, rb);
+      std::vector<RootBlock<double>> rb;
+      for (const Prob& P : pr)
+        rb.push_back(RootBlock<double>{P.nbase + 1, V + (size_t)P.pbase * nrhs, P.N, nrhs, nullptr, 0});
+      forest_solve<double>(rb);
     }
-    permute_rows<double>(V, N, out, N, perm.as<int>(), N, nrhs, true, st);
+    gather(V, out, nrhs, blocks, true);
   }
 
   // Iterative refinement against the FP64 operator: w <- w + Solve(u - A w).
   void refine_solve(double* rhs, int nrhs, int sweeps) {
-    const size_t n = (size_t)N * nrhs;
+    const size_t n = (size_t)Ntot * nrhs;
     double* u = rbuf.ensure_n<double>(2 * n);  // u copy, residual
     double* r = u + n;
     IA_CUDA(cudaMemcpyAsync(u, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    std::vector<double> un(nrhs), rn(nrhs);
+    std::vector<double> un, rn;
     column_norms(u, nrhs, un);
     plain_solve(u, nrhs, rhs);
     auto worst_residual = [&]() {
@@ -795,7 +990,7 @@ class Solver {
       axpby(u, r, n);                    // r = u - A w
       column_norms(r, nrhs, rn);
       double worst = 0;
-      for (int c = 0; c < nrhs; ++c) worst = std::max(worst, un[c] > 0 ? rn[c] / un[c] : rn[c]);
+      for (size_t c = 0; c < rn.size(); ++c) worst = std::max(worst, un[c] > 0 ? rn[c] / un[c] : rn[c]);
       stats.refine_hist.push_back(worst);
       return worst;
     };
@@ -809,99 +1004,122 @@ class Solver {
       throw Error(IASKIT_ERR_NOT_CONVERGED, "refinement did not converge");
   }
 
-  void column_norms(const double* x, int nrhs, std::vector<double>& out);
-  void axpby(const double* u, double* r, size_t n);
-  void add_inplace(double* w, const double* dlt, size_t n);
-  void scale_copy(const double* x, double* y, double a, size_t n);
+  void column_norms(const double* x, int nrhs, std::vector<double>& out) {
+    const BlockDesc* blocks = upload_blocks(nrhs, false);
+    double* dn = normbuf.ensure_n<double>((size_t)nrhs * pr.size());
+    {
+      ProfScope _ps(PK_MISC, st);
+      colnorm_kernel<<<dim3(nrhs, (unsigned)pr.size()), 256, 0, st>>>(x, blocks, nrhs, dn);
+      IA_LAUNCH_CHECK();
+    }
+    out.resize((size_t)nrhs * pr.size());
+    d2h(out.data(), dn, out.size(), st);
+    IA_CUDA(cudaStreamSynchronize(st));
+  }
+  void axpby(const double* u, double* r, size_t n) {
+    ProfScope _ps(PK_MISC, st);
+    axpby_kernel<<<grid_cap((int64_t)n, 8192), 256, 0, st>>>(u, r, n);
+    IA_LAUNCH_CHECK();
+  }
+  void add_inplace(double* w, const double* dl, size_t n) {
+    ProfScope _ps(PK_MISC, st);
+    add_kernel<<<grid_cap((int64_t)n, 8192), 256, 0, st>>>(w, dl, n);
+    IA_LAUNCH_CHECK();
+  }
 
   // ------------------------------------------------------- hierarchical apply
-  // u = (lambda I + K~) w, ORIGINAL order, device pointers.  Skeletonize (w~ = P w
-  // up the tree) then Evaluate (u_c += K_{c s~} w~_s for the sibling s of every
-  // node c, and the leaf blocks).  The plain form recomputes the kernel entries in
-  // FP64; the mixed form multiplies the FP64 blocks it stored.
+  // u = (lambda I + K~) w (all problems' blocks, ORIGINAL order, device).  Skeletonize
+  // (w~ = P w up the tree) then Evaluate (u_c += K_{c s~} w~_s for the sibling s of
+  // every non-root node c, and the leaf blocks).  The plain form recomputes the
+  // kernel entries in FP64; the mixed form multiplies the FP64 blocks it stored.
   void apply_device(const double* w, double* u, int nrhs) {
     if (!factored) throw Error(IASKIT_ERR_NOT_FACTORED, "no factorization");
     if (nrhs < 1) throw Error(IASKIT_ERR_ARG, "bad nrhs");
     const double t0 = now_ms();
     const bool stored = prec == PREC_MIXED;
-    const size_t n = (size_t)N * nrhs;
+    const size_t n = (size_t)Ntot * nrhs;
     double* Wp = ubuf.ensure_n<double>(2 * n);
     double* Up = Wp + n;
-    permute_rows<double>(w, N, Wp, N, perm.as<int>(), N, nrhs, false, st);
-    if (stored) IA_CUDA(cudaMemsetAsync(Up, 0, n * sizeof(double), st));
-    else scale_copy(Wp, Up, lam, n);
+    const BlockDesc* blocks = upload_blocks(nrhs, true);
+    gather(w, Wp, nrhs, blocks, false);
+    if (stored) {
+      IA_CUDA(cudaMemsetAsync(Up, 0, n * sizeof(double), st));
+    } else {
+      ProfScope _ps(PK_MISC, st);
+      scale_blocks_kernel<<<dim3(1024, (unsigned)pr.size()), 256, 0, st>>>(Wp, Up, blocks, nrhs);
+      IA_LAUNCH_CHECK();
+    }
+    // node g's rows inside its problem's block: base + pbase*nrhs + (off - pbase), ld N_p
+    auto rows = [&](double* base, int g) {
+      const Prob& P = pr[nd[g].prob];
+      return base + (size_t)P.pbase * nrhs + (nd[g].off - P.pbase);
+    };
+    auto ldp = [&](int g) { return pr[nd[g].prob].N; };
     std::vector<int64_t> woff(nd.size(), 0);
     int64_t tot = 0;
-    for (int l = 0; l < L; ++l)
-      for (int i = 0; i < (1 << l); ++i) {
-        int u_ = uid(l, i);
-        woff[u_] = tot;
-        tot += (int64_t)(nd[2 * u_].s + nd[2 * u_ + 1].s) * nrhs;
+    for (int hh = 1; hh <= Hmax; ++hh)
+      for (int g : by_height[hh]) {
+        woff[g] = tot;
+        tot += (int64_t)n2(g) * nrhs;
       }
     double* WT = wt.ensure_n<double>(std::max<int64_t>(tot, 1));
-    auto n2 = [&](int u_) { return nd[2 * u_].s + nd[2 * u_ + 1].s; };
     auto wsib = [&](int c) {  // w~ of the sibling of c, inside the parent's [w~_a; w~_b]
-      int par = c >> 1, sib = c ^ 1;
-      return WT + woff[par] + ((sib & 1) ? nd[2 * par].s : 0);
+      const int par = parent(c), sib = sibling(c);
+      return WT + woff[par] + rowoff(sib);
     };
-    if (L > 0) {
+    // Skeletonize: w~ = P w, leaves first, up to the children of the roots
+    for (int hh = 0; hh < Hmax; ++hh) {
       std::vector<GemmDesc> g;
-      for (int i = 0; i < (1 << L); ++i) {
-        int u_ = uid(L, i), par = u_ >> 1;
-        add_gemm<double>(g, Pl[L]->as<double>() + nd[u_].P_off, nd[u_].s, Wp + nd[u_].off, N,
-                         WT + woff[par] + ((u_ & 1) ? nd[2 * par].s : 0), n2(par), nd[u_].s, nrhs,
-                         nd[u_].size, 1.0, 0.0);
+      for (int c : by_height[hh]) {
+        if (is_root(c)) continue;
+        const int par = parent(c);
+        const double* src = hh == 0 ? rows(Wp, c) : WT + woff[c];
+        const int lds = hh == 0 ? ldp(c) : n2(c);
+        add_gemm<double>(g, Pd.as<double>() + nd[c].P_off, nd[c].s, src, lds,
+                         WT + woff[par] + rowoff(c), n2(par), nd[c].s, nrhs, nd[c].ncols, 1.0, 0.0);
       }
       run_gemms(g);
-      for (int l = L - 1; l >= 1; --l) {
-        g.clear();
-        for (int i = 0; i < (1 << l); ++i) {
-          int u_ = uid(l, i), par = u_ >> 1;
-          add_gemm<double>(g, Pl[l]->as<double>() + nd[u_].P_off, nd[u_].s, WT + woff[u_],
-                           n2(u_), WT + woff[par] + ((u_ & 1) ? nd[2 * par].s : 0), n2(par),
-                           nd[u_].s, nrhs, n2(u_), 1.0, 0.0);
-        }
-        run_gemms(g);
-      }
     }
-    // Evaluate: one launch per level keeps the rows written by a launch disjoint
+    // Evaluate: one launch per height keeps the rows written by a launch disjoint
     int* sk = skel.as<int>();
-    for (int l = 1; l <= L + 1; ++l) {
-      const bool leaves = l == L + 1;
-      const int lev = leaves ? L : l;
-      if (stored) {
+    for (int hh = 0; hh <= Hmax; ++hh) {
+      for (int pass = 0; pass < 2; ++pass) {  // pass 0: sibling skeletons, pass 1: leaf blocks
+        if (pass == 1 && hh != 0) continue;
         std::vector<GemmDesc> g;
-        for (int i = 0; i < (1 << lev); ++i) {
-          int c = uid(lev, i);
-          if (leaves)
-            add_gemm<double>(g, Kleaf.as<double>() + nd[c].LU_off, nd[c].size, Wp + nd[c].off, N,
-                             Up + nd[c].off, N, nd[c].size, nrhs, nd[c].size, 1.0, 1.0);
-          else
-            add_gemm<double>(g, Ustore.as<double>() + nd[c].W_off, nd[c].size, wsib(c),
-                             n2(c >> 1), Up + nd[c].off, N, nd[c].size, nrhs, nd[c ^ 1].s, 1.0, 1.0);
-        }
-        run_gemms(g);
-      } else {
         std::vector<KMatvecDesc> md;
         int max_rows = 0;
-        for (int i = 0; i < (1 << lev); ++i) {
-          int c = uid(lev, i);
-          if (leaves)
-            md.push_back(KMatvecDesc{nullptr, Wp + nd[c].off, Up + nd[c].off, nd[c].off, nd[c].size,
-                                     nd[c].off, nd[c].size, N, N});
-          else
-            md.push_back(KMatvecDesc{sk + (size_t)(c ^ 1) * s_max, wsib(c), Up + nd[c].off, nd[c].off,
-                                     nd[c].size, 0, nd[c ^ 1].s, n2(c >> 1), N});
+        for (int c : by_height[hh]) {
+          if (pass == 0 && is_root(c)) continue;
+          if (pass == 0) {
+            const int sib = sibling(c);
+            if (stored)
+              add_gemm<double>(g, Ustore.as<double>() + nd[c].W_off, nd[c].size, wsib(c), n2(parent(c)),
+                               rows(Up, c), ldp(c), nd[c].size, nrhs, nd[sib].s, 1.0, 1.0);
+            else
+              md.push_back(KMatvecDesc{sk + (size_t)sib * s_max, wsib(c), rows(Up, c), nd[c].off,
+                                       nd[c].size, 0, nd[sib].s, n2(parent(c)), ldp(c), scale_of(c)});
+          } else {
+            if (stored)
+              add_gemm<double>(g, Kleaf.as<double>() + nd[c].LU_off, nd[c].size, rows(Wp, c), ldp(c),
+                               rows(Up, c), ldp(c), nd[c].size, nrhs, nd[c].size, 1.0, 1.0);
+            else
+              md.push_back(KMatvecDesc{nullptr, rows(Wp, c), rows(Up, c), nd[c].off, nd[c].size,
+                                       nd[c].off, nd[c].size, ldp(c), ldp(c), scale_of(c)});
+          }
           max_rows = std::max(max_rows, nd[c].size);
         }
-        arena.clear();
-        size_t om = arena.push(md);
-        char* base = upload_arena();
-        kernel_matvec(Xp.as<double>(), d, h, nrhs, (const KMatvecDesc*)(base + om), (int)md.size(),
-                      max_rows, st);
+        if (stored) {
+          run_gemms(g);
+        } else if (!md.empty()) {
+          arena.clear();
+          size_t om = arena.push(md);
+          char* base = upload_arena();
+          kernel_matvec(Xp.as<double>(), d, nrhs, (const KMatvecDesc*)(base + om), (int)md.size(),
+                        max_rows, st);
+        }
       }
     }
-    permute_rows<double>(Up, N, u, N, perm.as<int>(), N, nrhs, true, st);
+    gather(Up, u, nrhs, blocks, true);
     IA_CUDA(cudaStreamSynchronize(st));
     prof().resolve();
     stats.t_apply = now_ms() - t0;
@@ -909,72 +1127,16 @@ class Solver {
 
   void release() {
     factored = false;
-    DevBuf* all[] = {&X, &Xp, &perm, &iperm, &split_dim, &knn, &knn_pos, &samp, &ranks, &skel,
-                     &piv_ws, &A_ws, &status, &arena_dev, &level_off_dev, &tbuf, &vbuf, &vbuf32,
-                     &ubuf, &rbuf, &wt, &io, &normbuf, &LU, &LUpiv, &Wb, &Zb, &Zpiv, &Cb, &LU32,
-                     &Wb32, &Zb32, &Cb32, &tbuf32, &Kleaf, &Ustore};
+    DevBuf* all[] = {&X, &Xp, &perm, &iperm, &pid, &knn, &knn_pos, &samp, &ranks, &skel,
+                     &piv_ws, &A_ws, &status, &arena_dev, &step_dev, &tbuf, &vbuf, &vbuf32,
+                     &ubuf, &rbuf, &wt, &io, &normbuf, &blocks_dev, &LU, &LUpiv, &Wb, &Zb, &Zpiv,
+                     &Cb, &LU32, &Wb32, &Zb32, &Cb32, &tbuf32, &Kleaf, &Ustore, &Pd, &Pf};
     for (DevBuf* b : all) b->release();
-    Pl.clear();
-    Pl32.clear();
     tree_s.release();
     knn_s.release();
     samp_s.release();
   }
 };
-
-__global__ void axpby_kernel(const double* u, double* r, size_t n) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    r[i] = u[i] - r[i];
-}
-__global__ void add_kernel(double* w, const double* dl, size_t n) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    w[i] += dl[i];
-}
-__global__ void scale_kernel(const double* x, double* y, double a, size_t n) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    y[i] = a * x[i];
-}
-__global__ void colnorm_kernel(const double* x, int N, double* out) {
-  __shared__ double red[32];
-  const double* c = x + (size_t)blockIdx.x * N;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) s = fma(c[i], c[i], s);
-  s = warp_sum(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    s = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    s = warp_sum(s);
-    if (threadIdx.x == 0) out[blockIdx.x] = sqrt(s);
-  }
-}
-
-void Solver::column_norms(const double* x, int nrhs, std::vector<double>& out) {
-  double* dn = normbuf.ensure_n<double>(nrhs);
-  {
-    ProfScope _ps(PK_MISC, st);
-    colnorm_kernel<<<nrhs, 256, 0, st>>>(x, N, dn);
-    IA_LAUNCH_CHECK();
-  }
-  out.resize(nrhs);
-  d2h(out.data(), dn, nrhs, st);
-  IA_CUDA(cudaStreamSynchronize(st));
-}
-void Solver::axpby(const double* u, double* r, size_t n) {
-  ProfScope _ps(PK_MISC, st);
-  axpby_kernel<<<std::min<size_t>(ceil_div(n, 256), 8192), 256, 0, st>>>(u, r, n);
-  IA_LAUNCH_CHECK();
-}
-void Solver::add_inplace(double* w, const double* dl, size_t n) {
-  ProfScope _ps(PK_MISC, st);
-  add_kernel<<<std::min<size_t>(ceil_div(n, 256), 8192), 256, 0, st>>>(w, dl, n);
-  IA_LAUNCH_CHECK();
-}
-void Solver::scale_copy(const double* x, double* y, double a, size_t n) {
-  ProfScope _ps(PK_MISC, st);
-  scale_kernel<<<std::min<size_t>(ceil_div(n, 256), 8192), 256, 0, st>>>(x, y, a, n);
-  IA_LAUNCH_CHECK();
-}
 
 Solver& S() {
   static Solver s;
@@ -1004,11 +1166,33 @@ void require_factored() {
   if (!S().factored) throw Error(IASKIT_ERR_NOT_FACTORED, "no factorization");
 }
 
-int check_node(int level, int index) {
+const Prob& selected_problem() {
   Solver& s = S();
-  if (level < 1 || level > s.L || index < 0 || index >= (1 << level))
+  if (s.opt.problem < 0 || s.opt.problem >= (int)s.pr.size())
+    throw Error(IASKIT_ERR_ARG, "selected problem out of range");
+  return s.pr[s.opt.problem];
+}
+
+// gid of node (level, index) of the selected problem
+int check_node(int level, int index) {
+  const Prob& P = selected_problem();
+  if (level < 1 || level > P.L || index < 0 || index >= (1 << level))
     throw Error(IASKIT_ERR_ARG, "node out of range");
-  return (1 << level) + index;
+  return P.nbase + (1 << level) + index;
+}
+
+int factor_batched_impl(int nprob, const double* const* points, const double* concat,
+                        const int64_t* N, int d, const double* h, const double* lambda, int leaf_m,
+                        int s_max, double tol, bool dev) {
+  int rc = guarded([&] {
+    if (nprob < 1 || !N || !h || !lambda) throw Error(IASKIT_ERR_ARG, "bad batch description");
+    std::vector<Solver::ProbIn> in;
+    for (int q = 0; q < nprob; ++q)
+      in.push_back(Solver::ProbIn{concat ? (q == 0 ? concat : nullptr) : points[q], N[q], h[q], lambda[q]});
+    S().factor(in, dev, concat != nullptr, d, leaf_m, s_max, tol);
+  });
+  if (rc != IASKIT_OK) S().factored = false;
+  return rc;
 }
 
 }  // namespace
@@ -1024,16 +1208,33 @@ extern "C" {
 
 int iaskit_factor(const double* points, int64_t N, int d, double h, double lambda, int leaf_m,
                   int s_max, double tol) {
-  int rc = guarded([&] { S().factor(points, false, N, d, h, lambda, leaf_m, s_max, tol); });
-  if (rc != IASKIT_OK) S().factored = false;
-  return rc;
+  if (!points) return fail(IASKIT_ERR_ARG, "points is null");
+  const double* pts[1] = {points};
+  return factor_batched_impl(1, pts, nullptr, &N, d, &h, &lambda, leaf_m, s_max, tol, false);
 }
 
 int iaskit_factor_device(const double* d_points, int64_t N, int d, double h, double lambda,
                          int leaf_m, int s_max, double tol) {
-  int rc = guarded([&] { S().factor(d_points, true, N, d, h, lambda, leaf_m, s_max, tol); });
-  if (rc != IASKIT_OK) S().factored = false;
-  return rc;
+  if (!d_points) return fail(IASKIT_ERR_ARG, "points is null");
+  return factor_batched_impl(1, nullptr, d_points, &N, d, &h, &lambda, leaf_m, s_max, tol, true);
+}
+
+int iaskit_factor_batched(int nprob, const double* const* points, const int64_t* N, int d,
+                          const double* h, const double* lambda, int leaf_m, int s_max, double tol) {
+  if (!points) return fail(IASKIT_ERR_ARG, "points is null");
+  return factor_batched_impl(nprob, points, nullptr, N, d, h, lambda, leaf_m, s_max, tol, false);
+}
+
+int iaskit_factor_batched_device(int nprob, const double* d_points, const int64_t* N, int d,
+                                 const double* h, const double* lambda, int leaf_m, int s_max,
+                                 double tol) {
+  if (!d_points) return fail(IASKIT_ERR_ARG, "points is null");
+  return factor_batched_impl(nprob, nullptr, d_points, N, d, h, lambda, leaf_m, s_max, tol, true);
+}
+
+int iaskit_num_problems(void) {
+  if (!S().factored) return fail(IASKIT_ERR_NOT_FACTORED, "no factorization");
+  return (int)S().pr.size();
 }
 
 int iaskit_solve_device(double* d_rhs, int nrhs) {
@@ -1043,17 +1244,38 @@ int iaskit_solve_device(double* d_rhs, int nrhs) {
   });
 }
 
+int iaskit_solve_batched_device(double* d_rhs, int nrhs) { return iaskit_solve_device(d_rhs, nrhs); }
+
 int iaskit_solve(double* rhs, int nrhs) {
   return guarded([&] {
     Solver& s = S();
     require_factored();
     if (!rhs) throw Error(IASKIT_ERR_ARG, "rhs is null");
     if (nrhs < 1) throw Error(IASKIT_ERR_ARG, "bad nrhs");
-    const size_t n = (size_t)s.N * nrhs;
+    const size_t n = (size_t)s.Ntot * nrhs;
     double* d = s.io.ensure_n<double>(n);
     h2d(d, rhs, n, s.st);
     s.solve_device(d, nrhs);
     d2h(rhs, d, n, s.st);
+    IA_CUDA(cudaStreamSynchronize(s.st));
+  });
+}
+
+int iaskit_solve_batched(double* const* rhs, int nrhs) {
+  return guarded([&] {
+    Solver& s = S();
+    require_factored();
+    if (!rhs) throw Error(IASKIT_ERR_ARG, "rhs is null");
+    if (nrhs < 1) throw Error(IASKIT_ERR_ARG, "bad nrhs");
+    const size_t n = (size_t)s.Ntot * nrhs;
+    double* d = s.io.ensure_n<double>(n);
+    for (size_t q = 0; q < s.pr.size(); ++q) {
+      if (!rhs[q]) throw Error(IASKIT_ERR_ARG, "rhs is null");
+      h2d(d + (size_t)s.pr[q].pbase * nrhs, rhs[q], (size_t)s.pr[q].N * nrhs, s.st);
+    }
+    s.solve_device(d, nrhs);
+    for (size_t q = 0; q < s.pr.size(); ++q)
+      d2h(rhs[q], d + (size_t)s.pr[q].pbase * nrhs, (size_t)s.pr[q].N * nrhs, s.st);
     IA_CUDA(cudaStreamSynchronize(s.st));
   });
 }
@@ -1071,7 +1293,7 @@ int iaskit_apply(const double* w, double* u, int nrhs) {
     require_factored();
     if (!w || !u) throw Error(IASKIT_ERR_ARG, "null pointer");
     if (nrhs < 1) throw Error(IASKIT_ERR_ARG, "bad nrhs");
-    const size_t n = (size_t)s.N * nrhs;
+    const size_t n = (size_t)s.Ntot * nrhs;
     double* dw = s.io.ensure_n<double>(2 * n);
     double* du = dw + n;
     h2d(dw, w, n, s.st);
@@ -1105,6 +1327,8 @@ int iaskit_set_option(const char* key, double value) {
       o.mem_cap_gb = value;
     } else if (k == "precision") {
       o.precision = as_int(0, 1);
+    } else if (k == "problem") {
+      o.problem = as_int(0, 1 << 30);
     } else if (k == "profile") {
       int v = as_int(0, 1);
       IA_CUDA(cudaStreamSynchronize(S().st));
@@ -1127,6 +1351,7 @@ int iaskit_get_option(const char* key, double* value) {
     else if (k == "mem_cap_gb") *value = o.mem_cap_gb;
     else if (k == "profile") *value = prof().enabled ? 1 : 0;
     else if (k == "precision") *value = o.precision;
+    else if (k == "problem") *value = o.problem;
     else throw Error(IASKIT_ERR_ARG, "unknown option " + k);
   });
 }
@@ -1139,16 +1364,16 @@ int iaskit_set_stream(void* cuda_stream) {
 int iaskit_stats(char* buf, size_t len) {
   Solver& s = S();
   std::string j = "{";
-  char tmp[512];
+  char tmp[640];
   snprintf(tmp, sizeof tmp,
-           "\"N\":%d,\"d\":%d,\"L\":%d,\"factored\":%s,\"ms\":{\"tree\":%.3f,\"knn\":%.3f,"
-           "\"skeletonize\":%.3f,\"leaf_lu\":%.3f,\"factor_levels\":%.3f,\"factor\":%.3f,"
-           "\"solve\":%.3f,\"apply\":%.3f},\"knn_fallback\":%d,\"bytes\":{\"W\":%lld,\"LU\":%lld,"
-           "\"P\":%lld,\"operator\":%lld},\"precision\":\"%s\",\"refine_sweeps\":%d,",
-           s.N, s.d, s.L, s.factored ? "true" : "false", s.stats.t_tree, s.stats.t_knn,
-           s.stats.t_skel, s.stats.t_leaf_lu, s.stats.t_factor_levels, s.stats.t_factor,
-           s.stats.t_solve, s.stats.t_apply, s.stats.knn_fallback, (long long)s.stats.bytes_W,
-           (long long)s.stats.bytes_LU, (long long)s.stats.bytes_P,
+           "\"N\":%d,\"d\":%d,\"problems\":%d,\"L\":%d,\"factored\":%s,\"ms\":{\"tree\":%.3f,"
+           "\"knn\":%.3f,\"skeletonize\":%.3f,\"leaf_lu\":%.3f,\"factor_levels\":%.3f,"
+           "\"factor\":%.3f,\"solve\":%.3f,\"apply\":%.3f},\"knn_fallback\":%d,\"bytes\":{\"W\":%lld,"
+           "\"LU\":%lld,\"P\":%lld,\"operator\":%lld},\"precision\":\"%s\",\"refine_sweeps\":%d,",
+           s.Ntot, s.d, (int)s.pr.size(), s.Hmax, s.factored ? "true" : "false", s.stats.t_tree,
+           s.stats.t_knn, s.stats.t_skel, s.stats.t_leaf_lu, s.stats.t_factor_levels,
+           s.stats.t_factor, s.stats.t_solve, s.stats.t_apply, s.stats.knn_fallback,
+           (long long)s.stats.bytes_W, (long long)s.stats.bytes_LU, (long long)s.stats.bytes_P,
            (long long)s.stats.bytes_operator, s.prec == PREC_MIXED ? "mixed" : "fp64",
            s.stats.refine_sweeps);
   j += tmp;
@@ -1165,11 +1390,16 @@ int iaskit_stats(char* buf, size_t len) {
              prof_name(k), prof().ms[k], prof().calls[k], prof().flops[k]);
     j += tmp;
   }
-  j += "},\"mean_rank_per_level\":[";
-  for (int l = 1; l <= s.L && s.factored; ++l) {
+  j += "},\"mean_rank_per_height\":[";
+  for (int hh = 0; hh < s.Hmax && s.factored; ++hh) {
     double tot = 0;
-    for (int i = 0; i < (1 << l); ++i) tot += s.nd[(1 << l) + i].s;
-    snprintf(tmp, sizeof tmp, "%s%.3f", l > 1 ? "," : "", tot / (1 << l));
+    int cnt = 0;
+    for (int g : s.by_height[hh])
+      if (!s.is_root(g)) {
+        tot += s.nd[g].s;
+        ++cnt;
+      }
+    snprintf(tmp, sizeof tmp, "%s%.3f", hh ? "," : "", cnt ? tot / cnt : 0.0);
     j += tmp;
   }
   j += "]}";
@@ -1187,15 +1417,19 @@ void iaskit_free(void) { S().release(); }
 
 int iaskit_depth(void) {
   if (!S().factored) return fail(IASKIT_ERR_NOT_FACTORED, "no factorization");
-  return S().L;
+  int L = 0;
+  const int rc = guarded([&] { L = selected_problem().L; });
+  return rc == IASKIT_OK ? L : rc;
 }
 
 int iaskit_get_perm(int32_t* out) {
   return guarded([&] {
     require_factored();
     Solver& s = S();
-    d2h(out, s.perm.as<int>(), s.N, s.st);
+    const Prob& P = selected_problem();
+    d2h(out, s.perm.as<int>() + P.pbase, P.N, s.st);
     IA_CUDA(cudaStreamSynchronize(s.st));
+    for (int i = 0; i < P.N; ++i) out[i] -= P.pbase;
   });
 }
 
@@ -1203,10 +1437,12 @@ int iaskit_get_knn(int32_t* out, int kappa_cap) {
   return guarded([&] {
     require_factored();
     Solver& s = S();
-    if (s.L == 0) throw Error(IASKIT_ERR_ARG, "no kNN lists for a single-leaf tree");
+    const Prob& P = selected_problem();
+    if (s.Hmax == 0) throw Error(IASKIT_ERR_ARG, "no kNN lists for single-leaf trees");
     if (kappa_cap < s.kappa) throw Error(IASKIT_ERR_ARG, "buffer too small");
-    d2h(out, s.knn.as<int>(), (size_t)s.N * s.kappa, s.st);
+    d2h(out, s.knn.as<int>() + (size_t)P.pbase * s.kappa, (size_t)P.N * s.kappa, s.st);
     IA_CUDA(cudaStreamSynchronize(s.st));
+    for (size_t i = 0; i < (size_t)P.N * s.kappa; ++i) out[i] -= P.pbase;
   });
 }
 
@@ -1214,8 +1450,9 @@ int iaskit_get_ranks(int32_t* out, int count) {
   return guarded([&] {
     require_factored();
     Solver& s = S();
-    if (count < (2 << s.L)) throw Error(IASKIT_ERR_ARG, "buffer too small");
-    for (int u = 0; u < (2 << s.L); ++u) out[u] = u == 0 ? 0 : s.nd[u].s;
+    const Prob& P = selected_problem();
+    if (count < (2 << P.L)) throw Error(IASKIT_ERR_ARG, "buffer too small");
+    for (int u = 0; u < (2 << P.L); ++u) out[u] = (u == 0 || u == 1) ? 0 : s.nd[P.nbase + u].s;
   });
 }
 
@@ -1224,11 +1461,13 @@ int iaskit_get_skeleton(int level, int index, int32_t* out, int cap) {
   int rc = guarded([&] {
     require_factored();
     Solver& s = S();
-    int u = check_node(level, index);
-    rs = s.nd[u].s;
+    const int g = check_node(level, index);
+    const Prob& P = selected_problem();
+    rs = s.nd[g].s;
     if (cap < rs) throw Error(IASKIT_ERR_ARG, "buffer too small");
-    d2h(out, s.skel.as<int>() + (size_t)u * s.s_max, rs, s.st);
+    d2h(out, s.skel.as<int>() + (size_t)g * s.s_max, rs, s.st);
     IA_CUDA(cudaStreamSynchronize(s.st));
+    for (int i = 0; i < rs; ++i) out[i] -= P.pbase;
   });
   return rc == IASKIT_OK ? rs : rc;
 }
@@ -1238,11 +1477,13 @@ int iaskit_get_samples(int level, int index, int32_t* out, int cap) {
   int rc = guarded([&] {
     require_factored();
     Solver& s = S();
-    int u = check_node(level, index);
-    ns = s.nd[u].nsamp;
+    const int g = check_node(level, index);
+    const Prob& P = selected_problem();
+    ns = s.nd[g].nsamp;
     if (cap < ns) throw Error(IASKIT_ERR_ARG, "buffer too small");
-    d2h(out, s.samp.as<int>() + s.nd[u].samp_off, ns, s.st);
+    d2h(out, s.samp.as<int>() + s.nd[g].samp_off, ns, s.st);
     IA_CUDA(cudaStreamSynchronize(s.st));
+    for (int i = 0; i < ns; ++i) out[i] -= P.pbase;
   });
   return rc == IASKIT_OK ? ns : rc;
 }
@@ -1252,11 +1493,11 @@ int iaskit_get_P(int level, int index, double* out, int64_t cap) {
   int rc = guarded([&] {
     require_factored();
     Solver& s = S();
-    int u = check_node(level, index);
-    nc = s.nd[u].ncols;
-    int64_t n = (int64_t)s.nd[u].s * nc;
+    const int g = check_node(level, index);
+    nc = s.nd[g].ncols;
+    int64_t n = (int64_t)s.nd[g].s * nc;
     if (cap < n) throw Error(IASKIT_ERR_ARG, "buffer too small");
-    d2h(out, s.Pl[level]->as<double>() + s.nd[u].P_off, n, s.st);
+    d2h(out, s.Pd.as<double>() + s.nd[g].P_off, n, s.st);
     IA_CUDA(cudaStreamSynchronize(s.st));
   });
   return rc == IASKIT_OK ? nc : rc;

@@ -10,6 +10,9 @@
 //   4. flag the first floor(n/2) ranks as "left", and stably partition every node's
 //      range by that flag (prefix sum of the flags), so both children keep their
 //      points in ascending original index.
+// Several independent problems are built together: a level's node list covers all
+// points; the nodes of a problem whose tree is already complete are passed through
+// unsplit (all their points flagged "left", so the partition leaves them in place).
 #include "kernels.cuh"
 #include "prims.cuh"
 
@@ -110,22 +113,22 @@ __global__ void node_keys_kernel(const uint32_t* vals, int N, const int* off, in
 }
 
 __global__ void left_flags_kernel(const uint64_t* node_keys, const uint32_t* vals, int N,
-                                  const int* off, int* flags) {
+                                  const int* off, const int* kleft, int* flags) {
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= N) return;
   int node = (int)node_keys[q];
-  int o = off[node], n = off[node + 1] - o;
-  flags[vals[q]] = (q - o) < n / 2 ? 1 : 0;
+  int o = off[node];
+  flags[vals[q]] = (q - o) < kleft[node] ? 1 : 0;
 }
 
 __global__ void partition_kernel(const int* perm, const int* flags, const int* pre, int N,
-                                 const int* off, int nnodes, int* perm_out) {
+                                 const int* off, const int* kleft, int nnodes, int* perm_out) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= N) return;
   int node = node_of(off, nnodes, p);
-  int o = off[node], n = off[node + 1] - o;
+  int o = off[node];
   int nl = pre[p] - pre[o];  // left-flagged positions in [o, p)
-  int dest = flags[p] ? o + nl : o + n / 2 + (p - o - nl);
+  int dest = flags[p] ? o + nl : o + kleft[node] + (p - o - nl);
   perm_out[dest] = perm[p];
 }
 
@@ -155,53 +158,58 @@ int bit_length(uint64_t v) {
 
 }  // namespace
 
-void build_tree(const double* X, int N, int d, int L, const std::vector<std::vector<int>>& level_off,
-                int* perm, int* split_dim, TreeScratch& s, cudaStream_t st) {
+void build_tree(const double* X, int N, int d, const std::vector<TreeLevel>& levels, int* perm,
+                TreeScratch& s, cudaStream_t st) {
   ProfScope _ps(PK_TREE, st);
   const int T = 256;
   iota_kernel<<<ceil_div(N, T), T, 0, st>>>(perm, N);
   IA_LAUNCH_CHECK();
-  if (L == 0) return;
+  if (levels.empty()) return;
   uint64_t* keys = s.keys.ensure_n<uint64_t>(N);
   uint32_t* vals = s.vals.ensure_n<uint32_t>(N);
   int* flags = s.flags.ensure_n<int>(N);
   int* pre = s.pre.ensure_n<int>(N);
   int* perm2 = s.perm2.ensure_n<int>(N);
-  const int max_nodes = 1 << (L - 1);
+  size_t max_nodes = 1;
+  for (const TreeLevel& lv : levels) max_nodes = std::max(max_nodes, lv.kleft.size());
   uint64_t* mm = s.minmax.ensure_n<uint64_t>((size_t)2 * max_nodes * d);
-  int* offs = s.offs.ensure_n<int>((size_t)max_nodes + 1 + 3 * ((size_t)N / 64 + 2 * max_nodes + 8));
-  for (int l = 0; l < L; ++l) {
-    const int nn = 1 << l;
-    const std::vector<int>& off = level_off[l];
-    // chunk list: node-aligned ranges of at most MM_ROWS_PER_BLOCK positions
+  int* dims = s.dims.ensure_n<int>(max_nodes);
+  for (const TreeLevel& lv : levels) {
+    const int nn = (int)lv.kleft.size();
+    const std::vector<int>& off = lv.off;
+    // chunk list: ranges of at most MM_ROWS_PER_BLOCK positions of the split nodes
     std::vector<int> cn, cs, ce;
-    for (int i = 0; i < nn; ++i)
+    for (int i = 0; i < nn; ++i) {
+      if (!lv.split[i]) continue;
       for (int a = off[i]; a < off[i + 1]; a += MM_ROWS_PER_BLOCK) {
         cn.push_back(i);
         cs.push_back(a);
         ce.push_back(std::min(off[i + 1], a + MM_ROWS_PER_BLOCK));
       }
+    }
     const int nch = (int)cn.size();
-    std::vector<int> host(nn + 1 + 3 * (size_t)nch);
+    std::vector<int> host(2 * (size_t)nn + 1 + 3 * (size_t)nch);
     std::copy(off.begin(), off.end(), host.begin());
-    std::copy(cn.begin(), cn.end(), host.begin() + nn + 1);
-    std::copy(cs.begin(), cs.end(), host.begin() + nn + 1 + nch);
-    std::copy(ce.begin(), ce.end(), host.begin() + nn + 1 + 2 * nch);
+    std::copy(lv.kleft.begin(), lv.kleft.end(), host.begin() + nn + 1);
+    std::copy(cn.begin(), cn.end(), host.begin() + 2 * nn + 1);
+    std::copy(cs.begin(), cs.end(), host.begin() + 2 * nn + 1 + nch);
+    std::copy(ce.begin(), ce.end(), host.begin() + 2 * nn + 1 + 2 * nch);
     int* dev = s.offs.ensure_n<int>(host.size());
-    offs = dev;
     h2d(dev, host.data(), host.size(), st);
     const int* doff = dev;
-    const int* dcn = dev + nn + 1;
+    const int* dkl = dev + nn + 1;
+    const int* dcn = dkl + nn;
     const int* dcs = dcn + nch;
     const int* dce = dcs + nch;
     uint64_t* nmin = mm;
     uint64_t* nmax = mm + (size_t)nn * d;
     init_minmax_kernel<<<ceil_div((size_t)nn * d, T), T, 0, st>>>(nmin, nmax, nn * d);
     IA_LAUNCH_CHECK();
-    minmax_kernel<<<nch, MM_WARPS * 32, 2 * MM_WARPS * d * sizeof(uint64_t), st>>>(
-        X, perm, d, dcn, dcs, dce, nmin, nmax);
-    IA_LAUNCH_CHECK();
-    int* dims = split_dim + (nn - 1);
+    if (nch > 0) {
+      minmax_kernel<<<nch, MM_WARPS * 32, 2 * MM_WARPS * d * sizeof(uint64_t), st>>>(
+          X, perm, d, dcn, dcs, dce, nmin, nmax);
+      IA_LAUNCH_CHECK();
+    }
     choose_dim_kernel<<<ceil_div(nn, T), T, 0, st>>>(nmin, nmax, nn, d, dims);
     IA_LAUNCH_CHECK();
     coord_keys_kernel<<<ceil_div(N, T), T, 0, st>>>(X, perm, N, d, doff, nn, dims, keys, vals);
@@ -215,16 +223,15 @@ void build_tree(const double* X, int N, int d, int L, const std::vector<std::vec
     } else {
       IA_CUDA(cudaMemsetAsync(keys, 0, (size_t)N * sizeof(uint64_t), st));
     }
-    left_flags_kernel<<<ceil_div(N, T), T, 0, st>>>(keys, vals, N, doff, flags);
+    left_flags_kernel<<<ceil_div(N, T), T, 0, st>>>(keys, vals, N, doff, dkl, flags);
     IA_LAUNCH_CHECK();
     exclusive_scan_i32(flags, pre, N, s.scan_tmp, st);
-    partition_kernel<<<ceil_div(N, T), T, 0, st>>>(perm, flags, pre, N, doff, nn, perm2);
+    partition_kernel<<<ceil_div(N, T), T, 0, st>>>(perm, flags, pre, N, doff, dkl, nn, perm2);
     IA_LAUNCH_CHECK();
     IA_CUDA(cudaMemcpyAsync(perm, perm2, (size_t)N * sizeof(int), cudaMemcpyDeviceToDevice, st));
     // the host vectors above are consumed by the copies before they go out of scope
     IA_CUDA(cudaStreamSynchronize(st));
   }
-  (void)offs;
 }
 
 void permute_points(const double* X, const int* perm, int N, int d, int* iperm, double* Xp,
