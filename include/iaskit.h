@@ -96,10 +96,17 @@ int iaskit_num_problems(void);
  * Solve (lambda*I + K~) w = u in place (Sec. II-C, Alg. "Solve").
  *   rhs      HOST pointer, N x nrhs column-major, original point order; on return
  *            it holds w.  nrhs >= 1.
- * With the option "refine" > 0 the solve iterates w += Solve(u - (lambda I + K~) w)
- * with the FP64 hierarchical operator until ||r||/||u|| <= "refine_tol" for every
- * column or "refine" sweeps were spent (then IASKIT_ERR_NOT_CONVERGED, w holds the
- * last iterate).
+ * With refinement on (option "refine" > 0, or the mixed precision), the solve refines
+ * against the FP64 hierarchical operator: residuals r = u - (lambda I + K~) w in FP64,
+ * corrections from restarted flexible GMRES on A z = r right-preconditioned by the
+ * stored factorization M^-1, w += Z y with Z the kept vectors M^-1 v_j (FGMRES-IR).
+ * A column is done when ||r||/||u|| <= "refine_tol", or when a cycle whose GMRES
+ * estimate met 0.1 "refine_tol" lowered the recomputed residual by less than half:
+ * the FP64 rounding floor of the residual (about 1e-16 ||A|| ||w|| / ||u||) is then
+ * above the target; iaskit_stats reports such columns as "refine_stagnated" and the
+ * last residuals in "refine_history".
+ * "refine" bounds the total GMRES iterations; when they are spent with a column still
+ * open the call returns IASKIT_ERR_NOT_CONVERGED and w holds the last iterate.
  * Errors: IASKIT_ERR_NOT_FACTORED, _ARG, _INPUT, _NOT_CONVERGED, _NOMEM, _CUDA.
  */
 int iaskit_solve(double* rhs, int nrhs);
@@ -134,14 +141,19 @@ int iaskit_apply_device(const double* d_w, double* d_u, int nrhs);
  *   "kappa"        neighbours per point for sampling (default 16)
  *   "samp_factor"  sampled rows per node = samp_factor * s_max, capped at N - |node| (2)
  *   "seed"         seed of the uniform-fill random stream (0)
- *   "refine"       max refinement sweeps in iaskit_solve* (0 = plain solve) [any time]
+ *   "refine"       max GMRES-IR iterations in iaskit_solve* (0 = plain solve in FP64,
+ *                  200 in the mixed precision) [any time]
  *   "refine_tol"   relative residual target of refinement (1e-10) [any time]
  *   "mem_cap_gb"   refuse factorizations whose device footprint exceeds this (0 = none)
  *   "profile"      1: time every kernel class with CUDA events (reported by iaskit_stats)
  *                  and reset the counters; 0: stop timing [any time]
  *   "precision"    0: plain FP64 (default); 1: mixed - FP32 factorization with FP64 pivot
- *                  norms, FP64 operator, solves refined to "refine_tol" (up to 50 sweeps
- *                  when "refine" is 0)
+ *                  comparisons, FP64 operator, solves refined to "refine_tol".  In the
+ *                  mixed precision a problem whose estimated condition number
+ *                  1 + max_i sum_j K(x_i, x_j) / lambda (64 sampled rows i) exceeds
+ *                  "mixed_cond_max" is factored in FP64 instead
+ *   "mixed_cond_max" condition estimate above which the mixed precision factors a
+ *                  problem in FP64 (1e6, >= 1)
  *   "problem"      which problem of a batch the introspection calls report (0) [any time]
  * Errors: IASKIT_ERR_ARG for an unknown key or an invalid value.
  */
@@ -153,7 +165,9 @@ int iaskit_set_stream(void* cuda_stream);
 
 /*
  * JSON with timings per phase (ms), the rank profile, algorithmic flop and byte
- * counts and the last refinement history.  Writes at most len bytes including the
+ * counts, the last refinement history (worst relative residual after each cycle), GMRES
+ * iterations, columns stopped at the rounding floor, each problem's condition estimate
+ * and how many problems were factored in FP64.  Writes at most len bytes including the
  * terminating NUL; returns the full length needed (>= 0) or a negative error.
  */
 int iaskit_stats(char* json_buf, size_t len);

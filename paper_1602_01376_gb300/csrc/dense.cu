@@ -822,6 +822,46 @@ void kernel_matvec(const double* Xp, int d, int nrhs, const KMatvecDesc* descs_d
   IA_LAUNCH_CHECK();
 }
 
+__global__ void __launch_bounds__(256) kernel_rowsums_kernel(const double* Xp, int d,
+                                                              const RowSumDesc* descs, double* out) {
+  extern __shared__ double xi[];
+  __shared__ double part[8];
+  const RowSumDesc D = descs[blockIdx.y];
+  const int i = D.pbase + (int)(((int64_t)blockIdx.x * D.N) / KROWSUM_ROWS);
+  for (int q = threadIdx.x; q < d; q += blockDim.x) xi[q] = Xp[(size_t)i * d + q];
+  __syncthreads();
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < D.N; j += blockDim.x) {
+    const double* xj = Xp + (size_t)(D.pbase + j) * d;
+    double d2 = 0.0;
+    for (int q = 0; q < d; ++q) {
+      const double t = xi[q] - xj[q];
+      d2 = fma(t, t, d2);
+    }
+    acc += exp(d2 * D.scale);
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += part[w];
+    out[(size_t)blockIdx.y * KROWSUM_ROWS + blockIdx.x] = s;
+  }
+}
+
+void kernel_rowsums(const double* Xp, int d, const RowSumDesc* descs_dev, int nprob, double* out,
+                    cudaStream_t st) {
+  if (nprob <= 0) return;
+  const size_t smem = (size_t)d * sizeof(double);
+  if (smem > 48 * 1024)
+    IA_CUDA(cudaFuncSetAttribute(kernel_rowsums_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  ProfScope _ps(PK_MISC, st);
+  kernel_rowsums_kernel<<<dim3(KROWSUM_ROWS, nprob), 256, smem, st>>>(Xp, d, descs_dev, out);
+  IA_LAUNCH_CHECK();
+}
+
 void check_finite(const double* x, int64_t n, int* dev_status, cudaStream_t st) {
   if (n <= 0) return;
   ProfScope _ps(PK_MISC, st);

@@ -244,6 +244,17 @@ struct KMatvecDesc {
 void kernel_matvec(const double* Xp, int d, int nrhs, const KMatvecDesc* descs_dev, int ndesc,
                    int max_rows, cudaStream_t st);
 
+// Conditioning probe: out[q * KROWSUM_ROWS + r] = sum_j K(x_i, x_j) over the N points of
+// problem q, for KROWSUM_ROWS rows i spread evenly over the problem's tree order.  The
+// largest of them bounds ||K||_2 from below for a near-constant kernel and estimates it.
+constexpr int KROWSUM_ROWS = 64;
+struct RowSumDesc {
+  int pbase, N;
+  double scale;  // -1 / (2 h^2)
+};
+void kernel_rowsums(const double* Xp, int d, const RowSumDesc* descs_dev, int nprob, double* out,
+                    cudaStream_t st);
+
 // Any entry non-finite -> atomicOr(status, DEV_BADINPUT).
 void check_finite(const double* x, int64_t n, int* dev_status, cudaStream_t st);
 

@@ -77,6 +77,8 @@ struct Options {
   double mem_cap_gb = 0.0;
   int precision = PREC_FP64;
   int problem = 0;  // problem the introspection calls refer to
+  // mixed form: problems whose estimated condition number exceeds this are factored in FP64
+  double mixed_cond_max = 1e6;
 };
 
 struct Prob {
@@ -84,6 +86,8 @@ struct Prob {
   double h = 0, lam = 0, scale = 0;  // scale = -1 / (2 h^2)
   int pbase = 0;                     // first global position (and original index)
   int nbase = 0;                     // global id of heap id 0: gid = nbase + uid
+  double cond_est = 0;               // 1 + max sampled kernel row sum / lambda
+  bool f64 = true;                   // factorization stored in FP64 (else FP32)
 };
 
 struct Node {
@@ -93,8 +97,10 @@ struct Node {
   int ncols = 0;          // ID columns: size (leaf) or s_l + s_r
   int nsamp = 0;
   int leaf = -1;          // global leaf index (leaves only)
+  // offsets into the typed factorization buffers of the node's problem precision (LU, W,
+  // Z, C) and into the FP64 operator blocks kept by the mixed form (K: leaf, U)
   int64_t samp_off = 0, P_off = 0, W_off = 0, LU_off = 0, Z_off = 0, Zpiv_off = 0, CL_off = 0,
-          CR_off = 0;
+          CR_off = 0, K_off = 0, U_off = 0;
 };
 
 struct Stats {
@@ -104,6 +110,9 @@ struct Stats {
   int64_t bytes_W = 0, bytes_LU = 0, bytes_P = 0, bytes_operator = 0;
   std::vector<double> refine_hist;
   int refine_sweeps = 0;
+  int refine_iters = 0;       // GMRES iterations (operator applications) of the last solve
+  int refine_stagnated = 0;   // columns stopped at the rounding floor of the FP64 operator
+  int fp64_problems = 0;      // problems factored in FP64
 };
 
 template <typename T>
@@ -188,10 +197,6 @@ __global__ void axpby_kernel(const double* u, double* r, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     r[i] = u[i] - r[i];
 }
-__global__ void add_kernel(double* w, const double* dl, size_t n) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    w[i] += dl[i];
-}
 // One block per (column, problem): the 2-norm of that column of that problem's block.
 __global__ void colnorm_kernel(const double* x, const BlockDesc* blocks, int nrhs, double* out) {
   __shared__ double red[32];
@@ -208,6 +213,60 @@ __global__ void colnorm_kernel(const double* x, const BlockDesc* blocks, int nrh
     s = warp_sum(s);
     if (threadIdx.x == 0) out[(size_t)q * nrhs + c] = sqrt(s);
   }
+}
+
+// One GMRES segment: a column of one problem's block, [base, base + len).
+struct GSeg {
+  int64_t base;
+  int len;
+};
+
+__global__ void seg_dots_kernel(const double* V, size_t vstride, const double* x, const GSeg* segs,
+                                int S, double* out) {
+  __shared__ double red[32];
+  const int i = blockIdx.x, q = blockIdx.y;
+  const GSeg sg = segs[q];
+  const double* v = V + (size_t)i * vstride + sg.base;
+  const double* y = x + sg.base;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < sg.len; e += blockDim.x) acc = fma(v[e], y[e], acc);
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    acc = warp_sum(acc);
+    if (threadIdx.x == 0) out[(size_t)i * S + q] = acc;
+  }
+}
+__global__ void seg_axpy_kernel(double* x, const double* V, size_t vstride, int k, const double* coef,
+                                double sign, const GSeg* segs, int S) {
+  const int q = blockIdx.y;
+  const GSeg sg = segs[q];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < sg.len; e += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < k; ++i) acc = fma(coef[(size_t)i * S + q], V[(size_t)i * vstride + sg.base + e], acc);
+    x[sg.base + e] += sign * acc;
+  }
+}
+__global__ void seg_scale_kernel(double* out, const double* x, const double* coef, const GSeg* segs) {
+  const int q = blockIdx.y;
+  const GSeg sg = segs[q];
+  const double a = coef[q];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < sg.len; e += gridDim.x * blockDim.x)
+    out[sg.base + e] = a * x[sg.base + e];
+}
+
+// Copy with type conversion of element ranges: dst[dst + e] = src[src + e], e < len.
+struct ConvSeg {
+  int64_t src, dst, len;
+};
+template <typename S, typename D>
+__global__ void conv_segs_kernel(const S* __restrict__ src, D* __restrict__ dst, const ConvSeg* segs) {
+  const ConvSeg sg = segs[blockIdx.y];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < sg.len;
+       e += (int64_t)gridDim.x * blockDim.x)
+    dst[sg.dst + e] = (D)src[sg.src + e];
 }
 
 unsigned grid_cap(int64_t work, unsigned cap) {
@@ -228,7 +287,8 @@ class Solver {
   std::vector<Node> nd;                       // global ids; unused slot at each nbase
   std::vector<std::vector<int>> by_height;    // gids of each height (0 = leaves), roots included
   DevBuf X, Xp, perm, iperm, pid, knn, knn_pos, samp, ranks, skel, piv_ws, A_ws, status,
-      arena_dev, step_dev, tbuf, vbuf, vbuf32, ubuf, rbuf, wt, io, normbuf, blocks_dev;
+      arena_dev, step_dev, tbuf, vbuf, vbuf32, ubuf, rbuf, wt, io, normbuf, blocks_dev, gseg_dev,
+      kryl, kzb, coefbuf, cseg_dev, rowsum;
   // factorization storage: FP64 (plain) and FP32 (mixed)
   DevBuf LU, LUpiv, Wb, Zb, Zpiv, Cb, LU32, Wb32, Zb32, Cb32, tbuf32;
   // FP64 operator blocks kept by the mixed form: leaf blocks lambda I + K_aa and U blocks
@@ -309,6 +369,23 @@ class Solver {
     BlockDesc* dv = blocks_dev.ensure_n<BlockDesc>(b.size());
     h2d(dv, b.data(), b.size(), st);
     return dv;
+  }
+  template <typename Src, typename Dst>
+  void conv_segs(const Src* src, Dst* dst, const std::vector<ConvSeg>& segs) {
+    int64_t mx = 0;
+    for (const ConvSeg& c : segs) mx = std::max(mx, c.len);
+    if (mx == 0) return;
+    ConvSeg* dv = cseg_dev.ensure_n<ConvSeg>(segs.size());
+    h2d(dv, segs.data(), segs.size(), st);
+    ProfScope _ps(PK_MISC, st);
+    conv_segs_kernel<Src, Dst><<<dim3(grid_cap(mx, 1024), (unsigned)segs.size()), 256, 0, st>>>(src, dst, dv);
+    IA_LAUNCH_CHECK();
+  }
+  bool f64(int g) const { return pr[nd[g].prob].f64; }
+  bool any_prec(bool want_f64) const {
+    for (const Prob& P : pr)
+      if (P.f64 == want_f64) return true;
+    return false;
   }
   void gather(const double* in, double* out, int nrhs, const BlockDesc* blocks, bool scatter) {
     ProfScope _ps(PK_MISC, st);
@@ -584,7 +661,7 @@ class Solver {
     int* pm = perm.ensure_n<int>(Ntot);
     build_tree(Xd, Ntot, d, levels, pm, tree_s, st);
     permute_points(Xd, pm, Ntot, d, iperm.ensure_n<int>(Ntot), Xp.ensure_n<double>((size_t)Ntot * d), st);
-    IA_CUDA(cudaStreamSynchronize(st));
+    choose_precisions();
     const double t1 = now_ms();
     stats.t_tree = t1 - t0;
 
@@ -607,13 +684,39 @@ class Solver {
     raise_status(read_status_and_clear());
     const double t4 = now_ms();
     stats.t_leaf_lu = t4 - t3;
-    if (prec == PREC_MIXED) factor_levels<float>();
-    else factor_levels<double>();
+    factor_levels();
     raise_status(read_status_and_clear());
     stats.t_factor_levels = now_ms() - t4;
     stats.t_factor = now_ms() - t0;
     prof().resolve();
     factored = true;
+  }
+
+  // Per problem: cond_est = 1 + r / lambda with r the largest of KROWSUM_ROWS sampled kernel
+  // row sums (an estimate of ||K||_2 and of the largest eigenvalue of lambda I + K, whose
+  // smallest is about lambda).  The plain form factors every problem in FP64; the mixed
+  // form factors a problem in FP32 only while cond_est <= mixed_cond_max, so that the
+  // FP32 factorization keeps a few correct digits and refinement converges quickly.
+  void choose_precisions() {
+    std::vector<RowSumDesc> rd(pr.size());
+    for (size_t q = 0; q < pr.size(); ++q) rd[q] = RowSumDesc{pr[q].pbase, pr[q].N, pr[q].scale};
+    arena.clear();
+    size_t o = arena.push(rd);
+    char* base = upload_arena();
+    double* rs = rowsum.ensure_n<double>(pr.size() * KROWSUM_ROWS);
+    kernel_rowsums(Xp.as<double>(), d, (const RowSumDesc*)(base + o), (int)pr.size(), rs, st);
+    std::vector<double> hrs(pr.size() * KROWSUM_ROWS);
+    d2h(hrs.data(), rs, hrs.size(), st);
+    IA_CUDA(cudaStreamSynchronize(st));
+    stats.fp64_problems = 0;
+    for (size_t q = 0; q < pr.size(); ++q) {
+      double mx = 0.0;
+      for (int r = 0; r < KROWSUM_ROWS; ++r) mx = std::max(mx, hrs[q * KROWSUM_ROWS + r]);
+      Prob& P = pr[q];
+      P.cond_est = P.lam > 0.0 ? 1.0 + mx / P.lam : HUGE_VAL;
+      P.f64 = prec != PREC_MIXED || !(P.cond_est <= opt.mixed_cond_max);
+      stats.fp64_problems += P.f64 ? 1 : 0;
+    }
   }
 
   // a3 + a4 + a5: skeletons, heights 0 .. Hmax-1 (roots excluded); TS is the
@@ -777,16 +880,20 @@ class Solver {
     if (prec == PREC_MIXED && p_total > 0) convert_d2f(Pd.as<double>(), Pf.ensure_n<float>(p_total), p_total, st);
   }
 
-  // a4 + a6: leaf LU of lambda I + K_aa.  Mixed: the FP64 blocks are kept for the
-  // operator and their FP32 rounding is factored.
+  // a4 + a6: leaf LU of lambda I + K_aa, in each problem's precision.  The mixed form
+  // keeps the FP64 blocks for the operator (Kleaf) and factors a copy: rounded to FP32,
+  // or in FP64 for the problems it factors in FP64.
   void leaf_lu() {
-    int64_t tot = 0;
+    const bool mixed = prec == PREC_MIXED;
+    int64_t tot = 0, tot_t[2] = {0, 0};
     for (int g : by_height[0]) {
       Node& n = nd[g];
-      n.LU_off = tot;
-      tot += (int64_t)n.size * n.size;
+      const int64_t e = (int64_t)n.size * n.size;
+      n.K_off = tot;
+      tot += e;
+      n.LU_off = tot_t[f64(g)];
+      tot_t[f64(g)] += e;
     }
-    const bool mixed = prec == PREC_MIXED;
     double* blocks = mixed ? Kleaf.ensure_n<double>(tot) : LU.ensure_n<double>(tot);
     int* lp = LUpiv.ensure_n<int>((size_t)nleaves * m_max);
     std::vector<KDesc> kd;
@@ -797,7 +904,7 @@ class Solver {
       k.nrows = n.size;
       k.col0 = n.off;
       k.ncols = n.size;
-      k.out = blocks + n.LU_off;
+      k.out = blocks + n.K_off;
       k.ld = n.size;
       k.diag = pr[n.prob].lam;
       k.scale = scale_of(g);
@@ -808,80 +915,100 @@ class Solver {
     size_t ok = arena.push(kd);
     char* base = upload_arena();
     kernel_blocks<double>(Xp.as<double>(), d, (const KDesc*)(base + ok), nl, (int64_t)m_max * m_max, st);
+    float* lu32 = tot_t[0] ? LU32.ensure_n<float>(tot_t[0]) : nullptr;
+    double* lu64 = blocks;
     if (mixed) {
-      float* lu = LU32.ensure_n<float>(tot);
-      convert_d2f(blocks, lu, tot, st);
-      std::vector<LuDescT<float>> ld;
-      for (int g : by_height[0]) {
-        const Node& n = nd[g];
-        ld.push_back(LuDescT<float>{lu + n.LU_off, lp + (int64_t)n.leaf * m_max, n.size, n.size});
+      // one range per problem: its leaves are consecutive in both layouts
+      std::vector<ConvSeg> s32, s64;
+      for (const Prob& P : pr) {
+        const int first = P.nbase + (1 << P.L), nlv = 1 << P.L;
+        const Node& a = nd[first];
+        const Node& b = nd[first + nlv - 1];
+        const int64_t len = b.K_off + (int64_t)b.size * b.size - a.K_off;
+        (P.f64 ? s64 : s32).push_back(ConvSeg{a.K_off, a.LU_off, len});
       }
-      arena.clear();
-      size_t ol = arena.push(ld);
-      base = upload_arena();
-      prof().flops[PK_GETRF32] += getrf_flops(ld);
-      getrf_batched<float>((const LuDescT<float>*)(base + ol), nl, m_max, status.as<int>(), st);
+      if (tot_t[1]) {
+        lu64 = LU.ensure_n<double>(tot_t[1]);
+        conv_segs<double, double>(blocks, lu64, s64);
+      }
+      conv_segs<double, float>(blocks, lu32, s32);
       stats.bytes_operator += tot * 8;
-      stats.bytes_LU = tot * 4;
-    } else {
-      std::vector<LuDesc> ld;
-      for (int g : by_height[0]) {
-        const Node& n = nd[g];
-        ld.push_back(LuDesc{blocks + n.LU_off, lp + (int64_t)n.leaf * m_max, n.size, n.size});
-      }
-      arena.clear();
-      size_t ol = arena.push(ld);
-      base = upload_arena();
-      prof().flops[PK_GETRF] += getrf_flops(ld);
-      getrf_batched<double>((const LuDesc*)(base + ol), nl, m_max, status.as<int>(), st);
-      stats.bytes_LU = tot * 8;
+    }
+    stats.bytes_LU = tot_t[0] * 4 + tot_t[1] * 8;
+    std::vector<LuDescT<float>> l32;
+    std::vector<LuDesc> l64;
+    for (int g : by_height[0]) {
+      const Node& n = nd[g];
+      int* piv = lp + (int64_t)n.leaf * m_max;
+      if (f64(g)) l64.push_back(LuDesc{lu64 + n.LU_off, piv, n.size, n.size});
+      else l32.push_back(LuDescT<float>{lu32 + n.LU_off, piv, n.size, n.size});
+    }
+    arena.clear();
+    size_t o32 = arena.push(l32), o64 = arena.push(l64);
+    base = upload_arena();
+    if (!l32.empty()) {
+      prof().flops[PK_GETRF32] += getrf_flops(l32);
+      getrf_batched<float>((const LuDescT<float>*)(base + o32), (int)l32.size(), m_max, status.as<int>(), st);
+    }
+    if (!l64.empty()) {
+      prof().flops[PK_GETRF] += getrf_flops(l64);
+      getrf_batched<double>((const LuDesc*)(base + o64), (int)l64.size(), m_max, status.as<int>(), st);
     }
   }
 
-  // a7 + a8: W and Z, heights 1 .. Hmax, factorization stored in precision T
-  template <typename T>
+  // a7 + a8: W and Z, heights 1 .. Hmax, each problem's factorization in its own
+  // precision.  The U blocks K_{c s~} are evaluated in FP64 for every child c of the
+  // height; the mixed form keeps them (Ustore) for the operator and solves a copy.
   void factor_levels() {
     if (Hmax == 0) return;
-    const bool mixed = std::is_same<T, float>::value;
-    int64_t wsz = 0, zsz = 0, zp = 0, csz = 0;
+    const bool mixed = prec == PREC_MIXED;
+    int64_t wsz[2] = {0, 0}, zsz[2] = {0, 0}, csz[2] = {0, 0}, usz = 0, zp = 0;
     for (int hh = 0; hh < Hmax; ++hh)
       for (int g : by_height[hh]) {
         if (is_root(g)) continue;
         Node& n = nd[g];
-        n.W_off = wsz;
-        wsz += (int64_t)n.size * nd[sibling(g)].s;
+        const int64_t e = (int64_t)n.size * nd[sibling(g)].s;
+        n.U_off = usz;
+        usz += e;
+        n.W_off = wsz[f64(g)];
+        wsz[f64(g)] += e;
       }
     for (int hh = 1; hh <= Hmax; ++hh)
       for (int g : by_height[hh]) {
         Node& n = nd[g];
+        const int t = f64(g);
         const int sa = nd[left(g)].s, sb = nd[right(g)].s;
-        n.Z_off = zsz;
-        zsz += (int64_t)(sa + sb) * (sa + sb);
+        n.Z_off = zsz[t];
+        zsz[t] += (int64_t)(sa + sb) * (sa + sb);
         n.Zpiv_off = zp;
         zp += sa + sb;
-        n.CL_off = csz;
-        csz += (int64_t)sa * sb;
-        n.CR_off = csz;
-        csz += (int64_t)sb * sa;
+        n.CL_off = csz[t];
+        csz[t] += (int64_t)sa * sb;
+        n.CR_off = csz[t];
+        csz[t] += (int64_t)sb * sa;
       }
-    const double bytes = (double)(wsz + zsz + csz) * sizeof(T) + (mixed ? (double)wsz * 8 : 0.0);
+    const double bytes = (double)(wsz[0] + zsz[0] + csz[0]) * 4 + (double)(wsz[1] + zsz[1] + csz[1]) * 8 +
+                         (mixed ? (double)usz * 8 : 0.0);
     if (opt.mem_cap_gb > 0 && bytes > opt.mem_cap_gb * 1e9)
       throw Error(IASKIT_ERR_NOMEM, "factorization exceeds mem_cap_gb");
-    T* W = (mixed ? Wb32 : Wb).template ensure_n<T>(std::max<int64_t>(wsz, 1));
-    double* U64 = mixed ? Ustore.ensure_n<double>(std::max<int64_t>(wsz, 1)) : (double*)W;
-    (mixed ? Zb32 : Zb).template ensure_n<T>(std::max<int64_t>(zsz, 1));
+    if (wsz[0]) Wb32.ensure_n<float>(wsz[0]);
+    if (zsz[0]) Zb32.ensure_n<float>(zsz[0]);
+    if (csz[0]) Cb32.ensure_n<float>(csz[0]);
+    if (wsz[1]) Wb.ensure_n<double>(wsz[1]);
+    if (zsz[1]) Zb.ensure_n<double>(zsz[1]);
+    if (csz[1]) Cb.ensure_n<double>(csz[1]);
     Zpiv.ensure_n<int>(std::max<int64_t>(zp, 1));
-    (mixed ? Cb32 : Cb).template ensure_n<T>(std::max<int64_t>(csz, 1));
-    stats.bytes_W = wsz * (int64_t)sizeof(T);
-    if (mixed) stats.bytes_operator += wsz * 8;
+    // the plain form evaluates U straight into W (same layout: every problem is FP64)
+    double* U64 = mixed ? Ustore.ensure_n<double>(std::max<int64_t>(usz, 1))
+                        : Wb.ensure_n<double>(std::max<int64_t>(wsz[1], 1));
+    stats.bytes_W = wsz[0] * 4 + wsz[1] * 8;
+    if (mixed) stats.bytes_operator += usz * 8;
     int* sk = skel.as<int>();
-    T* C = cP<T>();
     for (int hh = 1; hh <= Hmax; ++hh) {
       const std::vector<int>& nodes = by_height[hh];
-      // U blocks of the children of every node of this height (FP64)
       std::vector<KDesc> kd;
-      int64_t max_e = 0, lo = INT64_MAX, hi = 0;
-      std::vector<RootBlock<T>> rb;
+      int64_t max_e = 0;
+      std::vector<ConvSeg> s32, s64;
       for (int g : nodes)
         for (int c : {left(g), right(g)}) {
           const Node& n = nd[c];
@@ -892,44 +1019,72 @@ class Solver {
           k.colsA = sk + (size_t)sib * s_max;
           k.nA = nd[sib].s;
           k.ncols = nd[sib].s;
-          k.out = U64 + n.W_off;
+          k.out = U64 + n.U_off;
           k.ld = n.size;
           k.diag = 0.0;
           k.scale = scale_of(c);
           kd.push_back(k);
-          max_e = std::max<int64_t>(max_e, (int64_t)n.size * k.ncols);
-          lo = std::min<int64_t>(lo, n.W_off);
-          hi = std::max<int64_t>(hi, n.W_off + (int64_t)n.size * k.ncols);
-          // left child: C_l = P_l W_{l r~} (s_l x s_r); right child: C_r = P_r W_{r l~}
-          T* tout = C + ((n.uid & 1) == 0 ? nd[g].CL_off : nd[g].CR_off);
-          rb.push_back(RootBlock<T>{c, W + n.W_off, n.size, nd[sib].s, tout, n.s});
+          const int64_t e = (int64_t)n.size * k.ncols;
+          max_e = std::max<int64_t>(max_e, e);
+          // consecutive children of one precision extend the previous range
+          std::vector<ConvSeg>& sv = f64(c) ? s64 : s32;
+          if (!sv.empty() && sv.back().src + sv.back().len == n.U_off &&
+              sv.back().dst + sv.back().len == n.W_off)
+            sv.back().len += e;
+          else
+            sv.push_back(ConvSeg{n.U_off, n.W_off, e});
         }
       arena.clear();
       size_t ok = arena.push(kd);
       char* base = upload_arena();
       kernel_blocks<double>(Xp.as<double>(), d, (const KDesc*)(base + ok), (int)kd.size(), max_e, st);
-      if (mixed && hi > lo) convert_d2f(U64 + lo, (float*)W + lo, hi - lo, st);
-      // W = Solve(child, U) for all children at once; C blocks come back as P_c W_c
-      forest_solve<T>(rb);
-      // reduced systems Z'' = [[I, C_l], [C_r, I]] and their LU
-      std::vector<ZDescT<T>> zd;
-      std::vector<LuDescT<T>> ld;
-      int64_t max_z = 0;
-      int max_n = 0;
-      for (int g : nodes) {
-        const int sa = nd[left(g)].s, sb = nd[right(g)].s;
-        zd.push_back(ZDescT<T>{C + nd[g].CL_off, C + nd[g].CR_off, zP<T>() + nd[g].Z_off, sa, sb});
-        ld.push_back(LuDescT<T>{zP<T>() + nd[g].Z_off, Zpiv.as<int>() + nd[g].Zpiv_off, sa + sb, sa + sb});
-        max_z = std::max<int64_t>(max_z, (int64_t)(sa + sb) * (sa + sb));
-        max_n = std::max(max_n, sa + sb);
+      if (mixed) {
+        conv_segs<double, float>(U64, Wb32.as<float>(), s32);
+        conv_segs<double, double>(U64, Wb.as<double>(), s64);
       }
-      arena.clear();
-      size_t oz = arena.push(zd), ol = arena.push(ld);
-      base = upload_arena();
-      form_Z<T>((const ZDescT<T>*)(base + oz), (int)zd.size(), max_z, st);
-      prof().flops[pk_of<T>(PK_GETRF)] += getrf_flops(ld);
-      getrf_batched<T>((const LuDescT<T>*)(base + ol), (int)ld.size(), max_n, status.as<int>(), st);
+      level_step<float>(nodes);
+      level_step<double>(nodes);
     }
+  }
+
+  // W = Solve(child, U) for the children of the nodes of one height whose problems are
+  // stored in precision T (C blocks come back as P_c W_c), then the reduced systems
+  // Z'' = [[I, C_l], [C_r, I]] and their LU.
+  template <typename T>
+  void level_step(const std::vector<int>& all_nodes) {
+    std::vector<int> nodes;
+    for (int g : all_nodes)
+      if (f64(g) == std::is_same<T, double>::value) nodes.push_back(g);
+    if (nodes.empty()) return;
+    T* W = wP<T>();
+    T* C = cP<T>();
+    std::vector<RootBlock<T>> rb;
+    for (int g : nodes)
+      for (int c : {left(g), right(g)}) {
+        const Node& n = nd[c];
+        const int sib = sibling(c);
+        // left child: C_l = P_l W_{l r~} (s_l x s_r); right child: C_r = P_r W_{r l~}
+        T* tout = C + ((n.uid & 1) == 0 ? nd[g].CL_off : nd[g].CR_off);
+        rb.push_back(RootBlock<T>{c, W + n.W_off, n.size, nd[sib].s, tout, n.s});
+      }
+    forest_solve<T>(rb);
+    std::vector<ZDescT<T>> zd;
+    std::vector<LuDescT<T>> ld;
+    int64_t max_z = 0;
+    int max_n = 0;
+    for (int g : nodes) {
+      const int sa = nd[left(g)].s, sb = nd[right(g)].s;
+      zd.push_back(ZDescT<T>{C + nd[g].CL_off, C + nd[g].CR_off, zP<T>() + nd[g].Z_off, sa, sb});
+      ld.push_back(LuDescT<T>{zP<T>() + nd[g].Z_off, Zpiv.as<int>() + nd[g].Zpiv_off, sa + sb, sa + sb});
+      max_z = std::max<int64_t>(max_z, (int64_t)(sa + sb) * (sa + sb));
+      max_n = std::max(max_n, sa + sb);
+    }
+    arena.clear();
+    size_t oz = arena.push(zd), ol = arena.push(ld);
+    char* base = upload_arena();
+    form_Z<T>((const ZDescT<T>*)(base + oz), (int)zd.size(), max_z, st);
+    prof().flops[pk_of<T>(PK_GETRF)] += getrf_flops(ld);
+    getrf_batched<T>((const LuDescT<T>*)(base + ol), (int)ld.size(), max_n, status.as<int>(), st);
   }
 
   // ------------------------------------------------------------------ solve
@@ -942,7 +1097,8 @@ class Solver {
     raise_status(read_status_and_clear());
     stats.refine_hist.clear();
     stats.refine_sweeps = 0;
-    const int sweeps = opt.refine > 0 ? opt.refine : (prec == PREC_MIXED ? 50 : 0);
+    stats.refine_stagnated = 0;
+    const int sweeps = opt.refine > 0 ? opt.refine : (prec == PREC_MIXED ? 200 : 0);
     if (sweeps <= 0) {
       plain_solve(rhs, nrhs, rhs);
     } else {
@@ -954,54 +1110,193 @@ class Solver {
   }
 
   // out <- (lambda I + K~)^{-1} in with the stored factorization; in and out may alias.
+  // Problems factored in FP32 are solved on an FP32 copy of their blocks.
   void plain_solve(const double* in, int nrhs, double* out) {
     const size_t n = (size_t)Ntot * nrhs;
     const BlockDesc* blocks = upload_blocks(nrhs, false);
     double* V = vbuf.ensure_n<double>(n);
     gather(in, V, nrhs, blocks, false);
-    if (prec == PREC_MIXED) {
-      float* V32 = vbuf32.ensure_n<float>(n);
-      convert_d2f(V, V32, (int64_t)n, st);
-      std::vector<RootBlock<float>> rb;
-      for (const Prob& P : pr)
-        rb.push_back(RootBlock<float>{P.nbase + 1, V32 + (size_t)P.pbase * nrhs, P.N, nrhs, nullptr, 0});
-      forest_solve<float>(rb);
-      convert_f2d(V32, V, (int64_t)n, st);
-    } else {
-      std::vector<RootBlock<double>> rb;
-      for (const Prob& P : pr)
-        rb.push_back(RootBlock<double>{P.nbase + 1, V + (size_t)P.pbase * nrhs, P.N, nrhs, nullptr, 0});
-      forest_solve<double>(rb);
+    std::vector<RootBlock<float>> r32;
+    std::vector<RootBlock<double>> r64;
+    std::vector<ConvSeg> back;
+    float* V32 = any_prec(false) ? vbuf32.ensure_n<float>(n) : nullptr;
+    for (const Prob& P : pr) {
+      const int64_t o = (int64_t)P.pbase * nrhs;
+      if (P.f64) {
+        r64.push_back(RootBlock<double>{P.nbase + 1, V + o, P.N, nrhs, nullptr, 0});
+      } else {
+        r32.push_back(RootBlock<float>{P.nbase + 1, V32 + o, P.N, nrhs, nullptr, 0});
+        const int64_t len = (int64_t)P.N * nrhs;
+        if (!back.empty() && back.back().src + back.back().len == o) back.back().len += len;
+        else back.push_back(ConvSeg{o, o, len});
+      }
     }
+    if (!r32.empty()) {
+      conv_segs<double, float>(V, V32, back);
+      forest_solve<float>(r32);
+      conv_segs<float, double>(V32, V, back);
+    }
+    if (!r64.empty()) forest_solve<double>(r64);
     gather(V, out, nrhs, blocks, true);
   }
 
-  // Iterative refinement against the FP64 operator: w <- w + Solve(u - A w).
-  void refine_solve(double* rhs, int nrhs, int sweeps) {
+  // Iterative refinement with flexible GMRES (FGMRES-IR; Carson & Higham's GMRES-IR with
+  // the preconditioned basis kept, Saad's flexible variant): residuals r = u - A w with the
+  // FP64 operator; each correction solves A z = r by restarted GMRES in FP64, right-
+  // preconditioned by the stored factorization M^-1.  The vectors Z_j = M^-1 v_j are kept
+  // and the update is w += Z y, so it matches the Arnoldi relation even though M^-1 runs
+  // partly in FP32 (no second, differently rounded application of M^-1).
+  // Every (problem, column) pair is its own segment; all open segments advance together,
+  // so one preconditioner and one operator application serve all of them per iteration.
+  // A segment closes when its relative residual is <= refine_tol, or when a cycle whose
+  // own GMRES estimate reached 0.1 refine_tol lowered the recomputed residual by less than
+  // half: then the rounding floor of the FP64 residual itself, about
+  // eps ||A|| ||w|| / ||u||, lies above the target and further cycles cannot help.
+  // max_iters bounds the total number of GMRES iterations.
+  void refine_solve(double* w, int nrhs, int max_iters) {
     const size_t n = (size_t)Ntot * nrhs;
-    double* u = rbuf.ensure_n<double>(2 * n);  // u copy, residual
+    const int S = (int)pr.size() * nrhs;
+    // restart length: at most 30, and (2m + 1) n doubles of bases within about 16 GB
+    const int m = (int)std::max<int64_t>(1, std::min<int64_t>(30, (int64_t)(1e9 / (double)n) - 1));
+    std::vector<GSeg> hseg(S);
+    for (size_t q = 0; q < pr.size(); ++q)
+      for (int c = 0; c < nrhs; ++c)
+        hseg[q * nrhs + c] = GSeg{(int64_t)pr[q].pbase * nrhs + (int64_t)c * pr[q].N, pr[q].N};
+    GSeg* segs = gseg_dev.ensure_n<GSeg>(S);
+    h2d(segs, hseg.data(), S, st);
+    double* u = rbuf.ensure_n<double>(2 * n);  // copy of the right-hand side, residual
     double* r = u + n;
-    IA_CUDA(cudaMemcpyAsync(u, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    std::vector<double> un, rn;
+    double* V = kryl.ensure_n<double>((size_t)(m + 1) * n);
+    double* Zb_ = kzb.ensure_n<double>((size_t)m * n);
+    double* coef = coefbuf.ensure_n<double>((size_t)(m + 1) * S);
+    IA_CUDA(cudaMemcpyAsync(u, w, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    std::vector<double> un, rn, hn, prev(S, 0.0), est_end(S, HUGE_VAL);
+    std::vector<int> state(S, 0);  // 0 open, 1 converged, 2 at the rounding floor
     column_norms(u, nrhs, un);
-    plain_solve(u, nrhs, rhs);
-    auto worst_residual = [&]() {
-      apply_device(rhs, r, nrhs);        // r = A w
-      axpby(u, r, n);                    // r = u - A w
+    plain_solve(u, nrhs, w);  // x0 = M^-1 u
+    int& iters = stats.refine_iters;
+    iters = 0;
+    bool first = true;
+    while (true) {
+      apply_device(w, r, nrhs);  // r = u - A w
+      axpby(u, r, n);
       column_norms(r, nrhs, rn);
       double worst = 0;
-      for (size_t c = 0; c < rn.size(); ++c) worst = std::max(worst, un[c] > 0 ? rn[c] / un[c] : rn[c]);
+      bool open = false;
+      for (int q = 0; q < S; ++q) {
+        const double rel = un[q] > 0 ? rn[q] / un[q] : rn[q];
+        if (!std::isfinite(rel)) throw Error(IASKIT_ERR_NOT_CONVERGED, "refinement produced a non-finite residual");
+        worst = std::max(worst, rel);
+        if (state[q] == 0) {
+          if (rel <= opt.refine_tol) state[q] = 1;
+          else if (!first && est_end[q] <= 0.1 * opt.refine_tol * std::max(un[q], 1e-300) &&
+                   rn[q] > 0.5 * prev[q])
+            state[q] = 2;
+        }
+        prev[q] = rn[q];
+        open = open || state[q] == 0;
+      }
       stats.refine_hist.push_back(worst);
-      return worst;
-    };
-    for (int it = 0; it < sweeps; ++it) {
-      if (worst_residual() <= opt.refine_tol) return;
-      plain_solve(r, nrhs, r);           // delta
-      add_inplace(rhs, r, n);            // w += delta
-      stats.refine_sweeps = it + 1;
+      if (!open) {
+        stats.refine_stagnated = (int)std::count(state.begin(), state.end(), 2);
+        return;
+      }
+      if (iters >= max_iters) throw Error(IASKIT_ERR_NOT_CONVERGED, "refinement did not converge");
+      // inner GMRES(m) on A z = r, right-preconditioned, open segments only
+      std::vector<double> H((size_t)S * (m + 1) * m, 0.0), cs((size_t)S * m), sn((size_t)S * m),
+          g((size_t)S * (m + 1), 0.0);
+      auto Hs = [&](int q, int i, int j) -> double& { return H[((size_t)q * (m + 1) + i) * m + j]; };
+      std::vector<double> inv(S);
+      for (int q = 0; q < S; ++q) {
+        const bool live = state[q] == 0 && rn[q] > 0;
+        g[(size_t)q * (m + 1)] = live ? rn[q] : 0.0;
+        inv[q] = live ? 1.0 / rn[q] : 0.0;  // closed segments get a zero basis and no update
+      }
+      h2d(coef, inv.data(), S, st);
+      seg_scale(V, r, coef, segs, S);  // V_0 = r / beta
+      int k = 0;
+      for (int j = 0; j < m && iters < max_iters; ++j) {
+        double* vj = V + (size_t)j * n;
+        double* vn = V + (size_t)(j + 1) * n;
+        double* zj = Zb_ + (size_t)j * n;
+        plain_solve(vj, nrhs, zj);      // Z_j = M^-1 v_j
+        apply_device(zj, vn, nrhs);     // v_{j+1} = A Z_j
+        std::vector<double> h1, h2;
+        seg_dots(V, n, j + 1, vn, segs, S, coef, h1);     // classical Gram-Schmidt,
+        seg_axpy(vn, V, n, j + 1, coef, -1.0, segs, S);    // twice
+        seg_dots(V, n, j + 1, vn, segs, S, coef, h2);
+        seg_axpy(vn, V, n, j + 1, coef, -1.0, segs, S);
+        column_norms(vn, nrhs, hn);
+        for (int q = 0; q < S; ++q) inv[q] = hn[q] > 0 ? 1.0 / hn[q] : 0.0;
+        h2d(coef, inv.data(), S, st);
+        seg_scale(vn, vn, coef, segs, S);
+        ++iters;
+        k = j + 1;
+        double worst_est = 0;
+        for (int q = 0; q < S; ++q) {
+          for (int i = 0; i <= j; ++i) Hs(q, i, j) = h1[(size_t)i * S + q] + h2[(size_t)i * S + q];
+          Hs(q, j + 1, j) = hn[q];
+          for (int i = 0; i < j; ++i) {  // earlier Givens rotations
+            const double a = Hs(q, i, j), b = Hs(q, i + 1, j);
+            Hs(q, i, j) = cs[(size_t)q * m + i] * a + sn[(size_t)q * m + i] * b;
+            Hs(q, i + 1, j) = -sn[(size_t)q * m + i] * a + cs[(size_t)q * m + i] * b;
+          }
+          const double a = Hs(q, j, j), b = Hs(q, j + 1, j);
+          const double rr = std::hypot(a, b);
+          const double c = rr > 0 ? a / rr : 1.0, sgn = rr > 0 ? b / rr : 0.0;
+          cs[(size_t)q * m + j] = c;
+          sn[(size_t)q * m + j] = sgn;
+          Hs(q, j, j) = rr;
+          Hs(q, j + 1, j) = 0.0;
+          double& gj = g[(size_t)q * (m + 1) + j];
+          g[(size_t)q * (m + 1) + j + 1] = -sgn * gj;
+          gj = c * gj;
+          const double est = std::fabs(g[(size_t)q * (m + 1) + j + 1]);
+          est_end[q] = est;
+          worst_est = std::max(worst_est, un[q] > 0 ? est / un[q] : est);
+        }
+        if (worst_est <= 0.1 * opt.refine_tol) break;
+      }
+      // y = R^-1 g per segment, w += Z y
+      std::vector<double> y((size_t)k * S, 0.0);
+      for (int q = 0; q < S; ++q)
+        for (int i = k - 1; i >= 0; --i) {
+          double acc = g[(size_t)q * (m + 1) + i];
+          for (int l = i + 1; l < k; ++l) acc -= Hs(q, i, l) * y[(size_t)l * S + q];
+          const double dd = Hs(q, i, i);
+          y[(size_t)i * S + q] = dd != 0.0 ? acc / dd : 0.0;
+        }
+      h2d(coef, y.data(), y.size(), st);
+      seg_axpy(w, Zb_, n, k, coef, 1.0, segs, S);
+      stats.refine_sweeps += 1;
+      first = false;
     }
-    if (worst_residual() > opt.refine_tol)
-      throw Error(IASKIT_ERR_NOT_CONVERGED, "refinement did not converge");
+  }
+
+  // out[i*S + q] = <V_i, x> over segment q, i < k
+  void seg_dots(const double* V, size_t vstride, int k, const double* x, const GSeg* segs, int S,
+                double* dev_out, std::vector<double>& out) {
+    {
+      ProfScope _ps(PK_MISC, st);
+      seg_dots_kernel<<<dim3(k, S), 256, 0, st>>>(V, vstride, x, segs, S, dev_out);
+      IA_LAUNCH_CHECK();
+    }
+    out.resize((size_t)k * S);
+    d2h(out.data(), dev_out, out.size(), st);  // dev_out keeps them for the following update
+    IA_CUDA(cudaStreamSynchronize(st));
+  }
+  // x_seg += sign * sum_{i<k} coef[i*S + q] V_i,seg
+  void seg_axpy(double* x, const double* V, size_t vstride, int k, const double* coef, double sign,
+                const GSeg* segs, int S) {
+    ProfScope _ps(PK_MISC, st);
+    seg_axpy_kernel<<<dim3(256, S), 256, 0, st>>>(x, V, vstride, k, coef, sign, segs, S);
+    IA_LAUNCH_CHECK();
+  }
+  // out_seg = coef[q] * x_seg
+  void seg_scale(double* out, const double* x, const double* coef, const GSeg* segs, int S) {
+    ProfScope _ps(PK_MISC, st);
+    seg_scale_kernel<<<dim3(256, S), 256, 0, st>>>(out, x, coef, segs);
+    IA_LAUNCH_CHECK();
   }
 
   void column_norms(const double* x, int nrhs, std::vector<double>& out) {
@@ -1019,11 +1314,6 @@ class Solver {
   void axpby(const double* u, double* r, size_t n) {
     ProfScope _ps(PK_MISC, st);
     axpby_kernel<<<grid_cap((int64_t)n, 8192), 256, 0, st>>>(u, r, n);
-    IA_LAUNCH_CHECK();
-  }
-  void add_inplace(double* w, const double* dl, size_t n) {
-    ProfScope _ps(PK_MISC, st);
-    add_kernel<<<grid_cap((int64_t)n, 8192), 256, 0, st>>>(w, dl, n);
     IA_LAUNCH_CHECK();
   }
 
@@ -1093,14 +1383,14 @@ class Solver {
           if (pass == 0) {
             const int sib = sibling(c);
             if (stored)
-              add_gemm<double>(g, Ustore.as<double>() + nd[c].W_off, nd[c].size, wsib(c), n2(parent(c)),
+              add_gemm<double>(g, Ustore.as<double>() + nd[c].U_off, nd[c].size, wsib(c), n2(parent(c)),
                                rows(Up, c), ldp(c), nd[c].size, nrhs, nd[sib].s, 1.0, 1.0);
             else
               md.push_back(KMatvecDesc{sk + (size_t)sib * s_max, wsib(c), rows(Up, c), nd[c].off,
                                        nd[c].size, 0, nd[sib].s, n2(parent(c)), ldp(c), scale_of(c)});
           } else {
             if (stored)
-              add_gemm<double>(g, Kleaf.as<double>() + nd[c].LU_off, nd[c].size, rows(Wp, c), ldp(c),
+              add_gemm<double>(g, Kleaf.as<double>() + nd[c].K_off, nd[c].size, rows(Wp, c), ldp(c),
                                rows(Up, c), ldp(c), nd[c].size, nrhs, nd[c].size, 1.0, 1.0);
             else
               md.push_back(KMatvecDesc{nullptr, rows(Wp, c), rows(Up, c), nd[c].off, nd[c].size,
@@ -1130,7 +1420,8 @@ class Solver {
     DevBuf* all[] = {&X, &Xp, &perm, &iperm, &pid, &knn, &knn_pos, &samp, &ranks, &skel,
                      &piv_ws, &A_ws, &status, &arena_dev, &step_dev, &tbuf, &vbuf, &vbuf32,
                      &ubuf, &rbuf, &wt, &io, &normbuf, &blocks_dev, &LU, &LUpiv, &Wb, &Zb, &Zpiv,
-                     &Cb, &LU32, &Wb32, &Zb32, &Cb32, &tbuf32, &Kleaf, &Ustore, &Pd, &Pf};
+                     &Cb, &LU32, &Wb32, &Zb32, &Cb32, &tbuf32, &Kleaf, &Ustore, &Pd, &Pf,
+                     &gseg_dev, &kryl, &kzb, &coefbuf, &cseg_dev, &rowsum};
     for (DevBuf* b : all) b->release();
     tree_s.release();
     knn_s.release();
@@ -1329,6 +1620,9 @@ int iaskit_set_option(const char* key, double value) {
       o.precision = as_int(0, 1);
     } else if (k == "problem") {
       o.problem = as_int(0, 1 << 30);
+    } else if (k == "mixed_cond_max") {
+      if (!(value >= 1.0)) throw Error(IASKIT_ERR_ARG, "invalid mixed_cond_max");
+      o.mixed_cond_max = value;
     } else if (k == "profile") {
       int v = as_int(0, 1);
       IA_CUDA(cudaStreamSynchronize(S().st));
@@ -1352,6 +1646,7 @@ int iaskit_get_option(const char* key, double* value) {
     else if (k == "profile") *value = prof().enabled ? 1 : 0;
     else if (k == "precision") *value = o.precision;
     else if (k == "problem") *value = o.problem;
+    else if (k == "mixed_cond_max") *value = o.mixed_cond_max;
     else throw Error(IASKIT_ERR_ARG, "unknown option " + k);
   });
 }
@@ -1380,6 +1675,14 @@ int iaskit_stats(char* buf, size_t len) {
   j += "\"refine_history\":[";
   for (size_t i = 0; i < s.stats.refine_hist.size(); ++i) {
     snprintf(tmp, sizeof tmp, "%s%.6g", i ? "," : "", s.stats.refine_hist[i]);
+    j += tmp;
+  }
+  snprintf(tmp, sizeof tmp, "],\"refine_iters\":%d,\"refine_stagnated\":%d,\"fp64_problems\":%d,",
+           s.stats.refine_iters, s.stats.refine_stagnated, s.stats.fp64_problems);
+  j += tmp;
+  j += "\"cond_est\":[";
+  for (size_t q = 0; q < s.pr.size() && s.factored; ++q) {
+    snprintf(tmp, sizeof tmp, "%s%.4g", q ? "," : "", std::min(s.pr[q].cond_est, 1e300));
     j += tmp;
   }
   j += "],\"launches\":";

@@ -1,0 +1,123 @@
+"""Refinement and the per-problem precision of the mixed form.
+
+* The condition estimate each problem gets is 1 + max_i sum_j K(x_i, x_j) / lambda over
+  64 rows i spread evenly over the tree order; recomputed here with numpy from the
+  returned permutation.
+* The mixed form factors a problem in FP64 when that estimate exceeds
+  "mixed_cond_max", and every column of a batch mixing both precisions is refined.
+* A target below the FP64 rounding floor of the residual ends with the columns marked
+  "stagnated" instead of spending the whole iteration budget.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _uniform(n, seed):
+    return np.ascontiguousarray(np.random.default_rng(seed).random((n, 16)))
+
+
+ILL = (_uniform(6000, 31), 1.2, 1e-3)     # ||K|| ~ 0.4 N, cond ~ 2e6
+WELL = (_uniform(3000, 32), 0.6, 1e-1)    # cond ~ 1e3
+
+
+def _cond_est(X, perm, h, lam):
+    N = len(X)
+    Xp = X[perm]
+    rows = Xp[(np.arange(64) * N) // 64]
+    d2 = ((rows[:, None, :] - Xp[None, :, :]) ** 2).sum(axis=2)
+    return 1.0 + np.exp(-d2 / (2 * h * h)).sum(axis=1).max() / lam
+
+
+@pytest.fixture()
+def mixed_opts(gpu_lib):
+    ia = gpu_lib
+    ia.iaskit_set_option("precision", 1)
+    yield ia
+    ia.iaskit_set_option("precision", 0)
+    ia.iaskit_set_option("mixed_cond_max", 1e6)
+    ia.iaskit_set_option("refine", 0)
+    ia.iaskit_set_option("refine_tol", 1e-10)
+
+
+def test_condition_estimate_and_precision_choice(mixed_opts):
+    ia = mixed_opts
+    probs = [ILL, WELL]
+    ia.iaskit_factor_batched([p[0] for p in probs], [p[1] for p in probs], [p[2] for p in probs],
+                             128, 64, 1e-6)
+    st = ia.iaskit_stats()
+    for q, (X, h, lam) in enumerate(probs):
+        ia.iaskit_set_option("problem", q)
+        ref = _cond_est(X, ia.iaskit_get_perm(len(X)), h, lam)
+        assert st["cond_est"][q] == pytest.approx(ref, rel=1e-3), q
+    ia.iaskit_set_option("problem", 0)
+    assert st["cond_est"][0] > 1e6 > st["cond_est"][1]
+    assert st["fp64_problems"] == 1
+    ia.iaskit_set_option("mixed_cond_max", 1e300)
+    ia.iaskit_factor_batched([p[0] for p in probs], [p[1] for p in probs], [p[2] for p in probs],
+                             128, 64, 1e-6)
+    assert ia.iaskit_stats()["fp64_problems"] == 0
+    ia.iaskit_set_option("mixed_cond_max", 1.0)
+    ia.iaskit_factor_batched([p[0] for p in probs], [p[1] for p in probs], [p[2] for p in probs],
+                             128, 64, 1e-6)
+    assert ia.iaskit_stats()["fp64_problems"] == 2
+    with pytest.raises(ia.IaskitError):
+        ia.iaskit_set_option("mixed_cond_max", 0.5)
+
+
+def _batch_residuals(ia, probs, rhs, w):
+    """Per problem, the worst relative residual of its columns against the FP64 operator
+    (the batched operator applied to all solutions at once)."""
+    import torch
+    Ns = [len(p[0]) for p in probs]
+    nrhs = rhs[0].shape[1]
+    W = torch.from_numpy(np.concatenate([np.asarray(x).T.reshape(-1) for x in w])).cuda()
+    AW = torch.empty_like(W)
+    ia.iaskit_apply_device(W, AW, nrhs)
+    AW = AW.cpu().numpy()
+    out, o = [], 0
+    for q, n in enumerate(Ns):
+        Au = AW[o:o + n * nrhs].reshape(nrhs, n).T
+        o += n * nrhs
+        out.append((np.linalg.norm(rhs[q] - Au, axis=0) / np.linalg.norm(rhs[q], axis=0)).max())
+    return out
+
+
+def test_mixed_batch_with_an_ill_conditioned_problem_is_refined(mixed_opts):
+    ia = mixed_opts
+    probs = [ILL, WELL]
+    rng = np.random.default_rng(33)
+    rhs = [rng.standard_normal((len(p[0]), 3)) for p in probs]
+    ia.iaskit_factor_batched([p[0] for p in probs], [p[1] for p in probs], [p[2] for p in probs],
+                             128, 64, 1e-6)
+    w = ia.iaskit_solve_batched(rhs)
+    st = ia.iaskit_stats()
+    assert st["fp64_problems"] == 1
+    res = _batch_residuals(ia, probs, rhs, w)
+    print("residuals", res, "history", st["refine_history"], "stagnated", st["refine_stagnated"])
+    assert res[1] <= 1e-10
+    # the FP64-factored problem meets the target unless its rounding floor is above it
+    assert res[0] <= 1e-10 or (st["refine_stagnated"] >= 1 and res[0] <= 1e-9)
+    assert st["refine_iters"] <= 40
+
+
+def test_target_below_the_rounding_floor_stagnates(gpu_lib):
+    ia = gpu_lib
+    X, h, lam = ILL
+    u = np.random.default_rng(34).standard_normal((len(X), 2))
+    ia.iaskit_set_option("refine", 60)
+    ia.iaskit_set_option("refine_tol", 1e-17)
+    try:
+        ia.iaskit_factor(X, h, lam, 128, 64, 1e-6)
+        w = ia.iaskit_solve(u)
+        st = ia.iaskit_stats()
+    finally:
+        ia.iaskit_set_option("refine", 0)
+        ia.iaskit_set_option("refine_tol", 1e-10)
+    assert st["refine_stagnated"] == 2
+    assert st["refine_sweeps"] <= 6
+    assert 1e-17 < st["refine_history"][-1] <= 1e-9
+    Au = ia.iaskit_apply(w)
+    rho = (np.linalg.norm(u - Au, axis=0) / np.linalg.norm(u, axis=0)).max()
+    assert rho <= 1e-9
