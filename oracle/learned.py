@@ -125,3 +125,117 @@ def ridge_leverage(B_rows: np.ndarray, G: np.ndarray, mu: float) -> np.ndarray:
     """l_i = b_i^T (G + mu I)^{-1} b_i for the rows b_i of B_rows, G a Gram matrix."""
     M = np.linalg.solve(G + mu * np.eye(G.shape[0]), B_rows.T)
     return np.einsum("ij,ji->i", B_rows, M)
+
+
+# ---------------------------------------------------------------------------
+# Learned sampling inside skeletonization.  For a non-root node alpha owning the
+# permuted positions [o, o + n) of a problem of N points (complement size N - n) with
+# n_samp = min(samp_factor s_max, N - n) rows to sample:
+#
+# * candidates (n_samp < N - n only): n_cand = min(cand_factor n_samp, N - n) rows.
+#   First, at most n_cand // 2 of the node's kNN candidates in the plain sampling order
+#   (hits descending, position ascending) with their hit counts; then uniform draws
+#   without replacement from the complement on the node's LEARN stream until n_cand
+#   rows are held (their hits feature is 0).
+# * selection: the n_samp candidates of largest MLP score (ties to the lower position),
+#   returned in ascending position order.
+# * judge: NHOLD rows drawn uniformly with replacement from the complement on the
+#   node's HOLD stream; the held-out ID error of a skeleton set S with interpolation
+#   matrix P is ||K(H, cols) - K(H, S) P||_F^2 / ||K(H, cols)||_F^2; the learned ID is
+#   kept when its error is <= the plain sample's, otherwise the node falls back.
+# * labels (training): NGRAM rows drawn uniformly with replacement on the GRAM stream
+#   give G = (N - n) / NGRAM * B^T B, B = K(gram rows, cols), mu = tol^2 trace(G)
+#   (tol = 1e-6 for fixed ranks); the label of candidate c is the ridge leverage
+#   b_c^T (G + mu I)^{-1} b_c with b_c = K(x_c, cols), and the training target its
+#   logarithm standardized over the node's candidates.
+# Each auxiliary stream is SplitMix64 with state s0 = splitmix64(splitmix64(seed ^ salt)
+# ^ uid) and draw q equal to splitmix64(s0 + q gamma), j = draw mod (N - n) mapped to
+# position j (j < o) or j + n, as for the plain uniform fill.
+# ---------------------------------------------------------------------------
+from .sampling import GAMMA, MASK64, splitmix64  # noqa: E402
+
+LEARN_SALT = 0x4C4541524E
+HOLD_SALT = 0x484F4C44
+GRAM_SALT = 0x4752414D
+NHOLD = 32
+NGRAM = 4096
+CAND_FACTOR = 8
+
+
+def stream_state(seed: int, salt: int, uid: int) -> int:
+    return splitmix64(splitmix64((seed ^ salt) & MASK64) ^ uid)
+
+
+def stream_position(s0: int, q: int, o: int, n: int, N: int) -> int:
+    j = splitmix64((s0 + q * GAMMA) & MASK64) % (N - n)
+    return j if j < o else j + n
+
+
+def knn_ranked(knn_pos: np.ndarray, o: int, n: int):
+    """The node's kNN candidates outside [o, o + n) with hit counts, hits descending then
+    position ascending (the plain sampling order)."""
+    cand = knn_pos.ravel()
+    cand = cand[(cand < o) | (cand >= o + n)]
+    if cand.size == 0:
+        return np.empty(0, dtype=np.int64), np.empty(0, dtype=np.int64)
+    vals, counts = np.unique(cand, return_counts=True)
+    order = np.lexsort((vals, -counts))
+    return vals[order].astype(np.int64), counts[order].astype(np.int64)
+
+
+def learned_candidates(knn_pos: np.ndarray, o: int, n: int, N: int, n_samp: int, seed: int,
+                       uid: int, cand_factor: int = CAND_FACTOR):
+    """(candidate positions, hit counts) of the node, kNN part first, then the draws."""
+    comp = N - n
+    n_samp = min(n_samp, comp)
+    n_cand = min(cand_factor * n_samp, comp)
+    vals, counts = knn_ranked(knn_pos, o, n)
+    k = min(vals.size, n_cand // 2)
+    cand = [int(v) for v in vals[:k]]
+    hits = [int(c) for c in counts[:k]]
+    taken = set(cand)
+    s0 = stream_state(seed, LEARN_SALT, uid)
+    q = 0
+    while len(cand) < n_cand:
+        pos = stream_position(s0, q, o, n, N)
+        if pos not in taken:
+            taken.add(pos)
+            cand.append(pos)
+            hits.append(0)
+        q += 1
+    return np.array(cand, dtype=np.int64), np.array(hits, dtype=np.int64)
+
+
+def uniform_rows(o: int, n: int, N: int, count: int, seed: int, salt: int, uid: int) -> np.ndarray:
+    """``count`` positions of the complement drawn with replacement on a node stream."""
+    s0 = stream_state(seed, salt, uid)
+    return np.array([stream_position(s0, q, o, n, N) for q in range(count)], dtype=np.int64)
+
+
+def select_top(scores: np.ndarray, cand: np.ndarray, n_samp: int) -> np.ndarray:
+    """The n_samp candidates of largest score (ties: lower position first), ascending."""
+    order = np.lexsort((cand, -np.asarray(scores, dtype=np.float64)))
+    return np.sort(cand[order[:n_samp]])
+
+
+def heldout_error(Xp: np.ndarray, H: np.ndarray, cols: np.ndarray, skel: np.ndarray,
+                  P: np.ndarray, h: float) -> float:
+    """||K(H, cols) - K(H, skel) P||_F^2 / ||K(H, cols)||_F^2 on the held-out rows H."""
+    A = gaussian_kernel(Xp[H], Xp[cols], h)
+    E = A - gaussian_kernel(Xp[H], Xp[skel], h) @ P
+    den = float((A * A).sum())
+    return float((E * E).sum()) / den if den > 0 else 0.0
+
+
+def leverage_labels(Xp: np.ndarray, cand: np.ndarray, cols: np.ndarray, gram: np.ndarray,
+                    h: float, tol: float, comp: int):
+    """(ridge leverage of each candidate, standardized log leverage)."""
+    B = gaussian_kernel(Xp[gram], Xp[cols], h)
+    G = (comp / gram.size) * (B.T @ B)
+    t = tol if tol > 0 else 1e-6
+    mu = t * t * float(np.trace(G))
+    lev = ridge_leverage(gaussian_kernel(Xp[cand], Xp[cols], h), G, mu)
+    z = np.log(np.maximum(lev, 1e-300))
+    sd = z.std()
+    target = (z - z.mean()) / sd if sd > 1e-12 else np.zeros_like(z)
+    return lev, target

@@ -89,3 +89,90 @@ def test_column_subset_is_evenly_spaced():
     sub = L.column_subset(cols)
     assert sub.size == 32 and sub[0] == 100 and list(sub[:3]) == [100, 103, 106]
     assert list(L.column_subset(np.arange(5))) == [0, 1, 2, 3, 4]
+
+
+# ---------------------------------------------------------------- learned sampling
+from oracle.sampling import sample_rows  # noqa: E402
+
+
+def _knn_setup(N=120, kappa=6, seed=11):
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, N, size=(16, kappa)), N
+
+
+def test_knn_ranked_brute_force_and_plain_sampling_agree():
+    knn_pos, N = _knn_setup()
+    o, n = 40, 16
+    vals, counts = L.knn_ranked(knn_pos, o, n)
+    hits = {}
+    for row in knn_pos:
+        for c in row:
+            if not (o <= c < o + n):
+                hits[int(c)] = hits.get(int(c), 0) + 1
+    ref = sorted(hits.items(), key=lambda kv: (-kv[1], kv[0]))
+    assert [int(v) for v in vals] == [k for k, _ in ref]
+    assert [int(c) for c in counts] == [v for _, v in ref]
+    # the plain sample takes the same ranked list first
+    ns = min(10, vals.size)
+    assert set(sample_rows(knn_pos, o, n, N, ns, seed=3, uid=9)) == set(int(v) for v in vals[:ns])
+
+
+def test_learned_candidates_structure():
+    knn_pos, N = _knn_setup()
+    o, n = 40, 16
+    cand, hits = L.learned_candidates(knn_pos, o, n, N, n_samp=6, seed=5, uid=13)
+    assert cand.size == 48 == np.unique(cand).size
+    assert np.all((cand < o) | (cand >= o + n)) and np.all((cand >= 0) & (cand < N))
+    vals, counts = L.knn_ranked(knn_pos, o, n)
+    k = min(vals.size, 24)
+    assert np.array_equal(cand[:k], vals[:k]) and np.array_equal(hits[:k], counts[:k])
+    assert np.all(hits[k:] == 0)
+    # a budget as large as the complement takes all of it
+    cand, _ = L.learned_candidates(knn_pos, o, n, N, n_samp=50, seed=5, uid=13)
+    assert sorted(cand.tolist()) == [p for p in range(N) if not (o <= p < o + n)]
+
+
+def test_uniform_rows_cover_the_complement_evenly():
+    o, n, N = 7, 5, 40
+    rows = L.uniform_rows(o, n, N, 35000, seed=1, salt=L.HOLD_SALT, uid=6)
+    assert np.all((rows < o) | (rows >= o + n))
+    counts = np.bincount(rows, minlength=N)
+    comp = [p for p in range(N) if not (o <= p < o + n)]
+    assert np.all(counts[comp] > 0) and counts[o:o + n].sum() == 0
+    chi2 = ((counts[comp] - 1000.0) ** 2 / 1000.0).sum()
+    assert chi2 < 80          # 34 degrees of freedom
+    assert not np.array_equal(rows[:32], L.uniform_rows(o, n, N, 32, 1, L.GRAM_SALT, 6))
+
+
+def test_select_top_brute_force():
+    rng = np.random.default_rng(2)
+    cand = rng.permutation(100)[:30]
+    scores = rng.integers(0, 5, size=30).astype(float)        # many ties
+    got = L.select_top(scores, cand, 12)
+    ref = sorted(sorted(zip(-scores, cand))[:12], key=lambda t: t[1])
+    assert got.tolist() == [int(c) for _, c in ref]
+
+
+def test_heldout_error_exact_and_trivial_cases():
+    rng = np.random.default_rng(3)
+    Xp = rng.random((20, 3))
+    Xp[5] = Xp[4]                                      # duplicate point: identical columns
+    H, cols = np.arange(10, 20), np.array([4, 5, 6])
+    assert L.heldout_error(Xp, H, cols, cols, np.eye(3), 0.7) == 0.0
+    assert L.heldout_error(Xp, H, cols, cols, np.zeros((3, 3)), 0.7) == pytest.approx(1.0)
+    P = np.array([[1.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    assert L.heldout_error(Xp, H, cols, np.array([4, 6]), P, 0.7) < 1e-30
+    assert L.heldout_error(Xp, H, cols, np.array([4]), P[:1], 0.7) > 1e-3
+
+
+def test_leverage_labels_sum_to_the_effective_rank():
+    rng = np.random.default_rng(4)
+    Xp = rng.random((80, 2))
+    cols = np.arange(10)
+    rest = np.arange(10, 80)
+    lev, t = L.leverage_labels(Xp, rest, cols, rest, h=0.5, tol=1e-3, comp=rest.size)
+    B = L.gaussian_kernel(Xp[rest], Xp[cols], 0.5)
+    s = np.linalg.svd(B, compute_uv=False)
+    mu = 1e-6 * float((s ** 2).sum())
+    assert lev.sum() == pytest.approx(float((s ** 2 / (s ** 2 + mu)).sum()), rel=1e-6)
+    assert t.mean() == pytest.approx(0.0, abs=1e-12) and t.std() == pytest.approx(1.0)
