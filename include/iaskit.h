@@ -154,6 +154,12 @@ int iaskit_apply_device(const double* d_w, double* d_u, int nrhs);
  *                  "mixed_cond_max" is factored in FP64 instead
  *   "mixed_cond_max" condition estimate above which the mixed precision factors a
  *                  problem in FP64 (1e6, >= 1)
+ *   "sampling"     0: kNN + uniform rows (Sec. II-B, default); 1: learned proposal
+ *                  judged per node against the plain sample (needs weights)
+ *   "cand_factor"  learned candidates per sampled row (8, 2..64)
+ *   "keep_candidates" 1: keep candidates, features and scores for iaskit_get_learned (0)
+ *   "train_batch"  rows per Adam step of iaskit_sampler_train (4096)
+ *   "learned_temp" Gumbel temperature of the learned selection (1; 0 = top scores)
  *   "problem"      which problem of a batch the introspection calls report (0) [any time]
  * Errors: IASKIT_ERR_ARG for an unknown key or an invalid value.
  */
@@ -195,6 +201,69 @@ int iaskit_get_skeleton(int level, int index, int32_t* skel, int cap);
 int iaskit_get_samples(int level, int index, int32_t* samp, int cap);
 /* Nested P of node (l, i): s x n_cols column-major; returns n_cols. */
 int iaskit_get_P(int level, int index, double* P, int64_t cap);
+
+/*
+ * Learned row proposal for skeletonization.  The paper samples the rows of
+ * K_{[1:N] alpha} with nearest-neighbour information plus uniform draws (Sec. II-B);
+ * with option "sampling" = 1 each node whose sample is not its whole complement
+ * also gets a learned sample, and keeps whichever of the two IDs has the smaller
+ * held-out error (below).  Not in the paper.
+ *   candidates  n_cand = min(cand_factor * n_samp, N - n) rows: at most n_cand / 2 kNN
+ *               candidates in the plain order (hits descending, position ascending),
+ *               then uniform draws without replacement from the complement on the
+ *               node's LEARN stream;
+ *   features    8 per candidate, from the column subset Y (at most 32 evenly spaced
+ *               ID columns, mean mu, radius r = max ||y - mu||): log(1 + hits) /
+ *               log(1 + kappa), ||x - mu|| / h, max and mean K(x, Y), level / L,
+ *               log2 n / log2 N, min(||x - mu|| / r, 1e3), 0;
+ *   score       MLP 8 -> 128 -> 128 -> 1, ReLU, BF16 operands, FP32 accumulation;
+ *   selection   the n_samp highest keys (ties to the lower position), ascending; key =
+ *               score + learned_temp * g, g = -log(-log(u)), u = ((r >> 11) + 1/2) 2^-53
+ *               for draw r of the candidate's index on the node's GUMBEL stream (salt
+ *               0x47554D42): a sample without replacement ~ exp(score / learned_temp);
+ *   judge       64 stratified rows H on the HOLD stream (below); the ID of sample v
+ *               (skeletons S_v, interpolation P_v) has error sum_h w_h ||K(h, cols) -
+ *               K(h, S_v) P_v||^2 / sum_h w_h ||K(h, cols)||^2 (FP64); the learned ID
+ *               is kept when its error is not larger than the plain one's.
+ * Stream of a node: s0 = splitmix64(splitmix64(seed ^ salt) ^ (2^l + i)), draw q =
+ * r_q = splitmix64(s0 + q * 0x9E3779B97F4A7C15); salts LEARN 0x4C4541524E, HOLD
+ * 0x484F4C44, GRAM 0x4752414D.  Candidate draws take j = r mod (N - n) as position j
+ * (j < offset) or j + n.  A stratified draw of c rows takes its first c/2 (all of them
+ * when the parent is the root) from the sibling, position sib_offset + r mod |sib|,
+ * and the rest from outside the parent, j = r mod (N - |parent|) taken as j or
+ * j + |parent|; a row weighs its stratum's size over the stratum's draws.
+ * Weights: 17793 FP32 values in the order W1 [128][8] (row = hidden unit), b1 [128],
+ * W2 [128][128] (row = output unit), b2 [128], w3 [128], b3.
+ */
+
+/* Trains the proposal on one problem (host points, N x d row-major): factors it in
+ * FP64 with plain sampling (lambda = 1; that factorization becomes the current one),
+ * labels every candidate of every node with its ridge leverage b^T (G + mu I)^{-1} b
+ * (b = K(x, cols), G = B^T diag(w) B over 4096 stratified GRAM-stream rows B with
+ * weights w, mu = tol^2 trace G), standardizes the log labels per node, then runs
+ * `epochs` epochs of
+ * Adam (beta 0.9, 0.999, eps 1e-8, step lr) on the mean squared error in batches of
+ * option "train_batch" shuffled rows.  Starts from the current weights if any, else a
+ * He-uniform draw.  Errors: IASKIT_ERR_ARG, _INPUT, _NOMEM, _SINGULAR, _CUDA. */
+int iaskit_sampler_train(const double* points, int64_t N, int d, double h, int leaf_m, int s_max,
+                         double tol, int epochs, double lr);
+/* Replace (n = 17793, host FP32) or read the weights; setting clears Adam's state. */
+int iaskit_sampler_set_weights(const float* w, int n);
+int iaskit_sampler_get_weights(float* w, int n);
+/* Scores of n host feature rows (n x 8 FP32, rounded to BF16 on upload). */
+int iaskit_mlp_forward(const float* feats, int64_t n, float* scores);
+/* One training step on n host rows: forward, gradient of the mean squared error
+ * (written to grad, 17793 floats, if not NULL; loss to *loss if not NULL), then one
+ * Adam update with step lr. */
+int iaskit_mlp_train_step(const float* feats, const float* targets, int64_t n, double lr, float* grad,
+                          float* loss);
+/* Candidates of node (l, i) kept by the last factorization or training (option
+ * "keep_candidates" = 1): positions (permuted, problem-local), features (n x 8, the
+ * BF16 values) and the selection keys (factorization) or training targets; info[4] = {plain
+ * held-out error, learned held-out error, 1 if the learned ID was kept (0 if not, -1
+ * when not judged), n_samp}.  Returns the candidate count (0 if the node had none). */
+int iaskit_get_learned(int level, int index, int32_t* cand, float* feat, float* value, int cap,
+                       double* info);
 
 /*
  * The kNN lists of iaskit_factor (same order, same ties, bit for bit) for callers

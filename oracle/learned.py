@@ -137,27 +137,37 @@ def ridge_leverage(B_rows: np.ndarray, G: np.ndarray, mu: float) -> np.ndarray:
 #   (hits descending, position ascending) with their hit counts; then uniform draws
 #   without replacement from the complement on the node's LEARN stream until n_cand
 #   rows are held (their hits feature is 0).
-# * selection: the n_samp candidates of largest MLP score (ties to the lower position),
-#   returned in ascending position order.
-# * judge: NHOLD rows drawn uniformly with replacement from the complement on the
-#   node's HOLD stream; the held-out ID error of a skeleton set S with interpolation
-#   matrix P is ||K(H, cols) - K(H, S) P||_F^2 / ||K(H, cols)||_F^2; the learned ID is
-#   kept when its error is <= the plain sample's, otherwise the node falls back.
-# * labels (training): NGRAM rows drawn uniformly with replacement on the GRAM stream
-#   give G = (N - n) / NGRAM * B^T B, B = K(gram rows, cols), mu = tol^2 trace(G)
-#   (tol = 1e-6 for fixed ranks); the label of candidate c is the ridge leverage
-#   b_c^T (G + mu I)^{-1} b_c with b_c = K(x_c, cols), and the training target its
-#   logarithm standardized over the node's candidates.
+# * selection: the n_samp candidates of largest key (ties to the lower position),
+#   returned in ascending position order; the key is the MLP score plus temp times a
+#   Gumbel draw of the node's GUMBEL stream (temp = 0: the score itself), which makes
+#   the selection a sample without replacement with probabilities ~ exp(score / temp).
+# * row strata: the complement of alpha splits into its sibling (whose rows use alpha's
+#   skeletons directly, and hold most of the kernel mass) and the points outside the
+#   parent.  A stratified draw of `count` rows takes c_s = count // 2 rows uniformly with
+#   replacement from the sibling and the rest from outside the parent (all from the
+#   sibling when the parent is the root); a row of stratum t weighs |t| / (its draws).
+# * judge: NHOLD stratified rows H (weights w) on the node's HOLD stream; the held-out
+#   ID error of a skeleton set S with interpolation matrix P is
+#   sum_h w_h ||K(h, cols) - K(h, S) P||^2 / sum_h w_h ||K(h, cols)||^2; the learned ID
+#   is kept when its error is <= the plain sample's, otherwise the node falls back.
+# * labels (training): NGRAM stratified rows on the GRAM stream give
+#   G = B^T diag(w) B, B = K(gram rows, cols), mu = tol^2 trace(G) (tol = 1e-6 for fixed
+#   ranks); the label of candidate c is the ridge leverage b_c^T (G + mu I)^{-1} b_c with
+#   b_c = K(x_c, cols), and the training target its logarithm standardized over the
+#   node's candidates.
 # Each auxiliary stream is SplitMix64 with state s0 = splitmix64(splitmix64(seed ^ salt)
-# ^ uid) and draw q equal to splitmix64(s0 + q gamma), j = draw mod (N - n) mapped to
-# position j (j < o) or j + n, as for the plain uniform fill.
+# ^ uid) and draw q equal to splitmix64(s0 + q gamma); a draw r is mapped to the sibling
+# position sib_o + r mod |sib|, or to j = r mod (N - |parent|) taken as j (j < parent
+# offset) or j + |parent|; the candidates' uniform part maps j = r mod (N - n) around
+# alpha itself, as the plain uniform fill does.
 # ---------------------------------------------------------------------------
 from .sampling import GAMMA, MASK64, splitmix64  # noqa: E402
 
 LEARN_SALT = 0x4C4541524E
 HOLD_SALT = 0x484F4C44
 GRAM_SALT = 0x4752414D
-NHOLD = 32
+GUMBEL_SALT = 0x47554D42
+NHOLD = 64
 NGRAM = 4096
 CAND_FACTOR = 8
 
@@ -212,26 +222,57 @@ def uniform_rows(o: int, n: int, N: int, count: int, seed: int, salt: int, uid: 
     return np.array([stream_position(s0, q, o, n, N) for q in range(count)], dtype=np.int64)
 
 
+def stratified_rows(sib_o: int, sib_n: int, par_o: int, par_n: int, N: int, count: int,
+                    seed: int, salt: int, uid: int):
+    """(positions, weights) of a stratified draw: sibling rows first, then rows outside
+    the parent."""
+    s0 = stream_state(seed, salt, uid)
+    far = N - par_n
+    cs = count if far == 0 else count // 2
+    rows = np.empty(count, dtype=np.int64)
+    wts = np.empty(count)
+    for q in range(count):
+        r = splitmix64((s0 + q * GAMMA) & MASK64)
+        if q < cs:
+            rows[q] = sib_o + r % sib_n
+            wts[q] = sib_n / cs
+        else:
+            j = r % far
+            rows[q] = j if j < par_o else j + par_n
+            wts[q] = far / (count - cs)
+    return rows, wts
+
+
+def gumbel_keys(scores: np.ndarray, seed: int, uid: int, temp: float) -> np.ndarray:
+    """scores + temp * g with Gumbel draws g_c = -log(-log(u_c)), u_c = ((r_c >> 11) + 1/2)
+    2^-53 from draw c of the node's GUMBEL stream, rounded to FP32.  The top n of the
+    keys are a sample without replacement with probabilities ~ exp(score / temp)."""
+    s0 = stream_state(seed, GUMBEL_SALT, uid)
+    u = np.array([((splitmix64((s0 + c * GAMMA) & MASK64) >> 11) + 0.5) * 2.0 ** -53
+                  for c in range(len(scores))])
+    return (np.asarray(scores, dtype=np.float64) + temp * -np.log(-np.log(u))).astype(np.float32)
+
+
 def select_top(scores: np.ndarray, cand: np.ndarray, n_samp: int) -> np.ndarray:
     """The n_samp candidates of largest score (ties: lower position first), ascending."""
     order = np.lexsort((cand, -np.asarray(scores, dtype=np.float64)))
     return np.sort(cand[order[:n_samp]])
 
 
-def heldout_error(Xp: np.ndarray, H: np.ndarray, cols: np.ndarray, skel: np.ndarray,
-                  P: np.ndarray, h: float) -> float:
-    """||K(H, cols) - K(H, skel) P||_F^2 / ||K(H, cols)||_F^2 on the held-out rows H."""
+def heldout_error(Xp: np.ndarray, H: np.ndarray, wts: np.ndarray, cols: np.ndarray,
+                  skel: np.ndarray, P: np.ndarray, h: float) -> float:
+    """sum_h w_h ||K(h, cols) - K(h, skel) P||^2 / sum_h w_h ||K(h, cols)||^2."""
     A = gaussian_kernel(Xp[H], Xp[cols], h)
     E = A - gaussian_kernel(Xp[H], Xp[skel], h) @ P
-    den = float((A * A).sum())
-    return float((E * E).sum()) / den if den > 0 else 0.0
+    den = float(wts @ (A * A).sum(axis=1))
+    return float(wts @ (E * E).sum(axis=1)) / den if den > 0 else 0.0
 
 
 def leverage_labels(Xp: np.ndarray, cand: np.ndarray, cols: np.ndarray, gram: np.ndarray,
-                    h: float, tol: float, comp: int):
-    """(ridge leverage of each candidate, standardized log leverage)."""
+                    wts: np.ndarray, h: float, tol: float):
+    """(ridge leverage of each candidate against G = B^T diag(w) B, standardized log)."""
     B = gaussian_kernel(Xp[gram], Xp[cols], h)
-    G = (comp / gram.size) * (B.T @ B)
+    G = B.T @ (wts[:, None] * B)
     t = tol if tol > 0 else 1e-6
     mu = t * t * float(np.trace(G))
     lev = ridge_leverage(gaussian_kernel(Xp[cand], Xp[cols], h), G, mu)

@@ -38,8 +38,11 @@ EXPORTS = [
     "iaskit_get_perm", "iaskit_get_knn", "iaskit_get_ranks", "iaskit_get_skeleton",
     "iaskit_get_samples", "iaskit_get_P", "iaskit_knn_noalloc", "iaskit_factor_batched",
     "iaskit_factor_batched_device", "iaskit_num_problems", "iaskit_solve_batched",
-    "iaskit_solve_batched_device",
+    "iaskit_solve_batched_device", "iaskit_sampler_train", "iaskit_sampler_set_weights",
+    "iaskit_sampler_get_weights", "iaskit_mlp_forward", "iaskit_mlp_train_step", "iaskit_get_learned",
 ]
+
+MLP_NPARAM = 17793
 
 
 class IaskitError(RuntimeError):
@@ -90,6 +93,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "iaskit_num_problems": ([], i32),
         "iaskit_solve_batched": ([vp, i32], i32),
         "iaskit_solve_batched_device": ([vp, i32], i32),
+        "iaskit_sampler_train": ([vp, i64, i32, dbl, i32, i32, dbl, i32, dbl], i32),
+        "iaskit_sampler_set_weights": ([vp, i32], i32),
+        "iaskit_sampler_get_weights": ([vp, i32], i32),
+        "iaskit_mlp_forward": ([vp, i64, vp], i32),
+        "iaskit_mlp_train_step": ([vp, vp, i64, dbl, vp, vp], i32),
+        "iaskit_get_learned": ([i32, i32, vp, vp, vp, i32, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -313,3 +322,65 @@ def iaskit_knn_noalloc(points, kappa: int, out, stream=None) -> None:
     handle = 0 if stream is None else getattr(stream, "cuda_stream", stream)
     _check(lib.iaskit_knn_noalloc(_dev_ptr(points), N, d, kappa, out.data_ptr(),
                                   ctypes.c_void_p(handle)))
+
+
+# ------------------------------------------------------------- learned sampling
+def iaskit_sampler_train(points, h: float, leaf_m: int, s_max: int, tol: float, epochs: int,
+                         lr: float) -> None:
+    """Label the candidates of every node of this host problem and train the MLP."""
+    X = _host_f64(points)
+    _check(load().iaskit_sampler_train(X.ctypes.data, X.shape[0], X.shape[1], float(h), leaf_m,
+                                       s_max, float(tol), epochs, float(lr)))
+
+
+def iaskit_sampler_set_weights(w) -> None:
+    a = np.ascontiguousarray(np.asarray(w, dtype=np.float32).reshape(-1))
+    _check(load().iaskit_sampler_set_weights(a.ctypes.data, a.size))
+
+
+def iaskit_sampler_get_weights() -> np.ndarray:
+    out = np.empty(MLP_NPARAM, dtype=np.float32)
+    _check(load().iaskit_sampler_get_weights(out.ctypes.data, out.size))
+    return out
+
+
+def iaskit_mlp_forward(feats) -> np.ndarray:
+    F = np.ascontiguousarray(np.asarray(feats, dtype=np.float32).reshape(-1, 8))
+    out = np.empty(F.shape[0], dtype=np.float32)
+    _check(load().iaskit_mlp_forward(F.ctypes.data, F.shape[0], out.ctypes.data))
+    return out
+
+
+def iaskit_mlp_train_step(feats, targets, lr: float):
+    """One Adam step; returns (gradient before the step, loss)."""
+    F = np.ascontiguousarray(np.asarray(feats, dtype=np.float32).reshape(-1, 8))
+    t = np.ascontiguousarray(np.asarray(targets, dtype=np.float32).reshape(-1))
+    g = np.empty(MLP_NPARAM, dtype=np.float32)
+    loss = np.zeros(1, dtype=np.float32)
+    _check(load().iaskit_mlp_train_step(F.ctypes.data, t.ctypes.data, F.shape[0], float(lr),
+                                        g.ctypes.data, loss.ctypes.data))
+    return g, float(loss[0])
+
+
+def iaskit_get_learned(level: int, index: int, cap: int = 1 << 16):
+    """(candidates, features (n, 8), scores or targets, info[4]) of a kept node."""
+    cand = np.empty(cap, dtype=np.int32)
+    feat = np.empty((cap, 8), dtype=np.float32)
+    val = np.empty(cap, dtype=np.float32)
+    info = np.zeros(4, dtype=np.float64)
+    n = _check(load().iaskit_get_learned(level, index, cand.ctypes.data, feat.ctypes.data,
+                                         val.ctypes.data, cap, info.ctypes.data))
+    return cand[:n].astype(np.int64), feat[:n].copy(), val[:n].copy(), info
+
+
+def mlp_pack(p: dict) -> np.ndarray:
+    """Oracle-style parameter dict -> the library's flat FP32 layout."""
+    return np.concatenate([np.asarray(p[k], dtype=np.float64).reshape(-1)
+                           for k in ("W1", "b1", "W2", "b2", "w3", "b3")]).astype(np.float32)
+
+
+def mlp_unpack(w) -> dict:
+    """The library's flat layout -> a dict of float64 arrays (W1, b1, W2, b2, w3, b3)."""
+    w = np.asarray(w, dtype=np.float64)
+    return {"W1": w[0:1024].reshape(128, 8), "b1": w[1024:1152], "W2": w[1152:17536].reshape(128, 128),
+            "b2": w[17536:17664], "w3": w[17664:17792], "b3": w[17792:17793]}

@@ -255,6 +255,108 @@ struct RowSumDesc {
 void kernel_rowsums(const double* Xp, int d, const RowSumDesc* descs_dev, int nprob, double* out,
                     cudaStream_t st);
 
+// ------------------------------------------------------ learned sampling (a11)
+// MLP 8 -> 128 -> 128 -> 1 (ReLU).  FP32 master parameters, in this order:
+// W1 [128][8] (row = hidden unit), b1 [128], W2 [128][128] (row = output unit), b2 [128],
+// w3 [128], b3 [1]; BF16 copies of W1, W2, W2^T and w3 feed the tensor-core kernels.
+constexpr int MLP_F = 8, MLP_W = 128;
+constexpr int MLP_OFF_W1 = 0, MLP_OFF_B1 = 1024, MLP_OFF_W2 = 1152, MLP_OFF_B2 = 17536,
+              MLP_OFF_W3 = 17664, MLP_OFF_B3 = 17792, MLP_NPARAM = 17793;
+constexpr uint64_t LEARN_SALT = 0x4C4541524Eull, HOLD_SALT = 0x484F4C44ull, GRAM_SALT = 0x4752414Dull,
+                   GUMBEL_SALT = 0x47554D42ull;
+constexpr int NHOLD = 64;    // held-out rows per judged node
+constexpr int NGRAM = 4096;  // Gram-estimate rows per labelled node
+struct MlpDev {
+  float* master;
+  uint16_t *W1, *W2, *W2T, *w3;  // BF16 bit patterns
+};
+// Per node of a sampling step (same indexing as SampleNodeInfo): where its candidates
+// start, how many (0: no learned sample), and its n_samp.
+struct LearnNodeInfo {
+  int cand_off, n_cand, n_samp;
+};
+struct LearnFeatDesc {
+  const int* colsA;
+  const int* colsB;
+  int col0, nA, ncols;
+  const int* cand;      // n_cand positions (already offset)
+  const float* hits;    // n_cand hit counts (already offset)
+  int n_cand, cand_off; // rows of the feature array start at cand_off
+  float f4, f5, inv_h, inv_log1p_kappa;
+  double scale;         // -1 / (2 h^2)
+};
+// Stratified row draw of a node (offsets inside its problem): the first cs rows from
+// the sibling [sib_o, sib_o + sib_n), the others from outside the parent [par_o, par_o +
+// par_n); cs = count / 2, or count when the parent is the whole problem.
+struct StreamDesc {
+  int pb, pn, uid, out_off, sib_o, sib_n, par_o, par_n;
+};
+struct JudgeDesc {
+  const int* H;       // nh held-out positions, the first nh_s from the sibling
+  int nh_s;
+  double w_s, w_r;    // weights of a sibling row and of a row outside the parent
+  const int* colsA;
+  const int* colsB;
+  int col0, nA, ncols;
+  const int* skel;    // s positions
+  int s;
+  const double* P;    // s x ncols, column-major
+  double scale;
+};
+struct ColsDesc {
+  const int* colsA;
+  const int* colsB;
+  int col0, nA, ncols, out_off;
+};
+struct RidgeDesc {
+  double* G;
+  int n;
+};
+struct LevDesc {
+  const double* Bc;   // nc x n_cand K(cols, cand)
+  const double* Xs;   // nc x n_cand (G + mu I)^{-1} K(cols, cand)
+  int nc, n_cand, out_off;
+};
+void learned_candidates(const uint32_t* cand_sorted, const uint64_t* keys_sorted, const int* node_start,
+                        const int* node_cnt, int cnt_bits, const int* off, const SampleNodeInfo* info,
+                        const LearnNodeInfo* linfo, int nn, uint64_t seed, int max_cand, int* cand,
+                        float* hits, int* status, cudaStream_t st);
+void learned_features(const double* Xp, int d, const LearnFeatDesc* descs, int nd, int max_cand,
+                      uint16_t* feat, cudaStream_t st);
+void mlp_forward(const uint16_t* X, int64_t n, const MlpDev& w, float* y, uint16_t* H1, uint16_t* H2,
+                 cudaStream_t st);
+void mlp_backward(const uint16_t* X, const uint16_t* H1, const uint16_t* H2, const float* y,
+                  const float* t, int64_t n, double inv_batch, const MlpDev& w, float* grad,
+                  float* loss, cudaStream_t st);
+void mlp_adam(const MlpDev& w, float* grad, float* m, float* v, int step, double lr, double beta1,
+              double beta2, double eps, cudaStream_t st);
+void mlp_refresh_copies(const MlpDev& w, cudaStream_t st);
+// score[c] <- score[c] + temp * g_c with g_c = -log(-log(u_c)) a Gumbel draw, u_c =
+// ((r_c >> 11) + 1/2) 2^-53 from draw c of the node's GUMBEL stream (FP64, rounded to
+// FP32): the top n_samp of the perturbed scores sample without replacement with
+// probabilities proportional to exp(score / temp).
+void perturb_scores(float* score, const LearnNodeInfo* linfo, const SampleNodeInfo* info, int nn,
+                    int max_cand, uint64_t seed, double temp, cudaStream_t st);
+void learned_select(const float* score, const int* cand, const LearnNodeInfo* linfo,
+                    const SampleNodeInfo* info, int nn, int max_cand, int* samp, cudaStream_t st);
+void stream_rows(const StreamDesc* descs, int nd, int count, uint64_t seed, uint64_t salt, int* out,
+                 cudaStream_t st);
+void id_judge(const double* Xp, int d, const JudgeDesc* descs, int nd, int nh, int max_s, double* out,
+              cudaStream_t st);
+void gather_cols(const ColsDesc* descs, int nd, int* out, cudaStream_t st);
+void add_ridge(const RidgeDesc* descs, int nd, double tol2, cudaStream_t st);
+void leverage_targets(const LevDesc* descs, int nd, double* lev, float* target, cudaStream_t st);
+// B[r, :] *= (r < split ? w0 : w1) for the rows of each block (column-major, ld)
+struct RowScaleDesc {
+  double* B;
+  int rows, cols, ld, split;
+  double w0, w1;
+};
+void scale_rows(const RowScaleDesc* descs, int nd, cudaStream_t st);
+// Training batch: of[i] = feat row idx[i] (8 BF16), ot[i] = tgt[idx[i]].
+void gather_train(const uint16_t* feat, const float* tgt, const int* idx, int n, uint16_t* of, float* ot,
+                  cudaStream_t st);
+
 // Any entry non-finite -> atomicOr(status, DEV_BADINPUT).
 void check_finite(const double* x, int64_t n, int* dev_status, cudaStream_t st);
 

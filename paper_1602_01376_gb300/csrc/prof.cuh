@@ -28,6 +28,9 @@ enum ProfKind {
   PK_GETRF32,
   PK_GETRS32,
   PK_GEMM32,
+  PK_LEARN,      // learned sampling: candidates, features, selection, streams, labels
+  PK_MLP,        // BF16 MLP forward / backward / Adam (tensor cores)
+  PK_JUDGE,      // held-out ID error of the learned and plain samples
   PK_COUNT
 };
 

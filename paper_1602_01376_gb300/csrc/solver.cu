@@ -37,6 +37,9 @@
 //    approximate inverse of exactly the operator the residual uses.
 #include <algorithm>
 #include <chrono>
+#include <climits>
+#include <numeric>
+#include <random>
 #include <cmath>
 #include <memory>
 #include <type_traits>
@@ -79,6 +82,11 @@ struct Options {
   int problem = 0;  // problem the introspection calls refer to
   // mixed form: problems whose estimated condition number exceeds this are factored in FP64
   double mixed_cond_max = 1e6;
+  int sampling = 0;         // 0: kNN + uniform; 1: learned proposal judged per node
+  int cand_factor = 8;      // learned candidates per sampled row
+  int keep_candidates = 0;  // keep candidates, features and scores for introspection
+  int train_batch = 4096;
+  double learned_temp = 1.0;  // Gumbel temperature of the learned selection (0: top scores)
 };
 
 struct Prob {
@@ -113,6 +121,10 @@ struct Stats {
   int refine_iters = 0;       // GMRES iterations (operator applications) of the last solve
   int refine_stagnated = 0;   // columns stopped at the rounding floor of the FP64 operator
   int fp64_problems = 0;      // problems factored in FP64
+  int learned_nodes = 0, fallback_nodes = 0, judged_nodes = 0;
+  double judge_err_plain = 0, judge_err_chosen = 0;  // sums over judged nodes
+  std::vector<double> train_loss;                    // mean batch loss per epoch
+  int64_t train_rows = 0;
 };
 
 template <typename T>
@@ -289,6 +301,12 @@ class Solver {
   DevBuf X, Xp, perm, iperm, pid, knn, knn_pos, samp, ranks, skel, piv_ws, A_ws, status,
       arena_dev, step_dev, tbuf, vbuf, vbuf32, ubuf, rbuf, wt, io, normbuf, blocks_dev, gseg_dev,
       kryl, kzb, coefbuf, cseg_dev, rowsum;
+  // learned sampling: per-step scratch, MLP parameters and training data
+  DevBuf l_cand, l_hits, l_feat, l_score, l_linfo, l_samp, l_rk, l_Ptmp, l_sktmp, l_hold, l_err,
+      l_cols, l_gram, l_dense, mlp_master, mlp_m, mlp_v, mlp_grad, mlp_b16, mlp_loss, tr_feat, tr_tgt,
+      tr_lev, tr_bx, tr_bt, tr_y, tr_H1, tr_H2, tr_idx;
+  int mlp_step = 0;
+  bool mlp_ready = false;
   // factorization storage: FP64 (plain) and FP32 (mixed)
   DevBuf LU, LUpiv, Wb, Zb, Zpiv, Cb, LU32, Wb32, Zb32, Cb32, tbuf32;
   // FP64 operator blocks kept by the mixed form: leaf blocks lambda I + K_aa and U blocks
@@ -719,8 +737,203 @@ class Solver {
     }
   }
 
+  // ------------------------------------------------------------ sampling steps
+  // One sampling step (height hh): the node list covering all points (problems with no
+  // node at this height pass through), uploaded, and the plain samples of its nodes.
+  struct StepLists {
+    std::vector<int> nodes;            // gids of the height's non-root nodes
+    std::vector<int> off;              // nn + 1 offsets
+    std::vector<SampleNodeInfo> info;  // nn entries
+    std::vector<int> gid;              // nn entries: the node's gid, -1 for a pass-through
+    int* od = nullptr;
+    SampleNodeInfo* id = nullptr;
+  };
+  void sample_step(int hh, int samp_cap, int* sp, StepLists& L) {
+    L = StepLists{};
+    for (int g : by_height[hh])
+      if (!is_root(g)) L.nodes.push_back(g);
+    if (L.nodes.empty()) return;
+    size_t k = 0;
+    for (size_t q = 0; q < pr.size(); ++q) {
+      const Prob& P = pr[q];
+      const int l = P.L - hh;
+      if (l >= 1) {
+        for (int i = 0; i < (1 << l); ++i) {
+          const int g = L.nodes[k++];
+          const Node& n = nd[g];
+          L.off.push_back(n.off);
+          L.info.push_back(SampleNodeInfo{P.pbase, P.N, n.uid, (int)n.samp_off, 1});
+          L.gid.push_back(g);
+        }
+      } else {
+        L.off.push_back(P.pbase);
+        L.info.push_back(SampleNodeInfo{P.pbase, P.N, 0, 0, 0});
+        L.gid.push_back(-1);
+      }
+    }
+    L.off.push_back(Ntot);
+    const int nn = (int)L.info.size();
+    L.od = step_dev.ensure_n<int>(nn + 1 + (int64_t)nn * (sizeof(SampleNodeInfo) / sizeof(int)));
+    h2d(L.od, L.off.data(), nn + 1, st);
+    L.id = reinterpret_cast<SampleNodeInfo*>(L.od + nn + 1);
+    h2d(L.id, L.info.data(), L.info.size(), st);
+    sample_level(knn_pos.as<int>(), Ntot, kappa, L.od, L.id, L.off, L.info, samp_cap, opt.seed, sp,
+                 status.as<int>(), samp_s, st);
+  }
+
+  // ID columns of node g as a KDesc/feature column spec
+  void cols_of(int g, const int*& colsA, const int*& colsB, int& col0, int& nA, int& ncols) const {
+    const Node& n = nd[g];
+    if (is_leaf(g)) {
+      colsA = colsB = nullptr;
+      col0 = n.off;
+      nA = 0;
+      ncols = n.size;
+    } else {
+      const int* sk = skel.as<int>();
+      colsA = sk + (size_t)left(g) * s_max;
+      colsB = sk + (size_t)right(g) * s_max;
+      col0 = 0;
+      nA = nd[left(g)].s;
+      ncols = nA + nd[right(g)].s;
+    }
+  }
+
+  // Candidates and features of the learned proposal for the nodes of a step right after
+  // its sample_level (which left the kNN candidate ranking in samp_s).  Fills li (nn
+  // entries, uploaded to l_linfo) and l_cand / l_hits / l_feat; returns the nodes
+  // with candidates and their total count in tot.
+  std::vector<int> learned_candidates_step(const StepLists& L, std::vector<LearnNodeInfo>& li,
+                                           int64_t& tot, int& max_cand) {
+    const int nn = (int)L.info.size();
+    li.assign(nn, LearnNodeInfo{0, 0, 0});
+    std::vector<int> out;
+    tot = 0;
+    max_cand = 0;
+    for (int e = 0; e < nn; ++e) {
+      const int g = L.gid[e];
+      if (g < 0) continue;
+      const Node& n = nd[g];
+      const int comp = pr[n.prob].N - n.size;
+      if (n.nsamp <= 0 || n.nsamp >= comp) continue;
+      const int nc = (int)std::min<int64_t>((int64_t)opt.cand_factor * n.nsamp, comp);
+      li[e] = LearnNodeInfo{(int)tot, nc, n.nsamp};
+      tot += nc;
+      max_cand = std::max(max_cand, nc);
+      out.push_back(g);
+    }
+    if (out.empty()) return out;
+    if (tot > (int64_t)INT_MAX / 8) throw Error(IASKIT_ERR_UNSUPPORTED, "too many learned candidates");
+    int* cand = l_cand.ensure_n<int>(tot);
+    float* hits = l_hits.ensure_n<float>(tot);
+    uint16_t* feat = l_feat.ensure_n<uint16_t>(tot * 8);
+    LearnNodeInfo* lid = l_linfo.ensure_n<LearnNodeInfo>(nn);
+    h2d(lid, li.data(), nn, st);
+    int pos_bits = 0;
+    while (((uint64_t)1 << pos_bits) <= (uint64_t)Ntot) ++pos_bits;
+    learned_candidates(samp_s.vals2.as<uint32_t>(), samp_s.keys2.as<uint64_t>(), samp_s.node_start.as<int>(),
+                       samp_s.node_cnt.as<int>(), pos_bits, L.od, L.id, lid, nn, opt.seed, max_cand, cand,
+                       hits, status.as<int>(), st);
+    std::vector<LearnFeatDesc> fd;
+    for (int e = 0; e < nn; ++e) {
+      if (li[e].n_cand <= 0) continue;
+      const int g = L.gid[e];
+      const Node& n = nd[g];
+      const Prob& P = pr[n.prob];
+      LearnFeatDesc f{};
+      cols_of(g, f.colsA, f.colsB, f.col0, f.nA, f.ncols);
+      f.cand = cand + li[e].cand_off;
+      f.hits = hits + li[e].cand_off;
+      f.n_cand = li[e].n_cand;
+      f.cand_off = li[e].cand_off;
+      f.f4 = (float)(n.level / (double)std::max(P.L, 1));
+      f.f5 = (float)(std::log2((double)n.size) / std::log2((double)P.N));
+      f.inv_h = (float)(1.0 / P.h);
+      f.inv_log1p_kappa = (float)(1.0 / std::log1p((double)kappa));
+      f.scale = P.scale;
+      fd.push_back(f);
+    }
+    arena.clear();
+    size_t of = arena.push(fd);
+    char* base = upload_arena();
+    learned_features(Xp.as<double>(), d, (const LearnFeatDesc*)(base + of), (int)fd.size(), max_cand, feat, st);
+    return out;
+  }
+
+  // stratified row draw of node g (sibling half, outside-the-parent half)
+  StreamDesc strat_desc(int g, int out_off) const {
+    const Node& n = nd[g];
+    const Prob& P = pr[n.prob];
+    const Node& sb = nd[sibling(g)];
+    const Node& pa = nd[parent(g)];
+    return StreamDesc{P.pbase, P.N, n.uid, out_off, sb.off - P.pbase, sb.size, pa.off - P.pbase, pa.size};
+  }
+  void strat_weights(int g, int count, int& cs, double& ws, double& wr) const {
+    const Node& sb = nd[sibling(g)];
+    const int far = pr[nd[g].prob].N - nd[parent(g)].size;
+    cs = far == 0 ? count : count / 2;
+    ws = (double)sb.size / cs;
+    wr = far == 0 ? 0.0 : (double)far / (count - cs);
+  }
+
+  MlpDev mlp_dev() {
+    uint16_t* b = mlp_b16.as<uint16_t>();
+    return MlpDev{mlp_master.as<float>(), b, b + 1024, b + 1024 + 16384, b + 1024 + 2 * 16384};
+  }
+  void mlp_alloc() {
+    mlp_master.ensure_n<float>(MLP_NPARAM);
+    mlp_m.ensure_n<float>(MLP_NPARAM);
+    mlp_v.ensure_n<float>(MLP_NPARAM);
+    mlp_grad.ensure_n<float>(MLP_NPARAM);
+    mlp_b16.ensure_n<uint16_t>(1024 + 2 * 16384 + 128);
+    mlp_loss.ensure_n<float>(1);
+  }
+  // new master weights: Adam state cleared, BF16 copies refreshed
+  void mlp_load(const float* host) {
+    mlp_alloc();
+    h2d(mlp_master.as<float>(), host, MLP_NPARAM, st);
+    IA_CUDA(cudaMemsetAsync(mlp_m.p, 0, MLP_NPARAM * sizeof(float), st));
+    IA_CUDA(cudaMemsetAsync(mlp_v.p, 0, MLP_NPARAM * sizeof(float), st));
+    IA_CUDA(cudaMemsetAsync(mlp_grad.p, 0, MLP_NPARAM * sizeof(float), st));
+    mlp_refresh_copies(mlp_dev(), st);
+    IA_CUDA(cudaStreamSynchronize(st));
+    mlp_step = 0;
+    mlp_ready = true;
+  }
+
+  // Kept candidates for introspection (option keep_candidates): per node gid.
+  struct Kept {
+    int64_t off = -1;
+    int n = 0, n_samp = 0, chosen = -1;
+    double err_plain = 0, err_learned = 0;
+  };
+  std::vector<Kept> kept;
+  std::vector<int> kept_cand;
+  std::vector<uint16_t> kept_feat;
+  std::vector<float> kept_val;
+  void keep_step(const StepLists& L, const std::vector<LearnNodeInfo>& li, int64_t tot, const float* val) {
+    if (!opt.keep_candidates || tot == 0) return;
+    const int64_t base = (int64_t)kept_cand.size();
+    kept_cand.resize(base + tot);
+    kept_feat.resize((base + tot) * 8);
+    kept_val.resize(base + tot);
+    d2h(kept_cand.data() + base, l_cand.as<int>(), tot, st);
+    d2h(kept_feat.data() + base * 8, l_feat.as<uint16_t>(), tot * 8, st);
+    d2h(kept_val.data() + base, val, tot, st);
+    IA_CUDA(cudaStreamSynchronize(st));
+    for (size_t e = 0; e < li.size(); ++e)
+      if (li[e].n_cand > 0) {
+        Kept& k = kept[L.gid[e]];
+        k.off = base + li[e].cand_off;
+        k.n = li[e].n_cand;
+        k.n_samp = li[e].n_samp;
+      }
+  }
+
   // a3 + a4 + a5: skeletons, heights 0 .. Hmax-1 (roots excluded); TS is the
-  // precision of the sampled blocks and of the Householder updates.
+  // precision of the sampled blocks and of the Householder updates.  With learned
+  // sampling every eligible node also takes the ID of its learned sample, and the
+  // held-out error of the two IDs picks the one it keeps.
   template <typename TS>
   void skeletonize() {
     int* kp = knn_pos.ensure_n<int>((size_t)Ntot * kappa);
@@ -735,52 +948,51 @@ class Solver {
         n.samp_off = tot;
         tot += n.nsamp;
       }
+    const bool learn = opt.sampling == 1;
+    if (learn && !mlp_ready) throw Error(IASKIT_ERR_ARG, "learned sampling needs trained or set weights");
     int* sp = samp.ensure_n<int>(std::max<int64_t>(tot, 1));
+    int* lsp = learn ? l_samp.ensure_n<int>(std::max<int64_t>(tot, 1)) : nullptr;
     int* rk = ranks.ensure_n<int>(nd.size());
+    int* rkl = learn ? l_rk.ensure_n<int>(nd.size()) : nullptr;
     IA_CUDA(cudaMemsetAsync(rk, 0, nd.size() * sizeof(int), st));
     int* sk = skel.ensure_n<int>(nd.size() * (size_t)s_max);
+    kept.assign(opt.keep_candidates ? nd.size() : 0, Kept{});
+    kept_cand.clear();
+    kept_feat.clear();
+    kept_val.clear();
     int64_t p_total = 0;
+    std::vector<int> rall(nd.size(), 0), rlrn(learn ? nd.size() : 0, 0);
     for (int hh = 0; hh < Hmax; ++hh) {
-      std::vector<int> nodes;
-      for (int g : by_height[hh])
-        if (!is_root(g)) nodes.push_back(g);
+      StepLists S;
+      sample_step(hh, samp_cap, sp, S);
+      const std::vector<int>& nodes = S.nodes;
       if (nodes.empty()) continue;
-      // sampling step: node list covering all points (problems without a node here pass)
-      std::vector<int> off;
-      std::vector<SampleNodeInfo> info;
-      {
-        size_t k = 0;
-        for (size_t q = 0; q < pr.size(); ++q) {
-          const Prob& P = pr[q];
-          const int l = P.L - hh;
-          if (l >= 1) {
-            for (int i = 0; i < (1 << l); ++i) {
-              const Node& n = nd[nodes[k++]];
-              off.push_back(n.off);
-              info.push_back(SampleNodeInfo{P.pbase, P.N, n.uid, (int)n.samp_off, 1});
-            }
-          } else {
-            off.push_back(P.pbase);
-            info.push_back(SampleNodeInfo{P.pbase, P.N, 0, 0, 0});
-          }
+      // learned proposal: candidates, features, scores, the best n_samp of each node
+      std::vector<int> lnodes;
+      std::vector<LearnNodeInfo> li;
+      int64_t ctot = 0;
+      if (learn) {
+        int max_cand = 0;
+        lnodes = learned_candidates_step(S, li, ctot, max_cand);
+        if (!lnodes.empty()) {
+          float* score = l_score.ensure_n<float>(ctot);
+          mlp_forward(l_feat.as<uint16_t>(), ctot, mlp_dev(), score, nullptr, nullptr, st);
+          perturb_scores(score, l_linfo.as<LearnNodeInfo>(), S.id, (int)S.info.size(), max_cand, opt.seed,
+                         opt.learned_temp, st);
+          learned_select(score, l_cand.as<int>(), l_linfo.as<LearnNodeInfo>(), S.id, (int)S.info.size(),
+                         max_cand, lsp, st);
+          keep_step(S, li, ctot, score);
         }
-        off.push_back(Ntot);
       }
-      const int nn = (int)info.size();
-      int* od = step_dev.ensure_n<int>(nn + 1 + (int64_t)nn * (sizeof(SampleNodeInfo) / sizeof(int)));
-      h2d(od, off.data(), nn + 1, st);
-      SampleNodeInfo* id = reinterpret_cast<SampleNodeInfo*>(od + nn + 1);
-      h2d(id, info.data(), info.size(), st);
-      sample_level(kp, Ntot, kappa, od, id, off, info, samp_cap, opt.seed, sp, status.as<int>(),
-                   samp_s, st);
-      // sampled blocks
-      const int nk = (int)nodes.size();
+      // sampled blocks and IDs: plain [0, nk), learned [nk, nk + nl)
+      const int nk = (int)nodes.size(), nl = (int)lnodes.size(), nt = nk + nl;
+      auto node_of = [&](int i) { return i < nk ? nodes[i] : lnodes[i - nk]; };
       int64_t asz = 0, pvsz = 0, max_e = 0;
       int max_r = 0, max_c = 0;
-      std::vector<int64_t> aoff(nk), poff(nk);
-      for (int i = 0; i < nk; ++i) {
-        Node& n = nd[nodes[i]];
-        n.ncols = is_leaf(nodes[i]) ? n.size : n2(nodes[i]);
+      std::vector<int64_t> aoff(nt), poff(nt);
+      for (int i = 0; i < nt; ++i) {
+        Node& n = nd[node_of(i)];
+        n.ncols = is_leaf(node_of(i)) ? n.size : n2(node_of(i));
         aoff[i] = asz;
         poff[i] = pvsz;
         asz += (int64_t)n.nsamp * n.ncols;
@@ -791,51 +1003,147 @@ class Solver {
       }
       TS* A = A_ws.ensure_n<TS>(asz);
       int* pv = piv_ws.ensure_n<int>(pvsz);
-      std::vector<KDescT<TS>> kd(nk);
-      std::vector<CpqrDescT<TS>> qd(nk);
-      for (int i = 0; i < nk; ++i) {
-        const int g = nodes[i];
+      std::vector<KDescT<TS>> kd(nt);
+      std::vector<CpqrDescT<TS>> qd(nt);
+      for (int i = 0; i < nt; ++i) {
+        const int g = node_of(i);
         Node& n = nd[g];
         KDescT<TS> k{};
-        k.rows = sp + n.samp_off;
+        k.rows = (i < nk ? sp : lsp) + n.samp_off;
         k.nrows = n.nsamp;
         k.out = A + aoff[i];
         k.ld = n.nsamp;
         k.ncols = n.ncols;
         k.diag = 0.0;
         k.scale = scale_of(g);
-        if (is_leaf(g)) {
-          k.col0 = n.off;
-        } else {
-          k.colsA = sk + (size_t)left(g) * s_max;
-          k.nA = nd[left(g)].s;
-          k.colsB = sk + (size_t)right(g) * s_max;
-        }
+        cols_of(g, k.colsA, k.colsB, k.col0, k.nA, k.ncols);
         kd[i] = k;
-        qd[i] = CpqrDescT<TS>{A + aoff[i], pv + poff[i], rk + g, n.nsamp, n.nsamp, n.ncols};
+        qd[i] = CpqrDescT<TS>{A + aoff[i], pv + poff[i], (i < nk ? rk : rkl) + g, n.nsamp, n.nsamp, n.ncols};
       }
       arena.clear();
       size_t ok = arena.push(kd), oq = arena.push(qd);
       char* base = upload_arena();
-      kernel_blocks<TS>(Xp.as<double>(), d, (const KDescT<TS>*)(base + ok), nk, max_e, st);
-      cpqr_id<TS>((const CpqrDescT<TS>*)(base + oq), nk, max_r, max_c, s_max, tol, st);
-      // ranks of this height
-      std::vector<int> rall(nd.size());
+      kernel_blocks<TS>(Xp.as<double>(), d, (const KDescT<TS>*)(base + ok), nt, max_e, st);
+      cpqr_id<TS>((const CpqrDescT<TS>*)(base + oq), nt, max_r, max_c, s_max, tol, st);
       d2h(rall.data(), rk, nd.size(), st);
+      if (nl) d2h(rlrn.data(), rkl, nd.size(), st);
       IA_CUDA(cudaStreamSynchronize(st));
       raise_status(read_status_and_clear());
-      int64_t psz = 0;
+      std::vector<int> rank_of(nt);
       double qr_flops = 0;
-      for (int i = 0; i < nk; ++i) {
-        Node& n = nd[nodes[i]];
-        n.s = rall[nodes[i]];
-        n.P_off = p_total + psz;
-        psz += (int64_t)n.s * n.ncols;
+      for (int i = 0; i < nt; ++i) {
+        const Node& n = nd[node_of(i)];
+        rank_of[i] = i < nk ? rall[node_of(i)] : rlrn[node_of(i)];
         // Householder update (dot + axpy) and norm recomputation per step, then R11^{-1} R12
-        for (int k = 0; k < n.s; ++k) qr_flops += 6.0 * (n.nsamp - k) * (double)(n.ncols - k);
-        qr_flops += (double)n.s * n.s * (n.ncols - n.s);
+        for (int k = 0; k < rank_of[i]; ++k) qr_flops += 6.0 * (n.nsamp - k) * (double)(n.ncols - k);
+        qr_flops += (double)rank_of[i] * rank_of[i] * (n.ncols - rank_of[i]);
       }
       prof().flops[pk_of<TS>(PK_CPQR)] += qr_flops;
+      // P and skeletons of every ID: straight into the final storage without learning,
+      // else into temporaries from which the chosen ID is copied
+      std::vector<int> chosen(nk);  // descriptor index kept by plain node i
+      for (int i = 0; i < nk; ++i) chosen[i] = i;
+      std::vector<int64_t> ptoff(nt);
+      int64_t ptsz = 0;
+      for (int i = 0; i < nt; ++i) {
+        ptoff[i] = ptsz;
+        ptsz += (int64_t)rank_of[i] * nd[node_of(i)].ncols;
+      }
+      double* Pt = nl ? l_Ptmp.ensure_n<double>(std::max<int64_t>(ptsz, 1)) : nullptr;
+      int* skt = nl ? l_sktmp.ensure_n<int>((size_t)nt * s_max) : nullptr;
+      if (nl) {
+        std::vector<PDescT<TS>> pd(nt);
+        for (int i = 0; i < nt; ++i) {
+          const int g = node_of(i);
+          const Node& n = nd[g];
+          PDescT<TS> pp{};
+          pp.A = A + aoff[i];
+          pp.piv = pv + poff[i];
+          pp.P = Pt + ptoff[i];
+          pp.skel = skt + (size_t)i * s_max;
+          pp.ld = n.nsamp;
+          pp.s = rank_of[i];
+          int ncols_unused;
+          cols_of(g, pp.colsA, pp.colsB, pp.col0, pp.nA, ncols_unused);
+          pp.ncols = n.ncols;
+          pd[i] = pp;
+        }
+        arena.clear();
+        size_t op = arena.push(pd);
+        base = upload_arena();
+        assemble_P<TS>((const PDescT<TS>*)(base + op), nt, max_c, st);
+        // judge: held-out rows, then both IDs' errors
+        std::vector<StreamDesc> sd(nl);
+        std::vector<int> plain_idx(nl);
+        std::vector<int> pos_of(nd.size(), -1);
+        for (int i = 0; i < nk; ++i) pos_of[nodes[i]] = i;
+        for (int j = 0; j < nl; ++j) {
+          const int g = lnodes[j];
+          const Node& n = nd[g];
+          const Prob& P = pr[n.prob];
+          sd[j] = strat_desc(g, j * NHOLD);
+          plain_idx[j] = pos_of[g];
+        }
+        int* hold = l_hold.ensure_n<int>((size_t)nl * NHOLD);
+        std::vector<JudgeDesc> jd(2 * nl);
+        int max_s = 1;
+        for (int j = 0; j < nl; ++j)
+          for (int v = 0; v < 2; ++v) {
+            const int i = v == 0 ? plain_idx[j] : nk + j;
+            const int g = lnodes[j];
+            JudgeDesc J{};
+            J.H = hold + (size_t)j * NHOLD;
+            strat_weights(g, NHOLD, J.nh_s, J.w_s, J.w_r);
+            cols_of(g, J.colsA, J.colsB, J.col0, J.nA, J.ncols);
+            J.skel = skt + (size_t)i * s_max;
+            J.s = rank_of[i];
+            J.P = Pt + ptoff[i];
+            J.scale = scale_of(g);
+            jd[2 * j + v] = J;
+            max_s = std::max(max_s, J.s);
+          }
+        arena.clear();
+        size_t os = arena.push(sd), oj = arena.push(jd);
+        base = upload_arena();
+        stream_rows((const StreamDesc*)(base + os), nl, NHOLD, opt.seed, HOLD_SALT, hold, st);
+        double* errd = l_err.ensure_n<double>((size_t)4 * nl);
+        id_judge(Xp.as<double>(), d, (const JudgeDesc*)(base + oj), 2 * nl, NHOLD, max_s, errd, st);
+        std::vector<double> err(4 * (size_t)nl);
+        d2h(err.data(), errd, err.size(), st);
+        IA_CUDA(cudaStreamSynchronize(st));
+        std::vector<ConvSeg> sseg;
+        for (int j = 0; j < nl; ++j) {
+          const double ep = err[4 * j + 1] > 0 ? err[4 * j] / err[4 * j + 1] : 0.0;
+          const double el = err[4 * j + 3] > 0 ? err[4 * j + 2] / err[4 * j + 3] : 0.0;
+          const bool take = el <= ep;
+          const Node& n = nd[lnodes[j]];
+          if (take) {
+            chosen[plain_idx[j]] = nk + j;
+            sseg.push_back(ConvSeg{n.samp_off, n.samp_off, n.nsamp});
+            ++stats.learned_nodes;
+          } else {
+            ++stats.fallback_nodes;
+          }
+          stats.judge_err_plain += ep;
+          stats.judge_err_chosen += take ? el : ep;
+          ++stats.judged_nodes;
+          if (opt.keep_candidates) {
+            Kept& kk = kept[lnodes[j]];
+            kk.chosen = take ? 1 : 0;
+            kk.err_plain = ep;
+            kk.err_learned = el;
+          }
+        }
+        conv_segs<int, int>(lsp, sp, sseg);  // the kept sample of every node that took the learned one
+      }
+      int64_t psz = 0;
+      for (int i = 0; i < nk; ++i) {
+        Node& n = nd[nodes[i]];
+        n.s = rank_of[chosen[i]];
+        rall[nodes[i]] = n.s;
+        n.P_off = p_total + psz;
+        psz += (int64_t)n.s * n.ncols;
+      }
       // P storage grows by height; earlier heights are copied along when it grows
       if ((p_total + psz) * (int64_t)sizeof(double) > (int64_t)Pd.bytes) {
         DevBuf tmp;
@@ -849,35 +1157,259 @@ class Solver {
         IA_CUDA(cudaStreamSynchronize(st));
       }
       double* P = Pd.as<double>();
-      std::vector<PDescT<TS>> pd(nk);
-      for (int i = 0; i < nk; ++i) {
-        const int g = nodes[i];
-        Node& n = nd[g];
-        PDescT<TS> p{};
-        p.A = A + aoff[i];
-        p.piv = pv + poff[i];
-        p.P = P + n.P_off;
-        p.skel = sk + (size_t)g * s_max;
-        p.ld = n.nsamp;
-        p.ncols = n.ncols;
-        p.s = n.s;
-        if (is_leaf(g)) {
-          p.col0 = n.off;
-        } else {
-          p.colsA = sk + (size_t)left(g) * s_max;
-          p.nA = nd[left(g)].s;
-          p.colsB = sk + (size_t)right(g) * s_max;
+      if (nl) {
+        std::vector<ConvSeg> pseg, kseg;
+        for (int i = 0; i < nk; ++i) {
+          const Node& n = nd[nodes[i]];
+          pseg.push_back(ConvSeg{ptoff[chosen[i]], n.P_off, (int64_t)n.s * n.ncols});
+          kseg.push_back(ConvSeg{(int64_t)chosen[i] * s_max, (int64_t)nodes[i] * s_max, n.s});
         }
-        pd[i] = p;
+        conv_segs<double, double>(Pt, P, pseg);
+        conv_segs<int, int>(skt, sk, kseg);
+        h2d(rk, rall.data(), nd.size(), st);
+      } else {
+        std::vector<PDescT<TS>> pd(nk);
+        for (int i = 0; i < nk; ++i) {
+          const int g = nodes[i];
+          Node& n = nd[g];
+          PDescT<TS> pp{};
+          pp.A = A + aoff[i];
+          pp.piv = pv + poff[i];
+          pp.P = P + n.P_off;
+          pp.skel = sk + (size_t)g * s_max;
+          pp.ld = n.nsamp;
+          pp.s = n.s;
+          int ncols_unused;
+          cols_of(g, pp.colsA, pp.colsB, pp.col0, pp.nA, ncols_unused);
+          pp.ncols = n.ncols;
+          pd[i] = pp;
+        }
+        arena.clear();
+        size_t op = arena.push(pd);
+        base = upload_arena();
+        assemble_P<TS>((const PDescT<TS>*)(base + op), nk, max_c, st);
       }
-      arena.clear();
-      size_t op = arena.push(pd);
-      base = upload_arena();
-      assemble_P<TS>((const PDescT<TS>*)(base + op), nk, max_c, st);
       p_total += psz;
       stats.bytes_P += psz * 8;
     }
     if (prec == PREC_MIXED && p_total > 0) convert_d2f(Pd.as<double>(), Pf.ensure_n<float>(p_total), p_total, st);
+  }
+
+  // ------------------------------------------------------- sampler training
+  // Labels for every node of a training problem, then Adam epochs on the MLP.  The
+  // problem is factored in FP64 with plain sampling (lambda = 1); that factorization
+  // stays current.  Per height, for each node with a learned candidate set: B = K(gram
+  // rows, cols) over NGRAM stratified rows and its transpose, G = B^T diag(w) B + mu I,
+  // the LU of G, and the candidates' ridge leverage b_c^T G^{-1} b_c as standardized
+  // log targets.
+  void train_sampler(const double* Xh, int64_t N, int d_, double h, int leaf_m, int s_max_, double tol_,
+                     int epochs, double lr) {
+    if (epochs < 0 || epochs > 100000) throw Error(IASKIT_ERR_ARG, "invalid epochs");
+    if (!(lr > 0.0) || !std::isfinite(lr)) throw Error(IASKIT_ERR_ARG, "invalid learning rate");
+    const Options saved = opt;
+    opt.sampling = 0;
+    opt.precision = PREC_FP64;
+    try {
+      factor({ProbIn{Xh, N, h, 1.0}}, false, false, d_, leaf_m, s_max_, tol_);
+    } catch (...) {
+      opt = saved;
+      throw;
+    }
+    opt = saved;
+    const int samp_cap = opt.samp_factor * s_max;
+    kept.assign(opt.keep_candidates ? nd.size() : 0, Kept{});
+    kept_cand.clear();
+    kept_feat.clear();
+    kept_val.clear();
+    const double tol2 = tol > 0 ? tol * tol : 1e-12;
+    int64_t rows = 0;
+    // first pass: candidate counts per height for the training arrays
+    std::vector<int64_t> per_h(Hmax, 0);
+    for (int hh = 0; hh < Hmax; ++hh)
+      for (int g : by_height[hh]) {
+        if (is_root(g)) continue;
+        const Node& n = nd[g];
+        const int comp = pr[n.prob].N - n.size;
+        if (n.nsamp > 0 && n.nsamp < comp) per_h[hh] += std::min<int64_t>((int64_t)opt.cand_factor * n.nsamp, comp);
+      }
+    const int64_t total = std::accumulate(per_h.begin(), per_h.end(), (int64_t)0);
+    if (total == 0) throw Error(IASKIT_ERR_ARG, "training problem has no node with a candidate set");
+    if (total > (int64_t)INT_MAX / 8) throw Error(IASKIT_ERR_UNSUPPORTED, "training set too large");
+    uint16_t* TF = tr_feat.ensure_n<uint16_t>(total * 8);
+    float* TT = tr_tgt.ensure_n<float>(total);
+    double* TL = tr_lev.ensure_n<double>(total);
+    for (int hh = 0; hh < Hmax; ++hh) {
+      if (per_h[hh] == 0) continue;
+      StepLists S;
+      sample_step(hh, samp_cap, samp.as<int>(), S);
+      std::vector<LearnNodeInfo> li;
+      int64_t ctot = 0;
+      int max_cand = 0;
+      const std::vector<int> lnodes = learned_candidates_step(S, li, ctot, max_cand);
+      IA_CUDA(cudaMemcpyAsync(TF + rows * 8, l_feat.p, ctot * 8 * sizeof(uint16_t), cudaMemcpyDeviceToDevice, st));
+      // node -> its candidate range inside this step
+      std::vector<int> cand_off(nd.size(), -1), ncand(nd.size(), 0);
+      for (size_t e = 0; e < li.size(); ++e)
+        if (li[e].n_cand > 0) {
+          cand_off[S.gid[e]] = li[e].cand_off;
+          ncand[S.gid[e]] = li[e].n_cand;
+        }
+      // nodes in chunks of at most ~4e8 doubles of dense blocks
+      size_t j0 = 0;
+      while (j0 < lnodes.size()) {
+        size_t j1 = j0;
+        int64_t dsz = 0;
+        while (j1 < lnodes.size()) {
+          const Node& n = nd[lnodes[j1]];
+          const int64_t need = 2 * (int64_t)n.ncols * NGRAM + (int64_t)n.ncols * n.ncols +
+                               2 * (int64_t)n.ncols * ncand[lnodes[j1]];
+          if (j1 > j0 && dsz + need > (int64_t)400000000) break;
+          dsz += need;
+          ++j1;
+        }
+        const int nl = (int)(j1 - j0);
+        std::vector<ColsDesc> cd(nl);
+        std::vector<StreamDesc> sd(nl);
+        int64_t csz = 0;
+        std::vector<int64_t> coff(nl), boff(nl), toff(nl), goff(nl), c1off(nl), c2off(nl);
+        int64_t o = 0;
+        int max_nc = 0, max_ncand = 0;
+        int64_t max_bt = 0, max_b = 0, max_c = 0;
+        for (int j = 0; j < nl; ++j) {
+          const int g = lnodes[j0 + j];
+          const Node& n = nd[g];
+          const Prob& P = pr[n.prob];
+          ColsDesc c{};
+          int nc;
+          cols_of(g, c.colsA, c.colsB, c.col0, c.nA, nc);
+          c.ncols = nc;
+          c.out_off = (int)csz;
+          cd[j] = c;
+          coff[j] = csz;
+          csz += nc;
+          sd[j] = strat_desc(g, j * NGRAM);
+          toff[j] = o;  o += (int64_t)nc * NGRAM;   // K(cols, gram), nc x NGRAM
+          boff[j] = o;  o += (int64_t)nc * NGRAM;   // K(gram, cols), NGRAM x nc
+          goff[j] = o;  o += (int64_t)nc * nc;      // G
+          c1off[j] = o; o += (int64_t)nc * ncand[g];
+          c2off[j] = o; o += (int64_t)nc * ncand[g];
+          max_nc = std::max(max_nc, nc);
+          max_ncand = std::max(max_ncand, ncand[g]);
+          max_bt = std::max<int64_t>(max_bt, (int64_t)nc * NGRAM);
+          max_c = std::max<int64_t>(max_c, (int64_t)nc * ncand[g]);
+        }
+        max_b = max_bt;
+        int* cols = l_cols.ensure_n<int>(std::max<int64_t>(csz, 1));
+        int* gram = l_gram.ensure_n<int>((size_t)nl * NGRAM);
+        double* D = l_dense.ensure_n<double>(std::max<int64_t>(o, 1));
+        int* gpiv = piv_ws.ensure_n<int>((size_t)nl * max_nc);
+        std::vector<KDesc> kt, kb, kc;
+        std::vector<GemmDesc> gg;
+        std::vector<RidgeDesc> rd;
+        std::vector<LuDesc> ld;
+        std::vector<LuSolveDesc> ls;
+        std::vector<LevDesc> lv;
+        std::vector<RowScaleDesc> rs;
+        for (int j = 0; j < nl; ++j) {
+          const int g = lnodes[j0 + j];
+          const Node& n = nd[g];
+          const int nc = cd[j].ncols, nca = ncand[g];
+          const double sc = scale_of(g);
+          KDesc a{};
+          a.rows = cols + coff[j]; a.nrows = nc; a.colsA = gram + (size_t)j * NGRAM; a.nA = NGRAM;
+          a.ncols = NGRAM; a.out = D + toff[j]; a.ld = nc; a.scale = sc;
+          kt.push_back(a);
+          KDesc b{};
+          b.rows = gram + (size_t)j * NGRAM; b.nrows = NGRAM; b.colsA = cols + coff[j]; b.nA = nc;
+          b.ncols = nc; b.out = D + boff[j]; b.ld = NGRAM; b.scale = sc;
+          kb.push_back(b);
+          for (int rep = 0; rep < 2; ++rep) {
+            KDesc c{};
+            c.rows = cols + coff[j]; c.nrows = nc; c.colsA = l_cand.as<int>() + cand_off[g]; c.nA = nca;
+            c.ncols = nca; c.out = D + (rep ? c2off[j] : c1off[j]); c.ld = nc; c.scale = sc;
+            kc.push_back(c);
+          }
+          int cs;
+          double ws, wr;
+          strat_weights(g, NGRAM, cs, ws, wr);
+          rs.push_back(RowScaleDesc{D + boff[j], NGRAM, nc, NGRAM, cs, ws, wr});
+          gg.push_back(GemmDesc{D + toff[j], D + boff[j], D + goff[j], nc, nc, NGRAM, nc, NGRAM, nc, 1.0, 0.0});
+          rd.push_back(RidgeDesc{D + goff[j], nc});
+          ld.push_back(LuDesc{D + goff[j], gpiv + (size_t)j * max_nc, nc, nc});
+          ls.push_back(LuSolveDesc{D + goff[j], gpiv + (size_t)j * max_nc, D + c1off[j], nc, nc, nc, nca});
+          lv.push_back(LevDesc{D + c2off[j], D + c1off[j], nc, nca, (int)(rows + cand_off[g])});
+        }
+        arena.clear();
+        const size_t ocd = arena.push(cd), osd = arena.push(sd), okt = arena.push(kt), okb = arena.push(kb),
+                     okc = arena.push(kc), ors = arena.push(rs);
+        char* base = upload_arena();
+        gather_cols((const ColsDesc*)(base + ocd), nl, cols, st);
+        stream_rows((const StreamDesc*)(base + osd), nl, NGRAM, opt.seed, GRAM_SALT, gram, st);
+        kernel_blocks<double>(Xp.as<double>(), d, (const KDesc*)(base + okt), nl, max_bt, st);
+        kernel_blocks<double>(Xp.as<double>(), d, (const KDesc*)(base + okb), nl, max_b, st);
+        kernel_blocks<double>(Xp.as<double>(), d, (const KDesc*)(base + okc), 2 * nl, max_c, st);
+        scale_rows((const RowScaleDesc*)(base + ors), nl, st);  // B <- diag(w) B
+        run_gemms(gg);  // its own upload is stream-ordered after the launches above
+        arena.clear();
+        const size_t ord2 = arena.push(rd), old2 = arena.push(ld), ols2 = arena.push(ls), olv2 = arena.push(lv);
+        base = upload_arena();
+        add_ridge((const RidgeDesc*)(base + ord2), nl, tol2, st);
+        prof().flops[PK_GETRF] += getrf_flops(ld);
+        getrf_batched<double>((const LuDesc*)(base + old2), nl, max_nc, status.as<int>(), st);
+        prof().flops[PK_GETRS] += getrs_flops(ls);
+        getrs_batched<double>((const LuSolveDesc*)(base + ols2), nl, max_nc, max_ncand, st);
+        leverage_targets((const LevDesc*)(base + olv2), nl, TL, TT, st);
+        IA_CUDA(cudaStreamSynchronize(st));
+        raise_status(read_status_and_clear());
+        j0 = j1;
+      }
+      keep_step(S, li, ctot, TT + rows);
+      rows += ctot;
+    }
+    stats.train_rows = rows;
+    // training
+    if (!mlp_ready) {
+      std::vector<float> w0(MLP_NPARAM, 0.0f);
+      std::mt19937_64 gen(opt.seed ^ 0x5EEDull);
+      std::uniform_real_distribution<double> u1(-std::sqrt(6.0 / MLP_F), std::sqrt(6.0 / MLP_F));
+      std::uniform_real_distribution<double> u2(-std::sqrt(6.0 / MLP_W), std::sqrt(6.0 / MLP_W));
+      for (int e = MLP_OFF_W1; e < MLP_OFF_B1; ++e) w0[e] = (float)u1(gen);
+      for (int e = MLP_OFF_W2; e < MLP_OFF_B2; ++e) w0[e] = (float)u2(gen);
+      for (int e = MLP_OFF_W3; e < MLP_OFF_B3; ++e) w0[e] = (float)u2(gen);
+      mlp_load(w0.data());
+    }
+    const int B = std::max(1, std::min<int>(opt.train_batch, (int)std::min<int64_t>(rows, INT_MAX)));
+    uint16_t* bx = tr_bx.ensure_n<uint16_t>((size_t)B * 8);
+    float* bt = tr_bt.ensure_n<float>(B);
+    float* by = tr_y.ensure_n<float>(B);
+    uint16_t* H1 = tr_H1.ensure_n<uint16_t>((size_t)B * MLP_W);
+    uint16_t* H2 = tr_H2.ensure_n<uint16_t>((size_t)B * MLP_W);
+    int* idx = tr_idx.ensure_n<int>(rows);
+    std::vector<int> perm_h(rows);
+    std::iota(perm_h.begin(), perm_h.end(), 0);
+    std::mt19937_64 gen(opt.seed ^ 0x5A4D1Eull);
+    stats.train_loss.clear();
+    const MlpDev w = mlp_dev();
+    for (int ep = 0; ep < epochs; ++ep) {
+      std::shuffle(perm_h.begin(), perm_h.end(), gen);
+      h2d(idx, perm_h.data(), rows, st);
+      IA_CUDA(cudaMemsetAsync(mlp_loss.p, 0, sizeof(float), st));
+      int nb = 0;
+      for (int64_t r0 = 0; r0 < rows; r0 += B) {
+        const int nbt = (int)std::min<int64_t>(B, rows - r0);
+        gather_train(TF, TT, idx + r0, nbt, bx, bt, st);
+        mlp_forward(bx, nbt, w, by, H1, H2, st);
+        mlp_backward(bx, H1, H2, by, bt, nbt, 1.0 / nbt, w, mlp_grad.as<float>(), mlp_loss.as<float>(), st);
+        mlp_adam(w, mlp_grad.as<float>(), mlp_m.as<float>(), mlp_v.as<float>(), ++mlp_step, lr, 0.9, 0.999,
+                 1e-8, st);
+        ++nb;
+      }
+      float loss = 0.0f;
+      d2h(&loss, mlp_loss.as<float>(), 1, st);
+      IA_CUDA(cudaStreamSynchronize(st));
+      stats.train_loss.push_back(loss / std::max(nb, 1));
+    }
+    IA_CUDA(cudaStreamSynchronize(st));
   }
 
   // a4 + a6: leaf LU of lambda I + K_aa, in each problem's precision.  The mixed form
@@ -1421,7 +1953,11 @@ class Solver {
                      &piv_ws, &A_ws, &status, &arena_dev, &step_dev, &tbuf, &vbuf, &vbuf32,
                      &ubuf, &rbuf, &wt, &io, &normbuf, &blocks_dev, &LU, &LUpiv, &Wb, &Zb, &Zpiv,
                      &Cb, &LU32, &Wb32, &Zb32, &Cb32, &tbuf32, &Kleaf, &Ustore, &Pd, &Pf,
-                     &gseg_dev, &kryl, &kzb, &coefbuf, &cseg_dev, &rowsum};
+                     &gseg_dev, &kryl, &kzb, &coefbuf, &cseg_dev, &rowsum, &l_cand, &l_hits,
+                     &l_feat, &l_score, &l_linfo, &l_samp, &l_rk, &l_Ptmp, &l_sktmp, &l_hold, &l_err,
+                     &l_cols, &l_gram, &l_dense, &mlp_master, &mlp_m, &mlp_v, &mlp_grad, &mlp_b16,
+                     &mlp_loss, &tr_feat, &tr_tgt, &tr_lev, &tr_bx, &tr_bt, &tr_y, &tr_H1, &tr_H2, &tr_idx};
+    mlp_ready = false;
     for (DevBuf* b : all) b->release();
     tree_s.release();
     knn_s.release();
@@ -1623,6 +2159,17 @@ int iaskit_set_option(const char* key, double value) {
     } else if (k == "mixed_cond_max") {
       if (!(value >= 1.0)) throw Error(IASKIT_ERR_ARG, "invalid mixed_cond_max");
       o.mixed_cond_max = value;
+    } else if (k == "sampling") {
+      o.sampling = as_int(0, 1);
+    } else if (k == "cand_factor") {
+      o.cand_factor = as_int(2, 64);
+    } else if (k == "keep_candidates") {
+      o.keep_candidates = as_int(0, 1);
+    } else if (k == "train_batch") {
+      o.train_batch = as_int(64, 1 << 20);
+    } else if (k == "learned_temp") {
+      if (!(value >= 0.0) || !std::isfinite(value)) throw Error(IASKIT_ERR_ARG, "invalid learned_temp");
+      o.learned_temp = value;
     } else if (k == "profile") {
       int v = as_int(0, 1);
       IA_CUDA(cudaStreamSynchronize(S().st));
@@ -1647,6 +2194,11 @@ int iaskit_get_option(const char* key, double* value) {
     else if (k == "precision") *value = o.precision;
     else if (k == "problem") *value = o.problem;
     else if (k == "mixed_cond_max") *value = o.mixed_cond_max;
+    else if (k == "sampling") *value = o.sampling;
+    else if (k == "cand_factor") *value = o.cand_factor;
+    else if (k == "keep_candidates") *value = o.keep_candidates;
+    else if (k == "train_batch") *value = o.train_batch;
+    else if (k == "learned_temp") *value = o.learned_temp;
     else throw Error(IASKIT_ERR_ARG, "unknown option " + k);
   });
 }
@@ -1680,6 +2232,19 @@ int iaskit_stats(char* buf, size_t len) {
   snprintf(tmp, sizeof tmp, "],\"refine_iters\":%d,\"refine_stagnated\":%d,\"fp64_problems\":%d,",
            s.stats.refine_iters, s.stats.refine_stagnated, s.stats.fp64_problems);
   j += tmp;
+  snprintf(tmp, sizeof tmp,
+           "\"learned_nodes\":%d,\"fallback_nodes\":%d,\"judge_err_plain\":%.6g,\"judge_err_chosen\":%.6g,"
+           "\"train_rows\":%lld,\"train_loss\":[",
+           s.stats.learned_nodes, s.stats.fallback_nodes,
+           s.stats.judged_nodes ? s.stats.judge_err_plain / s.stats.judged_nodes : 0.0,
+           s.stats.judged_nodes ? s.stats.judge_err_chosen / s.stats.judged_nodes : 0.0,
+           (long long)s.stats.train_rows);
+  j += tmp;
+  for (size_t i = 0; i < s.stats.train_loss.size(); ++i) {
+    snprintf(tmp, sizeof tmp, "%s%.6g", i ? "," : "", s.stats.train_loss[i]);
+    j += tmp;
+  }
+  j += "],";
   j += "\"cond_est\":[";
   for (size_t q = 0; q < s.pr.size() && s.factored; ++q) {
     snprintf(tmp, sizeof tmp, "%s%.4g", q ? "," : "", std::min(s.pr[q].cond_est, 1e300));
@@ -1802,6 +2367,123 @@ int iaskit_get_P(int level, int index, double* out, int64_t cap) {
     if (cap < n) throw Error(IASKIT_ERR_ARG, "buffer too small");
     d2h(out, s.Pd.as<double>() + s.nd[g].P_off, n, s.st);
     IA_CUDA(cudaStreamSynchronize(s.st));
+  });
+  return rc == IASKIT_OK ? nc : rc;
+}
+
+int iaskit_sampler_train(const double* points, int64_t N, int d, double h, int leaf_m, int s_max,
+                         double tol, int epochs, double lr) {
+  return guarded([&] {
+    if (!points) throw Error(IASKIT_ERR_ARG, "points is null");
+    S().train_sampler(points, N, d, h, leaf_m, s_max, tol, epochs, lr);
+  });
+}
+
+int iaskit_sampler_set_weights(const float* w, int n) {
+  return guarded([&] {
+    if (!w || n != MLP_NPARAM) throw Error(IASKIT_ERR_ARG, "weights must hold 17793 floats");
+    for (int i = 0; i < n; ++i)
+      if (!std::isfinite(w[i])) throw Error(IASKIT_ERR_INPUT, "non-finite weight");
+    S().mlp_load(w);
+  });
+}
+
+int iaskit_sampler_get_weights(float* w, int n) {
+  return guarded([&] {
+    Solver& s = S();
+    if (!w || n != MLP_NPARAM) throw Error(IASKIT_ERR_ARG, "weights must hold 17793 floats");
+    if (!s.mlp_ready) throw Error(IASKIT_ERR_NOT_FACTORED, "the sampler has no weights");
+    d2h(w, s.mlp_master.as<float>(), n, s.st);
+    IA_CUDA(cudaStreamSynchronize(s.st));
+  });
+}
+
+namespace {
+// round to nearest even BF16, NaN kept quiet
+uint16_t host_bf16(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u && (u & 0x007fffffu)) return (uint16_t)((u >> 16) | 0x40u);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+void upload_features(Solver& s, const float* feats, int64_t n, uint16_t* dst) {
+  std::vector<uint16_t> hb((size_t)n * MLP_F);
+  for (size_t i = 0; i < hb.size(); ++i) hb[i] = host_bf16(feats[i]);
+  h2d(dst, hb.data(), hb.size(), s.st);
+}
+}  // namespace
+
+int iaskit_mlp_forward(const float* feats, int64_t n, float* scores) {
+  return guarded([&] {
+    Solver& s = S();
+    if (!feats || !scores || n < 1 || n > ((int64_t)1 << 28)) throw Error(IASKIT_ERR_ARG, "bad arguments");
+    if (!s.mlp_ready) throw Error(IASKIT_ERR_NOT_FACTORED, "the sampler has no weights");
+    uint16_t* X = s.tr_bx.ensure_n<uint16_t>((size_t)n * MLP_F);
+    float* y = s.tr_y.ensure_n<float>(n);
+    upload_features(s, feats, n, X);
+    mlp_forward(X, n, s.mlp_dev(), y, nullptr, nullptr, s.st);
+    d2h(scores, y, n, s.st);
+    IA_CUDA(cudaStreamSynchronize(s.st));
+  });
+}
+
+int iaskit_mlp_train_step(const float* feats, const float* targets, int64_t n, double lr, float* grad,
+                          float* loss) {
+  return guarded([&] {
+    Solver& s = S();
+    if (!feats || !targets || n < 1 || n > ((int64_t)1 << 24) || !(lr >= 0.0))
+      throw Error(IASKIT_ERR_ARG, "bad arguments");
+    if (!s.mlp_ready) throw Error(IASKIT_ERR_NOT_FACTORED, "the sampler has no weights");
+    uint16_t* X = s.tr_bx.ensure_n<uint16_t>((size_t)n * MLP_F);
+    float* t = s.tr_bt.ensure_n<float>(n);
+    float* y = s.tr_y.ensure_n<float>(n);
+    uint16_t* H1 = s.tr_H1.ensure_n<uint16_t>((size_t)n * MLP_W);
+    uint16_t* H2 = s.tr_H2.ensure_n<uint16_t>((size_t)n * MLP_W);
+    upload_features(s, feats, n, X);
+    h2d(t, targets, n, s.st);
+    IA_CUDA(cudaMemsetAsync(s.mlp_loss.p, 0, sizeof(float), s.st));
+    const MlpDev w = s.mlp_dev();
+    mlp_forward(X, n, w, y, H1, H2, s.st);
+    mlp_backward(X, H1, H2, y, t, n, 1.0 / n, w, s.mlp_grad.as<float>(), s.mlp_loss.as<float>(), s.st);
+    if (grad) d2h(grad, s.mlp_grad.as<float>(), MLP_NPARAM, s.st);
+    if (loss) d2h(loss, s.mlp_loss.as<float>(), 1, s.st);
+    mlp_adam(w, s.mlp_grad.as<float>(), s.mlp_m.as<float>(), s.mlp_v.as<float>(), ++s.mlp_step, lr, 0.9,
+             0.999, 1e-8, s.st);
+    IA_CUDA(cudaStreamSynchronize(s.st));
+  });
+}
+
+int iaskit_get_learned(int level, int index, int32_t* cand, float* feat, float* value, int cap,
+                       double* info) {
+  int nc = 0;
+  int rc = guarded([&] {
+    require_factored();
+    Solver& s = S();
+    const int g = check_node(level, index);
+    const Prob& P = selected_problem();
+    if (s.kept.empty()) throw Error(IASKIT_ERR_ARG, "candidates were not kept (option keep_candidates)");
+    const Solver::Kept& k = s.kept[g];
+    nc = k.n;
+    if (info) {
+      info[0] = k.err_plain;
+      info[1] = k.err_learned;
+      info[2] = k.chosen;
+      info[3] = k.n_samp;
+    }
+    if (k.off < 0) return;
+    if (cap < nc) throw Error(IASKIT_ERR_ARG, "buffer too small");
+    for (int i = 0; i < nc; ++i) {
+      if (cand) cand[i] = s.kept_cand[k.off + i] - P.pbase;
+      if (value) value[i] = s.kept_val[k.off + i];
+      if (feat)
+        for (int q = 0; q < MLP_F; ++q) {
+          const uint32_t u = (uint32_t)s.kept_feat[(k.off + i) * MLP_F + q] << 16;
+          float f;
+          std::memcpy(&f, &u, 4);
+          feat[(size_t)i * MLP_F + q] = f;
+        }
+    }
   });
   return rc == IASKIT_OK ? nc : rc;
 }

@@ -158,11 +158,32 @@ def test_heldout_error_exact_and_trivial_cases():
     Xp = rng.random((20, 3))
     Xp[5] = Xp[4]                                      # duplicate point: identical columns
     H, cols = np.arange(10, 20), np.array([4, 5, 6])
-    assert L.heldout_error(Xp, H, cols, cols, np.eye(3), 0.7) == 0.0
-    assert L.heldout_error(Xp, H, cols, cols, np.zeros((3, 3)), 0.7) == pytest.approx(1.0)
+    w = rng.random(10) + 0.5
+    assert L.heldout_error(Xp, H, w, cols, cols, np.eye(3), 0.7) == 0.0
+    assert L.heldout_error(Xp, H, w, cols, cols, np.zeros((3, 3)), 0.7) == pytest.approx(1.0)
     P = np.array([[1.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
-    assert L.heldout_error(Xp, H, cols, np.array([4, 6]), P, 0.7) < 1e-30
-    assert L.heldout_error(Xp, H, cols, np.array([4]), P[:1], 0.7) > 1e-3
+    assert L.heldout_error(Xp, H, w, cols, np.array([4, 6]), P, 0.7) < 1e-30
+    assert L.heldout_error(Xp, H, w, cols, np.array([4]), P[:1], 0.7) > 1e-3
+    # weights act per row: a row of weight 2 counts as that row taken twice
+    H2, w2 = np.concatenate([H, H[:1]]), np.concatenate([w, [w[0]]])
+    w1 = w.copy()
+    w1[0] *= 2
+    Q = np.array([[0.9, 1.1, 0.2]])
+    assert L.heldout_error(Xp, H2, w2, cols, np.array([4]), Q, 0.7) == pytest.approx(
+        L.heldout_error(Xp, H, w1, cols, np.array([4]), Q, 0.7), rel=1e-12)
+
+
+def test_stratified_rows_strata_and_weights():
+    N, par_o, par_n = 100, 40, 20            # parent [40, 60): alpha [40, 50), sibling [50, 60)
+    rows, w = L.stratified_rows(50, 10, par_o, par_n, N, 4000, seed=2, salt=L.HOLD_SALT, uid=9)
+    assert np.all((rows[:2000] >= 50) & (rows[:2000] < 60))
+    far = rows[2000:]
+    assert np.all((far < 40) | (far >= 60))
+    assert np.unique(far).size == 80 and np.unique(rows[:2000]).size == 10
+    assert w.sum() == pytest.approx(10 + 80)  # each stratum's weights sum to its size
+    # parent = the whole problem: all rows from the sibling
+    rows, w = L.stratified_rows(0, 50, 0, 100, 100, 64, seed=2, salt=L.HOLD_SALT, uid=3)
+    assert np.all(rows < 50) and w.sum() == pytest.approx(50)
 
 
 def test_leverage_labels_sum_to_the_effective_rank():
@@ -170,9 +191,24 @@ def test_leverage_labels_sum_to_the_effective_rank():
     Xp = rng.random((80, 2))
     cols = np.arange(10)
     rest = np.arange(10, 80)
-    lev, t = L.leverage_labels(Xp, rest, cols, rest, h=0.5, tol=1e-3, comp=rest.size)
+    lev, t = L.leverage_labels(Xp, rest, cols, rest, np.ones(rest.size), h=0.5, tol=1e-3)
     B = L.gaussian_kernel(Xp[rest], Xp[cols], 0.5)
     s = np.linalg.svd(B, compute_uv=False)
     mu = 1e-6 * float((s ** 2).sum())
     assert lev.sum() == pytest.approx(float((s ** 2 / (s ** 2 + mu)).sum()), rel=1e-6)
     assert t.mean() == pytest.approx(0.0, abs=1e-12) and t.std() == pytest.approx(1.0)
+
+
+def test_gumbel_keys_sample_proportionally_to_exp_score():
+    scores = np.log(np.array([1.0, 2.0, 3.0]))
+    assert np.array_equal(L.gumbel_keys(scores, 1, 5, 0.0), scores.astype(np.float32))
+    wins = np.zeros(3)
+    for uid in range(6000):
+        wins[int(np.argmax(L.gumbel_keys(scores, 1, uid, 1.0)))] += 1
+    np.testing.assert_allclose(wins / 6000, [1 / 6, 2 / 6, 3 / 6], atol=0.025)
+    # temperature 2 flattens to weights ~ sqrt(1), sqrt(2), sqrt(3)
+    wins[:] = 0
+    for uid in range(6000):
+        wins[int(np.argmax(L.gumbel_keys(scores, 2, uid, 2.0)))] += 1
+    p = np.sqrt([1.0, 2.0, 3.0])
+    np.testing.assert_allclose(wins / 6000, p / p.sum(), atol=0.025)
