@@ -159,7 +159,7 @@ int iaskit_apply_device(const double* d_w, double* d_u, int nrhs);
  *   "cand_factor"  learned candidates per sampled row (8, 2..64)
  *   "keep_candidates" 1: keep candidates, features and scores for iaskit_get_learned (0)
  *   "train_batch"  rows per Adam step of iaskit_sampler_train (4096)
- *   "learned_temp" Gumbel temperature of the learned selection (1; 0 = top scores)
+ *   "learned_temp" Gumbel temperature of the learned selection (0 = top scores, default)
  *   "problem"      which problem of a batch the introspection calls report (0) [any time]
  * Errors: IASKIT_ERR_ARG for an unknown key or an invalid value.
  */

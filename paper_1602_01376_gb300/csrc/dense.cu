@@ -822,43 +822,50 @@ void kernel_matvec(const double* Xp, int d, int nrhs, const KMatvecDesc* descs_d
   IA_LAUNCH_CHECK();
 }
 
+// Each block sums a chunk of one sampled row in FP32 (an estimate needs no more) and
+// adds it to out in FP64.
+constexpr int RS_CHUNK = 8192;
 __global__ void __launch_bounds__(256) kernel_rowsums_kernel(const double* Xp, int d,
                                                               const RowSumDesc* descs, double* out) {
-  extern __shared__ double xi[];
-  __shared__ double part[8];
+  extern __shared__ float xi[];
+  __shared__ float part[8];
   const RowSumDesc D = descs[blockIdx.y];
-  const int i = D.pbase + (int)(((int64_t)blockIdx.x * D.N) / KROWSUM_ROWS);
-  for (int q = threadIdx.x; q < d; q += blockDim.x) xi[q] = Xp[(size_t)i * d + q];
+  const int r = blockIdx.x % KROWSUM_ROWS, chunk = blockIdx.x / KROWSUM_ROWS;
+  const int j0 = chunk * RS_CHUNK;
+  if (j0 >= D.N) return;
+  const int j1 = min(D.N, j0 + RS_CHUNK);
+  const int i = D.pbase + (int)(((int64_t)r * D.N) / KROWSUM_ROWS);
+  for (int q = threadIdx.x; q < d; q += blockDim.x) xi[q] = (float)Xp[(size_t)i * d + q];
   __syncthreads();
-  double acc = 0.0;
-  for (int j = threadIdx.x; j < D.N; j += blockDim.x) {
+  const float sc = (float)D.scale;
+  float acc = 0.0f;
+  for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
     const double* xj = Xp + (size_t)(D.pbase + j) * d;
-    double d2 = 0.0;
+    float d2 = 0.0f;
     for (int q = 0; q < d; ++q) {
-      const double t = xi[q] - xj[q];
-      d2 = fma(t, t, d2);
+      const float t = xi[q] - (float)xj[q];
+      d2 = fmaf(t, t, d2);
     }
-    acc += exp(d2 * D.scale);
+    acc += __expf(d2 * sc);
   }
-  acc = warp_sum(acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double s = 0.0;
+    float s = 0.0f;
     for (int w = 0; w < 8; ++w) s += part[w];
-    out[(size_t)blockIdx.y * KROWSUM_ROWS + blockIdx.x] = s;
+    atomicAdd(&out[(size_t)blockIdx.y * KROWSUM_ROWS + r], (double)s);
   }
 }
 
-void kernel_rowsums(const double* Xp, int d, const RowSumDesc* descs_dev, int nprob, double* out,
-                    cudaStream_t st) {
+void kernel_rowsums(const double* Xp, int d, const RowSumDesc* descs_dev, int nprob, int max_n,
+                    double* out, cudaStream_t st) {
   if (nprob <= 0) return;
-  const size_t smem = (size_t)d * sizeof(double);
-  if (smem > 48 * 1024)
-    IA_CUDA(cudaFuncSetAttribute(kernel_rowsums_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
+  const size_t smem = (size_t)d * sizeof(float);
   ProfScope _ps(PK_MISC, st);
-  kernel_rowsums_kernel<<<dim3(KROWSUM_ROWS, nprob), 256, smem, st>>>(Xp, d, descs_dev, out);
+  IA_CUDA(cudaMemsetAsync(out, 0, (size_t)nprob * KROWSUM_ROWS * sizeof(double), st));
+  const unsigned chunks = ceil_div(max_n, RS_CHUNK);
+  kernel_rowsums_kernel<<<dim3(KROWSUM_ROWS * chunks, nprob), 256, smem, st>>>(Xp, d, descs_dev, out);
   IA_LAUNCH_CHECK();
 }
 

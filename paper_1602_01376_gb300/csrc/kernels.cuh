@@ -245,15 +245,16 @@ void kernel_matvec(const double* Xp, int d, int nrhs, const KMatvecDesc* descs_d
                    int max_rows, cudaStream_t st);
 
 // Conditioning probe: out[q * KROWSUM_ROWS + r] = sum_j K(x_i, x_j) over the N points of
-// problem q, for KROWSUM_ROWS rows i spread evenly over the problem's tree order.  The
+// problem q (evaluated in FP32), for KROWSUM_ROWS rows i spread evenly over the
+// problem's tree order.  The
 // largest of them bounds ||K||_2 from below for a near-constant kernel and estimates it.
 constexpr int KROWSUM_ROWS = 64;
 struct RowSumDesc {
   int pbase, N;
   double scale;  // -1 / (2 h^2)
 };
-void kernel_rowsums(const double* Xp, int d, const RowSumDesc* descs_dev, int nprob, double* out,
-                    cudaStream_t st);
+void kernel_rowsums(const double* Xp, int d, const RowSumDesc* descs_dev, int nprob, int max_n,
+                    double* out, cudaStream_t st);
 
 // ------------------------------------------------------ learned sampling (a11)
 // MLP 8 -> 128 -> 128 -> 1 (ReLU).  FP32 master parameters, in this order:

@@ -86,7 +86,7 @@ struct Options {
   int cand_factor = 8;      // learned candidates per sampled row
   int keep_candidates = 0;  // keep candidates, features and scores for introspection
   int train_batch = 4096;
-  double learned_temp = 1.0;  // Gumbel temperature of the learned selection (0: top scores)
+  double learned_temp = 0.0;  // Gumbel temperature of the learned selection (0: top scores)
 };
 
 struct Prob {
@@ -722,7 +722,9 @@ class Solver {
     size_t o = arena.push(rd);
     char* base = upload_arena();
     double* rs = rowsum.ensure_n<double>(pr.size() * KROWSUM_ROWS);
-    kernel_rowsums(Xp.as<double>(), d, (const RowSumDesc*)(base + o), (int)pr.size(), rs, st);
+    int max_n = 0;
+    for (const Prob& P : pr) max_n = std::max(max_n, P.N);
+    kernel_rowsums(Xp.as<double>(), d, (const RowSumDesc*)(base + o), (int)pr.size(), max_n, rs, st);
     std::vector<double> hrs(pr.size() * KROWSUM_ROWS);
     d2h(hrs.data(), rs, hrs.size(), st);
     IA_CUDA(cudaStreamSynchronize(st));

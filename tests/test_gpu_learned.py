@@ -119,6 +119,7 @@ def learned_run(gpu_lib):
     ia.iaskit_sampler_set_weights(ia.mlp_pack(p))
     ia.iaskit_set_option("sampling", 1)
     ia.iaskit_set_option("keep_candidates", 1)
+    ia.iaskit_set_option("learned_temp", 1.0)     # exercise the Gumbel selection
     try:
         ia.iaskit_factor(X, h, lam, m, s_max, tol)
         st = ia.iaskit_stats()
@@ -139,6 +140,7 @@ def learned_run(gpu_lib):
     finally:
         ia.iaskit_set_option("sampling", 0)
         ia.iaskit_set_option("keep_candidates", 0)
+        ia.iaskit_set_option("learned_temp", 0.0)
     return dict(X=X, tree=tree, nodes=nodes, st=st, p=ia.mlp_unpack(ia.mlp_pack(p)), u=u, w=wsol,
                 params=(h, lam, m, s_max, tol), ia=ia)
 
