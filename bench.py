@@ -177,6 +177,19 @@ def config_of(w):
 FP32_LANES_PER_SM = 128              # GB300: FP32 FMA lanes per SM
 PEAK_CLASS = {                       # kernel classes whose arithmetic is FP32
     "kernel_blocks_f32", "cpqr_id_f32", "getrf_f32", "getrs_f32", "gemm_f32", "knn"}
+TENSOR_CLASS = {                     # tensor-core classes: nominal dense rate / bf16's
+    "mlp_bf16": (1.0, "BF16"),
+}
+
+
+def roof_peak(kernel: str, pk: dict, src: str) -> tuple:
+    """(bound, peak TFLOP/s, how) for a kernel class."""
+    if kernel in TENSOR_CLASS:
+        ratio, dt = TENSOR_CLASS[kernel]
+        return ("tensor", pk["bf16_tflops"] * ratio,
+                f"{src} bf16 {pk['bf16_tflops']:.0f} TFLOP/s x nominal {dt}/BF16 ratio {ratio:.3f}")
+    peak, how = alu_peak_tflops(kernel, pk.get("sm_max_mhz", 2070.0))
+    return ("alu", peak, f"{how} ({src} max clock)")
 
 
 def alu_peak_tflops(kernel: str, sm_mhz: float) -> tuple:
@@ -265,10 +278,10 @@ def run_batched(args, w, form):
     roof = None
     if kern[top]["flops"] > 0 and kern[top]["ms"] > 0:
         achieved = kern[top]["flops"] / (kern[top]["ms"] / 1e3) / 1e12
-        peak, how = alu_peak_tflops(top, pk.get("sm_max_mhz", 2070.0))
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        bound, peak, how = roof_peak(top, pk, src)
+        roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "kernel": top,
-                "peak_source": f"{how} ({src} max clock)", "launches": kern[top]["calls"],
+                "peak_source": how, "launches": kern[top]["calls"],
                 "ms_total": kern[top]["ms"]}
     cfg = config_of(w)
     cfg["path"] = "batched " + form
@@ -419,10 +432,10 @@ def main():
     roof = None
     if kern[top]["flops"] > 0 and kern[top]["ms"] > 0:
         achieved = kern[top]["flops"] / (kern[top]["ms"] / 1e3) / 1e12      # TFLOP/s
-        peak, how = alu_peak_tflops(top, pk.get("sm_max_mhz", 2070.0))
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        bound, peak, how = roof_peak(top, pk, src)
+        roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "kernel": top,
-                "peak_source": f"{how} ({src} max clock)",
+                "peak_source": how,
                 "launches": kern[top]["calls"], "ms_total": kern[top]["ms"]}
     st = chosen["stats"]
     cfg = config_of(w)

@@ -40,16 +40,18 @@ void permute_points(const double* X, const int* perm, int N, int d, int* iperm, 
 
 // ------------------------------------------------------------------- kNN (a2)
 struct KnnScratch {
-  DevBuf x32, cand_d, cand_i, flagged, counter, maxabs, tiles;
+  DevBuf x32, qnorm, part, mean, rmax, probs, cand_d, cand_i, flagged, counter, tiles;
   void release() {
-    for (DevBuf* b : {&x32, &cand_d, &cand_i, &flagged, &counter, &maxabs, &tiles}) b->release();
+    for (DevBuf* b : {&x32, &qnorm, &part, &mean, &rmax, &probs, &cand_d, &cand_i, &flagged, &counter,
+                      &tiles})
+      b->release();
   }
 };
 
 // Work tile of the kNN kernels: queries [q0, q0 + qn) against the points
-// [rb, rb + rn) of their problem.
+// [rb, rb + rn) of their problem `prob`.
 struct KnnTile {
-  int q0, qn, rb, rn;
+  int q0, qn, rb, rn, prob;
 };
 
 // kappa nearest neighbours of every point by (squared distance, index), self
