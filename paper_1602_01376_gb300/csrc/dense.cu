@@ -18,6 +18,7 @@
 // In FP64 these kernels are bound by the FP64 pipe (2 FMA per clock per SM on this
 // part); they keep it fed with many independent blocks.
 #include <cfloat>
+#include <type_traits>
 #include <climits>
 
 #include "kernels.cuh"
@@ -34,29 +35,68 @@ template <>
 __device__ __forceinline__ float kexp<float>(float x) { return expf(x); }
 
 // ------------------------------------------------------------ kernel blocks
+// One thread per row and group of KB_C consecutive columns, so that the row's
+// coordinates are read once per group.  FP64 blocks use the Gram form
+// |x|^2 + |y|^2 - 2 x.y with the squared norms precomputed (one FMA per coordinate;
+// the cancellation error, about 2^-52 (|x|^2 + |y|^2), moves a kernel value by a
+// relative 2^-52 (|x|^2 + |y|^2) / (2 h^2)); FP32 blocks keep the difference form,
+// whose error is relative to the distance itself.
+constexpr int KB_C = 4;
 template <typename T>
-__global__ void kernel_blocks_kernel(const double* Xp, int d, const KDescT<T>* descs, int ndesc) {
+__global__ void kernel_blocks_kernel(const double* Xp, const double* xn, int d, const KDescT<T>* descs,
+                                     int ndesc) {
   for (int q = blockIdx.y; q < ndesc; q += gridDim.y) {
     const KDescT<T> D = descs[q];
     const T scale = (T)D.scale;
-    const int64_t total = (int64_t)D.nrows * D.ncols;
+    const int ncg = (D.ncols + KB_C - 1) / KB_C;
+    const int64_t total = (int64_t)D.nrows * ncg;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-      const int i = (int)(e % D.nrows), j = (int)(e / D.nrows);
+      const int i = (int)(e % D.nrows), j0 = (int)(e / D.nrows) * KB_C;
       const int r = D.rows ? D.rows[i] : D.row0 + i;
-      const int c = D.colsA ? (j < D.nA ? D.colsA[j] : D.colsB[j - D.nA]) : D.col0 + j;
       const double* xr = Xp + (size_t)r * d;
-      const double* xc = Xp + (size_t)c * d;
-      T d2 = 0;
-      for (int k = 0; k < d; ++k) {
-        T t = (T)xr[k] - (T)xc[k];
-        d2 = fma(t, t, d2);
+      int c[KB_C];
+      const double* xc[KB_C];
+#pragma unroll
+      for (int u = 0; u < KB_C; ++u) {
+        const int j = min(j0 + u, D.ncols - 1);
+        c[u] = D.colsA ? (j < D.nA ? D.colsA[j] : D.colsB[j - D.nA]) : D.col0 + j;
+        xc[u] = Xp + (size_t)c[u] * d;
       }
-      T v = kexp<T>(d2 * scale);
-      if (r == c) v += (T)D.diag;
-      D.out[(size_t)i + (size_t)j * D.ld] = v;
+      T acc[KB_C];
+#pragma unroll
+      for (int u = 0; u < KB_C; ++u) acc[u] = 0;
+      for (int k = 0; k < d; ++k) {
+        const T a = (T)xr[k];
+#pragma unroll
+        for (int u = 0; u < KB_C; ++u) {
+          if (std::is_same<T, double>::value) {
+            acc[u] = fma(a, (T)xc[u][k], acc[u]);
+          } else {
+            const T t = a - (T)xc[u][k];
+            acc[u] = fma(t, t, acc[u]);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < KB_C; ++u) {
+        if (j0 + u >= D.ncols) break;
+        T d2 = acc[u];
+        if (std::is_same<T, double>::value) d2 = fmax((xn[r] + xn[c[u]]) - 2.0 * acc[u], 0.0);
+        T v = kexp<T>(d2 * scale);
+        if (r == c[u]) v += (T)D.diag;
+        D.out[(size_t)i + (size_t)(j0 + u) * D.ld] = v;
+      }
     }
   }
+}
+
+__global__ void row_norms_kernel(const double* Xp, int N, int d, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double s = 0.0;
+  for (int k = 0; k < d; ++k) s = fma(Xp[(size_t)i * d + k], Xp[(size_t)i * d + k], s);
+  out[i] = s;
 }
 
 // ----------------------------------------------------------------- CPQR / ID
@@ -627,15 +667,17 @@ __global__ void f2d_kernel(const float* in, double* out, int64_t n) {
 constexpr int MV_THREADS = 128;
 constexpr int MV_R = 16;
 constexpr int MV_TILE = 32;
-__global__ void __launch_bounds__(MV_THREADS) kernel_matvec_kernel(const double* Xp, int d, int nrhs,
-                                                                   const KMatvecDesc* descs) {
-  extern __shared__ double xs[];  // MV_TILE x d
+__global__ void __launch_bounds__(MV_THREADS) kernel_matvec_kernel(const double* Xp, const double* xn, int d,
+                                                                   int nrhs, const KMatvecDesc* descs) {
+  extern __shared__ double xs[];  // MV_TILE x d, then the MV_TILE column norms
+  double* xcn = xs + MV_TILE * d;
   const KMatvecDesc D = descs[blockIdx.y];
   const double neg_inv_2h2 = D.scale;
   const int i = blockIdx.x * MV_THREADS + threadIdx.x;
   const bool active = i < D.nrows;
   const int row = D.row0 + (active ? i : 0);
   const double* xr = Xp + (size_t)row * d;
+  const double xrn = xn[row];
   for (int c0 = 0; c0 < nrhs; c0 += MV_R) {
     const int nr = min(MV_R, nrhs - c0);
     double acc[MV_R];
@@ -649,14 +691,14 @@ __global__ void __launch_bounds__(MV_THREADS) kernel_matvec_kernel(const double*
         const int col = D.cols ? D.cols[k0 + kk] : D.col0 + k0 + kk;
         xs[kk * d + q] = Xp[(size_t)col * d + q];
       }
+      for (int kk = threadIdx.x; kk < nt; kk += MV_THREADS)
+        xcn[kk] = xn[D.cols ? D.cols[k0 + kk] : D.col0 + k0 + kk];
       __syncthreads();
       if (!active) continue;
       for (int kk = 0; kk < nt; ++kk) {
-        double d2 = 0.0;
-        for (int q = 0; q < d; ++q) {
-          double t = xr[q] - xs[kk * d + q];
-          d2 = fma(t, t, d2);
-        }
+        double dot = 0.0;
+        for (int q = 0; q < d; ++q) dot = fma(xr[q], xs[kk * d + q], dot);
+        const double d2 = fmax((xrn + xcn[kk]) - 2.0 * dot, 0.0);  // Gram form, as kernel_blocks
         const double kv = exp(d2 * neg_inv_2h2);
         const double* yk = D.y + (size_t)(k0 + kk) + (size_t)c0 * D.ldy;
 #pragma unroll
@@ -700,12 +742,20 @@ void launch_getrs(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int ma
 }  // namespace
 
 template <typename T>
-void kernel_blocks(const double* Xp, int d, const KDescT<T>* descs_dev, int ndesc,
+void kernel_blocks(const double* Xp, const double* xnorm, int d, const KDescT<T>* descs_dev, int ndesc,
                    int64_t max_entries, cudaStream_t st) {
   if (ndesc <= 0) return;
+  if (std::is_same<T, double>::value && !xnorm) throw Error(IASKIT_ERR_ARG, "kernel blocks need point norms");
   ProfScope _ps(pk_of<T>(PK_KBLOCK), st);
-  dim3 grid(grid_for(max_entries, 256, 4096), std::min(ndesc, 65535));
-  kernel_blocks_kernel<T><<<grid, 256, 0, st>>>(Xp, d, descs_dev, ndesc);
+  dim3 grid(grid_for((max_entries + KB_C - 1) / KB_C, 256, 4096), std::min(ndesc, 65535));
+  kernel_blocks_kernel<T><<<grid, 256, 0, st>>>(Xp, xnorm, d, descs_dev, ndesc);
+  IA_LAUNCH_CHECK();
+}
+
+void point_norms(const double* Xp, int N, int d, double* out, cudaStream_t st) {
+  if (N <= 0) return;
+  ProfScope _ps(PK_MISC, st);
+  row_norms_kernel<<<ceil_div(N, 256), 256, 0, st>>>(Xp, N, d, out);
   IA_LAUNCH_CHECK();
 }
 
@@ -809,16 +859,16 @@ void convert_f2d(const float* in, double* out, int64_t n, cudaStream_t st) {
   IA_LAUNCH_CHECK();
 }
 
-void kernel_matvec(const double* Xp, int d, int nrhs, const KMatvecDesc* descs_dev, int ndesc,
-                   int max_rows, cudaStream_t st) {
+void kernel_matvec(const double* Xp, const double* xnorm, int d, int nrhs, const KMatvecDesc* descs_dev,
+                   int ndesc, int max_rows, cudaStream_t st) {
   if (ndesc <= 0 || max_rows <= 0) return;
-  const size_t smem = (size_t)MV_TILE * d * sizeof(double);
+  const size_t smem = (size_t)MV_TILE * (d + 1) * sizeof(double);
   if (smem > 48 * 1024)
     IA_CUDA(cudaFuncSetAttribute(kernel_matvec_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
   ProfScope _ps(PK_MATVEC, st);
   dim3 grid(ceil_div(max_rows, MV_THREADS), ndesc);
-  kernel_matvec_kernel<<<grid, MV_THREADS, smem, st>>>(Xp, d, nrhs, descs_dev);
+  kernel_matvec_kernel<<<grid, MV_THREADS, smem, st>>>(Xp, xnorm, d, nrhs, descs_dev);
   IA_LAUNCH_CHECK();
 }
 
@@ -877,7 +927,8 @@ void check_finite(const double* x, int64_t n, int* dev_status, cudaStream_t st) 
 }
 
 #define IASKIT_INSTANTIATE(T)                                                                    \
-  template void kernel_blocks<T>(const double*, int, const KDescT<T>*, int, int64_t, cudaStream_t); \
+  template void kernel_blocks<T>(const double*, const double*, int, const KDescT<T>*, int, int64_t,  \
+                                 cudaStream_t);                                                  \
   template void cpqr_id<T>(const CpqrDescT<T>*, int, int, int, int, double, cudaStream_t);        \
   template void assemble_P<T>(const PDescT<T>*, int, int, cudaStream_t);                          \
   template void getrf_batched<T>(const LuDescT<T>*, int, int, int*, cudaStream_t);                \

@@ -102,7 +102,8 @@ void sample_level(const int* knn_pos, int N, int kappa, const int* off_dev,
 // Kernel block K(x_rows, x_cols) (+ diag where the row and column positions agree),
 // column-major into out.  Rows: rows ? rows[i] : row0 + i.  Columns: colsA ?
 // (j < nA ? colsA[j] : colsB[j - nA]) : col0 + j.  Points are positions in Xp.
-// T = double evaluates in FP64; T = float evaluates distances and exp in FP32.
+// T = double evaluates in FP64 (Gram form with the precomputed squared norms);
+// T = float evaluates distances (difference form) and exp in FP32.
 // scale = -1 / (2 h^2) of the block's problem.
 template <typename T>
 struct KDescT {
@@ -114,9 +115,12 @@ struct KDescT {
   double diag;
   double scale;
 };
+// xnorm: squared norms of the rows of Xp (FP64 blocks use them; may be null for FP32).
 template <typename T>
-void kernel_blocks(const double* Xp, int d, const KDescT<T>* descs_dev, int ndesc,
+void kernel_blocks(const double* Xp, const double* xnorm, int d, const KDescT<T>* descs_dev, int ndesc,
                    int64_t max_entries_per_desc, cudaStream_t st);
+// out[i] = sum_k Xp[i][k]^2 in FP64, coordinates in order.
+void point_norms(const double* Xp, int N, int d, double* out, cudaStream_t st);
 
 // Column-pivoted Householder QR + interpolative decomposition of each block.
 // A (nrows x ncols, ld) is overwritten: its first s rows hold, in pivoted column
@@ -235,7 +239,7 @@ void permute_rows(const T* in, int ldi, T* out, int ldo, const int* perm, int N,
                   bool scatter, cudaStream_t st);
 
 // u_rows += K(x_rows, x_cols) * y for each descriptor, kernel values recomputed in
-// FP64.  y is ncols x nrhs (ldy), u is nrows x nrhs (ldu) with rows starting at row0.
+// FP64 in the Gram form of kernel_blocks (xnorm: squared norms of the rows of Xp).  y is ncols x nrhs (ldy), u is nrows x nrhs (ldu) with rows starting at row0.
 struct KMatvecDesc {
   const int* cols;
   const double* y;
@@ -243,8 +247,8 @@ struct KMatvecDesc {
   int row0, nrows, col0, ncols, ldy, ldu;
   double scale;  // -1 / (2 h^2)
 };
-void kernel_matvec(const double* Xp, int d, int nrhs, const KMatvecDesc* descs_dev, int ndesc,
-                   int max_rows, cudaStream_t st);
+void kernel_matvec(const double* Xp, const double* xnorm, int d, int nrhs, const KMatvecDesc* descs_dev,
+                   int ndesc, int max_rows, cudaStream_t st);
 
 // Conditioning probe: out[q * KROWSUM_ROWS + r] = sum_j K(x_i, x_j) over the N points of
 // problem q (evaluated in FP32), for KROWSUM_ROWS rows i spread evenly over the

@@ -300,7 +300,7 @@ class Solver {
   std::vector<std::vector<int>> by_height;    // gids of each height (0 = leaves), roots included
   DevBuf X, Xp, perm, iperm, pid, knn, knn_pos, samp, ranks, skel, piv_ws, A_ws, status,
       arena_dev, step_dev, tbuf, vbuf, vbuf32, ubuf, rbuf, wt, io, normbuf, blocks_dev, gseg_dev,
-      kryl, kzb, coefbuf, cseg_dev, rowsum;
+      kryl, kzb, coefbuf, cseg_dev, rowsum, xnrm;
   // learned sampling: per-step scratch, MLP parameters and training data
   DevBuf l_cand, l_hits, l_feat, l_score, l_linfo, l_samp, l_rk, l_Ptmp, l_sktmp, l_hold, l_err,
       l_cols, l_gram, l_dense, mlp_master, mlp_m, mlp_v, mlp_grad, mlp_b16, mlp_loss, tr_feat, tr_tgt,
@@ -679,6 +679,7 @@ class Solver {
     int* pm = perm.ensure_n<int>(Ntot);
     build_tree(Xd, Ntot, d, levels, pm, tree_s, st);
     permute_points(Xd, pm, Ntot, d, iperm.ensure_n<int>(Ntot), Xp.ensure_n<double>((size_t)Ntot * d), st);
+    point_norms(Xp.as<double>(), Ntot, d, xnrm.ensure_n<double>(Ntot), st);
     choose_precisions();
     const double t1 = now_ms();
     stats.t_tree = t1 - t0;
@@ -1025,7 +1026,7 @@ class Solver {
       arena.clear();
       size_t ok = arena.push(kd), oq = arena.push(qd);
       char* base = upload_arena();
-      kernel_blocks<TS>(Xp.as<double>(), d, (const KDescT<TS>*)(base + ok), nt, max_e, st);
+      kernel_blocks<TS>(Xp.as<double>(), xnrm.as<double>(), d, (const KDescT<TS>*)(base + ok), nt, max_e, st);
       cpqr_id<TS>((const CpqrDescT<TS>*)(base + oq), nt, max_r, max_c, s_max, tol, st);
       d2h(rall.data(), rk, nd.size(), st);
       if (nl) d2h(rlrn.data(), rkl, nd.size(), st);
@@ -1347,9 +1348,9 @@ class Solver {
         char* base = upload_arena();
         gather_cols((const ColsDesc*)(base + ocd), nl, cols, st);
         stream_rows((const StreamDesc*)(base + osd), nl, NGRAM, opt.seed, GRAM_SALT, gram, st);
-        kernel_blocks<double>(Xp.as<double>(), d, (const KDesc*)(base + okt), nl, max_bt, st);
-        kernel_blocks<double>(Xp.as<double>(), d, (const KDesc*)(base + okb), nl, max_b, st);
-        kernel_blocks<double>(Xp.as<double>(), d, (const KDesc*)(base + okc), 2 * nl, max_c, st);
+        kernel_blocks<double>(Xp.as<double>(), xnrm.as<double>(), d, (const KDesc*)(base + okt), nl, max_bt, st);
+        kernel_blocks<double>(Xp.as<double>(), xnrm.as<double>(), d, (const KDesc*)(base + okb), nl, max_b, st);
+        kernel_blocks<double>(Xp.as<double>(), xnrm.as<double>(), d, (const KDesc*)(base + okc), 2 * nl, max_c, st);
         scale_rows((const RowScaleDesc*)(base + ors), nl, st);  // B <- diag(w) B
         run_gemms(gg);  // its own upload is stream-ordered after the launches above
         arena.clear();
@@ -1448,7 +1449,7 @@ class Solver {
     arena.clear();
     size_t ok = arena.push(kd);
     char* base = upload_arena();
-    kernel_blocks<double>(Xp.as<double>(), d, (const KDesc*)(base + ok), nl, (int64_t)m_max * m_max, st);
+    kernel_blocks<double>(Xp.as<double>(), xnrm.as<double>(), d, (const KDesc*)(base + ok), nl, (int64_t)m_max * m_max, st);
     float* lu32 = tot_t[0] ? LU32.ensure_n<float>(tot_t[0]) : nullptr;
     double* lu64 = blocks;
     if (mixed) {
@@ -1571,7 +1572,7 @@ class Solver {
       arena.clear();
       size_t ok = arena.push(kd);
       char* base = upload_arena();
-      kernel_blocks<double>(Xp.as<double>(), d, (const KDesc*)(base + ok), (int)kd.size(), max_e, st);
+      kernel_blocks<double>(Xp.as<double>(), xnrm.as<double>(), d, (const KDesc*)(base + ok), (int)kd.size(), max_e, st);
       if (mixed) {
         conv_segs<double, float>(U64, Wb32.as<float>(), s32);
         conv_segs<double, double>(U64, Wb.as<double>(), s64);
@@ -1938,7 +1939,7 @@ class Solver {
           arena.clear();
           size_t om = arena.push(md);
           char* base = upload_arena();
-          kernel_matvec(Xp.as<double>(), d, nrhs, (const KMatvecDesc*)(base + om), (int)md.size(),
+          kernel_matvec(Xp.as<double>(), xnrm.as<double>(), d, nrhs, (const KMatvecDesc*)(base + om), (int)md.size(),
                         max_rows, st);
         }
       }
@@ -1958,7 +1959,8 @@ class Solver {
                      &gseg_dev, &kryl, &kzb, &coefbuf, &cseg_dev, &rowsum, &l_cand, &l_hits,
                      &l_feat, &l_score, &l_linfo, &l_samp, &l_rk, &l_Ptmp, &l_sktmp, &l_hold, &l_err,
                      &l_cols, &l_gram, &l_dense, &mlp_master, &mlp_m, &mlp_v, &mlp_grad, &mlp_b16,
-                     &mlp_loss, &tr_feat, &tr_tgt, &tr_lev, &tr_bx, &tr_bt, &tr_y, &tr_H1, &tr_H2, &tr_idx};
+                     &mlp_loss, &tr_feat, &tr_tgt, &tr_lev, &tr_bx, &tr_bt, &tr_y, &tr_H1, &tr_H2, &tr_idx,
+                     &xnrm};
     mlp_ready = false;
     for (DevBuf* b : all) b->release();
     tree_s.release();
