@@ -277,7 +277,7 @@ int iaskit_get_learned(int level, int index, int32_t* cand, float* feat, float* 
  *             the work has finished.
  * Limits: 2 <= N <= 32768, 1 <= d <= 64, N*d <= 1048576, 1 <= kappa <= min(24, N-1);
  * anything larger returns IASKIT_ERR_ARG with the limit in iaskit_last_error().
- * Scratch: one static device array of about 12.4 MiB, which every GPU that loads
+ * Scratch: one static device array of about 37.3 MiB, which every GPU that loads
  * this library holds until the process exits.  The call makes no device
  * allocation.  Its first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) once; make that first call before any stream capture.

@@ -100,9 +100,9 @@ __global__ void row_norms_kernel(const double* Xp, int N, int d, double* out) {
 }
 
 // ----------------------------------------------------------------- CPQR / ID
-constexpr int QR_THREADS = 256;
+constexpr int QR_THREADS = 512;
 constexpr int QR_WARPS = QR_THREADS / 32;
-constexpr int QR_RPL = 32;  // rows per lane held in registers (columns of up to 1024 rows)
+constexpr int QR_RPL = 16;  // rows per lane held in registers (columns of up to 512 rows)
 
 __device__ void block_argmax(double& v, int& idx, double* rv, int* ri) {
   warp_argmax(v, idx);
@@ -227,34 +227,67 @@ __global__ void __launch_bounds__(QR_THREADS) cpqr_kernel(const CpqrDescT<T>* de
     __syncthreads();
     const T beta = vv > 0.0 ? (T)(2.0 / vv) : (T)0;
     const int tcount = (nr - k + 31) / 32;  // rows per lane of the trailing column
-    for (int j = k + 1 + warp; j < nc; j += QR_WARPS) {
-      T* col = A + (size_t)j * ld;
-      T dot = 0;
-      if (sizeof(T) == 4 && tcount <= QR_RPL) {
-        // FP32: the warp keeps the column in registers between the dot product and the
-        // update (FP64 is bound by its arithmetic pipe and keeps the two-pass form)
-        T x[QR_RPL];
+    if (sizeof(T) == 4 && tcount <= QR_RPL) {
+      // FP32: a warp keeps two columns in registers between the dot products and the
+      // updates, so that the two columns' loads and reductions overlap (FP64 is bound
+      // by its arithmetic pipe and keeps the two-pass form below)
+      for (int j = k + 1 + 2 * warp; j < nc; j += 2 * QR_WARPS) {
+        const bool two = j + 1 < nc;
+        T* c0 = A + (size_t)j * ld;
+        T* c1 = A + (size_t)(two ? j + 1 : j) * ld;
+        T x0[QR_RPL], x1[QR_RPL];
+        T d0 = 0, d1 = 0;
 #pragma unroll
         for (int t = 0; t < QR_RPL; ++t) {
           const int i = k + lane + 32 * t;
-          x[t] = (t < tcount && i < nr) ? col[i] : (T)0;
-          if (t < tcount && i < nr) dot = fma(v[i - k], x[t], dot);
+          const bool in = t < tcount && i < nr;
+          x0[t] = in ? c0[i] : (T)0;
+          x1[t] = in ? c1[i] : (T)0;
         }
-        dot = warp_sum_t<T>(dot);
-        const T f = beta * dot;
-        T part = 0;
+#pragma unroll
+        for (int t = 0; t < QR_RPL; ++t) {
+          const int i = k + lane + 32 * t;
+          const T vi = (t < tcount && i < nr) ? v[i - k] : (T)0;
+          d0 = fma(vi, x0[t], d0);
+          d1 = fma(vi, x1[t], d1);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+          d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+        }
+        const T f0 = beta * d0, f1 = beta * d1;
+        T p0 = 0, p1 = 0;
 #pragma unroll
         for (int t = 0; t < QR_RPL; ++t) {
           const int i = k + lane + 32 * t;
           if (t < tcount && i < nr) {
-            T a = x[t] - f * v[i - k];
-            col[i] = a;
-            if (i > k) part = fma(a, a, part);
+            const T vi = v[i - k];
+            const T a0 = x0[t] - f0 * vi, a1 = x1[t] - f1 * vi;
+            c0[i] = a0;
+            if (two) c1[i] = a1;
+            if (i > k) {
+              p0 = fma(a0, a0, p0);
+              p1 = fma(a1, a1, p1);
+            }
           }
         }
-        const double nrm = warp_sum((double)part);
-        if (lane == 0) norms[j] = nrm;
-      } else {
+        double n0 = (double)p0, n1 = (double)p1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          n0 += __shfl_xor_sync(0xffffffffu, n0, o);
+          n1 += __shfl_xor_sync(0xffffffffu, n1, o);
+        }
+        if (lane == 0) {
+          norms[j] = n0;
+          if (two) norms[j + 1] = n1;
+        }
+      }
+    } else {
+    for (int j = k + 1 + warp; j < nc; j += QR_WARPS) {
+      T* col = A + (size_t)j * ld;
+      T dot = 0;
+      {
         for (int i = k + lane; i < nr; i += 32) dot = fma(v[i - k], col[i], dot);
         dot = warp_sum_t<T>(dot);
         const T f = beta * dot;
@@ -267,6 +300,7 @@ __global__ void __launch_bounds__(QR_THREADS) cpqr_kernel(const CpqrDescT<T>* de
         const double nrm = warp_sum((double)part);
         if (lane == 0) norms[j] = nrm;
       }
+    }
     }
     for (int i = k + threadIdx.x; i < nr; i += QR_THREADS)
       A[(size_t)i + (size_t)k * ld] = (i == k) ? (T)alpha : (T)0;
@@ -450,10 +484,46 @@ __global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* des
 // (forward) or above (backward) with a register-tiled product.
 constexpr int RS_THREADS = 256;
 
+// 16-byte vector of T for shared-memory broadcasts
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
+
+// out[c] = X[row * NC + c] for c < NC: 16-byte loads where the row is 16-byte aligned
+template <typename T, int NC>
+__device__ __forceinline__ void load_row(const T* X, int row, T (&out)[NC]) {
+  if constexpr ((NC * sizeof(T)) % 16 == 0) {
+    using V = typename Vec16<T>::type;
+    const V* p = reinterpret_cast<const V*>(X + (size_t)row * NC);
+#pragma unroll
+    for (int q = 0; q < NC / Vec16<T>::n; ++q) {
+      const V v = p[q];
+      const T* e = reinterpret_cast<const T*>(&v);
+#pragma unroll
+      for (int u = 0; u < Vec16<T>::n; ++u) out[q * Vec16<T>::n + u] = e[u];
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) out[c] = X[(size_t)row * NC + c];
+  }
+}
+
+// X (n x NC chunk of right-hand sides) lives in shared memory row-major, so that the
+// register-tiled updates read a row of X with 16-byte broadcasts.  The 32 x 32
+// diagonal blocks are read into registers before their sequential substitution.
 template <typename T, int NC>
 __global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>* descs) {
   extern __shared__ __align__(16) unsigned char rs_sh[];
-  T* X = reinterpret_cast<T*>(rs_sh);  // n x NC, column-major, ld n
+  T* X = reinterpret_cast<T*>(rs_sh);  // n x NC, row-major, X[i * NC + c]
   const LuSolveDescT<T> D = descs[blockIdx.y];
   const int c0 = blockIdx.x * NC;
   if (c0 >= D.ncols) return;
@@ -464,17 +534,16 @@ __global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int t = tid; t < n * NC; t += RS_THREADS) {
     const int i = t % n, c = t / n;
-    X[(size_t)c * n + i] = c < nc ? D.B[(size_t)i + (size_t)(c0 + c) * D.ldb] : (T)0;
+    X[(size_t)i * NC + c] = c < nc ? D.B[(size_t)i + (size_t)(c0 + c) * D.ldb] : (T)0;
   }
   __syncthreads();
   if (tid < nc) {
-    T* x = X + (size_t)tid * n;
     for (int k = 0; k < n; ++k) {
       const int p = D.ipiv[k];
       if (p != k) {
-        T t = x[k];
-        x[k] = x[p];
-        x[p] = t;
+        const T t = X[(size_t)k * NC + tid];
+        X[(size_t)k * NC + tid] = X[(size_t)p * NC + tid];
+        X[(size_t)p * NC + tid] = t;
       }
     }
   }
@@ -482,13 +551,31 @@ __global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>
   // forward substitution with the unit lower triangle
   for (int b0 = 0; b0 < n; b0 += 32) {
     const int bs = min(32, n - b0);
-    for (int c = warp; c < nc; c += RS_THREADS / 32) {
-      T x = lane < bs ? X[(size_t)c * n + b0 + lane] : (T)0;
-      for (int k = 0; k < bs - 1; ++k) {
-        const T xk = __shfl_sync(0xffffffffu, x, k);
-        if (lane > k && lane < bs) x -= LU[(size_t)(b0 + lane) + (size_t)(b0 + k) * ld] * xk;
+    if (warp < nc) {
+      if constexpr (sizeof(T) == 4) {
+        T l[32];  // row b0 + lane of the diagonal block (FP32: registers to spare)
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+          l[k] = (lane < bs && k < bs) ? LU[(size_t)(b0 + lane) + (size_t)(b0 + k) * ld] : (T)0;
+        for (int c = warp; c < nc; c += RS_THREADS / 32) {
+          T x = lane < bs ? X[(size_t)(b0 + lane) * NC + c] : (T)0;
+#pragma unroll
+          for (int k = 0; k < 31; ++k) {
+            const T xk = __shfl_sync(0xffffffffu, x, k);
+            if (k < bs - 1 && lane > k && lane < bs) x -= l[k] * xk;
+          }
+          if (lane < bs) X[(size_t)(b0 + lane) * NC + c] = x;
+        }
+      } else {
+        for (int c = warp; c < nc; c += RS_THREADS / 32) {
+          T x = lane < bs ? X[(size_t)(b0 + lane) * NC + c] : (T)0;
+          for (int k = 0; k < bs - 1; ++k) {
+            const T xk = __shfl_sync(0xffffffffu, x, k);
+            if (lane > k && lane < bs) x -= LU[(size_t)(b0 + lane) + (size_t)(b0 + k) * ld] * xk;
+          }
+          if (lane < bs) X[(size_t)(b0 + lane) * NC + c] = x;
+        }
       }
-      if (lane < bs) X[(size_t)c * n + b0 + lane] = x;
     }
     __syncthreads();
     for (int r = b0 + bs + tid; r < n; r += RS_THREADS) {
@@ -496,26 +583,49 @@ __global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>
 #pragma unroll
       for (int c = 0; c < NC; ++c) acc[c] = 0;
       for (int k = 0; k < bs; ++k) {
-        const T l = LU[(size_t)r + (size_t)(b0 + k) * ld];
+        const T lv = LU[(size_t)r + (size_t)(b0 + k) * ld];
+        T xv[NC];
+        load_row<T, NC>(X, b0 + k, xv);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] = fma(l, X[(size_t)c * n + b0 + k], acc[c]);
+        for (int c = 0; c < NC; ++c) acc[c] = fma(lv, xv[c], acc[c]);
       }
 #pragma unroll
-      for (int c = 0; c < NC; ++c) X[(size_t)c * n + r] -= acc[c];
+      for (int c = 0; c < NC; ++c) X[(size_t)r * NC + c] -= acc[c];
     }
     __syncthreads();
   }
   // backward substitution with the upper triangle
   for (int b1 = n; b1 > 0; b1 -= 32) {
     const int b0 = max(0, b1 - 32), bs = b1 - b0;
-    for (int c = warp; c < nc; c += RS_THREADS / 32) {
-      T x = lane < bs ? X[(size_t)c * n + b0 + lane] : (T)0;
-      for (int k = bs - 1; k >= 0; --k) {
-        if (lane == k) x /= LU[(size_t)(b0 + k) + (size_t)(b0 + k) * ld];
-        const T xk = __shfl_sync(0xffffffffu, x, k);
-        if (lane < k) x -= LU[(size_t)(b0 + lane) + (size_t)(b0 + k) * ld] * xk;
+    if (warp < nc) {
+      if constexpr (sizeof(T) == 4) {
+        T u[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+          u[k] = (lane < bs && k < bs) ? LU[(size_t)(b0 + lane) + (size_t)(b0 + k) * ld] : (T)0;
+        for (int c = warp; c < nc; c += RS_THREADS / 32) {
+          T x = lane < bs ? X[(size_t)(b0 + lane) * NC + c] : (T)0;
+#pragma unroll
+          for (int k = 31; k >= 0; --k) {
+            if (k < bs) {
+              if (lane == k) x /= u[k];
+              const T xk = __shfl_sync(0xffffffffu, x, k);
+              if (lane < k) x -= u[k] * xk;
+            }
+          }
+          if (lane < bs) X[(size_t)(b0 + lane) * NC + c] = x;
+        }
+      } else {
+        for (int c = warp; c < nc; c += RS_THREADS / 32) {
+          T x = lane < bs ? X[(size_t)(b0 + lane) * NC + c] : (T)0;
+          for (int k = bs - 1; k >= 0; --k) {
+            if (lane == k) x /= LU[(size_t)(b0 + k) + (size_t)(b0 + k) * ld];
+            const T xk = __shfl_sync(0xffffffffu, x, k);
+            if (lane < k) x -= LU[(size_t)(b0 + lane) + (size_t)(b0 + k) * ld] * xk;
+          }
+          if (lane < bs) X[(size_t)(b0 + lane) * NC + c] = x;
+        }
       }
-      if (lane < bs) X[(size_t)c * n + b0 + lane] = x;
     }
     __syncthreads();
     for (int r = tid; r < b0; r += RS_THREADS) {
@@ -523,18 +633,20 @@ __global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>
 #pragma unroll
       for (int c = 0; c < NC; ++c) acc[c] = 0;
       for (int k = 0; k < bs; ++k) {
-        const T u = LU[(size_t)r + (size_t)(b0 + k) * ld];
+        const T uv = LU[(size_t)r + (size_t)(b0 + k) * ld];
+        T xv[NC];
+        load_row<T, NC>(X, b0 + k, xv);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] = fma(u, X[(size_t)c * n + b0 + k], acc[c]);
+        for (int c = 0; c < NC; ++c) acc[c] = fma(uv, xv[c], acc[c]);
       }
 #pragma unroll
-      for (int c = 0; c < NC; ++c) X[(size_t)c * n + r] -= acc[c];
+      for (int c = 0; c < NC; ++c) X[(size_t)r * NC + c] -= acc[c];
     }
     __syncthreads();
   }
   for (int t = tid; t < n * nc; t += RS_THREADS) {
     const int i = t % n, c = t / n;
-    D.B[(size_t)i + (size_t)(c0 + c) * D.ldb] = X[(size_t)c * n + i];
+    D.B[(size_t)i + (size_t)(c0 + c) * D.ldb] = X[(size_t)i * NC + c];
   }
 }
 
@@ -549,8 +661,8 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(const GemmDescT<T>* des
                                                          const GemmTile* tiles) {
   constexpr int TX = TM / 4, TY = TN / 4;
   static_assert(TX * TY == G_THREADS, "tile must map to 256 threads");
-  __shared__ T As[GK][TM + 1];
-  __shared__ T Bs[GK][TN + 1];
+  __shared__ __align__(16) T As[GK][TM + 4];
+  __shared__ __align__(16) T Bs[GK][TN + 4];
   const GemmTile Tl = tiles[blockIdx.x];
   const GemmDescT<T> D = descs[Tl.desc];
   const int m0 = Tl.tm * TM, n0 = Tl.tn * TN;
@@ -580,12 +692,9 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(const GemmDescT<T>* des
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      T a[4], b[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        a[r] = As[kk][tx + TX * r];
-        b[r] = Bs[kk][ty + TY * r];
-      }
+      T a[4], b[4];  // rows 4 tx .. 4 tx + 3 and columns 4 ty .. 4 ty + 3: 16-byte loads
+      load_row<T, 4>(&As[kk][0], tx, a);
+      load_row<T, 4>(&Bs[kk][0], ty, b);
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -598,7 +707,7 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(const GemmDescT<T>* des
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int gm = m0 + tx + TX * r, gn = n0 + ty + TY * c;
+      const int gm = m0 + 4 * tx + r, gn = n0 + 4 * ty + c;
       if (gm < D.M && gn < D.N) {
         T* cp = D.C + (size_t)gm + (size_t)gn * D.ldc;
         *cp = D.beta == 0.0 ? alpha * acc[r][c] : alpha * acc[r][c] + beta * *cp;

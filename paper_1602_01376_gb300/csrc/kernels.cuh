@@ -40,10 +40,10 @@ void permute_points(const double* X, const int* perm, int N, int d, int* iperm, 
 
 // ------------------------------------------------------------------- kNN (a2)
 struct KnnScratch {
-  DevBuf x32, qnorm, part, mean, rmax, probs, cand_d, cand_i, flagged, counter, tiles;
+  DevBuf x32, qnorm, part, mean, rmax, probs, cand_d, cand_i, flagged, counter, tiles, status;
   void release() {
     for (DevBuf* b : {&x32, &qnorm, &part, &mean, &rmax, &probs, &cand_d, &cand_i, &flagged, &counter,
-                      &tiles})
+                      &tiles, &status})
       b->release();
   }
 };

@@ -3,17 +3,20 @@
 // The lists are defined on the FP64 squared distance sum_k (x_k - y_k)^2 with the
 // coordinates summed in order and every operation rounded (no FMA), ties broken by
 // the lower index.  The search runs in three steps:
-//   1. FP32 prefilter: the points of each problem are centred on the problem's mean and
-//      rounded to FP32 (a = fl32(x - mean)); every query keeps the KP smallest values
-//      D = fl(fl(|a|^2 + |b|^2) - 2 a.b) (Gram form: one FMA per pair and coordinate,
-//      the dot product accumulated in coordinate order, the norms rounded up);
+//   1. tensor-core prefilter: the points of each problem are centred on the problem's
+//      mean and rounded to FP32 (a = fl32(x - mean)); every query keeps the KP smallest
+//      values D = fl(fl(|a|^2 + |b|^2) - 2 a.b), the norms rounded up and the dot
+//      products on the fifth-generation tensor cores (tcgen05.mma kind::tf32, TMEM
+//      accumulators) in 3xTF32: a = a_hi + a_lo with TF32 terms, a.b ~ a_lo.b_hi +
+//      a_hi.b_lo + a_hi.b_hi accumulated in FP32;
 //   2. exact re-rank: the KP candidates get their FP64 distances, sorted by
 //      (distance, index); the first kappa form the list.  A rounding bound proves that
 //      no excluded point comes before the kappa-th: for every pair,
-//      |D - |x - y|^2| <= E = (4K + 16) 2^-23 (|a|^2 + |b|^2)  (K = padded dimension:
-//      FP32 accumulation of K products K 2^-24, norm and final roundings 2.5 2^-23, FP32
-//      centring 2 2^-23, all relative to |a|^2 + |b|^2, with room to spare), so an
-//      excluded point, whose D is at least the largest kept D_KP, lies at FP64 distance
+//      |D - |x - y|^2| <= E = (8K + 32) 2^-23 (|a|^2 + |b|^2)  (K = padded dimension:
+//      TF32 split remainders 3 2^-22, accumulation of 3K products 3K 2^-23 even with
+//      truncating adds, norm and final roundings 2.5 2^-23, FP32 centring 2 2^-23, all
+//      relative to |a|^2 + |b|^2, then doubled), so an excluded point, whose D is at
+//      least the largest kept D_KP, lies at FP64 distance
 //      >= (D_KP - E(q, |b|^2 <= max_b |b|^2)) (1 - 1e-12);
 //   3. queries whose bound fails (near-ties at the cut) are redone by an exact FP64
 //      scan over all points.
@@ -21,13 +24,16 @@
 #include <climits>
 
 #include "kernels.cuh"
+#include "tc.cuh"
 
 namespace iaskit {
 
 namespace {
 
-constexpr int KT_QB = 256;    // queries per tile, one thread each
-constexpr int KT_RB = 32;     // points per streamed tile
+constexpr int KT_QB = 128;    // queries per tile: TMEM lanes
+constexpr int KT_RB = 128;    // points per streamed tile: accumulator columns
+constexpr int KT_SUB = 4;     // threads per query, one per quarter of a tile's columns
+constexpr int KT_NTH = KT_QB * KT_SUB;
 constexpr int KC_CHUNKS = 64; // partial sums per problem for the mean
 
 // Per problem and chunk of its points, the coordinate sums (FP64, in point order).
@@ -51,16 +57,16 @@ __global__ void center_mean_kernel(int d, const int2* probs, const double* part,
 }
 // Centred FP32 coordinates, their squared norms rounded up, and the largest norm of
 // each problem (as the bit pattern of a non-negative float, ordered like the value).
-__global__ void center_points_kernel(const double* X, int d, const KnnTile* tiles, const double* mean,
+__global__ void center_points_kernel(const double* X, int d, int Dp, const KnnTile* tiles, const double* mean,
                                      float* Xc, float* qn, unsigned* rmax) {
   const KnnTile tl = tiles[blockIdx.x];
   if ((int)threadIdx.x >= tl.qn) return;
   const int i = tl.q0 + threadIdx.x;
   const double* m = mean + (size_t)tl.prob * d;
   double nrm = 0.0;
-  for (int k = 0; k < d; ++k) {
-    const float c = (float)(X[(size_t)i * d + k] - m[k]);
-    Xc[(size_t)i * d + k] = c;
+  for (int k = 0; k < Dp; ++k) {
+    const float c = k < d ? (float)(X[(size_t)i * d + k] - m[k]) : 0.0f;
+    Xc[(size_t)i * Dp + k] = c;
     nrm = fma((double)c, (double)c, nrm);
   }
   const float q = __double2float_ru(nrm);
@@ -68,34 +74,107 @@ __global__ void center_points_kernel(const double* X, int d, const KnnTile* tile
   atomicMax(&rmax[tl.prob], __float_as_uint(q));
 }
 
-// Prefilter.  A block owns KT_QB queries (one thread each for the selection) and
-// streams the points in tiles of KT_RB:
-//   phase 1: every thread computes the dot products of 8 queries x 4 points of the
-//            tile, acc = fma(q_k, r_k, acc) in coordinate order (coordinates d..D-1 are
-//            zero on both sides), then D = (|q|^2 + |r|^2) - 2 acc, into shared memory;
-//   phase 2: every thread scans its query's row and updates its register list.
-// 8 x 4 keeps the kernel at two resident blocks per SM, so one block's selection and
-// barriers overlap the other's arithmetic.
-template <int D, int KP>
-__global__ void __launch_bounds__(KT_QB) knn_prefilter_kernel(const float* Xc, const float* qnorm, int d,
-                                                              const KnnTile* tiles, float* cand_d,
-                                                              int* cand_i) {
-  extern __shared__ float kt_sh[];
-  float* Qs = kt_sh;                      // [D][KT_QB]
-  float* Rs = Qs + D * KT_QB;             // [D][KT_RB]
-  float* qn_s = Rs + D * KT_RB;           // [KT_QB]
-  float* rn_s = qn_s + KT_QB;             // [KT_RB]
-  float* Dt = rn_s + KT_RB;               // [KT_QB][KT_RB + 1]
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const KnnTile tl = tiles[blockIdx.x];
-  const int q0 = tl.q0, qend = tl.q0 + tl.qn;
-  for (int e = tid; e < D * KT_QB; e += KT_QB) {
-    const int i = e / D, k = e % D;
-    Qs[k * KT_QB + i] = (q0 + i < qend && k < d) ? Xc[(size_t)(q0 + i) * d + k] : 0.0f;
+// Prefilter on the tensor cores.  A block owns KT_QB = 128 queries (TMEM lanes) and
+// streams its problem's points in tiles of KT_RB = 128:
+//   * the query block (TF32 hi and lo parts) stays in shared memory; point tiles are
+//     staged into one of two buffers while the tensor core works on the other;
+//   * thread 0 issues 3 MMAs (lo.hi, hi.lo, hi.hi) per 8 coordinates into one of two
+//     TMEM accumulator tiles (128 x 128 FP32) and commits them to that tile's mbarrier;
+//   * warp w reads TMEM lanes 32 (w % 4) .. + 31 (its queries) and columns
+//     32 (w / 4) .. + 31 of the finished tile: four threads per query, each keeping its
+//     own list of the KP smallest D = (|q|^2 + |r|^2) - 2 q.r over its quarter of the
+//     columns.  The re-rank merges the four lists.
+// Xc rows are padded to D floats (zeros), so a row is whole 16-byte chunks.  Waits are
+// bounded; a wait that gives up sets DEV_TIMEOUT and the block stops issuing.
+constexpr long KT_WAIT = 1L << 22;
+template <int D>
+__device__ __forceinline__ void stage_operand(const float* Xc, int row0, int nrows, uint32_t* H, uint32_t* L) {
+  constexpr int KC = D / 4;
+  for (int e = threadIdx.x; e < KT_QB * KC; e += KT_NTH) {
+    const int g = e / (8 * KC), rem = e % (8 * KC);
+    const int kc = rem / 8, rr = rem % 8;
+    const int r = g * 8 + rr;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r < nrows) v = *reinterpret_cast<const float4*>(Xc + (size_t)(row0 + r) * D + kc * 4);
+    uint4 h, l;
+    h.x = tc::to_tf32(v.x);
+    h.y = tc::to_tf32(v.y);
+    h.z = tc::to_tf32(v.z);
+    h.w = tc::to_tf32(v.w);
+    l.x = tc::to_tf32(v.x - __uint_as_float(h.x));
+    l.y = tc::to_tf32(v.y - __uint_as_float(h.y));
+    l.z = tc::to_tf32(v.z - __uint_as_float(h.z));
+    l.w = tc::to_tf32(v.w - __uint_as_float(h.w));
+    const uint32_t w = (uint32_t)((g * KC + kc) * 32 + rr * 4);  // 32-bit words
+    *reinterpret_cast<uint4*>(H + w) = h;
+    *reinterpret_cast<uint4*>(L + w) = l;
   }
-  const int my_q = q0 + tid;
-  const bool active = my_q < qend;
-  qn_s[tid] = active ? qnorm[my_q] : 0.0f;
+}
+
+template <int D>
+constexpr size_t prefilter_smem() {
+  return (size_t)6 * KT_QB * D * 4 + 2 * KT_RB * 4 + 64;
+}
+
+template <int D, int KP>
+__global__ void __launch_bounds__(KT_NTH) knn_prefilter_kernel(const float* Xc, const float* qnorm,
+                                                               const KnnTile* tiles, float* cand_d,
+                                                               int* cand_i, int* status) {
+  extern __shared__ __align__(1024) unsigned char kt_sh[];
+  constexpr int OPW = KT_QB * D;  // 32-bit words of one operand
+  uint32_t* Ah = reinterpret_cast<uint32_t*>(kt_sh);
+  uint32_t* Al = Ah + OPW;
+  uint32_t* Bh0 = Al + OPW;
+  uint32_t* Bl0 = Bh0 + OPW;
+  uint32_t* Bh1 = Bl0 + OPW;
+  uint32_t* Bl1 = Bh1 + OPW;
+  float* rn_s = reinterpret_cast<float*>(Bl1 + OPW);                // [2][KT_RB]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(rn_s + 2 * KT_RB);   // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+  __shared__ int abort_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int lq = warp & 3, cq = warp >> 2;  // lane quarter (queries) and column quarter
+  const int qi = lq * 32 + lane;
+  const KnnTile tl = tiles[blockIdx.x];
+  const int my_q = tl.q0 + qi;
+  const bool active = qi < tl.qn;
+  const int rend = tl.rb + tl.rn;
+  const int ntile = (tl.rn + KT_RB - 1) / KT_RB;
+  stage_operand<D>(Xc, tl.q0, tl.qn, Ah, Al);
+  stage_operand<D>(Xc, tl.rb, min(KT_RB, tl.rn), Bh0, Bl0);
+  if (tid < KT_RB) rn_s[tid] = tid < min(KT_RB, tl.rn) ? qnorm[tl.rb + tid] : 0.0f;
+  const float qv = active ? qnorm[my_q] : 0.0f;
+  if (warp == 0) tc::tmem_alloc(tslot, 2 * KT_RB);
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    abort_s = 0;
+  }
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  constexpr uint32_t idesc = tc::idesc_tf32(KT_QB, KT_RB);
+  constexpr uint32_t SBO = (D / 4) * 128;
+  auto issue = [&](int b) {
+    const uint32_t* Bh = b ? Bh1 : Bh0;
+    const uint32_t* Bl = b ? Bl1 : Bl0;
+    const uint32_t dt = tmem + (uint32_t)(b * KT_RB);
+#pragma unroll 1
+    for (int ks = 0; ks < D / 8; ++ks) {
+      const uint32_t ko = (uint32_t)ks * 256;
+      const uint64_t ah = tc::smem_desc(tc::smem_addr(Ah) + ko, 128, SBO);
+      const uint64_t al = tc::smem_desc(tc::smem_addr(Al) + ko, 128, SBO);
+      const uint64_t bh = tc::smem_desc(tc::smem_addr(Bh) + ko, 128, SBO);
+      const uint64_t bl = tc::smem_desc(tc::smem_addr(Bl) + ko, 128, SBO);
+      tc::mma_tf32(dt, al, bh, idesc, ks > 0);
+      tc::mma_tf32(dt, ah, bl, idesc, true);
+      tc::mma_tf32(dt, ah, bh, idesc, true);
+    }
+    tc::mma_commit(&mbar[b]);
+  };
+  if (tid == 0) issue(0);
   float bd[KP];
   int bi[KP];
 #pragma unroll
@@ -103,57 +182,58 @@ __global__ void __launch_bounds__(KT_QB) knn_prefilter_kernel(const float* Xc, c
     bd[u] = FLT_MAX;
     bi[u] = INT_MAX;
   }
-  const int rend = tl.rb + tl.rn;
-  for (int r0 = tl.rb; r0 < rend; r0 += KT_RB) {
-    const int nt = min(KT_RB, rend - r0);
-    __syncthreads();
-    for (int e = tid; e < D * KT_RB; e += KT_QB) {
-      const int j = e / D, k = e % D;
-      Rs[k * KT_RB + j] = (j < nt && k < d) ? Xc[(size_t)(r0 + j) * d + k] : 0.0f;
+  for (int t = 0; t < ntile; ++t) {
+    const int b = t & 1;
+    const int r0 = tl.rb + t * KT_RB, nt = min(KT_RB, rend - r0);
+    if (t + 1 < ntile) {  // the other buffer's last reader, MMA t-1, has completed
+      const int r1 = r0 + KT_RB, n1 = min(KT_RB, rend - r1);
+      stage_operand<D>(Xc, r1, n1, b ? Bh0 : Bh1, b ? Bl0 : Bl1);
+      if (tid < KT_RB) rn_s[(b ^ 1) * KT_RB + tid] = tid < n1 ? qnorm[r1 + tid] : 0.0f;
     }
-    if (tid < KT_RB) rn_s[tid] = tid < nt ? qnorm[r0 + tid] : 0.0f;
+    tc::fence_async_smem();
+    tc::fence_before_sync();
     __syncthreads();
-    float acc[8][4];
-#pragma unroll
-    for (int a = 0; a < 8; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = 0.0f;
-#pragma unroll 4
-    for (int k = 0; k < D; ++k) {
-      float qa[8];
-#pragma unroll
-      for (int a = 0; a < 8; ++a) qa[a] = Qs[k * KT_QB + lane + 32 * a];
-      const float4 rb = *reinterpret_cast<const float4*>(Rs + k * KT_RB + warp * 4);
-#pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        acc[a][0] = fmaf(qa[a], rb.x, acc[a][0]);
-        acc[a][1] = fmaf(qa[a], rb.y, acc[a][1]);
-        acc[a][2] = fmaf(qa[a], rb.z, acc[a][2]);
-        acc[a][3] = fmaf(qa[a], rb.w, acc[a][3]);
+    tc::fence_after_sync();
+    const bool stop = abort_s != 0;
+    if (!stop && t + 1 < ntile && tid == 0) issue(b ^ 1);
+    bool got = false;
+    if (!stop) {
+      got = tc::mbar_wait(&mbar[b], (uint32_t)((t >> 1) & 1), KT_WAIT);
+      if (!got) {
+        atomicOr(status, DEV_TIMEOUT);
+        abort_s = 1;
       }
     }
+    tc::fence_after_sync();
+    const bool use = __all_sync(0xffffffffu, got);  // tcgen05.ld needs the whole warp
+    if (use) {
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const int c0 = cq * 32 + h * 16;
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(b * KT_RB + c0), v);
+        // distances of the 16 columns, and the mask of those below the list's bound
+        unsigned mask = 0;
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const int q = lane + 32 * a;
+        for (int j = 0; j < 16; ++j) {
+          const int col = c0 + j;
+          v[j] = (qv + rn_s[b * KT_RB + col]) - 2.0f * v[j];
+          if (active && col < nt && r0 + col != my_q && v[j] <= bd[KP - 1]) mask |= 1u << j;
+        }
+        // insertions are rare: one copy of the insertion chain, column by column
+        while (mask) {
+          const int j = __ffs(mask) - 1;
+          mask &= mask - 1;
+          float cv = v[0];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int c = warp * 4 + b;
-        Dt[q * (KT_RB + 1) + c] = (qn_s[q] + rn_s[c]) - 2.0f * acc[a][b];
-      }
-    }
-    __syncthreads();
-    if (active) {
-      for (int j = 0; j < nt; ++j) {
-        const float v = Dt[tid * (KT_RB + 1) + j];
-        const int ref = r0 + j;
-        if (v <= bd[KP - 1] && ref != my_q) {
-          float cv = v;
-          int cj = ref;
+          for (int u = 1; u < 16; ++u) cv = (u == j) ? v[u] : cv;
+          int cj = r0 + c0 + j;
+          if (!(cv <= bd[KP - 1])) continue;
 #pragma unroll
           for (int u = 0; u < KP; ++u) {
-            bool less = cv < bd[u] || (cv == bd[u] && cj < bi[u]);
-            float tv = less ? bd[u] : cv;
-            int tj = less ? bi[u] : cj;
+            const bool less = cv < bd[u] || (cv == bd[u] && cj < bi[u]);
+            const float tv = less ? bd[u] : cv;
+            const int tj = less ? bi[u] : cj;
             bd[u] = less ? cv : bd[u];
             bi[u] = less ? cj : bi[u];
             cv = tv;
@@ -162,12 +242,17 @@ __global__ void __launch_bounds__(KT_QB) knn_prefilter_kernel(const float* Xc, c
         }
       }
     }
+    tc::fence_before_sync();
+    __syncthreads();  // rn_s and the TMEM tile are reused two tiles later
   }
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_free(tmem, 2 * KT_RB);
   if (active) {
+    const size_t o = (size_t)my_q * (KT_SUB * KP) + (size_t)cq * KP;
 #pragma unroll
     for (int u = 0; u < KP; ++u) {
-      cand_d[(size_t)my_q * KP + u] = bd[u];
-      cand_i[(size_t)my_q * KP + u] = bi[u];
+      cand_d[o + u] = bd[u];
+      cand_i[o + u] = bi[u];
     }
   }
 }
@@ -186,9 +271,13 @@ __device__ __forceinline__ bool pair_less(double a, int ia, double b, int ib) {
   return a < b || (a == b && ia < ib);
 }
 
-// One block of KT_QB threads per work tile, one thread per query.  Kdim is the
-// padded dimension of the prefilter (its accumulation length).
-template <int KP>
+// One block of KT_QB threads per work tile, one thread per query.  Its KT_SUB lists of
+// KP candidates are merged: exact FP64 distances, the kappa smallest by (distance,
+// index) kept by insertion.  Every point outside the lists has D >= the smallest of
+// the lists' last values (a list that is not full holds all of its quarter's points).
+// Kdim is the padded dimension of the prefilter (its accumulation length).
+constexpr int RR_MAXK = 48;
+template <int KP, int KAP>  // KAP >= kappa: size of the sorted list
 __global__ void knn_rerank_kernel(const double* X, int d, int kappa, int Kdim, const KnnTile* tiles,
                                   const float* cand_d, const int* cand_i, const float* qnorm,
                                   const unsigned* rmax_bits, int* knn, int2* flagged, int* nflagged) {
@@ -196,43 +285,56 @@ __global__ void knn_rerank_kernel(const double* X, int d, int kappa, int Kdim, c
   if ((int)threadIdx.x >= tl.qn) return;
   const int i = tl.q0 + threadIdx.x;
   const int N = tl.rn, rb = tl.rb;
-  double dd[KP];
-  int ii[KP];
+  double dd[KAP];
+  int ii[KAP];
+#pragma unroll
+  for (int u = 0; u < KAP; ++u) {
+    dd[u] = DBL_MAX;
+    ii[u] = INT_MAX;
+  }
   const double* xi = X + (size_t)i * d;
-  const int nc = min(KP, N - 1);
-  for (int u = 0; u < nc; ++u) {
-    int j = cand_i[(size_t)i * KP + u];
-    if (j < rb || j >= rb + N) {  // an FP32 distance overflowed: redo this query exactly
-      int slot = atomicAdd(nflagged, 1);
-      flagged[slot] = make_int2(i, blockIdx.x);
-      return;
+  const size_t o = (size_t)i * (KT_SUB * KP);
+  float cut = FLT_MAX;
+  int found = 0;
+  for (int q = 0; q < KT_SUB; ++q) {
+    cut = fminf(cut, cand_d[o + (size_t)q * KP + KP - 1]);
+    for (int u = 0; u < KP; ++u) {
+      const int j = cand_i[o + (size_t)q * KP + u];
+      if (j == INT_MAX) break;  // the rest of this list is empty
+      if (j < rb || j >= rb + N) {  // cannot happen with finite norms; redo exactly
+        int slot = atomicAdd(nflagged, 1);
+        flagged[slot] = make_int2(i, blockIdx.x);
+        return;
+      }
+      ++found;
+      double v = exact_sqdist(xi, X + (size_t)j * d, d);
+      int jj = j;
+      if (!pair_less(v, jj, dd[kappa - 1], ii[kappa - 1])) continue;
+#pragma unroll
+      for (int w = 0; w < KAP; ++w) {  // insertion into the sorted kappa list
+        if (w >= kappa) break;
+        if (pair_less(v, jj, dd[w], ii[w])) {
+          const double tv = dd[w];
+          const int tj = ii[w];
+          dd[w] = v;
+          ii[w] = jj;
+          v = tv;
+          jj = tj;
+        }
+      }
     }
-    ii[u] = j;
-    dd[u] = exact_sqdist(xi, X + (size_t)j * d, d);
   }
-  for (int a = 1; a < nc; ++a) {  // insertion sort by (distance, index)
-    double v = dd[a];
-    int j = ii[a];
-    int b = a - 1;
-    while (b >= 0 && pair_less(v, j, dd[b], ii[b])) {
-      dd[b + 1] = dd[b];
-      ii[b + 1] = ii[b];
-      --b;
-    }
-    dd[b + 1] = v;
-    ii[b + 1] = j;
-  }
-  for (int u = 0; u < kappa; ++u) knn[(size_t)i * kappa + u] = ii[u];
-  if (N - 1 <= KP) return;  // every other point was a candidate
-  const double c = (4.0 * Kdim + 16.0) * 1.1920928955078125e-07;  // (4K + 16) 2^-23
+  const double c = (8.0 * Kdim + 32.0) * 1.1920928955078125e-07;  // (8K + 32) 2^-23
   const double E = c * ((double)qnorm[i] + (double)__uint_as_float(rmax_bits[tl.prob]));
-  const double Dkept = (double)cand_d[(size_t)i * KP + KP - 1];
-  const double lo = (Dkept - E) * (1.0 - 1e-12);
-  const bool ok = lo > dd[kappa - 1];
+  const bool all_in = found >= N - 1;  // every other point was a candidate
+  const double lo = ((double)cut - E) * (1.0 - 1e-12);
+  const bool ok = found >= kappa && isfinite(E) && (all_in || lo > dd[kappa - 1]);
   if (!ok) {
     int slot = atomicAdd(nflagged, 1);
     flagged[slot] = make_int2(i, blockIdx.x);
+    return;
   }
+  for (int u = 0; u < kappa; ++u) knn[(size_t)i * kappa + u] = ii[u];
 }
 
 // Exact scan for one flagged query per block: every thread keeps a sorted top-kappa
@@ -292,14 +394,12 @@ __global__ void knn_fallback_kernel(const double* X, int d, int kappa, const Knn
 }
 
 template <int D, int KP>
-void launch_prefilter(const float* Xc, const float* qn, int d, const KnnTile* tiles, int ntiles, float* cd,
-                      int* ci, cudaStream_t st) {
-  const size_t smem = sizeof(float) * ((size_t)D * KT_QB + (size_t)D * KT_RB + KT_QB + KT_RB +
-                                       (size_t)KT_QB * (KT_RB + 1));
-  if (smem > 48 * 1024)
-    IA_CUDA(cudaFuncSetAttribute(knn_prefilter_kernel<D, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
-  knn_prefilter_kernel<D, KP><<<ntiles, KT_QB, smem, st>>>(Xc, qn, d, tiles, cd, ci);
+void launch_prefilter(const float* Xc, const float* qn, const KnnTile* tiles, int ntiles, float* cd, int* ci,
+                      int* status, cudaStream_t st) {
+  // at least 80 KB so that at most two blocks share an SM's 512 TMEM columns
+  const size_t smem = std::max<size_t>(prefilter_smem<D>(), 80 * 1024);
+  IA_CUDA(cudaFuncSetAttribute(knn_prefilter_kernel<D, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  knn_prefilter_kernel<D, KP><<<ntiles, KT_NTH, smem, st>>>(Xc, qn, tiles, cd, ci, status);
   IA_LAUNCH_CHECK();
 }
 
@@ -308,23 +408,24 @@ int padded_dim(int d) { return (d + 7) / 8 * 8; }
 
 template <int KP>
 void prefilter_dispatch(const float* Xc, const float* qn, int d, const KnnTile* tl, int nt, float* cd, int* ci,
-                        cudaStream_t st) {
+                        int* status, cudaStream_t st) {
   switch (padded_dim(d)) {
-    case 8: launch_prefilter<8, KP>(Xc, qn, d, tl, nt, cd, ci, st); break;
-    case 16: launch_prefilter<16, KP>(Xc, qn, d, tl, nt, cd, ci, st); break;
-    case 24: launch_prefilter<24, KP>(Xc, qn, d, tl, nt, cd, ci, st); break;
-    case 32: launch_prefilter<32, KP>(Xc, qn, d, tl, nt, cd, ci, st); break;
-    case 40: launch_prefilter<40, KP>(Xc, qn, d, tl, nt, cd, ci, st); break;
-    case 48: launch_prefilter<48, KP>(Xc, qn, d, tl, nt, cd, ci, st); break;
-    case 56: launch_prefilter<56, KP>(Xc, qn, d, tl, nt, cd, ci, st); break;
-    case 64: launch_prefilter<64, KP>(Xc, qn, d, tl, nt, cd, ci, st); break;
+    case 8: launch_prefilter<8, KP>(Xc, qn, tl, nt, cd, ci, status, st); break;
+    case 16: launch_prefilter<16, KP>(Xc, qn, tl, nt, cd, ci, status, st); break;
+    case 24: launch_prefilter<24, KP>(Xc, qn, tl, nt, cd, ci, status, st); break;
+    case 32: launch_prefilter<32, KP>(Xc, qn, tl, nt, cd, ci, status, st); break;
+    case 40: launch_prefilter<40, KP>(Xc, qn, tl, nt, cd, ci, status, st); break;
+    case 48: launch_prefilter<48, KP>(Xc, qn, tl, nt, cd, ci, status, st); break;
+    case 56: launch_prefilter<56, KP>(Xc, qn, tl, nt, cd, ci, status, st); break;
+    case 64: launch_prefilter<64, KP>(Xc, qn, tl, nt, cd, ci, status, st); break;
     default: throw Error(IASKIT_ERR_UNSUPPORTED, "kNN supports d <= 64");
   }
 }
 
 // Scratch pointers of one kNN run (the allocating and the allocation-free callers).
 struct KnnBufs {
-  float* Xc;
+  int* status;  // device word: DEV_TIMEOUT when a bounded wait gave up
+  float* Xc;    // N x padded_dim(d)
   float* qn;
   double* part;
   double* mean;
@@ -348,19 +449,29 @@ int knn_run(const double* X, int d, int kappa, const std::vector<std::pair<int, 
   IA_CUDA(cudaMemcpyAsync(b.tiles, tiles.data(), nt * sizeof(KnnTile), cudaMemcpyHostToDevice, st));
   IA_CUDA(cudaMemsetAsync(b.rmax, 0, np * sizeof(unsigned), st));
   IA_CUDA(cudaMemsetAsync(b.nfl, 0, sizeof(int), st));
+  IA_CUDA(cudaMemsetAsync(b.status, 0, sizeof(int), st));
   center_partial_kernel<<<dim3(KC_CHUNKS, np), 64, 0, st>>>(X, d, b.probs, b.part);
   IA_LAUNCH_CHECK();
   center_mean_kernel<<<np, 64, 0, st>>>(d, b.probs, b.part, b.mean);
   IA_LAUNCH_CHECK();
-  center_points_kernel<<<nt, KT_QB, 0, st>>>(X, d, b.tiles, b.mean, b.Xc, b.qn, b.rmax);
+  center_points_kernel<<<nt, KT_QB, 0, st>>>(X, d, padded_dim(d), b.tiles, b.mean, b.Xc, b.qn, b.rmax);
   IA_LAUNCH_CHECK();
-  prefilter_dispatch<KP>(b.Xc, b.qn, d, b.tiles, nt, b.cd, b.ci, st);
-  knn_rerank_kernel<KP><<<nt, KT_QB, 0, st>>>(X, d, kappa, padded_dim(d), b.tiles, b.cd, b.ci, b.qn, b.rmax,
-                                              knn, b.flagged, b.nfl);
+  prefilter_dispatch<KP>(b.Xc, b.qn, d, b.tiles, nt, b.cd, b.ci, b.status, st);
+  if (kappa <= 16)
+    knn_rerank_kernel<KP, 16><<<nt, KT_QB, 0, st>>>(X, d, kappa, padded_dim(d), b.tiles, b.cd, b.ci, b.qn,
+                                                    b.rmax, knn, b.flagged, b.nfl);
+  else if (kappa <= 32)
+    knn_rerank_kernel<KP, 32><<<nt, KT_QB, 0, st>>>(X, d, kappa, padded_dim(d), b.tiles, b.cd, b.ci, b.qn,
+                                                    b.rmax, knn, b.flagged, b.nfl);
+  else
+    knn_rerank_kernel<KP, RR_MAXK><<<nt, KT_QB, 0, st>>>(X, d, kappa, padded_dim(d), b.tiles, b.cd, b.ci,
+                                                         b.qn, b.rmax, knn, b.flagged, b.nfl);
   IA_LAUNCH_CHECK();
-  int nf = 0;
+  int nf = 0, dev_status = 0;
   IA_CUDA(cudaMemcpyAsync(&nf, b.nfl, sizeof(int), cudaMemcpyDeviceToHost, st));
+  IA_CUDA(cudaMemcpyAsync(&dev_status, b.status, sizeof(int), cudaMemcpyDeviceToHost, st));
   IA_CUDA(cudaStreamSynchronize(st));
+  if (dev_status & DEV_TIMEOUT) throw Error(IASKIT_ERR_TIMEOUT, "kNN tensor-core wait expired");
   if (nf > 0) {
     knn_fallback_kernel<<<nf, FB_THREADS, 0, st>>>(X, d, kappa, b.tiles, b.flagged, knn);
     IA_LAUNCH_CHECK();
@@ -387,22 +498,23 @@ int knn_bruteforce(const double* X, int N, int d, int kappa, int* knn,
   int min_n = N;
   for (const auto& pr : problems) min_n = std::min(min_n, pr.second);
   if (kappa < 1 || kappa > min_n - 1) throw Error(IASKIT_ERR_ARG, "kappa must be in [1, N-1]");
-  if (kappa > FB_MAXK - 16) throw Error(IASKIT_ERR_UNSUPPORTED, "kappa > 48");
+  if (kappa > RR_MAXK) throw Error(IASKIT_ERR_UNSUPPORTED, "kappa > 48");
   if (d > 64) throw Error(IASKIT_ERR_UNSUPPORTED, "kNN supports d <= 64");
   const int np = (int)problems.size();
   const std::vector<KnnTile> tiles = knn_tiles(problems);
   const bool wide = kappa + 8 > 32;
   const int KP = wide ? 64 : 32;
   KnnBufs b{};
-  b.Xc = s.x32.ensure_n<float>((size_t)N * d);
+  b.status = s.status.ensure_n<int>(1);
+  b.Xc = s.x32.ensure_n<float>((size_t)N * padded_dim(d));
   b.qn = s.qnorm.ensure_n<float>(N);
   b.part = s.part.ensure_n<double>((size_t)np * KC_CHUNKS * d);
   b.mean = s.mean.ensure_n<double>((size_t)np * d);
   b.rmax = s.rmax.ensure_n<unsigned>(np);
   b.probs = s.probs.ensure_n<int2>(np);
   b.tiles = s.tiles.ensure_n<KnnTile>(tiles.size());
-  b.cd = s.cand_d.ensure_n<float>((size_t)N * KP);
-  b.ci = s.cand_i.ensure_n<int>((size_t)N * KP);
+  b.cd = s.cand_d.ensure_n<float>((size_t)N * KT_SUB * KP);
+  b.ci = s.cand_i.ensure_n<int>((size_t)N * KT_SUB * KP);
   b.flagged = s.flagged.ensure_n<int2>(N);
   b.nfl = s.counter.ensure_n<int>(1);
   // algorithmic work of the prefilter: one multiply-add per pair and coordinate
@@ -426,18 +538,19 @@ namespace {
 constexpr int64_t NA_MAX_N = 32768;             // points
 constexpr int64_t NA_MAX_ND = int64_t(1) << 20;  // N * d coordinates
 constexpr int NA_KP = 32;                        // candidates kept per query (kappa <= 24)
-constexpr size_t NA_X32 = 0;
-constexpr size_t NA_QN = NA_X32 + sizeof(float) * NA_MAX_ND;
+constexpr size_t NA_X32 = 0;                     // rows padded to a multiple of 8 floats
+constexpr size_t NA_QN = NA_X32 + sizeof(float) * (NA_MAX_ND + 7 * NA_MAX_N);
 constexpr size_t NA_PART = NA_QN + sizeof(float) * NA_MAX_N;
 constexpr size_t NA_MEAN = NA_PART + sizeof(double) * KC_CHUNKS * 64;
 constexpr size_t NA_CD = NA_MEAN + sizeof(double) * 64;
-constexpr size_t NA_CI = NA_CD + sizeof(float) * NA_MAX_N * NA_KP;
-constexpr size_t NA_FLAGGED = NA_CI + sizeof(int) * NA_MAX_N * NA_KP;
+constexpr size_t NA_CI = NA_CD + sizeof(float) * NA_MAX_N * KT_SUB * NA_KP;
+constexpr size_t NA_FLAGGED = NA_CI + sizeof(int) * NA_MAX_N * KT_SUB * NA_KP;
 constexpr size_t NA_TILES = NA_FLAGGED + sizeof(int2) * NA_MAX_N;
 constexpr size_t NA_COUNTER = NA_TILES + sizeof(KnnTile) * (NA_MAX_N / KT_QB);
 constexpr size_t NA_RMAX = NA_COUNTER + 256;
 constexpr size_t NA_PROBS = NA_RMAX + 256;
-constexpr size_t NA_BYTES = NA_PROBS + 256;   // about 12.5 MiB
+constexpr size_t NA_STATUS = NA_PROBS + 256;
+constexpr size_t NA_BYTES = NA_STATUS + 256;   // about 37.3 MiB
 
 __device__ __align__(256) unsigned char g_knn_noalloc_scratch[NA_BYTES];
 
@@ -462,6 +575,7 @@ unsigned char* noalloc_scratch() {
 void knn_noalloc(const double* X, int N, int d, int kappa, int* knn, cudaStream_t st) {
   unsigned char* base = noalloc_scratch();
   KnnBufs b{};
+  b.status = reinterpret_cast<int*>(base + NA_STATUS);
   b.Xc = reinterpret_cast<float*>(base + NA_X32);
   b.qn = reinterpret_cast<float*>(base + NA_QN);
   b.part = reinterpret_cast<double*>(base + NA_PART);

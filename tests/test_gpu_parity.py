@@ -127,15 +127,26 @@ def test_two_points(gpu_lib):
 
 
 def test_duplicate_points_use_exact_fallback(gpu_lib):
-    # 40 copies of each of 50 points: every kNN cut falls inside a run of exact ties,
-    # which the FP32 prefilter cannot certify, so the exact scan decides by index
+    # 200 copies of each of 10 points: every query has 199 exact ties at distance 0,
+    # more than the prefilter keeps (4 lists of 32), so no cut can be certified and the
+    # exact scan decides by index
+    ia = gpu_lib
+    rng = np.random.default_rng(4)
+    X = np.repeat(rng.random((10, 3)), 200, axis=0)[rng.permutation(2000)]
+    ia.iaskit_factor(X, 0.5, 1.0, 64, 16, 1e-8)
+    assert np.array_equal(ia.iaskit_get_knn(len(X), 16), oracle.knn_bruteforce(X, 16))
+    assert np.array_equal(ia.iaskit_get_perm(len(X)), oracle.build_tree(X, 64).perm)
+    assert ia.iaskit_stats()["knn_fallback"] > 0
+
+
+def test_duplicate_points_within_the_candidate_lists(gpu_lib):
+    # 40 copies of each of 50 points: the 39 ties of a query fit in the candidate lists,
+    # so the re-rank orders them by index without the exact scan
     ia = gpu_lib
     rng = np.random.default_rng(4)
     X = np.repeat(rng.random((50, 3)), 40, axis=0)[rng.permutation(2000)]
     ia.iaskit_factor(X, 0.5, 1.0, 64, 16, 1e-8)
     assert np.array_equal(ia.iaskit_get_knn(len(X), 16), oracle.knn_bruteforce(X, 16))
-    assert np.array_equal(ia.iaskit_get_perm(len(X)), oracle.build_tree(X, 64).perm)
-    assert ia.iaskit_stats()["knn_fallback"] > 0
 
 
 def test_error_codes(gpu_lib):
