@@ -454,6 +454,8 @@ def main():
         "knn_exact_fallback_rows": st.get("knn_fallback"),
         "gpu_launches": chosen["launches"], "clocks": clocks, "roofline": roof,
         "kernel_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in kern.items() if v["ms"] > 0},
+        "kernel_tflops": {k: round(v["flops"] / (v["ms"] / 1e3) / 1e12, 3)
+                          for k, v in kern.items() if v["ms"] > 0 and v["flops"] > 0},
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * w.N * (w.d + w.nrhs), "d2h_bytes_per_step": 8 * w.N * w.nrhs},
     }

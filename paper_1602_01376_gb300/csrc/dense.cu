@@ -4,9 +4,9 @@
 //  * kernel_blocks   Gaussian kernel blocks from coordinates (Sec. I, eq. gaussian):
 //                    sampled blocks K(samples, columns), leaf blocks lambda I + K_aa
 //                    and the U blocks K_{l r~}, K_{r l~} (eq. uv-askit).
-//  * cpqr_id         column-pivoted Householder QR of a sampled block and the
+//  * cpqr_id         column-pivoted Householder QR of a sampled block; the
 //                    interpolative decomposition T = R11^{-1} R12 (Sec. II-B; GEQP3 and
-//                    GELS in Sec. II-C).  Trailing column norms are recomputed from the
+//                    GELS in Sec. II-C) is then trsm_upper_batched.  Trailing column norms are recomputed from the
 //                    updated block at every step, accumulated in FP64; pivot ties go to
 //                    the lowest column.
 //  * getrf / getrs   LU with partial pivoting (ties to the lowest row) and the
@@ -228,60 +228,67 @@ __global__ void __launch_bounds__(QR_THREADS) cpqr_kernel(const CpqrDescT<T>* de
     const T beta = vv > 0.0 ? (T)(2.0 / vv) : (T)0;
     const int tcount = (nr - k + 31) / 32;  // rows per lane of the trailing column
     if (sizeof(T) == 4 && tcount <= QR_RPL) {
-      // FP32: a warp keeps two columns in registers between the dot products and the
-      // updates, so that the two columns' loads and reductions overlap (FP64 is bound
-      // by its arithmetic pipe and keeps the two-pass form below)
-      for (int j = k + 1 + 2 * warp; j < nc; j += 2 * QR_WARPS) {
-        const bool two = j + 1 < nc;
-        T* c0 = A + (size_t)j * ld;
-        T* c1 = A + (size_t)(two ? j + 1 : j) * ld;
-        T x0[QR_RPL], x1[QR_RPL];
-        T d0 = 0, d1 = 0;
+      // FP32: a warp keeps CW columns in registers between the dot products and the
+      // updates, so that their loads and reductions overlap (FP64 is bound by its
+      // arithmetic pipe and keeps the two-pass form below)
+      constexpr int CW = 4;
+      for (int j = k + 1 + CW * warp; j < nc; j += CW * QR_WARPS) {
+        T* cp[CW];
+        bool has[CW];
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+          has[c] = j + c < nc;
+          cp[c] = A + (size_t)(has[c] ? j + c : j) * ld;
+        }
+        T x[CW][QR_RPL];
 #pragma unroll
         for (int t = 0; t < QR_RPL; ++t) {
           const int i = k + lane + 32 * t;
           const bool in = t < tcount && i < nr;
-          x0[t] = in ? c0[i] : (T)0;
-          x1[t] = in ? c1[i] : (T)0;
+#pragma unroll
+          for (int c = 0; c < CW; ++c) x[c][t] = in ? cp[c][i] : (T)0;
         }
+        T dt[CW];
+#pragma unroll
+        for (int c = 0; c < CW; ++c) dt[c] = 0;
 #pragma unroll
         for (int t = 0; t < QR_RPL; ++t) {
           const int i = k + lane + 32 * t;
           const T vi = (t < tcount && i < nr) ? v[i - k] : (T)0;
-          d0 = fma(vi, x0[t], d0);
-          d1 = fma(vi, x1[t], d1);
+#pragma unroll
+          for (int c = 0; c < CW; ++c) dt[c] = fma(vi, x[c][t], dt[c]);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          d0 += __shfl_xor_sync(0xffffffffu, d0, o);
-          d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-        }
-        const T f0 = beta * d0, f1 = beta * d1;
-        T p0 = 0, p1 = 0;
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int c = 0; c < CW; ++c) dt[c] += __shfl_xor_sync(0xffffffffu, dt[c], o);
+        T pn[CW];
+#pragma unroll
+        for (int c = 0; c < CW; ++c) pn[c] = 0;
 #pragma unroll
         for (int t = 0; t < QR_RPL; ++t) {
           const int i = k + lane + 32 * t;
           if (t < tcount && i < nr) {
             const T vi = v[i - k];
-            const T a0 = x0[t] - f0 * vi, a1 = x1[t] - f1 * vi;
-            c0[i] = a0;
-            if (two) c1[i] = a1;
-            if (i > k) {
-              p0 = fma(a0, a0, p0);
-              p1 = fma(a1, a1, p1);
+#pragma unroll
+            for (int c = 0; c < CW; ++c) {
+              const T a = x[c][t] - (beta * dt[c]) * vi;
+              if (has[c]) cp[c][i] = a;
+              if (i > k) pn[c] = fma(a, a, pn[c]);
             }
           }
         }
-        double n0 = (double)p0, n1 = (double)p1;
+        double nn[CW];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          n0 += __shfl_xor_sync(0xffffffffu, n0, o);
-          n1 += __shfl_xor_sync(0xffffffffu, n1, o);
-        }
-        if (lane == 0) {
-          norms[j] = n0;
-          if (two) norms[j + 1] = n1;
-        }
+        for (int c = 0; c < CW; ++c) nn[c] = (double)pn[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int c = 0; c < CW; ++c) nn[c] += __shfl_xor_sync(0xffffffffu, nn[c], o);
+        if (lane == 0)
+#pragma unroll
+          for (int c = 0; c < CW; ++c)
+            if (has[c]) norms[j + c] = nn[c];
       }
     } else {
     for (int j = k + 1 + warp; j < nc; j += QR_WARPS) {
@@ -307,23 +314,7 @@ __global__ void __launch_bounds__(QR_THREADS) cpqr_kernel(const CpqrDescT<T>* de
     s = k + 1;
     __syncthreads();
   }
-  // T = R11^{-1} R12 in place, column-oriented back substitution; a zero diagonal
-  // entry of R11 gives a zero row of T.
-  const int nt = nc - s;
-  for (int kk = s - 1; kk >= 0 && nt > 0; --kk) {
-    const T rkk = A[(size_t)kk + (size_t)kk * ld];
-    for (int j = threadIdx.x; j < nt; j += QR_THREADS) {
-      T* a = &A[(size_t)kk + (size_t)(s + j) * ld];
-      *a = (rkk == (T)0) ? (T)0 : *a / rkk;
-    }
-    __syncthreads();
-    const int64_t items = (int64_t)kk * nt;
-    for (int64_t t = threadIdx.x; t < items; t += QR_THREADS) {
-      const int i = (int)(t % kk), j = s + (int)(t / kk);
-      A[(size_t)i + (size_t)j * ld] -= A[(size_t)i + (size_t)kk * ld] * A[(size_t)kk + (size_t)j * ld];
-    }
-    __syncthreads();
-  }
+  // T = R11^{-1} R12 follows in trsm_upper_batched (blocked, many blocks per node)
   for (int j = threadIdx.x; j < nc; j += QR_THREADS) D.piv[j] = piv[j];
   if (threadIdx.x == 0) *D.rank = s;
 }
@@ -520,7 +511,7 @@ __device__ __forceinline__ void load_row(const T* X, int row, T (&out)[NC]) {
 // X (n x NC chunk of right-hand sides) lives in shared memory row-major, so that the
 // register-tiled updates read a row of X with 16-byte broadcasts.  The 32 x 32
 // diagonal blocks are read into registers before their sequential substitution.
-template <typename T, int NC>
+template <typename T, int NC, bool UPPER_ONLY>
 __global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>* descs) {
   extern __shared__ __align__(16) unsigned char rs_sh[];
   T* X = reinterpret_cast<T*>(rs_sh);  // n x NC, row-major, X[i * NC + c]
@@ -537,7 +528,7 @@ __global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>
     X[(size_t)i * NC + c] = c < nc ? D.B[(size_t)i + (size_t)(c0 + c) * D.ldb] : (T)0;
   }
   __syncthreads();
-  if (tid < nc) {
+  if (!UPPER_ONLY && tid < nc) {
     for (int k = 0; k < n; ++k) {
       const int p = D.ipiv[k];
       if (p != k) {
@@ -549,7 +540,7 @@ __global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>
   }
   __syncthreads();
   // forward substitution with the unit lower triangle
-  for (int b0 = 0; b0 < n; b0 += 32) {
+  for (int b0 = 0; b0 < (UPPER_ONLY ? 0 : n); b0 += 32) {
     const int bs = min(32, n - b0);
     if (warp < nc) {
       if constexpr (sizeof(T) == 4) {
@@ -608,7 +599,8 @@ __global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>
 #pragma unroll
           for (int k = 31; k >= 0; --k) {
             if (k < bs) {
-              if (lane == k) x /= u[k];
+              // a zero diagonal entry (rank-deficient R11) gives a zero row in the ID
+              if (lane == k) x = (UPPER_ONLY && u[k] == (T)0) ? (T)0 : x / u[k];
               const T xk = __shfl_sync(0xffffffffu, x, k);
               if (lane < k) x -= u[k] * xk;
             }
@@ -619,7 +611,10 @@ __global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>
         for (int c = warp; c < nc; c += RS_THREADS / 32) {
           T x = lane < bs ? X[(size_t)(b0 + lane) * NC + c] : (T)0;
           for (int k = bs - 1; k >= 0; --k) {
-            if (lane == k) x /= LU[(size_t)(b0 + k) + (size_t)(b0 + k) * ld];
+            if (lane == k) {
+              const T dk = LU[(size_t)(b0 + k) + (size_t)(b0 + k) * ld];
+              x = (UPPER_ONLY && dk == (T)0) ? (T)0 : x / dk;
+            }
             const T xk = __shfl_sync(0xffffffffu, x, k);
             if (lane < k) x -= LU[(size_t)(b0 + lane) + (size_t)(b0 + k) * ld] * xk;
           }
@@ -834,18 +829,31 @@ unsigned grid_for(int64_t work, int threads, unsigned cap = 65535u) {
   return (unsigned)std::min<int64_t>(b, cap);
 }
 
-template <typename T, int NC>
+template <typename T, int NC, bool UPPER_ONLY>
 void launch_getrs(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int max_cols,
                   cudaStream_t st) {
   const size_t smem = (size_t)max_n * NC * sizeof(T);
   if (smem > 220 * 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "LU block too large");
   if (smem > 48 * 1024)
-    IA_CUDA(cudaFuncSetAttribute(getrs_kernel<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    IA_CUDA(cudaFuncSetAttribute(getrs_kernel<T, NC, UPPER_ONLY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
   if (ndesc > 65535) throw Error(IASKIT_ERR_UNSUPPORTED, "more than 65535 LU solves in one launch");
   dim3 grid(ceil_div(max_cols, NC), ndesc);
-  getrs_kernel<T, NC><<<grid, RS_THREADS, smem, st>>>(descs_dev);
+  getrs_kernel<T, NC, UPPER_ONLY><<<grid, RS_THREADS, smem, st>>>(descs_dev);
   IA_LAUNCH_CHECK();
+}
+
+template <typename T, bool UPPER_ONLY>
+void solve_dispatch(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int max_cols, cudaStream_t st) {
+  // chunk width: 16 columns while the chunk stays small enough for 3 blocks per SM
+  if (max_cols >= 16 && (size_t)max_n * 16 * sizeof(T) <= 72 * 1024)
+    launch_getrs<T, 16, UPPER_ONLY>(descs_dev, ndesc, max_n, max_cols, st);
+  else if (max_cols >= 8 && (size_t)max_n * 8 * sizeof(T) <= 144 * 1024)
+    launch_getrs<T, 8, UPPER_ONLY>(descs_dev, ndesc, max_n, max_cols, st);
+  else if (max_cols >= 4)
+    launch_getrs<T, 4, UPPER_ONLY>(descs_dev, ndesc, max_n, max_cols, st);
+  else
+    launch_getrs<T, 1, UPPER_ONLY>(descs_dev, ndesc, max_n, max_cols, st);
 }
 
 }  // namespace
@@ -905,15 +913,15 @@ void getrs_batched(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int m
                    cudaStream_t st) {
   if (ndesc <= 0 || max_cols <= 0) return;
   ProfScope _ps(pk_of<T>(PK_GETRS), st);
-  // chunk width: 16 columns while the chunk stays small enough for 3 blocks per SM
-  if (max_cols >= 16 && (size_t)max_n * 16 * sizeof(T) <= 72 * 1024)
-    launch_getrs<T, 16>(descs_dev, ndesc, max_n, max_cols, st);
-  else if (max_cols >= 8 && (size_t)max_n * 8 * sizeof(T) <= 144 * 1024)
-    launch_getrs<T, 8>(descs_dev, ndesc, max_n, max_cols, st);
-  else if (max_cols >= 4)
-    launch_getrs<T, 4>(descs_dev, ndesc, max_n, max_cols, st);
-  else
-    launch_getrs<T, 1>(descs_dev, ndesc, max_n, max_cols, st);
+  solve_dispatch<T, false>(descs_dev, ndesc, max_n, max_cols, st);
+}
+
+template <typename T>
+void trsm_upper_batched(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int max_cols,
+                        cudaStream_t st) {
+  if (ndesc <= 0 || max_cols <= 0 || max_n <= 0) return;
+  ProfScope _ps(pk_of<T>(PK_GETRS), st);
+  solve_dispatch<T, true>(descs_dev, ndesc, max_n, max_cols, st);
 }
 
 template <typename T>
@@ -1042,6 +1050,7 @@ void check_finite(const double* x, int64_t n, int* dev_status, cudaStream_t st) 
   template void assemble_P<T>(const PDescT<T>*, int, int, cudaStream_t);                          \
   template void getrf_batched<T>(const LuDescT<T>*, int, int, int*, cudaStream_t);                \
   template void getrs_batched<T>(const LuSolveDescT<T>*, int, int, int, cudaStream_t);            \
+  template void trsm_upper_batched<T>(const LuSolveDescT<T>*, int, int, int, cudaStream_t);       \
   template void gemm_grouped<T>(const GemmDescT<T>*, const GemmTile*, int, GemmShape,             \
                                 cudaStream_t);                                                   \
   template void copy_batched<T>(const CopyDescT<T>*, int, int64_t, cudaStream_t);                 \

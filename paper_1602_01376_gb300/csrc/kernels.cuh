@@ -122,7 +122,8 @@ void kernel_blocks(const double* Xp, const double* xnorm, int d, const KDescT<T>
 // out[i] = sum_k Xp[i][k]^2 in FP64, coordinates in order.
 void point_norms(const double* Xp, int N, int d, double* out, cudaStream_t st);
 
-// Column-pivoted Householder QR + interpolative decomposition of each block.
+// Column-pivoted Householder QR of each block (the ID's T follows with
+// trsm_upper_batched).
 // A (nrows x ncols, ld) is overwritten: its first s rows hold, in pivoted column
 // order, R11 and T = R11^{-1} R12 in place of R12.  piv receives the column
 // permutation; rank[0] receives s.  Column norms are accumulated in FP64 for both
@@ -176,6 +177,11 @@ struct LuSolveDescT {
 template <typename T>
 void getrs_batched(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int max_cols,
                    cudaStream_t st);
+// B <- U^{-1} B with U the upper triangle of the n x n block at LU (ipiv unused): the
+// ID's T = R11^{-1} R12 after cpqr_id.  A zero diagonal entry gives a zero row.
+template <typename T>
+void trsm_upper_batched(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int max_cols,
+                        cudaStream_t st);
 
 // C <- alpha * A * B + beta * C (column-major, no transposes) for each descriptor.
 template <typename T>

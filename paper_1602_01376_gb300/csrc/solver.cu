@@ -1037,11 +1037,30 @@ class Solver {
       for (int i = 0; i < nt; ++i) {
         const Node& n = nd[node_of(i)];
         rank_of[i] = i < nk ? rall[node_of(i)] : rlrn[node_of(i)];
-        // Householder update (dot + axpy) and norm recomputation per step, then R11^{-1} R12
+        // Householder update (dot + axpy) and norm recomputation per step
         for (int k = 0; k < rank_of[i]; ++k) qr_flops += 6.0 * (n.nsamp - k) * (double)(n.ncols - k);
-        qr_flops += (double)rank_of[i] * rank_of[i] * (n.ncols - rank_of[i]);
       }
       prof().flops[pk_of<TS>(PK_CPQR)] += qr_flops;
+      {  // T = R11^{-1} R12 in place (the ID), many blocks per node
+        std::vector<LuSolveDescT<TS>> td;
+        int max_s = 0, max_t = 0;
+        for (int i = 0; i < nt; ++i) {
+          const Node& n = nd[node_of(i)];
+          const int si = rank_of[i], ti = n.ncols - si;
+          if (si <= 0 || ti <= 0) continue;
+          td.push_back(LuSolveDescT<TS>{A + aoff[i], nullptr, A + aoff[i] + (size_t)si * n.nsamp, si, n.nsamp,
+                                        n.nsamp, ti});
+          max_s = std::max(max_s, si);
+          max_t = std::max(max_t, ti);
+        }
+        if (!td.empty()) {
+          arena.clear();
+          size_t otd = arena.push(td);
+          base = upload_arena();
+          prof().flops[pk_of<TS>(PK_GETRS)] += getrs_flops(td) / 2;  // one triangle
+          trsm_upper_batched<TS>((const LuSolveDescT<TS>*)(base + otd), (int)td.size(), max_s, max_t, st);
+        }
+      }
       // P and skeletons of every ID: straight into the final storage without learning,
       // else into temporaries from which the chosen ID is copied
       std::vector<int> chosen(nk);  // descriptor index kept by plain node i
