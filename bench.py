@@ -176,8 +176,9 @@ def config_of(w):
 # ------------------------------------------------------------------- GPU leg
 FP32_LANES_PER_SM = 128              # GB300: FP32 FMA lanes per SM
 PEAK_CLASS = {                       # kernel classes whose arithmetic is FP32
-    "kernel_blocks_f32", "cpqr_id_f32", "getrf_f32", "getrs_f32", "gemm_f32", "knn"}
+    "kernel_blocks_f32", "cpqr_id_f32", "getrf_f32", "getrs_f32", "gemm_f32"}
 TENSOR_CLASS = {                     # tensor-core classes: nominal dense rate / bf16's
+    "knn": (1.1 / 2.25, "TF32"),     # tcgen05 3xTF32 distance tiles, algorithmic work once
     "mlp_bf16": (1.0, "BF16"),
 }
 
