@@ -35,58 +35,85 @@ template <>
 __device__ __forceinline__ float kexp<float>(float x) { return expf(x); }
 
 // ------------------------------------------------------------ kernel blocks
-// One thread per row and group of KB_C consecutive columns, so that the row's
-// coordinates are read once per group.  FP64 blocks use the Gram form
+// One block per 64 x 64 tile of one descriptor.  The tile's row and column points are
+// staged in shared memory (transposed, [coordinate][point]) and every thread forms a
+// 4 x 4 register tile of entries.  FP64 blocks use the Gram form
 // |x|^2 + |y|^2 - 2 x.y with the squared norms precomputed (one FMA per coordinate;
 // the cancellation error, about 2^-52 (|x|^2 + |y|^2), moves a kernel value by a
 // relative 2^-52 (|x|^2 + |y|^2) / (2 h^2)); FP32 blocks keep the difference form,
 // whose error is relative to the distance itself.
-constexpr int KB_C = 4;
+constexpr int KB_T = 64;        // tile edge
+constexpr int KB_THREADS = 256; // 16 x 16 threads, 4 x 4 entries each
 template <typename T>
-__global__ void kernel_blocks_kernel(const double* Xp, const double* xn, int d, const KDescT<T>* descs,
-                                     int ndesc) {
-  for (int q = blockIdx.y; q < ndesc; q += gridDim.y) {
-    const KDescT<T> D = descs[q];
-    const T scale = (T)D.scale;
-    const int ncg = (D.ncols + KB_C - 1) / KB_C;
-    const int64_t total = (int64_t)D.nrows * ncg;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-      const int i = (int)(e % D.nrows), j0 = (int)(e / D.nrows) * KB_C;
-      const int r = D.rows ? D.rows[i] : D.row0 + i;
-      const double* xr = Xp + (size_t)r * d;
-      int c[KB_C];
-      const double* xc[KB_C];
+__global__ void __launch_bounds__(KB_THREADS) kernel_blocks_kernel(const double* Xp, const double* xn, int d,
+                                                                   const KDescT<T>* descs) {
+  extern __shared__ __align__(16) unsigned char kb_sh[];
+  T* Xr = reinterpret_cast<T*>(kb_sh);         // [d][KB_T]
+  T* Xc = Xr + (size_t)d * KB_T;               // [d][KB_T]
+  __shared__ double nr_s[KB_T], nc_s[KB_T];
+  __shared__ int ri_s[KB_T], ci_s[KB_T];
+  const KDescT<T> D = descs[blockIdx.y];
+  const int tr = (D.nrows + KB_T - 1) / KB_T, tcn = (D.ncols + KB_T - 1) / KB_T;
+  const int tid = threadIdx.x;
+  for (int tile = blockIdx.x; tile < tr * tcn; tile += gridDim.x) {
+  const int i0 = (tile % tr) * KB_T, j0 = (tile / tr) * KB_T;
+  __syncthreads();  // the previous tile's readers are done with the staging buffers
+  if (tid < KB_T) {
+    const int i = min(i0 + tid, D.nrows - 1);
+    const int r = D.rows ? D.rows[i] : D.row0 + i;
+    ri_s[tid] = r;
+    nr_s[tid] = xn ? xn[r] : 0.0;
+  } else if (tid < 2 * KB_T) {
+    const int j = min(j0 + tid - KB_T, D.ncols - 1);
+    const int c = D.colsA ? (j < D.nA ? D.colsA[j] : D.colsB[j - D.nA]) : D.col0 + j;
+    ci_s[tid - KB_T] = c;
+    nc_s[tid - KB_T] = xn ? xn[c] : 0.0;
+  }
+  __syncthreads();
+  for (int e = tid; e < KB_T * d; e += KB_THREADS) {
+    const int p = e / d, k = e % d;
+    Xr[(size_t)k * KB_T + p] = (T)Xp[(size_t)ri_s[p] * d + k];
+    Xc[(size_t)k * KB_T + p] = (T)Xp[(size_t)ci_s[p] * d + k];
+  }
+  __syncthreads();
+  const int tx = tid % 16, ty = tid / 16;
+  T acc[4][4];
 #pragma unroll
-      for (int u = 0; u < KB_C; ++u) {
-        const int j = min(j0 + u, D.ncols - 1);
-        c[u] = D.colsA ? (j < D.nA ? D.colsA[j] : D.colsB[j - D.nA]) : D.col0 + j;
-        xc[u] = Xp + (size_t)c[u] * d;
-      }
-      T acc[KB_C];
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int u = 0; u < KB_C; ++u) acc[u] = 0;
-      for (int k = 0; k < d; ++k) {
-        const T a = (T)xr[k];
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+  for (int k = 0; k < d; ++k) {
+    T xr[4], xc[4];
 #pragma unroll
-        for (int u = 0; u < KB_C; ++u) {
-          if (std::is_same<T, double>::value) {
-            acc[u] = fma(a, (T)xc[u][k], acc[u]);
-          } else {
-            const T t = a - (T)xc[u][k];
-            acc[u] = fma(t, t, acc[u]);
-          }
+    for (int a = 0; a < 4; ++a) {
+      xr[a] = Xr[(size_t)k * KB_T + tx + 16 * a];
+      xc[a] = Xc[(size_t)k * KB_T + ty + 16 * a];
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        if (std::is_same<T, double>::value) {
+          acc[a][b] = fma(xr[a], xc[b], acc[a][b]);
+        } else {
+          const T t = xr[a] - xc[b];
+          acc[a][b] = fma(t, t, acc[a][b]);
         }
       }
+  }
+  const T scale = (T)D.scale;
 #pragma unroll
-      for (int u = 0; u < KB_C; ++u) {
-        if (j0 + u >= D.ncols) break;
-        T d2 = acc[u];
-        if (std::is_same<T, double>::value) d2 = fmax((xn[r] + xn[c[u]]) - 2.0 * acc[u], 0.0);
-        T v = kexp<T>(d2 * scale);
-        if (r == c[u]) v += (T)D.diag;
-        D.out[(size_t)i + (size_t)(j0 + u) * D.ld] = v;
-      }
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int li = tx + 16 * a, lj = ty + 16 * b;
+      const int i = i0 + li, j = j0 + lj;
+      if (i >= D.nrows || j >= D.ncols) continue;
+      T d2 = acc[a][b];
+      if (std::is_same<T, double>::value) d2 = fmax((nr_s[li] + nc_s[lj]) - 2.0 * acc[a][b], 0.0);
+      T v = kexp<T>(d2 * scale);
+      if (ri_s[li] == ci_s[lj]) v += (T)D.diag;
+      D.out[(size_t)i + (size_t)j * D.ld] = v;
     }
   }
 }
@@ -861,11 +888,18 @@ void solve_dispatch(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int 
 template <typename T>
 void kernel_blocks(const double* Xp, const double* xnorm, int d, const KDescT<T>* descs_dev, int ndesc,
                    int64_t max_entries, cudaStream_t st) {
-  if (ndesc <= 0) return;
+  if (ndesc <= 0 || max_entries <= 0) return;
   if (std::is_same<T, double>::value && !xnorm) throw Error(IASKIT_ERR_ARG, "kernel blocks need point norms");
+  if (ndesc > 65535) throw Error(IASKIT_ERR_UNSUPPORTED, "more than 65535 kernel blocks in one launch");
+  // blocks per descriptor: about its tile count (the kernel strides over the tiles)
+  const int64_t max_tiles = std::min<int64_t>(max_entries / (KB_T * KB_T / 2) + 1, 4096);
+  const size_t smem = (size_t)2 * KB_T * d * sizeof(T);
+  if (smem > 200 * 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "dimension too large for kernel blocks");
+  if (smem > 48 * 1024)
+    IA_CUDA(cudaFuncSetAttribute(kernel_blocks_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ProfScope _ps(pk_of<T>(PK_KBLOCK), st);
-  dim3 grid(grid_for((max_entries + KB_C - 1) / KB_C, 256, 4096), std::min(ndesc, 65535));
-  kernel_blocks_kernel<T><<<grid, 256, 0, st>>>(Xp, xnorm, d, descs_dev, ndesc);
+  dim3 grid((unsigned)max_tiles, ndesc);
+  kernel_blocks_kernel<T><<<grid, KB_THREADS, smem, st>>>(Xp, xnorm, d, descs_dev);
   IA_LAUNCH_CHECK();
 }
 
