@@ -176,9 +176,11 @@ def config_of(w):
 # ------------------------------------------------------------------- GPU leg
 FP32_LANES_PER_SM = 128              # GB300: FP32 FMA lanes per SM
 PEAK_CLASS = {                       # kernel classes whose arithmetic is FP32
-    "kernel_blocks_f32", "cpqr_id_f32", "getrf_f32", "getrs_f32", "gemm_f32"}
+    "kernel_blocks_f32", "cpqr_id_f32", "getrf_f32", "getrs_f32"}
+PAIR_INSTR_PER_MAC = 12              # FP32 instructions of one FP32-pair multiply-add
 TENSOR_CLASS = {                     # tensor-core classes: nominal dense rate / bf16's
     "knn": (1.1 / 2.25, "TF32"),     # tcgen05 3xTF32 distance tiles, algorithmic work once
+    "gemm_f32": (1.1 / 2.25, "TF32"),  # tcgen05 3xTF32 tiles (FP32 CUDA-core tiles with gemm_tc=0)
     "mlp_bf16": (1.0, "BF16"),
 }
 
@@ -194,6 +196,10 @@ def roof_peak(kernel: str, pk: dict, src: str) -> tuple:
 
 
 def alu_peak_tflops(kernel: str, sm_mhz: float) -> tuple:
+    if kernel == "gemm_pair":          # 2 algorithmic flops per pair multiply-add
+        return (SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / PAIR_INSTR_PER_MAC / 1e12,
+                f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 instr/clk x {sm_mhz:.0f} MHz "
+                f"/ {PAIR_INSTR_PER_MAC} instr per pair multiply-add x 2 flops")
     if kernel in PEAK_CLASS:
         return (SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12,
                 f"derived: {SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 FMA/clk x {sm_mhz:.0f} MHz")

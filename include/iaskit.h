@@ -160,6 +160,9 @@ int iaskit_apply_device(const double* d_w, double* d_u, int nrhs);
  *   "keep_candidates" 1: keep candidates, features and scores for iaskit_get_learned (0)
  *   "train_batch"  rows per Adam step of iaskit_sampler_train (4096)
  *   "learned_temp" Gumbel temperature of the learned selection (0 = top scores, default)
+ *   "gemm_tc"      1: FP32 products with more than 16 columns run on the tensor cores as
+ *                  three TF32 products (hi.hi + hi.lo + lo.hi), about FP32 accuracy
+ *                  (default); 0: FP32 CUDA-core tiles [any time]
  *   "problem"      which problem of a batch the introspection calls report (0) [any time]
  * Errors: IASKIT_ERR_ARG for an unknown key or an invalid value.
  */

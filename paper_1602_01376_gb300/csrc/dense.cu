@@ -22,6 +22,7 @@
 #include <climits>
 
 #include "kernels.cuh"
+#include "tc.cuh"
 
 namespace iaskit {
 
@@ -344,6 +345,164 @@ __global__ void __launch_bounds__(QR_THREADS) cpqr_kernel(const CpqrDescT<T>* de
   // T = R11^{-1} R12 follows in trsm_upper_batched (blocked, many blocks per node)
   for (int j = threadIdx.x; j < nc; j += QR_THREADS) D.piv[j] = piv[j];
   if (threadIdx.x == 0) *D.rank = s;
+}
+
+// ------------------------------------------------ FP32 GEMM on the tensor cores
+// C = alpha A B + beta C for one 128 x 128 tile of one descriptor per block.  The K
+// dimension is walked in chunks of 32: each thread holds the next chunk's values of A
+// and B in registers (loaded while the tensor core works on the current chunk), then
+// splits them into TF32 hi/lo pairs and stores them K-major into shared memory, and one
+// thread issues 3 tcgen05 MMAs per 8 values of K (lo.hi, hi.lo, hi.hi) into a 128 x 128
+// FP32 accumulator in TMEM.  One staging buffer per block (64 KB), three blocks per SM,
+// so one block's staging overlaps the others' MMAs.  The epilogue reads the tile back
+// with tcgen05.ld.  Waits are bounded; a wait that gives up stops the block's work and
+// leaves its tile unwritten.
+constexpr int GT_M = 128, GT_N = 128, GT_K = 32, GT_THREADS = 256;
+constexpr int GT_UNITS = GT_M * GT_K / 4 / GT_THREADS;  // 16-byte units per thread per operand
+constexpr long GT_WAIT = 1L << 22;
+static_assert(GT_M == GT_N, "A and B tiles share the staging layout");
+
+// Unit u = (row group rg, K group kg, row rr) holds the 4 consecutive K values of one
+// row: 16 contiguous bytes of the K-major layout (word offset 4 u), so a quarter warp
+// stores 128 contiguous bytes and 8 lanes read 8 consecutive rows of a column of A.
+struct GtFrag {
+  float a[GT_UNITS][4], b[GT_UNITS][4];
+};
+__device__ __forceinline__ void gt_load(const GemmDescT<float>& D, int m0, int n0, int k0, GtFrag& f) {
+  const float* A = D.A + (size_t)m0 + (size_t)k0 * D.lda;  // A: M x K column-major
+  const float* B = D.B + (size_t)k0 + (size_t)n0 * D.ldb;  // B: K x N column-major
+  const int ra = D.M - m0, rb = D.N - n0, kk = D.K - k0;
+#pragma unroll
+  for (int i = 0; i < GT_UNITS; ++i) {
+    const int u = threadIdx.x + i * GT_THREADS;
+    const int r = (u / (8 * (GT_K / 4))) * 8 + (u & 7), k = ((u >> 3) & (GT_K / 4 - 1)) * 4;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      f.a[i][j] = (r < ra && k + j < kk) ? A[(size_t)r + (size_t)(k + j) * D.lda] : 0.0f;
+      f.b[i][j] = (r < rb && k + j < kk) ? B[(size_t)(k + j) + (size_t)r * D.ldb] : 0.0f;
+    }
+  }
+}
+__device__ __forceinline__ void gt_split_store(const float (&v)[4], uint4* hi, uint4* lo) {
+  uint4 h, l;
+  h.x = tc::to_tf32(v[0]);
+  h.y = tc::to_tf32(v[1]);
+  h.z = tc::to_tf32(v[2]);
+  h.w = tc::to_tf32(v[3]);
+  l.x = tc::to_tf32(v[0] - __uint_as_float(h.x));
+  l.y = tc::to_tf32(v[1] - __uint_as_float(h.y));
+  l.z = tc::to_tf32(v[2] - __uint_as_float(h.z));
+  l.w = tc::to_tf32(v[3] - __uint_as_float(h.w));
+  *hi = h;
+  *lo = l;
+}
+__device__ __forceinline__ void gt_store(const GtFrag& f, uint32_t* Ah, uint32_t* Al, uint32_t* Bh,
+                                         uint32_t* Bl) {
+#pragma unroll
+  for (int i = 0; i < GT_UNITS; ++i) {
+    const int u = threadIdx.x + i * GT_THREADS;
+    gt_split_store(f.a[i], reinterpret_cast<uint4*>(Ah) + u, reinterpret_cast<uint4*>(Al) + u);
+    gt_split_store(f.b[i], reinterpret_cast<uint4*>(Bh) + u, reinterpret_cast<uint4*>(Bl) + u);
+  }
+}
+
+__global__ void __launch_bounds__(GT_THREADS, 3) gemm_tc_kernel(const GemmDescT<float>* descs,
+                                                                const GemmTile* tiles, int* status) {
+  extern __shared__ __align__(1024) unsigned char gt_sh[];
+  constexpr int OPW = GT_M * GT_K;  // words of one operand array
+  uint32_t* Ah = reinterpret_cast<uint32_t*>(gt_sh);
+  uint32_t* Al = Ah + OPW;
+  uint32_t* Bh = Al + OPW;
+  uint32_t* Bl = Bh + OPW;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Bl + OPW);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  __shared__ int abort_s;
+  const GemmTile Tl = tiles[blockIdx.x];
+  const GemmDescT<float> D = descs[Tl.desc];
+  const int m0 = Tl.tm * GT_M, n0 = Tl.tn * GT_N;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nk = (D.K + GT_K - 1) / GT_K;
+  if (warp == 0) tc::tmem_alloc(tslot, GT_N);
+  if (tid == 0) {
+    tc::mbar_init(mbar, 1);
+    abort_s = 0;
+  }
+  GtFrag f;
+  if (nk > 0) gt_load(D, m0, n0, 0, f);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  constexpr uint32_t idesc = tc::idesc_tf32(GT_M, GT_N);
+  constexpr uint32_t SBO = (GT_K / 4) * 128;
+  const uint32_t sah = tc::smem_addr(Ah), sal = tc::smem_addr(Al), sbh = tc::smem_addr(Bh),
+                 sbl = tc::smem_addr(Bl);
+  int inflight = -1;  // chunk whose MMAs have not reported completion
+  for (int kc = 0; kc < nk; ++kc) {
+    gt_store(f, Ah, Al, Bh, Bl);  // the MMAs of chunk kc - 1 have completed
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (tid == 0) {
+#pragma unroll
+      for (int ks = 0; ks < GT_K / 8; ++ks) {
+        const uint32_t ko = (uint32_t)ks * 256;
+        const uint64_t dah = tc::smem_desc(sah + ko, 128, SBO), dal = tc::smem_desc(sal + ko, 128, SBO);
+        const uint64_t dbh = tc::smem_desc(sbh + ko, 128, SBO), dbl = tc::smem_desc(sbl + ko, 128, SBO);
+        tc::mma_tf32(tmem, dal, dbh, idesc, kc > 0 || ks > 0);
+        tc::mma_tf32(tmem, dah, dbl, idesc, true);
+        tc::mma_tf32(tmem, dah, dbh, idesc, true);
+      }
+      tc::mma_commit(mbar);
+    }
+    inflight = kc;
+    if (kc + 1 < nk) gt_load(D, m0, n0, (kc + 1) * GT_K, f);  // in flight during the MMAs
+    if (warp == 0) {
+      if (!tc::mbar_wait(mbar, (uint32_t)(kc & 1), GT_WAIT) && lane == 0) {
+        atomicOr(status, DEV_TIMEOUT);
+        abort_s = 1;
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (abort_s) break;
+    inflight = -1;
+  }
+  if (abort_s) {
+    // give the MMAs that did not report completion one more bounded wait before the
+    // block releases its TMEM and shared memory
+    if (warp == 0 && inflight >= 0) tc::mbar_wait(mbar, (uint32_t)(inflight & 1), GT_WAIT);
+  } else {
+    // warp w: TMEM lanes 32 (w % 4) .., columns 64 (w / 4) .. + 63
+    const int row = m0 + (warp & 3) * 32 + lane;
+    const float alpha = (float)D.alpha, beta = (float)D.beta;
+#pragma unroll 1
+    for (int c0 = (warp >> 2) * 64; c0 < (warp >> 2) * 64 + 64; c0 += 16) {
+      float v[16];
+      if (nk > 0) {
+        tc::tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, v);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = 0.0f;
+      }
+      if (row < D.M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = n0 + c0 + j;
+          if (col < D.N) {
+            float* cp = D.C + (size_t)row + (size_t)col * D.ldc;
+            *cp = beta == 0.0f ? alpha * v[j] : alpha * v[j] + beta * *cp;
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_free(tmem, GT_N);
 }
 
 template <typename T>
@@ -960,9 +1119,19 @@ void trsm_upper_batched(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, 
 
 template <typename T>
 void gemm_grouped(const GemmDescT<T>* descs_dev, const GemmTile* tiles_dev, int ntiles,
-                  GemmShape shape, cudaStream_t st) {
+                  GemmShape shape, cudaStream_t st, int* dev_status) {
   if (ntiles <= 0) return;
   ProfScope _ps(pk_of<T>(PK_GEMM), st);
+  if (shape == GEMM_TC) {
+    if (!std::is_same<T, float>::value || !dev_status)
+      throw Error(IASKIT_ERR_ARG, "tensor-core tiles are for FP32 products with a status word");
+    const size_t smem = (size_t)4 * GT_M * GT_K * sizeof(uint32_t) + 64;
+    IA_CUDA(cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    gemm_tc_kernel<<<ntiles, GT_THREADS, smem, st>>>(reinterpret_cast<const GemmDescT<float>*>(descs_dev),
+                                                    tiles_dev, dev_status);
+    IA_LAUNCH_CHECK();
+    return;
+  }
   if (shape == GEMM_SKINNY)
     gemm_kernel<T, 256, 16><<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
   else
@@ -994,6 +1163,107 @@ void permute_rows(const T* in, int ldi, T* out, int ldo, const int* perm, int N,
   ProfScope _ps(PK_MISC, st);
   permute_rows_kernel<T><<<grid_for((int64_t)N * ncols, 256, 8192), 256, 0, st>>>(
       in, ldi, out, ldo, perm, N, ncols, scatter);
+  IA_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------ FP64-accurate products on FP32 pairs
+__global__ void split_pairs_kernel(const double* in, float2* out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = in[i];
+    const float hi = __double2float_rn(x);
+    out[i] = make_float2(hi, __double2float_rn(x - (double)hi));  // same bytes as in[i] when aliased
+  }
+}
+void split_pairs(const double* in, float2* out, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  ProfScope _ps(PK_MISC, st);
+  split_pairs_kernel<<<grid_for(n, 256, 8192), 256, 0, st>>>(in, out, n);
+  IA_LAUNCH_CHECK();
+}
+
+// (s, c) += (ah + al)(bh + bl): the product ah bh exactly as p + e (FMA), the cross
+// terms and e into the low part, p into the high part by Knuth's two-sum (its rounding
+// error into the low part as well).  The explicitly rounded operations keep the
+// compiler from contracting the two-sum into FMAs.
+__device__ __forceinline__ void pair_mac(float ah, float al, float bh, float bl, float& s, float& c) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  c = __fadd_rn(c, __fadd_rn(err, e));
+  s = t;
+}
+
+constexpr int GP_K = 16;
+__global__ void __launch_bounds__(G_THREADS) gemm_pair_kernel(const GemmDescPair* descs, const GemmTile* tiles) {
+  constexpr int TM = GEMM_PAIR_TM, TN = GEMM_PAIR_TN, TX = TM / 4;
+  static_assert(TX * (TN / 4) == G_THREADS, "tile must map to 256 threads");
+  __shared__ __align__(16) float Ash[GP_K][TM + 4], Asl[GP_K][TM + 4];
+  __shared__ __align__(16) float Bsh[GP_K][TN + 4], Bsl[GP_K][TN + 4];
+  const GemmTile Tl = tiles[blockIdx.x];
+  const GemmDescPair D = descs[Tl.desc];
+  const int m0 = Tl.tm * TM, n0 = Tl.tn * TN;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  float s[4][4], c[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) s[a][b] = c[a][b] = 0.0f;
+  for (int k0 = 0; k0 < D.K; k0 += GP_K) {
+#pragma unroll
+    for (int r = 0; r < TM * GP_K / G_THREADS; ++r) {
+      const int e = threadIdx.x + r * G_THREADS;
+      const int am = e % TM, ak = e / TM;
+      const int gm = m0 + am, gk = k0 + ak;
+      const float2 v = (gm < D.M && gk < D.K) ? D.A[(size_t)gm + (size_t)gk * D.lda] : make_float2(0.0f, 0.0f);
+      Ash[ak][am] = v.x;
+      Asl[ak][am] = v.y;
+    }
+    {
+      static_assert(TN * GP_K == G_THREADS, "one B element per thread");
+      const int bk = threadIdx.x % GP_K, bn = threadIdx.x / GP_K;
+      const int gk = k0 + bk, gn = n0 + bn;
+      const double b = (gk < D.K && gn < D.N) ? D.B[(size_t)gk + (size_t)gn * D.ldb] : 0.0;
+      const float bh = __double2float_rn(b);
+      Bsh[bk][bn] = bh;
+      Bsl[bk][bn] = __double2float_rn(b - (double)bh);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GP_K; ++kk) {
+      const float4 ah = *reinterpret_cast<const float4*>(&Ash[kk][4 * tx]);
+      const float4 al = *reinterpret_cast<const float4*>(&Asl[kk][4 * tx]);
+      const float4 bh = *reinterpret_cast<const float4*>(&Bsh[kk][4 * ty]);
+      const float4 bl = *reinterpret_cast<const float4*>(&Bsl[kk][4 * ty]);
+      const float ahv[4] = {ah.x, ah.y, ah.z, ah.w}, alv[4] = {al.x, al.y, al.z, al.w};
+      const float bhv[4] = {bh.x, bh.y, bh.z, bh.w}, blv[4] = {bl.x, bl.y, bl.z, bl.w};
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pair_mac(ahv[r], alv[r], bhv[q], blv[q], s[r][q], c[r][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int gm = m0 + 4 * tx + r, gn = n0 + 4 * ty + q;
+      if (gm < D.M && gn < D.N) {
+        double* cp = D.C + (size_t)gm + (size_t)gn * D.ldc;
+        const double v = (double)s[r][q] + (double)c[r][q];
+        *cp = D.beta == 0.0 ? D.alpha * v : D.alpha * v + D.beta * *cp;
+      }
+    }
+}
+
+void gemm_pair_grouped(const GemmDescPair* descs_dev, const GemmTile* tiles_dev, int ntiles, cudaStream_t st) {
+  if (ntiles <= 0) return;
+  ProfScope _ps(PK_GEMM_PAIR, st);
+  gemm_pair_kernel<<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
   IA_LAUNCH_CHECK();
 }
 
@@ -1086,7 +1356,7 @@ void check_finite(const double* x, int64_t n, int* dev_status, cudaStream_t st) 
   template void getrs_batched<T>(const LuSolveDescT<T>*, int, int, int, cudaStream_t);            \
   template void trsm_upper_batched<T>(const LuSolveDescT<T>*, int, int, int, cudaStream_t);       \
   template void gemm_grouped<T>(const GemmDescT<T>*, const GemmTile*, int, GemmShape,             \
-                                cudaStream_t);                                                   \
+                                cudaStream_t, int*);                                             \
   template void copy_batched<T>(const CopyDescT<T>*, int, int64_t, cudaStream_t);                 \
   template void form_Z<T>(const ZDescT<T>*, int, int64_t, cudaStream_t);                          \
   template void permute_rows<T>(const T*, int, T*, int, const int*, int, int, bool, cudaStream_t);

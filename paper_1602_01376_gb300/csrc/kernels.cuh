@@ -193,16 +193,20 @@ struct GemmDescT {
   double alpha, beta;
 };
 // Work items (descriptor index, tile row, tile column).  Tile shape: 64 x 64
-// (GEMM_SQUARE) or 256 x 16 (GEMM_SKINNY, every problem with N <= 16).
+// (GEMM_SQUARE), 256 x 16 (GEMM_SKINNY, every problem with N <= 16) or 128 x 128
+// (GEMM_TC).
 struct GemmTile {
   int desc, tm, tn;
 };
-enum GemmShape { GEMM_SQUARE = 0, GEMM_SKINNY = 1 };
-inline int gemm_tile_m(GemmShape s) { return s == GEMM_SKINNY ? 256 : 64; }
-inline int gemm_tile_n(GemmShape s) { return s == GEMM_SKINNY ? 16 : 64; }
+// GEMM_TC: 128 x 128 tiles on the tensor cores (tcgen05, 3xTF32), FP32 products only.
+enum GemmShape { GEMM_SQUARE = 0, GEMM_SKINNY = 1, GEMM_TC = 2 };
+inline int gemm_tile_m(GemmShape s) { return s == GEMM_SKINNY ? 256 : s == GEMM_TC ? 128 : 64; }
+inline int gemm_tile_n(GemmShape s) { return s == GEMM_SKINNY ? 16 : s == GEMM_TC ? 128 : 64; }
+// dev_status: device status word; a tensor-core tile whose bounded wait expires sets
+// DEV_TIMEOUT there and leaves its C tile unwritten.
 template <typename T>
 void gemm_grouped(const GemmDescT<T>* descs_dev, const GemmTile* tiles_dev, int ntiles,
-                  GemmShape shape, cudaStream_t st);
+                  GemmShape shape, cudaStream_t st, int* dev_status);
 
 // dst (rows x cols, ldd) <- src (rows x cols, lds), batched.
 template <typename T>
@@ -237,6 +241,25 @@ using ZDesc = ZDescT<double>;
 // Elementwise conversions between FP64 and FP32 buffers.
 void convert_d2f(const double* in, float* out, int64_t n, cudaStream_t st);
 void convert_f2d(const float* in, double* out, int64_t n, cudaStream_t st);
+
+// FP64 values as pairs of FP32 values: x = hi + lo with hi = fl32(x), lo = fl32(x - hi),
+// so |x - hi - lo| <= 2^-48 |x| (for |x| inside the FP32 normal range).  out may alias
+// in (element i of the pair array occupies the bytes of element i of the FP64 array).
+void split_pairs(const double* in, float2* out, int64_t n, cudaStream_t st);
+
+// C = alpha A B + beta C with A stored as FP32 pairs (M x K, column-major, lda in
+// pairs) and B, C in FP64: every product is formed exactly (FMA error term) and the
+// sums are kept as FP32 pairs (two-sum), so the result carries about 2^-44 relative
+// error for K up to a few thousand, on the FP32 pipes.  Tiles of 256 x 16.
+struct GemmDescPair {
+  const float2* A;
+  const double* B;
+  double* C;
+  int M, N, K, lda, ldb, ldc;
+  double alpha, beta;
+};
+constexpr int GEMM_PAIR_TM = 256, GEMM_PAIR_TN = 16;
+void gemm_pair_grouped(const GemmDescPair* descs_dev, const GemmTile* tiles_dev, int ntiles, cudaStream_t st);
 
 // Row permutation of an N x ncols column-major block: out[p] = in[perm[p]] (gather)
 // or out[perm[p]] = in[p] (scatter).

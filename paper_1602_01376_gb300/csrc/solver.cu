@@ -87,6 +87,7 @@ struct Options {
   int keep_candidates = 0;  // keep candidates, features and scores for introspection
   int train_batch = 4096;
   double learned_temp = 0.0;  // Gumbel temperature of the learned selection (0: top scores)
+  int gemm_tc = 1;            // FP32 products with more than 16 columns on the tensor cores (3xTF32)
 };
 
 struct Prob {
@@ -163,12 +164,15 @@ void add_gemm(std::vector<GemmDescT<T>>& g, const T* A, int lda, const T* B, int
 }
 
 // Tile list of one grouped launch: 256 x 16 tiles when no problem has more than 16
-// columns (right-hand-side blocks of a solve), 64 x 64 tiles otherwise.
+// columns (right-hand-side blocks of a solve); otherwise 128 x 128 tensor-core tiles
+// for FP32 products (when enabled) and 64 x 64 tiles for FP64 ones.
 template <typename T>
-GemmShape make_tiles(const std::vector<GemmDescT<T>>& g, std::vector<GemmTile>& t) {
+GemmShape make_tiles(const std::vector<GemmDescT<T>>& g, std::vector<GemmTile>& t, bool tc) {
   int maxn = 0;
   for (const auto& d : g) maxn = std::max(maxn, d.N);
-  const GemmShape shape = maxn <= 16 ? GEMM_SKINNY : GEMM_SQUARE;
+  const GemmShape shape = maxn <= 16                                     ? GEMM_SKINNY
+                          : (tc && std::is_same<T, float>::value) ? GEMM_TC
+                                                                        : GEMM_SQUARE;
   const int tm_ = gemm_tile_m(shape), tn_ = gemm_tile_n(shape);
   t.clear();
   for (int idx = 0; idx < (int)g.size(); ++idx)
@@ -309,9 +313,11 @@ class Solver {
   bool mlp_ready = false;
   // factorization storage: FP64 (plain) and FP32 (mixed)
   DevBuf LU, LUpiv, Wb, Zb, Zpiv, Cb, LU32, Wb32, Zb32, Cb32, tbuf32;
-  // FP64 operator blocks kept by the mixed form: leaf blocks lambda I + K_aa and U blocks
+  // operator blocks kept by the mixed form, evaluated in FP64 and stored as FP32 pairs:
+  // leaf blocks lambda I + K_aa and U blocks
   DevBuf Kleaf, Ustore;
   DevBuf Pd, Pf;  // nested P of every node: FP64, and its FP32 copy (mixed)
+  DevBuf Ppair;   // mixed form: P as FP32 pairs for the operator (Kleaf, Ustore hold pairs too)
   TreeScratch tree_s;
   KnnScratch knn_s;
   SampleScratch samp_s;
@@ -371,13 +377,34 @@ class Solver {
   void run_gemms(const std::vector<GemmDescT<T>>& g) {
     if (g.empty()) return;
     std::vector<GemmTile> t;
-    const GemmShape shape = make_tiles(g, t);
+    const GemmShape shape = make_tiles(g, t, opt.gemm_tc != 0);
     arena.clear();
     size_t og = arena.push(g), ot = arena.push(t);
     char* base = upload_arena();
     prof().flops[pk_of<T>(PK_GEMM)] += gemm_flops(g);
     gemm_grouped((const GemmDescT<T>*)(base + og), (const GemmTile*)(base + ot), (int)t.size(),
-                 shape, st);
+                 shape, st, status.as<int>());
+  }
+  // C (+)= A B with A stored as FP32 pairs (the operator blocks of the mixed form)
+  static void add_pair_gemm(std::vector<GemmDescPair>& g, const float2* A, int lda, const double* B, int ldb,
+                            double* C, int ldc, int M, int Ncol, int K, double beta) {
+    if (M <= 0 || Ncol <= 0) return;
+    g.push_back(GemmDescPair{A, B, C, M, Ncol, K, lda, ldb, ldc, 1.0, beta});
+  }
+  void run_pair_gemms(const std::vector<GemmDescPair>& g) {
+    if (g.empty()) return;
+    std::vector<GemmTile> t;
+    double fl = 0;
+    for (int idx = 0; idx < (int)g.size(); ++idx) {
+      for (int tn = 0; tn < (g[idx].N + GEMM_PAIR_TN - 1) / GEMM_PAIR_TN; ++tn)
+        for (int tm = 0; tm < (g[idx].M + GEMM_PAIR_TM - 1) / GEMM_PAIR_TM; ++tm) t.push_back(GemmTile{idx, tm, tn});
+      fl += 2.0 * g[idx].M * g[idx].N * g[idx].K;
+    }
+    arena.clear();
+    size_t og = arena.push(g), ot = arena.push(t);
+    char* base = upload_arena();
+    prof().flops[PK_GEMM_PAIR] += fl;
+    gemm_pair_grouped((const GemmDescPair*)(base + og), (const GemmTile*)(base + ot), (int)t.size(), st);
   }
   // per-problem blocks of an nrhs-column right-hand side (uploaded to blocks_dev)
   const BlockDesc* upload_blocks(int nrhs, bool lam_scalar) {
@@ -524,7 +551,7 @@ class Solver {
       }
       if (cp.empty()) continue;
       std::vector<GemmTile> t1, t2;
-      const GemmShape sh1 = make_tiles(g1, t1), sh2 = make_tiles(g2, t2);
+      const GemmShape sh1 = make_tiles(g1, t1, opt.gemm_tc != 0), sh2 = make_tiles(g2, t2, opt.gemm_tc != 0);
       arena.clear();
       size_t ocp = arena.push(cp), ozs = arena.push(zs), og1 = arena.push(g1), ot1 = arena.push(t1),
              og2 = arena.push(g2), ot2 = arena.push(t2);
@@ -534,9 +561,9 @@ class Solver {
       copy_batched((const CopyDescT<T>*)(base + ocp), (int)cp.size(), max_cp, st);
       getrs_batched((const LuSolveDescT<T>*)(base + ozs), (int)zs.size(), max_n2, max_nc, st);
       gemm_grouped((const GemmDescT<T>*)(base + og1), (const GemmTile*)(base + ot1), (int)t1.size(),
-                   sh1, st);
+                   sh1, st, status.as<int>());
       gemm_grouped((const GemmDescT<T>*)(base + og2), (const GemmTile*)(base + ot2), (int)t2.size(),
-                   sh2, st);
+                   sh2, st, status.as<int>());
     }
   }
 
@@ -1214,7 +1241,10 @@ class Solver {
       p_total += psz;
       stats.bytes_P += psz * 8;
     }
-    if (prec == PREC_MIXED && p_total > 0) convert_d2f(Pd.as<double>(), Pf.ensure_n<float>(p_total), p_total, st);
+    if (prec == PREC_MIXED && p_total > 0) {
+      convert_d2f(Pd.as<double>(), Pf.ensure_n<float>(p_total), p_total, st);
+      split_pairs(Pd.as<double>(), Ppair.ensure_n<float2>(p_total), p_total, st);
+    }
   }
 
   // ------------------------------------------------------- sampler training
@@ -1486,6 +1516,8 @@ class Solver {
         conv_segs<double, double>(blocks, lu64, s64);
       }
       conv_segs<double, float>(blocks, lu32, s32);
+      // the operator keeps the blocks as FP32 pairs (same bytes, converted in place)
+      split_pairs(blocks, reinterpret_cast<float2*>(blocks), tot, st);
       stats.bytes_operator += tot * 8;
     }
     stats.bytes_LU = tot_t[0] * 4 + tot_t[1] * 8;
@@ -1599,6 +1631,8 @@ class Solver {
       level_step<float>(nodes);
       level_step<double>(nodes);
     }
+    // the operator keeps the U blocks as FP32 pairs (same bytes, converted in place)
+    if (mixed) split_pairs(U64, reinterpret_cast<float2*>(U64), usz, st);
   }
 
   // W = Solve(child, U) for the children of the nodes of one height whose problems are
@@ -1912,24 +1946,31 @@ class Solver {
       return WT + woff[par] + rowoff(sib);
     };
     // Skeletonize: w~ = P w, leaves first, up to the children of the roots
+    const float2* Pp = Ppair.as<float2>();
     for (int hh = 0; hh < Hmax; ++hh) {
       std::vector<GemmDesc> g;
+      std::vector<GemmDescPair> gp;
       for (int c : by_height[hh]) {
         if (is_root(c)) continue;
         const int par = parent(c);
         const double* src = hh == 0 ? rows(Wp, c) : WT + woff[c];
         const int lds = hh == 0 ? ldp(c) : n2(c);
-        add_gemm<double>(g, Pd.as<double>() + nd[c].P_off, nd[c].s, src, lds,
-                         WT + woff[par] + rowoff(c), n2(par), nd[c].s, nrhs, nd[c].ncols, 1.0, 0.0);
+        if (stored)
+          add_pair_gemm(gp, Pp + nd[c].P_off, nd[c].s, src, lds, WT + woff[par] + rowoff(c), n2(par), nd[c].s,
+                        nrhs, nd[c].ncols, 0.0);
+        else
+          add_gemm<double>(g, Pd.as<double>() + nd[c].P_off, nd[c].s, src, lds,
+                           WT + woff[par] + rowoff(c), n2(par), nd[c].s, nrhs, nd[c].ncols, 1.0, 0.0);
       }
       run_gemms(g);
+      run_pair_gemms(gp);
     }
     // Evaluate: one launch per height keeps the rows written by a launch disjoint
     int* sk = skel.as<int>();
     for (int hh = 0; hh <= Hmax; ++hh) {
       for (int pass = 0; pass < 2; ++pass) {  // pass 0: sibling skeletons, pass 1: leaf blocks
         if (pass == 1 && hh != 0) continue;
-        std::vector<GemmDesc> g;
+        std::vector<GemmDescPair> g;
         std::vector<KMatvecDesc> md;
         int max_rows = 0;
         for (int c : by_height[hh]) {
@@ -1937,15 +1978,15 @@ class Solver {
           if (pass == 0) {
             const int sib = sibling(c);
             if (stored)
-              add_gemm<double>(g, Ustore.as<double>() + nd[c].U_off, nd[c].size, wsib(c), n2(parent(c)),
-                               rows(Up, c), ldp(c), nd[c].size, nrhs, nd[sib].s, 1.0, 1.0);
+              add_pair_gemm(g, Ustore.as<float2>() + nd[c].U_off, nd[c].size, wsib(c), n2(parent(c)),
+                            rows(Up, c), ldp(c), nd[c].size, nrhs, nd[sib].s, 1.0);
             else
               md.push_back(KMatvecDesc{sk + (size_t)sib * s_max, wsib(c), rows(Up, c), nd[c].off,
                                        nd[c].size, 0, nd[sib].s, n2(parent(c)), ldp(c), scale_of(c)});
           } else {
             if (stored)
-              add_gemm<double>(g, Kleaf.as<double>() + nd[c].K_off, nd[c].size, rows(Wp, c), ldp(c),
-                               rows(Up, c), ldp(c), nd[c].size, nrhs, nd[c].size, 1.0, 1.0);
+              add_pair_gemm(g, Kleaf.as<float2>() + nd[c].K_off, nd[c].size, rows(Wp, c), ldp(c),
+                            rows(Up, c), ldp(c), nd[c].size, nrhs, nd[c].size, 1.0);
             else
               md.push_back(KMatvecDesc{nullptr, rows(Wp, c), rows(Up, c), nd[c].off, nd[c].size,
                                        nd[c].off, nd[c].size, ldp(c), ldp(c), scale_of(c)});
@@ -1953,7 +1994,7 @@ class Solver {
           max_rows = std::max(max_rows, nd[c].size);
         }
         if (stored) {
-          run_gemms(g);
+          run_pair_gemms(g);
         } else if (!md.empty()) {
           arena.clear();
           size_t om = arena.push(md);
@@ -1974,7 +2015,7 @@ class Solver {
     DevBuf* all[] = {&X, &Xp, &perm, &iperm, &pid, &knn, &knn_pos, &samp, &ranks, &skel,
                      &piv_ws, &A_ws, &status, &arena_dev, &step_dev, &tbuf, &vbuf, &vbuf32,
                      &ubuf, &rbuf, &wt, &io, &normbuf, &blocks_dev, &LU, &LUpiv, &Wb, &Zb, &Zpiv,
-                     &Cb, &LU32, &Wb32, &Zb32, &Cb32, &tbuf32, &Kleaf, &Ustore, &Pd, &Pf,
+                     &Cb, &LU32, &Wb32, &Zb32, &Cb32, &tbuf32, &Kleaf, &Ustore, &Pd, &Pf, &Ppair,
                      &gseg_dev, &kryl, &kzb, &coefbuf, &cseg_dev, &rowsum, &l_cand, &l_hits,
                      &l_feat, &l_score, &l_linfo, &l_samp, &l_rk, &l_Ptmp, &l_sktmp, &l_hold, &l_err,
                      &l_cols, &l_gram, &l_dense, &mlp_master, &mlp_m, &mlp_v, &mlp_grad, &mlp_b16,
@@ -2193,6 +2234,8 @@ int iaskit_set_option(const char* key, double value) {
     } else if (k == "learned_temp") {
       if (!(value >= 0.0) || !std::isfinite(value)) throw Error(IASKIT_ERR_ARG, "invalid learned_temp");
       o.learned_temp = value;
+    } else if (k == "gemm_tc") {
+      o.gemm_tc = as_int(0, 1);
     } else if (k == "profile") {
       int v = as_int(0, 1);
       IA_CUDA(cudaStreamSynchronize(S().st));
@@ -2222,6 +2265,7 @@ int iaskit_get_option(const char* key, double* value) {
     else if (k == "keep_candidates") *value = o.keep_candidates;
     else if (k == "train_batch") *value = o.train_batch;
     else if (k == "learned_temp") *value = o.learned_temp;
+    else if (k == "gemm_tc") *value = o.gemm_tc;
     else throw Error(IASKIT_ERR_ARG, "unknown option " + k);
   });
 }
