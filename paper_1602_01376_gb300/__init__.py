@@ -40,6 +40,7 @@ EXPORTS = [
     "iaskit_factor_batched_device", "iaskit_num_problems", "iaskit_solve_batched",
     "iaskit_solve_batched_device", "iaskit_sampler_train", "iaskit_sampler_set_weights",
     "iaskit_sampler_get_weights", "iaskit_mlp_forward", "iaskit_mlp_train_step", "iaskit_get_learned",
+    "iaskit_kernel_block",
 ]
 
 MLP_NPARAM = 17793
@@ -99,6 +100,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "iaskit_mlp_forward": ([vp, i64, vp], i32),
         "iaskit_mlp_train_step": ([vp, vp, i64, dbl, vp, vp], i32),
         "iaskit_get_learned": ([i32, i32, vp, vp, vp, i32, vp], i32),
+        "iaskit_kernel_block": ([vp, i64, i32, dbl, vp, i32, vp, i32, dbl, i32, vp], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -304,6 +306,21 @@ def iaskit_get_P(level: int, index: int, s: int, cap: int = 1 << 22) -> np.ndarr
     out = np.empty(cap, dtype=np.float64)
     nc = _check(load().iaskit_get_P(level, index, out.ctypes.data, cap))
     return out[: s * nc].reshape(nc, s).T.copy()
+
+
+KERNEL_FORMS = {"fp64": 0, "pair": 1, "fp32": 2}
+
+
+def iaskit_kernel_block(points, h: float, rows, cols, diag: float = 0.0, form: str = "fp64") -> np.ndarray:
+    """K(x_rows, x_cols) (+ diag where row point == column point) from the library's
+    kernel-block kernels: form "fp64", "pair" (FP32 pairs) or "fp32"."""
+    X = np.ascontiguousarray(points, dtype=np.float64)
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    c = np.ascontiguousarray(cols, dtype=np.int32)
+    out = np.empty((len(c), len(r)), dtype=np.float64)   # column-major nr x nc
+    _check(load().iaskit_kernel_block(X.ctypes.data, X.shape[0], X.shape[1], h, r.ctypes.data, len(r),
+                                      c.ctypes.data, len(c), diag, KERNEL_FORMS[form], out.ctypes.data))
+    return out.T.copy()
 
 
 def iaskit_knn_noalloc(points, kappa: int, out, stream=None) -> None:

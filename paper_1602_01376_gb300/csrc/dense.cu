@@ -22,6 +22,7 @@
 #include <climits>
 
 #include "kernels.cuh"
+#include "pair.cuh"
 #include "tc.cuh"
 
 namespace iaskit {
@@ -116,6 +117,86 @@ __global__ void __launch_bounds__(KB_THREADS) kernel_blocks_kernel(const double*
       if (ri_s[li] == ci_s[lj]) v += (T)D.diag;
       D.out[(size_t)i + (size_t)j * D.ld] = v;
     }
+  }
+}
+
+// Kernel blocks on FP32 pairs (the operator blocks of the mixed form): coordinates
+// as pairs (Xpair = split Xp), the squared distance in the difference form with every
+// coordinate difference, square and partial sum kept as a pair (error relative to the
+// distance itself, no cancellation), then exp as a pair (fp2::exp_neg) and the
+// diagonal shift; the result is written as pairs (hi, lo).
+__global__ void __launch_bounds__(KB_THREADS) kernel_blocks_pair_kernel(const float2* Xpair, int d,
+                                                                        const KDescT<float2>* descs) {
+  extern __shared__ __align__(16) unsigned char kb_sh[];
+  float2* Xr = reinterpret_cast<float2*>(kb_sh);  // [d][KB_T]
+  float2* Xc = Xr + (size_t)d * KB_T;              // [d][KB_T]
+  __shared__ int ri_s[KB_T], ci_s[KB_T];
+  const KDescT<float2> D = descs[blockIdx.y];
+  const fp2::pair scale = fp2::from_double(D.scale), diag = fp2::from_double(D.diag);
+  const int tr = (D.nrows + KB_T - 1) / KB_T, tcn = (D.ncols + KB_T - 1) / KB_T;
+  const int tid = threadIdx.x;
+  for (int tile = blockIdx.x; tile < tr * tcn; tile += gridDim.x) {
+    const int i0 = (tile % tr) * KB_T, j0 = (tile / tr) * KB_T;
+    __syncthreads();  // the previous tile's readers are done with the staging buffers
+    if (tid < KB_T) {
+      const int i = min(i0 + tid, D.nrows - 1);
+      ri_s[tid] = D.rows ? D.rows[i] : D.row0 + i;
+    } else if (tid < 2 * KB_T) {
+      const int j = min(j0 + tid - KB_T, D.ncols - 1);
+      ci_s[tid - KB_T] = D.colsA ? (j < D.nA ? D.colsA[j] : D.colsB[j - D.nA]) : D.col0 + j;
+    }
+    __syncthreads();
+    for (int e = tid; e < KB_T * d; e += KB_THREADS) {
+      const int p = e / d, k = e % d;
+      Xr[(size_t)k * KB_T + p] = Xpair[(size_t)ri_s[p] * d + k];
+      Xc[(size_t)k * KB_T + p] = Xpair[(size_t)ci_s[p] * d + k];
+    }
+    __syncthreads();
+    const int tx = tid % 16, ty = tid / 16;
+    float sh[4][4], sl[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) sh[a][b] = sl[a][b] = 0.0f;
+    for (int k = 0; k < d; ++k) {
+      float2 xr[4], xc[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        xr[a] = Xr[(size_t)k * KB_T + tx + 16 * a];
+        xc[a] = Xc[(size_t)k * KB_T + ty + 16 * a];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          // t = x_r - x_c as th + tl, then (sh, sl) += t^2.  th is often the exact
+          // difference of the high parts and tl (the low parts' difference) is then
+          // not small against it: t^2 = th^2 + 2 th tl + tl^2 keeps all three terms.
+          float th, te;
+          fp2::two_sum(xr[a].x, -xc[b].x, th, te);
+          const float tl = __fadd_rn(te, __fsub_rn(xr[a].y, xc[b].y));
+          const float p = __fmul_rn(th, th);
+          float q = fmaf(th, th, -p);
+          q = fmaf(tl, tl, q);
+          q = fmaf(__fadd_rn(th, th), tl, q);
+          float s2, e2;
+          fp2::two_sum(sh[a][b], p, s2, e2);
+          sl[a][b] = __fadd_rn(sl[a][b], __fadd_rn(e2, q));
+          sh[a][b] = s2;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int li = tx + 16 * a, lj = ty + 16 * b;
+        const int i = i0 + li, j = j0 + lj;
+        if (i >= D.nrows || j >= D.ncols) continue;
+        const fp2::pair d2 = fp2::renorm(sh[a][b], sl[a][b]);
+        fp2::pair v = fp2::exp_neg(fp2::mul(d2, scale));
+        if (ri_s[li] == ci_s[lj]) v = fp2::add(v, diag);
+        D.out[(size_t)i + (size_t)j * D.ld] = make_float2(v.h, v.l);
+      }
   }
 }
 
@@ -1059,6 +1140,21 @@ void kernel_blocks(const double* Xp, const double* xnorm, int d, const KDescT<T>
   ProfScope _ps(pk_of<T>(PK_KBLOCK), st);
   dim3 grid((unsigned)max_tiles, ndesc);
   kernel_blocks_kernel<T><<<grid, KB_THREADS, smem, st>>>(Xp, xnorm, d, descs_dev);
+  IA_LAUNCH_CHECK();
+}
+
+void kernel_blocks_pair(const float2* Xpair, int d, const KDescT<float2>* descs_dev, int ndesc,
+                        int64_t max_entries, cudaStream_t st) {
+  if (ndesc <= 0 || max_entries <= 0) return;
+  if (ndesc > 65535) throw Error(IASKIT_ERR_UNSUPPORTED, "more than 65535 kernel blocks in one launch");
+  const int64_t max_tiles = std::min<int64_t>(max_entries / (KB_T * KB_T / 2) + 1, 4096);
+  const size_t smem = (size_t)2 * KB_T * d * sizeof(float2);
+  if (smem > 200 * 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "dimension too large for kernel blocks");
+  if (smem > 48 * 1024)
+    IA_CUDA(cudaFuncSetAttribute(kernel_blocks_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ProfScope _ps(PK_KBLOCK_PAIR, st);
+  dim3 grid((unsigned)max_tiles, ndesc);
+  kernel_blocks_pair_kernel<<<grid, KB_THREADS, smem, st>>>(Xpair, d, descs_dev);
   IA_LAUNCH_CHECK();
 }
 

@@ -119,6 +119,10 @@ struct KDescT {
 template <typename T>
 void kernel_blocks(const double* Xp, const double* xnorm, int d, const KDescT<T>* descs_dev, int ndesc,
                    int64_t max_entries_per_desc, cudaStream_t st);
+// The same blocks evaluated on FP32 pairs (coordinates Xpair = split Xp, d per point)
+// and written as pairs: relative error a few 2^-48 per entry.
+void kernel_blocks_pair(const float2* Xpair, int d, const KDescT<float2>* descs_dev, int ndesc,
+                        int64_t max_entries, cudaStream_t st);
 // out[i] = sum_k Xp[i][k]^2 in FP64, coordinates in order.
 void point_norms(const double* Xp, int N, int d, double* out, cudaStream_t st);
 

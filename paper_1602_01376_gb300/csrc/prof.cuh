@@ -32,6 +32,7 @@ enum ProfKind {
   PK_MLP,        // BF16 MLP forward / backward / Adam (tensor cores)
   PK_JUDGE,      // held-out ID error of the learned and plain samples
   PK_GEMM_PAIR,  // FP64-accurate products on FP32 pairs (operator of the mixed form)
+  PK_KBLOCK_PAIR,  // kernel blocks evaluated on FP32 pairs (operator of the mixed form)
   PK_COUNT
 };
 

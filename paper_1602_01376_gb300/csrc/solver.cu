@@ -277,12 +277,30 @@ __global__ void seg_scale_kernel(double* out, const double* x, const double* coe
 struct ConvSeg {
   int64_t src, dst, len;
 };
+template <typename D, typename S>
+__device__ __forceinline__ D conv_val(S v) {
+  return (D)v;
+}
+// FP32 pairs: the FP32 value is hi (hi = fl32(hi + lo)); the FP64 value is hi + lo
+template <>
+__device__ __forceinline__ float conv_val<float, float2>(float2 v) {
+  return v.x;
+}
+template <>
+__device__ __forceinline__ double conv_val<double, float2>(float2 v) {
+  return (double)v.x + (double)v.y;
+}
 template <typename S, typename D>
 __global__ void conv_segs_kernel(const S* __restrict__ src, D* __restrict__ dst, const ConvSeg* segs) {
   const ConvSeg sg = segs[blockIdx.y];
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < sg.len;
        e += (int64_t)gridDim.x * blockDim.x)
-    dst[sg.dst + e] = (D)src[sg.src + e];
+    dst[sg.dst + e] = conv_val<D, S>(src[sg.src + e]);
+}
+// The same block descriptor writing FP32 pairs into the bytes of an FP64 array.
+KDescT<float2> pair_desc(const KDesc& k) {
+  return KDescT<float2>{k.rows, k.colsA, k.colsB, reinterpret_cast<float2*>(k.out), k.row0, k.nrows,
+                        k.col0, k.nA, k.ncols, k.ld, k.diag, k.scale};
 }
 
 unsigned grid_cap(int64_t work, unsigned cap) {
@@ -318,6 +336,7 @@ class Solver {
   DevBuf Kleaf, Ustore;
   DevBuf Pd, Pf;  // nested P of every node: FP64, and its FP32 copy (mixed)
   DevBuf Ppair;   // mixed form: P as FP32 pairs for the operator (Kleaf, Ustore hold pairs too)
+  DevBuf Xpair;   // mixed form: permuted coordinates as FP32 pairs
   TreeScratch tree_s;
   KnnScratch knn_s;
   SampleScratch samp_s;
@@ -707,6 +726,8 @@ class Solver {
     build_tree(Xd, Ntot, d, levels, pm, tree_s, st);
     permute_points(Xd, pm, Ntot, d, iperm.ensure_n<int>(Ntot), Xp.ensure_n<double>((size_t)Ntot * d), st);
     point_norms(Xp.as<double>(), Ntot, d, xnrm.ensure_n<double>(Ntot), st);
+    if (prec == PREC_MIXED)  // coordinates as FP32 pairs for the operator blocks
+      split_pairs(Xp.as<double>(), Xpair.ensure_n<float2>((size_t)Ntot * d), (int64_t)Ntot * d, st);
     choose_precisions();
     const double t1 = now_ms();
     stats.t_tree = t1 - t0;
@@ -1496,9 +1517,18 @@ class Solver {
     }
     const int nl = (int)kd.size();
     arena.clear();
-    size_t ok = arena.push(kd);
-    char* base = upload_arena();
-    kernel_blocks<double>(Xp.as<double>(), xnrm.as<double>(), d, (const KDesc*)(base + ok), nl, (int64_t)m_max * m_max, st);
+    if (mixed) {  // the operator keeps the blocks as FP32 pairs (in the bytes of Kleaf)
+      std::vector<KDescT<float2>> kp;
+      for (const KDesc& k : kd) kp.push_back(pair_desc(k));
+      size_t ok = arena.push(kp);
+      char* base = upload_arena();
+      kernel_blocks_pair(Xpair.as<float2>(), d, (const KDescT<float2>*)(base + ok), nl, (int64_t)m_max * m_max, st);
+    } else {
+      size_t ok = arena.push(kd);
+      char* base = upload_arena();
+      kernel_blocks<double>(Xp.as<double>(), xnrm.as<double>(), d, (const KDesc*)(base + ok), nl,
+                            (int64_t)m_max * m_max, st);
+    }
     float* lu32 = tot_t[0] ? LU32.ensure_n<float>(tot_t[0]) : nullptr;
     double* lu64 = blocks;
     if (mixed) {
@@ -1511,13 +1541,12 @@ class Solver {
         const int64_t len = b.K_off + (int64_t)b.size * b.size - a.K_off;
         (P.f64 ? s64 : s32).push_back(ConvSeg{a.K_off, a.LU_off, len});
       }
+      const float2* kp = reinterpret_cast<const float2*>(blocks);
       if (tot_t[1]) {
         lu64 = LU.ensure_n<double>(tot_t[1]);
-        conv_segs<double, double>(blocks, lu64, s64);
+        conv_segs<float2, double>(kp, lu64, s64);
       }
-      conv_segs<double, float>(blocks, lu32, s32);
-      // the operator keeps the blocks as FP32 pairs (same bytes, converted in place)
-      split_pairs(blocks, reinterpret_cast<float2*>(blocks), tot, st);
+      conv_segs<float2, float>(kp, lu32, s32);
       stats.bytes_operator += tot * 8;
     }
     stats.bytes_LU = tot_t[0] * 4 + tot_t[1] * 8;
@@ -1531,7 +1560,7 @@ class Solver {
     }
     arena.clear();
     size_t o32 = arena.push(l32), o64 = arena.push(l64);
-    base = upload_arena();
+    char* base = upload_arena();
     if (!l32.empty()) {
       prof().flops[PK_GETRF32] += getrf_flops(l32);
       getrf_batched<float>((const LuDescT<float>*)(base + o32), (int)l32.size(), m_max, status.as<int>(), st);
@@ -1621,18 +1650,24 @@ class Solver {
             sv.push_back(ConvSeg{n.U_off, n.W_off, e});
         }
       arena.clear();
-      size_t ok = arena.push(kd);
-      char* base = upload_arena();
-      kernel_blocks<double>(Xp.as<double>(), xnrm.as<double>(), d, (const KDesc*)(base + ok), (int)kd.size(), max_e, st);
-      if (mixed) {
-        conv_segs<double, float>(U64, Wb32.as<float>(), s32);
-        conv_segs<double, double>(U64, Wb.as<double>(), s64);
+      if (mixed) {  // the operator keeps the U blocks as FP32 pairs (in the bytes of Ustore)
+        std::vector<KDescT<float2>> kp;
+        for (const KDesc& k : kd) kp.push_back(pair_desc(k));
+        size_t ok = arena.push(kp);
+        char* base = upload_arena();
+        kernel_blocks_pair(Xpair.as<float2>(), d, (const KDescT<float2>*)(base + ok), (int)kp.size(), max_e, st);
+        const float2* up = reinterpret_cast<const float2*>(U64);
+        conv_segs<float2, float>(up, Wb32.as<float>(), s32);
+        conv_segs<float2, double>(up, Wb.as<double>(), s64);
+      } else {
+        size_t ok = arena.push(kd);
+        char* base = upload_arena();
+        kernel_blocks<double>(Xp.as<double>(), xnrm.as<double>(), d, (const KDesc*)(base + ok), (int)kd.size(),
+                              max_e, st);
       }
       level_step<float>(nodes);
       level_step<double>(nodes);
     }
-    // the operator keeps the U blocks as FP32 pairs (same bytes, converted in place)
-    if (mixed) split_pairs(U64, reinterpret_cast<float2*>(U64), usz, st);
   }
 
   // W = Solve(child, U) for the children of the nodes of one height whose problems are
@@ -2015,7 +2050,7 @@ class Solver {
     DevBuf* all[] = {&X, &Xp, &perm, &iperm, &pid, &knn, &knn_pos, &samp, &ranks, &skel,
                      &piv_ws, &A_ws, &status, &arena_dev, &step_dev, &tbuf, &vbuf, &vbuf32,
                      &ubuf, &rbuf, &wt, &io, &normbuf, &blocks_dev, &LU, &LUpiv, &Wb, &Zb, &Zpiv,
-                     &Cb, &LU32, &Wb32, &Zb32, &Cb32, &tbuf32, &Kleaf, &Ustore, &Pd, &Pf, &Ppair,
+                     &Cb, &LU32, &Wb32, &Zb32, &Cb32, &tbuf32, &Kleaf, &Ustore, &Pd, &Pf, &Ppair, &Xpair,
                      &gseg_dev, &kryl, &kzb, &coefbuf, &cseg_dev, &rowsum, &l_cand, &l_hits,
                      &l_feat, &l_score, &l_linfo, &l_samp, &l_rk, &l_Ptmp, &l_sktmp, &l_hold, &l_err,
                      &l_cols, &l_gram, &l_dense, &mlp_master, &mlp_m, &mlp_v, &mlp_grad, &mlp_b16,
@@ -2436,6 +2471,64 @@ int iaskit_get_P(int level, int index, double* out, int64_t cap) {
     IA_CUDA(cudaStreamSynchronize(s.st));
   });
   return rc == IASKIT_OK ? nc : rc;
+}
+
+int iaskit_kernel_block(const double* points, int64_t N, int d, double h, const int32_t* rows, int nr,
+                        const int32_t* cols, int nc, double diag, int form, double* out) {
+  return guarded([&] {
+    if (!points || !rows || !cols || !out) throw Error(IASKIT_ERR_ARG, "null argument");
+    if (N < 1 || N > INT_MAX || d < 1 || nr < 1 || nc < 1 || !(h > 0) || form < 0 || form > 2)
+      throw Error(IASKIT_ERR_ARG, "invalid size, bandwidth or form");
+    for (int i = 0; i < nr; ++i)
+      if (rows[i] < 0 || rows[i] >= N) throw Error(IASKIT_ERR_ARG, "row index out of range");
+    for (int j = 0; j < nc; ++j)
+      if (cols[j] < 0 || cols[j] >= N) throw Error(IASKIT_ERR_ARG, "column index out of range");
+    for (int64_t e = 0; e < N * d; ++e)
+      if (!std::isfinite(points[e])) throw Error(IASKIT_ERR_INPUT, "non-finite coordinate");
+    cudaStream_t st = S().st;
+    DevBuf X, aux, ri, ci, ob, db;
+    double* Xd = X.ensure_n<double>((size_t)N * d);
+    h2d(Xd, points, (size_t)N * d, st);
+    int* rd = ri.ensure_n<int>(nr);
+    int* cd = ci.ensure_n<int>(nc);
+    h2d(rd, reinterpret_cast<const int*>(rows), nr, st);
+    h2d(cd, reinterpret_cast<const int*>(cols), nc, st);
+    const int64_t ne = (int64_t)nr * nc;
+    const double scale = -1.0 / (2.0 * h * h);
+    if (form == 0) {
+      double* xn = aux.ensure_n<double>(N);
+      point_norms(Xd, (int)N, d, xn, st);
+      double* o = ob.ensure_n<double>(ne);
+      KDesc k{rd, cd, nullptr, o, 0, nr, 0, nc, nc, nr, diag, scale};
+      KDesc* kd = db.ensure_n<KDesc>(1);
+      h2d(kd, &k, 1, st);
+      kernel_blocks<double>(Xd, xn, d, kd, 1, ne, st);
+      d2h(out, o, ne, st);
+      IA_CUDA(cudaStreamSynchronize(st));
+    } else if (form == 1) {
+      float2* xp = aux.ensure_n<float2>((size_t)N * d);
+      split_pairs(Xd, xp, N * d, st);
+      float2* o = ob.ensure_n<float2>(ne);
+      KDescT<float2> k{rd, cd, nullptr, o, 0, nr, 0, nc, nc, nr, diag, scale};
+      KDescT<float2>* kd = db.ensure_n<KDescT<float2>>(1);
+      h2d(kd, &k, 1, st);
+      kernel_blocks_pair(xp, d, kd, 1, ne, st);
+      std::vector<float2> hv(ne);
+      d2h(hv.data(), o, ne, st);
+      IA_CUDA(cudaStreamSynchronize(st));
+      for (int64_t e = 0; e < ne; ++e) out[e] = (double)hv[e].x + (double)hv[e].y;
+    } else {
+      float* o = ob.ensure_n<float>(ne);
+      KDescT<float> k{rd, cd, nullptr, o, 0, nr, 0, nc, nc, nr, diag, scale};
+      KDescT<float>* kd = db.ensure_n<KDescT<float>>(1);
+      h2d(kd, &k, 1, st);
+      kernel_blocks<float>(Xd, nullptr, d, kd, 1, ne, st);
+      std::vector<float> hv(ne);
+      d2h(hv.data(), o, ne, st);
+      IA_CUDA(cudaStreamSynchronize(st));
+      for (int64_t e = 0; e < ne; ++e) out[e] = hv[e];
+    }
+  });
 }
 
 int iaskit_sampler_train(const double* points, int64_t N, int d, double h, int leaf_m, int s_max,
