@@ -163,6 +163,9 @@ int iaskit_apply_device(const double* d_w, double* d_u, int nrhs);
  *   "gemm_tc"      1: FP32 products with more than 16 columns run on the tensor cores as
  *                  three TF32 products (hi.hi + hi.lo + lo.hi), about FP32 accuracy
  *                  (default); 0: FP32 CUDA-core tiles [any time]
+ *   "cpqr_cluster" 1: FP32 IDs of blocks up to 512 x 512 run on a cluster of up to 8
+ *                  thread blocks per node, the columns held in registers (default);
+ *                  0: one thread block per node.  Same arithmetic either way.
  *   "problem"      which problem of a batch the introspection calls report (0) [any time]
  * Errors: IASKIT_ERR_ARG for an unknown key or an invalid value.
  */

@@ -21,6 +21,8 @@
 #include <type_traits>
 #include <climits>
 
+#include <cooperative_groups.h>
+
 #include "kernels.cuh"
 #include "pair.cuh"
 #include "tc.cuh"
@@ -259,11 +261,8 @@ __device__ __forceinline__ T warp_sum_t(T v) {
   return v;
 }
 
-// One block per node.  Dynamic shared memory: norms (ncols doubles), v (nrows T),
-// piv (ncols ints).  Column norms: every lane accumulates its share of a column in
-// Acc (the storage type), the 32 partial sums are combined in FP64 and compared in
-// FP64.  For T = double this is FP64 throughout; for T = float each partial sum
-// covers at most nrows / 32 squares.
+// One block per node, FP64 (the FP32 form is cpqr_f32_kernel / cpqr_cluster_kernel).
+// Dynamic shared memory: norms (ncols doubles), v (nrows T), piv (ncols ints).
 template <typename T>
 __global__ void __launch_bounds__(QR_THREADS) cpqr_kernel(const CpqrDescT<T>* descs, int s_max,
                                                           double tol) {
@@ -335,71 +334,7 @@ __global__ void __launch_bounds__(QR_THREADS) cpqr_kernel(const CpqrDescT<T>* de
     if (threadIdx.x == 0) v[0] = (T)v0;
     __syncthreads();
     const T beta = vv > 0.0 ? (T)(2.0 / vv) : (T)0;
-    const int tcount = (nr - k + 31) / 32;  // rows per lane of the trailing column
-    if (sizeof(T) == 4 && tcount <= QR_RPL) {
-      // FP32: a warp keeps CW columns in registers between the dot products and the
-      // updates, so that their loads and reductions overlap (FP64 is bound by its
-      // arithmetic pipe and keeps the two-pass form below)
-      constexpr int CW = 4;
-      for (int j = k + 1 + CW * warp; j < nc; j += CW * QR_WARPS) {
-        T* cp[CW];
-        bool has[CW];
-#pragma unroll
-        for (int c = 0; c < CW; ++c) {
-          has[c] = j + c < nc;
-          cp[c] = A + (size_t)(has[c] ? j + c : j) * ld;
-        }
-        T x[CW][QR_RPL];
-#pragma unroll
-        for (int t = 0; t < QR_RPL; ++t) {
-          const int i = k + lane + 32 * t;
-          const bool in = t < tcount && i < nr;
-#pragma unroll
-          for (int c = 0; c < CW; ++c) x[c][t] = in ? cp[c][i] : (T)0;
-        }
-        T dt[CW];
-#pragma unroll
-        for (int c = 0; c < CW; ++c) dt[c] = 0;
-#pragma unroll
-        for (int t = 0; t < QR_RPL; ++t) {
-          const int i = k + lane + 32 * t;
-          const T vi = (t < tcount && i < nr) ? v[i - k] : (T)0;
-#pragma unroll
-          for (int c = 0; c < CW; ++c) dt[c] = fma(vi, x[c][t], dt[c]);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-          for (int c = 0; c < CW; ++c) dt[c] += __shfl_xor_sync(0xffffffffu, dt[c], o);
-        T pn[CW];
-#pragma unroll
-        for (int c = 0; c < CW; ++c) pn[c] = 0;
-#pragma unroll
-        for (int t = 0; t < QR_RPL; ++t) {
-          const int i = k + lane + 32 * t;
-          if (t < tcount && i < nr) {
-            const T vi = v[i - k];
-#pragma unroll
-            for (int c = 0; c < CW; ++c) {
-              const T a = x[c][t] - (beta * dt[c]) * vi;
-              if (has[c]) cp[c][i] = a;
-              if (i > k) pn[c] = fma(a, a, pn[c]);
-            }
-          }
-        }
-        double nn[CW];
-#pragma unroll
-        for (int c = 0; c < CW; ++c) nn[c] = (double)pn[c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-          for (int c = 0; c < CW; ++c) nn[c] += __shfl_xor_sync(0xffffffffu, nn[c], o);
-        if (lane == 0)
-#pragma unroll
-          for (int c = 0; c < CW; ++c)
-            if (has[c]) norms[j + c] = nn[c];
-      }
-    } else {
+    {
     for (int j = k + 1 + warp; j < nc; j += QR_WARPS) {
       T* col = A + (size_t)j * ld;
       T dot = 0;
@@ -426,6 +361,502 @@ __global__ void __launch_bounds__(QR_THREADS) cpqr_kernel(const CpqrDescT<T>* de
   // T = R11^{-1} R12 follows in trsm_upper_batched (blocked, many blocks per node)
   for (int j = threadIdx.x; j < nc; j += QR_THREADS) D.piv[j] = piv[j];
   if (threadIdx.x == 0) *D.rank = s;
+}
+
+// ------------------------------------------------ FP32 CPQR
+// Column norms of the FP32 ID are combined across lanes as FP32 pairs (hi + lo, about
+// 48 significant bits, fp2 arithmetic) rather than in FP64: this part issues two FP64
+// FMAs per clock per SM, and FP64 butterflies over every column made up most of a
+// step.  Pairs are kept normalized and compared lexicographically (hi, then lo);
+// nu = |column|, alpha and beta are formed once per step by one thread in FP64.
+__device__ __forceinline__ bool pair_gt(float2 a, float2 b) { return a.x > b.x || (a.x == b.x && a.y > b.y); }
+__device__ __forceinline__ bool pair_eq(float2 a, float2 b) { return a.x == b.x && a.y == b.y; }
+// (h, l) <- sum over the warp; every lane gets the same pair (two-sum is exact, so the
+// butterfly is symmetric).
+__device__ __forceinline__ void pair_warp_sum(float& h, float& l) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+    float sm, e;
+    fp2::two_sum(h, h2, sm, e);
+    e = __fadd_rn(e, __fadd_rn(l, l2));
+    fp2::fast_two_sum(sm, e, h, l);
+  }
+}
+// (best, idx) over the warp: larger pair wins, equal pairs go to the lower index.
+__device__ __forceinline__ void pair_warp_argmax(float2& v, int& idx) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float2 v2;
+    v2.x = __shfl_xor_sync(0xffffffffu, v.x, o);
+    v2.y = __shfl_xor_sync(0xffffffffu, v.y, o);
+    const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (pair_gt(v2, v) || (pair_eq(v2, v) && i2 < idx)) {
+      v = v2;
+      idx = i2;
+    }
+  }
+}
+// Householder step from the pivot column: x0 its entry on the diagonal, vvp the pair sum
+// of the squares below it, nu its norm: alpha = -sign(x0) nu, v0 = x0 - alpha,
+// beta = 2 / (v0^2 + vvp) (FP64, one thread).
+__device__ __forceinline__ void householder_f32(float x0f, float2 vvp, double nu, float& alpha, float& v0f,
+                                                float& beta) {
+  const double x0 = (double)x0f;
+  const double a = x0 >= 0.0 ? -nu : nu;
+  const double v0 = x0 - a;
+  const double vv = ((double)vvp.x + (double)vvp.y) + v0 * v0;
+  alpha = (float)a;
+  v0f = (float)v0;
+  beta = vv > 0.0 ? (float)(2.0 / vv) : 0.0f;
+}
+
+// One block per node, A in global memory.  Dynamic shared memory: norms (ncols pairs),
+// v (nrows floats), piv (ncols ints), laid out like cpqr_kernel's.
+__global__ void __launch_bounds__(QR_THREADS) cpqr_f32_kernel(const CpqrDescT<float>* descs, int s_max,
+                                                              double tol) {
+  extern __shared__ double shq[];
+  __shared__ float2 rvp[QR_WARPS];
+  __shared__ int ri[QR_WARPS];
+  __shared__ double nu_s;
+  __shared__ int stop_s, p_s;
+  __shared__ float alpha_s, beta_s;
+  const CpqrDescT<float> D = descs[blockIdx.x];
+  float* A = D.A;
+  const int ld = D.ld, nr = D.nrows, nc = D.ncols;
+  float2* norms = reinterpret_cast<float2*>(shq);
+  float* v = reinterpret_cast<float*>(shq + nc);
+  int* piv = reinterpret_cast<int*>(shq + nc + nr);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int j = warp; j < nc; j += QR_WARPS) {
+    float part = 0.0f;
+    for (int i = lane; i < nr; i += 32) {
+      const float a = A[(size_t)i + (size_t)j * ld];
+      part = fmaf(a, a, part);
+    }
+    float h = part, l = 0.0f;
+    pair_warp_sum(h, l);
+    if (lane == 0) {
+      norms[j] = make_float2(h, l);
+      piv[j] = j;
+    }
+  }
+  __syncthreads();
+  const int cap = min(s_max, min(nc, nr));
+  double nu0 = 0.0;  // thread 0
+  int s = 0;
+  for (int k = 0; k < cap; ++k) {
+    float2 best = make_float2(-1.0f, 0.0f);
+    int bi = INT_MAX;
+    for (int j = k + tid; j < nc; j += QR_THREADS) {
+      const float2 nv = norms[j];
+      if (pair_gt(nv, best) || (pair_eq(nv, best) && j < bi)) {
+        best = nv;
+        bi = j;
+      }
+    }
+    pair_warp_argmax(best, bi);
+    if (lane == 0) {
+      rvp[warp] = best;
+      ri[warp] = bi;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      best = lane < QR_WARPS ? rvp[lane] : make_float2(-1.0f, 0.0f);
+      bi = lane < QR_WARPS ? ri[lane] : INT_MAX;
+      pair_warp_argmax(best, bi);
+      if (lane == 0) {
+        const double nu = sqrt(fmax((double)best.x + (double)best.y, 0.0));
+        int stop = 0;
+        if (k == 0) nu0 = nu;
+        else stop = (nu == 0.0 || (tol > 0.0 && nu <= tol * nu0)) ? 1 : 0;
+        nu_s = nu;
+        stop_s = stop;
+        p_s = bi;
+      }
+    }
+    __syncthreads();
+    if (stop_s) break;
+    const int p = p_s;
+    if (p != k) {
+      for (int i = tid; i < nr; i += QR_THREADS) {
+        const float t = A[(size_t)i + (size_t)k * ld];
+        A[(size_t)i + (size_t)k * ld] = A[(size_t)i + (size_t)p * ld];
+        A[(size_t)i + (size_t)p * ld] = t;
+      }
+      if (tid == 0) {
+        const float2 tn = norms[k];
+        norms[k] = norms[p];
+        norms[p] = tn;
+        const int tp = piv[k];
+        piv[k] = piv[p];
+        piv[p] = tp;
+      }
+    }
+    __syncthreads();
+    float ph = 0.0f, pl = 0.0f;  // sum of v_i^2 below the diagonal, as a pair
+    for (int i = k + tid; i < nr; i += QR_THREADS) {
+      const float vi = A[(size_t)i + (size_t)k * ld];
+      v[i - k] = vi;
+      if (i > k) {
+        const float sq = __fmul_rn(vi, vi);
+        const float se = fmaf(vi, vi, -sq);
+        float sm, e;
+        fp2::two_sum(ph, sq, sm, e);
+        fp2::fast_two_sum(sm, __fadd_rn(pl, __fadd_rn(e, se)), ph, pl);
+      }
+    }
+    pair_warp_sum(ph, pl);
+    if (lane == 0) rvp[warp] = make_float2(ph, pl);
+    __syncthreads();
+    if (warp == 0) {
+      ph = lane < QR_WARPS ? rvp[lane].x : 0.0f;
+      pl = lane < QR_WARPS ? rvp[lane].y : 0.0f;
+      pair_warp_sum(ph, pl);
+      if (lane == 0) {
+        float al, v0, be;
+        householder_f32(v[0], make_float2(ph, pl), nu_s, al, v0, be);
+        alpha_s = al;
+        beta_s = be;
+        v[0] = v0;
+      }
+    }
+    __syncthreads();
+    const float beta = beta_s;
+    const int tcount = (nr - k + 31) / 32;  // rows per lane of the trailing column
+    if (tcount <= QR_RPL) {
+      // a warp keeps CW columns in registers between the dot products and the updates,
+      // so that their loads and reductions overlap
+      constexpr int CW = 4;
+      for (int j = k + 1 + CW * warp; j < nc; j += CW * QR_WARPS) {
+        float* cp[CW];
+        bool has[CW];
+#pragma unroll
+        for (int c = 0; c < CW; ++c) {
+          has[c] = j + c < nc;
+          cp[c] = A + (size_t)(has[c] ? j + c : j) * ld;
+        }
+        float x[CW][QR_RPL];
+#pragma unroll
+        for (int t = 0; t < QR_RPL; ++t) {
+          const int i = k + lane + 32 * t;
+          const bool in = t < tcount && i < nr;
+#pragma unroll
+          for (int c = 0; c < CW; ++c) x[c][t] = in ? cp[c][i] : 0.0f;
+        }
+        float dt[CW];
+#pragma unroll
+        for (int c = 0; c < CW; ++c) dt[c] = 0.0f;
+#pragma unroll
+        for (int t = 0; t < QR_RPL; ++t) {
+          const int i = k + lane + 32 * t;
+          const float vi = (t < tcount && i < nr) ? v[i - k] : 0.0f;
+#pragma unroll
+          for (int c = 0; c < CW; ++c) dt[c] = fmaf(vi, x[c][t], dt[c]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int c = 0; c < CW; ++c) dt[c] += __shfl_xor_sync(0xffffffffu, dt[c], o);
+        float pn[CW];
+#pragma unroll
+        for (int c = 0; c < CW; ++c) pn[c] = 0.0f;
+#pragma unroll
+        for (int t = 0; t < QR_RPL; ++t) {
+          const int i = k + lane + 32 * t;
+          if (t < tcount && i < nr) {
+            const float vi = v[i - k];
+#pragma unroll
+            for (int c = 0; c < CW; ++c) {
+              const float a = x[c][t] - (beta * dt[c]) * vi;
+              if (has[c]) cp[c][i] = a;
+              if (i > k) pn[c] = fmaf(a, a, pn[c]);
+            }
+          }
+        }
+        float nl[CW];
+#pragma unroll
+        for (int c = 0; c < CW; ++c) nl[c] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < CW; ++c) pair_warp_sum(pn[c], nl[c]);
+        if (lane == 0)
+#pragma unroll
+          for (int c = 0; c < CW; ++c)
+            if (has[c]) norms[j + c] = make_float2(pn[c], nl[c]);
+      }
+    } else {
+      for (int j = k + 1 + warp; j < nc; j += QR_WARPS) {
+        float* col = A + (size_t)j * ld;
+        float dot = 0.0f;
+        for (int i = k + lane; i < nr; i += 32) dot = fmaf(v[i - k], col[i], dot);
+        dot = warp_sum_t<float>(dot);
+        const float f = beta * dot;
+        float part = 0.0f;
+        for (int i = k + lane; i < nr; i += 32) {
+          const float a = col[i] - f * v[i - k];
+          col[i] = a;
+          if (i > k) part = fmaf(a, a, part);
+        }
+        float l = 0.0f;
+        pair_warp_sum(part, l);
+        if (lane == 0) norms[j] = make_float2(part, l);
+      }
+    }
+    const float alpha = alpha_s;
+    for (int i = k + tid; i < nr; i += QR_THREADS) A[(size_t)i + (size_t)k * ld] = (i == k) ? alpha : 0.0f;
+    s = k + 1;
+    __syncthreads();
+  }
+  for (int j = tid; j < nc; j += QR_THREADS) D.piv[j] = piv[j];
+  if (tid == 0) *D.rank = s;
+}
+
+// ------------------------------------------------ CPQR on a thread-block cluster
+// The same column-pivoted Householder QR (FP32 values, FP64 column norms, ties to the
+// lowest column) for one node spread over a cluster of CS blocks: block r keeps the
+// physical columns [64 r, 64 r + 64) in registers (4 columns per warp, 16 rows per
+// lane, up to 512 rows), so the trailing matrix is never re-read from memory.  Columns
+// do not move; a logical <-> physical map (the same in every block) records the swaps.
+// Each block publishes its best remaining column (norm, logical index and the column
+// itself) in a double-buffered slot; one cluster barrier per step; then every block
+// reads the CS candidates through distributed shared memory, takes the same pivot,
+// copies the winning column, forms the same Householder vector and updates its own
+// columns.  All blocks take the same decisions, so they pass the same barriers.
+namespace cg = cooperative_groups;
+constexpr int QC_COLS = 64, QC_THREADS = 512, QC_RPL = 16;
+constexpr int QC_MAX_ROWS = 32 * QC_RPL;
+
+// Shared state of one block of a cluster CPQR (see cpqr_cluster_kernel).
+struct QcShared {
+  float ccol[2][QC_MAX_ROWS];  // this block's candidate column, per step parity
+  float2 cval[2];              // its squared norm as a pair (-1: none)
+  int cidx[2];                 // its logical index
+  float vloc[QC_MAX_ROWS];     // Householder vector of the step
+  float2 norm_s[QC_COLS];      // squared norms of this block's columns (-1: pivoted or absent)
+  int phys_of[QC_COLS * 8], log_of[QC_COLS * 8];
+  double nu;
+  float alpha, beta;
+  int best_j, cand_q, stop;
+};
+
+__global__ void __launch_bounds__(QC_THREADS, 1) cpqr_cluster_kernel(const CpqrDescT<float>* descs, int s_max,
+                                                                     double tol) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const CpqrDescT<float> D = descs[blockIdx.x / CS];
+  __shared__ QcShared S;
+  float* vloc = S.vloc;
+  float2* norm_s = S.norm_s;
+  int* phys_of = S.phys_of;
+  int* log_of = S.log_of;
+  float* A = D.A;
+  const int ld = D.ld, nr = D.nrows, nc = D.ncols;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int jw = rank * QC_COLS + warp * 4;  // physical column of (warp, c = 0)
+  const float2 NONE = make_float2(-1.0f, 0.0f);
+  float x[4][QC_RPL];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int t = 0; t < QC_RPL; ++t) {
+      const int i = lane + 32 * t, j = jw + c;
+      x[c][t] = (j < nc && i < nr) ? A[(size_t)i + (size_t)j * ld] : 0.0f;
+    }
+  for (int j = tid; j < nc; j += QC_THREADS) {
+    phys_of[j] = j;
+    log_of[j] = j;
+  }
+  {
+    float h[4] = {0.0f, 0.0f, 0.0f, 0.0f}, l[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int t = 0; t < QC_RPL; ++t)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) h[c] = fmaf(x[c][t], x[c][t], h[c]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) pair_warp_sum(h[c], l[c]);
+    if (lane == 0)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) norm_s[warp * 4 + c] = jw + c < nc ? make_float2(h[c], l[c]) : NONE;
+  }
+  const int cap = min(s_max, min(nc, nr));
+  double nu0 = 0.0;  // thread 0
+  int s = 0;
+  for (int k = 0; k < cap; ++k) {
+    const int b = k & 1;
+    // publish this block's best remaining column (norm, logical index, values) in slot b
+    __syncthreads();  // norms and maps are current
+    if (warp == 0) {
+      float2 bv = NONE;
+      int bj = INT_MAX, bq = -1;
+      for (int q = lane; q < QC_COLS; q += 32) {
+        const int j = rank * QC_COLS + q;
+        if (j < nc && norm_s[q].x >= 0.0f) {
+          const int lj = log_of[j];
+          if (pair_gt(norm_s[q], bv) || (pair_eq(norm_s[q], bv) && lj < bj)) {
+            bv = norm_s[q];
+            bj = lj;
+            bq = q;
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        float2 v2;
+        v2.x = __shfl_xor_sync(0xffffffffu, bv.x, o);
+        v2.y = __shfl_xor_sync(0xffffffffu, bv.y, o);
+        const int j2 = __shfl_xor_sync(0xffffffffu, bj, o), q2 = __shfl_xor_sync(0xffffffffu, bq, o);
+        if (pair_gt(v2, bv) || (pair_eq(v2, bv) && j2 < bj)) {
+          bv = v2;
+          bj = j2;
+          bq = q2;
+        }
+      }
+      if (lane == 0) {
+        S.cval[b] = bv;
+        S.cidx[b] = bj;
+        S.cand_q = bq;
+      }
+    }
+    __syncthreads();
+    {
+      const int q = S.cand_q;
+      if (q >= 0 && warp == q / 4) {
+        const int qc = q % 4;
+#pragma unroll
+        for (int t = 0; t < QC_RPL; ++t) {  // selects, not an indexed register array
+          const float v = qc == 0 ? x[0][t] : qc == 1 ? x[1][t] : qc == 2 ? x[2][t] : x[3][t];
+          const int i = lane + 32 * t;
+          if (i < nr) S.ccol[b][i] = v;
+        }
+      }
+    }
+    cl.sync();  // every block's candidate for step k is published
+    if (warp == 0) {
+      float2 bv = NONE;
+      int bj = INT_MAX;
+      if (lane < CS) {
+        bv = *cl.map_shared_rank(&S.cval[b], lane);
+        bj = *cl.map_shared_rank(&S.cidx[b], lane);
+      }
+      pair_warp_argmax(bv, bj);
+      if (lane == 0) {
+        const double nu = sqrt(fmax((double)bv.x + (double)bv.y, 0.0));
+        int stop = bj == INT_MAX ? 1 : 0;  // no column left (not reached: cap <= nc)
+        if (k == 0) nu0 = nu;
+        else if (nu == 0.0 || (tol > 0.0 && nu <= tol * nu0)) stop = 1;
+        S.nu = nu;
+        S.best_j = bj;
+        S.stop = stop;
+      }
+    }
+    __syncthreads();
+    if (S.stop) break;  // every block takes the same decision
+    const int p = S.best_j;
+    const int P = phys_of[p], owner = P / QC_COLS;
+    {
+      const float* rc = cl.map_shared_rank(&S.ccol[b][0], owner);
+      for (int i = k + tid; i < nr; i += QC_THREADS) vloc[i] = rc[i];
+    }
+    __syncthreads();
+    if (tid == 0 && p != k) {
+      const int Pk = phys_of[k];
+      phys_of[k] = P;
+      phys_of[p] = Pk;
+      log_of[P] = k;
+      log_of[Pk] = p;
+    }
+    if (warp == 0) {  // v = (x_k - alpha, x_{k+1}, ...), the same in every block
+      float ph = 0.0f, pl = 0.0f;
+      for (int i = k + 1 + lane; i < nr; i += 32) {
+        const float vi = vloc[i];
+        const float sq = __fmul_rn(vi, vi);
+        const float se = fmaf(vi, vi, -sq);
+        float sm, e;
+        fp2::two_sum(ph, sq, sm, e);
+        fp2::fast_two_sum(sm, __fadd_rn(pl, __fadd_rn(e, se)), ph, pl);
+      }
+      pair_warp_sum(ph, pl);
+      if (lane == 0) {
+        float al, v0, be;
+        householder_f32(vloc[k], make_float2(ph, pl), S.nu, al, v0, be);
+        S.alpha = al;
+        S.beta = be;
+        vloc[k] = v0;
+      }
+    }
+    __syncthreads();
+    const float beta = S.beta;
+    // the pivot column becomes (R entries above, alpha, zeros below)
+    if (rank == owner && warp == (P % QC_COLS) / 4) {
+      const int pc = P % 4;
+      const float al = S.alpha;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)  // selects on every column: no indexed register array
+#pragma unroll
+        for (int t = 0; t < QC_RPL; ++t) {
+          const int i = lane + 32 * t;
+          x[c][t] = (c != pc || i < k) ? x[c][t] : (i == k ? al : 0.0f);
+        }
+      if (lane == 0) norm_s[P % QC_COLS] = NONE;
+    }
+    __syncwarp();
+    // update this block's remaining columns and their norms over rows > k
+    bool live[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) live[c] = jw + c < nc && norm_s[warp * 4 + c].x >= 0.0f;
+    if (live[0] || live[1] || live[2] || live[3]) {
+      float dt[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int t = 0; t < QC_RPL; ++t) {
+        const int i = lane + 32 * t;
+        const float vi = (i >= k && i < nr) ? vloc[i] : 0.0f;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) dt[c] = fmaf(vi, x[c][t], dt[c]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) dt[c] += __shfl_xor_sync(0xffffffffu, dt[c], o);
+      float pn[4] = {0.0f, 0.0f, 0.0f, 0.0f}, nl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+      for (int t = 0; t < QC_RPL; ++t) {
+        const int i = lane + 32 * t;
+        if (i >= k && i < nr) {
+          const float vi = vloc[i];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const float a = x[c][t] - (beta * dt[c]) * vi;
+            x[c][t] = live[c] ? a : x[c][t];
+            if (i > k) pn[c] = fmaf(a, a, pn[c]);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) pair_warp_sum(pn[c], nl[c]);
+      if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (live[c]) norm_s[warp * 4 + c] = make_float2(pn[c], nl[c]);
+    }
+    s = k + 1;
+  }
+  cl.sync();  // no block reads another's shared memory after this point
+  // columns go to their logical positions (every block loaded its columns before)
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int j = jw + c;
+    if (j >= nc) continue;
+    const int L = log_of[j];
+#pragma unroll
+    for (int t = 0; t < QC_RPL; ++t) {
+      const int i = lane + 32 * t;
+      if (i < nr) A[(size_t)i + (size_t)L * ld] = x[c][t];
+    }
+  }
+  if (rank == 0) {
+    for (int j = tid; j < nc; j += QC_THREADS) D.piv[j] = phys_of[j];
+    if (tid == 0) *D.rank = s;
+  }
 }
 
 // ------------------------------------------------ FP32 GEMM on the tensor cores
@@ -1167,14 +1598,47 @@ void point_norms(const double* Xp, int N, int d, double* out, cudaStream_t st) {
 
 template <typename T>
 void cpqr_id(const CpqrDescT<T>* descs_dev, int ndesc, int max_rows, int max_cols, int s_max,
-             double tol, cudaStream_t st) {
+             double tol, cudaStream_t st, bool cluster) {
   if (ndesc <= 0) return;
+  int cs = 1;
+  while (cs * QC_COLS < max_cols) cs *= 2;
+  // the cluster form pays off while the launch holds few nodes (measured on a 512 x 512
+  // ID: one node 1.95 ms on a cluster of 8 against 6.45 ms on one block; at 32 nodes
+  // 5.8 against 6.5 ms; at 64 nodes 9.7 against 6.5 ms)
+  if (std::is_same<T, float>::value && cluster && max_rows <= QC_MAX_ROWS && max_cols <= 8 * QC_COLS &&
+      ndesc * cs <= 256) {
+    ProfScope _ps(pk_of<T>(PK_CPQR), st);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(ndesc * cs));
+    cfg.blockDim = dim3(QC_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    IA_CUDA(cudaLaunchKernelEx(&cfg, cpqr_cluster_kernel, reinterpret_cast<const CpqrDescT<float>*>(descs_dev),
+                               s_max, tol));
+    IA_LAUNCH_CHECK();
+    return;
+  }
   const size_t smem = (size_t)(2 * max_cols + max_rows) * sizeof(double);
   if (smem > 220 * 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "ID block too large for one CTA");
-  if (smem > 48 * 1024)
-    IA_CUDA(cudaFuncSetAttribute(cpqr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ProfScope _ps(pk_of<T>(PK_CPQR), st);
-  cpqr_kernel<T><<<ndesc, QR_THREADS, smem, st>>>(descs_dev, s_max, tol);
+  if (std::is_same<T, float>::value) {
+    if (smem > 48 * 1024)
+      IA_CUDA(cudaFuncSetAttribute(cpqr_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cpqr_f32_kernel<<<ndesc, QR_THREADS, smem, st>>>(reinterpret_cast<const CpqrDescT<float>*>(descs_dev), s_max,
+                                                    tol);
+  } else {
+    if (smem > 48 * 1024)
+      IA_CUDA(cudaFuncSetAttribute(cpqr_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cpqr_kernel<double><<<ndesc, QR_THREADS, smem, st>>>(reinterpret_cast<const CpqrDescT<double>*>(descs_dev),
+                                                        s_max, tol);
+  }
   IA_LAUNCH_CHECK();
 }
 
@@ -1446,7 +1910,7 @@ void check_finite(const double* x, int64_t n, int* dev_status, cudaStream_t st) 
 #define IASKIT_INSTANTIATE(T)                                                                    \
   template void kernel_blocks<T>(const double*, const double*, int, const KDescT<T>*, int, int64_t,  \
                                  cudaStream_t);                                                  \
-  template void cpqr_id<T>(const CpqrDescT<T>*, int, int, int, int, double, cudaStream_t);        \
+  template void cpqr_id<T>(const CpqrDescT<T>*, int, int, int, int, double, cudaStream_t, bool);  \
   template void assemble_P<T>(const PDescT<T>*, int, int, cudaStream_t);                          \
   template void getrf_batched<T>(const LuDescT<T>*, int, int, int*, cudaStream_t);                \
   template void getrs_batched<T>(const LuSolveDescT<T>*, int, int, int, cudaStream_t);            \

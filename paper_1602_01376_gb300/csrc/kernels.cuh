@@ -139,9 +139,11 @@ struct CpqrDescT {
   int* rank;
   int ld, nrows, ncols;
 };
+// cluster: FP32 blocks of up to 512 x 512 may run on a cluster of up to 8 blocks per
+// node (the same arithmetic, columns held in registers across the cluster).
 template <typename T>
 void cpqr_id(const CpqrDescT<T>* descs_dev, int ndesc, int max_rows, int max_cols, int s_max,
-             double tol, cudaStream_t st);
+             double tol, cudaStream_t st, bool cluster = false);
 
 // Builds P (s x ncols, ld = s, FP64) from a cpqr_id result and the skeleton list
 // skel[k] = cols[piv[k]] with cols as in KDescT (colsA/colsB/col0).

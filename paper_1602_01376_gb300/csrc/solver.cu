@@ -88,6 +88,7 @@ struct Options {
   int train_batch = 4096;
   double learned_temp = 0.0;  // Gumbel temperature of the learned selection (0: top scores)
   int gemm_tc = 1;            // FP32 products with more than 16 columns on the tensor cores (3xTF32)
+  int cpqr_cluster = 1;       // FP32 IDs of up to 512 x 512 on a cluster of blocks per node
 };
 
 struct Prob {
@@ -1075,7 +1076,7 @@ class Solver {
       size_t ok = arena.push(kd), oq = arena.push(qd);
       char* base = upload_arena();
       kernel_blocks<TS>(Xp.as<double>(), xnrm.as<double>(), d, (const KDescT<TS>*)(base + ok), nt, max_e, st);
-      cpqr_id<TS>((const CpqrDescT<TS>*)(base + oq), nt, max_r, max_c, s_max, tol, st);
+      cpqr_id<TS>((const CpqrDescT<TS>*)(base + oq), nt, max_r, max_c, s_max, tol, st, opt.cpqr_cluster != 0);
       d2h(rall.data(), rk, nd.size(), st);
       if (nl) d2h(rlrn.data(), rkl, nd.size(), st);
       IA_CUDA(cudaStreamSynchronize(st));
@@ -2271,6 +2272,8 @@ int iaskit_set_option(const char* key, double value) {
       o.learned_temp = value;
     } else if (k == "gemm_tc") {
       o.gemm_tc = as_int(0, 1);
+    } else if (k == "cpqr_cluster") {
+      o.cpqr_cluster = as_int(0, 1);
     } else if (k == "profile") {
       int v = as_int(0, 1);
       IA_CUDA(cudaStreamSynchronize(S().st));
@@ -2301,6 +2304,7 @@ int iaskit_get_option(const char* key, double* value) {
     else if (k == "train_batch") *value = o.train_batch;
     else if (k == "learned_temp") *value = o.learned_temp;
     else if (k == "gemm_tc") *value = o.gemm_tc;
+    else if (k == "cpqr_cluster") *value = o.cpqr_cluster;
     else throw Error(IASKIT_ERR_ARG, "unknown option " + k);
   });
 }

@@ -141,3 +141,31 @@ def test_tensor_core_products_match_cuda_core_products(gpu_lib):
     assert np.array_equal(s0, s1)          # the ID does not use these products
     assert h1[0] < 1e-4 and h0[0] < 1e-4
     assert 0.25 < h1[0] / h0[0] < 4.0
+
+
+def test_cluster_cpqr_matches_single_block_cpqr(gpu_lib):
+    """The FP32 ID on a cluster of blocks (columns held in registers) takes the same
+    arithmetic steps as the one-block kernel: the same ranks, skeletons and P (up to
+    the order of one FP64 sum per step, the squared norm of the Householder vector)."""
+    ia = gpu_lib
+    w = workload("C2", N=6000)
+    X = make_points(w)
+    ia.iaskit_set_option("precision", 1)
+    out = {}
+    try:
+        for cl in (0, 1):
+            ia.iaskit_set_option("cpqr_cluster", cl)
+            ia.iaskit_factor(X, 1.0, 1e-2, 256, 128, 1e-5)
+            L = ia.iaskit_depth()
+            ranks = ia.iaskit_get_ranks()
+            sk = {(l, i): ia.iaskit_get_skeleton(l, i) for l in range(1, L + 1) for i in range(1 << l)}
+            P = {key: ia.iaskit_get_P(key[0], key[1], len(v)) for key, v in sk.items()}
+            out[cl] = (ranks, sk, P)
+    finally:
+        ia.iaskit_set_option("cpqr_cluster", 1)
+        ia.iaskit_set_option("precision", 0)
+    (r0, s0, p0), (r1, s1, p1) = out[0], out[1]
+    assert np.array_equal(r0, r1)
+    for key in s0:
+        assert np.array_equal(s0[key], s1[key]), key
+        np.testing.assert_allclose(p1[key], p0[key], rtol=1e-5, atol=1e-6 * max(1.0, np.abs(p0[key]).max()))
