@@ -215,6 +215,45 @@ constexpr int QR_THREADS = 512;
 constexpr int QR_WARPS = QR_THREADS / 32;
 constexpr int QR_RPL = 16;  // rows per lane held in registers (columns of up to 512 rows)
 
+// (v, idx) over the block, in the value's own type: larger value wins, equal values go
+// to the lower index.  FP32 magnitudes compare exactly as their FP64 images would (the
+// conversion is exact and monotone), without FP64 instructions.
+template <typename V>
+__device__ __forceinline__ void warp_argmax_t(V& v, int& i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const V v2 = __shfl_xor_sync(0xffffffffu, v, o);
+    const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+    if (v2 > v || (v2 == v && i2 < i)) {
+      v = v2;
+      i = i2;
+    }
+  }
+}
+template <typename V>
+__device__ void block_argmax_t(V& v, int& idx, V* rv, int* ri) {
+  warp_argmax_t(v, idx);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    rv[warp] = v;
+    ri[warp] = idx;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? rv[lane] : (V)-1;
+    idx = lane < (int)(blockDim.x >> 5) ? ri[lane] : INT_MAX;
+    warp_argmax_t(v, idx);
+    if (lane == 0) {
+      rv[0] = v;
+      ri[0] = idx;
+    }
+  }
+  __syncthreads();
+  v = rv[0];
+  idx = ri[0];
+}
+
 __device__ void block_argmax(double& v, int& idx, double* rv, int* ri) {
   warp_argmax(v, idx);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1046,7 +1085,7 @@ constexpr int LU_TN = 64;  // trailing-update tile (cols)
 
 template <typename T>
 __global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* descs, int* status) {
-  __shared__ double rv[LU_THREADS / 32];
+  __shared__ T rv[LU_THREADS / 32];
   __shared__ int ri[LU_THREADS / 32];
   __shared__ T L11[LU_NB][LU_NB + 1];
   __shared__ T As[LU_NB][LU_TM + 1];
@@ -1061,10 +1100,16 @@ __global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* des
     // 1. panel factorization
     for (int j = 0; j < nb; ++j) {
       const int k = k0 + j;
-      double best = -1.0;
+      T best = (T)-1;  // partial pivoting on |a_ik| in T (ties to the lowest row)
       int bi = INT_MAX;
-      for (int i = k + tid; i < n; i += LU_THREADS) argmax_merge(best, bi, fabs((double)at(i, k)), i);
-      block_argmax(best, bi, rv, ri);
+      for (int i = k + tid; i < n; i += LU_THREADS) {
+        const T a = fabs(at(i, k));
+        if (a > best || (a == best && i < bi)) {
+          best = a;
+          bi = i;
+        }
+      }
+      block_argmax_t<T>(best, bi, rv, ri);
       const int p = bi;
       if (tid == 0) D.ipiv[k] = p;
       if (p != k && tid < nb) {

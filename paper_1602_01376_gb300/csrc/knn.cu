@@ -111,9 +111,50 @@ __device__ __forceinline__ void stage_operand(const float* Xc, int row0, int nro
   }
 }
 
+// The next-but-one point tile arrives as raw FP32 rows through asynchronous 16-byte
+// copies (cp.async, zero-filled past the end), overlapping the scan of the current
+// tile; split_raw then forms its TF32 hi/lo operand from shared memory.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_addr(smem)), "l"(gmem),
+               "r"(valid ? 16 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+template <int D>
+__device__ __forceinline__ void fetch_raw(const float* Xc, int row0, int nrows, float* raw) {
+  constexpr int KC = D / 4;
+  for (int e = threadIdx.x; e < KT_RB * KC; e += KT_NTH) {
+    const int r = e / KC, kc = e % KC;
+    const bool ok = r < nrows;
+    cp_async16(raw + r * D + kc * 4, ok ? Xc + (size_t)(row0 + r) * D + kc * 4 : Xc, ok);
+  }
+  cp_async_commit();
+}
+template <int D>
+__device__ __forceinline__ void split_raw(const float* raw, uint32_t* H, uint32_t* L) {
+  constexpr int KC = D / 4;
+  for (int e = threadIdx.x; e < KT_RB * KC; e += KT_NTH) {
+    const int g = e / (8 * KC), rem = e % (8 * KC);
+    const int kc = rem / 8, rr = rem % 8;
+    const float4 v = *reinterpret_cast<const float4*>(raw + (g * 8 + rr) * D + kc * 4);
+    uint4 h, l;
+    h.x = tc::to_tf32(v.x);
+    h.y = tc::to_tf32(v.y);
+    h.z = tc::to_tf32(v.z);
+    h.w = tc::to_tf32(v.w);
+    l.x = tc::to_tf32(v.x - __uint_as_float(h.x));
+    l.y = tc::to_tf32(v.y - __uint_as_float(h.y));
+    l.z = tc::to_tf32(v.z - __uint_as_float(h.z));
+    l.w = tc::to_tf32(v.w - __uint_as_float(h.w));
+    const uint32_t w = (uint32_t)((g * KC + kc) * 32 + rr * 4);  // 32-bit words
+    *reinterpret_cast<uint4*>(H + w) = h;
+    *reinterpret_cast<uint4*>(L + w) = l;
+  }
+}
+
 template <int D>
 constexpr size_t prefilter_smem() {
-  return (size_t)6 * KT_QB * D * 4 + 2 * KT_RB * 4 + 64;
+  return (size_t)6 * KT_QB * D * 4 + (size_t)KT_RB * D * 4 + 2 * KT_RB * 4 + 64;
 }
 
 template <int D, int KP>
@@ -128,7 +169,8 @@ __global__ void __launch_bounds__(KT_NTH) knn_prefilter_kernel(const float* Xc, 
   uint32_t* Bl0 = Bh0 + OPW;
   uint32_t* Bh1 = Bl0 + OPW;
   uint32_t* Bl1 = Bh1 + OPW;
-  float* rn_s = reinterpret_cast<float*>(Bl1 + OPW);                // [2][KT_RB]
+  float* raw = reinterpret_cast<float*>(Bl1 + OPW);                 // [KT_RB][D]
+  float* rn_s = raw + KT_RB * D;                                     // [2][KT_RB]
   uint64_t* mbar = reinterpret_cast<uint64_t*>(rn_s + 2 * KT_RB);   // [2]
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
   __shared__ int abort_s;
@@ -140,9 +182,11 @@ __global__ void __launch_bounds__(KT_NTH) knn_prefilter_kernel(const float* Xc, 
   const bool active = qi < tl.qn;
   const int rend = tl.rb + tl.rn;
   const int ntile = (tl.rn + KT_RB - 1) / KT_RB;
+  auto tile_row = [&](int t) { return tl.rb + t * KT_RB; };
   stage_operand<D>(Xc, tl.q0, tl.qn, Ah, Al);
-  stage_operand<D>(Xc, tl.rb, min(KT_RB, tl.rn), Bh0, Bl0);
-  if (tid < KT_RB) rn_s[tid] = tid < min(KT_RB, tl.rn) ? qnorm[tl.rb + tid] : 0.0f;
+  stage_operand<D>(Xc, tile_row(0), min(KT_RB, rend - tile_row(0)), Bh0, Bl0);
+  if (tid < KT_RB) rn_s[tid] = tid < min(KT_RB, rend - tile_row(0)) ? qnorm[tile_row(0) + tid] : 0.0f;
+  if (ntile > 1) fetch_raw<D>(Xc, tile_row(1), min(KT_RB, rend - tile_row(1)), raw);
   const float qv = active ? qnorm[my_q] : 0.0f;
   if (warp == 0) tc::tmem_alloc(tslot, 2 * KT_RB);
   if (tid == 0) {
@@ -150,6 +194,7 @@ __global__ void __launch_bounds__(KT_NTH) knn_prefilter_kernel(const float* Xc, 
     tc::mbar_init(&mbar[1], 1);
     abort_s = 0;
   }
+  cp_async_wait_all();
   tc::fence_async_smem();
   tc::fence_before_sync();
   __syncthreads();
@@ -184,10 +229,10 @@ __global__ void __launch_bounds__(KT_NTH) knn_prefilter_kernel(const float* Xc, 
   }
   for (int t = 0; t < ntile; ++t) {
     const int b = t & 1;
-    const int r0 = tl.rb + t * KT_RB, nt = min(KT_RB, rend - r0);
+    const int r0 = tile_row(t), nt = min(KT_RB, rend - r0);
     if (t + 1 < ntile) {  // the other buffer's last reader, MMA t-1, has completed
-      const int r1 = r0 + KT_RB, n1 = min(KT_RB, rend - r1);
-      stage_operand<D>(Xc, r1, n1, b ? Bh0 : Bh1, b ? Bl0 : Bl1);
+      const int r1 = tile_row(t + 1), n1 = min(KT_RB, rend - r1);
+      split_raw<D>(raw, b ? Bh0 : Bh1, b ? Bl0 : Bl1);
       if (tid < KT_RB) rn_s[(b ^ 1) * KT_RB + tid] = tid < n1 ? qnorm[r1 + tid] : 0.0f;
     }
     tc::fence_async_smem();
@@ -196,6 +241,10 @@ __global__ void __launch_bounds__(KT_NTH) knn_prefilter_kernel(const float* Xc, 
     tc::fence_after_sync();
     const bool stop = abort_s != 0;
     if (!stop && t + 1 < ntile && tid == 0) issue(b ^ 1);
+    if (t + 2 < ntile) {  // every thread is past split_raw: the raw buffer is free
+      const int r2 = tile_row(t + 2);
+      fetch_raw<D>(Xc, r2, min(KT_RB, rend - r2), raw);
+    }
     bool got = false;
     if (!stop) {
       got = tc::mbar_wait(&mbar[b], (uint32_t)((t >> 1) & 1), KT_WAIT);
@@ -242,8 +291,9 @@ __global__ void __launch_bounds__(KT_NTH) knn_prefilter_kernel(const float* Xc, 
         }
       }
     }
+    cp_async_wait_all();  // the next tile's raw rows have landed (this thread's copies)
     tc::fence_before_sync();
-    __syncthreads();  // rn_s and the TMEM tile are reused two tiles later
+    __syncthreads();  // rn_s and the TMEM tile are reused two tiles later; raw is complete
   }
   tc::fence_after_sync();
   if (warp == 0) tc::tmem_free(tmem, 2 * KT_RB);
