@@ -553,7 +553,9 @@ int knn_bruteforce(const double* X, int N, int d, int kappa, int* knn,
   const int np = (int)problems.size();
   const std::vector<KnnTile> tiles = knn_tiles(problems);
   const bool wide = kappa + 8 > 32;
-  const int KP = wide ? 64 : 32;
+  // candidates kept per sub-list: kappa <= 16 keeps 16 (the kappa nearest are among
+  // the 16 smallest of their own sub-lists; a shorter list halves the insertion work)
+  const int KP = kappa <= 16 ? 16 : wide ? 64 : 32;
   KnnBufs b{};
   b.status = s.status.ensure_n<int>(1);
   b.Xc = s.x32.ensure_n<float>((size_t)N * padded_dim(d));
@@ -569,8 +571,9 @@ int knn_bruteforce(const double* X, int N, int d, int kappa, int* knn,
   b.nfl = s.counter.ensure_n<int>(1);
   // algorithmic work of the prefilter: one multiply-add per pair and coordinate
   for (const auto& pr : problems) prof().flops[PK_KNN] += 2.0 * (double)pr.second * pr.second * d;
-  return wide ? knn_run<64>(X, d, kappa, problems, tiles, b, knn, st)
-              : knn_run<32>(X, d, kappa, problems, tiles, b, knn, st);
+  return KP == 16 ? knn_run<16>(X, d, kappa, problems, tiles, b, knn, st)
+         : wide     ? knn_run<64>(X, d, kappa, problems, tiles, b, knn, st)
+                    : knn_run<32>(X, d, kappa, problems, tiles, b, knn, st);
 }
 
 }  // namespace iaskit
