@@ -1083,6 +1083,79 @@ constexpr int LU_NB = 32;
 constexpr int LU_TM = 64;  // trailing-update tile (rows)
 constexpr int LU_TN = 64;  // trailing-update tile (cols)
 
+// After an LU (every thread of the block): per 32 x 32 diagonal block, the inverse of
+// L's unit lower block and of U's upper block, and the permutation of the pivots (see
+// LuDescT).  A warp inverts one block: lane i holds row i of the block and builds row i
+// of the inverse, every step a broadcast of one finished row (32 shuffles) and one
+// multiply-add per column.  A zero diagonal of U (reported as singular by the LU)
+// leaves an infinite row.
+template <typename T>
+__device__ void lu_diag_inverses(const LuDescT<T>& D) {
+  if constexpr (sizeof(T) == 4) {
+    if (!D.dinv) return;
+    __shared__ int perm_s[1024];
+    const int n = D.n, ld = D.ld, nb = (n + 31) / 32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const T* A = D.A;
+    __syncthreads();
+    for (int job = warp; job < 2 * nb; job += LU_THREADS / 32) {
+      const int blk = job >> 1, upper = job & 1, b0 = 32 * blk, bs = min(32, n - b0);
+      T row[32], inv[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        row[k] = (lane < bs && k < bs) ? A[(size_t)(b0 + lane) + (size_t)(b0 + k) * ld] : (T)0;
+        inv[k] = (k == lane && lane < bs) ? (T)1 : (T)0;
+      }
+      if (!upper) {
+        // row i of L^-1 = e_i - sum_{k < i} l_ik (row k of L^-1)
+#pragma unroll
+        for (int k = 0; k < 31; ++k) {
+          const T l = row[k];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const T v = __shfl_sync(0xffffffffu, inv[j], k);
+            if (lane > k) inv[j] -= l * v;
+          }
+        }
+      } else {
+        // row i of U^-1 = (e_i - sum_{k > i} u_ik (row k of U^-1)) / u_ii, from the bottom
+#pragma unroll
+        for (int k = 31; k >= 0; --k) {
+          if (lane == k && k < bs) {
+            const T r = (T)1 / row[k];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) inv[j] *= r;
+          }
+          const T u = row[k];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const T v = __shfl_sync(0xffffffffu, inv[j], k);
+            if (lane < k) inv[j] -= u * v;
+          }
+        }
+      }
+      T* out = D.dinv + (size_t)2048 * blk + (size_t)upper * 1024 + (size_t)lane * 32;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) out[j] = lane < bs ? inv[j] : (T)0;
+    }
+    // the pivots' row permutation: perm[i] = source row of row i after all interchanges
+    for (int i = tid; i < n; i += LU_THREADS) perm_s[i] = i;
+    __syncthreads();
+    if (tid == 0)
+      for (int k = 0; k < n; ++k) {
+        const int p = D.ipiv[k];
+        if (p != k) {
+          const int t = perm_s[k];
+          perm_s[k] = perm_s[p];
+          perm_s[p] = t;
+        }
+      }
+    __syncthreads();
+    int* perm = reinterpret_cast<int*>(D.dinv + (size_t)2048 * nb);
+    for (int i = tid; i < n; i += LU_THREADS) perm[i] = perm_s[i];
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* descs, int* status) {
   __shared__ T rv[LU_THREADS / 32];
@@ -1208,6 +1281,11 @@ __global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* des
         __syncthreads();
       }
   }
+}
+
+// One block per factored LU: its dinv area (lu_diag_inverses).
+__global__ void __launch_bounds__(LU_THREADS, 1) lu_dinv_kernel(const LuDescT<float>* descs) {
+  lu_diag_inverses(descs[blockIdx.x]);
 }
 
 // ---------------------------------------------------------------- GETRS
@@ -1385,6 +1463,116 @@ __global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>
   for (int t = tid; t < n * nc; t += RS_THREADS) {
     const int i = t % n, c = t / n;
     D.B[(size_t)i + (size_t)(c0 + c) * D.ldb] = X[(size_t)i * NC + c];
+  }
+}
+
+// FP32 LU solve with the diagonal blocks' inverses (lu_diag_inverses): rows gathered
+// through the pivots' permutation; per 32-row block, X_b <- (L_bb)^-1 X_b as a small
+// product (every thread: one row, two columns), then the rows below get
+// X_r -= L_rb X_b, two rows per thread with the 16 columns in registers; the same
+// upwards with U.  No step is a sequential substitution, and every global load of a
+// step is issued before its values are used: the block's 32 L (or U) values of a row
+// are loaded together, and the next step's inverse block is fetched during this one.
+constexpr int RI_NC = 16;
+__global__ void __launch_bounds__(RS_THREADS, 2) getrs_inv_kernel(const LuSolveDescT<float>* descs) {
+  extern __shared__ __align__(16) unsigned char ri_sh[];
+  float* X = reinterpret_cast<float*>(ri_sh);  // n x RI_NC, row-major
+  __shared__ __align__(16) float Dv[32][33];
+  const LuSolveDescT<float> D = descs[blockIdx.y];
+  const int c0 = blockIdx.x * RI_NC;
+  if (c0 >= D.ncols) return;
+  const int nc = min(RI_NC, D.ncols - c0), n = D.n, ld = D.ldlu, nb = (n + 31) / 32;
+  const float* LU = D.LU;
+  const int* perm = reinterpret_cast<const int*>(D.dinv + (size_t)2048 * nb);
+  const int tid = threadIdx.x;
+  for (int t = tid; t < n * RI_NC; t += RS_THREADS) {
+    const int i = t % n, c = t / n;
+    X[(size_t)i * RI_NC + c] = c < nc ? D.B[(size_t)perm[i] + (size_t)(c0 + c) * D.ldb] : 0.0f;
+  }
+  const int di = tid >> 3, dc = (tid & 7) * 2;  // diagonal product: row di, columns dc, dc + 1
+  constexpr int DV_PER = 1024 / RS_THREADS;     // inverse entries staged per thread
+  float dnext[DV_PER];
+  auto fetch_inv = [&](int pass, int step) {
+    const int blk = pass == 0 ? step : nb - 1 - step;
+    const float* inv = D.dinv + (size_t)2048 * blk + (size_t)pass * 1024;
+#pragma unroll
+    for (int u = 0; u < DV_PER; ++u) dnext[u] = inv[tid + u * RS_THREADS];
+  };
+  fetch_inv(0, 0);
+  for (int pass = 0; pass < 2; ++pass) {  // 0: L downwards, 1: U upwards
+    for (int step = 0; step < nb; ++step) {
+      const int blk = pass == 0 ? step : nb - 1 - step;
+      const int b0 = 32 * blk, bs = min(32, n - b0);
+      __syncthreads();  // X rows of the previous step are final; Dv is free
+#pragma unroll
+      for (int u = 0; u < DV_PER; ++u) {
+        const int e = tid + u * RS_THREADS;
+        Dv[e >> 5][e & 31] = dnext[u];
+      }
+      __syncthreads();
+      // the next step's inverse block, in flight during this step
+      if (step + 1 < nb) fetch_inv(pass, step + 1);
+      else if (pass == 0) fetch_inv(1, 0);
+      float o0 = 0.0f, o1 = 0.0f;
+      if (di < bs) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          if (k < bs) {
+            const float a = Dv[di][k];
+            const float2 xv = *reinterpret_cast<const float2*>(&X[(size_t)(b0 + k) * RI_NC + dc]);
+            o0 = fmaf(a, xv.x, o0);
+            o1 = fmaf(a, xv.y, o1);
+          }
+        }
+      }
+      __syncthreads();
+      if (di < bs) *reinterpret_cast<float2*>(&X[(size_t)(b0 + di) * RI_NC + dc]) = make_float2(o0, o1);
+      __syncthreads();
+      // rows to update: below the block (L) or above it (U)
+      const int r_lo = pass == 0 ? b0 + bs : 0, r_hi = pass == 0 ? n : b0;
+      for (int r = r_lo + tid; r < r_hi; r += 2 * RS_THREADS) {
+        const int r2 = r + RS_THREADS;
+        const bool two = r2 < r_hi;
+        const float* l0 = LU + (size_t)r + (size_t)b0 * ld;
+        const float* l1 = LU + (size_t)(two ? r2 : r) + (size_t)b0 * ld;
+        float a0[RI_NC], a1[RI_NC];
+#pragma unroll
+        for (int c = 0; c < RI_NC; ++c) a0[c] = a1[c] = 0.0f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // two halves of 16 columns of L (or U), each loaded at once
+          float lv0[16], lv1[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int kk = h * 16 + k;
+            lv0[k] = kk < bs ? l0[(size_t)kk * ld] : 0.0f;
+            lv1[k] = kk < bs ? l1[(size_t)kk * ld] : 0.0f;
+          }
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const int kk = h * 16 + k;
+            if (kk < bs) {
+              float xv[RI_NC];
+              load_row<float, RI_NC>(X, b0 + kk, xv);
+#pragma unroll
+              for (int c = 0; c < RI_NC; ++c) {
+                a0[c] = fmaf(lv0[k], xv[c], a0[c]);
+                a1[c] = fmaf(lv1[k], xv[c], a1[c]);
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < RI_NC; ++c) X[(size_t)r * RI_NC + c] -= a0[c];
+        if (two)
+#pragma unroll
+          for (int c = 0; c < RI_NC; ++c) X[(size_t)r2 * RI_NC + c] -= a1[c];
+      }
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < n * nc; t += RS_THREADS) {
+    const int i = t % n, c = t / n;
+    D.B[(size_t)i + (size_t)(c0 + c) * D.ldb] = X[(size_t)i * RI_NC + c];
   }
 }
 
@@ -1698,19 +1886,34 @@ void assemble_P(const PDescT<T>* descs_dev, int ndesc, int max_cols, cudaStream_
 
 template <typename T>
 void getrf_batched(const LuDescT<T>* descs_dev, int ndesc, int max_n, int* dev_status,
-                   cudaStream_t st) {
+                   cudaStream_t st, bool inv) {
   if (ndesc <= 0) return;
-  (void)max_n;
   ProfScope _ps(pk_of<T>(PK_GETRF), st);
   getrf_kernel<T><<<ndesc, LU_THREADS, 0, st>>>(descs_dev, dev_status);
   IA_LAUNCH_CHECK();
+  if (std::is_same<T, float>::value && inv) {
+    if (max_n > 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "LU block too large for its inverse blocks");
+    lu_dinv_kernel<<<ndesc, LU_THREADS, 0, st>>>(reinterpret_cast<const LuDescT<float>*>(descs_dev));
+    IA_LAUNCH_CHECK();
+  }
 }
 
 template <typename T>
 void getrs_batched(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int max_cols,
-                   cudaStream_t st) {
+                   cudaStream_t st, bool inv) {
   if (ndesc <= 0 || max_cols <= 0) return;
   ProfScope _ps(pk_of<T>(PK_GETRS), st);
+  if (std::is_same<T, float>::value && inv) {
+    const size_t smem = (size_t)max_n * RI_NC * sizeof(float);
+    if (smem > 200 * 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "LU block too large");
+    if (smem > 48 * 1024)
+      IA_CUDA(cudaFuncSetAttribute(getrs_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (ndesc > 65535) throw Error(IASKIT_ERR_UNSUPPORTED, "more than 65535 LU solves in one launch");
+    dim3 grid(ceil_div(max_cols, RI_NC), ndesc);
+    getrs_inv_kernel<<<grid, RS_THREADS, smem, st>>>(reinterpret_cast<const LuSolveDescT<float>*>(descs_dev));
+    IA_LAUNCH_CHECK();
+    return;
+  }
   solve_dispatch<T, false>(descs_dev, ndesc, max_n, max_cols, st);
 }
 
@@ -1957,8 +2160,8 @@ void check_finite(const double* x, int64_t n, int* dev_status, cudaStream_t st) 
                                  cudaStream_t);                                                  \
   template void cpqr_id<T>(const CpqrDescT<T>*, int, int, int, int, double, cudaStream_t, bool);  \
   template void assemble_P<T>(const PDescT<T>*, int, int, cudaStream_t);                          \
-  template void getrf_batched<T>(const LuDescT<T>*, int, int, int*, cudaStream_t);                \
-  template void getrs_batched<T>(const LuSolveDescT<T>*, int, int, int, cudaStream_t);            \
+  template void getrf_batched<T>(const LuDescT<T>*, int, int, int*, cudaStream_t, bool);          \
+  template void getrs_batched<T>(const LuSolveDescT<T>*, int, int, int, cudaStream_t, bool);      \
   template void trsm_upper_batched<T>(const LuSolveDescT<T>*, int, int, int, cudaStream_t);       \
   template void gemm_grouped<T>(const GemmDescT<T>*, const GemmTile*, int, GemmShape,             \
                                 cudaStream_t, int*);                                             \

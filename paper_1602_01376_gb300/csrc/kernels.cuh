@@ -167,10 +167,17 @@ struct LuDescT {
   T* A;
   int* ipiv;
   int n, ld;
+  // optional (FP32): receives, per 32 x 32 diagonal block b, the inverse of L's unit
+  // lower block and of U's upper block (row-major, 2 x 1024 values at 2048 b), then
+  // the row permutation of the pivots as n ints (perm[i] = source row of row i).
+  T* dinv;
 };
+// Values of a dinv area for an n x n LU (see LuDescT).
+inline int64_t lu_dinv_size(int n) { return (int64_t)2048 * ((n + 31) / 32) + n; }
+// inv: every descriptor carries a dinv area (FP32 only), filled after the LU.
 template <typename T>
 void getrf_batched(const LuDescT<T>* descs_dev, int ndesc, int max_n, int* dev_status,
-                   cudaStream_t st);
+                   cudaStream_t st, bool inv = false);
 
 // B <- A^{-1} B from getrf output, for each descriptor; B is n x ncols (ldb).
 template <typename T>
@@ -179,10 +186,13 @@ struct LuSolveDescT {
   const int* ipiv;
   T* B;
   int n, ldlu, ldb, ncols;
+  const T* dinv;  // the LU's dinv area (see LuDescT), for getrs_batched(..., inv = true)
 };
+// inv: every descriptor carries its dinv area (FP32 only): the solve multiplies by the
+// diagonal blocks' inverses instead of substituting through them.
 template <typename T>
 void getrs_batched(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int max_cols,
-                   cudaStream_t st);
+                   cudaStream_t st, bool inv = false);
 // B <- U^{-1} B with U the upper triangle of the n x n block at LU (ipiv unused): the
 // ID's T = R11^{-1} R12 after cpqr_id.  A zero diagonal entry gives a zero row.
 template <typename T>

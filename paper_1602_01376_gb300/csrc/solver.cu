@@ -109,6 +109,7 @@ struct Node {
   int leaf = -1;          // global leaf index (leaves only)
   // offsets into the typed factorization buffers of the node's problem precision (LU, W,
   // Z, C) and into the FP64 operator blocks kept by the mixed form (K: leaf, U)
+  int64_t DI_off = 0;  // FP32 nodes: the dinv area of the node's LU (leaf block or Z)
   int64_t samp_off = 0, P_off = 0, W_off = 0, LU_off = 0, Z_off = 0, Zpiv_off = 0, CL_off = 0,
           CR_off = 0, K_off = 0, U_off = 0;
 };
@@ -338,6 +339,7 @@ class Solver {
   DevBuf Pd, Pf;  // nested P of every node: FP64, and its FP32 copy (mixed)
   DevBuf Ppair;   // mixed form: P as FP32 pairs for the operator (Kleaf, Ustore hold pairs too)
   DevBuf Xpair;   // mixed form: permuted coordinates as FP32 pairs
+  DevBuf DInv32;  // FP32 LUs: inverses of their 32 x 32 diagonal blocks and pivot permutations
   TreeScratch tree_s;
   KnnScratch knn_s;
   SampleScratch samp_s;
@@ -359,6 +361,9 @@ class Solver {
   // typed views of the factorization storage
   template <typename T>
   T* luP() { return std::is_same<T, float>::value ? (T*)LU32.p : (T*)LU.p; }
+  // the dinv area of node g's LU (FP32 only; null for FP64)
+  template <typename T>
+  T* dinvP(int g) { return std::is_same<T, float>::value ? (T*)(DInv32.as<float>() + nd[g].DI_off) : nullptr; }
   template <typename T>
   T* wP() { return std::is_same<T, float>::value ? (T*)Wb32.p : (T*)Wb.p; }
   template <typename T>
@@ -518,7 +523,7 @@ class Solver {
         if (root_of[u] < 0) continue;
         ds.push_back(LuSolveDescT<T>{luP<T>() + nd[u].LU_off,
                                      LUpiv.as<int>() + (int64_t)nd[u].leaf * m_max, Vp[u],
-                                     nd[u].size, nd[u].size, ldV(u), ncV(u)});
+                                     nd[u].size, nd[u].size, ldV(u), ncV(u), dinvP<T>(u)});
         const bool top_root = roots[root_of[u]].gid == u;
         if (!top_root || need_t) {
           T* dst;
@@ -532,7 +537,8 @@ class Solver {
       size_t o = arena.push(ds);
       char* base = upload_arena();
       prof().flops[pk_of<T>(PK_GETRS)] += getrs_flops(ds);
-      getrs_batched((const LuSolveDescT<T>*)(base + o), (int)ds.size(), m_max, max_nc, st);
+      getrs_batched((const LuSolveDescT<T>*)(base + o), (int)ds.size(), m_max, max_nc, st,
+                    std::is_same<T, float>::value);
       run_gemms(g);
     }
     // 2. heights 1 .. top
@@ -550,7 +556,7 @@ class Solver {
         max_cp = std::max<int64_t>(max_cp, (int64_t)nb2 * nc);
         cp.push_back(CopyDescT<T>{Tp(b), Yp(b), nb2, nc, nb2, nb2});
         zs.push_back(LuSolveDescT<T>{zP<T>() + nd[b].Z_off, Zpiv.as<int>() + nd[b].Zpiv_off, Yp(b),
-                                     nb2, nb2, nb2, nc});
+                                     nb2, nb2, nb2, nc, dinvP<T>(b)});
         const T* W = wP<T>();
         // v_a -= W_{a c~} y1 (y1 = Y[sa : nb2]);  v_c -= W_{c a~} y2 (y2 = Y[0 : sa])
         add_gemm<T>(g1, W + nd[a].W_off, nd[a].size, Yp(b) + sa, nb2, Vp[a], ldV(b), nd[a].size, nc,
@@ -579,7 +585,8 @@ class Solver {
       prof().flops[pk_of<T>(PK_GETRS)] += getrs_flops(zs);
       prof().flops[pk_of<T>(PK_GEMM)] += gemm_flops(g1) + gemm_flops(g2);
       copy_batched((const CopyDescT<T>*)(base + ocp), (int)cp.size(), max_cp, st);
-      getrs_batched((const LuSolveDescT<T>*)(base + ozs), (int)zs.size(), max_n2, max_nc, st);
+      getrs_batched((const LuSolveDescT<T>*)(base + ozs), (int)zs.size(), max_n2, max_nc, st,
+                    std::is_same<T, float>::value);
       gemm_grouped((const GemmDescT<T>*)(base + og1), (const GemmTile*)(base + ot1), (int)t1.size(),
                    sh1, st, status.as<int>());
       gemm_grouped((const GemmDescT<T>*)(base + og2), (const GemmTile*)(base + ot2), (int)t2.size(),
@@ -1491,6 +1498,15 @@ class Solver {
   // or in FP64 for the problems it factors in FP64.
   void leaf_lu() {
     const bool mixed = prec == PREC_MIXED;
+    // dinv areas of every FP32 LU: the leaf blocks and the reduced systems (ranks known)
+    int64_t di = 0;
+    for (size_t g = 0; g < nd.size(); ++g) {
+      if (f64((int)g)) continue;
+      const bool leaf = is_leaf((int)g);
+      nd[g].DI_off = di;
+      di += lu_dinv_size(leaf ? nd[g].size : n2((int)g));
+    }
+    if (di > 0) DInv32.ensure_n<float>(di);
     int64_t tot = 0, tot_t[2] = {0, 0};
     for (int g : by_height[0]) {
       Node& n = nd[g];
@@ -1557,14 +1573,15 @@ class Solver {
       const Node& n = nd[g];
       int* piv = lp + (int64_t)n.leaf * m_max;
       if (f64(g)) l64.push_back(LuDesc{lu64 + n.LU_off, piv, n.size, n.size});
-      else l32.push_back(LuDescT<float>{lu32 + n.LU_off, piv, n.size, n.size});
+      else l32.push_back(LuDescT<float>{lu32 + n.LU_off, piv, n.size, n.size, dinvP<float>(g)});
     }
     arena.clear();
     size_t o32 = arena.push(l32), o64 = arena.push(l64);
     char* base = upload_arena();
     if (!l32.empty()) {
       prof().flops[PK_GETRF32] += getrf_flops(l32);
-      getrf_batched<float>((const LuDescT<float>*)(base + o32), (int)l32.size(), m_max, status.as<int>(), st);
+      getrf_batched<float>((const LuDescT<float>*)(base + o32), (int)l32.size(), m_max, status.as<int>(), st,
+                           true);
     }
     if (!l64.empty()) {
       prof().flops[PK_GETRF] += getrf_flops(l64);
@@ -1699,7 +1716,8 @@ class Solver {
     for (int g : nodes) {
       const int sa = nd[left(g)].s, sb = nd[right(g)].s;
       zd.push_back(ZDescT<T>{C + nd[g].CL_off, C + nd[g].CR_off, zP<T>() + nd[g].Z_off, sa, sb});
-      ld.push_back(LuDescT<T>{zP<T>() + nd[g].Z_off, Zpiv.as<int>() + nd[g].Zpiv_off, sa + sb, sa + sb});
+      ld.push_back(LuDescT<T>{zP<T>() + nd[g].Z_off, Zpiv.as<int>() + nd[g].Zpiv_off, sa + sb, sa + sb,
+                              dinvP<T>(g)});
       max_z = std::max<int64_t>(max_z, (int64_t)(sa + sb) * (sa + sb));
       max_n = std::max(max_n, sa + sb);
     }
@@ -1708,7 +1726,8 @@ class Solver {
     char* base = upload_arena();
     form_Z<T>((const ZDescT<T>*)(base + oz), (int)zd.size(), max_z, st);
     prof().flops[pk_of<T>(PK_GETRF)] += getrf_flops(ld);
-    getrf_batched<T>((const LuDescT<T>*)(base + ol), (int)ld.size(), max_n, status.as<int>(), st);
+    getrf_batched<T>((const LuDescT<T>*)(base + ol), (int)ld.size(), max_n, status.as<int>(), st,
+                     std::is_same<T, float>::value);
   }
 
   // ------------------------------------------------------------------ solve
@@ -2051,7 +2070,7 @@ class Solver {
     DevBuf* all[] = {&X, &Xp, &perm, &iperm, &pid, &knn, &knn_pos, &samp, &ranks, &skel,
                      &piv_ws, &A_ws, &status, &arena_dev, &step_dev, &tbuf, &vbuf, &vbuf32,
                      &ubuf, &rbuf, &wt, &io, &normbuf, &blocks_dev, &LU, &LUpiv, &Wb, &Zb, &Zpiv,
-                     &Cb, &LU32, &Wb32, &Zb32, &Cb32, &tbuf32, &Kleaf, &Ustore, &Pd, &Pf, &Ppair, &Xpair,
+                     &Cb, &LU32, &Wb32, &Zb32, &Cb32, &tbuf32, &Kleaf, &Ustore, &Pd, &Pf, &Ppair, &Xpair, &DInv32,
                      &gseg_dev, &kryl, &kzb, &coefbuf, &cseg_dev, &rowsum, &l_cand, &l_hits,
                      &l_feat, &l_score, &l_linfo, &l_samp, &l_rk, &l_Ptmp, &l_sktmp, &l_hold, &l_err,
                      &l_cols, &l_gram, &l_dense, &mlp_master, &mlp_m, &mlp_v, &mlp_grad, &mlp_b16,
