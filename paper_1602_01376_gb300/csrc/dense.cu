@@ -1157,12 +1157,13 @@ __device__ void lu_diag_inverses(const LuDescT<T>& D) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* descs, int* status) {
+__global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* descs, int* status, int pld) {
   __shared__ T rv[LU_THREADS / 32];
   __shared__ int ri[LU_THREADS / 32];
   __shared__ T L11[LU_NB][LU_NB + 1];
   __shared__ T As[LU_NB][LU_TM + 1];
   __shared__ T Bs[LU_NB][LU_TN + 1];
+  extern __shared__ __align__(16) unsigned char lu_sh[];
   const LuDescT<T> D = descs[blockIdx.x];
   T* A = D.A;
   const int n = D.n, ld = D.ld;
@@ -1170,13 +1171,24 @@ __global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* des
   auto at = [&](int i, int j) -> T& { return A[(size_t)i + (size_t)j * ld]; };
   for (int k0 = 0; k0 < n; k0 += LU_NB) {
     const int nb = min(LU_NB, n - k0);
-    // 1. panel factorization
+    // 1. panel factorization: rows k0.. of the panel's columns, in shared memory when
+    //    the launch gave room for them (pld > 0), else in place
+    T* pb = pld > 0 ? reinterpret_cast<T*>(lu_sh) : A + (size_t)k0 * ld;
+    const int pl = pld > 0 ? pld : ld, roff = pld > 0 ? k0 : 0;
+    auto pn = [&](int i, int c) -> T& { return pb[(size_t)(i - roff) + (size_t)c * pl]; };
+    if (pld > 0) {
+      for (int e = tid; e < (n - k0) * nb; e += LU_THREADS) {
+        const int i = k0 + e % (n - k0), c = e / (n - k0);
+        pn(i, c) = at(i, k0 + c);
+      }
+      __syncthreads();
+    }
     for (int j = 0; j < nb; ++j) {
       const int k = k0 + j;
       T best = (T)-1;  // partial pivoting on |a_ik| in T (ties to the lowest row)
       int bi = INT_MAX;
       for (int i = k + tid; i < n; i += LU_THREADS) {
-        const T a = fabs(at(i, k));
+        const T a = fabs(pn(i, j));
         if (a > best || (a == best && i < bi)) {
           best = a;
           bi = i;
@@ -1186,22 +1198,29 @@ __global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* des
       const int p = bi;
       if (tid == 0) D.ipiv[k] = p;
       if (p != k && tid < nb) {
-        T t = at(k, k0 + tid);
-        at(k, k0 + tid) = at(p, k0 + tid);
-        at(p, k0 + tid) = t;
+        T t = pn(k, tid);
+        pn(k, tid) = pn(p, tid);
+        pn(p, tid) = t;
       }
       __syncthreads();
-      const T piv = at(k, k);
+      const T piv = pn(k, j);
       if (piv == (T)0) {
         if (tid == 0) atomicOr(status, DEV_SINGULAR);
         continue;
       }
-      for (int i = k + 1 + tid; i < n; i += LU_THREADS) at(i, k) /= piv;
+      for (int i = k + 1 + tid; i < n; i += LU_THREADS) pn(i, j) /= piv;
       __syncthreads();
-      const int rows = n - k - 1, cols = k0 + nb - k - 1;
+      const int rows = n - k - 1, cols = nb - j - 1;
       for (int t = tid; t < rows * cols; t += LU_THREADS) {
-        const int i = k + 1 + t % rows, c = k + 1 + t / rows;
-        at(i, c) -= at(i, k) * at(k, c);
+        const int i = k + 1 + t % rows, c = j + 1 + t / rows;
+        pn(i, c) -= pn(i, j) * pn(k, c);
+      }
+      __syncthreads();
+    }
+    if (pld > 0) {
+      for (int e = tid; e < (n - k0) * nb; e += LU_THREADS) {
+        const int i = k0 + e % (n - k0), c = e / (n - k0);
+        at(i, k0 + c) = pn(i, c);
       }
       __syncthreads();
     }
@@ -1888,8 +1907,16 @@ template <typename T>
 void getrf_batched(const LuDescT<T>* descs_dev, int ndesc, int max_n, int* dev_status,
                    cudaStream_t st, bool inv) {
   if (ndesc <= 0) return;
+  if (max_n <= 0) return;  // every block is empty
   ProfScope _ps(pk_of<T>(PK_GETRF), st);
-  getrf_kernel<T><<<ndesc, LU_THREADS, 0, st>>>(descs_dev, dev_status);
+  // the panel (rows x 32) in shared memory when it fits next to the static tiles
+  const int pld = max_n;
+  size_t smem = (size_t)pld * LU_NB * sizeof(T);
+  const bool fits = smem <= 160 * 1024;
+  if (!fits) smem = 0;
+  // (the kernel's static tiles take up to 42 KB: the opt-in is needed for any panel)
+  IA_CUDA(cudaFuncSetAttribute(getrf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  getrf_kernel<T><<<ndesc, LU_THREADS, smem, st>>>(descs_dev, dev_status, fits ? pld : 0);
   IA_LAUNCH_CHECK();
   if (std::is_same<T, float>::value && inv) {
     if (max_n > 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "LU block too large for its inverse blocks");
