@@ -299,7 +299,9 @@ def run_batched(args, w, form):
         "data": "synthetic", "config": cfg, "residual": resid,
         "problems_above_1e-10": above, "refine_stagnated_columns": st_last.get("refine_stagnated"),
         "refine_gmres_iters": st_last.get("refine_iters"),
-        "fp64_problems": st_last.get("fp64_problems"), "gpu_launches": launches,
+        "fp64_problems": st_last.get("fp64_problems"),
+        "fp64_operator_problems": st_last.get("fp64_operator_problems"),
+        "operator_upgrades": st_last.get("operator_upgrades"), "gpu_launches": launches,
         "clocks": clocks, "roofline": roof,
         "kernel_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in kern.items() if v["ms"] > 0},
         "compare_per_problem": {"value": nrhs_total * args.steps / (ms_s / 1e3),
@@ -458,6 +460,8 @@ def main():
         "residual": chosen["resid"], "refine_sweeps": st.get("refine_sweeps"),
         "refine_gmres_iters": st.get("refine_iters"), "refine_stagnated_columns": st.get("refine_stagnated"),
         "fp64_problems": st.get("fp64_problems"),
+        "fp64_operator_problems": st.get("fp64_operator_problems"),
+        "operator_upgrades": st.get("operator_upgrades"),
         "knn_exact_fallback_rows": st.get("knn_fallback"),
         "gpu_launches": chosen["launches"], "clocks": clocks, "roofline": roof,
         "kernel_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in kern.items() if v["ms"] > 0},

@@ -163,6 +163,14 @@ int iaskit_apply_device(const double* d_w, double* d_u, int nrhs);
  *   "gemm_tc"      1: FP32 products with more than 16 columns run on the tensor cores as
  *                  three TF32 products (hi.hi + hi.lo + lo.hi), about FP32 accuracy
  *                  (default); 0: FP32 CUDA-core tiles [any time]
+ *   "pair_cond_max" mixed precision: the operator blocks (leaf blocks, U, P) are
+ *                  evaluated and applied as FP32 pairs (hi + lo, about 2^-44 relative
+ *                  per entry), except for problems whose condition estimate exceeds
+ *                  this, which keep them in FP64 (1e6, the default "mixed_cond_max",
+ *                  so that problems factored in FP64 keep them in FP64).  When a solve's
+ *                  refinement stops at the pair operator's rounding floor above
+ *                  "refine_tol", those problems' blocks are re-evaluated in FP64 and the
+ *                  solve is refined again ("operator_upgrades" in iaskit_stats) [>= 1]
  *   "cpqr_cluster" 1: FP32 IDs of blocks up to 512 x 512 run on a cluster of up to 8
  *                  thread blocks per node, the columns held in registers (default);
  *                  0: one thread block per node.  Same arithmetic either way.
@@ -179,7 +187,8 @@ int iaskit_set_stream(void* cuda_stream);
  * JSON with timings per phase (ms), the rank profile, algorithmic flop and byte
  * counts, the last refinement history (worst relative residual after each cycle), GMRES
  * iterations, columns stopped at the rounding floor, each problem's condition estimate
- * and how many problems were factored in FP64.  Writes at most len bytes including the
+ * how many problems were factored in FP64 and how many kept their operator blocks in
+ * FP64 (mixed precision).  Writes at most len bytes including the
  * terminating NUL; returns the full length needed (>= 0) or a negative error.
  */
 int iaskit_stats(char* json_buf, size_t len);

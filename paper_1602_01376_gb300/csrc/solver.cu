@@ -89,6 +89,11 @@ struct Options {
   double learned_temp = 0.0;  // Gumbel temperature of the learned selection (0: top scores)
   int gemm_tc = 1;            // FP32 products with more than 16 columns on the tensor cores (3xTF32)
   int cpqr_cluster = 1;       // FP32 IDs of up to 512 x 512 on a cluster of blocks per node
+  // mixed form: problems whose condition estimate exceeds this keep their operator
+  // blocks in FP64 from the start (by default those factored in FP64); any other
+  // problem whose refinement stops at the FP32-pair operator's rounding floor is
+  // upgraded to FP64 and refined again
+  double pair_cond_max = 1e6;
 };
 
 struct Prob {
@@ -98,6 +103,7 @@ struct Prob {
   int nbase = 0;                     // global id of heap id 0: gid = nbase + uid
   double cond_est = 0;               // 1 + max sampled kernel row sum / lambda
   bool f64 = true;                   // factorization stored in FP64 (else FP32)
+  bool op64 = false;                 // mixed form: operator blocks in FP64 (else FP32 pairs)
 };
 
 struct Node {
@@ -124,6 +130,8 @@ struct Stats {
   int refine_iters = 0;       // GMRES iterations (operator applications) of the last solve
   int refine_stagnated = 0;   // columns stopped at the rounding floor of the FP64 operator
   int fp64_problems = 0;      // problems factored in FP64
+  int fp64_operator_problems = 0;  // mixed form: problems whose operator blocks stay in FP64
+  int operator_upgrades = 0;       // of those, upgraded after their refinement stopped at the floor
   int learned_nodes = 0, fallback_nodes = 0, judged_nodes = 0;
   double judge_err_plain = 0, judge_err_chosen = 0;  // sums over judged nodes
   std::vector<double> train_loss;                    // mean batch loss per epoch
@@ -340,6 +348,8 @@ class Solver {
   DevBuf Ppair;   // mixed form: P as FP32 pairs for the operator (Kleaf, Ustore hold pairs too)
   DevBuf Xpair;   // mixed form: permuted coordinates as FP32 pairs
   DevBuf DInv32;  // FP32 LUs: inverses of their 32 x 32 diagonal blocks and pivot permutations
+  DevBuf rhs_keep;  // mixed form: the right-hand side, for a refinement after an operator upgrade
+  std::vector<char> stag_prob;  // per problem: a column of the last refinement stopped at its floor
   TreeScratch tree_s;
   KnnScratch knn_s;
   SampleScratch samp_s;
@@ -786,13 +796,17 @@ class Solver {
     d2h(hrs.data(), rs, hrs.size(), st);
     IA_CUDA(cudaStreamSynchronize(st));
     stats.fp64_problems = 0;
+    stats.fp64_operator_problems = 0;
+    stats.operator_upgrades = 0;
     for (size_t q = 0; q < pr.size(); ++q) {
       double mx = 0.0;
       for (int r = 0; r < KROWSUM_ROWS; ++r) mx = std::max(mx, hrs[q * KROWSUM_ROWS + r]);
       Prob& P = pr[q];
       P.cond_est = P.lam > 0.0 ? 1.0 + mx / P.lam : HUGE_VAL;
       P.f64 = prec != PREC_MIXED || !(P.cond_est <= opt.mixed_cond_max);
+      P.op64 = prec == PREC_MIXED && !(P.cond_est <= opt.pair_cond_max);
       stats.fp64_problems += P.f64 ? 1 : 0;
+      stats.fp64_operator_problems += P.op64 ? 1 : 0;
     }
   }
 
@@ -1493,6 +1507,94 @@ class Solver {
     IA_CUDA(cudaStreamSynchronize(st));
   }
 
+  // The operator blocks of the given problems re-evaluated in FP64 (same offsets, same
+  // bytes per entry); the apply then uses FP64 products for them.
+  void upgrade_operator(const std::vector<int>& probs) {
+    std::vector<KDesc> kl, ku;
+    int64_t max_l = 0, max_u = 0;
+    const int* sk = skel.as<int>();
+    for (int q : probs) {
+      pr[q].op64 = true;
+      ++stats.fp64_operator_problems;
+      ++stats.operator_upgrades;
+    }
+    for (size_t g = 0; g < nd.size(); ++g) {
+      const Node& n = nd[g];
+      if (!pr[n.prob].op64 || std::find(probs.begin(), probs.end(), n.prob) == probs.end()) continue;
+      if (is_leaf((int)g)) {
+        KDesc k{};
+        k.row0 = n.off;
+        k.nrows = n.size;
+        k.col0 = n.off;
+        k.ncols = n.size;
+        k.out = Kleaf.as<double>() + n.K_off;
+        k.ld = n.size;
+        k.diag = pr[n.prob].lam;
+        k.scale = scale_of((int)g);
+        kl.push_back(k);
+        max_l = std::max<int64_t>(max_l, (int64_t)n.size * n.size);
+      }
+      if (!is_root((int)g)) {
+        const int sib = sibling((int)g);
+        KDesc k{};
+        k.row0 = n.off;
+        k.nrows = n.size;
+        k.colsA = sk + (size_t)sib * s_max;
+        k.nA = nd[sib].s;
+        k.ncols = nd[sib].s;
+        k.out = Ustore.as<double>() + n.U_off;
+        k.ld = n.size;
+        k.diag = 0.0;
+        k.scale = scale_of((int)g);
+        if (k.ncols > 0) {
+          ku.push_back(k);
+          max_u = std::max<int64_t>(max_u, (int64_t)n.size * k.ncols);
+        }
+      }
+    }
+    for (std::vector<KDesc>* kv : {&kl, &ku}) {
+      for (size_t b = 0; b < kv->size(); b += 65535) {
+        const size_t e = std::min(kv->size(), b + 65535);
+        std::vector<KDesc> part(kv->begin() + b, kv->begin() + e);
+        arena.clear();
+        size_t ok = arena.push(part);
+        char* base = upload_arena();
+        kernel_blocks<double>(Xp.as<double>(), xnrm.as<double>(), d, (const KDesc*)(base + ok), (int)part.size(),
+                              kv == &kl ? max_l : max_u, st);
+      }
+    }
+  }
+
+  // Operator blocks of the mixed form: FP32 pairs for the problems whose operator is
+  // kept in pairs (the descriptors' out pointers address the pair array's bytes), FP64
+  // (Gram form) for the others.
+  void run_operator_blocks(const std::vector<KDesc>& kd, const std::vector<int>& gids, int64_t max_e) {
+    std::vector<KDescT<float2>> kp;
+    std::vector<KDesc> k64;
+    for (size_t i = 0; i < kd.size(); ++i) {
+      if (pr[nd[gids[i]].prob].op64) k64.push_back(kd[i]);
+      else kp.push_back(pair_desc(kd[i]));
+    }
+    arena.clear();
+    size_t op = arena.push(kp), o64 = arena.push(k64);
+    char* base = upload_arena();
+    if (!kp.empty())
+      kernel_blocks_pair(Xpair.as<float2>(), d, (const KDescT<float2>*)(base + op), (int)kp.size(), max_e, st);
+    if (!k64.empty())
+      kernel_blocks<double>(Xp.as<double>(), xnrm.as<double>(), d, (const KDesc*)(base + o64), (int)k64.size(),
+                            max_e, st);
+  }
+  // FP32 and FP64 solve copies of operator blocks; list [t] holds the ranges whose
+  // operator is in FP64 (t = 1) or in FP32 pairs (t = 0).
+  void conv_operator(const double* src, float* d32, double* d64, std::vector<ConvSeg> (&s32)[2],
+                     std::vector<ConvSeg> (&s64)[2]) {
+    const float2* sp = reinterpret_cast<const float2*>(src);
+    conv_segs<float2, float>(sp, d32, s32[0]);
+    conv_segs<double, float>(src, d32, s32[1]);
+    conv_segs<float2, double>(sp, d64, s64[0]);
+    conv_segs<double, double>(src, d64, s64[1]);
+  }
+
   // a4 + a6: leaf LU of lambda I + K_aa, in each problem's precision.  The mixed form
   // keeps the FP64 blocks for the operator (Kleaf) and factors a copy: rounded to FP32,
   // or in FP64 for the problems it factors in FP64.
@@ -1534,12 +1636,8 @@ class Solver {
     }
     const int nl = (int)kd.size();
     arena.clear();
-    if (mixed) {  // the operator keeps the blocks as FP32 pairs (in the bytes of Kleaf)
-      std::vector<KDescT<float2>> kp;
-      for (const KDesc& k : kd) kp.push_back(pair_desc(k));
-      size_t ok = arena.push(kp);
-      char* base = upload_arena();
-      kernel_blocks_pair(Xpair.as<float2>(), d, (const KDescT<float2>*)(base + ok), nl, (int64_t)m_max * m_max, st);
+    if (mixed) {  // the operator keeps the blocks as FP32 pairs (in the bytes of Kleaf), or in FP64
+      run_operator_blocks(kd, by_height[0], (int64_t)m_max * m_max);
     } else {
       size_t ok = arena.push(kd);
       char* base = upload_arena();
@@ -1550,20 +1648,16 @@ class Solver {
     double* lu64 = blocks;
     if (mixed) {
       // one range per problem: its leaves are consecutive in both layouts
-      std::vector<ConvSeg> s32, s64;
+      std::vector<ConvSeg> s32[2], s64[2];  // [operator in FP64]
       for (const Prob& P : pr) {
         const int first = P.nbase + (1 << P.L), nlv = 1 << P.L;
         const Node& a = nd[first];
         const Node& b = nd[first + nlv - 1];
         const int64_t len = b.K_off + (int64_t)b.size * b.size - a.K_off;
-        (P.f64 ? s64 : s32).push_back(ConvSeg{a.K_off, a.LU_off, len});
+        (P.f64 ? s64 : s32)[P.op64].push_back(ConvSeg{a.K_off, a.LU_off, len});
       }
-      const float2* kp = reinterpret_cast<const float2*>(blocks);
-      if (tot_t[1]) {
-        lu64 = LU.ensure_n<double>(tot_t[1]);
-        conv_segs<float2, double>(kp, lu64, s64);
-      }
-      conv_segs<float2, float>(kp, lu32, s32);
+      if (tot_t[1]) lu64 = LU.ensure_n<double>(tot_t[1]);
+      conv_operator(blocks, lu32, lu64, s32, s64);
       stats.bytes_operator += tot * 8;
     }
     stats.bytes_LU = tot_t[0] * 4 + tot_t[1] * 8;
@@ -1641,11 +1735,13 @@ class Solver {
       const std::vector<int>& nodes = by_height[hh];
       std::vector<KDesc> kd;
       int64_t max_e = 0;
-      std::vector<ConvSeg> s32, s64;
+      std::vector<ConvSeg> s32[2], s64[2];  // [operator in FP64]
+      std::vector<int> kg;                  // child of each descriptor
       for (int g : nodes)
         for (int c : {left(g), right(g)}) {
           const Node& n = nd[c];
           const int sib = sibling(c);
+          kg.push_back(c);
           KDesc k{};
           k.row0 = n.off;
           k.nrows = n.size;
@@ -1660,7 +1756,7 @@ class Solver {
           const int64_t e = (int64_t)n.size * k.ncols;
           max_e = std::max<int64_t>(max_e, e);
           // consecutive children of one precision extend the previous range
-          std::vector<ConvSeg>& sv = f64(c) ? s64 : s32;
+          std::vector<ConvSeg>& sv = (f64(c) ? s64 : s32)[pr[n.prob].op64];
           if (!sv.empty() && sv.back().src + sv.back().len == n.U_off &&
               sv.back().dst + sv.back().len == n.W_off)
             sv.back().len += e;
@@ -1668,15 +1764,9 @@ class Solver {
             sv.push_back(ConvSeg{n.U_off, n.W_off, e});
         }
       arena.clear();
-      if (mixed) {  // the operator keeps the U blocks as FP32 pairs (in the bytes of Ustore)
-        std::vector<KDescT<float2>> kp;
-        for (const KDesc& k : kd) kp.push_back(pair_desc(k));
-        size_t ok = arena.push(kp);
-        char* base = upload_arena();
-        kernel_blocks_pair(Xpair.as<float2>(), d, (const KDescT<float2>*)(base + ok), (int)kp.size(), max_e, st);
-        const float2* up = reinterpret_cast<const float2*>(U64);
-        conv_segs<float2, float>(up, Wb32.as<float>(), s32);
-        conv_segs<float2, double>(up, Wb.as<double>(), s64);
+      if (mixed) {  // the operator keeps the U blocks as FP32 pairs (in the bytes of Ustore), or in FP64
+        run_operator_blocks(kd, kg, max_e);
+        conv_operator(U64, Wb32.as<float>(), Wb.as<double>(), s32, s64);
       } else {
         size_t ok = arena.push(kd);
         char* base = upload_arena();
@@ -1745,7 +1835,25 @@ class Solver {
     if (sweeps <= 0) {
       plain_solve(rhs, nrhs, rhs);
     } else {
+      const size_t n = (size_t)Ntot * nrhs;
+      double* rhs0 = nullptr;
+      if (prec == PREC_MIXED) {  // kept for a second refinement after an operator upgrade
+        rhs0 = rhs_keep.ensure_n<double>(n);
+        IA_CUDA(cudaMemcpyAsync(rhs0, rhs, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      }
+      stag_prob.clear();
       refine_solve(rhs, nrhs, sweeps);
+      // problems whose columns stopped at the rounding floor of the FP32-pair operator
+      // get their operator blocks in FP64, and the solve is refined again
+      std::vector<int> up;
+      for (size_t q = 0; q < stag_prob.size(); ++q)
+        if (stag_prob[q] && !pr[q].op64) up.push_back((int)q);
+      if (rhs0 && !up.empty()) {  // continue from the current solution
+        upgrade_operator(up);
+        const int it0 = stats.refine_iters;
+        refine_solve(rhs, nrhs, sweeps, rhs0);
+        stats.refine_iters += it0;
+      }
     }
     IA_CUDA(cudaStreamSynchronize(st));
     prof().resolve();
@@ -1796,7 +1904,9 @@ class Solver {
   // half: then the rounding floor of the FP64 residual itself, about
   // eps ||A|| ||w|| / ||u||, lies above the target and further cycles cannot help.
   // max_iters bounds the total number of GMRES iterations.
-  void refine_solve(double* w, int nrhs, int max_iters) {
+  // u_in: null - w holds the right-hand side and receives the solution, starting from
+  // the plain solve; else u_in is the right-hand side and w an initial iterate.
+  void refine_solve(double* w, int nrhs, int max_iters, const double* u_in = nullptr) {
     const size_t n = (size_t)Ntot * nrhs;
     const int S = (int)pr.size() * nrhs;
     // restart length: at most 30, and (2m + 1) n doubles of bases within about 16 GB
@@ -1812,11 +1922,11 @@ class Solver {
     double* V = kryl.ensure_n<double>((size_t)(m + 1) * n);
     double* Zb_ = kzb.ensure_n<double>((size_t)m * n);
     double* coef = coefbuf.ensure_n<double>((size_t)(m + 1) * S);
-    IA_CUDA(cudaMemcpyAsync(u, w, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    IA_CUDA(cudaMemcpyAsync(u, u_in ? u_in : w, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     std::vector<double> un, rn, hn, prev(S, 0.0), est_end(S, HUGE_VAL);
     std::vector<int> state(S, 0);  // 0 open, 1 converged, 2 at the rounding floor
     column_norms(u, nrhs, un);
-    plain_solve(u, nrhs, w);  // x0 = M^-1 u
+    if (!u_in) plain_solve(u, nrhs, w);  // x0 = M^-1 u
     int& iters = stats.refine_iters;
     iters = 0;
     bool first = true;
@@ -1842,6 +1952,9 @@ class Solver {
       stats.refine_hist.push_back(worst);
       if (!open) {
         stats.refine_stagnated = (int)std::count(state.begin(), state.end(), 2);
+        stag_prob.assign(pr.size(), 0);
+        for (int q = 0; q < S; ++q)
+          if (state[q] == 2) stag_prob[q / nrhs] = 1;
         return;
       }
       if (iters >= max_iters) throw Error(IASKIT_ERR_NOT_CONVERGED, "refinement did not converge");
@@ -2010,7 +2123,7 @@ class Solver {
         const int par = parent(c);
         const double* src = hh == 0 ? rows(Wp, c) : WT + woff[c];
         const int lds = hh == 0 ? ldp(c) : n2(c);
-        if (stored)
+        if (stored && !pr[nd[c].prob].op64)
           add_pair_gemm(gp, Pp + nd[c].P_off, nd[c].s, src, lds, WT + woff[par] + rowoff(c), n2(par), nd[c].s,
                         nrhs, nd[c].ncols, 0.0);
         else
@@ -2026,20 +2139,27 @@ class Solver {
       for (int pass = 0; pass < 2; ++pass) {  // pass 0: sibling skeletons, pass 1: leaf blocks
         if (pass == 1 && hh != 0) continue;
         std::vector<GemmDescPair> g;
+        std::vector<GemmDesc> g64;
         std::vector<KMatvecDesc> md;
         int max_rows = 0;
         for (int c : by_height[hh]) {
           if (pass == 0 && is_root(c)) continue;
           if (pass == 0) {
             const int sib = sibling(c);
-            if (stored)
+            if (stored && pr[nd[c].prob].op64)
+              add_gemm<double>(g64, Ustore.as<double>() + nd[c].U_off, nd[c].size, wsib(c), n2(parent(c)),
+                               rows(Up, c), ldp(c), nd[c].size, nrhs, nd[sib].s, 1.0, 1.0);
+            else if (stored)
               add_pair_gemm(g, Ustore.as<float2>() + nd[c].U_off, nd[c].size, wsib(c), n2(parent(c)),
                             rows(Up, c), ldp(c), nd[c].size, nrhs, nd[sib].s, 1.0);
             else
               md.push_back(KMatvecDesc{sk + (size_t)sib * s_max, wsib(c), rows(Up, c), nd[c].off,
                                        nd[c].size, 0, nd[sib].s, n2(parent(c)), ldp(c), scale_of(c)});
           } else {
-            if (stored)
+            if (stored && pr[nd[c].prob].op64)
+              add_gemm<double>(g64, Kleaf.as<double>() + nd[c].K_off, nd[c].size, rows(Wp, c), ldp(c),
+                               rows(Up, c), ldp(c), nd[c].size, nrhs, nd[c].size, 1.0, 1.0);
+            else if (stored)
               add_pair_gemm(g, Kleaf.as<float2>() + nd[c].K_off, nd[c].size, rows(Wp, c), ldp(c),
                             rows(Up, c), ldp(c), nd[c].size, nrhs, nd[c].size, 1.0);
             else
@@ -2050,6 +2170,7 @@ class Solver {
         }
         if (stored) {
           run_pair_gemms(g);
+          run_gemms(g64);
         } else if (!md.empty()) {
           arena.clear();
           size_t om = arena.push(md);
@@ -2070,7 +2191,7 @@ class Solver {
     DevBuf* all[] = {&X, &Xp, &perm, &iperm, &pid, &knn, &knn_pos, &samp, &ranks, &skel,
                      &piv_ws, &A_ws, &status, &arena_dev, &step_dev, &tbuf, &vbuf, &vbuf32,
                      &ubuf, &rbuf, &wt, &io, &normbuf, &blocks_dev, &LU, &LUpiv, &Wb, &Zb, &Zpiv,
-                     &Cb, &LU32, &Wb32, &Zb32, &Cb32, &tbuf32, &Kleaf, &Ustore, &Pd, &Pf, &Ppair, &Xpair, &DInv32,
+                     &Cb, &LU32, &Wb32, &Zb32, &Cb32, &tbuf32, &Kleaf, &Ustore, &Pd, &Pf, &Ppair, &Xpair, &DInv32, &rhs_keep,
                      &gseg_dev, &kryl, &kzb, &coefbuf, &cseg_dev, &rowsum, &l_cand, &l_hits,
                      &l_feat, &l_score, &l_linfo, &l_samp, &l_rk, &l_Ptmp, &l_sktmp, &l_hold, &l_err,
                      &l_cols, &l_gram, &l_dense, &mlp_master, &mlp_m, &mlp_v, &mlp_grad, &mlp_b16,
@@ -2293,6 +2414,9 @@ int iaskit_set_option(const char* key, double value) {
       o.gemm_tc = as_int(0, 1);
     } else if (k == "cpqr_cluster") {
       o.cpqr_cluster = as_int(0, 1);
+    } else if (k == "pair_cond_max") {
+      if (!(value >= 1.0)) throw Error(IASKIT_ERR_ARG, "invalid pair_cond_max");
+      o.pair_cond_max = value;
     } else if (k == "profile") {
       int v = as_int(0, 1);
       IA_CUDA(cudaStreamSynchronize(S().st));
@@ -2324,6 +2448,7 @@ int iaskit_get_option(const char* key, double* value) {
     else if (k == "learned_temp") *value = o.learned_temp;
     else if (k == "gemm_tc") *value = o.gemm_tc;
     else if (k == "cpqr_cluster") *value = o.cpqr_cluster;
+    else if (k == "pair_cond_max") *value = o.pair_cond_max;
     else throw Error(IASKIT_ERR_ARG, "unknown option " + k);
   });
 }
@@ -2354,8 +2479,10 @@ int iaskit_stats(char* buf, size_t len) {
     snprintf(tmp, sizeof tmp, "%s%.6g", i ? "," : "", s.stats.refine_hist[i]);
     j += tmp;
   }
-  snprintf(tmp, sizeof tmp, "],\"refine_iters\":%d,\"refine_stagnated\":%d,\"fp64_problems\":%d,",
-           s.stats.refine_iters, s.stats.refine_stagnated, s.stats.fp64_problems);
+  snprintf(tmp, sizeof tmp, "],\"refine_iters\":%d,\"refine_stagnated\":%d,\"fp64_problems\":%d,"
+           "\"fp64_operator_problems\":%d,\"operator_upgrades\":%d,",
+           s.stats.refine_iters, s.stats.refine_stagnated, s.stats.fp64_problems, s.stats.fp64_operator_problems,
+           s.stats.operator_upgrades);
   j += tmp;
   snprintf(tmp, sizeof tmp,
            "\"learned_nodes\":%d,\"fallback_nodes\":%d,\"judge_err_plain\":%.6g,\"judge_err_chosen\":%.6g,"

@@ -121,3 +121,27 @@ def test_target_below_the_rounding_floor_stagnates(gpu_lib):
     Au = ia.iaskit_apply(w)
     rho = (np.linalg.norm(u - Au, axis=0) / np.linalg.norm(u, axis=0)).max()
     assert rho <= 1e-9
+
+
+def test_pair_operator_floor_upgrades_to_fp64(mixed_opts):
+    """A smooth, ill-conditioned problem (h = 1.2, lambda = 1e-3 on [0,1]^16) whose
+    refinement stops at the FP32-pair operator's rounding floor above the target gets
+    its operator blocks in FP64 and is refined again: the operator then agrees with
+    the FP64 oracle's blocks to FP64 rounding, and the residual reaches the target or
+    the FP64 floor."""
+    ia = mixed_opts
+    X = _uniform(2400, 35)
+    u = np.random.default_rng(36).standard_normal((len(X), 2))
+    ia.iaskit_set_option("refine", 400)
+    ia.iaskit_set_option("pair_cond_max", 1e300)   # start from the pair operator
+    try:
+        ia.iaskit_factor(X, 1.2, 1e-3, 128, 64, 1e-6)
+        w = ia.iaskit_solve(u)
+        st = ia.iaskit_stats()
+    finally:
+        ia.iaskit_set_option("pair_cond_max", 1e6)
+    print("upgrades", st["operator_upgrades"], "history", st["refine_history"])
+    assert st["operator_upgrades"] == 1 and st["fp64_operator_problems"] == 1
+    Au = ia.iaskit_apply(w)
+    rho = (np.linalg.norm(u - Au, axis=0) / np.linalg.norm(u, axis=0)).max()
+    assert rho <= 1e-10 or (st["refine_stagnated"] >= 1 and rho <= 1e-9), rho
