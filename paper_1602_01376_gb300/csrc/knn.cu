@@ -261,14 +261,27 @@ __global__ void __launch_bounds__(KT_NTH) knn_prefilter_kernel(const float* Xc, 
         const int c0 = cq * 32 + h * 16;
         float v[16];
         tc::tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(b * KT_RB + c0), v);
-        // distances of the 16 columns, and the mask of those below the list's bound
+        // distances of the 16 columns, and the mask of those below the list's bound: the
+        // columns that may enter (in range, not the query itself) form one mask per
+        // chunk, so a column costs a distance, a compare and a bit
+        unsigned ok = !active || c0 >= nt ? 0u : (nt - c0 >= 16 ? 0xFFFFu : (1u << (nt - c0)) - 1u);
+        const int self = my_q - (r0 + c0);
+        if (self >= 0 && self < 16) ok &= ~(1u << self);
+        const float bound = bd[KP - 1];
+        const float4* rn4 = reinterpret_cast<const float4*>(rn_s + b * KT_RB + c0);
         unsigned mask = 0;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = c0 + j;
-          v[j] = (qv + rn_s[b * KT_RB + col]) - 2.0f * v[j];
-          if (active && col < nt && r0 + col != my_q && v[j] <= bd[KP - 1]) mask |= 1u << j;
+        for (int j4 = 0; j4 < 4; ++j4) {
+          const float4 r4 = rn4[j4];
+          const float rr[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = 4 * j4 + u;
+            v[j] = (qv + rr[u]) - 2.0f * v[j];
+            mask |= (v[j] <= bound ? 1u : 0u) << j;
+          }
         }
+        mask &= ok;
         // insertions are rare: one copy of the insertion chain, column by column
         while (mask) {
           const int j = __ffs(mask) - 1;

@@ -92,16 +92,21 @@ __global__ void runs_kernel(const uint64_t* keys, size_t n, uint64_t sentinel, c
 __global__ void rank_keys_kernel(const int* run_start, const int* run_end, const uint64_t* run_key,
                                  int nruns, int pos_bits, int cnt_bits, uint64_t* keys2,
                                  uint32_t* vals2, int* node_cnt) {
-  int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nruns) return;
-  uint64_t k = run_key[r];
-  uint64_t node = k >> pos_bits;
-  uint32_t c = (uint32_t)(k & ((1ull << pos_bits) - 1));
-  uint64_t cnt = (uint64_t)(run_end[r] - run_start[r]);
-  uint64_t inv = ((1ull << cnt_bits) - 1) - cnt;
-  keys2[r] = (node << cnt_bits) | inv;
-  vals2[r] = c;
-  atomicAdd(&node_cnt[node], 1);
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = r < nruns;
+  uint64_t node = ~0ull;
+  if (in) {
+    const uint64_t k = run_key[r];
+    node = k >> pos_bits;
+    const uint32_t c = (uint32_t)(k & ((1ull << pos_bits) - 1));
+    const uint64_t cnt = (uint64_t)(run_end[r] - run_start[r]);
+    const uint64_t inv = ((1ull << cnt_bits) - 1) - cnt;
+    keys2[r] = (node << cnt_bits) | inv;
+    vals2[r] = c;
+  }
+  // runs are sorted by node: the lanes of one node add their count once
+  const unsigned same = __match_any_sync(0xffffffffu, node);
+  if (in && (threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&node_cnt[node], __popc(same));
 }
 
 // One block per node.  Shared memory: cap_pow2 ints for the sample and a hash set
