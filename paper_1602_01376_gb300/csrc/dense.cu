@@ -1485,6 +1485,18 @@ __global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>
   }
 }
 
+// D (16 x 8, FP32) += A (16 x 8) B (8 x 8), TF32 operands, one warp (mma.sync
+// m16n8k8; A row-major fragments: rows lane/4 and lane/4 + 8, columns lane%4 and
+// lane%4 + 4; B column fragments: rows lane%4 and lane%4 + 4, column lane/4; D: rows
+// lane/4 and lane/4 + 8, columns 2 (lane%4) and 2 (lane%4) + 1).
+__device__ __forceinline__ void mma_tf32_16x8x8(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
 // FP32 LU solve with the diagonal blocks' inverses (lu_diag_inverses): rows gathered
 // through the pivots' permutation; per 32-row block, X_b <- (L_bb)^-1 X_b as a small
 // product (every thread: one row, two columns), then the rows below get
@@ -1547,44 +1559,72 @@ __global__ void __launch_bounds__(RS_THREADS, 2) getrs_inv_kernel(const LuSolveD
       __syncthreads();
       if (di < bs) *reinterpret_cast<float2*>(&X[(size_t)(b0 + di) * RI_NC + dc]) = make_float2(o0, o1);
       __syncthreads();
-      // rows to update: below the block (L) or above it (U)
+      // rows to update: below the block (L) or above it (U).  X_r -= L_rb X_b as
+      // 16 x 16 x 32 products on the tensor cores (mma.sync m16n8k8 TF32, three
+      // products per FP32 product: lo.hi + hi.lo + hi.hi), one 16-row group per warp
+      // at a time; X_b's fragments are split once per step.
       const int r_lo = pass == 0 ? b0 + bs : 0, r_hi = pass == 0 ? n : b0;
-      for (int r = r_lo + tid; r < r_hi; r += 2 * RS_THREADS) {
-        const int r2 = r + RS_THREADS;
-        const bool two = r2 < r_hi;
-        const float* l0 = LU + (size_t)r + (size_t)b0 * ld;
-        const float* l1 = LU + (size_t)(two ? r2 : r) + (size_t)b0 * ld;
-        float a0[RI_NC], a1[RI_NC];
+      const int warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
+      uint32_t bh[4][2][2], bl[4][2][2];  // [k tile][n tile][reg]
 #pragma unroll
-        for (int c = 0; c < RI_NC; ++c) a0[c] = a1[c] = 0.0f;
+      for (int kt = 0; kt < 4; ++kt)
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {  // two halves of 16 columns of L (or U), each loaded at once
-          float lv0[16], lv1[16];
+        for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int kk = h * 16 + k;
-            lv0[k] = kk < bs ? l0[(size_t)kk * ld] : 0.0f;
-            lv1[k] = kk < bs ? l1[(size_t)kk * ld] : 0.0f;
+          for (int q = 0; q < 2; ++q) {
+            const int k = kt * 8 + tq + 4 * q;
+            const float x = k < bs ? X[(size_t)(b0 + k) * RI_NC + nt * 8 + gq] : 0.0f;
+            bh[kt][nt][q] = tc::to_tf32(x);
+            bl[kt][nt][q] = tc::to_tf32(x - __uint_as_float(bh[kt][nt][q]));
+          }
+      for (int R0 = r_lo + 16 * warp; R0 < r_hi; R0 += 16 * (RS_THREADS / 32)) {
+        const int ra = R0 + gq, rb = R0 + gq + 8;
+        const bool va = ra < r_hi, vb = rb < r_hi;
+        const float* la = LU + (size_t)(va ? ra : r_lo) + (size_t)b0 * ld;
+        const float* lb = LU + (size_t)(vb ? rb : r_lo) + (size_t)b0 * ld;
+        float av[4][4];  // [k tile][reg]: rows gq, gq + 8; columns tq, tq + 4
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+          const int k0 = kt * 8 + tq, k1 = k0 + 4;
+          av[kt][0] = (va && k0 < bs) ? la[(size_t)k0 * ld] : 0.0f;
+          av[kt][1] = (vb && k0 < bs) ? lb[(size_t)k0 * ld] : 0.0f;
+          av[kt][2] = (va && k1 < bs) ? la[(size_t)k1 * ld] : 0.0f;
+          av[kt][3] = (vb && k1 < bs) ? lb[(size_t)k1 * ld] : 0.0f;
+        }
+        float acc[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[nt][q] = 0.0f;
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) {
+          uint32_t ah[4], al[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            ah[q] = tc::to_tf32(av[kt][q]);
+            al[q] = tc::to_tf32(av[kt][q] - __uint_as_float(ah[q]));
           }
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int kk = h * 16 + k;
-            if (kk < bs) {
-              float xv[RI_NC];
-              load_row<float, RI_NC>(X, b0 + kk, xv);
-#pragma unroll
-              for (int c = 0; c < RI_NC; ++c) {
-                a0[c] = fmaf(lv0[k], xv[c], a0[c]);
-                a1[c] = fmaf(lv1[k], xv[c], a1[c]);
-              }
-            }
+          for (int nt = 0; nt < 2; ++nt) {
+            mma_tf32_16x8x8(acc[nt], al, bh[kt][nt]);
+            mma_tf32_16x8x8(acc[nt], ah, bl[kt][nt]);
+            mma_tf32_16x8x8(acc[nt], ah, bh[kt][nt]);
           }
         }
 #pragma unroll
-        for (int c = 0; c < RI_NC; ++c) X[(size_t)r * RI_NC + c] -= a0[c];
-        if (two)
-#pragma unroll
-          for (int c = 0; c < RI_NC; ++c) X[(size_t)r2 * RI_NC + c] -= a1[c];
+        for (int nt = 0; nt < 2; ++nt) {
+          const int c = nt * 8 + 2 * tq;
+          if (va) {
+            float2* xa = reinterpret_cast<float2*>(&X[(size_t)ra * RI_NC + c]);
+            const float2 t = *xa;
+            *xa = make_float2(t.x - acc[nt][0], t.y - acc[nt][1]);
+          }
+          if (vb) {
+            float2* xb = reinterpret_cast<float2*>(&X[(size_t)rb * RI_NC + c]);
+            const float2 t = *xb;
+            *xb = make_float2(t.x - acc[nt][2], t.y - acc[nt][3]);
+          }
+        }
       }
     }
   }
