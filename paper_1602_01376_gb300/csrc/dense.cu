@@ -1080,6 +1080,7 @@ __global__ void assemble_P_kernel(const PDescT<T>* descs, int ndesc) {
 //   tiled product.  The row swaps touch whole rows, as LAPACK's GETRF stores them.
 constexpr int LU_THREADS = 256;
 constexpr int LU_NB = 32;
+constexpr int LU_MAX_N = 1024;  // largest LU block
 constexpr int LU_TM = 64;  // trailing-update tile (rows)
 constexpr int LU_TN = 64;  // trailing-update tile (cols)
 
@@ -1163,6 +1164,8 @@ __global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* des
   __shared__ T L11[LU_NB][LU_NB + 1];
   __shared__ T As[LU_NB][LU_TM + 1];
   __shared__ T Bs[LU_NB][LU_TN + 1];
+  __shared__ int sw_perm[LU_MAX_N], sw_src[2 * LU_NB], sw_dst[2 * LU_NB];
+  __shared__ int sw_m;
   extern __shared__ __align__(16) unsigned char lu_sh[];
   const LuDescT<T> D = descs[blockIdx.x];
   T* A = D.A;
@@ -1210,10 +1213,11 @@ __global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* des
       }
       for (int i = k + 1 + tid; i < n; i += LU_THREADS) pn(i, j) /= piv;
       __syncthreads();
-      const int rows = n - k - 1, cols = nb - j - 1;
-      for (int t = tid; t < rows * cols; t += LU_THREADS) {
-        const int i = k + 1 + t % rows, c = j + 1 + t / rows;
-        pn(i, c) -= pn(i, j) * pn(k, c);
+      // rank-1 update of the panel's remaining columns: a thread per row, the pivot
+      // row's entries broadcast from the panel
+      for (int i = k + 1 + tid; i < n; i += LU_THREADS) {
+        const T l = pn(i, j);
+        for (int c = j + 1; c < nb; ++c) pn(i, c) -= l * pn(k, c);
       }
       __syncthreads();
     }
@@ -1224,16 +1228,51 @@ __global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* des
       }
       __syncthreads();
     }
-    // 2. the panel's row swaps on the columns outside the panel
-    for (int c = tid; c < n; c += LU_THREADS) {
-      if (c >= k0 && c < k0 + nb) continue;
+    // 2. the panel's row interchanges on the columns outside the panel, as one
+    //    permutation: row i receives old row sw_perm[i - k0]; the (at most 2 nb) rows
+    //    that move are listed, then every warp moves them column by column with all of
+    //    a column group's loads issued before its stores
+    for (int i = k0 + tid; i < n; i += LU_THREADS) sw_perm[i - k0] = i;
+    if (tid == 0) sw_m = 0;
+    __syncthreads();
+    if (tid == 0)
       for (int j = 0; j < nb; ++j) {
         const int p = D.ipiv[k0 + j];
         if (p != k0 + j) {
-          T t = at(k0 + j, c);
-          at(k0 + j, c) = at(p, c);
-          at(p, c) = t;
+          const int t = sw_perm[j];
+          sw_perm[j] = sw_perm[p - k0];
+          sw_perm[p - k0] = t;
         }
+      }
+    __syncthreads();
+    for (int i = k0 + tid; i < n; i += LU_THREADS)
+      if (sw_perm[i - k0] != i) {
+        const int q = atomicAdd(&sw_m, 1);
+        sw_src[q] = sw_perm[i - k0];
+        sw_dst[q] = i;
+      }
+    __syncthreads();
+    {
+      const int m = sw_m, nout = n - nb, lane = tid & 31, warp = tid >> 5;
+      for (int x0 = warp * 4; x0 < nout && m > 0; x0 += 4 * (LU_THREADS / 32)) {
+        T v[2][4];
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int t = lane + 32 * q, x = x0 + u;
+            const int c = x < k0 ? x : x + nb;
+            v[q][u] = (t < m && x < nout) ? at(sw_src[t], c) : (T)0;
+          }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int t = lane + 32 * q, x = x0 + u;
+            const int c = x < k0 ? x : x + nb;
+            if (t < m && x < nout) at(sw_dst[t], c) = v[q][u];
+          }
       }
     }
     __syncthreads();
@@ -1948,6 +1987,7 @@ void getrf_batched(const LuDescT<T>* descs_dev, int ndesc, int max_n, int* dev_s
                    cudaStream_t st, bool inv) {
   if (ndesc <= 0) return;
   if (max_n <= 0) return;  // every block is empty
+  if (max_n > LU_MAX_N) throw Error(IASKIT_ERR_UNSUPPORTED, "LU block larger than 1024");
   ProfScope _ps(pk_of<T>(PK_GETRF), st);
   // the panel (rows x 32) in shared memory when it fits next to the static tiles
   const int pld = max_n;
