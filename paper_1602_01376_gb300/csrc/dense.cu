@@ -422,6 +422,25 @@ __device__ __forceinline__ void pair_warp_sum(float& h, float& l) {
     fp2::fast_two_sum(sm, e, h, l);
   }
 }
+// Sum of 32 FP32 values x[0], x[stride], ... in order, as a pair (two-sum chain).
+__device__ __forceinline__ float2 pair_sum32(const float* x, int stride) {
+  float h = 0.0f, l = 0.0f;
+#pragma unroll 8
+  for (int i = 0; i < 32; ++i) {
+    float sm, e;
+    fp2::two_sum(h, x[i * stride], sm, e);
+    h = sm;
+    l = __fadd_rn(l, e);
+  }
+  float rh, rl;
+  fp2::fast_two_sum(h, l, rh, rl);
+  return make_float2(rh, rl);
+}
+// Per warp: the lane partials of up to QP_SLOTS columns (slot-major, padded rows), so
+// that lane s combines slot s's 32 partials in one sequential pair sum instead of a
+// butterfly per column.
+constexpr int QP_SLOTS = 64, QP_LD = 33;
+
 // (best, idx) over the warp: larger pair wins, equal pairs go to the lower index.
 __device__ __forceinline__ void pair_warp_argmax(float2& v, int& idx) {
 #pragma unroll
@@ -467,6 +486,8 @@ __global__ void __launch_bounds__(QR_THREADS) cpqr_f32_kernel(const CpqrDescT<fl
   float* v = reinterpret_cast<float*>(shq + nc);
   int* piv = reinterpret_cast<int*>(shq + nc + nr);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // per-warp lane partials of the column norms (after piv, 16-byte aligned)
+  float* psum = reinterpret_cast<float*>(shq + nc + nr + (nc + 1) / 2 + 1) + (size_t)warp * QP_SLOTS * QP_LD;
   for (int j = warp; j < nc; j += QR_WARPS) {
     float part = 0.0f;
     for (int i = lane; i < nr; i += 32) {
@@ -613,15 +634,17 @@ __global__ void __launch_bounds__(QR_THREADS) cpqr_f32_kernel(const CpqrDescT<fl
             }
           }
         }
-        float nl[CW];
+        const int slot0 = ((j - (k + 1 + CW * warp)) / (CW * QR_WARPS)) * CW;
 #pragma unroll
-        for (int c = 0; c < CW; ++c) nl[c] = 0.0f;
-#pragma unroll
-        for (int c = 0; c < CW; ++c) pair_warp_sum(pn[c], nl[c]);
-        if (lane == 0)
-#pragma unroll
-          for (int c = 0; c < CW; ++c)
-            if (has[c]) norms[j + c] = make_float2(pn[c], nl[c]);
+        for (int c = 0; c < CW; ++c) psum[(size_t)(slot0 + c) * QP_LD + lane] = pn[c];
+      }
+      // every column of this warp: its norm from the 32 lane partials, lane s for slot s
+      __syncwarp();
+      const int ncol_w = nc - (k + 1 + CW * warp);
+      const int nslot = ncol_w > 0 ? ((ncol_w + CW * QR_WARPS - 1) / (CW * QR_WARPS)) * CW : 0;
+      for (int sl = lane; sl < nslot; sl += 32) {
+        const int col = k + 1 + CW * warp + (sl / CW) * (CW * QR_WARPS) + sl % CW;
+        if (col < nc) norms[col] = pair_sum32(psum + (size_t)sl * QP_LD, 1);
       }
     } else {
       for (int j = k + 1 + warp; j < nc; j += QR_WARPS) {
@@ -676,6 +699,7 @@ struct QcShared {
   double nu;
   float alpha, beta;
   int best_j, cand_q, stop;
+  float psum[QC_THREADS / 32][4][32];  // per warp: lane partials of its 4 columns' norms
 };
 
 __global__ void __launch_bounds__(QC_THREADS, 1) cpqr_cluster_kernel(const CpqrDescT<float>* descs, int s_max,
@@ -856,7 +880,7 @@ __global__ void __launch_bounds__(QC_THREADS, 1) cpqr_cluster_kernel(const CpqrD
       for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
         for (int c = 0; c < 4; ++c) dt[c] += __shfl_xor_sync(0xffffffffu, dt[c], o);
-      float pn[4] = {0.0f, 0.0f, 0.0f, 0.0f}, nl[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      float pn[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
       for (int t = 0; t < QC_RPL; ++t) {
         const int i = lane + 32 * t;
@@ -870,12 +894,11 @@ __global__ void __launch_bounds__(QC_THREADS, 1) cpqr_cluster_kernel(const CpqrD
           }
         }
       }
+      // the norms from the 32 lane partials in lane order (as in cpqr_f32_kernel)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) pair_warp_sum(pn[c], nl[c]);
-      if (lane == 0)
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-          if (live[c]) norm_s[warp * 4 + c] = make_float2(pn[c], nl[c]);
+      for (int c = 0; c < 4; ++c) S.psum[warp][c][lane] = pn[c];
+      __syncwarp();
+      if (lane < 4 && live[lane]) norm_s[warp * 4 + lane] = pair_sum32(&S.psum[warp][lane][0], 1);
     }
     s = k + 1;
   }
@@ -1960,10 +1983,12 @@ void cpqr_id(const CpqrDescT<T>* descs_dev, int ndesc, int max_rows, int max_col
   if (smem > 220 * 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "ID block too large for one CTA");
   ProfScope _ps(pk_of<T>(PK_CPQR), st);
   if (std::is_same<T, float>::value) {
-    if (smem > 48 * 1024)
-      IA_CUDA(cudaFuncSetAttribute(cpqr_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    cpqr_f32_kernel<<<ndesc, QR_THREADS, smem, st>>>(reinterpret_cast<const CpqrDescT<float>*>(descs_dev), s_max,
-                                                    tol);
+    if (max_cols > QP_SLOTS * QR_WARPS) throw Error(IASKIT_ERR_UNSUPPORTED, "ID block wider than 1024 columns");
+    const size_t smem32 = (size_t)(2 * max_cols + max_rows + (max_cols + 1) / 2 + 1) * sizeof(double) +
+                          (size_t)QR_WARPS * QP_SLOTS * QP_LD * sizeof(float);
+    IA_CUDA(cudaFuncSetAttribute(cpqr_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
+    cpqr_f32_kernel<<<ndesc, QR_THREADS, smem32, st>>>(reinterpret_cast<const CpqrDescT<float>*>(descs_dev),
+                                                      s_max, tol);
   } else {
     if (smem > 48 * 1024)
       IA_CUDA(cudaFuncSetAttribute(cpqr_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
