@@ -1220,7 +1220,24 @@ __global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* des
           bi = i;
         }
       }
-      block_argmax_t<T>(best, bi, rv, ri);
+      // the warps' candidates, then every thread combines them (one barrier)
+      warp_argmax_t(best, bi);
+      if ((tid & 31) == 0) {
+        rv[tid >> 5] = best;
+        ri[tid >> 5] = bi;
+      }
+      __syncthreads();
+      best = rv[0];
+      bi = ri[0];
+#pragma unroll
+      for (int w = 1; w < LU_THREADS / 32; ++w) {
+        const T v2 = rv[w];
+        const int i2 = ri[w];
+        if (v2 > best || (v2 == best && i2 < bi)) {
+          best = v2;
+          bi = i2;
+        }
+      }
       const int p = bi;
       if (tid == 0) D.ipiv[k] = p;
       if (p != k && tid < nb) {
@@ -1234,12 +1251,11 @@ __global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* des
         if (tid == 0) atomicOr(status, DEV_SINGULAR);
         continue;
       }
-      for (int i = k + 1 + tid; i < n; i += LU_THREADS) pn(i, j) /= piv;
-      __syncthreads();
-      // rank-1 update of the panel's remaining columns: a thread per row, the pivot
-      // row's entries broadcast from the panel
+      // scaling and rank-1 update of the panel's remaining columns: a thread per row,
+      // the pivot row's entries broadcast from the panel
       for (int i = k + 1 + tid; i < n; i += LU_THREADS) {
-        const T l = pn(i, j);
+        const T l = pn(i, j) / piv;
+        pn(i, j) = l;
         for (int c = j + 1; c < nb; ++c) pn(i, c) -= l * pn(k, c);
       }
       __syncthreads();
