@@ -1655,20 +1655,28 @@ __global__ void __launch_bounds__(RS_THREADS, 2) getrs_inv_kernel(const LuSolveD
             bh[kt][nt][q] = tc::to_tf32(x);
             bl[kt][nt][q] = tc::to_tf32(x - __uint_as_float(bh[kt][nt][q]));
           }
-      for (int R0 = r_lo + 16 * warp; R0 < r_hi; R0 += 16 * (RS_THREADS / 32)) {
-        const int ra = R0 + gq, rb = R0 + gq + 8;
+      // the L (or U) fragments of a row group: rows gq, gq + 8; columns tq, tq + 4
+      auto load_frag = [&](int R, float (&f)[4][4]) {
+        const int ra = R + gq, rb = R + gq + 8;
         const bool va = ra < r_hi, vb = rb < r_hi;
         const float* la = LU + (size_t)(va ? ra : r_lo) + (size_t)b0 * ld;
         const float* lb = LU + (size_t)(vb ? rb : r_lo) + (size_t)b0 * ld;
-        float av[4][4];  // [k tile][reg]: rows gq, gq + 8; columns tq, tq + 4
 #pragma unroll
         for (int kt = 0; kt < 4; ++kt) {
           const int k0 = kt * 8 + tq, k1 = k0 + 4;
-          av[kt][0] = (va && k0 < bs) ? la[(size_t)k0 * ld] : 0.0f;
-          av[kt][1] = (vb && k0 < bs) ? lb[(size_t)k0 * ld] : 0.0f;
-          av[kt][2] = (va && k1 < bs) ? la[(size_t)k1 * ld] : 0.0f;
-          av[kt][3] = (vb && k1 < bs) ? lb[(size_t)k1 * ld] : 0.0f;
+          f[kt][0] = (va && k0 < bs) ? la[(size_t)k0 * ld] : 0.0f;
+          f[kt][1] = (vb && k0 < bs) ? lb[(size_t)k0 * ld] : 0.0f;
+          f[kt][2] = (va && k1 < bs) ? la[(size_t)k1 * ld] : 0.0f;
+          f[kt][3] = (vb && k1 < bs) ? lb[(size_t)k1 * ld] : 0.0f;
         }
+      };
+      constexpr int RSTEP = 16 * (RS_THREADS / 32);
+      float av[4][4], an[4][4];  // this row group's fragments, and the next one's (in flight)
+      if (r_lo + 16 * warp < r_hi) load_frag(r_lo + 16 * warp, av);
+      for (int R0 = r_lo + 16 * warp; R0 < r_hi; R0 += RSTEP) {
+        const int ra = R0 + gq, rb = R0 + gq + 8;
+        const bool va = ra < r_hi, vb = rb < r_hi;
+        if (R0 + RSTEP < r_hi) load_frag(R0 + RSTEP, an);
         float acc[2][4];
 #pragma unroll
         for (int nt = 0; nt < 2; ++nt)
@@ -1703,6 +1711,10 @@ __global__ void __launch_bounds__(RS_THREADS, 2) getrs_inv_kernel(const LuSolveD
             *xb = make_float2(t.x - acc[nt][2], t.y - acc[nt][3]);
           }
         }
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) av[kt][q] = an[kt][q];
       }
     }
   }
