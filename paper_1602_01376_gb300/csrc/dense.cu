@@ -2166,13 +2166,20 @@ __device__ __forceinline__ void pair_mac(float ah, float al, float bh, float bl,
 }
 
 constexpr int GP_K = 16;
-__global__ void __launch_bounds__(G_THREADS) gemm_pair_kernel(const GemmDescPair* descs, const GemmTile* tiles) {
+// An A entry as a pair: stored as a pair, or split from FP64 on the way in.
+__device__ __forceinline__ float2 a_pair(float2 v) { return v; }
+__device__ __forceinline__ float2 a_pair(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(v - (double)h));
+}
+template <typename DescT>
+__global__ void __launch_bounds__(G_THREADS) gemm_pair_kernel(const DescT* descs, const GemmTile* tiles) {
   constexpr int TM = GEMM_PAIR_TM, TN = GEMM_PAIR_TN, TX = TM / 4;
   static_assert(TX * (TN / 4) == G_THREADS, "tile must map to 256 threads");
   __shared__ __align__(16) float Ash[GP_K][TM + 4], Asl[GP_K][TM + 4];
   __shared__ __align__(16) float Bsh[GP_K][TN + 4], Bsl[GP_K][TN + 4];
   const GemmTile Tl = tiles[blockIdx.x];
-  const GemmDescPair D = descs[Tl.desc];
+  const DescT D = descs[Tl.desc];
   const int m0 = Tl.tm * TM, n0 = Tl.tn * TN;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   float s[4][4], c[4][4];
@@ -2186,7 +2193,7 @@ __global__ void __launch_bounds__(G_THREADS) gemm_pair_kernel(const GemmDescPair
       const int e = threadIdx.x + r * G_THREADS;
       const int am = e % TM, ak = e / TM;
       const int gm = m0 + am, gk = k0 + ak;
-      const float2 v = (gm < D.M && gk < D.K) ? D.A[(size_t)gm + (size_t)gk * D.lda] : make_float2(0.0f, 0.0f);
+      const float2 v = (gm < D.M && gk < D.K) ? a_pair(D.A[(size_t)gm + (size_t)gk * D.lda]) : make_float2(0.0f, 0.0f);
       Ash[ak][am] = v.x;
       Asl[ak][am] = v.y;
     }
@@ -2231,7 +2238,13 @@ __global__ void __launch_bounds__(G_THREADS) gemm_pair_kernel(const GemmDescPair
 void gemm_pair_grouped(const GemmDescPair* descs_dev, const GemmTile* tiles_dev, int ntiles, cudaStream_t st) {
   if (ntiles <= 0) return;
   ProfScope _ps(PK_GEMM_PAIR, st);
-  gemm_pair_kernel<<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
+  gemm_pair_kernel<GemmDescPair><<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
+  IA_LAUNCH_CHECK();
+}
+void gemm_pair64_grouped(const GemmDesc* descs_dev, const GemmTile* tiles_dev, int ntiles, cudaStream_t st) {
+  if (ntiles <= 0) return;
+  ProfScope _ps(PK_GEMM_PAIR, st);
+  gemm_pair_kernel<GemmDesc><<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
   IA_LAUNCH_CHECK();
 }
 

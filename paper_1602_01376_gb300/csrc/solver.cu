@@ -176,11 +176,12 @@ void add_gemm(std::vector<GemmDescT<T>>& g, const T* A, int lda, const T* B, int
 // Tile list of one grouped launch: 256 x 16 tiles when no problem has more than 16
 // columns (right-hand-side blocks of a solve); otherwise 128 x 128 tensor-core tiles
 // for FP32 products (when enabled) and 64 x 64 tiles for FP64 ones.
+// skinny: 256 x 16 tiles whatever the widths (the tiles of the FP32-pair products).
 template <typename T>
-GemmShape make_tiles(const std::vector<GemmDescT<T>>& g, std::vector<GemmTile>& t, bool tc) {
+GemmShape make_tiles(const std::vector<GemmDescT<T>>& g, std::vector<GemmTile>& t, bool tc, bool skinny = false) {
   int maxn = 0;
   for (const auto& d : g) maxn = std::max(maxn, d.N);
-  const GemmShape shape = maxn <= 16                                     ? GEMM_SKINNY
+  const GemmShape shape = (maxn <= 16 || skinny)                         ? GEMM_SKINNY
                           : (tc && std::is_same<T, float>::value) ? GEMM_TC
                                                                         : GEMM_SQUARE;
   const int tm_ = gemm_tile_m(shape), tn_ = gemm_tile_n(shape);
@@ -408,17 +409,31 @@ class Solver {
     if (v & DEV_TIMEOUT) throw Error(IASKIT_ERR_TIMEOUT, "bounded device wait expired");
     if (v & DEV_OVERFLOW) throw Error(IASKIT_ERR_UNSUPPORTED, "internal bound exceeded");
   }
+  // FP64 products of the mixed form's factorization and preconditioner (problems
+  // factored in FP64) run on FP32 pairs (about 2^-44 relative, on the FP32 pipes);
+  // the operator apply keeps FP64 products for the problems whose operator is in FP64.
+  bool in_apply = false;
+  template <typename T>
+  bool pair_products() const {
+    return std::is_same<T, double>::value && prec == PREC_MIXED && !in_apply;
+  }
+  template <typename T>
+  void launch_gemms(const GemmDescT<T>* descs_dev, const GemmTile* tiles_dev, int ntiles, GemmShape shape) {
+    if (pair_products<T>())
+      gemm_pair64_grouped(reinterpret_cast<const GemmDesc*>(descs_dev), tiles_dev, ntiles, st);
+    else
+      gemm_grouped(descs_dev, tiles_dev, ntiles, shape, st, status.as<int>());
+  }
   template <typename T>
   void run_gemms(const std::vector<GemmDescT<T>>& g) {
     if (g.empty()) return;
     std::vector<GemmTile> t;
-    const GemmShape shape = make_tiles(g, t, opt.gemm_tc != 0);
+    const GemmShape shape = make_tiles(g, t, opt.gemm_tc != 0, pair_products<T>());
     arena.clear();
     size_t og = arena.push(g), ot = arena.push(t);
     char* base = upload_arena();
-    prof().flops[pk_of<T>(PK_GEMM)] += gemm_flops(g);
-    gemm_grouped((const GemmDescT<T>*)(base + og), (const GemmTile*)(base + ot), (int)t.size(),
-                 shape, st, status.as<int>());
+    prof().flops[pair_products<T>() ? PK_GEMM_PAIR : pk_of<T>(PK_GEMM)] += gemm_flops(g);
+    launch_gemms((const GemmDescT<T>*)(base + og), (const GemmTile*)(base + ot), (int)t.size(), shape);
   }
   // C (+)= A B with A stored as FP32 pairs (the operator blocks of the mixed form)
   static void add_pair_gemm(std::vector<GemmDescPair>& g, const float2* A, int lda, const double* B, int ldb,
@@ -587,20 +602,19 @@ class Solver {
       }
       if (cp.empty()) continue;
       std::vector<GemmTile> t1, t2;
-      const GemmShape sh1 = make_tiles(g1, t1, opt.gemm_tc != 0), sh2 = make_tiles(g2, t2, opt.gemm_tc != 0);
+      const GemmShape sh1 = make_tiles(g1, t1, opt.gemm_tc != 0, pair_products<T>()),
+                      sh2 = make_tiles(g2, t2, opt.gemm_tc != 0, pair_products<T>());
       arena.clear();
       size_t ocp = arena.push(cp), ozs = arena.push(zs), og1 = arena.push(g1), ot1 = arena.push(t1),
              og2 = arena.push(g2), ot2 = arena.push(t2);
       char* base = upload_arena();
       prof().flops[pk_of<T>(PK_GETRS)] += getrs_flops(zs);
-      prof().flops[pk_of<T>(PK_GEMM)] += gemm_flops(g1) + gemm_flops(g2);
+      prof().flops[pair_products<T>() ? PK_GEMM_PAIR : pk_of<T>(PK_GEMM)] += gemm_flops(g1) + gemm_flops(g2);
       copy_batched((const CopyDescT<T>*)(base + ocp), (int)cp.size(), max_cp, st);
       getrs_batched((const LuSolveDescT<T>*)(base + ozs), (int)zs.size(), max_n2, max_nc, st,
                     std::is_same<T, float>::value);
-      gemm_grouped((const GemmDescT<T>*)(base + og1), (const GemmTile*)(base + ot1), (int)t1.size(),
-                   sh1, st, status.as<int>());
-      gemm_grouped((const GemmDescT<T>*)(base + og2), (const GemmTile*)(base + ot2), (int)t2.size(),
-                   sh2, st, status.as<int>());
+      launch_gemms((const GemmDescT<T>*)(base + og1), (const GemmTile*)(base + ot1), (int)t1.size(), sh1);
+      launch_gemms((const GemmDescT<T>*)(base + og2), (const GemmTile*)(base + ot2), (int)t2.size(), sh2);
     }
   }
 
@@ -2081,6 +2095,11 @@ class Solver {
   void apply_device(const double* w, double* u, int nrhs) {
     if (!factored) throw Error(IASKIT_ERR_NOT_FACTORED, "no factorization");
     if (nrhs < 1) throw Error(IASKIT_ERR_ARG, "bad nrhs");
+    struct ApplyScope {
+      bool& f;
+      explicit ApplyScope(bool& flag) : f(flag) { f = true; }
+      ~ApplyScope() { f = false; }
+    } scope(in_apply);
     const double t0 = now_ms();
     const bool stored = prec == PREC_MIXED;
     const size_t n = (size_t)Ntot * nrhs;
