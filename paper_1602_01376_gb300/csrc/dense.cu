@@ -2172,9 +2172,9 @@ __device__ __forceinline__ float2 a_pair(double v) {
   const float h = __double2float_rn(v);
   return make_float2(h, __double2float_rn(v - (double)h));
 }
-template <typename DescT>
+template <typename DescT, int TM, int TN>
 __global__ void __launch_bounds__(G_THREADS) gemm_pair_kernel(const DescT* descs, const GemmTile* tiles) {
-  constexpr int TM = GEMM_PAIR_TM, TN = GEMM_PAIR_TN, TX = TM / 4;
+  constexpr int TX = TM / 4;
   static_assert(TX * (TN / 4) == G_THREADS, "tile must map to 256 threads");
   __shared__ __align__(16) float Ash[GP_K][TM + 4], Asl[GP_K][TM + 4];
   __shared__ __align__(16) float Bsh[GP_K][TN + 4], Bsl[GP_K][TN + 4];
@@ -2197,9 +2197,11 @@ __global__ void __launch_bounds__(G_THREADS) gemm_pair_kernel(const DescT* descs
       Ash[ak][am] = v.x;
       Asl[ak][am] = v.y;
     }
-    {
-      static_assert(TN * GP_K == G_THREADS, "one B element per thread");
-      const int bk = threadIdx.x % GP_K, bn = threadIdx.x / GP_K;
+    static_assert((TN * GP_K) % G_THREADS == 0, "whole B elements per thread");
+#pragma unroll
+    for (int r = 0; r < TN * GP_K / G_THREADS; ++r) {
+      const int e = threadIdx.x + r * G_THREADS;
+      const int bk = e % GP_K, bn = e / GP_K;
       const int gk = k0 + bk, gn = n0 + bn;
       const double b = (gk < D.K && gn < D.N) ? D.B[(size_t)gk + (size_t)gn * D.ldb] : 0.0;
       const float bh = __double2float_rn(b);
@@ -2238,13 +2240,19 @@ __global__ void __launch_bounds__(G_THREADS) gemm_pair_kernel(const DescT* descs
 void gemm_pair_grouped(const GemmDescPair* descs_dev, const GemmTile* tiles_dev, int ntiles, cudaStream_t st) {
   if (ntiles <= 0) return;
   ProfScope _ps(PK_GEMM_PAIR, st);
-  gemm_pair_kernel<GemmDescPair><<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
+  gemm_pair_kernel<GemmDescPair, GEMM_PAIR_TM, GEMM_PAIR_TN><<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
   IA_LAUNCH_CHECK();
 }
-void gemm_pair64_grouped(const GemmDesc* descs_dev, const GemmTile* tiles_dev, int ntiles, cudaStream_t st) {
+void gemm_pair64_grouped(const GemmDesc* descs_dev, const GemmTile* tiles_dev, int ntiles, GemmShape shape,
+                         cudaStream_t st) {
   if (ntiles <= 0) return;
   ProfScope _ps(PK_GEMM_PAIR, st);
-  gemm_pair_kernel<GemmDesc><<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
+  if (shape == GEMM_SKINNY)
+    gemm_pair_kernel<GemmDesc, 256, 16><<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
+  else if (shape == GEMM_SQUARE)
+    gemm_pair_kernel<GemmDesc, 64, 64><<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
+  else
+    throw Error(IASKIT_ERR_ARG, "pair products take 256 x 16 or 64 x 64 tiles");
   IA_LAUNCH_CHECK();
 }
 

@@ -276,10 +276,11 @@ struct GemmDescPair {
 };
 constexpr int GEMM_PAIR_TM = 256, GEMM_PAIR_TN = 16;
 void gemm_pair_grouped(const GemmDescPair* descs_dev, const GemmTile* tiles_dev, int ntiles, cudaStream_t st);
-// The same products with A in FP64 (split into pairs as it is loaded), 256 x 16 tiles
-// (GEMM_PAIR_TM x GEMM_PAIR_TN): FP64 inputs and output at about 2^-44 relative, on
-// the FP32 pipes.
-void gemm_pair64_grouped(const GemmDesc* descs_dev, const GemmTile* tiles_dev, int ntiles, cudaStream_t st);
+// The same products with A in FP64 (split into pairs as it is loaded): FP64 inputs and
+// output at about 2^-44 relative, on the FP32 pipes.  Tiles of gemm_tile_m(shape) x
+// gemm_tile_n(shape) for GEMM_SKINNY (256 x 16) and GEMM_SQUARE (64 x 64).
+void gemm_pair64_grouped(const GemmDesc* descs_dev, const GemmTile* tiles_dev, int ntiles, GemmShape shape,
+                         cudaStream_t st);
 
 // Row permutation of an N x ncols column-major block: out[p] = in[perm[p]] (gather)
 // or out[perm[p]] = in[p] (scatter).

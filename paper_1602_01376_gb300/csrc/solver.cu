@@ -175,13 +175,13 @@ void add_gemm(std::vector<GemmDescT<T>>& g, const T* A, int lda, const T* B, int
 
 // Tile list of one grouped launch: 256 x 16 tiles when no problem has more than 16
 // columns (right-hand-side blocks of a solve); otherwise 128 x 128 tensor-core tiles
-// for FP32 products (when enabled) and 64 x 64 tiles for FP64 ones.
-// skinny: 256 x 16 tiles whatever the widths (the tiles of the FP32-pair products).
+// for FP32 products (when enabled) and 64 x 64 tiles for FP64 ones (on FP64 or on
+// FP32 pairs).
 template <typename T>
-GemmShape make_tiles(const std::vector<GemmDescT<T>>& g, std::vector<GemmTile>& t, bool tc, bool skinny = false) {
+GemmShape make_tiles(const std::vector<GemmDescT<T>>& g, std::vector<GemmTile>& t, bool tc) {
   int maxn = 0;
   for (const auto& d : g) maxn = std::max(maxn, d.N);
-  const GemmShape shape = (maxn <= 16 || skinny)                         ? GEMM_SKINNY
+  const GemmShape shape = maxn <= 16                                      ? GEMM_SKINNY
                           : (tc && std::is_same<T, float>::value) ? GEMM_TC
                                                                         : GEMM_SQUARE;
   const int tm_ = gemm_tile_m(shape), tn_ = gemm_tile_n(shape);
@@ -420,7 +420,7 @@ class Solver {
   template <typename T>
   void launch_gemms(const GemmDescT<T>* descs_dev, const GemmTile* tiles_dev, int ntiles, GemmShape shape) {
     if (pair_products<T>())
-      gemm_pair64_grouped(reinterpret_cast<const GemmDesc*>(descs_dev), tiles_dev, ntiles, st);
+      gemm_pair64_grouped(reinterpret_cast<const GemmDesc*>(descs_dev), tiles_dev, ntiles, shape, st);
     else
       gemm_grouped(descs_dev, tiles_dev, ntiles, shape, st, status.as<int>());
   }
@@ -428,7 +428,7 @@ class Solver {
   void run_gemms(const std::vector<GemmDescT<T>>& g) {
     if (g.empty()) return;
     std::vector<GemmTile> t;
-    const GemmShape shape = make_tiles(g, t, opt.gemm_tc != 0, pair_products<T>());
+    const GemmShape shape = make_tiles(g, t, opt.gemm_tc != 0);
     arena.clear();
     size_t og = arena.push(g), ot = arena.push(t);
     char* base = upload_arena();
@@ -602,8 +602,8 @@ class Solver {
       }
       if (cp.empty()) continue;
       std::vector<GemmTile> t1, t2;
-      const GemmShape sh1 = make_tiles(g1, t1, opt.gemm_tc != 0, pair_products<T>()),
-                      sh2 = make_tiles(g2, t2, opt.gemm_tc != 0, pair_products<T>());
+      const GemmShape sh1 = make_tiles(g1, t1, opt.gemm_tc != 0),
+                      sh2 = make_tiles(g2, t2, opt.gemm_tc != 0);
       arena.clear();
       size_t ocp = arena.push(cp), ozs = arena.push(zs), og1 = arena.push(g1), ot1 = arena.push(t1),
              og2 = arena.push(g2), ot2 = arena.push(t2);
