@@ -1426,13 +1426,70 @@ __device__ __forceinline__ void load_row(const T* X, int row, T (&out)[NC]) {
   }
 }
 
+// (s, c) += (ah + al)(bh + bl): the product ah bh exactly as p + e (FMA), the cross
+// terms and e into the low part, p into the high part by Knuth's two-sum (its rounding
+// error into the low part as well).  The explicitly rounded operations keep the
+// compiler from contracting the two-sum into FMAs.
+__device__ __forceinline__ void pair_mac(float ah, float al, float bh, float bl, float& s, float& c) {
+  const float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  c = __fadd_rn(c, __fadd_rn(err, e));
+  s = t;
+}
+
+// X_r -= sum_{k < bs} M[r, b0 + k] X_{b0 + k} (one row r, NC columns) with the 32 rows
+// X_{b0..} given as FP32 pairs in Xp (row-major, 32 x NC): each FP64 entry of M is split
+// into a pair as it is loaded, the products are formed exactly and summed as pairs
+// (pair_mac), and the sum is subtracted in FP64.  Only the split and the final
+// subtraction use the FP64 pipe: one FP64 operation per entry of M instead of NC FMAs.
+template <int NC>
+__device__ __forceinline__ void pair_row_update(const double* M, int ld, int r, int b0, int bs,
+                                                const float2* Xp, double* X) {
+  float s[NC], c[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) s[q] = c[q] = 0.0f;
+  for (int k = 0; k < bs; ++k) {
+    const double mv = M[(size_t)r + (size_t)(b0 + k) * ld];
+    const float mh = __double2float_rn(mv), ml = __double2float_rn(mv - (double)mh);
+    const float2* xr = Xp + k * NC;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      const float2 x = xr[q];
+      pair_mac(mh, ml, x.x, x.y, s[q], c[q]);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NC; ++q) X[(size_t)r * NC + q] -= (double)s[q] + (double)c[q];
+}
+
+// The rows b0 .. b0 + bs of X, split into FP32 pairs (rows past bs zero).
+template <int NC>
+__device__ __forceinline__ void split_rows(const double* X, int b0, int bs, float2* Xp, int tid) {
+  for (int e = tid; e < 32 * NC; e += RS_THREADS) {
+    const int k = e / NC;
+    const double v = k < bs ? X[(size_t)(b0 + k) * NC + (e % NC)] : 0.0;
+    const float h = __double2float_rn(v);
+    Xp[e] = make_float2(h, __double2float_rn(v - (double)h));
+  }
+}
+
 // X (n x NC chunk of right-hand sides) lives in shared memory row-major, so that the
 // register-tiled updates read a row of X with 16-byte broadcasts.  The 32 x 32
 // diagonal blocks are read into registers before their sequential substitution.
-template <typename T, int NC, bool UPPER_ONLY>
+// PAIR (FP64 only): the updates below and above each diagonal block run on FP32 pairs
+// (pair_row_update); the substitutions through the diagonal blocks stay in FP64.
+template <typename T, int NC, bool UPPER_ONLY, bool PAIR>
 __global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>* descs) {
+  static_assert(!PAIR || sizeof(T) == 8, "pair updates take FP64 factors");
   extern __shared__ __align__(16) unsigned char rs_sh[];
-  T* X = reinterpret_cast<T*>(rs_sh);  // n x NC, row-major, X[i * NC + c]
+  // PAIR: the current block's 32 rows as pairs first, 32 x NC float2
+  float2* Xp = reinterpret_cast<float2*>(rs_sh);
+  T* X = reinterpret_cast<T*>(rs_sh + (PAIR ? 32 * NC * sizeof(float2) : 0));  // n x NC, X[i * NC + c]
   const LuSolveDescT<T> D = descs[blockIdx.y];
   const int c0 = blockIdx.x * NC;
   if (c0 >= D.ncols) return;
@@ -1487,6 +1544,17 @@ __global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>
       }
     }
     __syncthreads();
+    if constexpr (PAIR) {
+      if (b0 + bs < n) {
+        split_rows<NC>(reinterpret_cast<const double*>(X), b0, bs, Xp, tid);
+        __syncthreads();
+        for (int r = b0 + bs + tid; r < n; r += RS_THREADS)
+          pair_row_update<NC>(reinterpret_cast<const double*>(LU), ld, r, b0, bs, Xp,
+                              reinterpret_cast<double*>(X));
+      }
+      __syncthreads();
+      continue;
+    }
     for (int r = b0 + bs + tid; r < n; r += RS_THREADS) {
       T acc[NC];
 #pragma unroll
@@ -1526,13 +1594,17 @@ __global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>
           if (lane < bs) X[(size_t)(b0 + lane) * NC + c] = x;
         }
       } else {
+        // each lane the reciprocal of its own diagonal entry, once per block: one FP64
+        // division per warp instead of one per substitution step
+        T rinv = (T)0;
+        if (lane < bs) {
+          const T dk = LU[(size_t)(b0 + lane) + (size_t)(b0 + lane) * ld];
+          rinv = (UPPER_ONLY && dk == (T)0) ? (T)0 : (T)1 / dk;
+        }
         for (int c = warp; c < nc; c += RS_THREADS / 32) {
           T x = lane < bs ? X[(size_t)(b0 + lane) * NC + c] : (T)0;
           for (int k = bs - 1; k >= 0; --k) {
-            if (lane == k) {
-              const T dk = LU[(size_t)(b0 + k) + (size_t)(b0 + k) * ld];
-              x = (UPPER_ONLY && dk == (T)0) ? (T)0 : x / dk;
-            }
+            if (lane == k) x *= rinv;
             const T xk = __shfl_sync(0xffffffffu, x, k);
             if (lane < k) x -= LU[(size_t)(b0 + lane) + (size_t)(b0 + k) * ld] * xk;
           }
@@ -1541,6 +1613,17 @@ __global__ void __launch_bounds__(RS_THREADS) getrs_kernel(const LuSolveDescT<T>
       }
     }
     __syncthreads();
+    if constexpr (PAIR) {
+      if (b0 > 0) {
+        split_rows<NC>(reinterpret_cast<const double*>(X), b0, bs, Xp, tid);
+        __syncthreads();
+        for (int r = tid; r < b0; r += RS_THREADS)
+          pair_row_update<NC>(reinterpret_cast<const double*>(LU), ld, r, b0, bs, Xp,
+                              reinterpret_cast<double*>(X));
+      }
+      __syncthreads();
+      continue;
+    }
     for (int r = tid; r < b0; r += RS_THREADS) {
       T acc[NC];
 #pragma unroll
@@ -1909,31 +1992,31 @@ unsigned grid_for(int64_t work, int threads, unsigned cap = 65535u) {
   return (unsigned)std::min<int64_t>(b, cap);
 }
 
-template <typename T, int NC, bool UPPER_ONLY>
+template <typename T, int NC, bool UPPER_ONLY, bool PAIR>
 void launch_getrs(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int max_cols,
                   cudaStream_t st) {
-  const size_t smem = (size_t)max_n * NC * sizeof(T);
+  const size_t smem = (size_t)max_n * NC * sizeof(T) + (PAIR ? 32 * NC * sizeof(float2) : 0);
   if (smem > 220 * 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "LU block too large");
   if (smem > 48 * 1024)
-    IA_CUDA(cudaFuncSetAttribute(getrs_kernel<T, NC, UPPER_ONLY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
+    IA_CUDA(cudaFuncSetAttribute(getrs_kernel<T, NC, UPPER_ONLY, PAIR>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (ndesc > 65535) throw Error(IASKIT_ERR_UNSUPPORTED, "more than 65535 LU solves in one launch");
   dim3 grid(ceil_div(max_cols, NC), ndesc);
-  getrs_kernel<T, NC, UPPER_ONLY><<<grid, RS_THREADS, smem, st>>>(descs_dev);
+  getrs_kernel<T, NC, UPPER_ONLY, PAIR><<<grid, RS_THREADS, smem, st>>>(descs_dev);
   IA_LAUNCH_CHECK();
 }
 
-template <typename T, bool UPPER_ONLY>
+template <typename T, bool UPPER_ONLY, bool PAIR = false>
 void solve_dispatch(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int max_cols, cudaStream_t st) {
   // chunk width: 16 columns while the chunk stays small enough for 3 blocks per SM
   if (max_cols >= 16 && (size_t)max_n * 16 * sizeof(T) <= 72 * 1024)
-    launch_getrs<T, 16, UPPER_ONLY>(descs_dev, ndesc, max_n, max_cols, st);
+    launch_getrs<T, 16, UPPER_ONLY, PAIR>(descs_dev, ndesc, max_n, max_cols, st);
   else if (max_cols >= 8 && (size_t)max_n * 8 * sizeof(T) <= 144 * 1024)
-    launch_getrs<T, 8, UPPER_ONLY>(descs_dev, ndesc, max_n, max_cols, st);
+    launch_getrs<T, 8, UPPER_ONLY, PAIR>(descs_dev, ndesc, max_n, max_cols, st);
   else if (max_cols >= 4)
-    launch_getrs<T, 4, UPPER_ONLY>(descs_dev, ndesc, max_n, max_cols, st);
+    launch_getrs<T, 4, UPPER_ONLY, PAIR>(descs_dev, ndesc, max_n, max_cols, st);
   else
-    launch_getrs<T, 1, UPPER_ONLY>(descs_dev, ndesc, max_n, max_cols, st);
+    launch_getrs<T, 1, UPPER_ONLY, PAIR>(descs_dev, ndesc, max_n, max_cols, st);
 }
 
 }  // namespace
@@ -2060,9 +2143,15 @@ void getrf_batched(const LuDescT<T>* descs_dev, int ndesc, int max_n, int* dev_s
 
 template <typename T>
 void getrs_batched(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int max_cols,
-                   cudaStream_t st, bool inv) {
+                   cudaStream_t st, bool inv, bool pair) {
   if (ndesc <= 0 || max_cols <= 0) return;
   ProfScope _ps(pk_of<T>(PK_GETRS), st);
+  if constexpr (std::is_same<T, double>::value) {
+    if (pair) {
+      solve_dispatch<double, false, true>(descs_dev, ndesc, max_n, max_cols, st);
+      return;
+    }
+  }
   if (std::is_same<T, float>::value && inv) {
     const size_t smem = (size_t)max_n * RI_NC * sizeof(float);
     if (smem > 200 * 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "LU block too large");
@@ -2147,22 +2236,6 @@ void split_pairs(const double* in, float2* out, int64_t n, cudaStream_t st) {
   ProfScope _ps(PK_MISC, st);
   split_pairs_kernel<<<grid_for(n, 256, 8192), 256, 0, st>>>(in, out, n);
   IA_LAUNCH_CHECK();
-}
-
-// (s, c) += (ah + al)(bh + bl): the product ah bh exactly as p + e (FMA), the cross
-// terms and e into the low part, p into the high part by Knuth's two-sum (its rounding
-// error into the low part as well).  The explicitly rounded operations keep the
-// compiler from contracting the two-sum into FMAs.
-__device__ __forceinline__ void pair_mac(float ah, float al, float bh, float bl, float& s, float& c) {
-  const float p = __fmul_rn(ah, bh);
-  float e = fmaf(ah, bh, -p);
-  e = fmaf(ah, bl, e);
-  e = fmaf(al, bh, e);
-  const float t = __fadd_rn(s, p);
-  const float z = __fsub_rn(t, s);
-  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
-  c = __fadd_rn(c, __fadd_rn(err, e));
-  s = t;
 }
 
 constexpr int GP_K = 16;
@@ -2342,7 +2415,7 @@ void check_finite(const double* x, int64_t n, int* dev_status, cudaStream_t st) 
   template void cpqr_id<T>(const CpqrDescT<T>*, int, int, int, int, double, cudaStream_t, bool);  \
   template void assemble_P<T>(const PDescT<T>*, int, int, cudaStream_t);                          \
   template void getrf_batched<T>(const LuDescT<T>*, int, int, int*, cudaStream_t, bool);          \
-  template void getrs_batched<T>(const LuSolveDescT<T>*, int, int, int, cudaStream_t, bool);      \
+  template void getrs_batched<T>(const LuSolveDescT<T>*, int, int, int, cudaStream_t, bool, bool);      \
   template void trsm_upper_batched<T>(const LuSolveDescT<T>*, int, int, int, cudaStream_t);       \
   template void gemm_grouped<T>(const GemmDescT<T>*, const GemmTile*, int, GemmShape,             \
                                 cudaStream_t, int*);                                             \

@@ -190,9 +190,11 @@ struct LuSolveDescT {
 };
 // inv: every descriptor carries its dinv area (FP32 only): the solve multiplies by the
 // diagonal blocks' inverses instead of substituting through them.
+// pair (FP64 only): the updates outside the 32 x 32 diagonal blocks run on FP32 pairs
+// (about 2^-44 relative per 32-term sum); the diagonal substitutions stay in FP64.
 template <typename T>
 void getrs_batched(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int max_cols,
-                   cudaStream_t st, bool inv = false);
+                   cudaStream_t st, bool inv = false, bool pair = false);
 // B <- U^{-1} B with U the upper triangle of the n x n block at LU (ipiv unused): the
 // ID's T = R11^{-1} R12 after cpqr_id.  A zero diagonal entry gives a zero row.
 template <typename T>

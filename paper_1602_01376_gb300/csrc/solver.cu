@@ -410,8 +410,9 @@ class Solver {
     if (v & DEV_OVERFLOW) throw Error(IASKIT_ERR_UNSUPPORTED, "internal bound exceeded");
   }
   // FP64 products of the mixed form's factorization and preconditioner (problems
-  // factored in FP64) run on FP32 pairs (about 2^-44 relative, on the FP32 pipes);
-  // the operator apply keeps FP64 products for the problems whose operator is in FP64.
+  // factored in FP64), and the updates of their LU solves outside the diagonal blocks,
+  // run on FP32 pairs (about 2^-44 relative, on the FP32 pipes); the operator apply
+  // keeps FP64 products for the problems whose operator is in FP64.
   bool in_apply = false;
   template <typename T>
   bool pair_products() const {
@@ -563,7 +564,7 @@ class Solver {
       char* base = upload_arena();
       prof().flops[pk_of<T>(PK_GETRS)] += getrs_flops(ds);
       getrs_batched((const LuSolveDescT<T>*)(base + o), (int)ds.size(), m_max, max_nc, st,
-                    std::is_same<T, float>::value);
+                    std::is_same<T, float>::value, pair_products<T>());
       run_gemms(g);
     }
     // 2. heights 1 .. top
@@ -612,7 +613,7 @@ class Solver {
       prof().flops[pair_products<T>() ? PK_GEMM_PAIR : pk_of<T>(PK_GEMM)] += gemm_flops(g1) + gemm_flops(g2);
       copy_batched((const CopyDescT<T>*)(base + ocp), (int)cp.size(), max_cp, st);
       getrs_batched((const LuSolveDescT<T>*)(base + ozs), (int)zs.size(), max_n2, max_nc, st,
-                    std::is_same<T, float>::value);
+                    std::is_same<T, float>::value, pair_products<T>());
       launch_gemms((const GemmDescT<T>*)(base + og1), (const GemmTile*)(base + ot1), (int)t1.size(), sh1);
       launch_gemms((const GemmDescT<T>*)(base + og2), (const GemmTile*)(base + ot2), (int)t2.size(), sh2);
     }
