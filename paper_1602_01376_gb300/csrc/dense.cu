@@ -1825,6 +1825,10 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(const GemmDescT<T>* des
   const GemmDescT<T> D = descs[Tl.desc];
   const int m0 = Tl.tm * TM, n0 = Tl.tn * TN;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  // the FP32 64 x 64 tiles (only used without the tensor-core GEMM) keep the plain loop:
+  // the test below costs them a register spill
+  constexpr bool SKIP = sizeof(T) == 8 || TN == 16;
+  const bool live = !SKIP || (m0 + 4 * tx < D.M && n0 + 4 * ty < D.N);
   T acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -1848,15 +1852,19 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(const GemmDescT<T>* des
       }
     }
     __syncthreads();
+    // a thread whose 4 x 4 outputs all lie outside C (a tile wider or taller than the
+    // problem: 4 right-hand sides in a 16-column tile) skips the arithmetic
+    if (live) {
 #pragma unroll
-    for (int kk = 0; kk < GK; ++kk) {
-      T a[4], b[4];  // rows 4 tx .. 4 tx + 3 and columns 4 ty .. 4 ty + 3: 16-byte loads
-      load_row<T, 4>(&As[kk][0], tx, a);
-      load_row<T, 4>(&Bs[kk][0], ty, b);
+      for (int kk = 0; kk < GK; ++kk) {
+        T a[4], b[4];  // rows 4 tx .. 4 tx + 3 and columns 4 ty .. 4 ty + 3: 16-byte loads
+        load_row<T, 4>(&As[kk][0], tx, a);
+        load_row<T, 4>(&Bs[kk][0], ty, b);
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+          for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+      }
     }
     __syncthreads();
   }
@@ -2255,6 +2263,7 @@ __global__ void __launch_bounds__(G_THREADS) gemm_pair_kernel(const DescT* descs
   const DescT D = descs[Tl.desc];
   const int m0 = Tl.tm * TM, n0 = Tl.tn * TN;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const bool live = m0 + 4 * tx < D.M && n0 + 4 * ty < D.N;  // some output inside C
   float s[4][4], c[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -2283,7 +2292,7 @@ __global__ void __launch_bounds__(G_THREADS) gemm_pair_kernel(const DescT* descs
     }
     __syncthreads();
 #pragma unroll 4
-    for (int kk = 0; kk < GP_K; ++kk) {
+    for (int kk = 0; kk < (live ? GP_K : 0); ++kk) {  // threads with no output inside C skip
       const float4 ah = *reinterpret_cast<const float4*>(&Ash[kk][4 * tx]);
       const float4 al = *reinterpret_cast<const float4*>(&Asl[kk][4 * tx]);
       const float4 bh = *reinterpret_cast<const float4*>(&Bsh[kk][4 * ty]);
