@@ -93,6 +93,25 @@ int iaskit_factor_batched_device(int nprob, const double* d_points, const int64_
 int iaskit_num_problems(void);
 
 /*
+ * Refactor for new regularizations (Sec. II-C: the skeletons and P do not depend on
+ * lambda, so a new lambda recomputes only the leaf LUs, W and Z).  Keeps the tree, the
+ * kNN lists, the samples, the skeletons and the P matrices of the current
+ * factorization (single or batched) and forms lambda[q] I + K~ for each problem q
+ * again: the leaf blocks and their LU, the U blocks, W and the reduced systems Z.  The
+ * form ("precision") of the kept factorization is kept; the mixed form re-chooses each
+ * problem's FP32/FP64 factorization and operator precision from its condition estimate
+ * 1 + r_q / lambda[q] (r_q: the largest sampled kernel row sum).  The result is the
+ * factorization iaskit_factor(_batched) would give for the same points and the new
+ * lambdas.
+ *   lambda   HOST pointer, nprob values >= 0, one per problem in batch order.
+ *   nprob    must equal iaskit_num_problems().
+ * Errors: IASKIT_ERR_NOT_FACTORED; _ARG (null pointer, wrong count, a negative or
+ * non-finite value: the current factorization stays usable); _SINGULAR, _NOMEM,
+ * _CUDA (the factorization is released).
+ */
+int iaskit_refactor(const double* lambda, int nprob);
+
+/*
  * Solve (lambda*I + K~) w = u in place (Sec. II-C, Alg. "Solve").
  *   rhs      HOST pointer, N x nrhs column-major, original point order; on return
  *            it holds w.  nrhs >= 1.
@@ -125,8 +144,8 @@ int iaskit_solve_batched(double* const* rhs, int nrhs);
 int iaskit_solve_batched_device(double* d_rhs, int nrhs);
 
 /*
- * u = (lambda*I + K~) w by the FP64 hierarchical MatVec (Sec. II-B, "Skeletonize"
- * lines that depend on w, then "Evaluate" with the separation i not in alpha).
+ * u = (lambda*I + K~) w by the FP64 hierarchical MatVec (Sec. II-B: the steps of
+ * "Skeletonize" that depend on w, then "Evaluate" with the separation i not in alpha).
  *   w, u     HOST pointers, N x nrhs column-major, original point order; u is
  *            overwritten.  The pointers may not alias.
  * Errors: IASKIT_ERR_NOT_FACTORED, _ARG, _NOMEM, _CUDA.

@@ -40,7 +40,7 @@ EXPORTS = [
     "iaskit_factor_batched_device", "iaskit_num_problems", "iaskit_solve_batched",
     "iaskit_solve_batched_device", "iaskit_sampler_train", "iaskit_sampler_set_weights",
     "iaskit_sampler_get_weights", "iaskit_mlp_forward", "iaskit_mlp_train_step", "iaskit_get_learned",
-    "iaskit_kernel_block",
+    "iaskit_kernel_block", "iaskit_refactor",
 ]
 
 MLP_NPARAM = 17793
@@ -92,6 +92,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "iaskit_factor_batched": ([i32, vp, vp, i32, vp, vp, i32, i32, dbl], i32),
         "iaskit_factor_batched_device": ([i32, vp, vp, i32, vp, vp, i32, i32, dbl], i32),
         "iaskit_num_problems": ([], i32),
+        "iaskit_refactor": ([vp, i32], i32),
         "iaskit_solve_batched": ([vp, i32], i32),
         "iaskit_solve_batched_device": ([vp, i32], i32),
         "iaskit_sampler_train": ([vp, i64, i32, dbl, i32, i32, dbl, i32, dbl], i32),
@@ -173,6 +174,15 @@ def iaskit_factor_batched_device(points, Ns, h_list, lam_list, leaf_m: int, s_ma
 
 def iaskit_num_problems() -> int:
     return _check(load().iaskit_num_problems())
+
+
+def iaskit_refactor(lam) -> None:
+    """Refactor the current factorization for new lambda values (a scalar for a single
+    problem, else one value per problem in batch order); tree, kNN lists, skeletons and
+    P are kept."""
+    lib = load()
+    ls = np.ascontiguousarray(np.atleast_1d(np.asarray(lam, dtype=np.float64)))
+    _check(lib.iaskit_refactor(ls.ctypes.data, len(ls)))
 
 
 def iaskit_solve_batched(rhs_list) -> list:

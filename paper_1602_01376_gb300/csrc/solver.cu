@@ -792,6 +792,40 @@ class Solver {
     factored = true;
   }
 
+  // Factorization of lambda' I + K~ for new regularizations lambda' (Sec. II-C: the
+  // skeletons and the P matrices do not depend on lambda, so a new lambda recomputes
+  // only the leaf LUs, W and the reduced systems Z).  The tree, the kNN lists, the
+  // samples, the skeletons and P are kept; the leaf blocks lambda' I + K_aa, the U
+  // blocks, W and Z are formed again, in the form (plain or mixed) of the kept
+  // factorization.  The mixed form re-chooses each problem's precisions, since the
+  // condition estimate 1 + r / lambda' changes with lambda'.
+  void refactor(const double* lam, int nprob) {
+    if (!lam) throw Error(IASKIT_ERR_ARG, "lambda is null");
+    if (nprob != (int)pr.size()) throw Error(IASKIT_ERR_ARG, "one lambda per factored problem");
+    for (int q = 0; q < nprob; ++q)
+      if (!(lam[q] >= 0.0) || !std::isfinite(lam[q])) throw Error(IASKIT_ERR_ARG, "lambda must be >= 0");
+    factored = false;
+    const double t0 = now_ms();
+    for (int q = 0; q < nprob; ++q) pr[q].lam = lam[q];
+    stats.t_tree = stats.t_knn = stats.t_skel = 0.0;
+    stats.t_solve = stats.t_apply = 0.0;
+    stats.bytes_operator = 0;
+    stats.refine_hist.clear();
+    stats.refine_sweeps = stats.refine_iters = stats.refine_stagnated = 0;
+    choose_precisions();
+    const double t1 = now_ms();
+    leaf_lu();
+    raise_status(read_status_and_clear());
+    const double t2 = now_ms();
+    stats.t_leaf_lu = t2 - t1;
+    factor_levels();
+    raise_status(read_status_and_clear());
+    stats.t_factor_levels = now_ms() - t2;
+    stats.t_factor = now_ms() - t0;
+    prof().resolve();
+    factored = true;
+  }
+
   // Per problem: cond_est = 1 + r / lambda with r the largest of KROWSUM_ROWS sampled kernel
   // row sums (an estimate of ||K||_2 and of the largest eigenvalue of lambda I + K, whose
   // smallest is about lambda).  The plain form factors every problem in FP64; the mixed
@@ -2324,6 +2358,16 @@ int iaskit_num_problems(void) {
   return (int)S().pr.size();
 }
 
+int iaskit_refactor(const double* lambda, int nprob) {
+  int rc = guarded([&] {
+    require_factored();
+    S().refactor(lambda, nprob);
+  });
+  // a failure past the argument checks leaves no usable factorization
+  if (rc != IASKIT_OK && rc != IASKIT_ERR_ARG && rc != IASKIT_ERR_NOT_FACTORED) S().factored = false;
+  return rc;
+}
+
 int iaskit_solve_device(double* d_rhs, int nrhs) {
   return guarded([&] {
     if (!d_rhs) throw Error(IASKIT_ERR_ARG, "rhs is null");
@@ -2519,7 +2563,7 @@ int iaskit_stats(char* buf, size_t len) {
   j += "],";
   j += "\"cond_est\":[";
   for (size_t q = 0; q < s.pr.size() && s.factored; ++q) {
-    snprintf(tmp, sizeof tmp, "%s%.4g", q ? "," : "", std::min(s.pr[q].cond_est, 1e300));
+    snprintf(tmp, sizeof tmp, "%s%.17g", q ? "," : "", std::min(s.pr[q].cond_est, 1e300));
     j += tmp;
   }
   j += "],\"launches\":";
