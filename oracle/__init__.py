@@ -17,6 +17,9 @@ What is computed (Yu, March, Xiao, Biros, "INV-ASKIT", arXiv 1602.01376):
 * ``askit``    skeletonization, nested projections P (eq. innerid), the dense
                definition of K~ (eqs. offdiag-askit, uv-askit) and the hierarchical
                MatVec (Skeletonize/Evaluate with the i-not-in-alpha criterion).
+* ``nearfield`` the kNN-separated operator lambda I + K~ + S of eq. (askit): the
+               Evaluate step with exact evaluation of the nodes holding a target's
+               nearest neighbours, and the same matrix entry by entry.
 * ``invaskit`` Alg. "Factorize" and Alg. "Solve" written literally with full P
                matrices (Sec. II-C, eqs. smw, hodlr, blocksmw), the dense reference
                solve, and the error metrics of eq. (error), Sec. III.
