@@ -193,6 +193,16 @@ int iaskit_apply_device(const double* d_w, double* d_u, int nrhs);
  *   "cpqr_cluster" 1: FP32 IDs of blocks up to 512 x 512 run on a cluster of up to 8
  *                  thread blocks per node, the columns held in registers (default);
  *                  0: one thread block per node.  Same arithmetic either way.
+ *   "near_field"   1: the operator is the kNN-separated lambda I + K~ + S of eq. (askit)
+ *                  (Sec. II-B): for each target i, a node that the Evaluate step reaches
+ *                  for i (the sibling of an ancestor of i's leaf) and that holds one of
+ *                  i's kappa nearest neighbours is evaluated exactly, K_{i a} w_a,
+ *                  instead of through its skeletons.  iaskit_apply applies it and the
+ *                  refinement's GMRES solves with it, preconditioned by the stored
+ *                  factorization of lambda I + K~ (the paper's use of INV-ASKIT for
+ *                  K~ + S); set "refine" > 0 for the plain form, whose direct solve
+ *                  alone inverts lambda I + K~ only.  0: lambda I + K~ (default)
+ *                  [any time after a factorization]
  *   "problem"      which problem of a batch the introspection calls report (0) [any time]
  * Errors: IASKIT_ERR_ARG for an unknown key or an invalid value.
  */

@@ -302,6 +302,26 @@ struct KMatvecDesc {
 void kernel_matvec(const double* Xp, const double* xnorm, int d, int nrhs, const KMatvecDesc* descs_dev,
                    int ndesc, int max_rows, cudaStream_t st);
 
+// Near-field correction of the kNN-separated operator (eq. askit, Sec. II-B).  For
+// every target position p and every node alpha of p's interaction list (the sibling of
+// each ancestor of p's leaf) that holds at least one of p's kappa nearest neighbours,
+//   u_p += K(x_p, X_alpha) w_alpha - K(x_p, X_skel(alpha)) w~_alpha,
+// i.e. the skeleton evaluation of alpha is replaced by the exact one (FP64, difference
+// form of the squared distance).  W and U hold the problems' N x nrhs column-major
+// blocks one after the other (problem q's at pbase * nrhs, ld N); w~_alpha lies at
+// WT + nodes[gid].wt_off with leading dimension nodes[gid].ld.
+struct NearProb {
+  int pbase, N, L, nbase;
+  double scale;  // -1 / (2 h^2)
+};
+struct NearNode {
+  int64_t wt_off;  // w~ of the node inside WT (column 0, row 0)
+  int ld, s;       // its leading dimension and the node's rank
+};
+void near_field(const double* Xp, int d, const int* knn_pos, int kappa, const int* pid, const NearProb* probs,
+                const NearNode* nodes, const int* skel, int s_max, const double* W, const double* WT, double* U,
+                int nrhs, int Ntot, cudaStream_t st);
+
 // Conditioning probe: out[q * KROWSUM_ROWS + r] = sum_j K(x_i, x_j) over the N points of
 // problem q (evaluated in FP32), for KROWSUM_ROWS rows i spread evenly over the
 // problem's tree order.  The

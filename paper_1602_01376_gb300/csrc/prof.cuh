@@ -33,6 +33,7 @@ enum ProfKind {
   PK_JUDGE,      // held-out ID error of the learned and plain samples
   PK_GEMM_PAIR,  // FP64-accurate products on FP32 pairs (operator of the mixed form)
   PK_KBLOCK_PAIR,  // kernel blocks evaluated on FP32 pairs (operator of the mixed form)
+  PK_NEAR,         // near-field correction S of the kNN-separated operator
   PK_COUNT
 };
 

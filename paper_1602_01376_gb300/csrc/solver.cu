@@ -94,6 +94,10 @@ struct Options {
   // problem whose refinement stops at the FP32-pair operator's rounding floor is
   // upgraded to FP64 and refined again
   double pair_cond_max = 1e6;
+  // operator: 0 = lambda I + K~ (i not in alpha), 1 = lambda I + K~ + S, the kNN-separated
+  // operator of eq. (askit); the factorization (of lambda I + K~) then preconditions the
+  // refinement's GMRES
+  int near_field = 0;
 };
 
 struct Prob {
@@ -2234,6 +2238,24 @@ class Solver {
         }
       }
     }
+    // kNN-separated operator: nodes of a target's list that hold one of its nearest
+    // neighbours are evaluated exactly instead of through their skeletons (eq. askit)
+    if (opt.near_field && Hmax > 0 && kappa > 0) {
+      std::vector<NearProb> np(pr.size());
+      for (size_t q = 0; q < pr.size(); ++q)
+        np[q] = NearProb{pr[q].pbase, pr[q].N, pr[q].L, pr[q].nbase, pr[q].scale};
+      std::vector<NearNode> nn(nd.size(), NearNode{0, 1, 0});
+      for (size_t g = 0; g < nd.size(); ++g) {
+        if (nd[g].prob < 0 || nd[g].uid < 2) continue;
+        const int par = parent((int)g);
+        nn[g] = NearNode{woff[par] + rowoff((int)g), n2(par), nd[g].s};
+      }
+      arena.clear();
+      size_t op = arena.push(np), on = arena.push(nn);
+      char* base = upload_arena();
+      near_field(Xp.as<double>(), d, knn_pos.as<int>(), kappa, pid.as<int>(), (const NearProb*)(base + op),
+                 (const NearNode*)(base + on), sk, s_max, Wp, WT, Up, nrhs, Ntot, st);
+    }
     gather(Up, u, nrhs, blocks, true);
     IA_CUDA(cudaStreamSynchronize(st));
     prof().resolve();
@@ -2481,6 +2503,8 @@ int iaskit_set_option(const char* key, double value) {
     } else if (k == "pair_cond_max") {
       if (!(value >= 1.0)) throw Error(IASKIT_ERR_ARG, "invalid pair_cond_max");
       o.pair_cond_max = value;
+    } else if (k == "near_field") {
+      o.near_field = as_int(0, 1);
     } else if (k == "profile") {
       int v = as_int(0, 1);
       IA_CUDA(cudaStreamSynchronize(S().st));
@@ -2513,6 +2537,7 @@ int iaskit_get_option(const char* key, double* value) {
     else if (k == "gemm_tc") *value = o.gemm_tc;
     else if (k == "cpqr_cluster") *value = o.cpqr_cluster;
     else if (k == "pair_cond_max") *value = o.pair_cond_max;
+    else if (k == "near_field") *value = o.near_field;
     else throw Error(IASKIT_ERR_ARG, "unknown option " + k);
   });
 }
