@@ -106,6 +106,39 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------ ranks (torchrun, N > 1)
+def dist_init(backend: str):
+    """The process group of a torchrun launch (RANK, WORLD_SIZE, MASTER_ADDR/PORT from the
+    environment); None for a single process."""
+    if int(os.environ.get("WORLD_SIZE", "1")) <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group(backend)
+    return dist
+
+
+def max_over_ranks(dist, x: float, device) -> float:
+    """The largest x over the ranks (x itself for a single process)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist) -> None:
+    if dist is not None:
+        dist.barrier()
+
+
+def batch_seed(rank: int) -> int:
+    """Seed of rank's batch of independent problems: every rank factors a batch of its
+    own (weak scaling, no data-path exchange); rank 0's is the single-GPU batch."""
+    import inspect
+    return inspect.signature(batched_problems).parameters["seed"].default + 1000 * rank
+
+
 # ----------------------------------------------------------------- CPU oracle leg
 def oracle_step(w, N_sample: int, nrhs: int) -> float:
     """One factor + solve of the oracle on a sample of the workload; returns seconds."""
@@ -208,12 +241,19 @@ def alu_peak_tflops(kernel: str, sm_mhz: float) -> tuple:
 
 
 def run_batched(args, w, form):
-    """C3: all problems in one batched factor + solve per step vs one call per problem."""
+    """C3: all problems in one batched factor + solve per step vs one call per problem.
+    Under torchrun every rank factors a batch of 64 problems of its own (weak scaling, no
+    data-path exchange); the time is the largest over the ranks."""
     import torch
     import paper_1602_01376_gb300 as ia
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = dist_init("nccl")
     ia.load()
     ia.iaskit_set_stream(None)
-    probs = batched_problems(count=64)
+    probs = batched_problems(count=64, seed=batch_seed(rank))
     Ns = [len(p[0]) for p in probs]
     hs = [p[1] for p in probs]
     lams = [p[2] for p in probs]
@@ -245,21 +285,24 @@ def run_batched(args, w, form):
         ia.iaskit_set_option("profile", 1)
         l0 = ia.iaskit_stats()["launches"]
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(dist)
         torch.cuda.synchronize()
-        with ClockSampler(0 if sample_clocks else -1) as clk:
+        with ClockSampler(local if sample_clocks else -1) as clk:
             ev0.record()
             for _ in range(args.steps):
                 fn()
             ev1.record()
             torch.cuda.synchronize()
+        barrier(dist)
         st = ia.iaskit_stats()
         ia.iaskit_set_option("profile", 0)
-        return ev0.elapsed_time(ev1), st, clk.summary(), st["launches"] - l0
+        ms = max_over_ranks(dist, ev0.elapsed_time(ev1), "cuda")
+        return ms, st, clk.summary(), st["launches"] - l0
 
     ms_b, st_b, clocks, launches = timed(step_batched, True)
     ms_s, st_s, _, launches_s = timed(step_single, False)
     nrhs_total = sum(w.nrhs for _ in Ns)
-    value = nrhs_total * args.steps / (ms_b / 1e3)
+    value = world * nrhs_total * args.steps / (ms_b / 1e3)
     # residual of the batched solution against the FP64 operator
     step_batched()
     AU = torch.empty_like(U)
@@ -274,11 +317,15 @@ def run_batched(args, w, form):
     # end to end: host points and right-hand sides through iaskit_factor_batched / solve_batched
     Xh = [np.ascontiguousarray(p[0]) for p in probs]
     Uh = [np.ascontiguousarray(U0[offs[q]:offs[q + 1]].cpu().numpy().reshape(w.nrhs, Ns[q]).T) for q in range(len(Ns))]
+    barrier(dist)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ia.iaskit_factor_batched(Xh, hs, lams, w.m, w.s_max, w.tol)
     ia.iaskit_solve_batched(Uh)
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0, "cuda")
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
     kern = st_b["kernels"]
     top = max(kern, key=lambda k: kern[k]["ms"])
     pk, src = peaks()
@@ -292,8 +339,10 @@ def run_batched(args, w, form):
                 "ms_total": kern[top]["ms"]}
     cfg = config_of(w)
     cfg["path"] = "batched " + form
+    if world > 1:
+        cfg["ranks"] = f"{world} ranks, each its own batch of 64 problems (seed + 1000 rank)"
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if form == "mixed" else "f64",
         "data": "synthetic", "config": cfg, "residual": resid,
@@ -304,13 +353,15 @@ def run_batched(args, w, form):
         "operator_upgrades": st_last.get("operator_upgrades"), "gpu_launches": launches,
         "clocks": clocks, "roofline": roof,
         "kernel_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in kern.items() if v["ms"] > 0},
-        "compare_per_problem": {"value": nrhs_total * args.steps / (ms_s / 1e3),
+        "compare_per_problem": {"value": world * nrhs_total * args.steps / (ms_s / 1e3),
                                 "ms_per_step": ms_s / args.steps, "gpu_launches": launches_s},
-        "e2e": {"value": nrhs_total / e2e_s, "unit": UNIT,
+        "e2e": {"value": world * nrhs_total / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * sum(Ns) * (16 + w.nrhs),
                 "d2h_bytes_per_step": 8 * sum(Ns) * w.nrhs},
     }
     print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
     return 0
 
 
@@ -340,21 +391,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    dist = dist_init("nccl")
 
     ia.load()
     ia.iaskit_set_stream(None)                     # legacy default stream = torch's default
@@ -386,7 +423,7 @@ def main():
         ia.iaskit_set_option("profile", 1)
         launches0 = ia.iaskit_stats()["launches"]
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
+        barrier(dist)
         torch.cuda.synchronize()
         with ClockSampler(local if sample_clocks else -1) as clk:
             ev0.record()
@@ -394,8 +431,8 @@ def main():
                 step()
             ev1.record()
             torch.cuda.synchronize()
-        barrier()
-        ms = max_over_ranks(ev0.elapsed_time(ev1))
+        barrier(dist)
+        ms = max_over_ranks(dist, ev0.elapsed_time(ev1), "cuda")
         stats = ia.iaskit_stats()
         ia.iaskit_set_option("profile", 0)
         return {"ms": ms, "stats": stats, "resid": resid, "clocks": clk.summary(),
@@ -433,7 +470,7 @@ def main():
     Xh_np, Uh_view = Xh.numpy(), Uh.numpy()
     lib = ia.load()
     e2e_steps = max(1, min(args.steps, 2))
-    barrier()
+    barrier(dist)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -445,7 +482,7 @@ def main():
             raise RuntimeError(ia.iaskit_last_error())
         Uh.copy_(U_src)                            # restore the right-hand sides
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0, "cuda")
     e2e_value = world * w.nrhs * e2e_steps / e2e_s
 
     if rank != 0:
