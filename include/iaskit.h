@@ -148,6 +148,9 @@ int iaskit_solve_batched_device(double* d_rhs, int nrhs);
  * "Skeletonize" that depend on w, then "Evaluate" with the separation i not in alpha).
  *   w, u     HOST pointers, N x nrhs column-major, original point order; u is
  *            overwritten.  The pointers may not alias.
+ * With option "near_field" = 1 the operator is lambda I + K~ + S (eq. askit): the nodes
+ * of a target's Evaluate list that hold one of its nearest neighbours are evaluated
+ * exactly instead of through their skeletons.
  * Errors: IASKIT_ERR_NOT_FACTORED, _ARG, _NOMEM, _CUDA.
  */
 int iaskit_apply(const double* w, double* u, int nrhs);

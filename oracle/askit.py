@@ -12,7 +12,7 @@ Part of the oracle (test infrastructure only).
 * ``dense_Ktilde``: the definition of K~ with the i-not-in-alpha separation
   (eqs. offdiag-askit, uv-askit): K~_aa = blockdiag(K~_ll, K~_rr) +
   [[0, K_{l r~} P_{r~ r}], [K_{r l~} P_{l~ l}, 0]], and K~_aa = K_aa at a leaf.
-* ``matvec``: the fast MatVec u = (lambda I + K~) w by Skeletonize (lines that
+* ``matvec``: the fast MatVec u = (lambda I + K~) w by Skeletonize (its steps that
   depend on w: w~ = P w up the tree) and Evaluate (u_i = K_{i a~} w~_a for every
   node a separated from i, exact leaf interactions otherwise).
 

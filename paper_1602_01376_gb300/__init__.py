@@ -226,7 +226,8 @@ def iaskit_solve_device(rhs) -> None:
 
 
 def iaskit_apply(w) -> np.ndarray:
-    """u = (lambda I + K~) w by the FP64 hierarchical MatVec (host arrays)."""
+    """u = (lambda I + K~) w by the FP64 hierarchical MatVec (host arrays); with option
+    "near_field" = 1, u = (lambda I + K~ + S) w, the kNN-separated operator."""
     lib = load()
     x = np.asarray(w, dtype=np.float64)
     vec = x.ndim == 1
