@@ -316,3 +316,18 @@ def test_single_leaf_problem_is_dense_lu():
     w = oracle.solve(F, u)
     A = 0.1 * np.eye(30) + gaussian_kernel(X, X, 0.5)
     assert np.linalg.norm(A @ w - u) / np.linalg.norm(u) < 1e-12
+
+
+def test_new_lambda_reuses_skeletons(small_problem):
+    # Sec. II-C: skeletons and P do not depend on lambda; a factorization for a new
+    # lambda on the same skeletons inverts lambda' I + K~ (dense solve of that matrix)
+    X, tree, sk, F, u = small_problem
+    _, _, sk2, _ = oracle.build_all(X, 0.4, 3.0, 40, 12, 0.0, seed=3)
+    for node in sk.skel:
+        assert np.array_equal(sk.skel[node], sk2.skel[node])
+        np.testing.assert_array_equal(sk.P[node], sk2.P[node])
+    for lam2 in (1e-3, 2.0):
+        F2 = oracle.factorize(sk, lam2)
+        w = oracle.solve(F2, u)
+        w_den = oracle.dense_solve(sk, lam2, u)
+        assert np.linalg.norm(w - w_den) / np.linalg.norm(w_den) < 1e-10, lam2
