@@ -20,6 +20,8 @@ What is computed (Yu, March, Xiao, Biros, "INV-ASKIT", arXiv 1602.01376):
 * ``nearfield`` the kNN-separated operator lambda I + K~ + S of eq. (askit): the
                Evaluate step with exact evaluation of the nodes holding a target's
                nearest neighbours, and the same matrix entry by entry.
+* ``regression`` kernel regression for binary classification (Sec. III): weights
+               from (lambda I + K~ + S) w = u, test labels sign(K(x, X) w).
 * ``invaskit`` Alg. "Factorize" and Alg. "Solve" written literally with full P
                matrices (Sec. II-C, eqs. smw, hodlr, blocksmw), the dense reference
                solve, and the error metrics of eq. (error), Sec. III.

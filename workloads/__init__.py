@@ -13,6 +13,7 @@ from .generators import (  # noqa: F401
     workload,
     uniform_cube,
     gaussian_mixture,
+    labeled_gaussian_mixture,
     tanh_manifold,
     batched_problems,
 )

@@ -54,6 +54,24 @@ def gaussian_mixture(N: int, d: int, ncomp: int, std_lo: float, std_hi: float,
     return X[rng.permutation(N)]
 
 
+def labeled_gaussian_mixture(N: int, d: int, ncomp: int, std_lo: float, std_hi: float,
+                             rng: np.random.Generator):
+    """Points of an equal-weight axis-aligned Gaussian mixture (drawn as in
+    ``gaussian_mixture``) with binary labels: +1 for the first ncomp // 2 components,
+    -1 for the others (a one-versus-rest task of the shape of the paper's
+    classification sets).  Returns (X (N, d), labels (N,) in {-1, +1})."""
+    counts = rng.multinomial(N, np.full(ncomp, 1.0 / ncomp))
+    means = rng.random((ncomp, d))
+    stds = np.exp(rng.uniform(np.log(std_lo), np.log(std_hi), size=(ncomp, d)))
+    parts, labels = [], []
+    for c in range(ncomp):
+        parts.append(means[c] + stds[c] * rng.standard_normal((counts[c], d)))
+        labels.append(np.full(counts[c], 1.0 if c < ncomp // 2 else -1.0))
+    X, y = np.concatenate(parts, axis=0), np.concatenate(labels)
+    order = rng.permutation(N)
+    return np.ascontiguousarray(X[order]), y[order]
+
+
 def tanh_manifold(N: int, rng: np.random.Generator, d: int = 64, intrinsic: int = 6,
                   noise: float = 0.01) -> np.ndarray:
     """Points on a random two-layer tanh image of N(0, I_6) in R^64 plus noise.
