@@ -59,6 +59,17 @@ def test_error_paths_without_device_work(lib_path):
     with pytest.raises(ia.IaskitError) as e:
         ia.iaskit_depth()
     assert e.value.name == "IASKIT_ERR_NOT_FACTORED"
+    # refactoring needs a factorization; option checks need no device
+    with pytest.raises(ia.IaskitError) as e:
+        ia.iaskit_refactor(0.1)
+    assert e.value.name == "IASKIT_ERR_NOT_FACTORED"
+    for bad in (2, -1):
+        with pytest.raises(ia.IaskitError) as e:
+            ia.iaskit_set_option("near_field", bad)
+        assert e.value.name == "IASKIT_ERR_ARG"
+    ia.iaskit_set_option("near_field", 1)
+    assert ia.iaskit_get_option("near_field") == 1.0
+    ia.iaskit_set_option("near_field", 0)
 
 
 def test_kernels_are_compiled_for_sm103a_only():
