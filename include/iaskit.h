@@ -19,8 +19,9 @@
  *    points[i*d .. i*d + d - 1].  Right-hand sides and solutions are N x nrhs
  *    column-major in the ORIGINAL point order (the tree permutation is internal).
  *  - One implicit factorization is held by the library.  It is owned by the
- *    library until iaskit_free() or the next iaskit_factor*; the library never
- *    keeps a caller pointer after a call returns.
+ *    library until iaskit_free() or the next iaskit_factor* (iaskit_refactor
+ *    replaces its lambda-dependent part in place); the library never keeps a
+ *    caller pointer after a call returns.
  *  - Calls are synchronous: they return after the device work they enqueued has
  *    finished.  Work is enqueued on the stream set by iaskit_set_stream (default:
  *    the legacy default stream).
