@@ -143,8 +143,14 @@ def batch_seed(rank: int) -> int:
 def oracle_step(w, N_sample: int, nrhs: int) -> float:
     """One factor + solve of the oracle on a sample of the workload; returns seconds."""
     import oracle
-    ws = w.scaled(N_sample)
-    X = make_points(ws)
+    if w.kind == "batched":
+        # the batch's first problem (its h and lambda), its first N_sample points
+        X, h, lam = batched_problems(count=64)[0]
+        X = np.ascontiguousarray(X[:N_sample])
+        ws = w.scaled(len(X), h=h, lam=lam)
+    else:
+        ws = w.scaled(N_sample)
+        X = make_points(ws)
     u = make_rhs(ws, nrhs=nrhs)
     t0 = time.perf_counter()
     _, _, _, F = oracle.build_all(X, ws.h, ws.lam, ws.m, ws.s_max, ws.tol, kappa=ws.kappa,
@@ -181,6 +187,9 @@ def run_reference(args, w):
     value = nrhs * len(ts) / total
     sample = (f"oracle factor+solve of N={CPU_SAMPLE_N} points of the {w.name} generator with "
               f"the same h, lambda, m, s_max, tol and {nrhs} RHS per step")
+    if w.kind == "batched":
+        sample = (f"oracle factor+solve of the first {CPU_SAMPLE_N} points of the batch's first "
+                  f"problem (its h and lambda; m, s_max, tol of the batch) with {nrhs} RHS per step")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(ts),
@@ -359,6 +368,17 @@ def run_batched(args, w, form):
                 "h2d_bytes_per_step": 8 * sum(Ns) * (16 + w.nrhs),
                 "d2h_bytes_per_step": 8 * sum(Ns) * w.nrhs},
     }
+    if not args.no_cpu_baseline:
+        res = cpu_baseline_subprocess(w.name, CPU_SAMPLE_N, w.nrhs, 1)
+        if "times" in res:
+            t = res["times"][0]
+            line["cpu_baseline"] = {
+                "value": w.nrhs / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"one oracle factor+solve of the first {CPU_SAMPLE_N} points of the batch's "
+                          f"first problem, {w.nrhs} RHS ({t:.1f} s)"}
+        else:
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": "failed: " + res.get("error", "")[-200:]}
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
