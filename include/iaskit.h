@@ -343,9 +343,11 @@ int iaskit_get_learned(int level, int index, int32_t* cand, float* feat, float* 
  * Scratch: one static device array of about 37.3 MiB, which every GPU that loads
  * this library holds until the process exits.  The call makes no device
  * allocation.  Its first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) once; make that first call before any stream capture.
- * All calls share the array, so calls that overlap on the GPU (other streams or
- * threads) race; serialize them.
+ * (cudaGetSymbolAddress) once, under a lock, so host threads may make that first
+ * call concurrently.  The call copies from host memory, reads a count back and
+ * synchronizes the stream before it returns, so it cannot be recorded into a CUDA
+ * graph.  All calls share the array, so calls that overlap on the GPU (other
+ * streams or threads) race; serialize them.
  * Errors: IASKIT_ERR_ARG, _UNSUPPORTED, _CUDA.
  */
 int iaskit_knn_noalloc(const double* d_points, int64_t N, int d, int kappa, int32_t* d_knn,

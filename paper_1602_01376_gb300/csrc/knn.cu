@@ -20,8 +20,10 @@
 //      >= (D_KP - E(q, |b|^2 <= max_b |b|^2)) (1 - 1e-12);
 //   3. queries whose bound fails (near-ties at the cut) are redone by an exact FP64
 //      scan over all points.
+#include <atomic>
 #include <cfloat>
 #include <climits>
+#include <mutex>
 
 #include "kernels.cuh"
 #include "tc.cuh"
@@ -621,21 +623,29 @@ constexpr size_t NA_BYTES = NA_STATUS + 256;   // about 37.3 MiB
 __device__ __align__(256) unsigned char g_knn_noalloc_scratch[NA_BYTES];
 
 constexpr int NA_MAX_DEVICES = 64;
-void* g_knn_noalloc_base[NA_MAX_DEVICES] = {};
+// Cached device addresses, one per device ordinal.  Host threads making their first
+// call at the same time look the address up under one mutex, so the table is never
+// written concurrently; later calls read an atomic entry without the lock.
+std::atomic<void*> g_knn_noalloc_base[NA_MAX_DEVICES] = {};
+std::mutex g_knn_noalloc_mutex;
 
 // Device address of the scratch array on the current device (looked up once).
 unsigned char* noalloc_scratch() {
   int dev = 0;
   IA_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= NA_MAX_DEVICES) throw Error(IASKIT_ERR_UNSUPPORTED, "device ordinal >= 64");
-  if (!g_knn_noalloc_base[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_knn_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      throw Error(IASKIT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_knn_noalloc_base[dev] = p;
+  void* p = g_knn_noalloc_base[dev].load(std::memory_order_acquire);
+  if (!p) {
+    std::lock_guard<std::mutex> lock(g_knn_noalloc_mutex);
+    p = g_knn_noalloc_base[dev].load(std::memory_order_relaxed);
+    if (!p) {
+      cudaError_t e = cudaGetSymbolAddress(&p, g_knn_noalloc_scratch);
+      if (e != cudaSuccess || !p)
+        throw Error(IASKIT_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      g_knn_noalloc_base[dev].store(p, std::memory_order_release);
+    }
   }
-  return static_cast<unsigned char*>(g_knn_noalloc_base[dev]);
+  return static_cast<unsigned char*>(p);
 }
 
 void knn_noalloc(const double* X, int N, int d, int kappa, int* knn, cudaStream_t st) {

@@ -329,6 +329,7 @@ class Solver {
   Options opt;
   Stats stats;
   bool factored = false;
+  bool skeletonized = false;  // ranks of the current tree are known (set before factor_levels)
   int prec = PREC_FP64;  // precision of the current factorization
   int Ntot = 0, d = 0, s_max = 0, kappa = 0, m_max = 0, Hmax = 0, nleaves = 0;
   double tol = 0;
@@ -633,6 +634,7 @@ class Solver {
   void factor(const std::vector<ProbIn>& in, bool on_device, bool concatenated, int d_, int leaf_m,
               int s_max_, double tol_) {
     factored = false;
+    skeletonized = false;
     if (in.empty()) throw Error(IASKIT_ERR_ARG, "no problem");
     if (d_ < 1) throw Error(IASKIT_ERR_ARG, "d must be >= 1");
     if (leaf_m < 2) throw Error(IASKIT_ERR_ARG, "leaf_m must be >= 2");
@@ -783,6 +785,7 @@ class Solver {
       IA_CUDA(cudaStreamSynchronize(st));
       stats.t_skel = now_ms() - t2;
     }
+    skeletonized = true;
     const double t3 = now_ms();
     leaf_lu();
     raise_status(read_status_and_clear());
@@ -2264,6 +2267,7 @@ class Solver {
 
   void release() {
     factored = false;
+    skeletonized = false;
     DevBuf* all[] = {&X, &Xp, &perm, &iperm, &pid, &knn, &knn_pos, &samp, &ranks, &skel,
                      &piv_ws, &A_ws, &status, &arena_dev, &step_dev, &tbuf, &vbuf, &vbuf32,
                      &ubuf, &rbuf, &wt, &io, &normbuf, &blocks_dev, &LU, &LUpiv, &Wb, &Zb, &Zpiv,
@@ -2599,19 +2603,30 @@ int iaskit_stats(char* buf, size_t len) {
              prof_name(k), prof().ms[k], prof().calls[k], prof().flops[k]);
     j += tmp;
   }
+  // rank profile of the last skeletonization (also after a factorization that stopped
+  // later, e.g. at mem_cap_gb): mean and largest rank per height, and the entries of
+  // W (= of the U blocks) that profile implies, sum over non-root nodes of |c| s_sibling
+  std::string mx = "],\"max_rank_per_height\":[";
   j += "},\"mean_rank_per_height\":[";
-  for (int hh = 0; hh < s.Hmax && s.factored; ++hh) {
+  double w_entries = 0;
+  for (int hh = 0; hh < s.Hmax && s.skeletonized; ++hh) {
     double tot = 0;
-    int cnt = 0;
+    int cnt = 0, big = 0;
     for (int g : s.by_height[hh])
       if (!s.is_root(g)) {
         tot += s.nd[g].s;
+        big = std::max(big, s.nd[g].s);
+        w_entries += (double)s.nd[g].size * s.nd[s.sibling(g)].s;
         ++cnt;
       }
     snprintf(tmp, sizeof tmp, "%s%.3f", hh ? "," : "", cnt ? tot / cnt : 0.0);
     j += tmp;
+    snprintf(tmp, sizeof tmp, "%s%d", hh ? "," : "", big);
+    mx += tmp;
   }
-  j += "]}";
+  j += mx;
+  snprintf(tmp, sizeof tmp, "],\"w_entries\":%.17g}", w_entries);
+  j += tmp;
   if (buf && len > 0) {
     size_t n = std::min(len - 1, j.size());
     std::memcpy(buf, j.data(), n);

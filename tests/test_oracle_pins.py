@@ -331,3 +331,50 @@ def test_new_lambda_reuses_skeletons(small_problem):
         w = oracle.solve(F2, u)
         w_den = oracle.dense_solve(sk, lam2, u)
         assert np.linalg.norm(w - w_den) / np.linalg.norm(w_den) < 1e-10, lam2
+
+
+# ------------------------------------------------- sampled eps_M (eq. error, Sec. III)
+def _dense_K_original(X, h):
+    """Exact kernel matrix in ORIGINAL order from scipy's distances (not the oracle's)."""
+    from scipy.spatial.distance import cdist
+    return np.exp(-cdist(X, X, "sqeuclidean") / (2.0 * h * h))
+
+
+def _dense_Ktilde_original(sk):
+    """The dense K~ of the oracle (permuted order) brought back to ORIGINAL order."""
+    perm = sk.tree.perm
+    Kt = dense_Ktilde(sk)
+    out = np.empty_like(Kt)
+    out[np.ix_(perm, perm)] = Kt
+    return out
+
+
+def test_eps_M_sampled_on_all_rows_is_the_dense_definition(small_problem):
+    # eq. error with S = 0: eps_M = ||K w - K~ w|| / ||K w||, K~ without lambda, both
+    # in original order.  Pinned against K from scipy's cdist and the dense K~.
+    X, tree, sk, F, u = small_problem
+    w = np.random.default_rng(21).standard_normal(X.shape[0])
+    K = _dense_K_original(X, sk.h)
+    Kt = _dense_Ktilde_original(sk)
+    want = np.linalg.norm(K @ w - Kt @ w) / np.linalg.norm(K @ w)
+    got = oracle.eps_M_sampled(sk, X, w, np.arange(X.shape[0]))
+    assert want > 1e-8          # a low-rank K~ differs from K
+    assert got == pytest.approx(want, rel=1e-9)
+    # a subset of rows: the same quotient restricted to those rows
+    rows = np.sort(np.random.default_rng(22).choice(X.shape[0], 100, replace=False))
+    want_r = np.linalg.norm((K @ w - Kt @ w)[rows]) / np.linalg.norm((K @ w)[rows])
+    assert oracle.eps_M_sampled(sk, X, w, rows) == pytest.approx(want_r, rel=1e-9)
+    # a plausible slip would show: lambda inside K~, or rows read in permuted order
+    slip_lam = np.linalg.norm((K @ w - (Kt @ w + F.lam * w))[rows]) / np.linalg.norm((K @ w)[rows])
+    slip_perm = np.linalg.norm((K @ w)[rows] - (Kt @ w)[tree.perm[rows]]) / np.linalg.norm((K @ w)[rows])
+    for slip in (slip_lam, slip_perm):
+        assert abs(slip - want_r) > 1e-3 * want_r
+
+
+def test_eps_M_is_zero_at_full_rank():
+    # s = the full node size: every P is a permutation, K~ = K and eps_M vanishes
+    w_ = workload("C1", N=500)
+    X = make_points(w_)
+    _, _, sk, _ = oracle.build_all(X, 0.5, 1.0, 40, 10 ** 6, 0.0, seed=2)
+    w = np.random.default_rng(23).standard_normal(500)
+    assert oracle.eps_M_sampled(sk, X, w, np.arange(500)) < 1e-13
