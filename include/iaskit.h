@@ -160,6 +160,29 @@ int iaskit_apply(const double* w, double* u, int nrhs);
 int iaskit_apply_device(const double* d_w, double* d_u, int nrhs);
 
 /*
+ * Exact kernel sums at test points (Sec. III, "Kernel regression for binary
+ * classification": a test point x gets the label sign(K(x, X) w), K(x, X) the exact
+ * kernel row over all training points; at training points the same sums give the exact
+ * K w of the error eps_M, eq. (error)):
+ *   scores(i, r) = sum_j exp(-|test_i - x_j|^2 / (2 h^2)) w(j, r)
+ * over every point x_j of the factored problem (the one selected by option "problem"
+ * in a batch), with that problem's h.  Not an approximation: no skeletons are used.
+ *   test     HOST pointer, M x d row-major FP64 (d of the factorization), caller-owned.
+ *   w        HOST pointer, N x nrhs column-major, the problem's original point order
+ *            (e.g. the weights returned by iaskit_solve).
+ *   scores   HOST pointer, M x nrhs column-major, overwritten.
+ * FP64 in the Gram form |x|^2 + |y|^2 - 2 x.y (relative error of a kernel value about
+ * 2^-52 (|x|^2 + |y|^2) / (2 h^2)); chunk partial sums are added in a fixed order, so
+ * repeated calls return identical scores.  M = 0 is a no-op.  1 <= nrhs <= 4096.
+ * Errors: IASKIT_ERR_NOT_FACTORED, _ARG, _INPUT (non-finite test point or weight),
+ * _NOMEM, _CUDA.
+ */
+int iaskit_predict(const double* test, int64_t M, const double* w, int nrhs, double* scores);
+
+/* As iaskit_predict with DEVICE pointers (test M x d, w N x nrhs, scores M x nrhs). */
+int iaskit_predict_device(const double* d_test, int64_t M, const double* d_w, int nrhs, double* d_scores);
+
+/*
  * Options (set before iaskit_factor* unless noted):
  *   "kappa"        neighbours per point for sampling (default 16)
  *   "samp_factor"  sampled rows per node = samp_factor * s_max, capped at N - |node| (2)
@@ -208,6 +231,12 @@ int iaskit_apply_device(const double* d_w, double* d_u, int nrhs);
  *                  alone inverts lambda I + K~ only.  0: lambda I + K~ (default)
  *                  [any time after a factorization]
  *   "problem"      which problem of a batch the introspection calls report (0) [any time]
+ *   "inject_status" failure-path test hook: device status flags (1 zero pivot, 2
+ *                  non-finite input, 4 internal bound, 8 expired bounded wait) that the
+ *                  host ORs into the library's device status word just before its next
+ *                  status read, exactly where a kernel would have set them; the call in
+ *                  progress then returns the matching error (8: IASKIT_ERR_TIMEOUT).
+ *                  One-shot: cleared once injected.  No kernel is made to fail [0..15]
  * Errors: IASKIT_ERR_ARG for an unknown key or an invalid value.
  */
 int iaskit_set_option(const char* key, double value);

@@ -40,7 +40,7 @@ EXPORTS = [
     "iaskit_factor_batched_device", "iaskit_num_problems", "iaskit_solve_batched",
     "iaskit_solve_batched_device", "iaskit_sampler_train", "iaskit_sampler_set_weights",
     "iaskit_sampler_get_weights", "iaskit_mlp_forward", "iaskit_mlp_train_step", "iaskit_get_learned",
-    "iaskit_kernel_block", "iaskit_refactor",
+    "iaskit_kernel_block", "iaskit_refactor", "iaskit_predict", "iaskit_predict_device",
 ]
 
 MLP_NPARAM = 17793
@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "iaskit_factor_batched_device": ([i32, vp, vp, i32, vp, vp, i32, i32, dbl], i32),
         "iaskit_num_problems": ([], i32),
         "iaskit_refactor": ([vp, i32], i32),
+        "iaskit_predict": ([vp, i64, vp, i32, vp], i32),
+        "iaskit_predict_device": ([vp, i64, vp, i32, vp], i32),
         "iaskit_solve_batched": ([vp, i32], i32),
         "iaskit_solve_batched_device": ([vp, i32], i32),
         "iaskit_sampler_train": ([vp, i64, i32, dbl, i32, i32, dbl, i32, dbl], i32),
@@ -244,6 +246,29 @@ def iaskit_apply_device(w, u, nrhs=None) -> None:
     if nrhs is None:
         nrhs = 1 if w.dim() == 1 else w.shape[0]
     _check(lib.iaskit_apply_device(_dev_ptr(w), _dev_ptr(u), nrhs))
+
+
+def iaskit_predict(test_points, w) -> np.ndarray:
+    """Exact kernel sums K(test, X) w of the factored problem: test (M, d) host array,
+    w (N,) or (N, nrhs) in original point order; returns (M,) or (M, nrhs)."""
+    T = _host_f64(test_points)
+    if T.ndim != 2:
+        raise ValueError("test_points must be (M, d)")
+    W = np.asarray(w, dtype=np.float64)
+    vec = W.ndim == 1
+    W2 = np.asfortranarray(W[:, None] if vec else W)
+    out = np.empty((T.shape[0], W2.shape[1]), dtype=np.float64, order="F")
+    _check(load().iaskit_predict(T.ctypes.data, T.shape[0], W2.ctypes.data, W2.shape[1], out.ctypes.data))
+    return out[:, 0] if vec else out
+
+
+def iaskit_predict_device(test_points, w, scores, nrhs=None) -> None:
+    """iaskit_predict on CUDA float64 tensors: test (M, d) row-major, w laid out like
+    iaskit_solve_device's right-hand sides ((nrhs, N) or (N,)), scores (nrhs, M) or (M,)."""
+    if nrhs is None:
+        nrhs = 1 if w.dim() == 1 else w.shape[0]
+    _check(load().iaskit_predict_device(_dev_ptr(test_points), test_points.shape[0], _dev_ptr(w), nrhs,
+                                        _dev_ptr(scores)))
 
 
 def iaskit_set_option(key: str, value: float) -> None:

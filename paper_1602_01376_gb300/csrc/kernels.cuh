@@ -302,6 +302,18 @@ struct KMatvecDesc {
 void kernel_matvec(const double* Xp, const double* xnorm, int d, int nrhs, const KMatvecDesc* descs_dev,
                    int ndesc, int max_rows, cudaStream_t st);
 
+// Exact kernel sums at M test points (Sec. III, kernel regression):
+//   out[i + r ldo] = sum_j exp(-|t_i - x_j|^2 / (2 h^2)) w[orig(j) + r ldw]
+// over the N points of one problem (Xp rows pbase .. pbase + N - 1, permuted order,
+// xnorm their squared norms, perm[pbase + j] - pbase the original index of j), w in
+// the problem's original order.  T: M x d row-major (device).  part: scratch of
+// predict_scratch_doubles(M, N, nrhs) doubles.  FP64, Gram form.
+void predict_chunks(int M, int N, int& chunk, int& nchunk);
+size_t predict_scratch_doubles(int M, int N, int nrhs);
+void kernel_predict(const double* T, int M, const double* Xp, const double* xnorm, const int* perm, int pbase,
+                    int N, int d, double h, const double* w, int ldw, int nrhs, double* part, double* out,
+                    int ldo, cudaStream_t st);
+
 // Near-field correction of the kNN-separated operator (eq. askit, Sec. II-B).  For
 // every target position p and every node alpha of p's interaction list (the sibling of
 // each ancestor of p's leaf) that holds at least one of p's kappa nearest neighbours,

@@ -9,7 +9,7 @@ const char* prof_name(int k) {
                                         "misc", "kernel_blocks_f32", "cpqr_id_f32", "getrf_f32",
                                         "getrs_f32", "gemm_f32", "learned_sampling", "mlp_bf16",
                                         "id_judge", "gemm_pair",
-                                        "kernel_blocks_pair", "near_field"};
+                                        "kernel_blocks_pair", "near_field", "predict"};
   return (k >= 0 && k < PK_COUNT) ? names[k] : "?";
 }
 

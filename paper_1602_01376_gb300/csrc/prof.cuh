@@ -34,6 +34,7 @@ enum ProfKind {
   PK_GEMM_PAIR,  // FP64-accurate products on FP32 pairs (operator of the mixed form)
   PK_KBLOCK_PAIR,  // kernel blocks evaluated on FP32 pairs (operator of the mixed form)
   PK_NEAR,         // near-field correction S of the kNN-separated operator
+  PK_PREDICT,      // exact kernel sums at test points (kernel regression, eps_M)
   PK_COUNT
 };
 

@@ -98,6 +98,10 @@ struct Options {
   // operator of eq. (askit); the factorization (of lambda I + K~) then preconditions the
   // refinement's GMRES
   int near_field = 0;
+  // failure-path test hook: flags (DEV_* bits) that the host ORs into the device status
+  // word just before the next status read, as a kernel's bounded wait or pivot check
+  // would; one-shot (cleared once injected)
+  int inject_status = 0;
 };
 
 struct Prob {
@@ -355,6 +359,7 @@ class Solver {
   DevBuf Xpair;   // mixed form: permuted coordinates as FP32 pairs
   DevBuf DInv32;  // FP32 LUs: inverses of their 32 x 32 diagonal blocks and pivot permutations
   DevBuf rhs_keep;  // mixed form: the right-hand side, for a refinement after an operator upgrade
+  DevBuf pred_part, pred_io;  // kernel sums at test points: chunk partials; host-call staging
   std::vector<char> stag_prob;  // per problem: a column of the last refinement stopped at its floor
   TreeScratch tree_s;
   KnnScratch knn_s;
@@ -403,6 +408,14 @@ class Solver {
   }
   int read_status_and_clear() {
     int v = 0;
+    if (opt.inject_status) {  // the hook writes the device word itself, from the host
+      d2h(&v, status.as<int>(), 1, st);
+      IA_CUDA(cudaStreamSynchronize(st));
+      v |= opt.inject_status;
+      opt.inject_status = 0;
+      h2d(status.as<int>(), &v, 1, st);
+      v = 0;
+    }
     d2h(&v, status.as<int>(), 1, st);
     IA_CUDA(cudaStreamSynchronize(st));
     IA_CUDA(cudaMemsetAsync(status.as<int>(), 0, sizeof(int), st));
@@ -1916,6 +1929,25 @@ class Solver {
     stats.t_solve = now_ms() - t0;
   }
 
+  // Exact kernel sums K(T, X_q) w at M test points for the selected problem q (Sec. III,
+  // kernel regression): T M x d row-major, w N_q x nrhs column-major in q's original
+  // order, out M x nrhs column-major; all device pointers.
+  void predict_device(const double* T, int64_t M, const double* w, int nrhs, double* out, int q) {
+    if (!skeletonized && !factored) throw Error(IASKIT_ERR_NOT_FACTORED, "no factorization");
+    if (M < 0 || M > INT_MAX / 2) throw Error(IASKIT_ERR_ARG, "bad number of test points");
+    if (nrhs < 1 || nrhs > 4096) throw Error(IASKIT_ERR_ARG, "bad nrhs");
+    if (M == 0) return;
+    const Prob& P = pr[q];
+    check_finite(T, M * d, status.as<int>(), st);
+    check_finite(w, (int64_t)P.N * nrhs, status.as<int>(), st);
+    raise_status(read_status_and_clear());
+    double* part = pred_part.ensure_n<double>(predict_scratch_doubles((int)M, P.N, nrhs));
+    kernel_predict(T, (int)M, Xp.as<double>(), xnrm.as<double>(), perm.as<int>(), P.pbase, P.N, d, P.h, w, P.N,
+                   nrhs, part, out, (int)M, st);
+    IA_CUDA(cudaStreamSynchronize(st));
+    prof().resolve();
+  }
+
   // out <- (lambda I + K~)^{-1} in with the stored factorization; in and out may alias.
   // Problems factored in FP32 are solved on an FP32 copy of their blocks.
   void plain_solve(const double* in, int nrhs, double* out) {
@@ -2276,7 +2308,7 @@ class Solver {
                      &l_feat, &l_score, &l_linfo, &l_samp, &l_rk, &l_Ptmp, &l_sktmp, &l_hold, &l_err,
                      &l_cols, &l_gram, &l_dense, &mlp_master, &mlp_m, &mlp_v, &mlp_grad, &mlp_b16,
                      &mlp_loss, &tr_feat, &tr_tgt, &tr_lev, &tr_bx, &tr_bt, &tr_y, &tr_H1, &tr_H2, &tr_idx,
-                     &xnrm};
+                     &xnrm, &pred_part, &pred_io};
     mlp_ready = false;
     for (DevBuf* b : all) b->release();
     tree_s.release();
@@ -2444,6 +2476,37 @@ int iaskit_apply_device(const double* d_w, double* d_u, int nrhs) {
   });
 }
 
+int iaskit_predict_device(const double* d_test, int64_t M, const double* d_w, int nrhs, double* d_scores) {
+  return guarded([&] {
+    Solver& s = S();
+    if ((!d_test || !d_w || !d_scores) && M > 0) throw Error(IASKIT_ERR_ARG, "null pointer");
+    const int q = s.opt.problem;
+    if (q < 0 || q >= (int)s.pr.size()) throw Error(IASKIT_ERR_ARG, "selected problem out of range");
+    s.predict_device(d_test, M, d_w, nrhs, d_scores, q);
+  });
+}
+
+int iaskit_predict(const double* test, int64_t M, const double* w, int nrhs, double* scores) {
+  return guarded([&] {
+    Solver& s = S();
+    if ((!test || !w || !scores) && M > 0) throw Error(IASKIT_ERR_ARG, "null pointer");
+    const int q = s.opt.problem;
+    if (q < 0 || q >= (int)s.pr.size()) throw Error(IASKIT_ERR_ARG, "selected problem out of range");
+    if (M < 0 || M > INT_MAX / 2) throw Error(IASKIT_ERR_ARG, "bad number of test points");
+    if (nrhs < 1 || nrhs > 4096) throw Error(IASKIT_ERR_ARG, "bad nrhs");
+    if (M == 0) return;
+    const int64_t nT = M * s.d, nW = (int64_t)s.pr[q].N * nrhs, nO = M * nrhs;
+    double* dT = s.pred_io.ensure_n<double>(nT + nW + nO);
+    double* dW = dT + nT;
+    double* dO = dW + nW;
+    h2d(dT, test, nT, s.st);
+    h2d(dW, w, nW, s.st);
+    s.predict_device(dT, M, dW, nrhs, dO, q);
+    d2h(scores, dO, nO, s.st);
+    IA_CUDA(cudaStreamSynchronize(s.st));
+  });
+}
+
 int iaskit_apply(const double* w, double* u, int nrhs) {
   return guarded([&] {
     Solver& s = S();
@@ -2509,6 +2572,8 @@ int iaskit_set_option(const char* key, double value) {
       o.pair_cond_max = value;
     } else if (k == "near_field") {
       o.near_field = as_int(0, 1);
+    } else if (k == "inject_status") {
+      o.inject_status = as_int(0, 15);
     } else if (k == "profile") {
       int v = as_int(0, 1);
       IA_CUDA(cudaStreamSynchronize(S().st));
@@ -2542,6 +2607,7 @@ int iaskit_get_option(const char* key, double* value) {
     else if (k == "cpqr_cluster") *value = o.cpqr_cluster;
     else if (k == "pair_cond_max") *value = o.pair_cond_max;
     else if (k == "near_field") *value = o.near_field;
+    else if (k == "inject_status") *value = o.inject_status;
     else throw Error(IASKIT_ERR_ARG, "unknown option " + k);
   });
 }
