@@ -3,15 +3,21 @@
 One step = iaskit_factor (tree, kNN, sampling, skeletonization, leaf LU, W and Z
 for every level) followed by iaskit_solve of the workload's right-hand sides.
 The metric is right-hand sides solved per second with the factorization counted
-in every step (RHS/s); the JSON line also carries the factor time and the
-solve-only rate.
+in every step (RHS/s); the JSON line also carries the factor time, the
+solve-only rate and the sampled eps_M of both forms (equal accuracy).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload C2]
+                  [--workload C4]
+
+The default workload is C4 (N = 1,048,576 points in d = 64 on a 6-dimensional
+manifold, m 512, s_max 256, tau 1e-6, lambda 1e-3, 8 RHS).  The metric's own
+configuration, C5 (N = 4M, d = 8, lambda 1e-4), has no FP64 solve that reaches its
+residual target and does not fit the mixed form in HBM; --workload C5 runs it anyway.
 
 --impl reference times the FP64 CPU oracle (the baseline) on a bounded sample of
-the same workload.  Under torchrun with N > 1 every rank factors its own copy of
-the workload (independent replicas, weak scaling); rank 0 prints the line.
+the same workload and extrapolates it to the full N with per-phase complexity
+models (labelled "extrapolated").  Under torchrun with N > 1 every rank factors its
+own copy of the workload (independent replicas, weak scaling); rank 0 prints the line.
 """
 from __future__ import annotations
 
@@ -34,7 +40,9 @@ METRIC = "factor s + RHS solves/s at N=4M,d=8: chosen form vs FP64 plain, resid<
 UNIT = "RHS/s (factor+solve per step)"
 SM_COUNT = 152
 FP64_FMA_PER_CLK_PER_SM = 2          # GB300: FP64 pipe width per SM and clock
-CPU_SAMPLE_N = 4096                  # oracle sample: same generator and parameters, smaller N
+CPU_SAMPLE_N = 2048                  # oracle sample: same generator and parameters, smaller N
+EPS_M_ROWS = 1000                    # rows of the sampled eps_M (eq. error, Sec. III)
+COMPARE_STEPS = 3                    # timed steps of the FP64 plain form beside the chosen one
 
 
 def peaks():
@@ -140,9 +148,28 @@ def batch_seed(rank: int) -> int:
 
 
 # ----------------------------------------------------------------- CPU oracle leg
-def oracle_step(w, N_sample: int, nrhs: int) -> float:
-    """One factor + solve of the oracle on a sample of the workload; returns seconds."""
+def _depth(N: int, m: int) -> int:
+    L = 0
+    while -(-N // (1 << L)) > m:
+        L += 1
+    return L
+
+
+# Per-phase growth models of the oracle (the method's complexities, Sec. II-C): tree
+# N log N; brute-force kNN N^2; skeletonization one ID per non-root node (2^(L+1) - 2
+# nodes, each of bounded size); factorization T^f = O(s^2 N log^2 N), i.e. N L^2 at
+# fixed s; solve O(N log N), N L.
+def _phase_growth(N: int, m: int) -> dict:
+    L = max(_depth(N, m), 1)
+    return {"tree": N * np.log2(max(N, 2)), "knn": float(N) * N, "skeletonize": float(2 ** (L + 1) - 2),
+            "factorize": float(N) * L * L, "solve": float(N) * L}
+
+
+def oracle_phases(w, N_sample: int, nrhs: int) -> dict:
+    """One factor + solve of the oracle on N_sample points of the workload's generator
+    (same parameters), each phase timed; returns seconds per phase."""
     import oracle
+    from oracle.askit import skeletonize
     if w.kind == "batched":
         # the batch's first problem (its h and lambda), its first N_sample points
         X, h, lam = batched_problems(count=64)[0]
@@ -152,50 +179,100 @@ def oracle_step(w, N_sample: int, nrhs: int) -> float:
         ws = w.scaled(N_sample)
         X = make_points(ws)
     u = make_rhs(ws, nrhs=nrhs)
+    t = {}
     t0 = time.perf_counter()
-    _, _, _, F = oracle.build_all(X, ws.h, ws.lam, ws.m, ws.s_max, ws.tol, kappa=ws.kappa,
-                                  samp_factor=ws.samp_factor)
+    tree = oracle.build_tree(X, ws.m)
+    t1 = time.perf_counter()
+    knn = oracle.knn_bruteforce(X, ws.kappa)
+    t2 = time.perf_counter()
+    sk = skeletonize(X, tree, knn, ws.h, ws.s_max, ws.tol, samp_factor=ws.samp_factor)
+    t3 = time.perf_counter()
+    F = oracle.factorize(sk, ws.lam)
+    t4 = time.perf_counter()
     oracle.solve(F, u)
-    return time.perf_counter() - t0
+    t5 = time.perf_counter()
+    return {"tree": t1 - t0, "knn": t2 - t1, "skeletonize": t3 - t2, "factorize": t4 - t3, "solve": t5 - t4}
+
+
+def extrapolate(phases: dict, N_sample: int, N_full: int, m: int) -> float:
+    """Seconds of the oracle at N_full from its phases at N_sample and the models above."""
+    gs, gf = _phase_growth(N_sample, m), _phase_growth(N_full, m)
+    return float(sum(phases[k] * gf[k] / gs[k] for k in phases))
+
+
+def _full_sizes(w):
+    if w.kind == "batched":
+        return [len(p[0]) for p in batched_problems(count=64)]
+    return [w.N]
 
 
 def cpu_baseline_subprocess(wname: str, N_sample: int, nrhs: int, steps: int) -> dict:
-    """Runs the oracle single-threaded in a child process (BLAS pinned to one thread)."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    """Runs the oracle in a child process with every host core in its BLAS pool."""
+    cores = os.cpu_count() or 1
+    env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores),
+               MKL_NUM_THREADS=str(cores))
     code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
             f"from workloads import workload; w = workload({wname!r}); "
-            f"ts = [bench.oracle_step(w, {N_sample}, {nrhs}) for _ in range({steps})]; "
+            f"ts = [bench.oracle_phases(w, {N_sample}, {nrhs}) for _ in range({steps})]; "
             f"print(json.dumps(ts))")
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True)
     if r.returncode != 0:
         return {"error": r.stderr[-400:]}
-    ts = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"times": ts}
+    return {"phases": json.loads(r.stdout.strip().splitlines()[-1]), "cores": cores}
+
+
+def cpu_estimate(w, phases: dict) -> tuple:
+    """(RHS/s of the oracle at the workload's full size, seconds per step, sample text):
+    the sampled phases extrapolated to every problem of the workload."""
+    sizes = _full_sizes(w)
+    N_s = min(CPU_SAMPLE_N, min(sizes))
+    secs = sum(extrapolate(phases, N_s, n, w.m) for n in sizes)
+    rhs = w.nrhs * len(sizes)
+    what = (f"extrapolated: oracle factor+solve of N={N_s} points of the {w.name} generator "
+            f"(same h, lambda, m, s_max, tol, {w.nrhs} RHS), each phase scaled to "
+            + (f"N={sizes[0]}" if len(sizes) == 1 else f"each of the {len(sizes)} problems' N")
+            + " by its complexity (tree N log N, kNN N^2, skeletonization per node, "
+              "factorization N L^2, solve N L; L = tree depth)")
+    if w.kind == "batched":
+        what = what.replace(f"N={N_s} points of the {w.name} generator",
+                            f"the first {N_s} points of the batch's first problem")
+    return rhs / secs, secs, what
+
+
+def cpu_baseline_entry(w) -> dict:
+    """The line's cpu_baseline: one sampled oracle run on all host cores, extrapolated."""
+    res = cpu_baseline_subprocess(w.name, min(CPU_SAMPLE_N, min(_full_sizes(w))), w.nrhs, 1)
+    if "error" in res:
+        return {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                "sample": "failed: " + res["error"][-200:]}
+    value, secs, what = cpu_estimate(w, res["phases"][0])
+    return {"value": value, "unit": UNIT, "cores": res["cores"], "kind": "oracle", "extrapolated": True,
+            "seconds_per_step": secs,
+            "sampled_phases_s": {k: round(v, 3) for k, v in res["phases"][0].items()}, "sample": what}
 
 
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    nrhs = w.nrhs
-    res = cpu_baseline_subprocess(w.name, CPU_SAMPLE_N, nrhs, args.warmup + args.steps)
+    res = cpu_baseline_subprocess(w.name, min(CPU_SAMPLE_N, min(_full_sizes(w))), w.nrhs,
+                                  args.warmup + args.steps)
     if "error" in res:
         print(json.dumps({"impl": "reference", "unavailable": "oracle failed: " + res["error"][-200:]}))
         return 0
-    ts = res["times"][args.warmup:]
-    total = float(sum(ts))
-    value = nrhs * len(ts) / total
-    sample = (f"oracle factor+solve of N={CPU_SAMPLE_N} points of the {w.name} generator with "
-              f"the same h, lambda, m, s_max, tol and {nrhs} RHS per step")
-    if w.kind == "batched":
-        sample = (f"oracle factor+solve of the first {CPU_SAMPLE_N} points of the batch's first "
-                  f"problem (its h and lambda; m, s_max, tol of the batch) with {nrhs} RHS per step")
+    per = [cpu_estimate(w, ph) for ph in res["phases"][args.warmup:]]
+    total = float(sum(p[1] for p in per))
+    rhs = w.nrhs * len(_full_sizes(w))
+    value = rhs * len(per) / total
+    sample_s = float(sum(sum(ph.values()) for ph in res["phases"][args.warmup:]))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(ts),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(per),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config_of(w),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "data": "synthetic", "config": config_of(w), "same_config": True, "extrapolated": True,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": res["cores"], "kind": "oracle",
+                         "sample": per[0][2] + f"; sampled oracle time {sample_s:.1f} s over "
+                                   f"{len(per)} steps"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -209,7 +286,10 @@ def config_of(w):
                 "problems": 64, "d": 16, "leaf_m": w.m, "s_max": w.s_max, "tol": w.tol,
                 "nrhs_per_problem": w.nrhs, "kappa": w.kappa,
                 "l2": "inputs and working set larger than L2 (no flush needed)"}
-    return {"workload": f"{w.name}: N={w.N}, d={w.d}, {w.kind}", "N": w.N, "d": w.d, "h": w.h,
+    kinds = {"gmm": f"{w.ncomp}-component Gaussian mixture, axis std in [{w.std_lo}, {w.std_hi}]",
+             "manifold": "random 2-layer tanh image of N(0, I_6) plus 0.01 noise",
+             "uniform": "uniform on the unit cube"}
+    return {"workload": f"{w.name}: N={w.N}, d={w.d}, {kinds.get(w.kind, w.kind)}", "N": w.N, "d": w.d, "h": w.h,
             "lambda": w.lam, "leaf_m": w.m, "s_max": w.s_max, "tol": w.tol, "nrhs": w.nrhs,
             "kappa": w.kappa, "path": "plain FP64",
             "l2": "inputs and working set larger than L2 (no flush needed)"}
@@ -369,16 +449,7 @@ def run_batched(args, w, form):
                 "d2h_bytes_per_step": 8 * sum(Ns) * w.nrhs},
     }
     if not args.no_cpu_baseline:
-        res = cpu_baseline_subprocess(w.name, CPU_SAMPLE_N, w.nrhs, 1)
-        if "times" in res:
-            t = res["times"][0]
-            line["cpu_baseline"] = {
-                "value": w.nrhs / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": f"one oracle factor+solve of the first {CPU_SAMPLE_N} points of the batch's "
-                          f"first problem, {w.nrhs} RHS ({t:.1f} s)"}
-        else:
-            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": "failed: " + res.get("error", "")[-200:]}
+        line["cpu_baseline"] = cpu_baseline_entry(w)
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
@@ -391,7 +462,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="C2")
+    ap.add_argument("--workload", default="C4")
     ap.add_argument("--form", choices=["mixed", "fp64"], default="mixed",
                     help="form timed for the headline value (mixed = the chosen form)")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other form")
@@ -432,9 +503,25 @@ def main():
         U.copy_(U0)
         ia.iaskit_solve_device(U)
 
-    def measure(form, sample_clocks):
+    # sampled eps_M (eq. error, S = 0) of the current factorization: ||K w - K~ w|| / ||K w||
+    # on EPS_M_ROWS seeded rows, K w by exact kernel sums (iaskit_predict), K~ w by the
+    # operator apply minus lambda w
+    erng = np.random.default_rng(w.seed + 11)
+    e_rows = torch.from_numpy(np.sort(erng.choice(w.N, EPS_M_ROWS, replace=False))).cuda()
+    e_w = torch.from_numpy(erng.standard_normal(w.N)).cuda()
+
+    def eps_M():
+        T = X[e_rows].contiguous()
+        Kw = torch.empty(EPS_M_ROWS, dtype=torch.float64, device="cuda")
+        ia.iaskit_predict_device(T, e_w, Kw)
+        Aw = torch.empty_like(e_w)
+        ia.iaskit_apply_device(e_w, Aw)
+        Ktw = (Aw - w.lam * e_w)[e_rows]
+        return float((Kw - Ktw).norm() / Kw.norm())
+
+    def measure(form, sample_clocks, steps, warmup):
         set_form(form)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             step()
         torch.cuda.synchronize()
         AU = torch.empty_like(U)
@@ -447,7 +534,7 @@ def main():
         torch.cuda.synchronize()
         with ClockSampler(local if sample_clocks else -1) as clk:
             ev0.record()
-            for _ in range(args.steps):
+            for _ in range(steps):
                 step()
             ev1.record()
             torch.cuda.synchronize()
@@ -456,11 +543,12 @@ def main():
         stats = ia.iaskit_stats()
         ia.iaskit_set_option("profile", 0)
         return {"ms": ms, "stats": stats, "resid": resid, "clocks": clk.summary(),
-                "launches": stats["launches"] - launches0}
+                "launches": stats["launches"] - launches0, "eps_M": eps_M(), "steps": steps}
 
-    chosen = measure(args.form, True)
+    chosen = measure(args.form, True, args.steps, args.warmup)
     other_form = "fp64" if args.form == "mixed" else "mixed"
-    other = None if args.no_compare else measure(other_form, False)
+    other = None if args.no_compare else measure(other_form, False, min(args.steps, COMPARE_STEPS),
+                                                 min(args.warmup, 1))
     set_form(args.form)
     value = world * w.nrhs * args.steps / (chosen["ms"] / 1e3)
 
@@ -523,8 +611,8 @@ def main():
                 "launches": kern[top]["calls"], "ms_total": kern[top]["ms"]}
     st = chosen["stats"]
     cfg = config_of(w)
-    cfg["path"] = ("mixed: FP32 factorization, FP64 pivots and operator, refined to 1e-10"
-                   if args.form == "mixed" else "plain FP64")
+    cfg["path"] = ("mixed: FP32 factorization, FP64 pivots and operator, refined to 1e-10; "
+                   "neighbour + uniform row sampling" if args.form == "mixed" else "plain FP64")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": chosen["ms"] / args.steps, "higher_is_better": True,
@@ -532,7 +620,12 @@ def main():
         "dtype": "f32+f64" if args.form == "mixed" else "f64", "data": "synthetic",
         "config": cfg,
         "factor_s": st["ms"]["factor"] / 1e3, "solve_rhs_per_s": w.nrhs / (st["ms"]["solve"] / 1e3),
-        "residual": chosen["resid"], "refine_sweeps": st.get("refine_sweeps"),
+        "residual": chosen["resid"],
+        "eps_M": {"chosen": chosen["eps_M"], "fp64_plain": other["eps_M"] if other else None,
+                  "rows": EPS_M_ROWS,
+                  "what": "||K w - K~ w|| / ||K w|| on seeded rows (eq. error, S = 0), K w by exact "
+                          "kernel sums, w ~ N(0,1): equal accuracy needs chosen <= fp64_plain"},
+        "refine_sweeps": st.get("refine_sweeps"),
         "refine_gmres_iters": st.get("refine_iters"), "refine_stagnated_columns": st.get("refine_stagnated"),
         "fp64_problems": st.get("fp64_problems"),
         "fp64_operator_problems": st.get("fp64_operator_problems"),
@@ -553,22 +646,15 @@ def main():
     if other is not None:
         so = other["stats"]
         line["compare_" + other_form] = {
-            "value": world * w.nrhs * args.steps / (other["ms"] / 1e3),
-            "ms_per_step": other["ms"] / args.steps, "factor_s": so["ms"]["factor"] / 1e3,
+            "value": world * w.nrhs * other["steps"] / (other["ms"] / 1e3),
+            "steps": other["steps"], "warmup": min(args.warmup, 1),
+            "sampled_steps": other["steps"] < args.steps,
+            "ms_per_step": other["ms"] / other["steps"], "factor_s": so["ms"]["factor"] / 1e3,
             "solve_rhs_per_s": w.nrhs / (so["ms"]["solve"] / 1e3), "residual": other["resid"],
-            "kernel_ms_per_step": {k: round(v["ms"] / args.steps, 3)
+            "kernel_ms_per_step": {k: round(v["ms"] / other["steps"], 3)
                                    for k, v in so["kernels"].items() if v["ms"] > 0}}
     if not args.no_cpu_baseline:
-        res = cpu_baseline_subprocess(w.name, CPU_SAMPLE_N, w.nrhs, 1)
-        if "times" in res:
-            t = res["times"][0]
-            line["cpu_baseline"] = {
-                "value": w.nrhs / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-                "sample": f"one oracle factor+solve of N={CPU_SAMPLE_N} points of the {w.name} "
-                          f"generator, same parameters, {w.nrhs} RHS ({t:.1f} s)"}
-        else:
-            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": "failed: " + res.get("error", "")[-200:]}
+        line["cpu_baseline"] = cpu_baseline_entry(w)
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
