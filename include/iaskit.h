@@ -231,6 +231,12 @@ int iaskit_predict_device(const double* d_test, int64_t M, const double* d_w, in
  *                  alone inverts lambda I + K~ only.  0: lambda I + K~ (default)
  *                  [any time after a factorization]
  *   "problem"      which problem of a batch the introspection calls report (0) [any time]
+ *   "knn_prune"    1: the kNN lists are searched with the points in tree order: each
+ *                  block of 128 queries scans its seed window of spatially close rows,
+ *                  then only the 128-point tiles whose bounding boxes come within its
+ *                  queries' largest kappa-th seed distance; the skipped tiles enter the
+ *                  certification of the exact re-rank (default).  0: every pair is
+ *                  scanned.  The lists are identical either way [any time]
  *   "inject_status" failure-path test hook: device status flags (1 zero pivot, 2
  *                  non-finite input, 4 internal bound, 8 expired bounded wait) that the
  *                  host ORs into the library's device status word just before its next

@@ -40,12 +40,20 @@ void permute_points(const double* X, const int* perm, int N, int d, int* iperm, 
 
 // ------------------------------------------------------------------- kNN (a2)
 struct KnnScratch {
-  DevBuf x32, qnorm, part, mean, rmax, probs, cand_d, cand_i, flagged, counter, tiles, status;
+  DevBuf x32, qnorm, part, mean, rmax, probs, cand_d, cand_i, flagged, counter, tiles, status, seed_tiles, first,
+      box, tau, tq, cnt, toff, tlist;
   void release() {
     for (DevBuf* b : {&x32, &qnorm, &part, &mean, &rmax, &probs, &cand_d, &cand_i, &flagged, &counter,
-                      &tiles, &status})
+                      &tiles, &status, &seed_tiles, &first, &box, &tau, &tq, &cnt, &toff, &tlist})
       b->release();
   }
+};
+
+// What the pruned search scanned: point tiles after the seed windows, query-point
+// pairs scanned in all, and the pairs of a brute-force search.
+struct KnnPruneStats {
+  int64_t tiles_scanned = 0;
+  double pairs_scanned = 0.0, pairs_all = 0.0;
 };
 
 // Work tile of the kNN kernels: queries [q0, q0 + qn) against the points
@@ -64,6 +72,16 @@ struct KnnTile {
 int knn_bruteforce(const double* X, int N, int d, int kappa, int* knn,
                    const std::vector<std::pair<int, int>>& problems, KnnScratch& s,
                    cudaStream_t st);
+
+// The same lists (bit for bit) from points held in tree order, Xp = X[perm] (perm[r] =
+// original index of row r, problems as row ranges of Xp), by the tensor-core prefilter
+// over each query block's seed window of spatially close rows, then only over the
+// point tiles whose bounding boxes come within the block's bound (an exact upper bound
+// on its queries' kappa-th distances); the skipped tiles enter the certification of
+// the exact re-rank.  Returns the number of queries redone by the exact scan.
+int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* knn,
+             const std::vector<std::pair<int, int>>& problems, KnnScratch& s, cudaStream_t st,
+             KnnPruneStats* pstats = nullptr);
 
 // ------------------------------------------------------------- sampling (a3)
 struct SampleScratch {

@@ -24,6 +24,7 @@
 #include <cfloat>
 #include <climits>
 #include <mutex>
+#include <type_traits>
 
 #include "kernels.cuh"
 #include "tc.cuh"
@@ -159,10 +160,15 @@ constexpr size_t prefilter_smem() {
   return (size_t)6 * KT_QB * D * 4 + (size_t)KT_RB * D * 4 + 2 * KT_RB * 4 + 64;
 }
 
+// With a tile list (tlist, toff: CSR per work tile) the block scans the listed point
+// tiles of its problem (local tile t = rows tl.rb + 128 t ..) instead of the whole
+// range [tl.rb, tl.rb + tl.rn); with load_init its lists start from the candidates
+// already in cand_d / cand_i (an earlier pass over other tiles) instead of empty.
 template <int D, int KP>
 __global__ void __launch_bounds__(KT_NTH) knn_prefilter_kernel(const float* Xc, const float* qnorm,
-                                                               const KnnTile* tiles, float* cand_d,
-                                                               int* cand_i, int* status) {
+                                                               const KnnTile* tiles, const int* tlist,
+                                                               const int* toff, int load_init,
+                                                               float* cand_d, int* cand_i, int* status) {
   extern __shared__ __align__(1024) unsigned char kt_sh[];
   constexpr int OPW = KT_QB * D;  // 32-bit words of one operand
   uint32_t* Ah = reinterpret_cast<uint32_t*>(kt_sh);
@@ -183,8 +189,10 @@ __global__ void __launch_bounds__(KT_NTH) knn_prefilter_kernel(const float* Xc, 
   const int my_q = tl.q0 + qi;
   const bool active = qi < tl.qn;
   const int rend = tl.rb + tl.rn;
-  const int ntile = (tl.rn + KT_RB - 1) / KT_RB;
-  auto tile_row = [&](int t) { return tl.rb + t * KT_RB; };
+  const int lbeg = tlist ? toff[blockIdx.x] : 0;
+  const int ntile = tlist ? toff[blockIdx.x + 1] - lbeg : (tl.rn + KT_RB - 1) / KT_RB;
+  if (ntile == 0) return;  // block-uniform: nothing to scan, the lists stay as they are
+  auto tile_row = [&](int t) { return tl.rb + (tlist ? tlist[lbeg + t] : t) * KT_RB; };
   stage_operand<D>(Xc, tl.q0, tl.qn, Ah, Al);
   stage_operand<D>(Xc, tile_row(0), min(KT_RB, rend - tile_row(0)), Bh0, Bl0);
   if (tid < KT_RB) rn_s[tid] = tid < min(KT_RB, rend - tile_row(0)) ? qnorm[tile_row(0) + tid] : 0.0f;
@@ -228,6 +236,14 @@ __global__ void __launch_bounds__(KT_NTH) knn_prefilter_kernel(const float* Xc, 
   for (int u = 0; u < KP; ++u) {
     bd[u] = FLT_MAX;
     bi[u] = INT_MAX;
+  }
+  if (load_init && active) {
+    const size_t o = (size_t)my_q * (KT_SUB * KP) + (size_t)cq * KP;
+#pragma unroll
+    for (int u = 0; u < KP; ++u) {
+      bd[u] = cand_d[o + u];
+      bi[u] = cand_i[o + u];
+    }
   }
   for (int t = 0; t < ntile; ++t) {
     const int b = t & 1;
@@ -342,10 +358,16 @@ __device__ __forceinline__ bool pair_less(double a, int ia, double b, int ib) {
 // the lists' last values (a list that is not full holds all of its quarter's points).
 // Kdim is the padded dimension of the prefilter (its accumulation length).
 constexpr int RR_MAXK = 48;
+// Rows may be in any order: ids[r] is the original index of row r (null: r itself);
+// ties are broken and the lists written in original indices, at row ids[i].  With
+// tau (the pruned search) the points of the tiles that were not scanned are known to
+// lie farther than tau[i] (exact FP64), so a list is certified only if its kappa-th
+// distance is <= tau[i] as well.
 template <int KP, int KAP>  // KAP >= kappa: size of the sorted list
 __global__ void knn_rerank_kernel(const double* X, int d, int kappa, int Kdim, const KnnTile* tiles,
                                   const float* cand_d, const int* cand_i, const float* qnorm,
-                                  const unsigned* rmax_bits, int* knn, int2* flagged, int* nflagged) {
+                                  const unsigned* rmax_bits, const int* ids, const double* tau, int* knn,
+                                  int2* flagged, int* nflagged) {
   const KnnTile tl = tiles[blockIdx.x];
   if ((int)threadIdx.x >= tl.qn) return;
   const int i = tl.q0 + threadIdx.x;
@@ -373,7 +395,7 @@ __global__ void knn_rerank_kernel(const double* X, int d, int kappa, int Kdim, c
       }
       ++found;
       double v = exact_sqdist(xi, X + (size_t)j * d, d);
-      int jj = j;
+      int jj = ids ? ids[j] : j;
       if (!pair_less(v, jj, dd[kappa - 1], ii[kappa - 1])) continue;
 #pragma unroll
       for (int w = 0; w < KAP; ++w) {  // insertion into the sorted kappa list
@@ -393,13 +415,15 @@ __global__ void knn_rerank_kernel(const double* X, int d, int kappa, int Kdim, c
   const double E = c * ((double)qnorm[i] + (double)__uint_as_float(rmax_bits[tl.prob]));
   const bool all_in = found >= N - 1;  // every other point was a candidate
   const double lo = ((double)cut - E) * (1.0 - 1e-12);
-  const bool ok = found >= kappa && isfinite(E) && (all_in || lo > dd[kappa - 1]);
+  const bool ok = found >= kappa && isfinite(E) && (all_in || lo > dd[kappa - 1]) &&
+                  (tau == nullptr || all_in || dd[kappa - 1] <= tau[i]);
   if (!ok) {
     int slot = atomicAdd(nflagged, 1);
     flagged[slot] = make_int2(i, blockIdx.x);
     return;
   }
-  for (int u = 0; u < kappa; ++u) knn[(size_t)i * kappa + u] = ii[u];
+  const size_t orow = (size_t)(ids ? ids[i] : i);
+  for (int u = 0; u < kappa; ++u) knn[orow * kappa + u] = ii[u];
 }
 
 // Exact scan for one flagged query per block: every thread keeps a sorted top-kappa
@@ -408,7 +432,7 @@ __global__ void knn_rerank_kernel(const double* X, int d, int kappa, int Kdim, c
 constexpr int FB_THREADS = 128;
 constexpr int FB_MAXK = 64;
 __global__ void knn_fallback_kernel(const double* X, int d, int kappa, const KnnTile* tiles,
-                                    const int2* flagged, int* knn) {
+                                    const int2* flagged, const int* ids, int* knn) {
   __shared__ double sd[FB_THREADS];
   __shared__ int si[FB_THREADS];
   __shared__ int st[FB_THREADS];
@@ -423,9 +447,10 @@ __global__ void knn_fallback_kernel(const double* X, int d, int kappa, const Knn
     ld[t] = DBL_MAX;
     li[t] = INT_MAX;
   }
-  for (int j = r_begin + threadIdx.x; j < r_end; j += FB_THREADS) {
-    if (j == i) continue;
-    double v = exact_sqdist(xi, X + (size_t)j * d, d);
+  for (int r = r_begin + threadIdx.x; r < r_end; r += FB_THREADS) {
+    if (r == i) continue;
+    double v = exact_sqdist(xi, X + (size_t)r * d, d);
+    const int j = ids ? ids[r] : r;
     if (!pair_less(v, j, ld[kappa - 1], li[kappa - 1])) continue;
     int b = kappa - 1;
     while (b > 0 && pair_less(v, j, ld[b - 1], li[b - 1])) {
@@ -455,16 +480,26 @@ __global__ void knn_fallback_kernel(const double* X, int d, int kappa, const Knn
     if (threadIdx.x == st[0]) ++head;
     __syncthreads();
   }
-  for (int t = threadIdx.x; t < kappa; t += FB_THREADS) knn[(size_t)i * kappa + t] = chosen[t];
+  const size_t orow = (size_t)(ids ? ids[i] : i);
+  for (int t = threadIdx.x; t < kappa; t += FB_THREADS) knn[orow * kappa + t] = chosen[t];
 }
+
+// Tile list of one prefilter pass: none (every block scans its whole range), or CSR
+// per block with the lists starting from the candidates of an earlier pass.
+struct TileList {
+  const int* tlist = nullptr;
+  const int* toff = nullptr;
+  int load_init = 0;
+};
 
 template <int D, int KP>
 void launch_prefilter(const float* Xc, const float* qn, const KnnTile* tiles, int ntiles, float* cd, int* ci,
-                      int* status, cudaStream_t st) {
+                      int* status, cudaStream_t st, TileList tl = TileList{}) {
   // at least 80 KB so that at most two blocks share an SM's 512 TMEM columns
   const size_t smem = std::max<size_t>(prefilter_smem<D>(), 80 * 1024);
   IA_CUDA(cudaFuncSetAttribute(knn_prefilter_kernel<D, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  knn_prefilter_kernel<D, KP><<<ntiles, KT_NTH, smem, st>>>(Xc, qn, tiles, cd, ci, status);
+  knn_prefilter_kernel<D, KP><<<ntiles, KT_NTH, smem, st>>>(Xc, qn, tiles, tl.tlist, tl.toff, tl.load_init, cd,
+                                                             ci, status);
   IA_LAUNCH_CHECK();
 }
 
@@ -473,16 +508,16 @@ int padded_dim(int d) { return (d + 7) / 8 * 8; }
 
 template <int KP>
 void prefilter_dispatch(const float* Xc, const float* qn, int d, const KnnTile* tl, int nt, float* cd, int* ci,
-                        int* status, cudaStream_t st) {
+                        int* status, cudaStream_t st, TileList list = TileList{}) {
   switch (padded_dim(d)) {
-    case 8: launch_prefilter<8, KP>(Xc, qn, tl, nt, cd, ci, status, st); break;
-    case 16: launch_prefilter<16, KP>(Xc, qn, tl, nt, cd, ci, status, st); break;
-    case 24: launch_prefilter<24, KP>(Xc, qn, tl, nt, cd, ci, status, st); break;
-    case 32: launch_prefilter<32, KP>(Xc, qn, tl, nt, cd, ci, status, st); break;
-    case 40: launch_prefilter<40, KP>(Xc, qn, tl, nt, cd, ci, status, st); break;
-    case 48: launch_prefilter<48, KP>(Xc, qn, tl, nt, cd, ci, status, st); break;
-    case 56: launch_prefilter<56, KP>(Xc, qn, tl, nt, cd, ci, status, st); break;
-    case 64: launch_prefilter<64, KP>(Xc, qn, tl, nt, cd, ci, status, st); break;
+    case 8: launch_prefilter<8, KP>(Xc, qn, tl, nt, cd, ci, status, st, list); break;
+    case 16: launch_prefilter<16, KP>(Xc, qn, tl, nt, cd, ci, status, st, list); break;
+    case 24: launch_prefilter<24, KP>(Xc, qn, tl, nt, cd, ci, status, st, list); break;
+    case 32: launch_prefilter<32, KP>(Xc, qn, tl, nt, cd, ci, status, st, list); break;
+    case 40: launch_prefilter<40, KP>(Xc, qn, tl, nt, cd, ci, status, st, list); break;
+    case 48: launch_prefilter<48, KP>(Xc, qn, tl, nt, cd, ci, status, st, list); break;
+    case 56: launch_prefilter<56, KP>(Xc, qn, tl, nt, cd, ci, status, st, list); break;
+    case 64: launch_prefilter<64, KP>(Xc, qn, tl, nt, cd, ci, status, st, list); break;
     default: throw Error(IASKIT_ERR_UNSUPPORTED, "kNN supports d <= 64");
   }
 }
@@ -524,13 +559,13 @@ int knn_run(const double* X, int d, int kappa, const std::vector<std::pair<int, 
   prefilter_dispatch<KP>(b.Xc, b.qn, d, b.tiles, nt, b.cd, b.ci, b.status, st);
   if (kappa <= 16)
     knn_rerank_kernel<KP, 16><<<nt, KT_QB, 0, st>>>(X, d, kappa, padded_dim(d), b.tiles, b.cd, b.ci, b.qn,
-                                                    b.rmax, knn, b.flagged, b.nfl);
+                                                    b.rmax, nullptr, nullptr, knn, b.flagged, b.nfl);
   else if (kappa <= 32)
     knn_rerank_kernel<KP, 32><<<nt, KT_QB, 0, st>>>(X, d, kappa, padded_dim(d), b.tiles, b.cd, b.ci, b.qn,
-                                                    b.rmax, knn, b.flagged, b.nfl);
+                                                    b.rmax, nullptr, nullptr, knn, b.flagged, b.nfl);
   else
     knn_rerank_kernel<KP, RR_MAXK><<<nt, KT_QB, 0, st>>>(X, d, kappa, padded_dim(d), b.tiles, b.cd, b.ci,
-                                                         b.qn, b.rmax, knn, b.flagged, b.nfl);
+                                                         b.qn, b.rmax, nullptr, nullptr, knn, b.flagged, b.nfl);
   IA_LAUNCH_CHECK();
   int nf = 0, dev_status = 0;
   IA_CUDA(cudaMemcpyAsync(&nf, b.nfl, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -538,10 +573,141 @@ int knn_run(const double* X, int d, int kappa, const std::vector<std::pair<int, 
   IA_CUDA(cudaStreamSynchronize(st));
   if (dev_status & DEV_TIMEOUT) throw Error(IASKIT_ERR_TIMEOUT, "kNN tensor-core wait expired");
   if (nf > 0) {
-    knn_fallback_kernel<<<nf, FB_THREADS, 0, st>>>(X, d, kappa, b.tiles, b.flagged, knn);
+    knn_fallback_kernel<<<nf, FB_THREADS, 0, st>>>(X, d, kappa, b.tiles, b.flagged, nullptr, knn);
     IA_LAUNCH_CHECK();
   }
   return nf;
+}
+
+// ----------------------------------------------------- tree-order search with pruning
+// The points are searched in the order of the tree permutation, where consecutive
+// rows are spatially close.  Each block of 128 queries first scans its seed window
+// (the aligned group of SEED_TILES point tiles around its own tile), which gives every
+// query an upper bound tau on its kappa-th distance; a point tile whose bounding box
+// lies farther than the block's largest tau from the block's own box cannot hold a
+// neighbour of any of its queries and is not scanned.
+constexpr int SEED_TILES = 8;
+
+// Bounding box (exact FP64 minimum and maximum per coordinate) of every 128-row tile:
+// box[g][0 .. d) = minima, box[g][d .. 2d) = maxima.
+__global__ void tile_box_kernel(const double* X, int d, const KnnTile* tiles, double* box) {
+  const KnnTile tl = tiles[blockIdx.x];
+  for (int k = threadIdx.x; k < d; k += blockDim.x) {
+    double lo = DBL_MAX, hi = -DBL_MAX;
+    for (int r = 0; r < tl.qn; ++r) {
+      const double v = X[(size_t)(tl.q0 + r) * d + k];
+      lo = fmin(lo, v);
+      hi = fmax(hi, v);
+    }
+    box[(size_t)blockIdx.x * 2 * d + k] = lo;
+    box[(size_t)blockIdx.x * 2 * d + d + k] = hi;
+  }
+}
+
+// tau[i] = the kappa-th smallest exact FP64 distance among the candidates of the seed
+// pass (an upper bound on the true kappa-th distance; DBL_MAX when fewer than kappa),
+// and Tq[g] = the largest tau of block g.
+template <int KP, int KAP>
+__global__ void knn_seed_bound_kernel(const double* X, int d, int kappa, const KnnTile* tiles,
+                                      const float* cand_d, const int* cand_i, const int* ids, double* tau,
+                                      double* Tq) {
+  __shared__ double red[KT_QB];
+  const KnnTile tl = tiles[blockIdx.x];
+  const int t = threadIdx.x;
+  double bound = 0.0;
+  if (t < tl.qn) {
+    const int i = tl.q0 + t;
+    double dd[KAP];
+    int ii[KAP];
+#pragma unroll
+    for (int u = 0; u < KAP; ++u) {
+      dd[u] = DBL_MAX;
+      ii[u] = INT_MAX;
+    }
+    const double* xi = X + (size_t)i * d;
+    const size_t o = (size_t)i * (KT_SUB * KP);
+    int found = 0;
+    for (int q = 0; q < KT_SUB; ++q)
+      for (int u = 0; u < KP; ++u) {
+        const int j = cand_i[o + (size_t)q * KP + u];
+        if (j == INT_MAX) break;
+        ++found;
+        double v = exact_sqdist(xi, X + (size_t)j * d, d);
+        int jj = ids[j];
+        if (!pair_less(v, jj, dd[kappa - 1], ii[kappa - 1])) continue;
+#pragma unroll
+        for (int w = 0; w < KAP; ++w) {
+          if (w >= kappa) break;
+          if (pair_less(v, jj, dd[w], ii[w])) {
+            const double tv = dd[w];
+            const int tj = ii[w];
+            dd[w] = v;
+            ii[w] = jj;
+            v = tv;
+            jj = tj;
+          }
+        }
+      }
+    bound = found >= kappa ? dd[kappa - 1] : DBL_MAX;
+    tau[i] = bound;
+  }
+  red[t] = bound;
+  __syncthreads();
+  for (int s = KT_QB / 2; s > 0; s >>= 1) {
+    if (t < s) red[t] = fmax(red[t], red[t + s]);
+    __syncthreads();
+  }
+  if (t == 0) Tq[blockIdx.x] = red[0];
+}
+
+// Point tiles that block g must scan after its seed window: every tile t of its problem
+// outside the window whose box's distance from g's box, a lower bound on every
+// query-to-point distance between them, is not above Tq[g].  The test is conservative
+// (the computed bound shrunk by 1e-10, the threshold grown by 1e-9), so a skipped tile
+// lies farther than tau from every query of g in exact FP64 too.  Counts only (tlist
+// null) or the list itself, in tile order, at toff[g].
+__global__ void knn_select_kernel(const KnnTile* tiles, const KnnTile* seed, const int* first_tile,
+                                  const double* box, int d, const double* Tq, const int* toff, int* cnt,
+                                  int* tlist) {
+  __shared__ int wcount[KT_QB / 32];
+  __shared__ int base_s;
+  const int g = blockIdx.x;
+  const KnnTile tl = tiles[g], sw = seed[g];
+  const int ft = first_tile[tl.prob];
+  const int nt = (tl.rn + KT_RB - 1) / KT_RB;
+  const int s0 = (sw.rb - tl.rb) / KT_RB, s1 = s0 + (sw.rn + KT_RB - 1) / KT_RB;
+  const double T = Tq[g] * (1.0 + 1e-9);
+  const double* bq = box + (size_t)g * 2 * d;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) base_s = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < nt; c0 += KT_QB) {
+    const int t = c0 + threadIdx.x;
+    bool take = false;
+    if (t < nt && (t < s0 || t >= s1)) {
+      const double* bp = box + (size_t)(ft + t) * 2 * d;
+      double lb = 0.0;
+      for (int k = 0; k < d; ++k) {
+        const double gap = fmax(0.0, fmax(bp[k] - bq[d + k], bq[k] - bp[d + k]));
+        lb += gap * gap;
+      }
+      take = !(lb * (1.0 - 1e-10) > T);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, take);
+    if (lane == 0) wcount[w] = __popc(m);
+    __syncthreads();
+    int off = base_s;
+    for (int ww = 0; ww < w; ++ww) off += wcount[ww];
+    if (take && tlist) tlist[toff[g] + off + __popc(m & ((1u << lane) - 1u))] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int ww = 0; ww < KT_QB / 32; ++ww) tot += wcount[ww];
+      base_s += tot;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && cnt) cnt[g] = base_s;
 }
 
 }  // namespace
@@ -589,6 +755,148 @@ int knn_bruteforce(const double* X, int N, int d, int kappa, int* knn,
   return KP == 16 ? knn_run<16>(X, d, kappa, problems, tiles, b, knn, st)
          : wide     ? knn_run<64>(X, d, kappa, problems, tiles, b, knn, st)
                     : knn_run<32>(X, d, kappa, problems, tiles, b, knn, st);
+}
+
+// Exact kNN lists of points held in tree order (see the pruning note above the
+// tile_box kernel).  Xp: N x d row-major FP64 rows in permuted order, perm[r] = the
+// original index of row r; problems = (first row, row count) in that order; knn is
+// written in original indices at original rows, bit for bit the lists of
+// knn_bruteforce on the original order.
+int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* knn,
+             const std::vector<std::pair<int, int>>& problems, KnnScratch& s, cudaStream_t st,
+             KnnPruneStats* pstats) {
+  ProfScope _ps(PK_KNN, st);
+  int min_n = N;
+  for (const auto& pr : problems) min_n = std::min(min_n, pr.second);
+  if (kappa < 1 || kappa > min_n - 1) throw Error(IASKIT_ERR_ARG, "kappa must be in [1, N-1]");
+  if (kappa > RR_MAXK) throw Error(IASKIT_ERR_UNSUPPORTED, "kappa > 48");
+  if (d > 64) throw Error(IASKIT_ERR_UNSUPPORTED, "kNN supports d <= 64");
+  const int np = (int)problems.size();
+  const std::vector<KnnTile> tiles = knn_tiles(problems);
+  const int nt = (int)tiles.size();
+  // seed windows and the first tile of every problem
+  std::vector<KnnTile> seed(tiles);
+  std::vector<int> first(np, 0);
+  for (int g = 0; g < nt; ++g) {
+    const KnnTile& t = tiles[g];
+    if (g == 0 || tiles[g - 1].prob != t.prob) first[t.prob] = g;
+    const int ntp = (t.rn + KT_RB - 1) / KT_RB;
+    const int local = (t.q0 - t.rb) / KT_RB;
+    const int w0 = local / SEED_TILES * SEED_TILES, w1 = std::min(ntp, w0 + SEED_TILES);
+    seed[g].rb = t.rb + w0 * KT_RB;
+    seed[g].rn = std::min(t.rb + t.rn, t.rb + w1 * KT_RB) - seed[g].rb;
+  }
+  const bool wide = kappa + 8 > 32;
+  const int KP = kappa <= 16 ? 16 : wide ? 64 : 32;
+  KnnBufs b{};
+  b.status = s.status.ensure_n<int>(1);
+  b.Xc = s.x32.ensure_n<float>((size_t)N * padded_dim(d));
+  b.qn = s.qnorm.ensure_n<float>(N);
+  b.part = s.part.ensure_n<double>((size_t)np * KC_CHUNKS * d);
+  b.mean = s.mean.ensure_n<double>((size_t)np * d);
+  b.rmax = s.rmax.ensure_n<unsigned>(np);
+  b.probs = s.probs.ensure_n<int2>(np);
+  b.tiles = s.tiles.ensure_n<KnnTile>(tiles.size());
+  b.cd = s.cand_d.ensure_n<float>((size_t)N * KT_SUB * KP);
+  b.ci = s.cand_i.ensure_n<int>((size_t)N * KT_SUB * KP);
+  b.flagged = s.flagged.ensure_n<int2>(N);
+  b.nfl = s.counter.ensure_n<int>(1);
+  KnnTile* seed_d = s.seed_tiles.ensure_n<KnnTile>(nt);
+  int* first_d = s.first.ensure_n<int>(np);
+  double* box = s.box.ensure_n<double>((size_t)nt * 2 * d);
+  double* tau = s.tau.ensure_n<double>(N);
+  double* Tq = s.tq.ensure_n<double>(nt);
+  int* cnt = s.cnt.ensure_n<int>(nt);
+  int* toff = s.toff.ensure_n<int>(nt + 1);
+  std::vector<int2> hp(np);
+  for (int q = 0; q < np; ++q) hp[q] = make_int2(problems[q].first, problems[q].second);
+  h2d(b.probs, hp.data(), np, st);
+  h2d(b.tiles, tiles.data(), tiles.size(), st);
+  h2d(seed_d, seed.data(), seed.size(), st);
+  h2d(first_d, first.data(), first.size(), st);
+  IA_CUDA(cudaMemsetAsync(b.rmax, 0, np * sizeof(unsigned), st));
+  IA_CUDA(cudaMemsetAsync(b.nfl, 0, sizeof(int), st));
+  IA_CUDA(cudaMemsetAsync(b.status, 0, sizeof(int), st));
+  center_partial_kernel<<<dim3(KC_CHUNKS, np), 64, 0, st>>>(Xp, d, b.probs, b.part);
+  IA_LAUNCH_CHECK();
+  center_mean_kernel<<<np, 64, 0, st>>>(d, b.probs, b.part, b.mean);
+  IA_LAUNCH_CHECK();
+  center_points_kernel<<<nt, KT_QB, 0, st>>>(Xp, d, padded_dim(d), b.tiles, b.mean, b.Xc, b.qn, b.rmax);
+  IA_LAUNCH_CHECK();
+  tile_box_kernel<<<nt, 64, 0, st>>>(Xp, d, b.tiles, box);
+  IA_LAUNCH_CHECK();
+  // 1. seed windows
+  auto prefilter = [&](const KnnTile* tl, TileList list) {
+    if (KP == 16) prefilter_dispatch<16>(b.Xc, b.qn, d, tl, nt, b.cd, b.ci, b.status, st, list);
+    else if (wide) prefilter_dispatch<64>(b.Xc, b.qn, d, tl, nt, b.cd, b.ci, b.status, st, list);
+    else prefilter_dispatch<32>(b.Xc, b.qn, d, tl, nt, b.cd, b.ci, b.status, st, list);
+  };
+  prefilter(seed_d, TileList{});
+  // 2. bounds and the tiles left to scan
+  auto seed_bound = [&](auto kp_tag, auto kap_tag) {
+    constexpr int kp = decltype(kp_tag)::value, kap = decltype(kap_tag)::value;
+    knn_seed_bound_kernel<kp, kap><<<nt, KT_QB, 0, st>>>(Xp, d, kappa, b.tiles, b.cd, b.ci, perm, tau, Tq);
+  };
+  using I16 = std::integral_constant<int, 16>;
+  using I32 = std::integral_constant<int, 32>;
+  using I48 = std::integral_constant<int, RR_MAXK>;
+  using I64 = std::integral_constant<int, 64>;
+  if (KP == 16) seed_bound(I16{}, I16{});
+  else if (!wide) seed_bound(I32{}, I32{});
+  else seed_bound(I64{}, I48{});
+  IA_LAUNCH_CHECK();
+  knn_select_kernel<<<nt, KT_QB, 0, st>>>(b.tiles, seed_d, first_d, box, d, Tq, nullptr, cnt, nullptr);
+  IA_LAUNCH_CHECK();
+  std::vector<int> hc(nt), ho(nt + 1, 0);
+  d2h(hc.data(), cnt, nt, st);
+  IA_CUDA(cudaStreamSynchronize(st));
+  int64_t total = 0;
+  double seed_pairs = 0.0, main_pairs = 0.0;
+  for (int g = 0; g < nt; ++g) {
+    ho[g] = (int)total;
+    total += hc[g];
+    seed_pairs += (double)tiles[g].qn * seed[g].rn;
+    main_pairs += (double)tiles[g].qn * KT_RB * hc[g];
+  }
+  if (total > INT_MAX) throw Error(IASKIT_ERR_UNSUPPORTED, "kNN tile list too long");
+  ho[nt] = (int)total;
+  prof().flops[PK_KNN] += 2.0 * (seed_pairs + main_pairs) * d;
+  if (pstats) {
+    pstats->tiles_scanned = total;
+    pstats->pairs_scanned = seed_pairs + main_pairs;
+    double all = 0.0;
+    for (const auto& pr : problems) all += (double)pr.second * pr.second;
+    pstats->pairs_all = all;
+  }
+  // 3. the selected tiles, continuing the seed lists
+  if (total > 0) {
+    h2d(toff, ho.data(), nt + 1, st);
+    int* tlist = s.tlist.ensure_n<int>((size_t)total);
+    knn_select_kernel<<<nt, KT_QB, 0, st>>>(b.tiles, seed_d, first_d, box, d, Tq, toff, nullptr, tlist);
+    IA_LAUNCH_CHECK();
+    prefilter(b.tiles, TileList{tlist, toff, 1});
+  }
+  // 4. exact re-rank (original indices), certified against the scanned and skipped points
+  if (kappa <= 16)
+    knn_rerank_kernel<16, 16><<<nt, KT_QB, 0, st>>>(Xp, d, kappa, padded_dim(d), b.tiles, b.cd, b.ci, b.qn,
+                                                    b.rmax, perm, tau, knn, b.flagged, b.nfl);
+  else if (!wide)
+    knn_rerank_kernel<32, 32><<<nt, KT_QB, 0, st>>>(Xp, d, kappa, padded_dim(d), b.tiles, b.cd, b.ci, b.qn,
+                                                    b.rmax, perm, tau, knn, b.flagged, b.nfl);
+  else
+    knn_rerank_kernel<64, RR_MAXK><<<nt, KT_QB, 0, st>>>(Xp, d, kappa, padded_dim(d), b.tiles, b.cd, b.ci,
+                                                         b.qn, b.rmax, perm, tau, knn, b.flagged, b.nfl);
+  IA_LAUNCH_CHECK();
+  int nf = 0, dev_status = 0;
+  d2h(&nf, b.nfl, 1, st);
+  d2h(&dev_status, b.status, 1, st);
+  IA_CUDA(cudaStreamSynchronize(st));
+  if (dev_status & DEV_TIMEOUT) throw Error(IASKIT_ERR_TIMEOUT, "kNN tensor-core wait expired");
+  if (nf > 0) {
+    knn_fallback_kernel<<<nf, FB_THREADS, 0, st>>>(Xp, d, kappa, b.tiles, b.flagged, perm, knn);
+    IA_LAUNCH_CHECK();
+  }
+  return nf;
 }
 
 }  // namespace iaskit

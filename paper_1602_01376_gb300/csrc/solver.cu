@@ -102,6 +102,9 @@ struct Options {
   // word just before the next status read, as a kernel's bounded wait or pivot check
   // would; one-shot (cleared once injected)
   int inject_status = 0;
+  // kNN: 1 = search in tree order with tile pruning (default), 0 = brute force over
+  // every pair; the lists are identical
+  int knn_prune = 1;
 };
 
 struct Prob {
@@ -128,15 +131,26 @@ struct Node {
           CR_off = 0, K_off = 0, U_off = 0;
 };
 
+// A refined column that stopped at its rounding floor: problem, column, its relative
+// residual and the floor estimate 2^-53 ||A|| ||w|| / ||u||, and whether the problem's
+// operator blocks were FP64 (else FP32 pairs, whose floor is about 2^9 higher).
+struct StagCol {
+  int prob, col;
+  double resid, floor;
+  bool op64;
+};
+
 struct Stats {
   double t_tree = 0, t_knn = 0, t_skel = 0, t_leaf_lu = 0, t_factor_levels = 0, t_factor = 0;
   double t_solve = 0, t_apply = 0;
   int knn_fallback = 0;
+  KnnPruneStats knn_prune;
   int64_t bytes_W = 0, bytes_LU = 0, bytes_P = 0, bytes_operator = 0;
   std::vector<double> refine_hist;
   int refine_sweeps = 0;
   int refine_iters = 0;       // GMRES iterations (operator applications) of the last solve
   int refine_stagnated = 0;   // columns stopped at the rounding floor of the FP64 operator
+  std::vector<StagCol> stagnated;  // those columns with their residual and floor estimate
   int fp64_problems = 0;      // problems factored in FP64
   int fp64_operator_problems = 0;  // mixed form: problems whose operator blocks stay in FP64
   int operator_upgrades = 0;       // of those, upgraded after their refinement stopped at the floor
@@ -788,8 +802,12 @@ class Solver {
       // a2: kNN inside every problem
       std::vector<std::pair<int, int>> probs;
       for (const Prob& P : pr) probs.emplace_back(P.pbase, P.N);
+      stats.knn_prune = KnnPruneStats{};
       stats.knn_fallback =
-          knn_bruteforce(Xd, Ntot, d, kappa, knn.ensure_n<int>((size_t)Ntot * kappa), probs, knn_s, st);
+          opt.knn_prune ? knn_tree(Xp.as<double>(), perm.as<int>(), Ntot, d, kappa,
+                                   knn.ensure_n<int>((size_t)Ntot * kappa), probs, knn_s, st, &stats.knn_prune)
+                        : knn_bruteforce(Xd, Ntot, d, kappa, knn.ensure_n<int>((size_t)Ntot * kappa), probs,
+                                         knn_s, st);
       IA_CUDA(cudaStreamSynchronize(st));
       const double t2 = now_ms();
       stats.t_knn = t2 - t1;
@@ -1900,6 +1918,7 @@ class Solver {
     stats.refine_hist.clear();
     stats.refine_sweeps = 0;
     stats.refine_stagnated = 0;
+    stats.stagnated.clear();
     const int sweeps = opt.refine > 0 ? opt.refine : (prec == PREC_MIXED ? 200 : 0);
     if (sweeps <= 0) {
       plain_solve(rhs, nrhs, rhs);
@@ -2043,6 +2062,21 @@ class Solver {
         stag_prob.assign(pr.size(), 0);
         for (int q = 0; q < S; ++q)
           if (state[q] == 2) stag_prob[q / nrhs] = 1;
+        // every stopped column beside the rounding floor of its residual: 2^-53 ||A|| ||w|| / ||u||
+        // with ||A|| ~ lambda + the largest sampled kernel row sum = lambda cond_est
+        stats.stagnated.clear();
+        if (stats.refine_stagnated > 0) {
+          std::vector<double> wn;
+          column_norms(w, nrhs, wn);
+          for (int q = 0; q < S; ++q)
+            if (state[q] == 2) {
+              const Prob& P = pr[q / nrhs];
+              const double anorm = P.lam > 0 ? P.lam * P.cond_est : HUGE_VAL;
+              const double rel = un[q] > 0 ? rn[q] / un[q] : rn[q];
+              stats.stagnated.push_back(
+                  StagCol{q / nrhs, q % nrhs, rel, 0x1p-53 * anorm * wn[q] / std::max(un[q], 1e-300), P.op64});
+            }
+        }
         return;
       }
       if (iters >= max_iters) throw Error(IASKIT_ERR_NOT_CONVERGED, "refinement did not converge");
@@ -2574,6 +2608,8 @@ int iaskit_set_option(const char* key, double value) {
       o.near_field = as_int(0, 1);
     } else if (k == "inject_status") {
       o.inject_status = as_int(0, 15);
+    } else if (k == "knn_prune") {
+      o.knn_prune = as_int(0, 1);
     } else if (k == "profile") {
       int v = as_int(0, 1);
       IA_CUDA(cudaStreamSynchronize(S().st));
@@ -2608,6 +2644,7 @@ int iaskit_get_option(const char* key, double* value) {
     else if (k == "pair_cond_max") *value = o.pair_cond_max;
     else if (k == "near_field") *value = o.near_field;
     else if (k == "inject_status") *value = o.inject_status;
+    else if (k == "knn_prune") *value = o.knn_prune;
     else throw Error(IASKIT_ERR_ARG, "unknown option " + k);
   });
 }
@@ -2638,6 +2675,13 @@ int iaskit_stats(char* buf, size_t len) {
     snprintf(tmp, sizeof tmp, "%s%.6g", i ? "," : "", s.stats.refine_hist[i]);
     j += tmp;
   }
+  j += "],\"stagnated\":[";
+  for (size_t i = 0; i < s.stats.stagnated.size() && i < 256; ++i) {
+    const StagCol& c = s.stats.stagnated[i];
+    snprintf(tmp, sizeof tmp, "%s{\"problem\":%d,\"column\":%d,\"residual\":%.4g,\"floor\":%.4g,\"op64\":%s}",
+             i ? "," : "", c.prob, c.col, c.resid, c.floor, c.op64 ? "true" : "false");
+    j += tmp;
+  }
   snprintf(tmp, sizeof tmp, "],\"refine_iters\":%d,\"refine_stagnated\":%d,\"fp64_problems\":%d,"
            "\"fp64_operator_problems\":%d,\"operator_upgrades\":%d,",
            s.stats.refine_iters, s.stats.refine_stagnated, s.stats.fp64_problems, s.stats.fp64_operator_problems,
@@ -2661,7 +2705,10 @@ int iaskit_stats(char* buf, size_t len) {
     snprintf(tmp, sizeof tmp, "%s%.17g", q ? "," : "", std::min(s.pr[q].cond_est, 1e300));
     j += tmp;
   }
-  j += "],\"launches\":";
+  snprintf(tmp, sizeof tmp, "],\"knn_pairs_scanned\":%.17g,\"knn_pairs_all\":%.17g,\"knn_tiles_listed\":%lld",
+           s.stats.knn_prune.pairs_scanned, s.stats.knn_prune.pairs_all, (long long)s.stats.knn_prune.tiles_scanned);
+  j += tmp;
+  j += ",\"launches\":";
   j += std::to_string(prof().launches);
   j += ",\"kernels\":{";
   for (int k = 0; k < PK_COUNT; ++k) {

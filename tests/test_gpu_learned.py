@@ -1,8 +1,9 @@
 """Learned row proposal: BF16 MLP kernels, candidates, features, selection, judge, labels.
 
 The GPU's BF16 MLP is compared with the FP64 oracle MLP on the same (BF16-rounded)
-inputs: scores and gradients within a few BF16 roundings (relative 2e-2 and 5e-2 of
-the norm), Adam's update exactly as the oracle's Adam applied to the GPU's gradient.
+inputs: scores and gradients within a few BF16 roundings, in norm (relative 2e-2 and
+5e-2) and element by element (4 2^-8 of the absolute-value network's output or
+gradient), Adam's update exactly as the oracle's Adam applied to the GPU's gradient.
 Integer parts (candidates, selection, held-out rows) are bit-exact; features within
 BF16 rounding; the held-out errors and the kept IDs match the oracle in FP64.
 """
@@ -46,12 +47,40 @@ def mlp(gpu_lib):
     return ia, ia.mlp_unpack(ia.iaskit_sampler_get_weights())
 
 
+# Element-by-element bounds: the GPU rounds the weights and the inputs of every layer
+# to BF16 (8 significant bits, relative error 2^-9 each) and accumulates in FP32, so
+# every output differs from the FP64 oracle's by at most a few 2^-8 of the same
+# network evaluated on absolute values with every unit active (an upper bound of the
+# sum of the absolute terms).  BF16_C = 4 covers the roundings of one layer's inputs,
+# weights and outputs plus the occasional unit whose pre-activation lies within
+# rounding of 0 and switches on one side only.
+BF16_C = 4 * 2.0 ** -8
+
+
+def _abs_net(p, X):
+    A1 = np.abs(X) @ np.abs(p["W1"]).T + np.abs(p["b1"])
+    A2 = A1 @ np.abs(p["W2"]).T + np.abs(p["b2"])
+    return A2 @ np.abs(p["w3"]) + abs(p["b3"][0]), A1, A2
+
+
+def _abs_grad(p, X, dy_abs):
+    y, A1, A2 = _abs_net(p, X)
+    dA2 = np.outer(dy_abs, np.abs(p["w3"]))
+    dA1 = dA2 @ np.abs(p["W2"])
+    return {"w3": A2.T @ dy_abs, "b3": np.array([dy_abs.sum()]), "W2": dA2.T @ A1, "b2": dA2.sum(axis=0),
+            "W1": dA1.T @ np.abs(X), "b1": dA1.sum(axis=0)}
+
+
 def test_mlp_forward_matches_oracle(mlp):
     ia, p = mlp
     F = _features(3000, 1)
     y = ia.iaskit_mlp_forward(F)
     ref, _ = OL.mlp_forward(p, bf16(F))
     assert _rel(y, ref) < 2e-2, _rel(y, ref)
+    bound = BF16_C * _abs_net(p, bf16(F))[0]
+    worst = np.max(np.abs(y - ref) / bound)
+    print(f"forward: largest error / element bound = {worst:.3f}")
+    assert worst <= 1.0
 
 
 def test_mlp_gradient_matches_oracle(mlp):
@@ -66,6 +95,12 @@ def test_mlp_gradient_matches_oracle(mlp):
     gg = ia.mlp_unpack(g)
     for k in gref:
         assert _rel(gg[k], gref[k]) < 5e-2, (k, _rel(gg[k], gref[k]))
+    # element by element: dy = 2 (y - t) / B is of one sign and size ~1 / B here
+    gabs = _abs_grad(p, bf16(F), np.abs(2.0 * (y - t) / t.size))
+    for k in gref:
+        worst = np.max(np.abs(np.asarray(gg[k]) - gref[k]) / (BF16_C * gabs[k] + 1e-30))
+        print(f"gradient {k}: largest error / element bound = {worst:.3f}")
+        assert worst <= 1.0, k
 
 
 def test_adam_steps_match_oracle(mlp):

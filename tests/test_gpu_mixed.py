@@ -86,7 +86,9 @@ def test_mixed_error_against_fp64_oracle(mixed_case):
     w64 = oracle.solve(F, c["u"])
     err = np.linalg.norm(c["w"] - w64) / np.linalg.norm(w64)
     print(f"mixed vs FP64 oracle: relative error {err:.3e}")
-    assert err < 1e-2
+    # measured 2.7e-8 .. 3.1e-7 on these cases (the mixed form's own skeletons and P
+    # define a slightly different K~); 10x margin
+    assert err < 3e-6
 
 
 def test_mixed_plain_solve_without_refinement_is_fp32_accurate(gpu_lib):
