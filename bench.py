@@ -329,19 +329,13 @@ def alu_peak_tflops(kernel: str, sm_mhz: float) -> tuple:
             f"derived: {SM_COUNT} SMs x {FP64_FMA_PER_CLK_PER_SM} FP64 FMA/clk x {sm_mhz:.0f} MHz")
 
 
-def run_batched(args, w, form):
+def batched_measure(w, form, steps, warmup, dist, rank, local, sample_clocks=True, with_e2e=True):
     """C3: all problems in one batched factor + solve per step vs one call per problem.
     Under torchrun every rank factors a batch of 64 problems of its own (weak scaling, no
     data-path exchange); the time is the largest over the ranks."""
     import torch
     import paper_1602_01376_gb300 as ia
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = dist_init("nccl")
-    ia.load()
-    ia.iaskit_set_stream(None)
     probs = batched_problems(count=64, seed=batch_seed(rank))
     Ns = [len(p[0]) for p in probs]
     hs = [p[1] for p in probs]
@@ -368,17 +362,17 @@ def run_batched(args, w, form):
             Uq.copy_(U0[offs[q]:offs[q + 1]].view(w.nrhs, Ns[q]))
             ia.iaskit_solve_device(Uq)
 
-    def timed(fn, sample_clocks):
-        for _ in range(args.warmup):
+    def timed(fn, clocks_on):
+        for _ in range(warmup):
             fn()
         ia.iaskit_set_option("profile", 1)
         l0 = ia.iaskit_stats()["launches"]
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier(dist)
         torch.cuda.synchronize()
-        with ClockSampler(local if sample_clocks else -1) as clk:
+        with ClockSampler(local if clocks_on else -1) as clk:
             ev0.record()
-            for _ in range(args.steps):
+            for _ in range(steps):
                 fn()
             ev1.record()
             torch.cuda.synchronize()
@@ -388,11 +382,10 @@ def run_batched(args, w, form):
         ms = max_over_ranks(dist, ev0.elapsed_time(ev1), "cuda")
         return ms, st, clk.summary(), st["launches"] - l0
 
-    ms_b, st_b, clocks, launches = timed(step_batched, True)
+    ms_b, st_b, clocks, launches = timed(step_batched, sample_clocks)
     ms_s, st_s, _, launches_s = timed(step_single, False)
-    nrhs_total = sum(w.nrhs for _ in Ns)
-    value = world * nrhs_total * args.steps / (ms_b / 1e3)
-    # residual of the batched solution against the FP64 operator
+    nrhs_total = w.nrhs * len(Ns)
+    # residual of the batched solution against the operator, every problem and column
     step_batched()
     AU = torch.empty_like(U)
     ia.iaskit_apply_device(U, AU, w.nrhs)
@@ -403,19 +396,55 @@ def run_batched(args, w, form):
         resid = max(resid, float(r.max()))
         above += int(float(r.max()) > 1e-10)
     st_last = ia.iaskit_stats()
-    # end to end: host points and right-hand sides through iaskit_factor_batched / solve_batched
-    Xh = [np.ascontiguousarray(p[0]) for p in probs]
-    Uh = [np.ascontiguousarray(U0[offs[q]:offs[q + 1]].cpu().numpy().reshape(w.nrhs, Ns[q]).T) for q in range(len(Ns))]
-    barrier(dist)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ia.iaskit_factor_batched(Xh, hs, lams, w.m, w.s_max, w.tol)
-    ia.iaskit_solve_batched(Uh)
-    e2e_s = max_over_ranks(dist, time.perf_counter() - t0, "cuda")
+    out = {"ms": ms_b, "stats": st_b, "clocks": clocks, "launches": launches, "ms_single": ms_s,
+           "launches_single": launches_s, "resid": resid, "above": above, "st_last": st_last,
+           "nrhs_total": nrhs_total, "Ns": Ns, "world": world}
+    if with_e2e:
+        # end to end: host points and right-hand sides through iaskit_factor_batched / solve_batched
+        Xh = [np.ascontiguousarray(p[0]) for p in probs]
+        Uh = [np.ascontiguousarray(U0[offs[q]:offs[q + 1]].cpu().numpy().reshape(w.nrhs, Ns[q]).T)
+              for q in range(len(Ns))]
+        barrier(dist)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ia.iaskit_factor_batched(Xh, hs, lams, w.m, w.s_max, w.tol)
+        ia.iaskit_solve_batched(Uh)
+        out["e2e_s"] = max_over_ranks(dist, time.perf_counter() - t0, "cuda")
+    return out
+
+
+def batched_summary(w, res, steps):
+    """The C3 figures of a batched_measure result (shared by the C3 line and the C3 entry
+    of the default line)."""
+    st = res["st_last"]
+    world = res["world"]
+    return {
+        "value": world * res["nrhs_total"] * steps / (res["ms"] / 1e3), "unit": UNIT,
+        "ms_per_step": res["ms"] / steps, "steps": steps, "residual": res["resid"],
+        "problems_above_1e-10": res["above"], "refine_stagnated_columns": st.get("refine_stagnated"),
+        "stagnated": st.get("stagnated"), "refine_gmres_iters": st.get("refine_iters"),
+        "fp64_problems": st.get("fp64_problems"), "fp64_operator_problems": st.get("fp64_operator_problems"),
+        "operator_upgrades": st.get("operator_upgrades"), "gpu_launches": res["launches"],
+        "compare_per_problem": {"value": world * res["nrhs_total"] * steps / (res["ms_single"] / 1e3),
+                                "ms_per_step": res["ms_single"] / steps,
+                                "gpu_launches": res["launches_single"]},
+    }
+
+
+def run_batched(args, w, form):
+    import torch
+    import paper_1602_01376_gb300 as ia
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = dist_init("nccl")
+    ia.load()
+    ia.iaskit_set_stream(None)
+    res = batched_measure(w, form, args.steps, args.warmup, dist, rank, local)
     if rank != 0:
         dist.destroy_process_group()
         return 0
-    kern = st_b["kernels"]
+    kern = res["stats"]["kernels"]
     top = max(kern, key=lambda k: kern[k]["ms"])
     pk, src = peaks()
     roof = None
@@ -426,28 +455,25 @@ def run_batched(args, w, form):
                 "frac": achieved / peak, "traffic": None, "kernel": top,
                 "peak_source": how, "launches": kern[top]["calls"],
                 "ms_total": kern[top]["ms"]}
+    world = res["world"]
     cfg = config_of(w)
     cfg["path"] = "batched " + form
     if world > 1:
         cfg["ranks"] = f"{world} ranks, each its own batch of 64 problems (seed + 1000 rank)"
+    summ = batched_summary(w, res, args.steps)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_b / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": summ["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": summ["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if form == "mixed" else "f64",
-        "data": "synthetic", "config": cfg, "residual": resid,
-        "problems_above_1e-10": above, "refine_stagnated_columns": st_last.get("refine_stagnated"),
-        "refine_gmres_iters": st_last.get("refine_iters"),
-        "fp64_problems": st_last.get("fp64_problems"),
-        "fp64_operator_problems": st_last.get("fp64_operator_problems"),
-        "operator_upgrades": st_last.get("operator_upgrades"), "gpu_launches": launches,
-        "clocks": clocks, "roofline": roof,
+        "data": "synthetic", "config": cfg, "clocks": res["clocks"], "roofline": roof,
         "kernel_ms_per_step": {k: round(v["ms"] / args.steps, 3) for k, v in kern.items() if v["ms"] > 0},
-        "compare_per_problem": {"value": world * nrhs_total * args.steps / (ms_s / 1e3),
-                                "ms_per_step": ms_s / args.steps, "gpu_launches": launches_s},
-        "e2e": {"value": world * nrhs_total / e2e_s, "unit": UNIT,
-                "h2d_bytes_per_step": 8 * sum(Ns) * (16 + w.nrhs),
-                "d2h_bytes_per_step": 8 * sum(Ns) * w.nrhs},
+        "e2e": {"value": world * res["nrhs_total"] / res["e2e_s"], "unit": UNIT,
+                "h2d_bytes_per_step": 8 * sum(res["Ns"]) * (16 + w.nrhs),
+                "d2h_bytes_per_step": 8 * sum(res["Ns"]) * w.nrhs},
     }
+    for k in ("residual", "problems_above_1e-10", "refine_stagnated_columns", "stagnated", "refine_gmres_iters",
+              "fp64_problems", "fp64_operator_problems", "operator_upgrades", "gpu_launches", "compare_per_problem"):
+        line[k] = summ[k]
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_entry(w)
     print(json.dumps(line))
@@ -468,6 +494,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other form")
     ap.add_argument("--N", type=int, default=None, help="override N (testing only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the C3 entry of the default line")
     args = ap.parse_args()
     w = workload(args.workload, N=args.N)
     if args.impl == "reference":
@@ -655,6 +682,14 @@ def main():
                                    for k, v in so["kernels"].items() if v["ms"] > 0}}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_entry(w)
+    if not args.no_batched:
+        # the batching workload (C3: 64 independent problems in one batched launch per
+        # level) on the same GPU, a few steps, beside the headline line
+        wb = workload("C3")
+        bsteps = min(args.steps, COMPARE_STEPS)
+        res = batched_measure(wb, "mixed", bsteps, 1, None, 0, local, sample_clocks=False, with_e2e=False)
+        line["batched_C3"] = dict(batched_summary(wb, res, bsteps), warmup=1,
+                                  workload=config_of(wb)["workload"])
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
