@@ -307,12 +307,50 @@ TENSOR_CLASS = {                     # tensor-core classes: nominal dense rate /
 }
 
 
-def roof_peak(kernel: str, pk: dict, src: str) -> tuple:
-    """(bound, peak TFLOP/s, how) for a kernel class."""
+def measure_gemm_peaks() -> dict:
+    """Dense TF32 and FP64 rates of this GPU, measured in this run with the library GEMM
+    (torch.matmul on cuBLAS: FP32 operands with TF32 allowed, 8192^3; FP64, 4096^3),
+    best of 10 after 3 warm-ups, CUDA events: the denominators of the tensor (TF32) and
+    FP64 roofline fractions, as MEASURED_PEAKS.json's bf16 figure is for BF16."""
+    import torch
+    out = {}
+    saved = torch.backends.cuda.matmul.allow_tf32
+    try:
+        torch.backends.cuda.matmul.allow_tf32 = True
+        for name, dt, n in (("tf32_tflops", torch.float32, 8192), ("fp64_tflops", torch.float64, 4096)):
+            a = torch.randn(n, n, dtype=dt, device="cuda")
+            b = torch.randn(n, n, dtype=dt, device="cuda")
+            for _ in range(3):
+                torch.matmul(a, b)
+            best = float("inf")
+            for _ in range(10):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[name] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+            del a, b
+        torch.cuda.empty_cache()
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = saved
+    return out
+
+
+def roof_peak(kernel: str, pk: dict, src: str, gp: dict = None) -> tuple:
+    """(bound, peak TFLOP/s, how) for a kernel class; gp = measure_gemm_peaks()."""
+    gp = gp or {}
     if kernel in TENSOR_CLASS:
         ratio, dt = TENSOR_CLASS[kernel]
+        if dt == "TF32" and gp.get("tf32_tflops"):
+            return ("tensor", gp["tf32_tflops"],
+                    f"measured in this run: cuBLAS TF32 GEMM 8192^3 {gp['tf32_tflops']:.0f} TFLOP/s (burst)")
         return ("tensor", pk["bf16_tflops"] * ratio,
                 f"{src} bf16 {pk['bf16_tflops']:.0f} TFLOP/s x nominal {dt}/BF16 ratio {ratio:.3f}")
+    if kernel not in PEAK_CLASS and kernel != "gemm_pair" and gp.get("fp64_tflops"):
+        return ("alu", gp["fp64_tflops"],
+                f"measured in this run: cuBLAS FP64 GEMM 4096^3 {gp['fp64_tflops']:.2f} TFLOP/s (burst)")
     peak, how = alu_peak_tflops(kernel, pk.get("sm_max_mhz", 2070.0))
     return ("alu", peak, f"{how} ({src} max clock)")
 
@@ -450,7 +488,7 @@ def run_batched(args, w, form):
     roof = None
     if kern[top]["flops"] > 0 and kern[top]["ms"] > 0:
         achieved = kern[top]["flops"] / (kern[top]["ms"] / 1e3) / 1e12
-        bound, peak, how = roof_peak(top, pk, src)
+        bound, peak, how = roof_peak(top, pk, src, measure_gemm_peaks())
         roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "kernel": top,
                 "peak_source": how, "launches": kern[top]["calls"],
@@ -631,11 +669,21 @@ def main():
     roof = None
     if kern[top]["flops"] > 0 and kern[top]["ms"] > 0:
         achieved = kern[top]["flops"] / (kern[top]["ms"] / 1e3) / 1e12      # TFLOP/s
-        bound, peak, how = roof_peak(top, pk, src)
+        gp = measure_gemm_peaks()
+        bound, peak, how = roof_peak(top, pk, src, gp)
         roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "kernel": top,
                 "peak_source": how,
                 "launches": kern[top]["calls"], "ms_total": kern[top]["ms"]}
+        # every class against the peak of its pipe and type
+        roof["by_class"] = {}
+        for k, v in kern.items():
+            if v["ms"] > 0 and v["flops"] > 0:
+                b_k, p_k, _ = roof_peak(k, pk, src, gp)
+                a_k = v["flops"] / (v["ms"] / 1e3) / 1e12
+                roof["by_class"][k] = {"ms_per_step": round(v["ms"] / args.steps, 3), "achieved": round(a_k, 3),
+                                       "peak": round(p_k, 2), "frac": round(a_k / p_k, 4), "bound": b_k}
+        roof["measured_peaks"] = gp
     st = chosen["stats"]
     cfg = config_of(w)
     cfg["path"] = ("mixed: FP32 factorization, FP64 pivots and operator, refined to 1e-10; "

@@ -212,8 +212,9 @@ int iaskit_predict_device(const double* d_test, int64_t M, const double* d_w, in
  *   "pair_cond_max" mixed precision: the operator blocks (leaf blocks, U, P) are
  *                  evaluated and applied as FP32 pairs (hi + lo, about 2^-44 relative
  *                  per entry), except for problems whose condition estimate exceeds
- *                  this, which keep them in FP64 (1e6, the default "mixed_cond_max",
- *                  so that problems factored in FP64 keep them in FP64).  When a solve's
+ *                  this, which keep them in FP64 (default 1e4: the pair operator's
+ *                  residual floor, about 0.2 x 2^-44 x the estimate, meets the default
+ *                  1e-10 target there; problems factored in FP64 are above it).  When a solve's
  *                  refinement stops at the pair operator's rounding floor above
  *                  "refine_tol", those problems' blocks are re-evaluated in FP64 and the
  *                  solve is refined again ("operator_upgrades" in iaskit_stats) [>= 1]

@@ -49,6 +49,9 @@ struct KnnScratch {
   }
 };
 
+// Rows per prefilter tile of the kNN search (and leaf size of its search-order tree).
+constexpr int KNN_TILE = 128;
+
 // What the pruned search scanned: point tiles after the seed windows, query-point
 // pairs scanned in all, and the pairs of a brute-force search.
 struct KnnPruneStats {

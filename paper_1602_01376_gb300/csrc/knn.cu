@@ -588,9 +588,10 @@ int knn_run(const double* X, int d, int kappa, const std::vector<std::pair<int, 
 // neighbour of any of its queries and is not scanned.
 constexpr int SEED_TILES = 8;
 
-// Bounding box (exact FP64 minimum and maximum per coordinate) of every 128-row tile:
-// box[g][0 .. d) = minima, box[g][d .. 2d) = maxima.
-__global__ void tile_box_kernel(const double* X, int d, const KnnTile* tiles, double* box) {
+// Bounding box of every 128-row tile in FP32, rounded outward (minima rounded down,
+// maxima up, so the box contains the FP64 points): box[g][0 .. d) = minima,
+// box[g][d .. 2d) = maxima.
+__global__ void tile_box_kernel(const double* X, int d, const KnnTile* tiles, float* box) {
   const KnnTile tl = tiles[blockIdx.x];
   for (int k = threadIdx.x; k < d; k += blockDim.x) {
     double lo = DBL_MAX, hi = -DBL_MAX;
@@ -599,8 +600,8 @@ __global__ void tile_box_kernel(const double* X, int d, const KnnTile* tiles, do
       lo = fmin(lo, v);
       hi = fmax(hi, v);
     }
-    box[(size_t)blockIdx.x * 2 * d + k] = lo;
-    box[(size_t)blockIdx.x * 2 * d + d + k] = hi;
+    box[(size_t)blockIdx.x * 2 * d + k] = __double2float_rd(lo);
+    box[(size_t)blockIdx.x * 2 * d + d + k] = __double2float_ru(hi);
   }
 }
 
@@ -662,12 +663,14 @@ __global__ void knn_seed_bound_kernel(const double* X, int d, int kappa, const K
 
 // Point tiles that block g must scan after its seed window: every tile t of its problem
 // outside the window whose box's distance from g's box, a lower bound on every
-// query-to-point distance between them, is not above Tq[g].  The test is conservative
-// (the computed bound shrunk by 1e-10, the threshold grown by 1e-9), so a skipped tile
-// lies farther than tau from every query of g in exact FP64 too.  Counts only (tlist
-// null) or the list itself, in tile order, at toff[g].
+// query-to-point distance between them, is not above Tq[g].  The bound is formed in FP32
+// with every operation rounded down (gaps, squares, sums) from the outward-rounded
+// boxes, and compared with Tq (1 + 1e-9) rounded up, so a skipped tile lies farther
+// than tau from every query of g in exact arithmetic, and so (by more than the FP64
+// rounding of a squared distance) in the FP64 distances that define the lists.  Counts
+// only (tlist null) or the list itself, in tile order, at toff[g].
 __global__ void knn_select_kernel(const KnnTile* tiles, const KnnTile* seed, const int* first_tile,
-                                  const double* box, int d, const double* Tq, const int* toff, int* cnt,
+                                  const float* box, int d, const double* Tq, const int* toff, int* cnt,
                                   int* tlist) {
   __shared__ int wcount[KT_QB / 32];
   __shared__ int base_s;
@@ -676,8 +679,8 @@ __global__ void knn_select_kernel(const KnnTile* tiles, const KnnTile* seed, con
   const int ft = first_tile[tl.prob];
   const int nt = (tl.rn + KT_RB - 1) / KT_RB;
   const int s0 = (sw.rb - tl.rb) / KT_RB, s1 = s0 + (sw.rn + KT_RB - 1) / KT_RB;
-  const double T = Tq[g] * (1.0 + 1e-9);
-  const double* bq = box + (size_t)g * 2 * d;
+  const float T = __double2float_ru(Tq[g] * (1.0 + 1e-9));
+  const float* bq = box + (size_t)g * 2 * d;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (threadIdx.x == 0) base_s = 0;
   __syncthreads();
@@ -685,13 +688,13 @@ __global__ void knn_select_kernel(const KnnTile* tiles, const KnnTile* seed, con
     const int t = c0 + threadIdx.x;
     bool take = false;
     if (t < nt && (t < s0 || t >= s1)) {
-      const double* bp = box + (size_t)(ft + t) * 2 * d;
-      double lb = 0.0;
+      const float* bp = box + (size_t)(ft + t) * 2 * d;
+      float lb = 0.0f;
       for (int k = 0; k < d; ++k) {
-        const double gap = fmax(0.0, fmax(bp[k] - bq[d + k], bq[k] - bp[d + k]));
-        lb += gap * gap;
+        const float gap = fmaxf(0.0f, fmaxf(__fsub_rd(bp[k], bq[d + k]), __fsub_rd(bq[k], bp[d + k])));
+        lb = __fadd_rd(lb, __fmul_rd(gap, gap));
       }
-      take = !(lb * (1.0 - 1e-10) > T);
+      take = !(lb > T);
     }
     const unsigned m = __ballot_sync(0xffffffffu, take);
     if (lane == 0) wcount[w] = __popc(m);
@@ -803,7 +806,7 @@ int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* kn
   b.nfl = s.counter.ensure_n<int>(1);
   KnnTile* seed_d = s.seed_tiles.ensure_n<KnnTile>(nt);
   int* first_d = s.first.ensure_n<int>(np);
-  double* box = s.box.ensure_n<double>((size_t)nt * 2 * d);
+  float* box = s.box.ensure_n<float>((size_t)nt * 2 * d);
   double* tau = s.tau.ensure_n<double>(N);
   double* Tq = s.tq.ensure_n<double>(nt);
   int* cnt = s.cnt.ensure_n<int>(nt);

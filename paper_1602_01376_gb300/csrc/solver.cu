@@ -90,10 +90,11 @@ struct Options {
   int gemm_tc = 1;            // FP32 products with more than 16 columns on the tensor cores (3xTF32)
   int cpqr_cluster = 1;       // FP32 IDs of up to 512 x 512 on a cluster of blocks per node
   // mixed form: problems whose condition estimate exceeds this keep their operator
-  // blocks in FP64 from the start (by default those factored in FP64); any other
-  // problem whose refinement stops at the FP32-pair operator's rounding floor is
-  // upgraded to FP64 and refined again
-  double pair_cond_max = 1e6;
+  // blocks in FP64 from the start; any other problem whose refinement stops at the
+  // FP32-pair operator's rounding floor is upgraded to FP64 and refined again.  The
+  // pair operator's floor was measured at about 0.2 x 2^-44 x cond_est (4.6e-9 at
+  // cond_est 4.7e5), so 1e4 is where it meets the default 1e-10 target
+  double pair_cond_max = 1e4;
   // operator: 0 = lambda I + K~ (i not in alpha), 1 = lambda I + K~ + S, the kNN-separated
   // operator of eq. (askit); the factorization (of lambda I + K~) then preconditions the
   // refinement's GMRES
@@ -374,6 +375,7 @@ class Solver {
   DevBuf DInv32;  // FP32 LUs: inverses of their 32 x 32 diagonal blocks and pivot permutations
   DevBuf rhs_keep;  // mixed form: the right-hand side, for a refinement after an operator upgrade
   DevBuf pred_part, pred_io;  // kernel sums at test points: chunk partials; host-call staging
+  DevBuf kperm, kiperm, Xk;   // kNN search order (tree of 128-point leaves) and its points
   std::vector<char> stag_prob;  // per problem: a column of the last refinement stopped at its floor
   TreeScratch tree_s;
   KnnScratch knn_s;
@@ -803,11 +805,52 @@ class Solver {
       std::vector<std::pair<int, int>> probs;
       for (const Prob& P : pr) probs.emplace_back(P.pbase, P.N);
       stats.knn_prune = KnnPruneStats{};
-      stats.knn_fallback =
-          opt.knn_prune ? knn_tree(Xp.as<double>(), perm.as<int>(), Ntot, d, kappa,
-                                   knn.ensure_n<int>((size_t)Ntot * kappa), probs, knn_s, st, &stats.knn_prune)
-                        : knn_bruteforce(Xd, Ntot, d, kappa, knn.ensure_n<int>((size_t)Ntot * kappa), probs,
-                                         knn_s, st);
+      if (opt.knn_prune) {
+        // the search runs in the order of a finer tree of the same splitting rule, with
+        // leaves of at most 128 points (one prefilter tile), so that every tile is a
+        // compact box; its first levels are the levels of the method's tree
+        std::vector<TreeLevel> kl;
+        std::vector<std::vector<std::pair<int, int>>> cur(pr.size());
+        int depth = 0;
+        for (size_t q = 0; q < pr.size(); ++q) {
+          cur[q] = {{pr[q].pbase, pr[q].N}};
+          int Lq = 0;
+          while ((pr[q].N + (1 << Lq) - 1) / (1 << Lq) > KNN_TILE) ++Lq;
+          depth = std::max(depth, Lq);
+        }
+        for (int l = 0; l < depth; ++l) {
+          TreeLevel lv;
+          for (size_t q = 0; q < pr.size(); ++q) {
+            std::vector<std::pair<int, int>> nxt;
+            const bool splits = std::any_of(cur[q].begin(), cur[q].end(),
+                                            [](const std::pair<int, int>& n) { return n.second > KNN_TILE; });
+            if (!splits) {  // finished: one pass-through node for the whole problem
+              lv.off.push_back(pr[q].pbase);
+              lv.kleft.push_back(pr[q].N);
+              lv.split.push_back(0);
+              continue;
+            }
+            for (const auto& n : cur[q]) {
+              lv.off.push_back(n.first);
+              lv.kleft.push_back(n.second / 2);
+              lv.split.push_back(1);
+              nxt.push_back({n.first, n.second / 2});
+              nxt.push_back({n.first + n.second / 2, n.second - n.second / 2});
+            }
+            cur[q] = nxt;
+          }
+          lv.off.push_back(Ntot);
+          kl.push_back(lv);
+        }
+        int* kp = kperm.ensure_n<int>(Ntot);
+        build_tree(Xd, Ntot, d, kl, kp, tree_s, st);
+        permute_points(Xd, kp, Ntot, d, kiperm.ensure_n<int>(Ntot), Xk.ensure_n<double>((size_t)Ntot * d), st);
+        stats.knn_fallback = knn_tree(Xk.as<double>(), kp, Ntot, d, kappa, knn.ensure_n<int>((size_t)Ntot * kappa),
+                                      probs, knn_s, st, &stats.knn_prune);
+      } else {
+        stats.knn_fallback =
+            knn_bruteforce(Xd, Ntot, d, kappa, knn.ensure_n<int>((size_t)Ntot * kappa), probs, knn_s, st);
+      }
       IA_CUDA(cudaStreamSynchronize(st));
       const double t2 = now_ms();
       stats.t_knn = t2 - t1;
@@ -2342,7 +2385,7 @@ class Solver {
                      &l_feat, &l_score, &l_linfo, &l_samp, &l_rk, &l_Ptmp, &l_sktmp, &l_hold, &l_err,
                      &l_cols, &l_gram, &l_dense, &mlp_master, &mlp_m, &mlp_v, &mlp_grad, &mlp_b16,
                      &mlp_loss, &tr_feat, &tr_tgt, &tr_lev, &tr_bx, &tr_bt, &tr_y, &tr_H1, &tr_H2, &tr_idx,
-                     &xnrm, &pred_part, &pred_io};
+                     &xnrm, &pred_part, &pred_io, &kperm, &kiperm, &Xk};
     mlp_ready = false;
     for (DevBuf* b : all) b->release();
     tree_s.release();

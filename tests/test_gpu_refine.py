@@ -7,9 +7,14 @@
   "mixed_cond_max", and every column of a batch mixing both precisions is refined.
 * A target below the FP64 rounding floor of the residual ends with the columns marked
   "stagnated" instead of spending the whole iteration budget.
+* A refinement that stops at the FP32-pair operator's floor upgrades that problem's
+  operator blocks to FP64; a later refactor for a new lambda still solves to the
+  target against the operator at that lambda.
 """
 import numpy as np
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -139,9 +144,44 @@ def test_pair_operator_floor_upgrades_to_fp64(mixed_opts):
         w = ia.iaskit_solve(u)
         st = ia.iaskit_stats()
     finally:
-        ia.iaskit_set_option("pair_cond_max", 1e6)
+        ia.iaskit_set_option("pair_cond_max", 1e4)
     print("upgrades", st["operator_upgrades"], "history", st["refine_history"])
     assert st["operator_upgrades"] == 1 and st["fp64_operator_problems"] == 1
     Au = ia.iaskit_apply(w)
     rho = (np.linalg.norm(u - Au, axis=0) / np.linalg.norm(u, axis=0)).max()
     assert rho <= 1e-10 or (st["refine_stagnated"] >= 1 and rho <= 1e-9), rho
+
+
+def test_refactor_after_an_operator_upgrade(mixed_opts):
+    """After a solve whose refinement upgraded the operator blocks to FP64, a refactor
+    for a new lambda re-chooses every problem's precisions from 1 + r / lambda' and forms
+    the leaf blocks, U, W and Z again: the next solve meets the target against the
+    operator at the new lambda, checked by the oracle on the library's own skeletons."""
+    from oracle.askit import Skeletons
+    ia = mixed_opts
+    X = _uniform(2400, 35)
+    u = np.random.default_rng(37).standard_normal((len(X), 2))
+    h, m = 1.2, 128
+    ia.iaskit_set_option("refine", 400)
+    ia.iaskit_set_option("pair_cond_max", 1e300)
+    try:
+        ia.iaskit_factor(X, h, 1e-3, m, 64, 1e-6)
+        ia.iaskit_solve(u)
+        assert ia.iaskit_stats()["operator_upgrades"] == 1
+        for lam2 in (1e-1, 1e-3):
+            ia.iaskit_refactor(lam2)
+            w = ia.iaskit_solve(u)
+            st = ia.iaskit_stats()
+            tree = oracle.build_tree(X, m)
+            sk = Skeletons(tree=tree, Xp=X[tree.perm], h=h)
+            ranks = ia.iaskit_get_ranks()
+            for l in range(1, tree.L + 1):
+                for i in range(1 << l):
+                    sk.skel[(l, i)] = ia.iaskit_get_skeleton(l, i).astype(np.int64)
+                    sk.P[(l, i)] = ia.iaskit_get_P(l, i, int(ranks[(1 << l) + i]))
+            rho = oracle.residual(sk, lam2, w, u)
+            print(f"lambda' {lam2}: residual {rho:.3e}, upgrades {st['operator_upgrades']}, "
+                  f"history {st['refine_history']}")
+            assert rho <= 1e-10 or (st["refine_stagnated"] >= 1 and rho <= 1e-9), (lam2, rho)
+    finally:
+        ia.iaskit_set_option("pair_cond_max", 1e4)
