@@ -121,10 +121,11 @@ int iaskit_refactor(const double* lambda, int nprob);
  * corrections from restarted flexible GMRES on A z = r right-preconditioned by the
  * stored factorization M^-1, w += Z y with Z the kept vectors M^-1 v_j (FGMRES-IR).
  * A column is done when ||r||/||u|| <= "refine_tol", or when a cycle whose GMRES
- * estimate met 0.1 "refine_tol" lowered the recomputed residual by less than half:
- * the FP64 rounding floor of the residual (about 1e-16 ||A|| ||w|| / ||u||) is then
- * above the target; iaskit_stats reports such columns as "refine_stagnated" and the
- * last residuals in "refine_history".
+ * estimate met 0.1 "refine_tol" lowered the recomputed residual by less than half, or
+ * left it more than 100 times above that estimate: the rounding floor of the residual
+ * (about 1e-16 ||A|| ||w|| / ||u|| in FP64) is then above the target; iaskit_stats
+ * reports such columns as "refine_stagnated", each with its residual and that floor
+ * estimate in "stagnated", and the last residuals in "refine_history".
  * "refine" bounds the total GMRES iterations; when they are spent with a column still
  * open the call returns IASKIT_ERR_NOT_CONVERGED and w holds the last iterate.
  * Errors: IASKIT_ERR_NOT_FACTORED, _ARG, _INPUT, _NOT_CONVERGED, _NOMEM, _CUDA.
@@ -212,9 +213,9 @@ int iaskit_predict_device(const double* d_test, int64_t M, const double* d_w, in
  *   "pair_cond_max" mixed precision: the operator blocks (leaf blocks, U, P) are
  *                  evaluated and applied as FP32 pairs (hi + lo, about 2^-44 relative
  *                  per entry), except for problems whose condition estimate exceeds
- *                  this, which keep them in FP64 (default 1e4: the pair operator's
- *                  residual floor, about 0.2 x 2^-44 x the estimate, meets the default
- *                  1e-10 target there; problems factored in FP64 are above it).  When a solve's
+ *                  this, which keep them in FP64 (default 1e5: measured pair floors
+ *                  were below 4e-13 at estimate 1.9e4 and 4.6e-9 at 4.5e5, against
+ *                  the default 1e-10 target; problems factored in FP64 are above it).  When a solve's
  *                  refinement stops at the pair operator's rounding floor above
  *                  "refine_tol", those problems' blocks are re-evaluated in FP64 and the
  *                  solve is refined again ("operator_upgrades" in iaskit_stats) [>= 1]
@@ -232,12 +233,13 @@ int iaskit_predict_device(const double* d_test, int64_t M, const double* d_w, in
  *                  alone inverts lambda I + K~ only.  0: lambda I + K~ (default)
  *                  [any time after a factorization]
  *   "problem"      which problem of a batch the introspection calls report (0) [any time]
- *   "knn_prune"    1: the kNN lists are searched with the points in tree order: each
- *                  block of 128 queries scans its seed window of spatially close rows,
- *                  then only the 128-point tiles whose bounding boxes come within its
- *                  queries' largest kappa-th seed distance; the skipped tiles enter the
- *                  certification of the exact re-rank (default).  0: every pair is
- *                  scanned.  The lists are identical either way [any time]
+ *   "knn_prune"    1: the kNN lists are searched with the points in the order of a
+ *                  tree with leaves of at most 128 points: each block of 128 queries
+ *                  scans the 8 tiles whose bounding boxes lie nearest its own, then
+ *                  only the tiles whose boxes come within its queries' largest kappa-th
+ *                  distance so far; the skipped tiles enter the certification of the
+ *                  exact re-rank (default).  0: every pair is scanned.  The lists are
+ *                  identical either way [any time]
  *   "inject_status" failure-path test hook: device status flags (1 zero pivot, 2
  *                  non-finite input, 4 internal bound, 8 expired bounded wait) that the
  *                  host ORs into the library's device status word just before its next

@@ -40,11 +40,11 @@ void permute_points(const double* X, const int* perm, int N, int d, int* iperm, 
 
 // ------------------------------------------------------------------- kNN (a2)
 struct KnnScratch {
-  DevBuf x32, qnorm, part, mean, rmax, probs, cand_d, cand_i, flagged, counter, tiles, status, seed_tiles, first,
-      box, tau, tq, cnt, toff, tlist;
+  DevBuf x32, qnorm, part, mean, rmax, probs, cand_d, cand_i, flagged, counter, tiles, status, seed_tiles, seeds,
+      first, box, tau, tq, cnt, toff, tlist;
   void release() {
     for (DevBuf* b : {&x32, &qnorm, &part, &mean, &rmax, &probs, &cand_d, &cand_i, &flagged, &counter,
-                      &tiles, &status, &seed_tiles, &first, &box, &tau, &tq, &cnt, &toff, &tlist})
+                      &tiles, &status, &seed_tiles, &seeds, &first, &box, &tau, &tq, &cnt, &toff, &tlist})
       b->release();
   }
 };
@@ -78,10 +78,11 @@ int knn_bruteforce(const double* X, int N, int d, int kappa, int* knn,
 
 // The same lists (bit for bit) from points held in tree order, Xp = X[perm] (perm[r] =
 // original index of row r, problems as row ranges of Xp), by the tensor-core prefilter
-// over each query block's seed window of spatially close rows, then only over the
-// point tiles whose bounding boxes come within the block's bound (an exact upper bound
-// on its queries' kappa-th distances); the skipped tiles enter the certification of
-// the exact re-rank.  Returns the number of queries redone by the exact scan.
+// over each 128-query block's seed tiles (the 8 tiles whose bounding boxes lie nearest
+// its own), then only over the tiles whose boxes come within the block's bound (an
+// exact upper bound on its queries' kappa-th distances); the skipped tiles enter the
+// certification of the exact re-rank.  Returns the number of queries redone by the
+// exact scan.
 int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* knn,
              const std::vector<std::pair<int, int>>& problems, KnnScratch& s, cudaStream_t st,
              KnnPruneStats* pstats = nullptr);

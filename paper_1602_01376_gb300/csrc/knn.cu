@@ -580,13 +580,24 @@ int knn_run(const double* X, int d, int kappa, const std::vector<std::pair<int, 
 }
 
 // ----------------------------------------------------- tree-order search with pruning
-// The points are searched in the order of the tree permutation, where consecutive
-// rows are spatially close.  Each block of 128 queries first scans its seed window
-// (the aligned group of SEED_TILES point tiles around its own tile), which gives every
-// query an upper bound tau on its kappa-th distance; a point tile whose bounding box
+// The points are searched in the order of a tree with leaves of at most 128 points, so
+// every 128-row tile is a compact box.  Each block of 128 queries first scans its seed
+// tiles (the SEED_TILES tiles whose boxes lie nearest to its own, its own first), which
+// gives every query an upper bound tau on its kappa-th distance; a point tile whose box
 // lies farther than the block's largest tau from the block's own box cannot hold a
 // neighbour of any of its queries and is not scanned.
 constexpr int SEED_TILES = 8;
+
+// FP32 lower bound of the squared distance between two boxes (minima, then maxima),
+// every operation rounded down.
+__device__ __forceinline__ float box_lower_bound(const float* a, const float* b, int d) {
+  float lb = 0.0f;
+  for (int k = 0; k < d; ++k) {
+    const float gap = fmaxf(0.0f, fmaxf(__fsub_rd(b[k], a[d + k]), __fsub_rd(a[k], b[d + k])));
+    lb = __fadd_rd(lb, __fmul_rd(gap, gap));
+  }
+  return lb;
+}
 
 // Bounding box of every 128-row tile in FP32, rounded outward (minima rounded down,
 // maxima up, so the box contains the FP64 points): box[g][0 .. d) = minima,
@@ -602,6 +613,68 @@ __global__ void tile_box_kernel(const double* X, int d, const KnnTile* tiles, fl
     }
     box[(size_t)blockIdx.x * 2 * d + k] = __double2float_rd(lo);
     box[(size_t)blockIdx.x * 2 * d + d + k] = __double2float_ru(hi);
+  }
+}
+
+// Seed tiles of block g: the min(SEED_TILES, tiles of its problem) tiles whose boxes have
+// the smallest lower bound from g's box, by (bound, tile index), g's own tile first;
+// written as local tile indices at soff[g].
+__global__ void knn_seed_pick_kernel(const KnnTile* tiles, const int* first_tile, const float* box, int d,
+                                     const int* soff, int* seeds) {
+  __shared__ float hv[KT_QB];
+  __shared__ int ht[KT_QB], hs[KT_QB];
+  __shared__ int chosen_s;
+  const int g = blockIdx.x;
+  const KnnTile tl = tiles[g];
+  const int ft = first_tile[tl.prob];
+  const int nt = (tl.rn + KT_RB - 1) / KT_RB;
+  const int ns = min(SEED_TILES, nt);
+  const float* bq = box + (size_t)g * 2 * d;
+  float lv[SEED_TILES];
+  int lt[SEED_TILES];
+#pragma unroll
+  for (int u = 0; u < SEED_TILES; ++u) {
+    lv[u] = FLT_MAX;
+    lt[u] = INT_MAX;
+  }
+  for (int t = threadIdx.x; t < nt; t += KT_QB) {
+    float v = ft + t == g ? -1.0f : box_lower_bound(bq, box + (size_t)(ft + t) * 2 * d, d);
+    int tt = t;
+#pragma unroll
+    for (int u = 0; u < SEED_TILES; ++u) {  // sorted insertion by (bound, index)
+      const bool less = v < lv[u] || (v == lv[u] && tt < lt[u]);
+      const float pv = lv[u];
+      const int pt = lt[u];
+      lv[u] = less ? v : pv;
+      lt[u] = less ? tt : pt;
+      v = less ? pv : v;
+      tt = less ? pt : tt;
+    }
+  }
+  int head = 0;
+  for (int r = 0; r < ns; ++r) {  // ns rounds of a block-wide argmin over the list heads
+    hv[threadIdx.x] = head < SEED_TILES ? lv[head] : FLT_MAX;
+    ht[threadIdx.x] = head < SEED_TILES ? lt[head] : INT_MAX;
+    hs[threadIdx.x] = threadIdx.x;
+    __syncthreads();
+    for (int w = KT_QB / 2; w > 0; w >>= 1) {
+      if (threadIdx.x < w) {
+        const int o = threadIdx.x + w;
+        if (hv[o] < hv[threadIdx.x] || (hv[o] == hv[threadIdx.x] && ht[o] < ht[threadIdx.x])) {
+          hv[threadIdx.x] = hv[o];
+          ht[threadIdx.x] = ht[o];
+          hs[threadIdx.x] = hs[o];
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      seeds[soff[g] + r] = ht[0];
+      chosen_s = hs[0];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x == chosen_s) ++head;
+    __syncthreads();
   }
 }
 
@@ -661,40 +734,38 @@ __global__ void knn_seed_bound_kernel(const double* X, int d, int kappa, const K
   if (t == 0) Tq[blockIdx.x] = red[0];
 }
 
-// Point tiles that block g must scan after its seed window: every tile t of its problem
-// outside the window whose box's distance from g's box, a lower bound on every
+// Point tiles that block g must scan after its seed tiles: every other tile t of its
+// problem whose box's distance from g's box, a lower bound on every
 // query-to-point distance between them, is not above Tq[g].  The bound is formed in FP32
 // with every operation rounded down (gaps, squares, sums) from the outward-rounded
 // boxes, and compared with Tq (1 + 1e-9) rounded up, so a skipped tile lies farther
 // than tau from every query of g in exact arithmetic, and so (by more than the FP64
 // rounding of a squared distance) in the FP64 distances that define the lists.  Counts
 // only (tlist null) or the list itself, in tile order, at toff[g].
-__global__ void knn_select_kernel(const KnnTile* tiles, const KnnTile* seed, const int* first_tile,
+__global__ void knn_select_kernel(const KnnTile* tiles, const int* soff, const int* seeds, const int* first_tile,
                                   const float* box, int d, const double* Tq, const int* toff, int* cnt,
                                   int* tlist) {
   __shared__ int wcount[KT_QB / 32];
   __shared__ int base_s;
+  __shared__ int sd[SEED_TILES];
   const int g = blockIdx.x;
-  const KnnTile tl = tiles[g], sw = seed[g];
+  const KnnTile tl = tiles[g];
   const int ft = first_tile[tl.prob];
   const int nt = (tl.rn + KT_RB - 1) / KT_RB;
-  const int s0 = (sw.rb - tl.rb) / KT_RB, s1 = s0 + (sw.rn + KT_RB - 1) / KT_RB;
+  const int ns = soff[g + 1] - soff[g];
   const float T = __double2float_ru(Tq[g] * (1.0 + 1e-9));
   const float* bq = box + (size_t)g * 2 * d;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (threadIdx.x == 0) base_s = 0;
+  if ((int)threadIdx.x < ns) sd[threadIdx.x] = seeds[soff[g] + threadIdx.x];
   __syncthreads();
   for (int c0 = 0; c0 < nt; c0 += KT_QB) {
     const int t = c0 + threadIdx.x;
     bool take = false;
-    if (t < nt && (t < s0 || t >= s1)) {
-      const float* bp = box + (size_t)(ft + t) * 2 * d;
-      float lb = 0.0f;
-      for (int k = 0; k < d; ++k) {
-        const float gap = fmaxf(0.0f, fmaxf(__fsub_rd(bp[k], bq[d + k]), __fsub_rd(bq[k], bp[d + k])));
-        lb = __fadd_rd(lb, __fmul_rd(gap, gap));
-      }
-      take = !(lb > T);
+    if (t < nt) {
+      bool seeded = false;
+      for (int r = 0; r < ns; ++r) seeded = seeded || sd[r] == t;
+      take = !seeded && !(box_lower_bound(bq, box + (size_t)(ft + t) * 2 * d, d) > T);
     }
     const unsigned m = __ballot_sync(0xffffffffu, take);
     if (lane == 0) wcount[w] = __popc(m);
@@ -777,17 +848,12 @@ int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* kn
   const int np = (int)problems.size();
   const std::vector<KnnTile> tiles = knn_tiles(problems);
   const int nt = (int)tiles.size();
-  // seed windows and the first tile of every problem
-  std::vector<KnnTile> seed(tiles);
-  std::vector<int> first(np, 0);
+  // seed list offsets and the first tile of every problem
+  std::vector<int> first(np, 0), soff(nt + 1, 0);
   for (int g = 0; g < nt; ++g) {
     const KnnTile& t = tiles[g];
     if (g == 0 || tiles[g - 1].prob != t.prob) first[t.prob] = g;
-    const int ntp = (t.rn + KT_RB - 1) / KT_RB;
-    const int local = (t.q0 - t.rb) / KT_RB;
-    const int w0 = local / SEED_TILES * SEED_TILES, w1 = std::min(ntp, w0 + SEED_TILES);
-    seed[g].rb = t.rb + w0 * KT_RB;
-    seed[g].rn = std::min(t.rb + t.rn, t.rb + w1 * KT_RB) - seed[g].rb;
+    soff[g + 1] = soff[g] + std::min(SEED_TILES, (t.rn + KT_RB - 1) / KT_RB);
   }
   const bool wide = kappa + 8 > 32;
   const int KP = kappa <= 16 ? 16 : wide ? 64 : 32;
@@ -804,7 +870,8 @@ int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* kn
   b.ci = s.cand_i.ensure_n<int>((size_t)N * KT_SUB * KP);
   b.flagged = s.flagged.ensure_n<int2>(N);
   b.nfl = s.counter.ensure_n<int>(1);
-  KnnTile* seed_d = s.seed_tiles.ensure_n<KnnTile>(nt);
+  int* soff_d = s.seed_tiles.ensure_n<int>(nt + 1);
+  int* seeds_d = s.seeds.ensure_n<int>(soff[nt]);
   int* first_d = s.first.ensure_n<int>(np);
   float* box = s.box.ensure_n<float>((size_t)nt * 2 * d);
   double* tau = s.tau.ensure_n<double>(N);
@@ -815,7 +882,7 @@ int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* kn
   for (int q = 0; q < np; ++q) hp[q] = make_int2(problems[q].first, problems[q].second);
   h2d(b.probs, hp.data(), np, st);
   h2d(b.tiles, tiles.data(), tiles.size(), st);
-  h2d(seed_d, seed.data(), seed.size(), st);
+  h2d(soff_d, soff.data(), soff.size(), st);
   h2d(first_d, first.data(), first.size(), st);
   IA_CUDA(cudaMemsetAsync(b.rmax, 0, np * sizeof(unsigned), st));
   IA_CUDA(cudaMemsetAsync(b.nfl, 0, sizeof(int), st));
@@ -828,13 +895,15 @@ int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* kn
   IA_LAUNCH_CHECK();
   tile_box_kernel<<<nt, 64, 0, st>>>(Xp, d, b.tiles, box);
   IA_LAUNCH_CHECK();
-  // 1. seed windows
-  auto prefilter = [&](const KnnTile* tl, TileList list) {
-    if (KP == 16) prefilter_dispatch<16>(b.Xc, b.qn, d, tl, nt, b.cd, b.ci, b.status, st, list);
-    else if (wide) prefilter_dispatch<64>(b.Xc, b.qn, d, tl, nt, b.cd, b.ci, b.status, st, list);
-    else prefilter_dispatch<32>(b.Xc, b.qn, d, tl, nt, b.cd, b.ci, b.status, st, list);
+  // 1. seed tiles: the nearest boxes
+  knn_seed_pick_kernel<<<nt, KT_QB, 0, st>>>(b.tiles, first_d, box, d, soff_d, seeds_d);
+  IA_LAUNCH_CHECK();
+  auto prefilter = [&](TileList list) {
+    if (KP == 16) prefilter_dispatch<16>(b.Xc, b.qn, d, b.tiles, nt, b.cd, b.ci, b.status, st, list);
+    else if (wide) prefilter_dispatch<64>(b.Xc, b.qn, d, b.tiles, nt, b.cd, b.ci, b.status, st, list);
+    else prefilter_dispatch<32>(b.Xc, b.qn, d, b.tiles, nt, b.cd, b.ci, b.status, st, list);
   };
-  prefilter(seed_d, TileList{});
+  prefilter(TileList{seeds_d, soff_d, 0});
   // 2. bounds and the tiles left to scan
   auto seed_bound = [&](auto kp_tag, auto kap_tag) {
     constexpr int kp = decltype(kp_tag)::value, kap = decltype(kap_tag)::value;
@@ -848,7 +917,7 @@ int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* kn
   else if (!wide) seed_bound(I32{}, I32{});
   else seed_bound(I64{}, I48{});
   IA_LAUNCH_CHECK();
-  knn_select_kernel<<<nt, KT_QB, 0, st>>>(b.tiles, seed_d, first_d, box, d, Tq, nullptr, cnt, nullptr);
+  knn_select_kernel<<<nt, KT_QB, 0, st>>>(b.tiles, soff_d, seeds_d, first_d, box, d, Tq, nullptr, cnt, nullptr);
   IA_LAUNCH_CHECK();
   std::vector<int> hc(nt), ho(nt + 1, 0);
   d2h(hc.data(), cnt, nt, st);
@@ -858,7 +927,7 @@ int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* kn
   for (int g = 0; g < nt; ++g) {
     ho[g] = (int)total;
     total += hc[g];
-    seed_pairs += (double)tiles[g].qn * seed[g].rn;
+    seed_pairs += (double)tiles[g].qn * KT_RB * (soff[g + 1] - soff[g]);
     main_pairs += (double)tiles[g].qn * KT_RB * hc[g];
   }
   if (total > INT_MAX) throw Error(IASKIT_ERR_UNSUPPORTED, "kNN tile list too long");
@@ -875,9 +944,9 @@ int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* kn
   if (total > 0) {
     h2d(toff, ho.data(), nt + 1, st);
     int* tlist = s.tlist.ensure_n<int>((size_t)total);
-    knn_select_kernel<<<nt, KT_QB, 0, st>>>(b.tiles, seed_d, first_d, box, d, Tq, toff, nullptr, tlist);
+    knn_select_kernel<<<nt, KT_QB, 0, st>>>(b.tiles, soff_d, seeds_d, first_d, box, d, Tq, toff, nullptr, tlist);
     IA_LAUNCH_CHECK();
-    prefilter(b.tiles, TileList{tlist, toff, 1});
+    prefilter(TileList{tlist, toff, 1});
   }
   // 4. exact re-rank (original indices), certified against the scanned and skipped points
   if (kappa <= 16)

@@ -91,10 +91,10 @@ struct Options {
   int cpqr_cluster = 1;       // FP32 IDs of up to 512 x 512 on a cluster of blocks per node
   // mixed form: problems whose condition estimate exceeds this keep their operator
   // blocks in FP64 from the start; any other problem whose refinement stops at the
-  // FP32-pair operator's rounding floor is upgraded to FP64 and refined again.  The
-  // pair operator's floor was measured at about 0.2 x 2^-44 x cond_est (4.6e-9 at
-  // cond_est 4.7e5), so 1e4 is where it meets the default 1e-10 target
-  double pair_cond_max = 1e4;
+  // FP32-pair operator's rounding floor is upgraded to FP64 and refined again.  Measured
+  // pair floors: below 4e-13 at condition estimate 1.9e4 (mixture in d 54), 4.6e-9 at
+  // 4.5e5 (manifold in d 64), against the default 1e-10 target
+  double pair_cond_max = 1e5;
   // operator: 0 = lambda I + K~ (i not in alpha), 1 = lambda I + K~ + S, the kNN-separated
   // operator of eq. (askit); the factorization (of lambda I + K~) then preconditions the
   // refinement's GMRES
@@ -2091,9 +2091,12 @@ class Solver {
         if (!std::isfinite(rel)) throw Error(IASKIT_ERR_NOT_CONVERGED, "refinement produced a non-finite residual");
         worst = std::max(worst, rel);
         if (state[q] == 0) {
+          // at the floor: the cycle's own GMRES estimate met 0.1 refine_tol, and the
+          // recomputed residual either fell by less than half or lies a hundred times
+          // above that estimate (FGMRES's estimate is the true residual up to rounding)
           if (rel <= opt.refine_tol) state[q] = 1;
           else if (!first && est_end[q] <= 0.1 * opt.refine_tol * std::max(un[q], 1e-300) &&
-                   rn[q] > 0.5 * prev[q])
+                   (rn[q] > 0.5 * prev[q] || rn[q] > 100.0 * est_end[q]))
             state[q] = 2;
         }
         prev[q] = rn[q];

@@ -144,7 +144,7 @@ def test_pair_operator_floor_upgrades_to_fp64(mixed_opts):
         w = ia.iaskit_solve(u)
         st = ia.iaskit_stats()
     finally:
-        ia.iaskit_set_option("pair_cond_max", 1e4)
+        ia.iaskit_set_option("pair_cond_max", 1e5)
     print("upgrades", st["operator_upgrades"], "history", st["refine_history"])
     assert st["operator_upgrades"] == 1 and st["fp64_operator_problems"] == 1
     Au = ia.iaskit_apply(w)
@@ -184,4 +184,4 @@ def test_refactor_after_an_operator_upgrade(mixed_opts):
                   f"history {st['refine_history']}")
             assert rho <= 1e-10 or (st["refine_stagnated"] >= 1 and rho <= 1e-9), (lam2, rho)
     finally:
-        ia.iaskit_set_option("pair_cond_max", 1e4)
+        ia.iaskit_set_option("pair_cond_max", 1e5)
