@@ -367,6 +367,30 @@ int iaskit_get_learned(int level, int index, int32_t* cand, float* feat, float* 
                        double* info);
 
 /*
+ * Autotuning of the grouped GEMM (the batched products of the factorization, the solve
+ * and the operator apply; the paper has no counterpart: a tile-shape table of this
+ * library).  Its CUDA-core tile shapes, 0 = 64 x 64, 1 = 256 x 16, 3 = 128 x 32 and
+ * 4 = 512 x 8 (FP32 only), all sum each output over k in the same order, so a shape
+ * changes the speed of a launch and never its result.  A launch that is not on the
+ * tensor cores or on FP32 pairs takes the shape of its bucket:
+ *   fp64      1 for FP64 products, 0 for FP32;
+ *   n_bucket  0 .. 5: the launch's largest column count N in (8 << (b-1), 8 << b]
+ *             (bucket 0 up to 8, bucket 5 above 128);
+ *   m_bucket  0 .. 4: its largest row count M in (128 << (b-1), 128 << b]
+ *             (bucket 0 up to 128, bucket 4 above 1024).
+ * iaskit_gemm_tile installs `shape` for a bucket (-1 removes the entry; without an
+ * entry the default rule holds: 256 x 16 up to 16 columns, else 64 x 64).
+ * iaskit_tune_gemm times one grouped launch of `count` M x N x K problems (zero data,
+ * library scratch) with `shape`: *ms = mean milliseconds over `reps` launches after
+ * one warm-up.  The binding's autotune module sweeps every bucket with it and writes
+ * the table that the binding installs when it loads the library.
+ * Errors: IASKIT_ERR_ARG (bad bucket, a shape this type lacks, sizes above 4 GB),
+ * _NOMEM, _CUDA.
+ */
+int iaskit_gemm_tile(int fp64, int n_bucket, int m_bucket, int shape);
+int iaskit_tune_gemm(int fp64, int M, int N, int K, int count, int shape, int reps, double* ms);
+
+/*
  * The kNN lists of iaskit_factor (same order, same ties, bit for bit) for callers
  * that must not allocate device memory: for example a serving process whose
  * device memory is entirely handed out by its own pool allocator, or a caller

@@ -41,6 +41,7 @@ EXPORTS = [
     "iaskit_solve_batched_device", "iaskit_sampler_train", "iaskit_sampler_set_weights",
     "iaskit_sampler_get_weights", "iaskit_mlp_forward", "iaskit_mlp_train_step", "iaskit_get_learned",
     "iaskit_kernel_block", "iaskit_refactor", "iaskit_predict", "iaskit_predict_device",
+    "iaskit_gemm_tile", "iaskit_tune_gemm",
 ]
 
 MLP_NPARAM = 17793
@@ -95,6 +96,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "iaskit_refactor": ([vp, i32], i32),
         "iaskit_predict": ([vp, i64, vp, i32, vp], i32),
         "iaskit_predict_device": ([vp, i64, vp, i32, vp], i32),
+        "iaskit_gemm_tile": ([i32, i32, i32, i32], i32),
+        "iaskit_tune_gemm": ([i32, i32, i32, i32, i32, i32, i32, _c_double_p], i32),
         "iaskit_solve_batched": ([vp, i32], i32),
         "iaskit_solve_batched_device": ([vp, i32], i32),
         "iaskit_sampler_train": ([vp, i64, i32, dbl, i32, i32, dbl, i32, dbl], i32),
@@ -110,6 +113,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         fn.argtypes = args
         fn.restype = res
     _lib = lib
+    load_tile_table()   # the committed autotuned grouped-GEMM tile shapes, when present
     return lib
 
 
@@ -269,6 +273,41 @@ def iaskit_predict_device(test_points, w, scores, nrhs=None) -> None:
         nrhs = 1 if w.dim() == 1 else w.shape[0]
     _check(load().iaskit_predict_device(_dev_ptr(test_points), test_points.shape[0], _dev_ptr(w), nrhs,
                                         _dev_ptr(scores)))
+
+
+GEMM_SHAPES = {"64x64": 0, "256x16": 1, "128x32": 3, "512x8": 4}
+
+
+def iaskit_gemm_tile(fp64: bool, n_bucket: int, m_bucket: int, shape) -> None:
+    """Install (or with shape None clear) the CUDA-core tile shape of one bucket of the
+    grouped-GEMM tile table."""
+    code = -1 if shape is None else GEMM_SHAPES[shape] if isinstance(shape, str) else int(shape)
+    _check(load().iaskit_gemm_tile(int(bool(fp64)), n_bucket, m_bucket, code))
+
+
+def iaskit_tune_gemm(fp64: bool, M: int, N: int, K: int, count: int, shape, reps: int = 5) -> float:
+    """Milliseconds of one grouped CUDA-core GEMM launch of `count` M x N x K problems."""
+    ms = ctypes.c_double()
+    code = GEMM_SHAPES[shape] if isinstance(shape, str) else int(shape)
+    _check(load().iaskit_tune_gemm(int(bool(fp64)), M, N, K, count, code, reps, ctypes.byref(ms)))
+    return ms.value
+
+
+TILE_TABLE = os.path.join(_HERE, "gemm_tiles.json")
+
+
+def load_tile_table(path: str = TILE_TABLE) -> int:
+    """Install the committed autotuned tile table (written by the autotune module);
+    returns the number of entries installed (0 without a table)."""
+    if not os.path.exists(path):
+        return 0
+    with open(path) as f:
+        table = json.load(f)
+    n = 0
+    for e in table["entries"]:
+        iaskit_gemm_tile(e["fp64"], e["n_bucket"], e["m_bucket"], e["shape"])
+        n += 1
+    return n
 
 
 def iaskit_set_option(key: str, value: float) -> None:

@@ -1827,7 +1827,7 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(const GemmDescT<T>* des
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   // the FP32 64 x 64 tiles (only used without the tensor-core GEMM) keep the plain loop:
   // the test below costs them a register spill
-  constexpr bool SKIP = sizeof(T) == 8 || TN == 16;
+  constexpr bool SKIP = sizeof(T) == 8 || TN <= 32;
   const bool live = !SKIP || (m0 + 4 * tx < D.M && n0 + 4 * ty < D.N);
   T acc[4][4];
 #pragma unroll
@@ -1879,6 +1879,15 @@ __global__ void __launch_bounds__(G_THREADS) gemm_kernel(const GemmDescT<T>* des
         *cp = D.beta == 0.0 ? alpha * acc[r][c] : alpha * acc[r][c] + beta * *cp;
       }
     }
+}
+
+// 512 x 8 tiles exist for FP32 only (the FP64 A tile would exceed static shared memory).
+template <typename T>
+void gemm_narrow(const GemmDescT<T>* descs_dev, const GemmTile* tiles_dev, int ntiles, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value)
+    gemm_kernel<float, 512, 8><<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
+  else
+    throw Error(IASKIT_ERR_ARG, "512 x 8 tiles are FP32 only");
 }
 
 // ---------------------------------------------------------------- small helpers
@@ -2197,8 +2206,13 @@ void gemm_grouped(const GemmDescT<T>* descs_dev, const GemmTile* tiles_dev, int 
     IA_LAUNCH_CHECK();
     return;
   }
+  if (!gemm_shape_valid(shape, sizeof(T) == 8)) throw Error(IASKIT_ERR_ARG, "tile shape not available");
   if (shape == GEMM_SKINNY)
     gemm_kernel<T, 256, 16><<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
+  else if (shape == GEMM_WIDE)
+    gemm_kernel<T, 128, 32><<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
+  else if (shape == GEMM_NARROW)
+    gemm_narrow<T>(descs_dev, tiles_dev, ntiles, st);
   else
     gemm_kernel<T, 64, 64><<<ntiles, G_THREADS, 0, st>>>(descs_dev, tiles_dev);
   IA_LAUNCH_CHECK();

@@ -41,10 +41,11 @@ void permute_points(const double* X, const int* perm, int N, int d, int* iperm, 
 // ------------------------------------------------------------------- kNN (a2)
 struct KnnScratch {
   DevBuf x32, qnorm, part, mean, rmax, probs, cand_d, cand_i, flagged, counter, tiles, status, seed_tiles, seeds,
-      first, box, tau, tq, cnt, toff, tlist;
+      first, box, tau, tq, cnt, toff, tlist, rec, tnorm;
   void release() {
     for (DevBuf* b : {&x32, &qnorm, &part, &mean, &rmax, &probs, &cand_d, &cand_i, &flagged, &counter,
-                      &tiles, &status, &seed_tiles, &seeds, &first, &box, &tau, &tq, &cnt, &toff, &tlist})
+                      &tiles, &status, &seed_tiles, &seeds, &first, &box, &tau, &tq, &cnt, &toff, &tlist, &rec,
+                      &tnorm})
       b->release();
   }
 };
@@ -232,16 +233,40 @@ struct GemmDescT {
   int M, N, K, lda, ldb, ldc;
   double alpha, beta;
 };
-// Work items (descriptor index, tile row, tile column).  Tile shape: 64 x 64
-// (GEMM_SQUARE), 256 x 16 (GEMM_SKINNY, every problem with N <= 16) or 128 x 128
-// (GEMM_TC).
+// Work items (descriptor index, tile row, tile column).  Tile shapes: 64 x 64
+// (GEMM_SQUARE), 256 x 16 (GEMM_SKINNY), 128 x 128 (GEMM_TC), 128 x 32 (GEMM_WIDE) and
+// 512 x 8 (GEMM_NARROW, FP32 only).  Every CUDA-core shape sums each output over k in
+// the same order, so they give identical results; the autotuner picks among them.
 struct GemmTile {
   int desc, tm, tn;
 };
 // GEMM_TC: 128 x 128 tiles on the tensor cores (tcgen05, 3xTF32), FP32 products only.
-enum GemmShape { GEMM_SQUARE = 0, GEMM_SKINNY = 1, GEMM_TC = 2 };
-inline int gemm_tile_m(GemmShape s) { return s == GEMM_SKINNY ? 256 : s == GEMM_TC ? 128 : 64; }
-inline int gemm_tile_n(GemmShape s) { return s == GEMM_SKINNY ? 16 : s == GEMM_TC ? 128 : 64; }
+enum GemmShape { GEMM_SQUARE = 0, GEMM_SKINNY = 1, GEMM_TC = 2, GEMM_WIDE = 3, GEMM_NARROW = 4 };
+constexpr int GEMM_NSHAPES = 5;
+inline int gemm_tile_m(GemmShape s) {
+  return s == GEMM_SKINNY ? 256 : s == GEMM_TC ? 128 : s == GEMM_WIDE ? 128 : s == GEMM_NARROW ? 512 : 64;
+}
+inline int gemm_tile_n(GemmShape s) {
+  return s == GEMM_SKINNY ? 16 : s == GEMM_TC ? 128 : s == GEMM_WIDE ? 32 : s == GEMM_NARROW ? 8 : 64;
+}
+// A CUDA-core shape the grouped GEMM of this element type supports.
+inline bool gemm_shape_valid(GemmShape s, bool fp64) {
+  return s == GEMM_SQUARE || s == GEMM_SKINNY || s == GEMM_WIDE || (s == GEMM_NARROW && !fp64);
+}
+// Autotuned CUDA-core tile shapes, keyed by element type and the launch's largest N and
+// M (buckets 0 .. GT_NB-1 of ceil(log2) above 8 resp. 128); -1 = no entry.
+constexpr int GT_NB = 6, GT_MB = 5;
+inline int gemm_n_bucket(int n) {
+  int b = 0;
+  while (b < GT_NB - 1 && n > (8 << b)) ++b;
+  return b;
+}
+inline int gemm_m_bucket(int m) {
+  int b = 0;
+  while (b < GT_MB - 1 && m > (128 << b)) ++b;
+  return b;
+}
+int& gemm_tuned(int fp64, int nb, int mb);
 // dev_status: device status word; a tensor-core tile whose bounded wait expires sets
 // DEV_TIMEOUT there and leaves its C tile unwritten.
 template <typename T>

@@ -338,6 +338,258 @@ __global__ void __launch_bounds__(KT_NTH) knn_prefilter_kernel(const float* Xc, 
   }
 }
 
+// ------------------------------------------------- prefilter on pre-split tile records
+// The tree-order search converts every 128-row tile once per call into a record: the
+// TF32 hi and lo parts of its centred FP32 rows in the operand layout of the tensor-core
+// descriptors (8-row x 16-byte core matrices), then (separately) the tile's 128 row
+// norms, rows past the tile's end zero.  A block then brings each point tile in with
+// one bulk copy (cp.async.bulk, mbarrier completion) instead of splitting it itself.
+template <int D>
+constexpr uint32_t rec_bytes() { return (uint32_t)(2 * KT_RB * D * 4); }
+
+template <int D>
+__global__ void knn_records_kernel(const float* Xc, const float* qnorm, const KnnTile* tiles, uint32_t* rec,
+                                   float* tnorm) {
+  constexpr int KC = D / 4;
+  const KnnTile tl = tiles[blockIdx.x];
+  uint32_t* H = rec + (size_t)blockIdx.x * (rec_bytes<D>() / 4);
+  uint32_t* L = H + KT_RB * D;
+  for (int e = threadIdx.x; e < KT_RB * KC; e += blockDim.x) {
+    const int g = e / (8 * KC), rem = e % (8 * KC);
+    const int kc = rem / 8, rr = rem % 8;
+    const int r = g * 8 + rr;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (r < tl.qn) v = *reinterpret_cast<const float4*>(Xc + (size_t)(tl.q0 + r) * D + kc * 4);
+    uint4 h, l;
+    h.x = tc::to_tf32(v.x);
+    h.y = tc::to_tf32(v.y);
+    h.z = tc::to_tf32(v.z);
+    h.w = tc::to_tf32(v.w);
+    l.x = tc::to_tf32(v.x - __uint_as_float(h.x));
+    l.y = tc::to_tf32(v.y - __uint_as_float(h.y));
+    l.z = tc::to_tf32(v.z - __uint_as_float(h.z));
+    l.w = tc::to_tf32(v.w - __uint_as_float(h.w));
+    const uint32_t w = (uint32_t)((g * KC + kc) * 32 + rr * 4);
+    *reinterpret_cast<uint4*>(H + w) = h;
+    *reinterpret_cast<uint4*>(L + w) = l;
+  }
+  for (int r = threadIdx.x; r < KT_RB; r += blockDim.x)
+    tnorm[(size_t)blockIdx.x * KT_RB + r] = r < tl.qn ? qnorm[tl.q0 + r] : 0.0f;
+}
+
+// The prefilter of knn_prefilter_kernel (same lists, same arithmetic) over tile records:
+// the query block is the record of its own tile; the point tile of step t (local index
+// tlist[..] or t, record first_tile[prob] + local) arrives by bulk copy into one of two
+// operand buffers, its norms into one of three slots.  Per step: wait for MMA t; thread
+// 0 starts the copy of tile t + 2 into the buffer MMA t has released, waits for tile
+// t + 1's copy and issues MMA t + 1 into the other accumulator; every thread scans
+// accumulator t; one barrier.  Waits are bounded; a wait that gives up sets DEV_TIMEOUT,
+// and the block stops issuing, waits (bounded) for its copies in flight and returns.
+template <int D>
+constexpr size_t prefilter2_smem() {
+  return (size_t)3 * rec_bytes<D>() + 3 * KT_RB * 4 + 8 * 8 + 64;
+}
+
+template <int D, int KP>
+__global__ void __launch_bounds__(KT_NTH) knn_prefilter2_kernel(const uint32_t* rec, const float* tnorm,
+                                                                const KnnTile* tiles, const int* first_tile,
+                                                                const int* tlist, const int* toff, int load_init,
+                                                                float* cand_d, int* cand_i, int* status) {
+  extern __shared__ __align__(1024) unsigned char kt_sh[];
+  constexpr uint32_t RB = rec_bytes<D>();
+  constexpr int OPW = KT_QB * D;  // 32-bit words of one operand (hi or lo)
+  uint32_t* Ah = reinterpret_cast<uint32_t*>(kt_sh);
+  uint32_t* Al = Ah + OPW;
+  uint32_t* B0 = Al + OPW;  // operand buffer b at B0 + 2 b OPW: hi, then lo
+  float* rn3 = reinterpret_cast<float*>(Al + OPW + 4 * OPW);     // [3][KT_RB]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(rn3 + 3 * KT_RB);  // A, B0, B1, M0, M1
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 8);
+  __shared__ int abort_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int lq = warp & 3, cq = warp >> 2;
+  const int qi = lq * 32 + lane;
+  const KnnTile tl = tiles[blockIdx.x];
+  const int my_q = tl.q0 + qi;
+  const bool active = qi < tl.qn;
+  const int rend = tl.rb + tl.rn;
+  const int lbeg = tlist ? toff[blockIdx.x] : 0;
+  const int ntile = tlist ? toff[blockIdx.x + 1] - lbeg : (tl.rn + KT_RB - 1) / KT_RB;
+  if (ntile == 0) return;  // block-uniform: nothing to scan, the lists stay as they are
+  const int ft = first_tile[tl.prob];
+  auto local = [&](int t) { return tlist ? tlist[lbeg + t] : t; };
+  auto load = [&](int t, int b) {  // thread 0: tile t into operand buffer b, norms into slot t % 3
+    const int r = ft + local(t);
+    tc::mbar_expect_tx(&bar[1 + b], RB + KT_RB * 4);
+    tc::bulk_g2s(B0 + 2 * b * OPW, rec + (size_t)r * (RB / 4), RB, &bar[1 + b]);
+    tc::bulk_g2s(rn3 + (t % 3) * KT_RB, tnorm + (size_t)r * KT_RB, KT_RB * 4, &bar[1 + b]);
+  };
+  if (warp == 0) tc::tmem_alloc(tslot, 2 * KT_RB);
+  if (tid == 0) {
+    for (int i = 0; i < 5; ++i) tc::mbar_init(&bar[i], 1);
+    abort_s = 0;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  // thread 0: copies started into / seen complete in each operand buffer
+  int issued0 = 0, issued1 = 0, waited0 = 0, waited1 = 0;
+  constexpr uint32_t idesc = tc::idesc_tf32(KT_QB, KT_RB);
+  constexpr uint32_t SBO = (D / 4) * 128;
+  auto issue = [&](int b) {
+    const uint32_t dt = tmem + (uint32_t)(b * KT_RB);
+#pragma unroll 1
+    for (int ks = 0; ks < D / 8; ++ks) {
+      const uint32_t ko = (uint32_t)ks * 256;
+      const uint64_t ah = tc::smem_desc(tc::smem_addr(Ah) + ko, 128, SBO);
+      const uint64_t al = tc::smem_desc(tc::smem_addr(Al) + ko, 128, SBO);
+      const uint64_t bh = tc::smem_desc(tc::smem_addr(B0 + 2 * b * OPW) + ko, 128, SBO);
+      const uint64_t bl = tc::smem_desc(tc::smem_addr(B0 + 2 * b * OPW + OPW) + ko, 128, SBO);
+      tc::mma_tf32(dt, al, bh, idesc, ks > 0);
+      tc::mma_tf32(dt, ah, bl, idesc, true);
+      tc::mma_tf32(dt, ah, bh, idesc, true);
+    }
+    tc::mma_commit(&bar[3 + b]);
+  };
+  if (tid == 0) {
+    tc::mbar_expect_tx(&bar[0], RB);
+    tc::bulk_g2s(Ah, rec + (size_t)blockIdx.x * (RB / 4), RB, &bar[0]);
+    load(0, 0);
+    issued0 = 1;
+    if (ntile > 1) {
+      load(1, 1);
+      issued1 = 1;
+    }
+    bool ok = tc::mbar_wait(&bar[0], 0, KT_WAIT) && tc::mbar_wait(&bar[1], 0, KT_WAIT);
+    if (ok) {
+      waited0 = 1;
+      tc::fence_after_sync();
+      issue(0);
+    } else {
+      atomicOr(status, DEV_TIMEOUT);
+      abort_s = 1;
+    }
+  }
+  float bd[KP];
+  int bi[KP];
+#pragma unroll
+  for (int u = 0; u < KP; ++u) {
+    bd[u] = FLT_MAX;
+    bi[u] = INT_MAX;
+  }
+  if (load_init && active) {
+    const size_t o = (size_t)my_q * (KT_SUB * KP) + (size_t)cq * KP;
+#pragma unroll
+    for (int u = 0; u < KP; ++u) {
+      bd[u] = cand_d[o + u];
+      bi[u] = cand_i[o + u];
+    }
+  }
+  const float qv = active ? tnorm[(size_t)blockIdx.x * KT_RB + qi] : 0.0f;
+  __syncthreads();  // abort_s of the first issue
+  for (int t = 0; t < ntile; ++t) {
+    const int b = t & 1;
+    const bool stop = abort_s != 0;
+    bool got = false;
+    if (!stop) {
+      got = tc::mbar_wait(&bar[3 + b], (uint32_t)((t >> 1) & 1), KT_WAIT);
+      if (!got) {
+        atomicOr(status, DEV_TIMEOUT);
+        abort_s = 1;
+      }
+    }
+    tc::fence_after_sync();
+    if (tid == 0 && got) {
+      if (t + 2 < ntile) {  // MMA t has released operand buffer b
+        load(t + 2, b);
+        if (b) ++issued1;
+        else ++issued0;
+      }
+      if (t + 1 < ntile) {
+        const int b1 = b ^ 1;
+        if (tc::mbar_wait(&bar[1 + b1], (uint32_t)(((t + 1) >> 1) & 1), KT_WAIT)) {
+          if (b1) ++waited1;
+          else ++waited0;
+          tc::fence_after_sync();
+          issue(b1);
+        } else {
+          atomicOr(status, DEV_TIMEOUT);
+          abort_s = 1;
+        }
+      }
+    }
+    const int r0 = tl.rb + local(t) * KT_RB, nt = min(KT_RB, rend - r0);
+    const bool use = __all_sync(0xffffffffu, got);  // tcgen05.ld needs the whole warp
+    if (use) {
+      const float* rn_t = rn3 + (t % 3) * KT_RB;
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const int c0 = cq * 32 + h * 16;
+        float v[16];
+        tc::tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(b * KT_RB + c0), v);
+        unsigned ok = !active || c0 >= nt ? 0u : (nt - c0 >= 16 ? 0xFFFFu : (1u << (nt - c0)) - 1u);
+        const int self = my_q - (r0 + c0);
+        if (self >= 0 && self < 16) ok &= ~(1u << self);
+        const float bound = bd[KP - 1];
+        const float4* rn4 = reinterpret_cast<const float4*>(rn_t + c0);
+        unsigned mask = 0;
+#pragma unroll
+        for (int j4 = 0; j4 < 4; ++j4) {
+          const float4 r4 = rn4[j4];
+          const float rr[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int j = 4 * j4 + u;
+            v[j] = (qv + rr[u]) - 2.0f * v[j];
+            mask |= (v[j] <= bound ? 1u : 0u) << j;
+          }
+        }
+        mask &= ok;
+        while (mask) {
+          const int j = __ffs(mask) - 1;
+          mask &= mask - 1;
+          float cv = v[0];
+#pragma unroll
+          for (int u = 1; u < 16; ++u) cv = (u == j) ? v[u] : cv;
+          int cj = r0 + c0 + j;
+          if (!(cv <= bd[KP - 1])) continue;
+#pragma unroll
+          for (int u = 0; u < KP; ++u) {
+            const bool less = cv < bd[u] || (cv == bd[u] && cj < bi[u]);
+            const float tv = less ? bd[u] : cv;
+            const int tj = less ? bi[u] : cj;
+            bd[u] = less ? cv : bd[u];
+            bi[u] = less ? cj : bi[u];
+            cv = tv;
+            cj = tj;
+          }
+        }
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();  // accumulator b and norm slot t % 3 are reused by later steps
+    if (abort_s) break;
+  }
+  if (tid == 0) {  // copies still in flight after an abort
+    for (; waited0 < issued0; ++waited0)
+      if (!tc::mbar_wait(&bar[1], (uint32_t)(waited0 & 1), KT_WAIT)) break;
+    for (; waited1 < issued1; ++waited1)
+      if (!tc::mbar_wait(&bar[2], (uint32_t)(waited1 & 1), KT_WAIT)) break;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_free(tmem, 2 * KT_RB);
+  if (active) {
+    const size_t o = (size_t)my_q * (KT_SUB * KP) + (size_t)cq * KP;
+#pragma unroll
+    for (int u = 0; u < KP; ++u) {
+      cand_d[o + u] = bd[u];
+      cand_i[o + u] = bi[u];
+    }
+  }
+}
+
 // Exact FP64 squared distance in coordinate order, no contraction.
 __device__ __forceinline__ double exact_sqdist(const double* a, const double* b, int d) {
   double acc = 0.0;
@@ -518,6 +770,49 @@ void prefilter_dispatch(const float* Xc, const float* qn, int d, const KnnTile* 
     case 48: launch_prefilter<48, KP>(Xc, qn, tl, nt, cd, ci, status, st, list); break;
     case 56: launch_prefilter<56, KP>(Xc, qn, tl, nt, cd, ci, status, st, list); break;
     case 64: launch_prefilter<64, KP>(Xc, qn, tl, nt, cd, ci, status, st, list); break;
+    default: throw Error(IASKIT_ERR_UNSUPPORTED, "kNN supports d <= 64");
+  }
+}
+
+// Records of every tile for the tree-order search, and its prefilter on them.
+template <int D, int KP>
+void launch_prefilter2(const uint32_t* rec, const float* tn, const KnnTile* tiles, const int* first, int ntiles,
+                       float* cd, int* ci, int* status, cudaStream_t st, TileList tl) {
+  const size_t smem = std::max<size_t>(prefilter2_smem<D>(), 80 * 1024);
+  IA_CUDA(cudaFuncSetAttribute(knn_prefilter2_kernel<D, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  knn_prefilter2_kernel<D, KP><<<ntiles, KT_NTH, smem, st>>>(rec, tn, tiles, first, tl.tlist, tl.toff, tl.load_init,
+                                                              cd, ci, status);
+  IA_LAUNCH_CHECK();
+}
+
+template <int D>
+void make_records(const float* Xc, const float* qn, const KnnTile* tiles, int ntiles, uint32_t* rec, float* tn,
+                  cudaStream_t st) {
+  knn_records_kernel<D><<<ntiles, 256, 0, st>>>(Xc, qn, tiles, rec, tn);
+  IA_LAUNCH_CHECK();
+}
+
+#define IA_KNN_DIMS(X) X(8) X(16) X(24) X(32) X(40) X(48) X(56) X(64)
+
+void records_dispatch(int Dp, const float* Xc, const float* qn, const KnnTile* tiles, int ntiles, uint32_t* rec,
+                      float* tn, cudaStream_t st) {
+  switch (Dp) {
+#define IA_CASE(D) \
+  case D: make_records<D>(Xc, qn, tiles, ntiles, rec, tn, st); break;
+    IA_KNN_DIMS(IA_CASE)
+#undef IA_CASE
+    default: throw Error(IASKIT_ERR_UNSUPPORTED, "kNN supports d <= 64");
+  }
+}
+
+template <int KP>
+void prefilter2_dispatch(int Dp, const uint32_t* rec, const float* tn, const KnnTile* tiles, const int* first,
+                         int ntiles, float* cd, int* ci, int* status, cudaStream_t st, TileList tl) {
+  switch (Dp) {
+#define IA_CASE(D) \
+  case D: launch_prefilter2<D, KP>(rec, tn, tiles, first, ntiles, cd, ci, status, st, tl); break;
+    IA_KNN_DIMS(IA_CASE)
+#undef IA_CASE
     default: throw Error(IASKIT_ERR_UNSUPPORTED, "kNN supports d <= 64");
   }
 }
@@ -735,17 +1030,27 @@ __global__ void knn_seed_bound_kernel(const double* X, int d, int kappa, const K
 }
 
 // Point tiles that block g must scan after its seed tiles: every other tile t of its
-// problem whose box's distance from g's box, a lower bound on every
-// query-to-point distance between them, is not above Tq[g].  The bound is formed in FP32
-// with every operation rounded down (gaps, squares, sums) from the outward-rounded
-// boxes, and compared with Tq (1 + 1e-9) rounded up, so a skipped tile lies farther
-// than tau from every query of g in exact arithmetic, and so (by more than the FP64
+// problem that may hold a neighbour of one of g's queries.  A tile is skipped when, for
+// every query q of g, the distance from q to the tile's box, a lower bound on q's
+// distance to any point of the tile, exceeds tau_q (1 + 1e-9): first the cheap test on
+// g's whole box against the largest tau (Tq), then, for the tiles it keeps, query by
+// query (one warp per tile, four queries per lane).  Bounds are formed in FP32 with
+// every operation rounded down, from the outward-rounded boxes and the queries rounded
+// toward the box, against thresholds rounded up; so a skipped tile lies farther than
+// tau_q from every query q of g in exact arithmetic, and so (by more than the FP64
 // rounding of a squared distance) in the FP64 distances that define the lists.  Counts
 // only (tlist null) or the list itself, in tile order, at toff[g].
-__global__ void knn_select_kernel(const KnnTile* tiles, const int* soff, const int* seeds, const int* first_tile,
-                                  const float* box, int d, const double* Tq, const int* toff, int* cnt,
-                                  int* tlist) {
-  __shared__ int wcount[KT_QB / 32];
+constexpr int SEL_WARPS = KT_QB / 32;
+__global__ void __launch_bounds__(KT_QB) knn_select_kernel(const double* Xp, const KnnTile* tiles, const int* soff,
+                                                           const int* seeds, const int* first_tile, const float* box,
+                                                           int d, const double* Tq, const double* tau,
+                                                           const int* toff, int* cnt, int* tlist) {
+  extern __shared__ float sel_q[];  // [d][KT_QB] queries rounded down, then rounded up
+  float* qlo = sel_q;
+  float* qhi = sel_q + (size_t)d * KT_QB;
+  __shared__ float tq_s[KT_QB];
+  __shared__ unsigned char cand[KT_QB], keep[KT_QB];
+  __shared__ int wcount[SEL_WARPS];
   __shared__ int base_s;
   __shared__ int sd[SEED_TILES];
   const int g = blockIdx.x;
@@ -755,18 +1060,53 @@ __global__ void knn_select_kernel(const KnnTile* tiles, const int* soff, const i
   const int ns = soff[g + 1] - soff[g];
   const float T = __double2float_ru(Tq[g] * (1.0 + 1e-9));
   const float* bq = box + (size_t)g * 2 * d;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (threadIdx.x == 0) base_s = 0;
-  if ((int)threadIdx.x < ns) sd[threadIdx.x] = seeds[soff[g] + threadIdx.x];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) base_s = 0;
+  if (tid < ns) sd[tid] = seeds[soff[g] + tid];
+  for (int e = tid; e < d * KT_QB; e += KT_QB) {
+    const int k = e / KT_QB, q = e % KT_QB;
+    const double x = q < tl.qn ? Xp[(size_t)(tl.q0 + q) * d + k] : 0.0;
+    qlo[e] = __double2float_rd(x);
+    qhi[e] = __double2float_ru(x);
+  }
+  // absent rows get a negative threshold, which no bound meets
+  tq_s[tid] = tid < tl.qn ? __double2float_ru(tau[tl.q0 + tid] * (1.0 + 1e-9)) : -1.0f;
   __syncthreads();
   for (int c0 = 0; c0 < nt; c0 += KT_QB) {
-    const int t = c0 + threadIdx.x;
-    bool take = false;
+    const int t = c0 + tid;
+    bool c = false;
     if (t < nt) {
       bool seeded = false;
       for (int r = 0; r < ns; ++r) seeded = seeded || sd[r] == t;
-      take = !seeded && !(box_lower_bound(bq, box + (size_t)(ft + t) * 2 * d, d) > T);
+      c = !seeded && !(box_lower_bound(bq, box + (size_t)(ft + t) * 2 * d, d) > T);
     }
+    cand[tid] = c ? 1 : 0;
+    __syncthreads();
+    for (int i = w; i < KT_QB; i += SEL_WARPS) {
+      if (!cand[i]) {  // warp-uniform
+        if (lane == 0) keep[i] = 0;
+        continue;
+      }
+      const float* bt = box + (size_t)(ft + c0 + i) * 2 * d;
+      float lb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      for (int k = 0; k < d; ++k) {
+        const float lo = bt[k], hi = bt[d + k];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int q = lane + 32 * j;
+          const float gap =
+              fmaxf(0.0f, fmaxf(__fsub_rd(lo, qhi[(size_t)k * KT_QB + q]), __fsub_rd(qlo[(size_t)k * KT_QB + q], hi)));
+          lb[j] = __fadd_rd(lb[j], __fmul_rd(gap, gap));
+        }
+      }
+      bool hit = false;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) hit = hit || lb[j] <= tq_s[lane + 32 * j];
+      const bool any = __any_sync(0xffffffffu, hit);
+      if (lane == 0) keep[i] = any ? 1 : 0;
+    }
+    __syncthreads();
+    const bool take = t < nt && keep[tid];
     const unsigned m = __ballot_sync(0xffffffffu, take);
     if (lane == 0) wcount[w] = __popc(m);
     __syncthreads();
@@ -774,14 +1114,14 @@ __global__ void knn_select_kernel(const KnnTile* tiles, const int* soff, const i
     for (int ww = 0; ww < w; ++ww) off += wcount[ww];
     if (take && tlist) tlist[toff[g] + off + __popc(m & ((1u << lane) - 1u))] = t;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       int tot = 0;
-      for (int ww = 0; ww < KT_QB / 32; ++ww) tot += wcount[ww];
+      for (int ww = 0; ww < SEL_WARPS; ++ww) tot += wcount[ww];
       base_s += tot;
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0 && cnt) cnt[g] = base_s;
+  if (tid == 0 && cnt) cnt[g] = base_s;
 }
 
 }  // namespace
@@ -895,13 +1235,17 @@ int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* kn
   IA_LAUNCH_CHECK();
   tile_box_kernel<<<nt, 64, 0, st>>>(Xp, d, b.tiles, box);
   IA_LAUNCH_CHECK();
+  const int Dp = padded_dim(d);
+  uint32_t* rec = s.rec.ensure_n<uint32_t>((size_t)nt * 2 * KT_RB * Dp);
+  float* tn = s.tnorm.ensure_n<float>((size_t)nt * KT_RB);
+  records_dispatch(Dp, b.Xc, b.qn, b.tiles, nt, rec, tn, st);
   // 1. seed tiles: the nearest boxes
   knn_seed_pick_kernel<<<nt, KT_QB, 0, st>>>(b.tiles, first_d, box, d, soff_d, seeds_d);
   IA_LAUNCH_CHECK();
   auto prefilter = [&](TileList list) {
-    if (KP == 16) prefilter_dispatch<16>(b.Xc, b.qn, d, b.tiles, nt, b.cd, b.ci, b.status, st, list);
-    else if (wide) prefilter_dispatch<64>(b.Xc, b.qn, d, b.tiles, nt, b.cd, b.ci, b.status, st, list);
-    else prefilter_dispatch<32>(b.Xc, b.qn, d, b.tiles, nt, b.cd, b.ci, b.status, st, list);
+    if (KP == 16) prefilter2_dispatch<16>(Dp, rec, tn, b.tiles, first_d, nt, b.cd, b.ci, b.status, st, list);
+    else if (wide) prefilter2_dispatch<64>(Dp, rec, tn, b.tiles, first_d, nt, b.cd, b.ci, b.status, st, list);
+    else prefilter2_dispatch<32>(Dp, rec, tn, b.tiles, first_d, nt, b.cd, b.ci, b.status, st, list);
   };
   prefilter(TileList{seeds_d, soff_d, 0});
   // 2. bounds and the tiles left to scan
@@ -917,7 +1261,11 @@ int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* kn
   else if (!wide) seed_bound(I32{}, I32{});
   else seed_bound(I64{}, I48{});
   IA_LAUNCH_CHECK();
-  knn_select_kernel<<<nt, KT_QB, 0, st>>>(b.tiles, soff_d, seeds_d, first_d, box, d, Tq, nullptr, cnt, nullptr);
+  const size_t sel_smem = (size_t)2 * d * KT_QB * sizeof(float);
+  if (sel_smem > 48 * 1024)
+    IA_CUDA(cudaFuncSetAttribute(knn_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sel_smem));
+  knn_select_kernel<<<nt, KT_QB, sel_smem, st>>>(Xp, b.tiles, soff_d, seeds_d, first_d, box, d, Tq, tau, nullptr, cnt,
+                                                 nullptr);
   IA_LAUNCH_CHECK();
   std::vector<int> hc(nt), ho(nt + 1, 0);
   d2h(hc.data(), cnt, nt, st);
@@ -944,7 +1292,8 @@ int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* kn
   if (total > 0) {
     h2d(toff, ho.data(), nt + 1, st);
     int* tlist = s.tlist.ensure_n<int>((size_t)total);
-    knn_select_kernel<<<nt, KT_QB, 0, st>>>(b.tiles, soff_d, seeds_d, first_d, box, d, Tq, toff, nullptr, tlist);
+    knn_select_kernel<<<nt, KT_QB, sel_smem, st>>>(Xp, b.tiles, soff_d, seeds_d, first_d, box, d, Tq, tau, toff,
+                                                   nullptr, tlist);
     IA_LAUNCH_CHECK();
     prefilter(TileList{tlist, toff, 1});
   }

@@ -200,13 +200,23 @@ void add_gemm(std::vector<GemmDescT<T>>& g, const T* A, int lda, const T* B, int
 // columns (right-hand-side blocks of a solve); otherwise 128 x 128 tensor-core tiles
 // for FP32 products (when enabled) and 64 x 64 tiles for FP64 ones (on FP64 or on
 // FP32 pairs).
+// A CUDA-core launch (tunable: not on the tensor cores, not on FP32 pairs) takes the
+// autotuned shape of its (type, largest N, largest M) bucket when the table has one.
 template <typename T>
-GemmShape make_tiles(const std::vector<GemmDescT<T>>& g, std::vector<GemmTile>& t, bool tc) {
-  int maxn = 0;
-  for (const auto& d : g) maxn = std::max(maxn, d.N);
-  const GemmShape shape = maxn <= 16                                      ? GEMM_SKINNY
-                          : (tc && std::is_same<T, float>::value) ? GEMM_TC
-                                                                        : GEMM_SQUARE;
+GemmShape make_tiles(const std::vector<GemmDescT<T>>& g, std::vector<GemmTile>& t, bool tc, bool tunable) {
+  int maxn = 0, maxm = 0;
+  for (const auto& d : g) {
+    maxn = std::max(maxn, d.N);
+    maxm = std::max(maxm, d.M);
+  }
+  GemmShape shape = maxn <= 16                                      ? GEMM_SKINNY
+                    : (tc && std::is_same<T, float>::value) ? GEMM_TC
+                                                                  : GEMM_SQUARE;
+  constexpr bool fp64 = std::is_same<T, double>::value;
+  if (tunable && shape != GEMM_TC) {
+    const int e = gemm_tuned(fp64, gemm_n_bucket(maxn), gemm_m_bucket(maxm));
+    if (e >= 0 && e < GEMM_NSHAPES && gemm_shape_valid((GemmShape)e, fp64)) shape = (GemmShape)e;
+  }
   const int tm_ = gemm_tile_m(shape), tn_ = gemm_tile_n(shape);
   t.clear();
   for (int idx = 0; idx < (int)g.size(); ++idx)
@@ -463,7 +473,7 @@ class Solver {
   void run_gemms(const std::vector<GemmDescT<T>>& g) {
     if (g.empty()) return;
     std::vector<GemmTile> t;
-    const GemmShape shape = make_tiles(g, t, opt.gemm_tc != 0);
+    const GemmShape shape = make_tiles(g, t, opt.gemm_tc != 0, !pair_products<T>());
     arena.clear();
     size_t og = arena.push(g), ot = arena.push(t);
     char* base = upload_arena();
@@ -637,8 +647,8 @@ class Solver {
       }
       if (cp.empty()) continue;
       std::vector<GemmTile> t1, t2;
-      const GemmShape sh1 = make_tiles(g1, t1, opt.gemm_tc != 0),
-                      sh2 = make_tiles(g2, t2, opt.gemm_tc != 0);
+      const GemmShape sh1 = make_tiles(g1, t1, opt.gemm_tc != 0, !pair_products<T>()),
+                      sh2 = make_tiles(g2, t2, opt.gemm_tc != 0, !pair_products<T>());
       arena.clear();
       size_t ocp = arena.push(cp), ozs = arena.push(zs), og1 = arena.push(g1), ot1 = arena.push(t1),
              og2 = arena.push(g2), ot2 = arena.push(t2);
@@ -2459,6 +2469,58 @@ int factor_batched_impl(int nprob, const double* const* points, const double* co
 // Records a failure for iaskit_last_error() and returns its code.
 int report_error(int code, const std::string& msg) { return fail(code, msg); }
 
+int& gemm_tuned(int fp64, int nb, int mb) {
+  static int table[2][GT_NB][GT_MB] = {};
+  static bool init = false;
+  if (!init) {
+    for (auto& a : table)
+      for (auto& b : a)
+        for (int& e : b) e = -1;
+    init = true;
+  }
+  return table[fp64 ? 1 : 0][nb][mb];
+}
+
+// One timed grouped CUDA-core GEMM of `count` independent M x N x K problems with the
+// given tile shape: average milliseconds over `reps` launches after one warm-up.
+double tune_gemm_ms(Solver& s, int fp64, int M, int N, int K, int count, GemmShape shape, int reps) {
+  auto run = [&](auto tag) -> double {
+    using T = decltype(tag);
+    const size_t a = (size_t)M * K, b = (size_t)K * N, c = (size_t)M * N;
+    T* base = s.io.ensure_n<T>((a + b + c) * count);
+    IA_CUDA(cudaMemsetAsync(base, 0, (a + b + c) * count * sizeof(T), s.st));
+    std::vector<GemmDescT<T>> g;
+    for (int i = 0; i < count; ++i) {
+      T* A = base + (a + b + c) * i;
+      add_gemm<T>(g, A, M, A + a, K, A + a + b, M, M, N, K, 1.0, 1.0);
+    }
+    std::vector<GemmTile> t;
+    const int tm = gemm_tile_m(shape), tn = gemm_tile_n(shape);
+    for (int idx = 0; idx < count; ++idx)
+      for (int j = 0; j < (N + tn - 1) / tn; ++j)
+        for (int i = 0; i < (M + tm - 1) / tm; ++i) t.push_back(GemmTile{idx, i, j});
+    s.arena.clear();
+    const size_t og = s.arena.push(g), ot = s.arena.push(t);
+    char* dev = s.upload_arena();
+    cudaEvent_t e0, e1;
+    IA_CUDA(cudaEventCreate(&e0));
+    IA_CUDA(cudaEventCreate(&e1));
+    gemm_grouped((const GemmDescT<T>*)(dev + og), (const GemmTile*)(dev + ot), (int)t.size(), shape, s.st,
+                 s.status.ensure_n<int>(1));
+    IA_CUDA(cudaEventRecord(e0, s.st));
+    for (int r = 0; r < reps; ++r)
+      gemm_grouped((const GemmDescT<T>*)(dev + og), (const GemmTile*)(dev + ot), (int)t.size(), shape, s.st,
+                   s.status.as<int>());
+    IA_CUDA(cudaEventRecord(e1, s.st));
+    IA_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    IA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms / reps;
+  };
+  return fp64 ? run(double{}) : run(float{});
+}
 }  // namespace iaskit
 
 using namespace iaskit;
@@ -2553,6 +2615,29 @@ int iaskit_apply_device(const double* d_w, double* d_u, int nrhs) {
   return guarded([&] {
     if (!d_w || !d_u) throw Error(IASKIT_ERR_ARG, "null pointer");
     S().apply_device(d_w, d_u, nrhs);
+  });
+}
+
+int iaskit_gemm_tile(int fp64, int n_bucket, int m_bucket, int shape) {
+  return guarded([&] {
+    if (fp64 < 0 || fp64 > 1 || n_bucket < 0 || n_bucket >= GT_NB || m_bucket < 0 || m_bucket >= GT_MB)
+      throw Error(IASKIT_ERR_ARG, "bad tile table key");
+    if (shape != -1 && (shape < 0 || shape >= GEMM_NSHAPES || !gemm_shape_valid((GemmShape)shape, fp64 != 0)))
+      throw Error(IASKIT_ERR_ARG, "not a CUDA-core tile shape of this type");
+    gemm_tuned(fp64, n_bucket, m_bucket) = shape;
+  });
+}
+
+int iaskit_tune_gemm(int fp64, int M, int N, int K, int count, int shape, int reps, double* ms) {
+  return guarded([&] {
+    if (!ms) throw Error(IASKIT_ERR_ARG, "null pointer");
+    if (M < 1 || N < 1 || K < 1 || count < 1 || reps < 1 || reps > 1000 || fp64 < 0 || fp64 > 1)
+      throw Error(IASKIT_ERR_ARG, "bad GEMM size");
+    if ((double)count * ((double)M * K + (double)K * N + (double)M * N) * (fp64 ? 8 : 4) > 4e9)
+      throw Error(IASKIT_ERR_ARG, "tuning problem above 4 GB");
+    if (shape < 0 || shape >= GEMM_NSHAPES || !gemm_shape_valid((GemmShape)shape, fp64 != 0))
+      throw Error(IASKIT_ERR_ARG, "not a CUDA-core tile shape of this type");
+    *ms = tune_gemm_ms(S(), fp64, M, N, K, count, (GemmShape)shape, reps);
   });
 }
 

@@ -66,6 +66,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long m
   return false;
 }
 
+// Expect `bytes` more transaction bytes on *bar and arrive once (the producer's arrival
+// of a phase that bulk copies complete).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) from global to
+// shared memory, completing as transaction bytes on *bar.
+__device__ __forceinline__ void bulk_g2s(void* smem, const void* gmem, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(smem)),
+               "l"(gmem), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
 // D[tmem] (+)= A B for one M x N x 8 TF32 step (one thread issues).
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          bool accumulate) {

@@ -75,3 +75,20 @@ def test_error_paths_without_device_work(lib_path):
 def test_kernels_are_compiled_for_sm103a_only():
     from paper_1602_01376_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_committed_tile_table_is_well_formed():
+    # the autotuner's committed cache: valid buckets and CUDA-core shapes
+    import json
+    import paper_1602_01376_gb300 as ia
+    if not os.path.exists(ia.TILE_TABLE):
+        pytest.skip("no committed tile table")
+    with open(ia.TILE_TABLE) as f:
+        table = json.load(f)
+    assert table["entries"]
+    for e in table["entries"]:
+        assert e["fp64"] in (0, 1)
+        assert 0 <= e["n_bucket"] < 6 and 0 <= e["m_bucket"] < 5
+        assert e["shape"] in ia.GEMM_SHAPES
+        assert not (e["fp64"] and e["shape"] == "512x8")
+        assert e["shape"] == min(e["ms"], key=e["ms"].get)
