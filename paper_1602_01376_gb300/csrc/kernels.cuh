@@ -365,21 +365,42 @@ void kernel_predict(const double* T, int M, const double* Xp, const double* xnor
 // every target position p and every node alpha of p's interaction list (the sibling of
 // each ancestor of p's leaf) that holds at least one of p's kappa nearest neighbours,
 //   u_p += K(x_p, X_alpha) w_alpha - K(x_p, X_skel(alpha)) w~_alpha,
-// i.e. the skeleton evaluation of alpha is replaced by the exact one (FP64, difference
-// form of the squared distance).  W and U hold the problems' N x nrhs column-major
-// blocks one after the other (problem q's at pbase * nrhs, ld N); w~_alpha lies at
-// WT + nodes[gid].wt_off with leading dimension nodes[gid].ld.
+// i.e. the skeleton evaluation of alpha is replaced by the exact one (FP64, Gram form
+// of the squared distance as kernel_blocks), grouped by node and tiled.
 struct NearProb {
   int pbase, N, L, nbase;
   double scale;  // -1 / (2 h^2)
 };
-struct NearNode {
-  int64_t wt_off;  // w~ of the node inside WT (column 0, row 0)
-  int ld, s;       // its leading dimension and the node's rank
+// masks[p] bit l (1 <= l <= L): the level-l node of target p's Evaluate list (the
+// sibling of p's level-l ancestor) holds one of p's kappa nearest neighbours.
+void near_masks(const int* knn_pos, int kappa, const int* pid, const NearProb* probs, int Ntot, unsigned* masks,
+                cudaStream_t st);
+// One tile of the exact-minus-skeleton sums: targets tgt[r0 .. r0 + 63] (global
+// positions, n in all) against columns cols[0 .. ncols) (or col0 .. col0 + ncols - 1),
+// weights y[j + r ldy]; part[t + 64 r] = sign * sum_j K(x_t, x_j) y_j,r.
+struct NearItem {
+  const int* tgt;
+  int n, r0;
+  const int* cols;
+  int col0, ncols;
+  const double* y;
+  int ldy;
+  double sign, scale;
+  double* part;
 };
-void near_field(const double* Xp, int d, const int* knn_pos, int kappa, const int* pid, const NearProb* probs,
-                const NearNode* nodes, const int* skel, int s_max, const double* W, const double* WT, double* U,
-                int nrhs, int Ntot, cudaStream_t st);
+// The partials of one node's list: tile t / 64 holds nchunks consecutive 64 x nrhs
+// blocks at part; U[ubase + tgt[t] - pbase + r ldu] += their sum.
+struct NearReduce {
+  const int* tgt;
+  int n, nchunks;
+  const double* part;
+  size_t ubase;
+  int pbase, ldu;
+};
+int near_tile_rows();
+int near_max_rhs();
+void near_tiles(const double* Xp, const double* xn, int d, int nrhs, const NearItem* items_dev, int nitems,
+                const NearReduce* lists_dev, int nlists, int max_list, double* U, cudaStream_t st);
 
 // Conditioning probe: out[q * KROWSUM_ROWS + r] = sum_j K(x_i, x_j) over the N points of
 // problem q (evaluated in FP32), for KROWSUM_ROWS rows i spread evenly over the

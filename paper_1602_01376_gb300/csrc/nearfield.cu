@@ -6,11 +6,18 @@
 // holds a neighbour of i, the skeleton evaluation K_{i a~} w~_a is replaced by the exact
 // K_{i a} w_a.  The operator apply adds that difference after its Evaluate step.
 //
-// One warp per target position.  The levels of the target's list that hold a neighbour
-// come from the first split at which each neighbour's root-to-leaf path leaves the
-// target's (node sizes follow the tree's median split: left = size / 2); the warp then
-// sums, per such node, the exact row over the node's points minus the skeleton row over
-// its w~, lanes striding over the points, and lane 0 adds the sums to the target's row.
+// The pairs (target, node) are grouped by node: near_masks marks, per target, the levels
+// of its list whose node holds a neighbour (the level at which each neighbour's
+// root-to-leaf path leaves the target's; node sizes follow the tree's median split:
+// left = size / 2), and the host collects, per node alpha, the targets that need it
+// (all of them in the sibling of alpha).  The sums then run as tiles: 64 targets of one
+// node's list against 64 of its columns at a time (the node's points, then its
+// skeletons with the opposite sign), both staged in shared memory so that every column
+// serves 64 targets, FP64 kernel values in the Gram form |x|^2 + |y|^2 - 2 x.y (as
+// kernel_blocks), the tile kept in shared memory for the products with the weights.
+// A node's columns are split into chunks (the caller's items), each writing its
+// partial sums; near_reduce adds a list's chunks in a fixed order, so the result does
+// not depend on scheduling.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,120 +28,172 @@ namespace iaskit {
 
 namespace {
 
-constexpr int NF_WARPS = 8;  // warps (targets in flight) per block
-constexpr int NF_CB = 8;     // right-hand sides per pass over a node
+constexpr int NF_T = 64;        // targets per tile and columns per shared-memory step
+constexpr int NF_THREADS = 256;
+constexpr int NF_RMAX = 64;     // right-hand sides per launch (16 per thread group)
 
-__device__ __forceinline__ double nf_kernel(const double* xs, const double* xj, int d, double scale) {
-  double s = 0.0;
-  for (int k = 0; k < d; ++k) {
-    const double t = xs[k] - xj[k];
-    s = fma(t, t, s);
+__global__ void near_mask_kernel(const int* knn_pos, int kappa, const int* pid, const NearProb* probs, int Ntot,
+                                 unsigned* masks) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= Ntot) return;
+  const NearProb P = probs[pid[p]];
+  unsigned mask = 0;
+  for (int t = 0; t < kappa && P.L > 0; ++t) {
+    const int q = knn_pos[(size_t)p * kappa + t];
+    int off = P.pbase, size = P.N;
+    for (int l = 0; l < P.L; ++l) {
+      const int half = size / 2;
+      const bool pl = p < off + half, ql = q < off + half;
+      if (pl != ql) {  // the level-(l+1) node of p's list holds q
+        mask |= 1u << (l + 1);
+        break;
+      }
+      if (pl) {
+        size = half;
+      } else {
+        off += half;
+        size -= half;
+      }
+    }
   }
-  return exp(s * scale);
+  masks[p] = mask;
 }
 
-__global__ void __launch_bounds__(NF_WARPS * 32)
-    near_field_kernel(const double* Xp, int d, const int* knn_pos, int kappa, const int* pid,
-                      const NearProb* probs, const NearNode* nodes, const int* skel, int s_max,
-                      const double* W, const double* WT, double* U, int nrhs, int Ntot) {
-  extern __shared__ double nf_x[];  // NF_WARPS x d: each warp's target coordinates
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  double* xs = nf_x + (size_t)wib * d;
-  for (int p = blockIdx.x * NF_WARPS + wib; p < Ntot; p += gridDim.x * NF_WARPS) {
-    const NearProb P = probs[pid[p]];
-    if (P.L == 0) continue;
-    // bit l: the level-l node of p's list holds a neighbour of p
-    unsigned mask = 0;
-    for (int t = lane; t < kappa; t += 32) {
-      const int q = knn_pos[(size_t)p * kappa + t];
-      int off = P.pbase, size = P.N;
-      for (int l = 0; l < P.L; ++l) {
-        const int half = size / 2;
-        const bool pl = p < off + half, ql = q < off + half;
-        if (pl != ql) {
-          mask |= 1u << (l + 1);
-          break;
-        }
-        if (pl) {
-          size = half;
-        } else {
-          off += half;
-          size -= half;
-        }
+// One block per item: targets r0 .. r0 + 63 of a node's list against the item's
+// columns; part[item.part + t + r 64] = sign * sum_j K(x_t, x_j) y_j,r.
+__global__ void __launch_bounds__(NF_THREADS) near_tile_kernel(const double* Xp, const double* xn, int d, int nrhs,
+                                                               const NearItem* items) {
+  extern __shared__ double nf_sh[];
+  double* xt = nf_sh;                          // [d][NF_T] targets
+  double* xc = xt + (size_t)d * NF_T;          // [d][NF_T] columns
+  double* Ks = xc + (size_t)d * NF_T;          // [NF_T][NF_T + 1] kernel tile
+  double* ws = Ks + NF_T * (NF_T + 1);         // [NF_T][nrhs] weights
+  __shared__ double nt_s[NF_T], nc_s[NF_T];
+  __shared__ int pos_t[NF_T], pos_c[NF_T];
+  const NearItem I = items[blockIdx.x];
+  const int tid = threadIdx.x;
+  const int nt = min(NF_T, I.n - I.r0);
+  if (tid < NF_T) {
+    const int p = tid < nt ? I.tgt[I.r0 + tid] : I.tgt[I.r0];
+    pos_t[tid] = p;
+    nt_s[tid] = xn[p];
+  }
+  __syncthreads();
+  for (int e = tid; e < NF_T * d; e += NF_THREADS) {
+    const int t = e / d, k = e % d;
+    xt[(size_t)k * NF_T + t] = Xp[(size_t)pos_t[t] * d + k];
+  }
+  // products: thread (t, q) owns target t and the right-hand sides q, q + 4, ...
+  const int mt = tid % NF_T, mq = tid / NF_T;
+  double acc[NF_RMAX / 4];
+#pragma unroll
+  for (int i = 0; i < NF_RMAX / 4; ++i) acc[i] = 0.0;
+  const int tx = tid % 16, ty = tid / 16;  // kernel tile: 4 targets x 4 columns per thread
+  for (int j0 = 0; j0 < I.ncols; j0 += NF_T) {
+    const int nc = min(NF_T, I.ncols - j0);
+    __syncthreads();  // the previous step's readers are done
+    if (tid < NF_T) {
+      const int j = min(j0 + tid, I.ncols - 1);
+      const int c = I.cols ? I.cols[j] : I.col0 + j;
+      pos_c[tid] = c;
+      nc_s[tid] = xn[c];
+    }
+    __syncthreads();
+    for (int e = tid; e < NF_T * d; e += NF_THREADS) {
+      const int j = e / d, k = e % d;
+      xc[(size_t)k * NF_T + j] = Xp[(size_t)pos_c[j] * d + k];
+    }
+    for (int e = tid; e < NF_T * nrhs; e += NF_THREADS) {
+      const int j = e % NF_T, r = e / NF_T;
+      ws[(size_t)j * nrhs + r] = j < nc ? I.y[(size_t)(j0 + j) + (size_t)r * I.ldy] : 0.0;
+    }
+    __syncthreads();
+    double dot[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) dot[a][b] = 0.0;
+    for (int k = 0; k < d; ++k) {
+      double a4[4], b4[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        a4[a] = xt[(size_t)k * NF_T + tx + 16 * a];
+        b4[a] = xc[(size_t)k * NF_T + ty + 16 * a];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) dot[a][b] = fma(a4[a], b4[b], dot[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int t = tx + 16 * a, j = ty + 16 * b;
+        const double d2 = fmax((nt_s[t] + nc_s[j]) - 2.0 * dot[a][b], 0.0);
+        Ks[t * (NF_T + 1) + j] = (t < nt && j < nc) ? exp(d2 * I.scale) : 0.0;
+      }
+    __syncthreads();
+    for (int j = 0; j < nc; ++j) {
+      const double kv = Ks[mt * (NF_T + 1) + j];
+      const double* wj = ws + (size_t)j * nrhs;
+#pragma unroll
+      for (int i = 0; i < NF_RMAX / 4; ++i) {
+        const int r = mq + 4 * i;
+        if (r < nrhs) acc[i] = fma(kv, wj[r], acc[i]);
       }
     }
-    mask = __reduce_or_sync(0xffffffffu, mask);
-    if (mask == 0) continue;
-    __syncwarp();
-    for (int k = lane; k < d; k += 32) xs[k] = Xp[(size_t)p * d + k];
-    __syncwarp();
-    const size_t blk = (size_t)P.pbase * nrhs + (size_t)(p - P.pbase);  // row p of its block
-    while (mask) {
-      const int l = __ffs(mask) - 1;
-      mask &= mask - 1;
-      // the level-l node of the list: p's path for l - 1 splits, then the other side
-      int off = P.pbase, size = P.N, uid = 1;
-      for (int ll = 0; ll < l; ++ll) {
-        const int half = size / 2;
-        const bool pl = p < off + half;
-        const bool left = (ll < l - 1) ? pl : !pl;
-        if (left) {
-          size = half;
-          uid = 2 * uid;
-        } else {
-          off += half;
-          size -= half;
-          uid = 2 * uid + 1;
-        }
-      }
-      const int g = P.nbase + uid;
-      const NearNode A = nodes[g];
-      const int* sk = skel + (size_t)g * s_max;
-      for (int c0 = 0; c0 < nrhs; c0 += NF_CB) {
-        const int nc = min(NF_CB, nrhs - c0);
-        double acc[NF_CB];
+  }
+  if (mt < nt)
 #pragma unroll
-        for (int c = 0; c < NF_CB; ++c) acc[c] = 0.0;
-        for (int j = off + lane; j < off + size; j += 32) {  // exact: K(x_p, X_alpha) w_alpha
-          const double kv = nf_kernel(xs, Xp + (size_t)j * d, d, P.scale);
-          const double* wj = W + (size_t)P.pbase * nrhs + (size_t)(j - P.pbase) + (size_t)c0 * P.N;
-#pragma unroll
-          for (int c = 0; c < NF_CB; ++c)
-            if (c < nc) acc[c] = fma(kv, wj[(size_t)c * P.N], acc[c]);
-        }
-        for (int k = lane; k < A.s; k += 32) {  // minus the skeleton row: K(x_p, X_skel) w~
-          const double kv = nf_kernel(xs, Xp + (size_t)sk[k] * d, d, P.scale);
-          const double* wt = WT + A.wt_off + k + (size_t)c0 * A.ld;
-#pragma unroll
-          for (int c = 0; c < NF_CB; ++c)
-            if (c < nc) acc[c] = fma(-kv, wt[(size_t)c * A.ld], acc[c]);
-        }
-#pragma unroll
-        for (int c = 0; c < NF_CB; ++c)
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
-        if (lane == 0)
-          for (int c = 0; c < nc; ++c) U[blk + (size_t)(c0 + c) * P.N] += acc[c];
-      }
+    for (int i = 0; i < NF_RMAX / 4; ++i) {
+      const int r = mq + 4 * i;
+      if (r < nrhs) I.part[(size_t)mt + (size_t)r * NF_T] = I.sign * acc[i];
     }
+}
+
+// U[tgt[t] - pbase + r ldu] += sum over the list's chunks, in order, of the partials of
+// target t (tile t / 64); one grid row per list.
+__global__ void near_reduce_kernel(const NearReduce* lists, int nrhs, double* U) {
+  const NearReduce R = lists[blockIdx.y];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < R.n * nrhs; e += gridDim.x * blockDim.x) {
+    const int t = e % R.n, r = e / R.n;
+    const double* p = R.part + (size_t)(t / NF_T) * R.nchunks * NF_T * nrhs + (t % NF_T) + (size_t)r * NF_T;
+    double s = 0.0;
+    for (int c = 0; c < R.nchunks; ++c) s += p[(size_t)c * NF_T * nrhs];
+    U[R.ubase + (size_t)(R.tgt[t] - R.pbase) + (size_t)r * R.ldu] += s;
   }
 }
 
 }  // namespace
 
-void near_field(const double* Xp, int d, const int* knn_pos, int kappa, const int* pid, const NearProb* probs,
-                const NearNode* nodes, const int* skel, int s_max, const double* W, const double* WT, double* U,
-                int nrhs, int Ntot, cudaStream_t st) {
-  if (Ntot <= 0 || kappa <= 0 || nrhs <= 0) return;
-  const size_t smem = (size_t)NF_WARPS * d * sizeof(double);
-  if (smem > 200 * 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "dimension too large for the near-field kernel");
-  if (smem > 48 * 1024)
-    IA_CUDA(cudaFuncSetAttribute(near_field_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+void near_masks(const int* knn_pos, int kappa, const int* pid, const NearProb* probs, int Ntot, unsigned* masks,
+                cudaStream_t st) {
+  if (Ntot <= 0) return;
   ProfScope _ps(PK_NEAR, st);
-  const int blocks = (int)std::min<int64_t>((Ntot + NF_WARPS - 1) / NF_WARPS, 152 * 16);
-  near_field_kernel<<<blocks, NF_WARPS * 32, smem, st>>>(Xp, d, knn_pos, kappa, pid, probs, nodes, skel, s_max,
-                                                          W, WT, U, nrhs, Ntot);
+  near_mask_kernel<<<ceil_div((size_t)Ntot, 256), 256, 0, st>>>(knn_pos, kappa, pid, probs, Ntot, masks);
   IA_LAUNCH_CHECK();
+}
+
+int near_tile_rows() { return NF_T; }
+int near_max_rhs() { return NF_RMAX; }
+
+void near_tiles(const double* Xp, const double* xn, int d, int nrhs, const NearItem* items_dev, int nitems,
+                const NearReduce* lists_dev, int nlists, int max_list, double* U, cudaStream_t st) {
+  if (nitems <= 0) return;
+  if (nrhs < 1 || nrhs > NF_RMAX) throw Error(IASKIT_ERR_ARG, "near field: nrhs above 64 per launch");
+  const size_t smem = sizeof(double) * ((size_t)2 * d * NF_T + NF_T * (NF_T + 1) + (size_t)NF_T * nrhs);
+  if (smem > 220 * 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "dimension too large for the near-field kernel");
+  if (smem > 48 * 1024)
+    IA_CUDA(cudaFuncSetAttribute(near_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  ProfScope _ps(PK_NEAR, st);
+  near_tile_kernel<<<nitems, NF_THREADS, smem, st>>>(Xp, xn, d, nrhs, items_dev);
+  IA_LAUNCH_CHECK();
+  for (int l0 = 0; l0 < nlists; l0 += 65535) {
+    dim3 grid(std::min<unsigned>(ceil_div((size_t)max_list * nrhs, 256), 4096), (unsigned)std::min(65535, nlists - l0));
+    near_reduce_kernel<<<grid, 256, 0, st>>>(lists_dev + l0, nrhs, U);
+    IA_LAUNCH_CHECK();
+  }
 }
 
 }  // namespace iaskit

@@ -674,6 +674,7 @@ class Solver {
               int s_max_, double tol_) {
     factored = false;
     skeletonized = false;
+    near_ready = false;
     if (in.empty()) throw Error(IASKIT_ERR_ARG, "no problem");
     if (d_ < 1) throw Error(IASKIT_ERR_ARG, "d must be >= 1");
     if (leaf_m < 2) throw Error(IASKIT_ERR_ARG, "leaf_m must be >= 2");
@@ -2256,6 +2257,121 @@ class Solver {
   // (w~ = P w up the tree) then Evaluate (u_c += K_{c s~} w~_s for the sibling s of
   // every non-root node c, and the leaf blocks).  The plain form recomputes the
   // kernel entries in FP64; the mixed form multiplies the FP64 blocks it stored.
+  // ---------------------------------------------------------- near field
+  // Per node: the targets whose Evaluate list holds the node and whose kNN lists hold
+  // one of its points (global positions), built once per tree and kNN lists.
+  struct NearList {
+    int g, level, first, n;
+  };
+  bool near_ready = false;
+  std::vector<NearList> near_lists;
+  DevBuf near_mask, near_tgt, near_part, near_io;
+  void near_build() {
+    std::vector<NearProb> np(pr.size());
+    for (size_t q = 0; q < pr.size(); ++q) np[q] = NearProb{pr[q].pbase, pr[q].N, pr[q].L, pr[q].nbase, pr[q].scale};
+    arena.clear();
+    const size_t op = arena.push(np);
+    char* base = upload_arena();
+    unsigned* dm = near_mask.ensure_n<unsigned>(Ntot);
+    near_masks(knn_pos.as<int>(), kappa, pid.as<int>(), (const NearProb*)(base + op), Ntot, dm, st);
+    std::vector<unsigned> hm(Ntot);
+    d2h(hm.data(), dm, Ntot, st);
+    IA_CUDA(cudaStreamSynchronize(st));
+    near_lists.clear();
+    std::vector<int> tgt;
+    for (int hh = 0; hh < Hmax; ++hh)
+      for (int g : by_height[hh]) {
+        if (is_root(g)) continue;
+        const Node& sb = nd[sibling(g)];
+        const int l = nd[g].level;
+        NearList L{g, l, (int)tgt.size(), 0};
+        for (int p = sb.off; p < sb.off + sb.size; ++p)
+          if (hm[p] >> l & 1u) tgt.push_back(p);
+        L.n = (int)tgt.size() - L.first;
+        if (L.n > 0) near_lists.push_back(L);
+      }
+    int* dt = near_tgt.ensure_n<int>(std::max<size_t>(tgt.size(), 1));
+    h2d(dt, tgt.data(), tgt.size(), st);
+    IA_CUDA(cudaStreamSynchronize(st));
+    near_ready = true;
+  }
+  void near_field_apply(const double* Wp, const double* WT, const std::vector<int64_t>& woff, double* Up,
+                        int nrhs) {
+    if (!near_ready) near_build();
+    const int TR = near_tile_rows(), RMAX = near_max_rhs();
+    constexpr int CHUNK = 4096;  // columns per item of a node's points
+    for (int c0 = 0; c0 < nrhs; c0 += RMAX) {
+      const int nr = std::min(RMAX, nrhs - c0);
+      for (int level = 1; level <= Hmax; ++level) {
+        std::vector<NearItem> items;
+        std::vector<NearReduce> red;
+        int64_t psz = 0;
+        int max_list = 0;
+        // sizes first: the partial blocks of every item of this level
+        for (const NearList& L : near_lists) {
+          if (L.level != level) continue;
+          const Node& A = nd[L.g];
+          const int nchunks = (A.size + CHUNK - 1) / CHUNK + (A.s > 0 ? 1 : 0);
+          psz += (int64_t)((L.n + TR - 1) / TR) * nchunks * TR * nr;
+        }
+        if (psz == 0) continue;
+        double* part = near_part.ensure_n<double>(psz);
+        int64_t po = 0;
+        for (const NearList& L : near_lists) {
+          if (L.level != level) continue;
+          const Node& A = nd[L.g];
+          const Prob& P = pr[A.prob];
+          const int par = parent(L.g);
+          const int nchunks = (A.size + CHUNK - 1) / CHUNK + (A.s > 0 ? 1 : 0);
+          const int* tg = near_tgt.as<int>() + L.first;
+          red.push_back(NearReduce{tg, L.n, nchunks, part + po, (size_t)P.pbase * nrhs + (size_t)c0 * P.N, P.pbase,
+                                   P.N});
+          max_list = std::max(max_list, L.n);
+          for (int r0 = 0; r0 < L.n; r0 += TR) {
+            for (int j = 0; j < A.size; j += CHUNK) {  // exact: the node's points
+              NearItem it{};
+              it.tgt = tg;
+              it.n = L.n;
+              it.r0 = r0;
+              it.cols = nullptr;
+              it.col0 = A.off + j;
+              it.ncols = std::min(CHUNK, A.size - j);
+              it.y = Wp + (size_t)P.pbase * nrhs + (size_t)(A.off + j - P.pbase) + (size_t)c0 * P.N;
+              it.ldy = P.N;
+              it.sign = 1.0;
+              it.scale = P.scale;
+              it.part = part + po;
+              po += (int64_t)TR * nr;
+              items.push_back(it);
+            }
+            if (A.s > 0) {  // minus the skeleton evaluation: K(x, X_skel) w~
+              NearItem it{};
+              it.tgt = tg;
+              it.n = L.n;
+              it.r0 = r0;
+              it.cols = skel.as<int>() + (size_t)L.g * s_max;
+              it.col0 = 0;
+              it.ncols = A.s;
+              it.y = WT + woff[par] + rowoff(L.g) + (size_t)c0 * n2(par);
+              it.ldy = n2(par);
+              it.sign = -1.0;
+              it.scale = P.scale;
+              it.part = part + po;
+              po += (int64_t)TR * nr;
+              items.push_back(it);
+            }
+          }
+        }
+        arena.clear();
+        const size_t oi = arena.push(items), orr = arena.push(red);
+        char* base = upload_arena();
+        near_tiles(Xp.as<double>(), xnrm.as<double>(), d, nr, (const NearItem*)(base + oi), (int)items.size(),
+                   (const NearReduce*)(base + orr), (int)red.size(), max_list, Up, st);
+        IA_CUDA(cudaStreamSynchronize(st));  // the arena is reused by the next level
+      }
+    }
+  }
+
   void apply_device(const double* w, double* u, int nrhs) {
     if (!factored) throw Error(IASKIT_ERR_NOT_FACTORED, "no factorization");
     if (nrhs < 1) throw Error(IASKIT_ERR_ARG, "bad nrhs");
@@ -2365,22 +2481,7 @@ class Solver {
     }
     // kNN-separated operator: nodes of a target's list that hold one of its nearest
     // neighbours are evaluated exactly instead of through their skeletons (eq. askit)
-    if (opt.near_field && Hmax > 0 && kappa > 0) {
-      std::vector<NearProb> np(pr.size());
-      for (size_t q = 0; q < pr.size(); ++q)
-        np[q] = NearProb{pr[q].pbase, pr[q].N, pr[q].L, pr[q].nbase, pr[q].scale};
-      std::vector<NearNode> nn(nd.size(), NearNode{0, 1, 0});
-      for (size_t g = 0; g < nd.size(); ++g) {
-        if (nd[g].prob < 0 || nd[g].uid < 2) continue;
-        const int par = parent((int)g);
-        nn[g] = NearNode{woff[par] + rowoff((int)g), n2(par), nd[g].s};
-      }
-      arena.clear();
-      size_t op = arena.push(np), on = arena.push(nn);
-      char* base = upload_arena();
-      near_field(Xp.as<double>(), d, knn_pos.as<int>(), kappa, pid.as<int>(), (const NearProb*)(base + op),
-                 (const NearNode*)(base + on), sk, s_max, Wp, WT, Up, nrhs, Ntot, st);
-    }
+    if (opt.near_field && Hmax > 0 && kappa > 0) near_field_apply(Wp, WT, woff, Up, nrhs);
     gather(Up, u, nrhs, blocks, true);
     IA_CUDA(cudaStreamSynchronize(st));
     prof().resolve();
@@ -2390,6 +2491,7 @@ class Solver {
   void release() {
     factored = false;
     skeletonized = false;
+    near_ready = false;
     DevBuf* all[] = {&X, &Xp, &perm, &iperm, &pid, &knn, &knn_pos, &samp, &ranks, &skel,
                      &piv_ws, &A_ws, &status, &arena_dev, &step_dev, &tbuf, &vbuf, &vbuf32,
                      &ubuf, &rbuf, &wt, &io, &normbuf, &blocks_dev, &LU, &LUpiv, &Wb, &Zb, &Zpiv,
@@ -2398,7 +2500,7 @@ class Solver {
                      &l_feat, &l_score, &l_linfo, &l_samp, &l_rk, &l_Ptmp, &l_sktmp, &l_hold, &l_err,
                      &l_cols, &l_gram, &l_dense, &mlp_master, &mlp_m, &mlp_v, &mlp_grad, &mlp_b16,
                      &mlp_loss, &tr_feat, &tr_tgt, &tr_lev, &tr_bx, &tr_bt, &tr_y, &tr_H1, &tr_H2, &tr_idx,
-                     &xnrm, &pred_part, &pred_io, &kperm, &kiperm, &Xk};
+                     &xnrm, &pred_part, &pred_io, &kperm, &kiperm, &Xk, &near_mask, &near_tgt, &near_part, &near_io};
     mlp_ready = false;
     for (DevBuf* b : all) b->release();
     tree_s.release();
