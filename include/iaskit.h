@@ -240,6 +240,12 @@ int iaskit_predict_device(const double* d_test, int64_t M, const double* d_w, in
  *                  distance so far; the skipped tiles enter the certification of the
  *                  exact re-rank (default).  0: every pair is scanned.  The lists are
  *                  identical either way [any time]
+ *   "inner_pair"   mixed precision, problems with FP64 operator blocks: 1 (default) the
+ *                  operator applies inside each GMRES cycle form their FP64 products on
+ *                  FP32 pairs (about 2^-44 relative) and a cycle aims at 1e-7 of its
+ *                  starting residual, while every cycle's residual is recomputed with
+ *                  FP64 products, so the solution is the FP64 operator's; 0: every apply
+ *                  in FP64 [any time]
  *   "inject_status" failure-path test hook: device status flags (1 zero pivot, 2
  *                  non-finite input, 4 internal bound, 8 expired bounded wait) that the
  *                  host ORs into the library's device status word just before its next

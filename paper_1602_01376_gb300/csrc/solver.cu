@@ -106,6 +106,9 @@ struct Options {
   // kNN: 1 = search in tree order with tile pruning (default), 0 = brute force over
   // every pair; the lists are identical
   int knn_prune = 1;
+  // mixed form with FP64 operator blocks: GMRES's inner operator applies on FP32 pairs,
+  // every cycle's residual in FP64 (1), or every apply in FP64 (0)
+  int inner_pair = 1;
 };
 
 struct Prob {
@@ -458,9 +461,10 @@ class Solver {
   // run on FP32 pairs (about 2^-44 relative, on the FP32 pipes); the operator apply
   // keeps FP64 products for the problems whose operator is in FP64.
   bool in_apply = false;
+  bool apply_low = false;  // an operator apply inside GMRES: FP64 products on pairs too
   template <typename T>
   bool pair_products() const {
-    return std::is_same<T, double>::value && prec == PREC_MIXED && !in_apply;
+    return std::is_same<T, double>::value && prec == PREC_MIXED && (!in_apply || apply_low);
   }
   template <typename T>
   void launch_gemms(const GemmDescT<T>* descs_dev, const GemmTile* tiles_dev, int ntiles, GemmShape shape) {
@@ -2060,10 +2064,17 @@ class Solver {
   // partly in FP32 (no second, differently rounded application of M^-1).
   // Every (problem, column) pair is its own segment; all open segments advance together,
   // so one preconditioner and one operator application serve all of them per iteration.
+  // In the mixed form with FP64 operator blocks (option inner_pair), the operator
+  // applies inside a GMRES cycle form their FP64 products on FP32 pairs (about 2^-44
+  // relative, on the FP32 pipes) and each cycle aims at a reduction of 1e-7 of its
+  // starting residual; every cycle's residual is recomputed with FP64 products, so the
+  // outer iteration converges to the FP64 operator's solution (GMRES-IR with an inner
+  // operator of lower precision than the residual, after Carson & Higham).
   // A segment closes when its relative residual is <= refine_tol, or when a cycle whose
-  // own GMRES estimate reached 0.1 refine_tol lowered the recomputed residual by less than
-  // half: then the rounding floor of the FP64 residual itself, about
-  // eps ||A|| ||w|| / ||u||, lies above the target and further cycles cannot help.
+  // own GMRES estimate reached its target lowered the recomputed residual by less than
+  // half, or (FP64 inner products) left it a hundred times above that estimate: then the
+  // rounding floor of the FP64 residual itself, about eps ||A|| ||w|| / ||u||, lies above
+  // the target and further cycles cannot help.
   // max_iters bounds the total number of GMRES iterations.
   // u_in: null - w holds the right-hand side and receives the solution, starting from
   // the plain solve; else u_in is the right-hand side and w an initial iterate.
@@ -2091,6 +2102,15 @@ class Solver {
     int& iters = stats.refine_iters;
     iters = 0;
     bool first = true;
+    bool low = false;  // inner applies on pairs: some problem keeps FP64 operator blocks
+    if (prec == PREC_MIXED && opt.inner_pair)
+      for (const Prob& P : pr) low = low || P.op64;
+    std::vector<double> cyc_tgt(S, 0.0);  // the last cycle's target per segment
+    struct LowScope {
+      bool& f;
+      explicit LowScope(bool& flag) : f(flag) {}
+      ~LowScope() { f = false; }
+    } low_scope(apply_low);
     while (true) {
       apply_device(w, r, nrhs);  // r = u - A w
       axpby(u, r, n);
@@ -2106,8 +2126,8 @@ class Solver {
           // recomputed residual either fell by less than half or lies a hundred times
           // above that estimate (FGMRES's estimate is the true residual up to rounding)
           if (rel <= opt.refine_tol) state[q] = 1;
-          else if (!first && est_end[q] <= 0.1 * opt.refine_tol * std::max(un[q], 1e-300) &&
-                   (rn[q] > 0.5 * prev[q] || rn[q] > 100.0 * est_end[q]))
+          else if (!first && est_end[q] <= cyc_tgt[q] &&
+                   (rn[q] > 0.5 * prev[q] || (!low && rn[q] > 100.0 * est_end[q])))
             state[q] = 2;
         }
         prev[q] = rn[q];
@@ -2146,6 +2166,7 @@ class Solver {
         const bool live = state[q] == 0 && rn[q] > 0;
         g[(size_t)q * (m + 1)] = live ? rn[q] : 0.0;
         inv[q] = live ? 1.0 / rn[q] : 0.0;  // closed segments get a zero basis and no update
+        cyc_tgt[q] = std::max(0.1 * opt.refine_tol * std::max(un[q], 1e-300), low ? 1e-7 * rn[q] : 0.0);
       }
       h2d(coef, inv.data(), S, st);
       seg_scale(V, r, coef, segs, S);  // V_0 = r / beta
@@ -2155,7 +2176,9 @@ class Solver {
         double* vn = V + (size_t)(j + 1) * n;
         double* zj = Zb_ + (size_t)j * n;
         plain_solve(vj, nrhs, zj);      // Z_j = M^-1 v_j
+        apply_low = low;
         apply_device(zj, vn, nrhs);     // v_{j+1} = A Z_j
+        apply_low = false;
         std::vector<double> h1, h2;
         seg_dots(V, n, j + 1, vn, segs, S, coef, h1);     // classical Gram-Schmidt,
         seg_axpy(vn, V, n, j + 1, coef, -1.0, segs, S);    // twice
@@ -2167,7 +2190,7 @@ class Solver {
         seg_scale(vn, vn, coef, segs, S);
         ++iters;
         k = j + 1;
-        double worst_est = 0;
+        bool met = true;
         for (int q = 0; q < S; ++q) {
           for (int i = 0; i <= j; ++i) Hs(q, i, j) = h1[(size_t)i * S + q] + h2[(size_t)i * S + q];
           Hs(q, j + 1, j) = hn[q];
@@ -2188,9 +2211,9 @@ class Solver {
           gj = c * gj;
           const double est = std::fabs(g[(size_t)q * (m + 1) + j + 1]);
           est_end[q] = est;
-          worst_est = std::max(worst_est, un[q] > 0 ? est / un[q] : est);
+          met = met && (state[q] != 0 || est <= cyc_tgt[q]);
         }
-        if (worst_est <= 0.1 * opt.refine_tol) break;
+        if (met) break;
       }
       // y = R^-1 g per segment, w += Z y
       std::vector<double> y((size_t)k * S, 0.0);
@@ -2843,6 +2866,8 @@ int iaskit_set_option(const char* key, double value) {
       o.inject_status = as_int(0, 15);
     } else if (k == "knn_prune") {
       o.knn_prune = as_int(0, 1);
+    } else if (k == "inner_pair") {
+      o.inner_pair = as_int(0, 1);
     } else if (k == "profile") {
       int v = as_int(0, 1);
       IA_CUDA(cudaStreamSynchronize(S().st));
@@ -2878,6 +2903,7 @@ int iaskit_get_option(const char* key, double* value) {
     else if (k == "near_field") *value = o.near_field;
     else if (k == "inject_status") *value = o.inject_status;
     else if (k == "knn_prune") *value = o.knn_prune;
+    else if (k == "inner_pair") *value = o.inner_pair;
     else throw Error(IASKIT_ERR_ARG, "unknown option " + k);
   });
 }
