@@ -4,8 +4,15 @@
 #include <initializer_list>
 
 #include "common.cuh"
+#include "kspec.cuh"
 
 namespace iaskit {
+
+// The kernel spec of the translation units that evaluate kernel values (kspec.cuh);
+// the solver sets all of them together.
+void kspec_set_dense(const KernelSpec& k, cudaStream_t st);
+void kspec_set_near(const KernelSpec& k, cudaStream_t st);
+void kspec_set_predict(const KernelSpec& k, cudaStream_t st);
 
 // ------------------------------------------------------------------ tree (a1)
 // Scratch buffers of the tree build.
@@ -41,11 +48,11 @@ void permute_points(const double* X, const int* perm, int N, int d, int* iperm, 
 // ------------------------------------------------------------------- kNN (a2)
 struct KnnScratch {
   DevBuf x32, qnorm, part, mean, rmax, probs, cand_d, cand_i, flagged, counter, tiles, status, seed_tiles, seeds,
-      first, box, tau, tq, cnt, toff, tlist, rec, tnorm;
+      first, box, tau, tq, cnt, toff, tlist, rec, tnorm, bits;
   void release() {
     for (DevBuf* b : {&x32, &qnorm, &part, &mean, &rmax, &probs, &cand_d, &cand_i, &flagged, &counter,
                       &tiles, &status, &seed_tiles, &seeds, &first, &box, &tau, &tq, &cnt, &toff, &tlist, &rec,
-                      &tnorm})
+                      &tnorm, &bits})
       b->release();
   }
 };

@@ -1038,13 +1038,14 @@ __global__ void knn_seed_bound_kernel(const double* X, int d, int kappa, const K
 // every operation rounded down, from the outward-rounded boxes and the queries rounded
 // toward the box, against thresholds rounded up; so a skipped tile lies farther than
 // tau_q from every query q of g in exact arithmetic, and so (by more than the FP64
-// rounding of a squared distance) in the FP64 distances that define the lists.  Counts
-// only (tlist null) or the list itself, in tile order, at toff[g].
+// rounding of a squared distance) in the FP64 distances that define the lists.
+// Writes block g's selection as bits (word c of bits[g * mstride ..] for tiles 32 c ..)
+// and their count.
 constexpr int SEL_WARPS = KT_QB / 32;
 __global__ void __launch_bounds__(KT_QB) knn_select_kernel(const double* Xp, const KnnTile* tiles, const int* soff,
                                                            const int* seeds, const int* first_tile, const float* box,
-                                                           int d, const double* Tq, const double* tau,
-                                                           const int* toff, int* cnt, int* tlist) {
+                                                           int d, const double* Tq, const double* tau, size_t mstride,
+                                                           unsigned* bits, int* cnt) {
   extern __shared__ float sel_q[];  // [d][KT_QB] queries rounded down, then rounded up
   float* qlo = sel_q;
   float* qhi = sel_q + (size_t)d * KT_QB;
@@ -1108,11 +1109,10 @@ __global__ void __launch_bounds__(KT_QB) knn_select_kernel(const double* Xp, con
     __syncthreads();
     const bool take = t < nt && keep[tid];
     const unsigned m = __ballot_sync(0xffffffffu, take);
-    if (lane == 0) wcount[w] = __popc(m);
-    __syncthreads();
-    int off = base_s;
-    for (int ww = 0; ww < w; ++ww) off += wcount[ww];
-    if (take && tlist) tlist[toff[g] + off + __popc(m & ((1u << lane) - 1u))] = t;
+    if (lane == 0) {
+      wcount[w] = __popc(m);
+      if (c0 + 32 * w < nt) bits[(size_t)g * mstride + (c0 >> 5) + w] = m;  // tiles c0 + 32 w ..
+    }
     __syncthreads();
     if (tid == 0) {
       int tot = 0;
@@ -1121,7 +1121,47 @@ __global__ void __launch_bounds__(KT_QB) knn_select_kernel(const double* Xp, con
     }
     __syncthreads();
   }
-  if (tid == 0 && cnt) cnt[g] = base_s;
+  if (tid == 0) cnt[g] = base_s;
+}
+
+// Block g's tile list, in tile order at toff[g], from its selection bits.
+__global__ void knn_list_kernel(const KnnTile* tiles, const unsigned* bits, size_t mstride, const int* toff,
+                                int* tlist) {
+  __shared__ int wbase[KT_QB / 32];
+  __shared__ int base_s;
+  const int g = blockIdx.x;
+  const KnnTile tl = tiles[g];
+  const int nt = (tl.rn + KT_RB - 1) / KT_RB;
+  const int nw = (nt + 31) / 32;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) base_s = 0;
+  __syncthreads();
+  for (int w0 = 0; w0 < nw; w0 += KT_QB) {  // one word per thread
+    const unsigned word = w0 + tid < nw ? bits[(size_t)g * mstride + w0 + tid] : 0u;
+    int c = __popc(word), incl = c;
+    for (int o = 1; o < 32; o <<= 1) {  // inclusive scan of the counts over the warp
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (lane == 31) wbase[w] = incl;
+    __syncthreads();
+    int off = base_s;
+    for (int ww = 0; ww < w; ++ww) off += wbase[ww];
+    off += incl - c;
+    unsigned m = word;
+    while (m) {
+      const int b = __ffs(m) - 1;
+      m &= m - 1;
+      tlist[toff[g] + off++] = (w0 + tid) * 32 + b;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int tot = 0;
+      for (int ww = 0; ww < KT_QB / 32; ++ww) tot += wbase[ww];
+      base_s += tot;
+    }
+    __syncthreads();
+  }
 }
 
 }  // namespace
@@ -1264,8 +1304,12 @@ int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* kn
   const size_t sel_smem = (size_t)2 * d * KT_QB * sizeof(float);
   if (sel_smem > 48 * 1024)
     IA_CUDA(cudaFuncSetAttribute(knn_select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sel_smem));
-  knn_select_kernel<<<nt, KT_QB, sel_smem, st>>>(Xp, b.tiles, soff_d, seeds_d, first_d, box, d, Tq, tau, nullptr, cnt,
-                                                 nullptr);
+  int max_nt = 0;
+  for (const auto& pr : problems) max_nt = std::max(max_nt, (pr.second + KT_RB - 1) / KT_RB);
+  const size_t mstride = (size_t)(max_nt + 31) / 32 + 4;  // words per block, padded to the last chunk
+  unsigned* bits = s.bits.ensure_n<unsigned>((size_t)nt * mstride);
+  knn_select_kernel<<<nt, KT_QB, sel_smem, st>>>(Xp, b.tiles, soff_d, seeds_d, first_d, box, d, Tq, tau, mstride,
+                                                 bits, cnt);
   IA_LAUNCH_CHECK();
   std::vector<int> hc(nt), ho(nt + 1, 0);
   d2h(hc.data(), cnt, nt, st);
@@ -1292,8 +1336,7 @@ int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* kn
   if (total > 0) {
     h2d(toff, ho.data(), nt + 1, st);
     int* tlist = s.tlist.ensure_n<int>((size_t)total);
-    knn_select_kernel<<<nt, KT_QB, sel_smem, st>>>(Xp, b.tiles, soff_d, seeds_d, first_d, box, d, Tq, tau, toff,
-                                                   nullptr, tlist);
+    knn_list_kernel<<<nt, KT_QB, 0, st>>>(b.tiles, bits, mstride, toff, tlist);
     IA_LAUNCH_CHECK();
     prefilter(TileList{tlist, toff, 1});
   }

@@ -149,6 +149,7 @@ struct Stats {
   double t_solve = 0, t_apply = 0;
   int knn_fallback = 0;
   KnnPruneStats knn_prune;
+  double near_values = 0.0;
   int64_t bytes_W = 0, bytes_LU = 0, bytes_P = 0, bytes_operator = 0;
   std::vector<double> refine_hist;
   int refine_sweeps = 0;
@@ -2313,6 +2314,8 @@ class Solver {
         L.n = (int)tgt.size() - L.first;
         if (L.n > 0) near_lists.push_back(L);
       }
+    stats.near_values = 0.0;  // kernel values of one near-field apply per right-hand side
+    for (const NearList& L : near_lists) stats.near_values += (double)L.n * (nd[L.g].size + nd[L.g].s);
     int* dt = near_tgt.ensure_n<int>(std::max<size_t>(tgt.size(), 1));
     h2d(dt, tgt.data(), tgt.size(), st);
     IA_CUDA(cudaStreamSynchronize(st));
@@ -2964,8 +2967,10 @@ int iaskit_stats(char* buf, size_t len) {
     snprintf(tmp, sizeof tmp, "%s%.17g", q ? "," : "", std::min(s.pr[q].cond_est, 1e300));
     j += tmp;
   }
-  snprintf(tmp, sizeof tmp, "],\"knn_pairs_scanned\":%.17g,\"knn_pairs_all\":%.17g,\"knn_tiles_listed\":%lld",
-           s.stats.knn_prune.pairs_scanned, s.stats.knn_prune.pairs_all, (long long)s.stats.knn_prune.tiles_scanned);
+  snprintf(tmp, sizeof tmp,
+           "],\"knn_pairs_scanned\":%.17g,\"knn_pairs_all\":%.17g,\"knn_tiles_listed\":%lld,\"near_values\":%.17g",
+           s.stats.knn_prune.pairs_scanned, s.stats.knn_prune.pairs_all, (long long)s.stats.knn_prune.tiles_scanned,
+           s.stats.near_values);
   j += tmp;
   j += ",\"launches\":";
   j += std::to_string(prof().launches);
