@@ -246,6 +246,16 @@ int iaskit_predict_device(const double* d_test, int64_t M, const double* d_w, in
  *                  starting residual, while every cycle's residual is recomputed with
  *                  FP64 products, so the solution is the FP64 operator's; 0: every apply
  *                  in FP64 [any time]
+ *   "kernel"       the kernel of the next factorization: 0 the Gaussian of eq.
+ *                  (gaussian), exp(-|x - y|^2 / (2 h^2)) (default); 1 the polynomial
+ *                  kernel (x . y / h^2 + "poly_c")^"poly_p" (Sec. IV reports tests with a
+ *                  polynomial kernel and gives no degree or constants; these are this
+ *                  library's).  The factorization keeps its kernel: apply, solve,
+ *                  predict and refactor use it whatever the option says later.  Learned
+ *                  sampling is built for the Gaussian and returns IASKIT_ERR_UNSUPPORTED
+ *                  with the polynomial kernel [0, 1]
+ *   "poly_p"       polynomial degree (2) [1 .. 16]
+ *   "poly_c"       polynomial constant (1.0) [>= 0]
  *   "inject_status" failure-path test hook: device status flags (1 zero pivot, 2
  *                  non-finite input, 4 internal bound, 8 expired bounded wait) that the
  *                  host ORs into the library's device status word just before its next

@@ -8,7 +8,8 @@ imports nothing from here.
 
 What is computed (Yu, March, Xiao, Biros, "INV-ASKIT", arXiv 1602.01376):
 
-* ``kernel``   Gaussian kernel, eq. (gaussian) of Sec. I.
+* ``kernel``   Gaussian kernel, eq. (gaussian) of Sec. I; the polynomial kernel of
+               Sec. IV (degree and constant chosen here, selected by a context).
 * ``tree``     balanced binary partition (Sec. II-A) and exact kNN lists (Sec. II-B).
 * ``sampling`` nearest-neighbour row sampling plus uniform fill (Sec. II-B).
 * ``linalg``   partial-pivoting LU (GETRF/GETRS of Alg. "Factorize"/"Solve") and
@@ -32,7 +33,7 @@ GETRF through scipy, numpy's dense solve, scipy's k-d tree), invariants and brut
 force.  The uniform-fill random stream (splitmix64) is pinned to the published
 reference outputs of that generator.
 """
-from .kernel import gaussian_kernel, sqdist  # noqa: F401
+from .kernel import gaussian_kernel, kernel_matrix, polynomial_kernel, PolynomialKernel, sqdist  # noqa: F401
 from .tree import Tree, build_tree, knn_bruteforce, tree_depth, node_sizes  # noqa: F401
 from .sampling import splitmix64, sample_rows  # noqa: F401
 from .linalg import lu_factor, lu_solve, cpqr_id, back_substitute  # noqa: F401

@@ -25,7 +25,7 @@ from typing import Dict, Tuple
 
 import numpy as np
 
-from .kernel import gaussian_kernel
+from .kernel import kernel_matrix
 from .linalg import cpqr_id
 from .sampling import sample_rows
 from .tree import Tree
@@ -65,7 +65,7 @@ def skeletonize(X: np.ndarray, tree: Tree, knn: np.ndarray, h: float, s_max: int
                 cols = np.arange(o, e, dtype=np.int64)
             else:
                 cols = np.concatenate([sk.skel[(l + 1, 2 * i)], sk.skel[(l + 1, 2 * i + 1)]])
-            A = gaussian_kernel(Xp[samp], Xp[cols], h)
+            A = kernel_matrix(Xp[samp], Xp[cols], h)
             piv, s, P, _, margin = cpqr_id(A, s_max, tol)
             node = (l, i)
             sk.samp[node] = samp
@@ -106,14 +106,14 @@ def dense_Ktilde(sk: Skeletons) -> np.ndarray:
     def block(l: int, i: int) -> np.ndarray:
         o, e = tree.node_range(l, i)
         if l == tree.L:
-            return gaussian_kernel(Xp[o:e], Xp[o:e], h)
+            return kernel_matrix(Xp[o:e], Xp[o:e], h)
         left, right = (l + 1, 2 * i), (l + 1, 2 * i + 1)
         ol, el = tree.node_range(*left)
         orr, er = tree.node_range(*right)
         Kll = block(*left)
         Krr = block(*right)
-        Klr = gaussian_kernel(Xp[ol:el], Xp[sk.skel[right]], h) @ full_P(sk, right, cache)
-        Krl = gaussian_kernel(Xp[orr:er], Xp[sk.skel[left]], h) @ full_P(sk, left, cache)
+        Klr = kernel_matrix(Xp[ol:el], Xp[sk.skel[right]], h) @ full_P(sk, right, cache)
+        Krl = kernel_matrix(Xp[orr:er], Xp[sk.skel[left]], h) @ full_P(sk, left, cache)
         return np.block([[Kll, Klr], [Krl, Krr]])
 
     return block(0, 0)
@@ -139,9 +139,9 @@ def matvec(sk: Skeletons, lam: float, w: np.ndarray) -> np.ndarray:
             left, right = (l + 1, 2 * i), (l + 1, 2 * i + 1)
             ol, el = tree.node_range(*left)
             orr, er = tree.node_range(*right)
-            U[ol:el] += gaussian_kernel(Xp[ol:el], Xp[sk.skel[right]], h) @ wt[right]
-            U[orr:er] += gaussian_kernel(Xp[orr:er], Xp[sk.skel[left]], h) @ wt[left]
+            U[ol:el] += kernel_matrix(Xp[ol:el], Xp[sk.skel[right]], h) @ wt[right]
+            U[orr:er] += kernel_matrix(Xp[orr:er], Xp[sk.skel[left]], h) @ wt[left]
     for i in range(1 << tree.L):                         # Evaluate: leaf self-interaction
         o, e = tree.node_range(tree.L, i)
-        U[o:e] += gaussian_kernel(Xp[o:e], Xp[o:e], h) @ W[o:e]
+        U[o:e] += kernel_matrix(Xp[o:e], Xp[o:e], h) @ W[o:e]
     return U[:, 0] if vec else U

@@ -30,7 +30,7 @@ from typing import Dict, Optional, Tuple
 import numpy as np
 
 from .askit import Skeletons, dense_Ktilde, full_P, matvec, skeletonize
-from .kernel import gaussian_kernel
+from .kernel import kernel_matrix
 from .linalg import lu_factor, lu_solve
 from .tree import Tree, build_tree, knn_bruteforce
 
@@ -67,7 +67,7 @@ def factorize(sk: Skeletons, lam: float) -> Factorization:
         l, i = node
         o, e = tree.node_range(l, i)
         if l == tree.L:
-            A = lam * np.eye(e - o) + gaussian_kernel(Xp[o:e], Xp[o:e], h)
+            A = lam * np.eye(e - o) + kernel_matrix(Xp[o:e], Xp[o:e], h)
             F.leaf_lu[node] = lu_factor(A)
             return
         left, right = _children(node)
@@ -75,8 +75,8 @@ def factorize(sk: Skeletons, lam: float) -> Factorization:
         fact(right)
         ol, el = tree.node_range(*left)
         orr, er = tree.node_range(*right)
-        K_lr = gaussian_kernel(Xp[ol:el], Xp[sk.skel[right]], h)      # K_{l r~}
-        K_rl = gaussian_kernel(Xp[orr:er], Xp[sk.skel[left]], h)      # K_{r l~}
+        K_lr = kernel_matrix(Xp[ol:el], Xp[sk.skel[right]], h)      # K_{l r~}
+        K_rl = kernel_matrix(Xp[orr:er], Xp[sk.skel[left]], h)      # K_{r l~}
         P_l = full_P(sk, left, F.Pfull)                               # P_{l~ l}
         P_r = full_P(sk, right, F.Pfull)                              # P_{r~ r}
         W_l = solve_node(F, left, K_lr)
@@ -163,7 +163,7 @@ def eps_I(F: Factorization, w: np.ndarray) -> float:
 
 def eps_M_sampled(sk: Skeletons, X: np.ndarray, w: np.ndarray, rows: np.ndarray) -> float:
     """eps_M = ||K w - K~ w|| / ||K w|| restricted to the sampled rows (eq. error, S = 0)."""
-    Kw_rows = gaussian_kernel(np.asarray(X)[rows], X, sk.h) @ w
+    Kw_rows = kernel_matrix(np.asarray(X)[rows], X, sk.h) @ w
     Ktw = apply_operator(sk, 0.0, w)[rows]
     return float(np.linalg.norm(Kw_rows - Ktw) / np.linalg.norm(Kw_rows))
 

@@ -33,7 +33,7 @@ from typing import Dict, Optional
 import numpy as np
 
 from .askit import Node, Skeletons, dense_Ktilde, full_P
-from .kernel import gaussian_kernel
+from .kernel import kernel_matrix
 from .tree import Tree
 
 
@@ -84,11 +84,11 @@ def matvec_knn(sk: Skeletons, lam: float, w: np.ndarray, knn_pos: np.ndarray) ->
             o, e = tree.node_range(l, i)
             if not (o <= t < e):                         # separated under t not in alpha
                 if (l, i) in near:                       # ... but holds a neighbour: exact
-                    U[t] += (gaussian_kernel(xt, Xp[o:e], h) @ W[o:e])[0]
+                    U[t] += (kernel_matrix(xt, Xp[o:e], h) @ W[o:e])[0]
                 else:
-                    U[t] += (gaussian_kernel(xt, Xp[sk.skel[(l, i)]], h) @ wt[(l, i)])[0]
+                    U[t] += (kernel_matrix(xt, Xp[sk.skel[(l, i)]], h) @ wt[(l, i)])[0]
             elif l == tree.L:                            # t's own leaf: exact
-                U[t] += (gaussian_kernel(xt, Xp[o:e], h) @ W[o:e])[0]
+                U[t] += (kernel_matrix(xt, Xp[o:e], h) @ W[o:e])[0]
             else:
                 visit(l + 1, 2 * i)
                 visit(l + 1, 2 * i + 1)
@@ -100,7 +100,7 @@ def matvec_knn(sk: Skeletons, lam: float, w: np.ndarray, knn_pos: np.ndarray) ->
 def dense_Ktilde_knn(sk: Skeletons, knn_pos: np.ndarray) -> np.ndarray:
     """K~ + S assembled entry by entry (permuted order)."""
     tree, Xp, h = sk.tree, sk.Xp, sk.h
-    K = gaussian_kernel(Xp, Xp, h)
+    K = kernel_matrix(Xp, Xp, h)
     Kt = dense_Ktilde(sk)
     out = Kt.copy()
     for i in range(tree.N):
@@ -116,5 +116,5 @@ def S_block(sk: Skeletons, i: int, node: Node) -> np.ndarray:
     """S_{i a} = K_{i a} - K_{i a~} P_{a~ a} for one target and one node of its list."""
     o, e = sk.tree.node_range(*node)
     xi = sk.Xp[i:i + 1]
-    return (gaussian_kernel(xi, sk.Xp[o:e], sk.h)
-            - gaussian_kernel(xi, sk.Xp[sk.skel[node]], sk.h) @ full_P(sk, node))[0]
+    return (kernel_matrix(xi, sk.Xp[o:e], sk.h)
+            - kernel_matrix(xi, sk.Xp[sk.skel[node]], sk.h) @ full_P(sk, node))[0]

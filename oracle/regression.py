@@ -19,7 +19,7 @@ from typing import Optional
 import numpy as np
 
 from .askit import Skeletons, dense_Ktilde
-from .kernel import gaussian_kernel
+from .kernel import kernel_matrix
 from .nearfield import dense_Ktilde_knn
 
 
@@ -37,7 +37,7 @@ def train_weights(sk: Skeletons, lam: float, labels: np.ndarray,
 
 def scores(Xtrain: np.ndarray, h: float, w: np.ndarray, Xtest: np.ndarray) -> np.ndarray:
     """K(Xtest, Xtrain) w: one score per test point (per column of w)."""
-    return gaussian_kernel(np.asarray(Xtest, dtype=np.float64), np.asarray(Xtrain, dtype=np.float64), h) @ w
+    return kernel_matrix(np.asarray(Xtest, dtype=np.float64), np.asarray(Xtrain, dtype=np.float64), h) @ w
 
 
 def classify(s: np.ndarray) -> np.ndarray:

@@ -27,6 +27,8 @@
 #include "pair.cuh"
 #include "tc.cuh"
 
+IA_KERNEL_SPEC_TU(kspec_set_dense)
+
 namespace iaskit {
 
 namespace {
@@ -57,6 +59,7 @@ __global__ void __launch_bounds__(KB_THREADS) kernel_blocks_kernel(const double*
   __shared__ double nr_s[KB_T], nc_s[KB_T];
   __shared__ int ri_s[KB_T], ci_s[KB_T];
   const KDescT<T> D = descs[blockIdx.y];
+  const bool poly = g_kspec.poly != 0;
   const int tr = (D.nrows + KB_T - 1) / KB_T, tcn = (D.ncols + KB_T - 1) / KB_T;
   const int tid = threadIdx.x;
   for (int tile = blockIdx.x; tile < tr * tcn; tile += gridDim.x) {
@@ -97,8 +100,8 @@ __global__ void __launch_bounds__(KB_THREADS) kernel_blocks_kernel(const double*
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
-        if (std::is_same<T, double>::value) {
-          acc[a][b] = fma(xr[a], xc[b], acc[a][b]);
+        if (std::is_same<T, double>::value || poly) {
+          acc[a][b] = fma(xr[a], xc[b], acc[a][b]);  // the dot product (Gram form)
         } else {
           const T t = xr[a] - xc[b];
           acc[a][b] = fma(t, t, acc[a][b]);
@@ -113,9 +116,14 @@ __global__ void __launch_bounds__(KB_THREADS) kernel_blocks_kernel(const double*
       const int li = tx + 16 * a, lj = ty + 16 * b;
       const int i = i0 + li, j = j0 + lj;
       if (i >= D.nrows || j >= D.ncols) continue;
-      T d2 = acc[a][b];
-      if (std::is_same<T, double>::value) d2 = fmax((nr_s[li] + nc_s[lj]) - 2.0 * acc[a][b], 0.0);
-      T v = kexp<T>(d2 * scale);
+      T v;
+      if (poly) {
+        v = kspec_pow<T>(fma(acc[a][b], scale, (T)g_kspec.c), g_kspec.p);
+      } else {
+        T d2 = acc[a][b];
+        if (std::is_same<T, double>::value) d2 = fmax((nr_s[li] + nc_s[lj]) - 2.0 * acc[a][b], 0.0);
+        v = kexp<T>(d2 * scale);
+      }
       if (ri_s[li] == ci_s[lj]) v += (T)D.diag;
       D.out[(size_t)i + (size_t)j * D.ld] = v;
     }
@@ -134,6 +142,7 @@ __global__ void __launch_bounds__(KB_THREADS) kernel_blocks_pair_kernel(const fl
   float2* Xc = Xr + (size_t)d * KB_T;              // [d][KB_T]
   __shared__ int ri_s[KB_T], ci_s[KB_T];
   const KDescT<float2> D = descs[blockIdx.y];
+  const bool poly = g_kspec.poly != 0;
   const fp2::pair scale = fp2::from_double(D.scale), diag = fp2::from_double(D.diag);
   const int tr = (D.nrows + KB_T - 1) / KB_T, tcn = (D.ncols + KB_T - 1) / KB_T;
   const int tid = threadIdx.x;
@@ -171,6 +180,13 @@ __global__ void __launch_bounds__(KB_THREADS) kernel_blocks_pair_kernel(const fl
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
+          if (poly) {  // the dot product as a pair: (sh, sl) += x_r x_c
+            const fp2::pair pr = fp2::mul(fp2::pair{xr[a].x, xr[a].y}, fp2::pair{xc[b].x, xc[b].y});
+            const fp2::pair s2 = fp2::add(fp2::pair{sh[a][b], sl[a][b]}, pr);
+            sh[a][b] = s2.h;
+            sl[a][b] = s2.l;
+            continue;
+          }
           // t = x_r - x_c as th + tl, then (sh, sl) += t^2.  th is often the exact
           // difference of the high parts and tl (the low parts' difference) is then
           // not small against it: t^2 = th^2 + 2 th tl + tl^2 keeps all three terms.
@@ -195,7 +211,14 @@ __global__ void __launch_bounds__(KB_THREADS) kernel_blocks_pair_kernel(const fl
         const int i = i0 + li, j = j0 + lj;
         if (i >= D.nrows || j >= D.ncols) continue;
         const fp2::pair d2 = fp2::renorm(sh[a][b], sl[a][b]);
-        fp2::pair v = fp2::exp_neg(fp2::mul(d2, scale));
+        fp2::pair v;
+        if (poly) {
+          const fp2::pair t = fp2::add(fp2::mul(d2, scale), fp2::from_double(g_kspec.c));
+          v = t;
+          for (int e = 1; e < g_kspec.p; ++e) v = fp2::mul(v, t);
+        } else {
+          v = fp2::exp_neg(fp2::mul(d2, scale));
+        }
         if (ri_s[li] == ci_s[lj]) v = fp2::add(v, diag);
         D.out[(size_t)i + (size_t)j * D.ld] = make_float2(v.h, v.l);
       }
@@ -1983,7 +2006,7 @@ __global__ void __launch_bounds__(MV_THREADS) kernel_matvec_kernel(const double*
         double dot = 0.0;
         for (int q = 0; q < d; ++q) dot = fma(xr[q], xs[kk * d + q], dot);
         const double d2 = fmax((xrn + xcn[kk]) - 2.0 * dot, 0.0);  // Gram form, as kernel_blocks
-        const double kv = exp(d2 * neg_inv_2h2);
+        const double kv = kspec_value(g_kspec, dot, d2, neg_inv_2h2);
         const double* yk = D.y + (size_t)(k0 + kk) + (size_t)c0 * D.ldy;
 #pragma unroll
         for (int c = 0; c < MV_R; ++c)
@@ -2398,6 +2421,11 @@ __global__ void __launch_bounds__(256) kernel_rowsums_kernel(const double* Xp, i
   for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
     const double* xj = Xp + (size_t)(D.pbase + j) * d;
     float d2 = 0.0f;
+    if (g_kspec.poly) {  // |K| of the polynomial kernel from the dot product
+      for (int q = 0; q < d; ++q) d2 = fmaf(xi[q], (float)xj[q], d2);
+      acc += fabsf(kspec_pow(fmaf(d2, sc, (float)g_kspec.c), g_kspec.p));
+      continue;
+    }
     for (int q = 0; q < d; ++q) {
       const float t = xi[q] - (float)xj[q];
       d2 = fmaf(t, t, d2);

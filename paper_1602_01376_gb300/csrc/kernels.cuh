@@ -361,11 +361,12 @@ void kernel_matvec(const double* Xp, const double* xnorm, int d, int nrhs, const
 // over the N points of one problem (Xp rows pbase .. pbase + N - 1, permuted order,
 // xnorm their squared norms, perm[pbase + j] - pbase the original index of j), w in
 // the problem's original order.  T: M x d row-major (device).  part: scratch of
-// predict_scratch_doubles(M, N, nrhs) doubles.  FP64, Gram form.
+// predict_scratch_doubles(M, N, nrhs) doubles.  FP64, Gram form; the kernel of the
+// factorization (kspec), scale the problem's.
 void predict_chunks(int M, int N, int& chunk, int& nchunk);
 size_t predict_scratch_doubles(int M, int N, int nrhs);
 void kernel_predict(const double* T, int M, const double* Xp, const double* xnorm, const int* perm, int pbase,
-                    int N, int d, double h, const double* w, int ldw, int nrhs, double* part, double* out,
+                    int N, int d, double scale, const double* w, int ldw, int nrhs, double* part, double* out,
                     int ldo, cudaStream_t st);
 
 // Near-field correction of the kNN-separated operator (eq. askit, Sec. II-B).  For

@@ -24,6 +24,8 @@
 
 #include "kernels.cuh"
 
+IA_KERNEL_SPEC_TU(kspec_set_near)
+
 namespace iaskit {
 
 namespace {
@@ -131,7 +133,7 @@ __global__ void __launch_bounds__(NF_THREADS) near_tile_kernel(const double* Xp,
       for (int b = 0; b < 4; ++b) {
         const int t = tx + 16 * a, j = ty + 16 * b;
         const double d2 = fmax((nt_s[t] + nc_s[j]) - 2.0 * dot[a][b], 0.0);
-        Ks[t * (NF_T + 1) + j] = (t < nt && j < nc) ? exp(d2 * I.scale) : 0.0;
+        Ks[t * (NF_T + 1) + j] = (t < nt && j < nc) ? kspec_value(g_kspec, dot[a][b], d2, I.scale) : 0.0;
       }
     __syncthreads();
     for (int j = 0; j < nc; ++j) {

@@ -13,6 +13,8 @@
 // order, so the result does not depend on scheduling.
 #include "kernels.cuh"
 
+IA_KERNEL_SPEC_TU(kspec_set_predict)
+
 namespace iaskit {
 
 namespace {
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(PR_THREADS) predict_partial_kernel(
         double dot = 0.0;
         for (int q = 0; q < d; ++q) dot = fma(t[q], xs[(size_t)kk * d + q], dot);
         const double d2 = fmax((tn + xcn[kk]) - 2.0 * dot, 0.0);
-        const double kv = exp(d2 * scale);
+        const double kv = kspec_value(g_kspec, dot, d2, scale);
 #pragma unroll
         for (int c = 0; c < PR_R; ++c) acc[c] = fma(kv, ws[c * PR_TILE + kk], acc[c]);
       }
@@ -100,7 +102,7 @@ void predict_chunks(int M, int N, int& chunk, int& nchunk) {
 }
 
 void kernel_predict(const double* T, int M, const double* Xp, const double* xnorm, const int* perm, int pbase,
-                    int N, int d, double h, const double* w, int ldw, int nrhs, double* part, double* out,
+                    int N, int d, double scale, const double* w, int ldw, int nrhs, double* part, double* out,
                     int ldo, cudaStream_t st) {
   if (M <= 0 || nrhs <= 0) return;
   int chunk = 0, nchunk = 0;
@@ -111,8 +113,8 @@ void kernel_predict(const double* T, int M, const double* Xp, const double* xnor
   ProfScope _ps(PK_PREDICT, st);
   prof().flops[PK_PREDICT] += (double)M * N * (2.0 * d + 2.0 * nrhs);
   dim3 grid(ceil_div((size_t)M, PR_THREADS), (unsigned)nchunk);
-  predict_partial_kernel<<<grid, PR_THREADS, smem, st>>>(T, M, Xp, xnorm, perm, pbase, N, d, -1.0 / (2.0 * h * h),
-                                                          w, ldw, nrhs, chunk, part);
+  predict_partial_kernel<<<grid, PR_THREADS, smem, st>>>(T, M, Xp, xnorm, perm, pbase, N, d, scale, w, ldw, nrhs,
+                                                          chunk, part);
   IA_LAUNCH_CHECK();
   const int64_t tot = (int64_t)M * nrhs;
   predict_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, M, nrhs, nchunk, out, ldo);

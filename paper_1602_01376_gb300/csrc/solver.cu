@@ -109,6 +109,10 @@ struct Options {
   // mixed form with FP64 operator blocks: GMRES's inner operator applies on FP32 pairs,
   // every cycle's residual in FP64 (1), or every apply in FP64 (0)
   int inner_pair = 1;
+  // the kernel of the next factorization: 0 Gaussian, 1 (x . y / h^2 + poly_c)^poly_p
+  int kernel = 0;
+  int poly_p = 2;
+  double poly_c = 1.0;
 };
 
 struct Prob {
@@ -363,6 +367,13 @@ class Solver {
   Stats stats;
   bool factored = false;
   bool skeletonized = false;  // ranks of the current tree are known (set before factor_levels)
+  KernelSpec kspec;           // the kernel of the current factorization
+  // Every translation unit that evaluates kernel values gets the spec (stream-ordered).
+  void use_kernel(const KernelSpec& k) {
+    kspec_set_dense(k, st);
+    kspec_set_near(k, st);
+    kspec_set_predict(k, st);
+  }
   int prec = PREC_FP64;  // precision of the current factorization
   int Ntot = 0, d = 0, s_max = 0, kappa = 0, m_max = 0, Hmax = 0, nleaves = 0;
   double tol = 0;
@@ -700,6 +711,10 @@ class Solver {
     s_max = s_max_;
     tol = tol_;
     prec = opt.precision;
+    kspec = KernelSpec{opt.kernel, opt.poly_p, opt.poly_c};
+    if (kspec.poly && opt.sampling == 1)
+      throw Error(IASKIT_ERR_UNSUPPORTED, "learned sampling is built for the Gaussian kernel");
+    use_kernel(kspec);
     const double t0 = now_ms();
     // problems and tree shapes (data independent)
     pr.assign(in.size(), Prob{});
@@ -710,7 +725,7 @@ class Solver {
       P.N = (int)in[q].N;
       P.h = in[q].h;
       P.lam = in[q].lam;
-      P.scale = -1.0 / (2.0 * P.h * P.h);
+      P.scale = kspec.poly ? 1.0 / (P.h * P.h) : -1.0 / (2.0 * P.h * P.h);
       P.pbase = pbase;
       P.nbase = nbase;
       P.L = 0;
@@ -902,6 +917,7 @@ class Solver {
     for (int q = 0; q < nprob; ++q)
       if (!(lam[q] >= 0.0) || !std::isfinite(lam[q])) throw Error(IASKIT_ERR_ARG, "lambda must be >= 0");
     factored = false;
+    use_kernel(kspec);
     const double t0 = now_ms();
     for (int q = 0; q < nprob; ++q) pr[q].lam = lam[q];
     stats.t_tree = stats.t_knn = stats.t_skel = 0.0;
@@ -1447,6 +1463,7 @@ class Solver {
                      int epochs, double lr) {
     if (epochs < 0 || epochs > 100000) throw Error(IASKIT_ERR_ARG, "invalid epochs");
     if (!(lr > 0.0) || !std::isfinite(lr)) throw Error(IASKIT_ERR_ARG, "invalid learning rate");
+    if (opt.kernel != 0) throw Error(IASKIT_ERR_UNSUPPORTED, "learned sampling is built for the Gaussian kernel");
     const Options saved = opt;
     opt.sampling = 0;
     opt.precision = PREC_FP64;
@@ -2020,7 +2037,8 @@ class Solver {
     check_finite(w, (int64_t)P.N * nrhs, status.as<int>(), st);
     raise_status(read_status_and_clear());
     double* part = pred_part.ensure_n<double>(predict_scratch_doubles((int)M, P.N, nrhs));
-    kernel_predict(T, (int)M, Xp.as<double>(), xnrm.as<double>(), perm.as<int>(), P.pbase, P.N, d, P.h, w, P.N,
+    use_kernel(kspec);
+    kernel_predict(T, (int)M, Xp.as<double>(), xnrm.as<double>(), perm.as<int>(), P.pbase, P.N, d, P.scale, w, P.N,
                    nrhs, part, out, (int)M, st);
     IA_CUDA(cudaStreamSynchronize(st));
     prof().resolve();
@@ -2401,6 +2419,7 @@ class Solver {
   void apply_device(const double* w, double* u, int nrhs) {
     if (!factored) throw Error(IASKIT_ERR_NOT_FACTORED, "no factorization");
     if (nrhs < 1) throw Error(IASKIT_ERR_ARG, "bad nrhs");
+    use_kernel(kspec);
     struct ApplyScope {
       bool& f;
       explicit ApplyScope(bool& flag) : f(flag) { f = true; }
@@ -2871,6 +2890,13 @@ int iaskit_set_option(const char* key, double value) {
       o.knn_prune = as_int(0, 1);
     } else if (k == "inner_pair") {
       o.inner_pair = as_int(0, 1);
+    } else if (k == "kernel") {
+      o.kernel = as_int(0, 1);
+    } else if (k == "poly_p") {
+      o.poly_p = as_int(1, 16);
+    } else if (k == "poly_c") {
+      if (!(value >= 0.0) || !std::isfinite(value)) throw Error(IASKIT_ERR_ARG, "invalid poly_c");
+      o.poly_c = value;
     } else if (k == "profile") {
       int v = as_int(0, 1);
       IA_CUDA(cudaStreamSynchronize(S().st));
@@ -2907,6 +2933,9 @@ int iaskit_get_option(const char* key, double* value) {
     else if (k == "inject_status") *value = o.inject_status;
     else if (k == "knn_prune") *value = o.knn_prune;
     else if (k == "inner_pair") *value = o.inner_pair;
+    else if (k == "kernel") *value = o.kernel;
+    else if (k == "poly_p") *value = o.poly_p;
+    else if (k == "poly_c") *value = o.poly_c;
     else throw Error(IASKIT_ERR_ARG, "unknown option " + k);
   });
 }
@@ -3125,7 +3154,10 @@ int iaskit_kernel_block(const double* points, int64_t N, int d, double h, const 
     h2d(rd, reinterpret_cast<const int*>(rows), nr, st);
     h2d(cd, reinterpret_cast<const int*>(cols), nc, st);
     const int64_t ne = (int64_t)nr * nc;
-    const double scale = -1.0 / (2.0 * h * h);
+    const Options& o = S().opt;
+    const KernelSpec ks{o.kernel, o.poly_p, o.poly_c};
+    S().use_kernel(ks);
+    const double scale = ks.poly ? 1.0 / (h * h) : -1.0 / (2.0 * h * h);
     if (form == 0) {
       double* xn = aux.ensure_n<double>(N);
       point_norms(Xd, (int)N, d, xn, st);
