@@ -305,13 +305,15 @@ int iaskit_get_samples(int level, int index, int32_t* samp, int cap);
 int iaskit_get_P(int level, int index, double* P, int64_t cap);
 
 /*
- * One Gaussian kernel block K(x_rows, x_cols) = exp(-|x_i - x_j|^2 / (2 h^2))
+ * One kernel block, by default the Gaussian K(x_rows, x_cols) = exp(-|x_i - x_j|^2 / (2 h^2))
  * (Sec. I), plus diag where the row and column point are the same, evaluated by the
  * library's kernel-block kernels (independent of any factorization):
  *   form 0  FP64, Gram form |x|^2 + |y|^2 - 2 x.y (the plain form's blocks)
  *   form 1  FP32 pairs, difference form, exp on pairs (the mixed form's operator
  *           blocks); returned as hi + lo
  *   form 2  FP32, difference form (the mixed form's sampled blocks)
+ * With option "kernel" = 1 the block is the polynomial kernel's, (x_i . x_j / h^2 +
+ * "poly_c")^"poly_p", from the dot product in the same three precisions.
  * points: HOST N x d row-major; rows[nr], cols[nc]: HOST point indices in [0, N);
  * out: HOST nr x nc column-major.  Errors: IASKIT_ERR_ARG (null pointer, bad size,
  * index or form), IASKIT_ERR_INPUT (non-finite coordinate).
