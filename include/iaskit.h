@@ -240,12 +240,13 @@ int iaskit_predict_device(const double* d_test, int64_t M, const double* d_w, in
  *                  distance so far; the skipped tiles enter the certification of the
  *                  exact re-rank (default).  0: every pair is scanned.  The lists are
  *                  identical either way [any time]
- *   "inner_pair"   mixed precision, problems with FP64 operator blocks: 1 (default) the
- *                  operator applies inside each GMRES cycle form their FP64 products on
- *                  FP32 pairs (about 2^-44 relative) and a cycle aims at 1e-7 of its
- *                  starting residual, while every cycle's residual is recomputed with
- *                  FP64 products, so the solution is the FP64 operator's; 0: every apply
- *                  in FP64 [any time]
+ *   "inner_pair"   mixed precision, problems with FP64 operator blocks: 1 the operator
+ *                  applies inside each GMRES cycle form their FP64 products on FP32 pairs
+ *                  (about 2^-44 relative) and a cycle aims at 1e-7 of its starting
+ *                  residual, while every cycle's residual is recomputed with FP64
+ *                  products, so the solution is the FP64 operator's; 0 (default): every
+ *                  apply in FP64 (splitting FP64-stored blocks into pairs costs FP64
+ *                  instructions: no faster on C4) [any time]
  *   "kernel"       the kernel of the next factorization: 0 the Gaussian of eq.
  *                  (gaussian), exp(-|x - y|^2 / (2 h^2)) (default); 1 the polynomial
  *                  kernel (x . y / h^2 + "poly_c")^"poly_p" (Sec. IV reports tests with a

@@ -107,8 +107,10 @@ struct Options {
   // every pair; the lists are identical
   int knn_prune = 1;
   // mixed form with FP64 operator blocks: GMRES's inner operator applies on FP32 pairs,
-  // every cycle's residual in FP64 (1), or every apply in FP64 (0)
-  int inner_pair = 1;
+  // every cycle's residual in FP64 (1), or every apply in FP64 (0, the default: the
+  // pair products of FP64-stored blocks split every entry on the FP64 pipe and were
+  // measured no faster than FP64 products on C4)
+  int inner_pair = 0;
   // the kernel of the next factorization: 0 Gaussian, 1 (x . y / h^2 + poly_c)^poly_p
   int kernel = 0;
   int poly_p = 2;
@@ -196,6 +198,14 @@ double getrf_flops(const std::vector<LuDescT<T>>& v) {
   double f = 0;
   for (const auto& d : v) f += 2.0 / 3.0 * d.n * (double)d.n * d.n;
   return f;
+}
+// Algorithmic work of kernel blocks: 2d + 3 flops per entry (the squared distance or
+// dot product, scale and shift) plus one exponential, counted as the entries' flops.
+template <typename D>
+double kblock_flops(const std::vector<D>& kd, int d) {
+  double e = 0;
+  for (const auto& k : kd) e += (double)k.nrows * k.ncols;
+  return e * (2.0 * d + 3.0);
 }
 template <typename T>
 void add_gemm(std::vector<GemmDescT<T>>& g, const T* A, int lda, const T* B, int ldb, T* C,
@@ -1258,6 +1268,7 @@ class Solver {
       arena.clear();
       size_t ok = arena.push(kd), oq = arena.push(qd);
       char* base = upload_arena();
+      prof().flops[pk_of<TS>(PK_KBLOCK)] += kblock_flops(kd, d);
       kernel_blocks<TS>(Xp.as<double>(), xnrm.as<double>(), d, (const KDescT<TS>*)(base + ok), nt, max_e, st);
       cpqr_id<TS>((const CpqrDescT<TS>*)(base + oq), nt, max_r, max_c, s_max, tol, st, opt.cpqr_cluster != 0);
       d2h(rall.data(), rk, nd.size(), st);
@@ -1722,6 +1733,7 @@ class Solver {
         arena.clear();
         size_t ok = arena.push(part);
         char* base = upload_arena();
+        prof().flops[PK_KBLOCK] += kblock_flops(part, d);
         kernel_blocks<double>(Xp.as<double>(), xnrm.as<double>(), d, (const KDesc*)(base + ok), (int)part.size(),
                               kv == &kl ? max_l : max_u, st);
       }
@@ -1741,6 +1753,8 @@ class Solver {
     arena.clear();
     size_t op = arena.push(kp), o64 = arena.push(k64);
     char* base = upload_arena();
+    prof().flops[PK_KBLOCK_PAIR] += kblock_flops(kp, d);
+    prof().flops[PK_KBLOCK] += kblock_flops(k64, d);
     if (!kp.empty())
       kernel_blocks_pair(Xpair.as<float2>(), d, (const KDescT<float2>*)(base + op), (int)kp.size(), max_e, st);
     if (!k64.empty())
@@ -1804,6 +1818,7 @@ class Solver {
     } else {
       size_t ok = arena.push(kd);
       char* base = upload_arena();
+      prof().flops[PK_KBLOCK] += kblock_flops(kd, d);
       kernel_blocks<double>(Xp.as<double>(), xnrm.as<double>(), d, (const KDesc*)(base + ok), nl,
                             (int64_t)m_max * m_max, st);
     }
@@ -1933,6 +1948,7 @@ class Solver {
       } else {
         size_t ok = arena.push(kd);
         char* base = upload_arena();
+        prof().flops[PK_KBLOCK] += kblock_flops(kd, d);
         kernel_blocks<double>(Xp.as<double>(), xnrm.as<double>(), d, (const KDesc*)(base + ok), (int)kd.size(),
                               max_e, st);
       }
