@@ -300,6 +300,9 @@ FP32_LANES_PER_SM = 128              # GB300: FP32 FMA lanes per SM
 PEAK_CLASS = {                       # kernel classes whose arithmetic is FP32
     "kernel_blocks_f32", "cpqr_id_f32", "getrf_f32", "getrs_f32"}
 PAIR_INSTR_PER_MAC = 12              # FP32 instructions of one FP32-pair multiply-add
+HBM_CLASS = {                        # memory-bound classes: algorithmic bytes / time vs HBM
+    "operator_slices",               # FP64 operator blocks as BF16 digits (14 B per entry) on the tensor cores
+    "slice_split"}
 TENSOR_CLASS = {                     # tensor-core classes: nominal dense rate / bf16's
     "knn": (1.1 / 2.25, "TF32"),     # tcgen05 3xTF32 distance tiles, algorithmic work once
     "gemm_f32": (1.1 / 2.25, "TF32"),  # tcgen05 3xTF32 tiles (FP32 CUDA-core tiles with gemm_tc=0)
@@ -353,6 +356,20 @@ def roof_peak(kernel: str, pk: dict, src: str, gp: dict = None) -> tuple:
                 f"measured in this run: cuBLAS FP64 GEMM 4096^3 {gp['fp64_tflops']:.2f} TFLOP/s (burst)")
     peak, how = alu_peak_tflops(kernel, pk.get("sm_max_mhz", 2070.0))
     return ("alu", peak, f"{how} ({src} max clock)")
+
+
+def class_roof(kernel: str, v: dict, pk: dict, src: str, gp: dict = None):
+    """(bound, achieved, peak, unit, how) of one kernel class from its summed event time
+    and algorithmic work (bytes for the memory-bound classes, else flops); None without."""
+    if v["ms"] <= 0:
+        return None
+    if kernel in HBM_CLASS and v.get("bytes", 0) > 0:
+        return ("hbm", v["bytes"] / (v["ms"] / 1e3) / 1e9, pk["hbm_gbs"], "GB/s",
+                f"{src} HBM copy bandwidth {pk['hbm_gbs']:.0f} GB/s")
+    if v["flops"] <= 0:
+        return None
+    bound, peak, how = roof_peak(kernel, pk, src, gp)
+    return (bound, v["flops"] / (v["ms"] / 1e3) / 1e12, peak, "TFLOP/s", how)
 
 
 def alu_peak_tflops(kernel: str, sm_mhz: float) -> tuple:
@@ -486,10 +503,10 @@ def run_batched(args, w, form):
     top = max(kern, key=lambda k: kern[k]["ms"])
     pk, src = peaks()
     roof = None
-    if kern[top]["flops"] > 0 and kern[top]["ms"] > 0:
-        achieved = kern[top]["flops"] / (kern[top]["ms"] / 1e3) / 1e12
-        bound, peak, how = roof_peak(top, pk, src, measure_gemm_peaks())
-        roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    cr = class_roof(top, kern[top], pk, src, measure_gemm_peaks())
+    if cr is not None:
+        bound, achieved, peak, unit, how = cr
+        roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": None, "kernel": top,
                 "peak_source": how, "launches": kern[top]["calls"],
                 "ms_total": kern[top]["ms"]}
@@ -667,22 +684,23 @@ def main():
     top = max(kern, key=lambda k: kern[k]["ms"])
     clocks = chosen["clocks"]
     roof = None
-    if kern[top]["flops"] > 0 and kern[top]["ms"] > 0:
-        achieved = kern[top]["flops"] / (kern[top]["ms"] / 1e3) / 1e12      # TFLOP/s
-        gp = measure_gemm_peaks()
-        bound, peak, how = roof_peak(top, pk, src, gp)
-        roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    gp = measure_gemm_peaks()
+    cr = class_roof(top, kern[top], pk, src, gp)
+    if cr is not None:
+        bound, achieved, peak, unit, how = cr
+        roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": None, "kernel": top,
                 "peak_source": how,
                 "launches": kern[top]["calls"], "ms_total": kern[top]["ms"]}
-        # every class against the peak of its pipe and type
+        # every class against the peak of its pipe and type (HBM for the memory-bound ones)
         roof["by_class"] = {}
         for k, v in kern.items():
-            if v["ms"] > 0 and v["flops"] > 0:
-                b_k, p_k, _ = roof_peak(k, pk, src, gp)
-                a_k = v["flops"] / (v["ms"] / 1e3) / 1e12
+            ck = class_roof(k, v, pk, src, gp)
+            if ck is not None:
+                b_k, a_k, p_k, u_k, _ = ck
                 roof["by_class"][k] = {"ms_per_step": round(v["ms"] / args.steps, 3), "achieved": round(a_k, 3),
-                                       "peak": round(p_k, 2), "frac": round(a_k / p_k, 4), "bound": b_k}
+                                       "peak": round(p_k, 2), "unit": u_k, "frac": round(a_k / p_k, 4),
+                                       "bound": b_k}
         roof["measured_peaks"] = gp
     st = chosen["stats"]
     cfg = config_of(w)

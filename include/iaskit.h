@@ -247,6 +247,17 @@ int iaskit_predict_device(const double* d_test, int64_t M, const double* d_w, in
  *                  products, so the solution is the FP64 operator's; 0 (default): every
  *                  apply in FP64 (splitting FP64-stored blocks into pairs costs FP64
  *                  instructions: no faster on C4) [any time]
+ *   "op_slices"    mixed precision, problems with FP64 operator blocks: 1 (default) the
+ *                  operator's products run on the BF16 tensor cores by exact slicing
+ *                  (Ozaki's error-free splitting): each block row and right-hand-side
+ *                  column is scaled by a power of two and split into 7 signed 8-bit
+ *                  digits (55 bits, |error| <= 2^-56 of the row's or column's largest
+ *                  value), digit products are summed exactly in FP32 on the tensor cores
+ *                  over segments of 128 values and recombined in 64-bit integers and
+ *                  FP64; the digits are kept beside the FP64 blocks (14 bytes per entry)
+ *                  and built at the first apply after a factorization; 0: FP64 products
+ *                  on the FP64 pipe.  Not used by the inner applies of "inner_pair"
+ *                  [any time]
  *   "kernel"       the kernel of the next factorization: 0 the Gaussian of eq.
  *                  (gaussian), exp(-|x - y|^2 / (2 h^2)) (default); 1 the polynomial
  *                  kernel (x . y / h^2 + "poly_c")^"poly_p" (Sec. IV reports tests with a

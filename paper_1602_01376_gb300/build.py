@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libiaskit.so")
-SOURCES = ["prof.cu", "prims.cu", "tree.cu", "knn.cu", "sampling.cu", "dense.cu", "learned.cu", "nearfield.cu", "predict.cu", "solver.cu"]
+SOURCES = ["prof.cu", "prims.cu", "tree.cu", "knn.cu", "sampling.cu", "dense.cu", "learned.cu", "nearfield.cu", "predict.cu", "ozaki.cu", "solver.cu"]
 HEADERS = ["common.cuh", "kernels.cuh", "prims.cuh", "prof.cuh", "kspec.cuh", "pair.cuh", "tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

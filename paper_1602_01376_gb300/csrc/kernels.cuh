@@ -422,6 +422,51 @@ struct RowSumDesc {
 void kernel_rowsums(const double* Xp, int d, const RowSumDesc* descs_dev, int nprob, int max_n,
                     double* out, cudaStream_t st);
 
+// ------------------------------------------- sliced FP64 operator products (a10)
+// FP64 operator blocks applied on the BF16 tensor cores by exact slicing: every value
+// is split into OZ_S signed 8-bit digits under a per-row (per-column for the right-hand
+// sides) power of two, the digit products are summed exactly in FP32 on the tensor
+// cores and recombined in integers and FP64 (ozaki.cu).
+constexpr int OZ_S = 7;                              // digits per value (55 bits)
+constexpr int OZ_TM = 128;                           // rows per tile (MMA M)
+constexpr int OZ_KC = 16;                            // columns per chunk (one MMA K step)
+constexpr int OZ_NR = 16;                            // right-hand sides per pass
+constexpr int OZ_AREC = OZ_S * OZ_TM * OZ_KC * 2;   // bytes of one block chunk (28,672)
+constexpr int OZ_BREC = OZ_S * OZ_NR * OZ_KC * 2;   // bytes of one right-hand-side chunk (3,584)
+// One FP64 block (rows x cols, column-major, ld) into digit records: tiles of 128 rows
+// x chunks of 16 columns x OZ_AREC bytes at rec, row exponents at rexp; tile0 = the
+// first tile of this block among the launch's tiles (blocks in tile order).
+struct OzSplitDesc {
+  const double* src;
+  int ld, rows, cols;
+  unsigned char* rec;
+  int* rexp;
+  int tile0;
+};
+// One K x nrhs block of right-hand sides (column-major, ldw; nrhs <= OZ_NR) into digit
+// records (chunks x OZ_BREC bytes) and OZ_NR column exponents.
+struct OzVecDesc {
+  const double* w;
+  int ldw, K, nrhs;
+  unsigned char* rec;
+  int* cexp;
+};
+// out[r + c ldo] += sum_k A[r, k] w[k, c] for r < rows, c < nrhs: A's records (all its
+// tiles) and row exponents, w's records and column exponents; nch chunks of 16 columns.
+struct OzApplyDesc {
+  const unsigned char* arec;
+  const int* rexp;
+  const unsigned char* brec;
+  const int* cexp;
+  double* out;
+  int ldo, rows, nch, nrhs, tile0;
+};
+size_t oz_arec_bytes(int rows, int cols);
+size_t oz_brec_bytes(int K);
+void oz_split_blocks(const OzSplitDesc* descs_dev, int ndesc, int ntiles, cudaStream_t st);
+void oz_split_vecs(const OzVecDesc* descs_dev, int ndesc, cudaStream_t st);
+void oz_apply(const OzApplyDesc* descs_dev, int ndesc, int ntiles, int* status, cudaStream_t st);
+
 // ------------------------------------------------------ learned sampling (a11)
 // MLP 8 -> 128 -> 128 -> 1 (ReLU).  FP32 master parameters, in this order:
 // W1 [128][8] (row = hidden unit), b1 [128], W2 [128][128] (row = output unit), b2 [128],

@@ -9,7 +9,8 @@ const char* prof_name(int k) {
                                         "misc", "kernel_blocks_f32", "cpqr_id_f32", "getrf_f32",
                                         "getrs_f32", "gemm_f32", "learned_sampling", "mlp_bf16",
                                         "id_judge", "gemm_pair",
-                                        "kernel_blocks_pair", "near_field", "predict"};
+                                        "kernel_blocks_pair", "near_field", "predict",
+                                        "operator_slices", "slice_split"};
   return (k >= 0 && k < PK_COUNT) ? names[k] : "?";
 }
 
@@ -45,6 +46,7 @@ void Profiler::reset() {
     ms[k] = 0;
     calls[k] = 0;
     flops[k] = 0;
+    bytes[k] = 0;
   }
 }
 

@@ -35,6 +35,8 @@ enum ProfKind {
   PK_KBLOCK_PAIR,  // kernel blocks evaluated on FP32 pairs (operator of the mixed form)
   PK_NEAR,         // near-field correction S of the kNN-separated operator
   PK_PREDICT,      // exact kernel sums at test points (kernel regression, eps_M)
+  PK_OZ,           // FP64 operator products by exact BF16 slices (tensor cores)
+  PK_OZ_SPLIT,     // splitting FP64 blocks and right-hand sides into BF16 digits
   PK_COUNT
 };
 
@@ -59,6 +61,7 @@ struct Profiler {
   double ms[PK_COUNT] = {};
   long long calls[PK_COUNT] = {};
   double flops[PK_COUNT] = {};
+  double bytes[PK_COUNT] = {};  // algorithmic device-memory bytes (memory-bound classes)
   long long launches = 0;
   struct Pending {
     int kind;

@@ -111,6 +111,9 @@ struct Options {
   // pair products of FP64-stored blocks split every entry on the FP64 pipe and were
   // measured no faster than FP64 products on C4)
   int inner_pair = 0;
+  // mixed form with FP64 operator blocks: the operator's FP64 products on the BF16
+  // tensor cores by exact 8-bit slicing (1, default), or on the FP64 pipe (0)
+  int op_slices = 1;
   // the kernel of the next factorization: 0 Gaussian, 1 (x . y / h^2 + poly_c)^poly_p
   int kernel = 0;
   int poly_p = 2;
@@ -156,7 +159,7 @@ struct Stats {
   int knn_fallback = 0;
   KnnPruneStats knn_prune;
   double near_values = 0.0;
-  int64_t bytes_W = 0, bytes_LU = 0, bytes_P = 0, bytes_operator = 0;
+  int64_t bytes_W = 0, bytes_LU = 0, bytes_P = 0, bytes_operator = 0, bytes_slices = 0;
   std::vector<double> refine_hist;
   int refine_sweeps = 0;
   int refine_iters = 0;       // GMRES iterations (operator applications) of the last solve
@@ -701,6 +704,7 @@ class Solver {
     factored = false;
     skeletonized = false;
     near_ready = false;
+    slices_ready = false;
     if (in.empty()) throw Error(IASKIT_ERR_ARG, "no problem");
     if (d_ < 1) throw Error(IASKIT_ERR_ARG, "d must be >= 1");
     if (leaf_m < 2) throw Error(IASKIT_ERR_ARG, "leaf_m must be >= 2");
@@ -927,12 +931,14 @@ class Solver {
     for (int q = 0; q < nprob; ++q)
       if (!(lam[q] >= 0.0) || !std::isfinite(lam[q])) throw Error(IASKIT_ERR_ARG, "lambda must be >= 0");
     factored = false;
+    slices_ready = false;
     use_kernel(kspec);
     const double t0 = now_ms();
     for (int q = 0; q < nprob; ++q) pr[q].lam = lam[q];
     stats.t_tree = stats.t_knn = stats.t_skel = 0.0;
     stats.t_solve = stats.t_apply = 0.0;
     stats.bytes_operator = 0;
+    stats.bytes_slices = 0;
     stats.refine_hist.clear();
     stats.refine_sweeps = stats.refine_iters = stats.refine_stagnated = 0;
     choose_precisions();
@@ -1684,6 +1690,7 @@ class Solver {
   // The operator blocks of the given problems re-evaluated in FP64 (same offsets, same
   // bytes per entry); the apply then uses FP64 products for them.
   void upgrade_operator(const std::vector<int>& probs) {
+    slices_ready = false;
     std::vector<KDesc> kl, ku;
     int64_t max_l = 0, max_u = 0;
     const int* sk = skel.as<int>();
@@ -2432,6 +2439,123 @@ class Solver {
     }
   }
 
+  // ------------------------------------------------- sliced FP64 operator blocks
+  // The mixed form's FP64 operator blocks (problems with op64) as BF16 digit records for
+  // the tensor-core products of ozaki.cu, split from Kleaf / Ustore at the first apply
+  // after a factorization, a refactorization or an operator upgrade.
+  bool slices_ready = false;
+  DevBuf ozrec, ozexp, ozb;
+  std::vector<int64_t> oz_lrec, oz_lexp, oz_urec, oz_uexp;  // per node: leaf and U block (-1: none)
+  size_t ozb_bytes = 0;  // B records of the largest Evaluate launch (OZ_NR columns each)
+  bool sliced(int g) const { return prec == PREC_MIXED && opt.op_slices && pr[nd[g].prob].op64; }
+  void build_slices() {
+    const size_t nn = nd.size();
+    oz_lrec.assign(nn, -1);
+    oz_lexp.assign(nn, -1);
+    oz_urec.assign(nn, -1);
+    oz_uexp.assign(nn, -1);
+    size_t rb = 0;
+    int64_t eb = 0;
+    for (size_t g = 0; g < nn; ++g) {
+      if (!sliced((int)g)) continue;
+      const Node& n = nd[g];
+      if (is_leaf((int)g)) {
+        oz_lrec[g] = (int64_t)rb;
+        rb += oz_arec_bytes(n.size, n.size);
+        oz_lexp[g] = eb;
+        eb += n.size;
+      }
+      if (!is_root((int)g) && nd[sibling((int)g)].s > 0) {
+        oz_urec[g] = (int64_t)rb;
+        rb += oz_arec_bytes(n.size, nd[sibling((int)g)].s);
+        oz_uexp[g] = eb;
+        eb += n.size;
+      }
+    }
+    // B records of one Evaluate launch: one height's U blocks, or the leaf blocks
+    ozb_bytes = 0;
+    for (int hh = 0; hh <= Hmax; ++hh) {
+      size_t bu = 0, bl = 0;
+      for (int c : by_height[hh]) {
+        if (oz_urec[c] >= 0) bu += oz_brec_bytes(nd[sibling(c)].s) + 256;
+        if (oz_lrec[c] >= 0) bl += oz_brec_bytes(nd[c].size) + 256;
+      }
+      ozb_bytes = std::max(ozb_bytes, std::max(bu, bl));
+    }
+    if (rb == 0) {
+      slices_ready = true;
+      return;
+    }
+    if (opt.mem_cap_gb > 0 && (double)rb > opt.mem_cap_gb * 1e9)
+      throw Error(IASKIT_ERR_NOMEM, "sliced operator exceeds mem_cap_gb");
+    unsigned char* rec = ozrec.ensure_n<unsigned char>(rb);
+    int* ex = ozexp.ensure_n<int>((size_t)eb);
+    ozb.ensure_n<unsigned char>(std::max<size_t>(ozb_bytes, 256));
+    stats.bytes_slices = (int64_t)rb + eb * 4;
+    std::vector<OzSplitDesc> sd;
+    int tiles = 0;
+    for (size_t g = 0; g < nn; ++g) {
+      const Node& n = nd[g];
+      if (oz_lrec[g] >= 0) {
+        sd.push_back(OzSplitDesc{Kleaf.as<double>() + n.K_off, n.size, n.size, n.size, rec + oz_lrec[g],
+                                 ex + oz_lexp[g], tiles});
+        tiles += (int)ceil_div((size_t)n.size, OZ_TM);
+      }
+      if (oz_urec[g] >= 0) {
+        sd.push_back(OzSplitDesc{Ustore.as<double>() + n.U_off, n.size, n.size, nd[sibling((int)g)].s,
+                                 rec + oz_urec[g], ex + oz_uexp[g], tiles});
+        tiles += (int)ceil_div((size_t)n.size, OZ_TM);
+      }
+    }
+    arena.clear();
+    const size_t od = arena.push(sd);
+    char* base = upload_arena();
+    prof().bytes[PK_OZ_SPLIT] += (double)rb + (double)rb / (OZ_S * 2) * 8;  // digits written, FP64 read
+    oz_split_blocks((const OzSplitDesc*)(base + od), (int)sd.size(), tiles, st);
+    slices_ready = true;
+  }
+  // One Evaluate launch of sliced blocks: out += A w per job, OZ_NR columns per pass.
+  struct OzJob {
+    const unsigned char* arec;
+    const int* rexp;
+    int rows, K;
+    const double* w;
+    int ldw;
+    double* out;
+    int ldo;
+  };
+  void run_slices(const std::vector<OzJob>& jobs, int nrhs) {
+    if (jobs.empty()) return;
+    for (int g0 = 0; g0 < nrhs; g0 += OZ_NR) {
+      const int nr = std::min(OZ_NR, nrhs - g0);
+      std::vector<OzVecDesc> vd;
+      std::vector<OzApplyDesc> ad;
+      unsigned char* brec = ozb.as<unsigned char>();
+      size_t bo = 0;
+      int tiles = 0;
+      double flops = 0, bytes = 0;
+      for (const OzJob& J : jobs) {
+        int* cexp = reinterpret_cast<int*>(brec + bo);  // 16 exponents, then the records
+        unsigned char* rec = brec + bo + 256;
+        bo += oz_brec_bytes(J.K) + 256;
+        vd.push_back(OzVecDesc{J.w + (size_t)g0 * J.ldw, J.ldw, J.K, nr, rec, cexp});
+        ad.push_back(OzApplyDesc{J.arec, J.rexp, rec, cexp, J.out + (size_t)g0 * J.ldo, J.ldo, J.rows,
+                                 (int)ceil_div((size_t)J.K, OZ_KC), nr, tiles});
+        tiles += (int)ceil_div((size_t)J.rows, OZ_TM);
+        flops += 2.0 * J.rows * J.K * nr;
+        bytes += (double)oz_arec_bytes(J.rows, J.K) + 2.0 * 8.0 * J.rows * nr;
+      }
+      if (bo > ozb.bytes) throw Error(IASKIT_ERR_UNSUPPORTED, "sliced operator: right-hand-side records");
+      arena.clear();
+      const size_t ov = arena.push(vd), oa = arena.push(ad);
+      char* base = upload_arena();
+      prof().flops[PK_OZ] += flops;
+      prof().bytes[PK_OZ] += bytes;
+      oz_split_vecs((const OzVecDesc*)(base + ov), (int)vd.size(), st);
+      oz_apply((const OzApplyDesc*)(base + oa), (int)ad.size(), tiles, status.as<int>(), st);
+    }
+  }
+
   void apply_device(const double* w, double* u, int nrhs) {
     if (!factored) throw Error(IASKIT_ERR_NOT_FACTORED, "no factorization");
     if (nrhs < 1) throw Error(IASKIT_ERR_ARG, "bad nrhs");
@@ -2495,15 +2619,29 @@ class Solver {
     }
     // Evaluate: one launch per height keeps the rows written by a launch disjoint
     int* sk = skel.as<int>();
+    const bool use_oz = stored && opt.op_slices && !apply_low;
+    if (use_oz && !slices_ready) build_slices();
+    bool oz_ran = false;
     for (int hh = 0; hh <= Hmax; ++hh) {
       for (int pass = 0; pass < 2; ++pass) {  // pass 0: sibling skeletons, pass 1: leaf blocks
         if (pass == 1 && hh != 0) continue;
         std::vector<GemmDescPair> g;
         std::vector<GemmDesc> g64;
         std::vector<KMatvecDesc> md;
+        std::vector<OzJob> oz;
         int max_rows = 0;
         for (int c : by_height[hh]) {
           if (pass == 0 && is_root(c)) continue;
+          if (use_oz && sliced(c)) {  // FP64 blocks on the tensor cores
+            const Prob& P = pr[nd[c].prob];
+            if (pass == 0 && oz_urec[c] >= 0)
+              oz.push_back(OzJob{ozrec.as<unsigned char>() + oz_urec[c], ozexp.as<int>() + oz_uexp[c], nd[c].size,
+                                 nd[sibling(c)].s, wsib(c), n2(parent(c)), rows(Up, c), P.N});
+            else if (pass == 1 && oz_lrec[c] >= 0)
+              oz.push_back(OzJob{ozrec.as<unsigned char>() + oz_lrec[c], ozexp.as<int>() + oz_lexp[c], nd[c].size,
+                                 nd[c].size, rows(Wp, c), ldp(c), rows(Up, c), P.N});
+            continue;
+          }
           if (pass == 0) {
             const int sib = sibling(c);
             if (stored && pr[nd[c].prob].op64)
@@ -2531,6 +2669,8 @@ class Solver {
         if (stored) {
           run_pair_gemms(g);
           run_gemms(g64);
+          run_slices(oz, nrhs);
+          oz_ran = oz_ran || !oz.empty();
         } else if (!md.empty()) {
           arena.clear();
           size_t om = arena.push(md);
@@ -2545,6 +2685,7 @@ class Solver {
     if (opt.near_field && Hmax > 0 && kappa > 0) near_field_apply(Wp, WT, woff, Up, nrhs);
     gather(Up, u, nrhs, blocks, true);
     IA_CUDA(cudaStreamSynchronize(st));
+    if (oz_ran) raise_status(read_status_and_clear());
     prof().resolve();
     stats.t_apply = now_ms() - t0;
   }
@@ -2553,6 +2694,7 @@ class Solver {
     factored = false;
     skeletonized = false;
     near_ready = false;
+    slices_ready = false;
     DevBuf* all[] = {&X, &Xp, &perm, &iperm, &pid, &knn, &knn_pos, &samp, &ranks, &skel,
                      &piv_ws, &A_ws, &status, &arena_dev, &step_dev, &tbuf, &vbuf, &vbuf32,
                      &ubuf, &rbuf, &wt, &io, &normbuf, &blocks_dev, &LU, &LUpiv, &Wb, &Zb, &Zpiv,
@@ -2561,7 +2703,8 @@ class Solver {
                      &l_feat, &l_score, &l_linfo, &l_samp, &l_rk, &l_Ptmp, &l_sktmp, &l_hold, &l_err,
                      &l_cols, &l_gram, &l_dense, &mlp_master, &mlp_m, &mlp_v, &mlp_grad, &mlp_b16,
                      &mlp_loss, &tr_feat, &tr_tgt, &tr_lev, &tr_bx, &tr_bt, &tr_y, &tr_H1, &tr_H2, &tr_idx,
-                     &xnrm, &pred_part, &pred_io, &kperm, &kiperm, &Xk, &near_mask, &near_tgt, &near_part, &near_io};
+                     &xnrm, &pred_part, &pred_io, &kperm, &kiperm, &Xk, &near_mask, &near_tgt, &near_part, &near_io,
+                     &ozrec, &ozexp, &ozb};
     mlp_ready = false;
     for (DevBuf* b : all) b->release();
     tree_s.release();
@@ -2906,6 +3049,8 @@ int iaskit_set_option(const char* key, double value) {
       o.knn_prune = as_int(0, 1);
     } else if (k == "inner_pair") {
       o.inner_pair = as_int(0, 1);
+    } else if (k == "op_slices") {
+      o.op_slices = as_int(0, 1);
     } else if (k == "kernel") {
       o.kernel = as_int(0, 1);
     } else if (k == "poly_p") {
@@ -2949,6 +3094,7 @@ int iaskit_get_option(const char* key, double* value) {
     else if (k == "inject_status") *value = o.inject_status;
     else if (k == "knn_prune") *value = o.knn_prune;
     else if (k == "inner_pair") *value = o.inner_pair;
+    else if (k == "op_slices") *value = o.op_slices;
     else if (k == "kernel") *value = o.kernel;
     else if (k == "poly_p") *value = o.poly_p;
     else if (k == "poly_c") *value = o.poly_c;
@@ -2969,12 +3115,12 @@ int iaskit_stats(char* buf, size_t len) {
            "\"N\":%d,\"d\":%d,\"problems\":%d,\"L\":%d,\"factored\":%s,\"ms\":{\"tree\":%.3f,"
            "\"knn\":%.3f,\"skeletonize\":%.3f,\"leaf_lu\":%.3f,\"factor_levels\":%.3f,"
            "\"factor\":%.3f,\"solve\":%.3f,\"apply\":%.3f},\"knn_fallback\":%d,\"bytes\":{\"W\":%lld,"
-           "\"LU\":%lld,\"P\":%lld,\"operator\":%lld},\"precision\":\"%s\",\"refine_sweeps\":%d,",
+           "\"LU\":%lld,\"P\":%lld,\"operator\":%lld,\"operator_slices\":%lld},\"precision\":\"%s\",\"refine_sweeps\":%d,",
            s.Ntot, s.d, (int)s.pr.size(), s.Hmax, s.factored ? "true" : "false", s.stats.t_tree,
            s.stats.t_knn, s.stats.t_skel, s.stats.t_leaf_lu, s.stats.t_factor_levels,
            s.stats.t_factor, s.stats.t_solve, s.stats.t_apply, s.stats.knn_fallback,
            (long long)s.stats.bytes_W, (long long)s.stats.bytes_LU, (long long)s.stats.bytes_P,
-           (long long)s.stats.bytes_operator, s.prec == PREC_MIXED ? "mixed" : "fp64",
+           (long long)s.stats.bytes_operator, (long long)s.stats.bytes_slices, s.prec == PREC_MIXED ? "mixed" : "fp64",
            s.stats.refine_sweeps);
   j += tmp;
   j += "\"refine_history\":[";
@@ -3021,8 +3167,8 @@ int iaskit_stats(char* buf, size_t len) {
   j += std::to_string(prof().launches);
   j += ",\"kernels\":{";
   for (int k = 0; k < PK_COUNT; ++k) {
-    snprintf(tmp, sizeof tmp, "%s\"%s\":{\"ms\":%.4f,\"calls\":%lld,\"flops\":%.6g}", k ? "," : "",
-             prof_name(k), prof().ms[k], prof().calls[k], prof().flops[k]);
+    snprintf(tmp, sizeof tmp, "%s\"%s\":{\"ms\":%.4f,\"calls\":%lld,\"flops\":%.6g,\"bytes\":%.6g}",
+             k ? "," : "", prof_name(k), prof().ms[k], prof().calls[k], prof().flops[k], prof().bytes[k]);
     j += tmp;
   }
   // rank profile of the last skeletonization (also after a factorization that stopped
