@@ -250,14 +250,14 @@ int iaskit_predict_device(const double* d_test, int64_t M, const double* d_w, in
  *   "op_slices"    mixed precision, problems with FP64 operator blocks: 1 (default) the
  *                  operator's products run on the BF16 tensor cores by exact slicing
  *                  (Ozaki's error-free splitting): each block row and right-hand-side
- *                  column is scaled by a power of two and split into 7 signed 8-bit
- *                  digits (55 bits, |error| <= 2^-56 of the row's or column's largest
+ *                  column is scaled by a power of two and split into 8 signed 8-bit
+ *                  digits (63 bits, |error| <= 2^-64 of the row's or column's largest
  *                  value), digit products are summed exactly in FP32 on the tensor cores
  *                  over segments of 128 values and recombined in 64-bit integers and
- *                  FP64; the digits are kept beside the FP64 blocks (14 bytes per entry)
- *                  and built at the first apply after a factorization; 0: FP64 products
- *                  on the FP64 pipe.  Not used by the inner applies of "inner_pair"
- *                  [any time]
+ *                  FP64; the digits of the operator blocks and of P are kept beside the
+ *                  FP64 ones (16 bytes per entry) and built at the first apply after a
+ *                  factorization; 0: FP64 products on the FP64 pipe.  Not used by the
+ *                  inner applies of "inner_pair" [any time]
  *   "kernel"       the kernel of the next factorization: 0 the Gaussian of eq.
  *                  (gaussian), exp(-|x - y|^2 / (2 h^2)) (default); 1 the polynomial
  *                  kernel (x . y / h^2 + "poly_c")^"poly_p" (Sec. IV reports tests with a
@@ -324,11 +324,15 @@ int iaskit_get_P(int level, int index, double* P, int64_t cap);
  *   form 1  FP32 pairs, difference form, exp on pairs (the mixed form's operator
  *           blocks); returned as hi + lo
  *   form 2  FP32, difference form (the mixed form's sampled blocks)
+ *   form 3  FP64 Gram form with the dot products on the BF16 tensor cores from 8-digit
+ *           slices of the coordinates (the mixed form's FP64 operator blocks under
+ *           "op_slices"); Gaussian kernel and d <= 64 only (else IASKIT_ERR_UNSUPPORTED)
  * With option "kernel" = 1 the block is the polynomial kernel's, (x_i . x_j / h^2 +
- * "poly_c")^"poly_p", from the dot product in the same three precisions.
+ * "poly_c")^"poly_p", from the dot product in the first three precisions.
  * points: HOST N x d row-major; rows[nr], cols[nc]: HOST point indices in [0, N);
  * out: HOST nr x nc column-major.  Errors: IASKIT_ERR_ARG (null pointer, bad size,
- * index or form), IASKIT_ERR_INPUT (non-finite coordinate).
+ * index or form), IASKIT_ERR_INPUT (non-finite coordinate), IASKIT_ERR_UNSUPPORTED
+ * (form 3 outside its range), IASKIT_ERR_TIMEOUT (an expired bounded wait of form 3).
  */
 int iaskit_kernel_block(const double* points, int64_t N, int d, double h, const int32_t* rows, int nr,
                         const int32_t* cols, int nc, double diag, int form, double* out);

@@ -383,12 +383,13 @@ def iaskit_get_P(level: int, index: int, s: int, cap: int = 1 << 22) -> np.ndarr
     return out[: s * nc].reshape(nc, s).T.copy()
 
 
-KERNEL_FORMS = {"fp64": 0, "pair": 1, "fp32": 2}
+KERNEL_FORMS = {"fp64": 0, "pair": 1, "fp32": 2, "sliced": 3}
 
 
 def iaskit_kernel_block(points, h: float, rows, cols, diag: float = 0.0, form: str = "fp64") -> np.ndarray:
     """K(x_rows, x_cols) (+ diag where row point == column point) from the library's
-    kernel-block kernels: form "fp64", "pair" (FP32 pairs) or "fp32"."""
+    kernel-block kernels: form "fp64", "pair" (FP32 pairs), "fp32" or "sliced" (FP64 with
+    the dot products on the tensor cores)."""
     X = np.ascontiguousarray(points, dtype=np.float64)
     r = np.ascontiguousarray(rows, dtype=np.int32)
     c = np.ascontiguousarray(cols, dtype=np.int32)

@@ -427,12 +427,12 @@ void kernel_rowsums(const double* Xp, int d, const RowSumDesc* descs_dev, int np
 // is split into OZ_S signed 8-bit digits under a per-row (per-column for the right-hand
 // sides) power of two, the digit products are summed exactly in FP32 on the tensor
 // cores and recombined in integers and FP64 (ozaki.cu).
-constexpr int OZ_S = 7;                              // digits per value (55 bits)
+constexpr int OZ_S = 8;                              // digits per value (63 bits)
 constexpr int OZ_TM = 128;                           // rows per tile (MMA M)
 constexpr int OZ_KC = 16;                            // columns per chunk (one MMA K step)
 constexpr int OZ_NR = 16;                            // right-hand sides per pass
-constexpr int OZ_AREC = OZ_S * OZ_TM * OZ_KC * 2;   // bytes of one block chunk (28,672)
-constexpr int OZ_BREC = OZ_S * OZ_NR * OZ_KC * 2;   // bytes of one right-hand-side chunk (3,584)
+constexpr int OZ_AREC = OZ_S * OZ_TM * OZ_KC * 2;   // bytes of one block chunk (32,768)
+constexpr int OZ_BREC = OZ_S * OZ_NR * OZ_KC * 2;   // bytes of one right-hand-side chunk (4,096)
 // One FP64 block (rows x cols, column-major, ld) into digit records: tiles of 128 rows
 // x chunks of 16 columns x OZ_AREC bytes at rec, row exponents at rexp; tile0 = the
 // first tile of this block among the launch's tiles (blocks in tile order).
@@ -451,16 +451,36 @@ struct OzVecDesc {
   unsigned char* rec;
   int* cexp;
 };
-// out[r + c ldo] += sum_k A[r, k] w[k, c] for r < rows, c < nrhs: A's records (all its
-// tiles) and row exponents, w's records and column exponents; nch chunks of 16 columns.
+// out[r + c ldo] (+)= sum_k A[r, k] w[k, c] for r < rows, c < nrhs (add = 0: overwrite):
+// A's records (all its tiles) and row exponents, w's records and column exponents; nch
+// chunks of 16 columns.
 struct OzApplyDesc {
   const unsigned char* arec;
   const int* rexp;
   const unsigned char* brec;
   const int* cexp;
   double* out;
-  int ldo, rows, nch, nrhs, tile0;
+  int ldo, rows, nch, nrhs, tile0, add;
 };
+// Gaussian kernel blocks with the dot products on the tensor cores (digits of every
+// point's coordinates: XD, OZ_S x oz_dpad(d) BF16 per point, and XE, built by oz_points):
+// out[i + j ld] = exp(scale (|x_r|^2 + |x_c|^2 - 2 x_r.x_c)) (+ diag when r == c) for the
+// rows r = row0 + i (i < nrows) and the columns c = colsA[j] (j < nA), colsB[j - nA], or
+// col0 + j without lists; tile0 = the first 128-row tile of this block in the launch.
+// The diagonal shift goes where ident[r] == ident[c] (r == c without ident).
+struct OzKDesc {
+  const int* colsA;
+  const int* colsB;
+  double* out;
+  int row0, nrows, col0, nA, ncols, ld;
+  double diag, scale;
+  int tile0;
+  const int* ident;
+};
+int oz_dpad(int d);  // coordinates per point in XD (d rounded up to 16), 0 above 64
+void oz_points(const double* X, int N, int d, uint16_t* XD, int* XE, cudaStream_t st);
+void oz_kblocks(const uint16_t* XD, const int* XE, const double* xn, int d, const OzKDesc* descs_dev, int ndesc,
+                int ntiles, int* status, cudaStream_t st);
 size_t oz_arec_bytes(int rows, int cols);
 size_t oz_brec_bytes(int K);
 void oz_split_blocks(const OzSplitDesc* descs_dev, int ndesc, int ntiles, cudaStream_t st);

@@ -7,18 +7,20 @@
 // tensor cores, and the sums are recombined in integers and FP64.
 //
 // Splitting.  A row r of a block gets the exponent E_r of its largest |a_rk| (so that
-// |a_rk| 2^-E_r < 1) and a_rk = 2^E_r sum_i A_i[r, k] 2^(-7 - 8 i) + e with integer digits
-// |A_i| <= 128 and |e| <= 2^(E_r - 56); a column c of the right-hand sides gets F_c and
-// digits W_j the same way.  Then
+// |a_rk| 2^-E_r < 1) and a_rk = 2^E_r sum_i A_i[r, k] 2^(-7 - 8 i) + e with OZ_S = 8
+// integer digits |A_i| <= 128 and |e| <= 2^(E_r - 64); a column c of the right-hand sides
+// gets F_c and digits W_j the same way.  Then
 //     sum_k a_rk w_kc ~ 2^(E_r + F_c - 14) sum_{t=0}^{OZ_S-1} 2^(-8 t) S_t,
 //     S_t = sum_{i+j=t} sum_k A_i[r, k] W_j[k, c],
-// the products with i + j >= OZ_S dropped (each below 2^-56 of max|a| max|w| per term).
-// Every S_t is an integer of magnitude <= 7 * 128 * 2^14 < 2^24 over 128 values of k, so
+// the products with i + j >= OZ_S dropped (each below 2^-64 of max|a| max|w| per term).
+// Every S_t is an integer of magnitude <= 8 * 128 * 2^14 = 2^24 over 128 values of k, so
 // an FP32 accumulator holds it exactly: the tensor core accumulates the diagonal t of a
 // 128-wide segment of k in one set of TMEM columns (the MMA of digit i of A writes its
 // product with [W_0 .. W_{OZ_S-1-i}] starting at diagonal i), and the epilogue adds the
-// segments in 64-bit integers.  The result's error is of the order of an FP64 product's
-// (a few 2^-53 of sum |a| |w| per entry for the blocks of a kernel matrix).
+// segments in 64-bit integers.  The truncation errors, about 2^-60 K max|a| max|w| per
+// entry, lie below an FP64 product's rounding (2^-53 sum |a| |w|) unless a row's or a
+// column's entries span more than 2^7; 7 digits (2^-52 K max|a| max|w|) measurably
+// raised the refinement's floor on C4 (1.06e-10 against 3.1e-11).
 //
 // Records.  A block's digits are stored once per factorization as 128-row tiles of
 // 16-column chunks, each chunk the OZ_S operands of one MMA step in the tensor core's
@@ -40,15 +42,19 @@ constexpr int OZ_NS = 3;                       // pipeline stages (chunks in fli
 constexpr int OZ_STAGE = OZ_AREC + OZ_BREC;    // bytes of one stage
 constexpr int OZ_SEGC = 8;                     // chunks of one exact segment (k = 128)
 constexpr int OZ_TCOLS = 256;                  // TMEM columns: two accumulators of OZ_S x 16
+constexpr int OZ_HI = 4;                       // diagonals summed into the high 64-bit word
 constexpr int OZ_ABUF = 128;                   // column distance of the two accumulators
 constexpr long OZ_WAIT = 1L << 22;             // bound of every mbarrier wait (try_wait calls)
 constexpr int OZ_THREADS = 160;                // warps 0-3: epilogue (TMEM lanes), warp 4: issue
 
 static_assert(OZ_S * OZ_NR <= OZ_ABUF, "an accumulator holds OZ_S diagonals of 16 columns");
+static_assert((long long)OZ_S * OZ_SEGC * OZ_KC * 128 * 128 <= (1ll << 24),
+              "a diagonal's sum over one segment stays within FP32's exact integers");
+static_assert(OZ_S > OZ_HI && 8 * OZ_S - 1 <= 63, "digits of a 64-bit fixed-point value");
 
 // Digits of a (|a| < 2^E): a = 2^E sum_i dg[i] 2^(-7 - 8 i) + e, |dg[i]| <= 128,
-// |e| <= 2^(E - 56).  V = round(|a| 2^(55 - E)) < 2^55 + 1 from the FP64 fields, then
-// signed base-256 digits from the lowest.
+// |e| <= 2^(E - 8 OZ_S).  V = round(|a| 2^(8 OZ_S - 1 - E)) <= 2^(8 OZ_S - 1) from the
+// FP64 fields, then signed base-256 digits from the lowest.
 __device__ __forceinline__ void oz_digits(double a, int E, int (&dg)[OZ_S]) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(a);
   int ex = (int)((bits >> 52) & 0x7FF);
@@ -173,7 +179,8 @@ __global__ void __launch_bounds__(128) oz_vec_kernel(const OzVecDesc* descs) {
 // bulk copy (OZ_NS stages) and issues OZ_S MMAs per chunk into the accumulator of the
 // chunk's segment (two accumulators alternate); warps 0-3 read a finished segment's
 // diagonals from TMEM (lane = row), convert them to integers and add them into 64-bit
-// sums, and at the end add 2^(E_r + F_c - 14) sum_t 2^(-8 t) S_t into the output.  Every
+// sums, and at the end add 2^(E_r + F_c - 14) sum_t 2^(-8 t) S_t into the output (or
+// write it).  Every
 // wait is bounded; a wait that gives up sets DEV_TIMEOUT, the issuing thread stops,
 // waits (bounded) for its MMAs and copies in flight, and the block frees its TMEM.
 __global__ void __launch_bounds__(OZ_THREADS, 2) oz_apply_kernel(const OzApplyDesc* descs, int nd, int* status) {
@@ -276,8 +283,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 2) oz_apply_kernel(const OzApplyDe
 #pragma unroll
         for (int c = 0; c < OZ_NR; ++c) {
           const long long s = (long long)__float2int_rn(v[c]);
-          if (q < 4) hi[c] += s * (1ll << (8 * (3 - q)));
-          else lo[c] += s * (1ll << (8 * (6 - q)));
+          if (q < OZ_HI) hi[c] += s * (1ll << (8 * (OZ_HI - 1 - q)));
+          else lo[c] += s * (1ll << (8 * (OZ_S - 1 - q)));
         }
       }
       tc::fence_before_sync();
@@ -291,7 +298,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 2) oz_apply_kernel(const OzApplyDe
         if (c < D.nrhs) {
           const int e = E + D.cexp[c];
           double* o = D.out + (size_t)row + (size_t)c * D.ldo;
-          *o += ldexp((double)hi[c], e - 38) + ldexp((double)lo[c], e - 62);
+          const double y = ldexp((double)hi[c], e - 14 - 8 * (OZ_HI - 1)) +
+                           ldexp((double)lo[c], e - 14 - 8 * (OZ_S - 1));
+          *o = D.add ? *o + y : y;
         }
     }
   }
@@ -301,7 +310,237 @@ __global__ void __launch_bounds__(OZ_THREADS, 2) oz_apply_kernel(const OzApplyDe
   if (warp == 0) tc::tmem_free(tmem, OZ_TCOLS);
 }
 
+// ------------------------------------------------------------ kernel blocks
+// Gaussian kernel blocks K_ij = exp(-(|x_i|^2 + |y_j|^2 - 2 x_i.y_j) / (2 h^2)) (+ diag on
+// the diagonal) with the dot products x_i.y_j on the tensor cores: every point's
+// coordinates are split once into OZ_S digits under the point's own power of two (the
+// same splitting as above, here with K = the dimension, at most 64, so a diagonal sums at
+// most 8 * 64 products of 2^14 and stays exact), and the Gram form, exp and the diagonal
+// shift run in FP64 on the dot products recombined from the diagonals.  The dot product's
+// error, about 2^-60 d max|x_i| max|y_j|, is below the Gram form's own cancellation
+// error 2^-52 (|x_i|^2 + |y_j|^2).
+
+// Point digits: XE[p] = exponent of the point's largest |coordinate|, XD[(p OZ_S + i) DP
+// + k] = digit i of coordinate k (zero for k >= d).  DP / 8 threads per point.
+__global__ void oz_points_kernel(const double* X, int N, int d, int DP, uint16_t* XD, int* XE) {
+  const int g = DP / 8;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long p = e / g;
+  const int kq = (int)(e % g);
+  const bool valid = p < N;
+  double mx = 0.0;
+  if (valid)
+    for (int k = kq * 8; k < min(d, kq * 8 + 8); ++k) mx = fmax(mx, fabs(X[(size_t)p * d + k]));
+  for (int o = g / 2; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  int E = 0;
+  if (mx > 0.0) frexp(mx, &E);
+  if (!valid) return;
+  if (kq == 0) XE[p] = E;
+  uint32_t pk[OZ_S][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int k = kq * 8 + 2 * q;
+    int d0[OZ_S], d1[OZ_S];
+    oz_digits(k < d ? X[(size_t)p * d + k] : 0.0, E, d0);
+    oz_digits(k + 1 < d ? X[(size_t)p * d + k + 1] : 0.0, E, d1);
+#pragma unroll
+    for (int i = 0; i < OZ_S; ++i) pk[i][q] = oz_bf16(d0[i]) | (oz_bf16(d1[i]) << 16);
+  }
+#pragma unroll
+  for (int i = 0; i < OZ_S; ++i)
+    *reinterpret_cast<uint4*>(XD + ((size_t)p * OZ_S + i) * DP + kq * 8) =
+        make_uint4(pk[i][0], pk[i][1], pk[i][2], pk[i][3]);
+}
+
+constexpr int OZK_TC = 32;        // columns per tile: OZ_S digits x 32 = 256 B-operand rows
+constexpr int OZK_THREADS = 256;  // 8 warps: warp w reads TMEM lanes 32 (w % 4), columns 16 (w / 4)
+constexpr long OZK_WAIT = 1L << 22;
+constexpr double OZ_LO_SCALE = 1.0 / (double)(1ull << (8 * (OZ_S - OZ_HI)));  // lo's weight against hi
+
+__device__ __forceinline__ double oz_pow2(int e) {
+  return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
+}
+
+// One block per 128-row tile of a descriptor (rows row0 + i, consecutive points): the
+// tile's digits stay in shared memory (A: OZ_S operands of 128 x DP); per tile of 32
+// columns the columns' digits are gathered (B: OZ_S * 32 rows, digit j of column c at row
+// 32 j + c) and one thread issues OZ_S MMAs per 16 coordinates into one of two TMEM
+// accumulators, so that the MMAs of tile c + 1 run while all threads finish tile c.
+template <int DP>
+__global__ void __launch_bounds__(OZK_THREADS, 1) oz_kblock_kernel(const uint16_t* XD, const int* XE, const double* xn,
+                                                                   const OzKDesc* descs, int nd, int* status) {
+  extern __shared__ __align__(1024) unsigned char ok_sh[];
+  constexpr int ABYTES = OZ_TM * DP * 2;  // one digit operand of the row tile
+  constexpr int BROWS = OZ_S * OZK_TC;
+  constexpr int BBYTES = BROWS * DP * 2;
+  constexpr uint32_t SBO = (DP / 8) * 128;
+  constexpr int PCS = DP / 8;              // 16-byte pieces of one digit row
+  unsigned char* As = ok_sh;
+  unsigned char* Bs = ok_sh + OZ_S * ABYTES;
+  __shared__ int pj_s[2][OZK_TC], ej_s[2][OZK_TC], idj_s[2][OZK_TC];
+  __shared__ double nj_s[2][OZK_TC];
+  __shared__ uint64_t mbar[2], fin;
+  __shared__ uint32_t tslot;
+  const int tid = (int)threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const OzKDesc D = descs[oz_find(descs, nd, (int)blockIdx.x)];
+  const int i0 = ((int)blockIdx.x - D.tile0) * OZ_TM;
+  const int nct = (D.ncols + OZK_TC - 1) / OZK_TC;
+  if (warp == 0) tc::tmem_alloc(&tslot, 512);
+  if (tid == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+    tc::mbar_init(&fin, 1);
+  }
+  for (int e = tid; e < OZ_S * OZ_TM * PCS; e += OZK_THREADS) {
+    const int kq = e % PCS, r = (e / PCS) % OZ_TM, i = e / (PCS * OZ_TM);
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (i0 + r < D.nrows)
+      v = *reinterpret_cast<const uint4*>(XD + ((size_t)(D.row0 + i0 + r) * OZ_S + i) * DP + kq * 8);
+    *reinterpret_cast<uint4*>(As + i * ABYTES + (r >> 3) * SBO + kq * 128 + (r & 7) * 16) = v;
+  }
+  auto gather = [&](int ct, int b) {  // all threads; ends with the operand visible to the MMA
+    if (tid < OZK_TC) {
+      const int j = ct * OZK_TC + tid;
+      int p = -1;
+      if (j < D.ncols) p = D.colsA ? (j < D.nA ? D.colsA[j] : D.colsB[j - D.nA]) : D.col0 + j;
+      pj_s[b][tid] = p;
+      idj_s[b][tid] = p >= 0 && D.ident ? D.ident[p] : p;
+      ej_s[b][tid] = p >= 0 ? XE[p] : 0;
+      nj_s[b][tid] = p >= 0 ? xn[p] : 0.0;
+    }
+    __syncthreads();
+    unsigned char* Bb = Bs + b * BBYTES;
+    for (int e = tid; e < BROWS * PCS; e += OZK_THREADS) {
+      const int kq = e % PCS, n = e / PCS, c = n % OZK_TC, jd = n / OZK_TC;
+      const int p = pj_s[b][c];
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (p >= 0) v = *reinterpret_cast<const uint4*>(XD + ((size_t)p * OZ_S + jd) * DP + kq * 8);
+      *reinterpret_cast<uint4*>(Bb + (n >> 3) * SBO + kq * 128 + (n & 7) * 16) = v;
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+  };
+  auto issue = [&](int b, uint32_t tmem) {  // thread 0
+    tc::fence_after_sync();
+    const uint32_t a0 = tc::smem_addr(As), b0 = tc::smem_addr(Bs + b * BBYTES);
+#pragma unroll 1
+    for (int ks = 0; ks < DP / 16; ++ks)
+#pragma unroll
+      for (int i = 0; i < OZ_S; ++i)
+        tc::mma_f16(tmem + (uint32_t)(b * 256 + i * OZK_TC), tc::smem_desc(a0 + i * ABYTES + ks * 256, 128, SBO),
+                    tc::smem_desc(b0 + ks * 256, 128, SBO), tc::idesc_bf16(OZ_TM, (OZ_S - i) * OZK_TC),
+                    !(ks == 0 && i == 0));
+    tc::mma_commit(&mbar[b]);
+  };
+  if (nct > 0) gather(0, 0);  // block-uniform
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  if (tid == 0 && nct > 0) issue(0, tmem);
+  const int q = warp & 3, hh = warp >> 2;
+  const int r = q * 32 + lane, i = i0 + r;
+  const bool rv = i < D.nrows;
+  const int pi = D.row0 + (rv ? i : 0);
+  const int idi = D.ident ? D.ident[pi] : pi;
+  const int Ei = XE[pi];
+  const double ni = xn[pi];
+  bool failed = false;
+  for (int ct = 0; ct < nct; ++ct) {
+    const int b = ct & 1;
+    if (ct + 1 < nct) {  // MMA ct - 1 is complete and its accumulator read: reuse both
+      gather(ct + 1, b ^ 1);
+      if (tid == 0) issue(b ^ 1, tmem);
+    }
+    const bool got = tc::mbar_wait(&mbar[b], (uint32_t)((ct >> 1) & 1), OZK_WAIT);
+    if (__syncthreads_or(!got)) {
+      failed = true;
+      break;
+    }
+    tc::fence_after_sync();
+    long long hi[16], lo[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) hi[c] = lo[c] = 0;
+#pragma unroll
+    for (int t = 0; t < OZ_S; ++t) {
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 256 + t * OZK_TC + hh * 16), v);
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const long long sv = (long long)__float2int_rn(v[c]);
+        if (t < OZ_HI) hi[c] += sv * (1ll << (8 * (OZ_HI - 1 - t)));
+        else lo[c] += sv * (1ll << (8 * (OZ_S - 1 - t)));
+      }
+    }
+    if (rv) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int cc = hh * 16 + c, j = ct * OZK_TC + cc;
+        if (j >= D.ncols) continue;
+        const int e = Ei + ej_s[b][cc] - 14 - 8 * (OZ_HI - 1);
+        const double dot = fma((double)lo[c], OZ_LO_SCALE, (double)hi[c]) * oz_pow2(e);
+        const double d2 = fmax((ni + nj_s[b][cc]) - 2.0 * dot, 0.0);
+        double kv = exp(d2 * D.scale);
+        if (idi == idj_s[b][cc]) kv += D.diag;
+        D.out[(size_t)i + (size_t)j * D.ld] = kv;
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();  // accumulator b and its column data are free for tile ct + 2
+  }
+  if (failed) {
+    if (tid == 0) {
+      atomicOr(status, DEV_TIMEOUT);
+      tc::mma_commit(&fin);  // every MMA issued so far
+      tc::mbar_wait(&fin, 0, OZK_WAIT);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_free(tmem, 512);
+}
+
 }  // namespace
+
+int oz_dpad(int d) { return d >= 1 && d <= 64 ? (d + 15) / 16 * 16 : 0; }
+
+void oz_points(const double* X, int N, int d, uint16_t* XD, int* XE, cudaStream_t st) {
+  const int DP = oz_dpad(d);
+  if (N <= 0 || DP == 0) return;
+  ProfScope _ps(PK_OZ_SPLIT, st);
+  const long long thr = (long long)N * (DP / 8);
+  oz_points_kernel<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(X, N, d, DP, XD, XE);
+  IA_LAUNCH_CHECK();
+}
+
+template <int DP>
+static void launch_kblock(const uint16_t* XD, const int* XE, const double* xn, const OzKDesc* descs_dev, int ndesc,
+                          int ntiles, int* status, cudaStream_t st) {
+  // at least 116 KB, so that one block holds an SM (its 512 TMEM columns are all of them)
+  const int smem = std::max(OZ_S * OZ_TM * DP * 2 + 2 * OZ_S * OZK_TC * DP * 2, 116 * 1024);
+  static bool attr = false;
+  if (!attr) {
+    IA_CUDA(cudaFuncSetAttribute(oz_kblock_kernel<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr = true;
+  }
+  oz_kblock_kernel<DP><<<ntiles, OZK_THREADS, smem, st>>>(XD, XE, xn, descs_dev, ndesc, status);
+  IA_LAUNCH_CHECK();
+}
+
+void oz_kblocks(const uint16_t* XD, const int* XE, const double* xn, int d, const OzKDesc* descs_dev, int ndesc,
+                int ntiles, int* status, cudaStream_t st) {
+  if (ndesc <= 0 || ntiles <= 0) return;
+  ProfScope _ps(PK_KBLOCK_OZ, st);
+  switch (oz_dpad(d)) {
+    case 16: launch_kblock<16>(XD, XE, xn, descs_dev, ndesc, ntiles, status, st); break;
+    case 32: launch_kblock<32>(XD, XE, xn, descs_dev, ndesc, ntiles, status, st); break;
+    case 48: launch_kblock<48>(XD, XE, xn, descs_dev, ndesc, ntiles, status, st); break;
+    case 64: launch_kblock<64>(XD, XE, xn, descs_dev, ndesc, ntiles, status, st); break;
+    default: throw Error(IASKIT_ERR_UNSUPPORTED, "sliced kernel blocks: dimension above 64");
+  }
+}
 
 size_t oz_arec_bytes(int rows, int cols) {
   if (rows <= 0 || cols <= 0) return 0;

@@ -37,6 +37,7 @@ enum ProfKind {
   PK_PREDICT,      // exact kernel sums at test points (kernel regression, eps_M)
   PK_OZ,           // FP64 operator products by exact BF16 slices (tensor cores)
   PK_OZ_SPLIT,     // splitting FP64 blocks and right-hand sides into BF16 digits
+  PK_KBLOCK_OZ,    // FP64 kernel blocks with the dot products on the tensor cores
   PK_COUNT
 };
 

@@ -705,6 +705,7 @@ class Solver {
     skeletonized = false;
     near_ready = false;
     slices_ready = false;
+    xdig_ready = false;
     if (in.empty()) throw Error(IASKIT_ERR_ARG, "no problem");
     if (d_ < 1) throw Error(IASKIT_ERR_ARG, "d must be >= 1");
     if (leaf_m < 2) throw Error(IASKIT_ERR_ARG, "leaf_m must be >= 2");
@@ -1737,12 +1738,7 @@ class Solver {
       for (size_t b = 0; b < kv->size(); b += 65535) {
         const size_t e = std::min(kv->size(), b + 65535);
         std::vector<KDesc> part(kv->begin() + b, kv->begin() + e);
-        arena.clear();
-        size_t ok = arena.push(part);
-        char* base = upload_arena();
-        prof().flops[PK_KBLOCK] += kblock_flops(part, d);
-        kernel_blocks<double>(Xp.as<double>(), xnrm.as<double>(), d, (const KDesc*)(base + ok), (int)part.size(),
-                              kv == &kl ? max_l : max_u, st);
+        kblocks64(part, kv == &kl ? max_l : max_u);
       }
     }
   }
@@ -1758,15 +1754,50 @@ class Solver {
       else kp.push_back(pair_desc(kd[i]));
     }
     arena.clear();
-    size_t op = arena.push(kp), o64 = arena.push(k64);
+    size_t op = arena.push(kp);
     char* base = upload_arena();
     prof().flops[PK_KBLOCK_PAIR] += kblock_flops(kp, d);
-    prof().flops[PK_KBLOCK] += kblock_flops(k64, d);
     if (!kp.empty())
       kernel_blocks_pair(Xpair.as<float2>(), d, (const KDescT<float2>*)(base + op), (int)kp.size(), max_e, st);
-    if (!k64.empty())
-      kernel_blocks<double>(Xp.as<double>(), xnrm.as<double>(), d, (const KDesc*)(base + o64), (int)k64.size(),
-                            max_e, st);
+    kblocks64(k64, max_e);
+  }
+  // FP64 operator blocks (leaf and U blocks: consecutive rows): with op_slices and the
+  // Gaussian, dot products on the tensor cores from the points' digits (built once per
+  // factorization), else the FP64 Gram form.
+  bool xdig_ready = false;
+  DevBuf ozXD, ozXE;
+  void kblocks64(const std::vector<KDesc>& kd, int64_t max_e) {
+    if (kd.empty()) return;
+    bool sliced_ok = prec == PREC_MIXED && opt.op_slices && kspec.poly == 0 && oz_dpad(d) > 0;
+    for (const KDesc& k : kd) sliced_ok = sliced_ok && k.rows == nullptr;
+    arena.clear();
+    if (!sliced_ok) {
+      const size_t ok = arena.push(kd);
+      char* base = upload_arena();
+      prof().flops[PK_KBLOCK] += kblock_flops(kd, d);
+      kernel_blocks<double>(Xp.as<double>(), xnrm.as<double>(), d, (const KDesc*)(base + ok), (int)kd.size(), max_e,
+                            st);
+      return;
+    }
+    if (!xdig_ready) {
+      uint16_t* XD = ozXD.ensure_n<uint16_t>((size_t)Ntot * OZ_S * oz_dpad(d));
+      int* XE = ozXE.ensure_n<int>((size_t)Ntot);
+      oz_points(Xp.as<double>(), Ntot, d, XD, XE, st);
+      xdig_ready = true;
+    }
+    std::vector<OzKDesc> od;
+    int tiles = 0;
+    for (const KDesc& k : kd) {
+      if (k.nrows <= 0 || k.ncols <= 0) continue;
+      od.push_back(OzKDesc{k.colsA, k.colsB, k.out, k.row0, k.nrows, k.col0, k.nA, k.ncols, k.ld, k.diag, k.scale,
+                           tiles, nullptr});
+      tiles += (int)ceil_div((size_t)k.nrows, OZ_TM);
+    }
+    const size_t oo = arena.push(od);
+    char* base = upload_arena();
+    prof().flops[PK_KBLOCK_OZ] += kblock_flops(kd, d);
+    oz_kblocks(ozXD.as<uint16_t>(), ozXE.as<int>(), xnrm.as<double>(), d, (const OzKDesc*)(base + oo), (int)od.size(),
+               tiles, status.as<int>(), st);
   }
   // FP32 and FP64 solve copies of operator blocks; list [t] holds the ranges whose
   // operator is in FP64 (t = 1) or in FP32 pairs (t = 0).
@@ -2445,7 +2476,7 @@ class Solver {
   // after a factorization, a refactorization or an operator upgrade.
   bool slices_ready = false;
   DevBuf ozrec, ozexp, ozb;
-  std::vector<int64_t> oz_lrec, oz_lexp, oz_urec, oz_uexp;  // per node: leaf and U block (-1: none)
+  std::vector<int64_t> oz_lrec, oz_lexp, oz_urec, oz_uexp, oz_prec, oz_pexp;  // per node (-1: none)
   size_t ozb_bytes = 0;  // B records of the largest Evaluate launch (OZ_NR columns each)
   bool sliced(int g) const { return prec == PREC_MIXED && opt.op_slices && pr[nd[g].prob].op64; }
   void build_slices() {
@@ -2454,6 +2485,8 @@ class Solver {
     oz_lexp.assign(nn, -1);
     oz_urec.assign(nn, -1);
     oz_uexp.assign(nn, -1);
+    oz_prec.assign(nn, -1);
+    oz_pexp.assign(nn, -1);
     size_t rb = 0;
     int64_t eb = 0;
     for (size_t g = 0; g < nn; ++g) {
@@ -2471,16 +2504,23 @@ class Solver {
         oz_uexp[g] = eb;
         eb += n.size;
       }
+      if (!is_root((int)g) && n.s > 0 && n.ncols > 0) {  // P of the skeletonize step
+        oz_prec[g] = (int64_t)rb;
+        rb += oz_arec_bytes(n.s, n.ncols);
+        oz_pexp[g] = eb;
+        eb += n.s;
+      }
     }
     // B records of one Evaluate launch: one height's U blocks, or the leaf blocks
     ozb_bytes = 0;
     for (int hh = 0; hh <= Hmax; ++hh) {
-      size_t bu = 0, bl = 0;
+      size_t bu = 0, bl = 0, bp = 0;
       for (int c : by_height[hh]) {
         if (oz_urec[c] >= 0) bu += oz_brec_bytes(nd[sibling(c)].s) + 256;
         if (oz_lrec[c] >= 0) bl += oz_brec_bytes(nd[c].size) + 256;
+        if (oz_prec[c] >= 0) bp += oz_brec_bytes(nd[c].ncols) + 256;
       }
-      ozb_bytes = std::max(ozb_bytes, std::max(bu, bl));
+      ozb_bytes = std::max(ozb_bytes, std::max(bp, std::max(bu, bl)));
     }
     if (rb == 0) {
       slices_ready = true;
@@ -2506,6 +2546,11 @@ class Solver {
                                  rec + oz_urec[g], ex + oz_uexp[g], tiles});
         tiles += (int)ceil_div((size_t)n.size, OZ_TM);
       }
+      if (oz_prec[g] >= 0) {
+        sd.push_back(OzSplitDesc{Pd.as<double>() + n.P_off, n.s, n.s, n.ncols, rec + oz_prec[g], ex + oz_pexp[g],
+                                 tiles});
+        tiles += (int)ceil_div((size_t)n.s, OZ_TM);
+      }
     }
     arena.clear();
     const size_t od = arena.push(sd);
@@ -2514,7 +2559,8 @@ class Solver {
     oz_split_blocks((const OzSplitDesc*)(base + od), (int)sd.size(), tiles, st);
     slices_ready = true;
   }
-  // One Evaluate launch of sliced blocks: out += A w per job, OZ_NR columns per pass.
+  // One launch of sliced blocks: out (+)= A w per job (add = 0: out = A w), OZ_NR columns
+  // per pass.
   struct OzJob {
     const unsigned char* arec;
     const int* rexp;
@@ -2523,6 +2569,7 @@ class Solver {
     int ldw;
     double* out;
     int ldo;
+    int add;
   };
   void run_slices(const std::vector<OzJob>& jobs, int nrhs) {
     if (jobs.empty()) return;
@@ -2540,7 +2587,7 @@ class Solver {
         bo += oz_brec_bytes(J.K) + 256;
         vd.push_back(OzVecDesc{J.w + (size_t)g0 * J.ldw, J.ldw, J.K, nr, rec, cexp});
         ad.push_back(OzApplyDesc{J.arec, J.rexp, rec, cexp, J.out + (size_t)g0 * J.ldo, J.ldo, J.rows,
-                                 (int)ceil_div((size_t)J.K, OZ_KC), nr, tiles});
+                                 (int)ceil_div((size_t)J.K, OZ_KC), nr, tiles, J.add});
         tiles += (int)ceil_div((size_t)J.rows, OZ_TM);
         flops += 2.0 * J.rows * J.K * nr;
         bytes += (double)oz_arec_bytes(J.rows, J.K) + 2.0 * 8.0 * J.rows * nr;
@@ -2599,14 +2646,24 @@ class Solver {
     };
     // Skeletonize: w~ = P w, leaves first, up to the children of the roots
     const float2* Pp = Ppair.as<float2>();
+    const bool use_oz = stored && opt.op_slices && !apply_low;
+    if (use_oz && !slices_ready) build_slices();
+    bool oz_ran = false;
     for (int hh = 0; hh < Hmax; ++hh) {
       std::vector<GemmDesc> g;
       std::vector<GemmDescPair> gp;
+      std::vector<OzJob> oz;
       for (int c : by_height[hh]) {
         if (is_root(c)) continue;
         const int par = parent(c);
         const double* src = hh == 0 ? rows(Wp, c) : WT + woff[c];
         const int lds = hh == 0 ? ldp(c) : n2(c);
+        if (use_oz && sliced(c)) {  // FP64 P on the tensor cores
+          if (oz_prec[c] >= 0)
+            oz.push_back(OzJob{ozrec.as<unsigned char>() + oz_prec[c], ozexp.as<int>() + oz_pexp[c], nd[c].s,
+                               nd[c].ncols, src, lds, WT + woff[par] + rowoff(c), n2(par), 0});
+          continue;
+        }
         if (stored && !pr[nd[c].prob].op64)
           add_pair_gemm(gp, Pp + nd[c].P_off, nd[c].s, src, lds, WT + woff[par] + rowoff(c), n2(par), nd[c].s,
                         nrhs, nd[c].ncols, 0.0);
@@ -2616,12 +2673,11 @@ class Solver {
       }
       run_gemms(g);
       run_pair_gemms(gp);
+      run_slices(oz, nrhs);
+      oz_ran = oz_ran || !oz.empty();
     }
     // Evaluate: one launch per height keeps the rows written by a launch disjoint
     int* sk = skel.as<int>();
-    const bool use_oz = stored && opt.op_slices && !apply_low;
-    if (use_oz && !slices_ready) build_slices();
-    bool oz_ran = false;
     for (int hh = 0; hh <= Hmax; ++hh) {
       for (int pass = 0; pass < 2; ++pass) {  // pass 0: sibling skeletons, pass 1: leaf blocks
         if (pass == 1 && hh != 0) continue;
@@ -2636,10 +2692,10 @@ class Solver {
             const Prob& P = pr[nd[c].prob];
             if (pass == 0 && oz_urec[c] >= 0)
               oz.push_back(OzJob{ozrec.as<unsigned char>() + oz_urec[c], ozexp.as<int>() + oz_uexp[c], nd[c].size,
-                                 nd[sibling(c)].s, wsib(c), n2(parent(c)), rows(Up, c), P.N});
+                                 nd[sibling(c)].s, wsib(c), n2(parent(c)), rows(Up, c), P.N, 1});
             else if (pass == 1 && oz_lrec[c] >= 0)
               oz.push_back(OzJob{ozrec.as<unsigned char>() + oz_lrec[c], ozexp.as<int>() + oz_lexp[c], nd[c].size,
-                                 nd[c].size, rows(Wp, c), ldp(c), rows(Up, c), P.N});
+                                 nd[c].size, rows(Wp, c), ldp(c), rows(Up, c), P.N, 1});
             continue;
           }
           if (pass == 0) {
@@ -2695,6 +2751,7 @@ class Solver {
     skeletonized = false;
     near_ready = false;
     slices_ready = false;
+    xdig_ready = false;
     DevBuf* all[] = {&X, &Xp, &perm, &iperm, &pid, &knn, &knn_pos, &samp, &ranks, &skel,
                      &piv_ws, &A_ws, &status, &arena_dev, &step_dev, &tbuf, &vbuf, &vbuf32,
                      &ubuf, &rbuf, &wt, &io, &normbuf, &blocks_dev, &LU, &LUpiv, &Wb, &Zb, &Zpiv,
@@ -2704,7 +2761,7 @@ class Solver {
                      &l_cols, &l_gram, &l_dense, &mlp_master, &mlp_m, &mlp_v, &mlp_grad, &mlp_b16,
                      &mlp_loss, &tr_feat, &tr_tgt, &tr_lev, &tr_bx, &tr_bt, &tr_y, &tr_H1, &tr_H2, &tr_idx,
                      &xnrm, &pred_part, &pred_io, &kperm, &kiperm, &Xk, &near_mask, &near_tgt, &near_part, &near_io,
-                     &ozrec, &ozexp, &ozb};
+                     &ozrec, &ozexp, &ozb, &ozXD, &ozXE};
     mlp_ready = false;
     for (DevBuf* b : all) b->release();
     tree_s.release();
@@ -3299,7 +3356,7 @@ int iaskit_kernel_block(const double* points, int64_t N, int d, double h, const 
                         const int32_t* cols, int nc, double diag, int form, double* out) {
   return guarded([&] {
     if (!points || !rows || !cols || !out) throw Error(IASKIT_ERR_ARG, "null argument");
-    if (N < 1 || N > INT_MAX || d < 1 || nr < 1 || nc < 1 || !(h > 0) || form < 0 || form > 2)
+    if (N < 1 || N > INT_MAX || d < 1 || nr < 1 || nc < 1 || !(h > 0) || form < 0 || form > 3)
       throw Error(IASKIT_ERR_ARG, "invalid size, bandwidth or form");
     for (int i = 0; i < nr; ++i)
       if (rows[i] < 0 || rows[i] >= N) throw Error(IASKIT_ERR_ARG, "row index out of range");
@@ -3342,6 +3399,44 @@ int iaskit_kernel_block(const double* points, int64_t N, int d, double h, const 
       d2h(hv.data(), o, ne, st);
       IA_CUDA(cudaStreamSynchronize(st));
       for (int64_t e = 0; e < ne; ++e) out[e] = (double)hv[e].x + (double)hv[e].y;
+    } else if (form == 3) {
+      // sliced: the rows' points first (consecutive), then all points; identities for the
+      // diagonal shift
+      if (ks.poly || oz_dpad(d) == 0 || N + nr > INT_MAX)
+        throw Error(IASKIT_ERR_UNSUPPORTED, "sliced kernel blocks: Gaussian kernel and d <= 64 only");
+      const int64_t M = N + nr;
+      std::vector<double> Y((size_t)M * d);
+      for (int i = 0; i < nr; ++i)
+        std::memcpy(&Y[(size_t)i * d], points + (size_t)rows[i] * d, sizeof(double) * d);
+      std::memcpy(&Y[(size_t)nr * d], points, sizeof(double) * N * d);
+      std::vector<int> ident(M), cs(nc);
+      for (int i = 0; i < nr; ++i) ident[i] = rows[i];
+      for (int64_t p = 0; p < N; ++p) ident[nr + p] = (int)p;
+      for (int j = 0; j < nc; ++j) cs[j] = nr + cols[j];
+      DevBuf Yb, yn, idb, xd, xe, cb, sb;
+      double* Yd = Yb.ensure_n<double>((size_t)M * d);
+      h2d(Yd, Y.data(), Y.size(), st);
+      double* ynd = yn.ensure_n<double>(M);
+      point_norms(Yd, (int)M, d, ynd, st);
+      int* idd = idb.ensure_n<int>(M);
+      h2d(idd, ident.data(), M, st);
+      int* csd = cb.ensure_n<int>(nc);
+      h2d(csd, cs.data(), nc, st);
+      uint16_t* XD = xd.ensure_n<uint16_t>((size_t)M * OZ_S * oz_dpad(d));
+      int* XE = xe.ensure_n<int>(M);
+      oz_points(Yd, (int)M, d, XD, XE, st);
+      double* o = ob.ensure_n<double>(ne);
+      OzKDesc k{csd, nullptr, o, 0, nr, 0, nc, nc, nr, diag, scale, 0, idd};
+      OzKDesc* kd = db.ensure_n<OzKDesc>(1);
+      h2d(kd, &k, 1, st);
+      int* stw = sb.ensure_n<int>(1);
+      IA_CUDA(cudaMemsetAsync(stw, 0, sizeof(int), st));
+      oz_kblocks(XD, XE, ynd, d, kd, 1, (int)ceil_div((size_t)nr, OZ_TM), stw, st);
+      int sv = 0;
+      d2h(&sv, stw, 1, st);
+      d2h(out, o, ne, st);
+      IA_CUDA(cudaStreamSynchronize(st));
+      if (sv & DEV_TIMEOUT) throw Error(IASKIT_ERR_TIMEOUT, "bounded device wait expired");
     } else {
       float* o = ob.ensure_n<float>(ne);
       KDescT<float> k{rd, cd, nullptr, o, 0, nr, 0, nc, nc, nr, diag, scale};

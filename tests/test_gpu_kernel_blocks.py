@@ -15,6 +15,13 @@
   and a ragged edge; the tolerance adds the oracle's own rounding (d 2^-53 of the
   squared distance) and, for FP64, the Gram form's cancellation bound.
 * values under the FP32 normal range come back as 0 from the pair form.
+* "sliced" (FP64 Gram form with the dot products on the tensor cores from 8-digit slices
+  of the coordinates: the mixed form's FP64 operator blocks) against the oracle with the
+  FP64 form's bound (the slices' dot-product error, about 2^-60 d max|x| max|y|, lies far
+  below the Gram form's cancellation), bit for bit equal to the FP64 form on points with
+  small integer coordinates (every dot product exact in both), on ragged 128-row and
+  32-column tiles and for d = 3, 8, 54 and 64 (the four operand widths); refused for the
+  polynomial kernel and for d > 64.
 """
 from decimal import Decimal, getcontext
 from fractions import Fraction
@@ -80,7 +87,7 @@ def test_pair_blocks_match_exact_values(gpu_lib, gmm):
     assert worst <= 1.0
 
 
-@pytest.mark.parametrize("form", ["fp64", "pair", "fp32"])
+@pytest.mark.parametrize("form", ["fp64", "pair", "fp32", "sliced"])
 def test_forms_match_oracle_blocks(gpu_lib, gmm, form):
     ia = gpu_lib
     X, rows, cols = gmm
@@ -91,7 +98,7 @@ def test_forms_match_oracle_blocks(gpu_lib, gmm, form):
         a = sqdist(X[rows], X[cols]) / (2 * h * h)
         base = np.exp(-a)
         oracle_err = d * 2.0 ** -53 * a * base
-        if form == "fp64":
+        if form in ("fp64", "sliced"):
             nrm = (X ** 2).sum(axis=1)
             tol = 8 * 2.0 ** -53 * (nrm[rows][:, None] + nrm[cols][None, :]) / (2 * h * h) * base + 4 * 2.0 ** -53 * np.abs(ref)
         elif form == "pair":
@@ -107,7 +114,7 @@ def test_ragged_and_degenerate_blocks(gpu_lib):
     X = np.random.default_rng(5).random((300, 3))
     # one entry, a single row, a column of identical points
     for rows, cols in (([7], [7]), ([3], list(range(130))), (list(range(200)), [11, 11, 11])):
-        for form in ("fp64", "pair", "fp32"):
+        for form in ("fp64", "pair", "fp32", "sliced"):
             K = ia.iaskit_kernel_block(X, 0.3, rows, cols, 0.5, form=form)
             ref = _oracle(X, np.array(rows), np.array(cols), 0.3, 0.5)
             assert K.shape == ref.shape
@@ -126,6 +133,37 @@ def test_ragged_and_degenerate_blocks(gpu_lib):
     assert small.any() and big.any() and np.all(K[small] == 0.0)
     tol = _pair_rel_tol(X, np.arange(100), np.arange(100, 250), 0.02) + 3 * 2.0 ** -53 * a
     assert np.all(np.abs(K[big] - ref[big]) <= tol[big] * ref[big] + 1e-44)
+
+
+@pytest.mark.parametrize("d", [3, 8, 54, 64])
+def test_sliced_equals_fp64_on_integer_points(gpu_lib, d):
+    ia = gpu_lib
+    rng = np.random.default_rng(40 + d)
+    X = rng.integers(-100, 101, size=(400, d)).astype(np.float64)
+    rows = np.arange(13, 400, 2)                          # 194 rows: two 128-row tiles
+    cols = np.concatenate([rows[:20], rng.choice(400, 77, replace=False)])
+    h = 3.0 * np.sqrt(d)
+    a = ia.iaskit_kernel_block(X, h, rows, cols, 0.25, form="sliced")
+    b = ia.iaskit_kernel_block(X, h, rows, cols, 0.25, form="fp64")
+    assert np.array_equal(a, b)
+    ref = _oracle(X, rows, cols, h, 0.25)
+    arg = sqdist(X[rows], X[cols]) / (2 * h * h)          # exact squared distances, rounded argument
+    assert np.all(np.abs(a - ref) <= 4 * 2.0 ** -52 * (1 + arg) * np.abs(ref) + 1e-300)
+
+
+def test_sliced_refuses_outside_its_range(gpu_lib):
+    ia = gpu_lib
+    X = np.random.default_rng(7).random((50, 65))
+    with pytest.raises(ia.IaskitError) as e:
+        ia.iaskit_kernel_block(X, 1.0, [0, 1], [2, 3], 0.0, form="sliced")
+    assert e.value.name == "IASKIT_ERR_UNSUPPORTED"
+    ia.iaskit_set_option("kernel", 1)
+    try:
+        with pytest.raises(ia.IaskitError) as e:
+            ia.iaskit_kernel_block(X[:, :8], 1.0, [0, 1], [2, 3], 0.0, form="sliced")
+        assert e.value.name == "IASKIT_ERR_UNSUPPORTED"
+    finally:
+        ia.iaskit_set_option("kernel", 0)
 
 
 def test_invalid_arguments(gpu_lib):

@@ -2,12 +2,12 @@
 
 The mixed form keeps FP64 operator blocks for problems whose condition estimate exceeds
 "pair_cond_max" (set to 1 here, so every problem does); with "op_slices" = 1 (default)
-its Evaluate step (Sec. II-B) multiplies them as 7 signed 8-bit digits per value on the
-tensor cores.  Checks, on the library's own skeletons and P read back into the oracle:
+its Skeletonize (P) and Evaluate (K blocks) steps (Sec. II-B) multiply them as 8 signed
+8-bit digits per value on the tensor cores.  Checks, on the library's own skeletons and P read back into the oracle:
 
 * the operator equals the oracle's MatVec and the FP64-pipe products ("op_slices" = 0)
   within FP64-level error, column by column relative to || |K~| |w| || (the splitting's
-  error is at most a few 2^-56 of a row's largest entry times a column's largest value per
+  error is at most a few 2^-64 of a row's largest entry times a column's largest value per
   term), on ragged tiles (leaves of ~94 points, ranks <= 40, N not a multiple of 128) and
   on several exact 128-column segments (leaves of 512, ranks 256);
 * exact invariants of the splitting: a zero column gives exactly zero, scaling a column
