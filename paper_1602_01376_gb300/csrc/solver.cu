@@ -279,21 +279,44 @@ __global__ void axpby_kernel(const double* u, double* r, size_t n) {
     r[i] = u[i] - r[i];
 }
 // One block per (column, problem): the 2-norm of that column of that problem's block.
-__global__ void colnorm_kernel(const double* x, const BlockDesc* blocks, int nrhs, double* out) {
+// Reductions over long vectors in two fixed-order stages: blocks of RED_CHUNK elements
+// write partial sums, then one thread per result adds its chunks in order (the result
+// does not depend on scheduling, and a vector of 2^20 elements spreads over 64 blocks).
+constexpr int RED_CHUNK = 16384;
+__device__ __forceinline__ double block_sum(double s) {
   __shared__ double red[32];
-  const int c = blockIdx.x, q = blockIdx.y;
-  const BlockDesc b = blocks[q];
-  const double* col = x + b.base + (int64_t)c * b.n;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < b.n; i += blockDim.x) s = fma(col[i], col[i], s);
   s = warp_sum(s);
+  __syncthreads();  // red is free (a previous call of this block has read it)
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x < 32) {
     s = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
     s = warp_sum(s);
-    if (threadIdx.x == 0) out[(size_t)q * nrhs + c] = sqrt(s);
   }
+  return s;  // valid in thread 0
+}
+// part[(q nrhs + c) nch + chunk] = sum of squares of column c of problem q over the chunk
+__global__ void colnorm_part_kernel(const double* x, const BlockDesc* blocks, int nrhs, int nch, double* part) {
+  const int ch = blockIdx.x, c = blockIdx.y, q = blockIdx.z;
+  const BlockDesc b = blocks[q];
+  const int64_t i0 = (int64_t)ch * RED_CHUNK;
+  if (i0 >= b.n) {
+    if (threadIdx.x == 0) part[((size_t)q * nrhs + c) * nch + ch] = 0.0;
+    return;
+  }
+  const double* col = x + b.base + (int64_t)c * b.n;
+  const int64_t i1 = min((int64_t)b.n, i0 + RED_CHUNK);
+  double s = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) s = fma(col[i], col[i], s);
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[((size_t)q * nrhs + c) * nch + ch] = s;
+}
+__global__ void colnorm_reduce_kernel(const double* part, int total, int nch, double* out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  double s = 0.0;
+  for (int ch = 0; ch < nch; ++ch) s += part[(size_t)e * nch + ch];
+  out[e] = sqrt(s);
 }
 
 // One GMRES segment: a column of one problem's block, [base, base + len).
@@ -302,23 +325,31 @@ struct GSeg {
   int len;
 };
 
-__global__ void seg_dots_kernel(const double* V, size_t vstride, const double* x, const GSeg* segs,
-                                int S, double* out) {
-  __shared__ double red[32];
-  const int i = blockIdx.x, q = blockIdx.y;
+// part[((i S) + q) nch + chunk] = <V_i, x> over one chunk of segment q
+__global__ void seg_dots_part_kernel(const double* V, size_t vstride, const double* x, const GSeg* segs, int S,
+                                     int nch, double* part) {
+  const int ch = blockIdx.x, i = blockIdx.y, q = blockIdx.z;
   const GSeg sg = segs[q];
+  const int64_t e0 = (int64_t)ch * RED_CHUNK;
+  double* dst = part + ((size_t)i * S + q) * nch + ch;
+  if (e0 >= sg.len) {
+    if (threadIdx.x == 0) *dst = 0.0;
+    return;
+  }
+  const int64_t e1 = min((int64_t)sg.len, e0 + RED_CHUNK);
   const double* v = V + (size_t)i * vstride + sg.base;
   const double* y = x + sg.base;
   double acc = 0.0;
-  for (int e = threadIdx.x; e < sg.len; e += blockDim.x) acc = fma(v[e], y[e], acc);
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    acc = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    acc = warp_sum(acc);
-    if (threadIdx.x == 0) out[(size_t)i * S + q] = acc;
-  }
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) acc = fma(v[e], y[e], acc);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) *dst = acc;
+}
+__global__ void chunk_sum_kernel(const double* part, int total, int nch, double* out) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  double s = 0.0;
+  for (int ch = 0; ch < nch; ++ch) s += part[(size_t)e * nch + ch];
+  out[e] = s;
 }
 __global__ void seg_axpy_kernel(double* x, const double* V, size_t vstride, int k, const double* coef,
                                 double sign, const GSeg* segs, int S) {
@@ -394,7 +425,7 @@ class Solver {
   std::vector<Node> nd;                       // global ids; unused slot at each nbase
   std::vector<std::vector<int>> by_height;    // gids of each height (0 = leaves), roots included
   DevBuf X, Xp, perm, iperm, pid, knn, knn_pos, samp, ranks, skel, piv_ws, A_ws, status,
-      arena_dev, step_dev, tbuf, vbuf, vbuf32, ubuf, rbuf, wt, io, normbuf, blocks_dev, gseg_dev,
+      arena_dev, step_dev, tbuf, vbuf, vbuf32, ubuf, rbuf, wt, io, normbuf, redpart, blocks_dev, gseg_dev,
       kryl, kzb, coefbuf, cseg_dev, rowsum, xnrm;
   // learned sampling: per-step scratch, MLP parameters and training data
   DevBuf l_cand, l_hits, l_feat, l_score, l_linfo, l_samp, l_rk, l_Ptmp, l_sktmp, l_hold, l_err,
@@ -2162,6 +2193,8 @@ class Solver {
         hseg[q * nrhs + c] = GSeg{(int64_t)pr[q].pbase * nrhs + (int64_t)c * pr[q].N, pr[q].N};
     GSeg* segs = gseg_dev.ensure_n<GSeg>(S);
     h2d(segs, hseg.data(), S, st);
+    max_seg_len = 1;
+    for (const GSeg& g : hseg) max_seg_len = std::max(max_seg_len, g.len);
     double* u = rbuf.ensure_n<double>(2 * n);  // copy of the right-hand side, residual
     double* r = u + n;
     double* V = kryl.ensure_n<double>((size_t)(m + 1) * n);
@@ -2304,12 +2337,17 @@ class Solver {
     }
   }
 
-  // out[i*S + q] = <V_i, x> over segment q, i < k
+  // out[i*S + q] = <V_i, x> over segment q, i < k (segments of at most max_seg_len)
+  int max_seg_len = 1;
   void seg_dots(const double* V, size_t vstride, int k, const double* x, const GSeg* segs, int S,
                 double* dev_out, std::vector<double>& out) {
     {
       ProfScope _ps(PK_MISC, st);
-      seg_dots_kernel<<<dim3(k, S), 256, 0, st>>>(V, vstride, x, segs, S, dev_out);
+      const int nch = std::max(1, (int)ceil_div((size_t)max_seg_len, RED_CHUNK));
+      double* part = redpart.ensure_n<double>((size_t)k * S * nch);
+      seg_dots_part_kernel<<<dim3(nch, k, S), 256, 0, st>>>(V, vstride, x, segs, S, nch, part);
+      IA_LAUNCH_CHECK();
+      chunk_sum_kernel<<<ceil_div((size_t)k * S, 256), 256, 0, st>>>(part, k * S, nch, dev_out);
       IA_LAUNCH_CHECK();
     }
     out.resize((size_t)k * S);
@@ -2335,7 +2373,14 @@ class Solver {
     double* dn = normbuf.ensure_n<double>((size_t)nrhs * pr.size());
     {
       ProfScope _ps(PK_MISC, st);
-      colnorm_kernel<<<dim3(nrhs, (unsigned)pr.size()), 256, 0, st>>>(x, blocks, nrhs, dn);
+      int max_n = 1;
+      for (const Prob& P : pr) max_n = std::max(max_n, P.N);
+      const int nch = (int)ceil_div((size_t)max_n, RED_CHUNK);
+      double* part = redpart.ensure_n<double>((size_t)nrhs * pr.size() * nch);
+      colnorm_part_kernel<<<dim3(nch, nrhs, (unsigned)pr.size()), 256, 0, st>>>(x, blocks, nrhs, nch, part);
+      IA_LAUNCH_CHECK();
+      const int tot = nrhs * (int)pr.size();
+      colnorm_reduce_kernel<<<ceil_div((size_t)tot, 256), 256, 0, st>>>(part, tot, nch, dn);
       IA_LAUNCH_CHECK();
     }
     out.resize((size_t)nrhs * pr.size());
@@ -2754,7 +2799,7 @@ class Solver {
     xdig_ready = false;
     DevBuf* all[] = {&X, &Xp, &perm, &iperm, &pid, &knn, &knn_pos, &samp, &ranks, &skel,
                      &piv_ws, &A_ws, &status, &arena_dev, &step_dev, &tbuf, &vbuf, &vbuf32,
-                     &ubuf, &rbuf, &wt, &io, &normbuf, &blocks_dev, &LU, &LUpiv, &Wb, &Zb, &Zpiv,
+                     &ubuf, &rbuf, &wt, &io, &normbuf, &redpart, &blocks_dev, &LU, &LUpiv, &Wb, &Zb, &Zpiv,
                      &Cb, &LU32, &Wb32, &Zb32, &Cb32, &tbuf32, &Kleaf, &Ustore, &Pd, &Pf, &Ppair, &Xpair, &DInv32, &rhs_keep,
                      &gseg_dev, &kryl, &kzb, &coefbuf, &cseg_dev, &rowsum, &l_cand, &l_hits,
                      &l_feat, &l_score, &l_linfo, &l_samp, &l_rk, &l_Ptmp, &l_sktmp, &l_hold, &l_err,
