@@ -48,11 +48,11 @@ void permute_points(const double* X, const int* perm, int N, int d, int* iperm, 
 // ------------------------------------------------------------------- kNN (a2)
 struct KnnScratch {
   DevBuf x32, qnorm, part, mean, rmax, probs, cand_d, cand_i, flagged, counter, tiles, status, seed_tiles, seeds,
-      first, box, tau, tq, cnt, toff, tlist, rec, tnorm, bits;
+      first, box, tau, tq, cnt, toff, tlist, rec, tnorm, bits, boxT, sbox, fgrp, grps;
   void release() {
     for (DevBuf* b : {&x32, &qnorm, &part, &mean, &rmax, &probs, &cand_d, &cand_i, &flagged, &counter,
                       &tiles, &status, &seed_tiles, &seeds, &first, &box, &tau, &tq, &cnt, &toff, &tlist, &rec,
-                      &tnorm, &bits})
+                      &tnorm, &bits, &boxT, &sbox, &fgrp, &grps})
       b->release();
   }
 };

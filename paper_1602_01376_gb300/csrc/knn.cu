@@ -896,8 +896,9 @@ __device__ __forceinline__ float box_lower_bound(const float* a, const float* b,
 
 // Bounding box of every 128-row tile in FP32, rounded outward (minima rounded down,
 // maxima up, so the box contains the FP64 points): box[g][0 .. d) = minima,
-// box[g][d .. 2d) = maxima.
-__global__ void tile_box_kernel(const double* X, int d, const KnnTile* tiles, float* box) {
+// box[g][d .. 2d) = maxima; the same coordinate-major in boxT[k NT + g] (minima) and
+// boxT[(d + k) NT + g] (maxima), NT tiles, for scans of many tiles by one warp.
+__global__ void tile_box_kernel(const double* X, int d, const KnnTile* tiles, int NT, float* box, float* boxT) {
   const KnnTile tl = tiles[blockIdx.x];
   for (int k = threadIdx.x; k < d; k += blockDim.x) {
     double lo = DBL_MAX, hi = -DBL_MAX;
@@ -906,16 +907,46 @@ __global__ void tile_box_kernel(const double* X, int d, const KnnTile* tiles, fl
       lo = fmin(lo, v);
       hi = fmax(hi, v);
     }
-    box[(size_t)blockIdx.x * 2 * d + k] = __double2float_rd(lo);
-    box[(size_t)blockIdx.x * 2 * d + d + k] = __double2float_ru(hi);
+    const float flo = __double2float_rd(lo), fhi = __double2float_ru(hi);
+    box[(size_t)blockIdx.x * 2 * d + k] = flo;
+    box[(size_t)blockIdx.x * 2 * d + d + k] = fhi;
+    boxT[(size_t)k * NT + blockIdx.x] = flo;
+    boxT[(size_t)(d + k) * NT + blockIdx.x] = fhi;
   }
+}
+
+// Box of every group of SEL_GROUP consecutive tiles of a problem (the union of their
+// boxes): grp[j] = (first global tile, count); sbox[j][0 .. 2d) as box.
+constexpr int SEL_GROUP = 32;
+__global__ void super_box_kernel(const float* box, int d, const int2* grp, float* sbox) {
+  const int2 G = grp[blockIdx.x];
+  for (int k = threadIdx.x; k < d; k += blockDim.x) {
+    float lo = FLT_MAX, hi = -FLT_MAX;
+    for (int t = 0; t < G.y; ++t) {
+      lo = fminf(lo, box[(size_t)(G.x + t) * 2 * d + k]);
+      hi = fmaxf(hi, box[(size_t)(G.x + t) * 2 * d + d + k]);
+    }
+    sbox[(size_t)blockIdx.x * 2 * d + k] = lo;
+    sbox[(size_t)blockIdx.x * 2 * d + d + k] = hi;
+  }
+}
+
+// box_lower_bound of box a against tile g of the coordinate-major boxes.
+__device__ __forceinline__ float box_lower_bound_T(const float* a, const float* boxT, size_t NT, int g, int d) {
+  float lb = 0.0f;
+  for (int k = 0; k < d; ++k) {
+    const float blo = boxT[(size_t)k * NT + g], bhi = boxT[(size_t)(d + k) * NT + g];
+    const float gap = fmaxf(0.0f, fmaxf(__fsub_rd(blo, a[d + k]), __fsub_rd(a[k], bhi)));
+    lb = __fadd_rd(lb, __fmul_rd(gap, gap));
+  }
+  return lb;
 }
 
 // Seed tiles of block g: the min(SEED_TILES, tiles of its problem) tiles whose boxes have
 // the smallest lower bound from g's box, by (bound, tile index), g's own tile first;
 // written as local tile indices at soff[g].
-__global__ void knn_seed_pick_kernel(const KnnTile* tiles, const int* first_tile, const float* box, int d,
-                                     const int* soff, int* seeds) {
+__global__ void knn_seed_pick_kernel(const KnnTile* tiles, const int* first_tile, const float* box,
+                                     const float* boxT, int NT, int d, const int* soff, int* seeds) {
   __shared__ float hv[KT_QB];
   __shared__ int ht[KT_QB], hs[KT_QB];
   __shared__ int chosen_s;
@@ -933,7 +964,7 @@ __global__ void knn_seed_pick_kernel(const KnnTile* tiles, const int* first_tile
     lt[u] = INT_MAX;
   }
   for (int t = threadIdx.x; t < nt; t += KT_QB) {
-    float v = ft + t == g ? -1.0f : box_lower_bound(bq, box + (size_t)(ft + t) * 2 * d, d);
+    float v = ft + t == g ? -1.0f : box_lower_bound_T(bq, boxT, NT, ft + t, d);
     int tt = t;
 #pragma unroll
     for (int u = 0; u < SEED_TILES; ++u) {  // sorted insertion by (bound, index)
@@ -1044,8 +1075,10 @@ __global__ void knn_seed_bound_kernel(const double* X, int d, int kappa, const K
 constexpr int SEL_WARPS = KT_QB / 32;
 __global__ void __launch_bounds__(KT_QB) knn_select_kernel(const double* Xp, const KnnTile* tiles, const int* soff,
                                                            const int* seeds, const int* first_tile, const float* box,
-                                                           int d, const double* Tq, const double* tau, size_t mstride,
-                                                           unsigned* bits, int* cnt) {
+                                                           const float* boxT, int NT, const float* sbox,
+                                                           const int* first_grp, int d, const double* Tq,
+                                                           const double* tau, size_t mstride, unsigned* bits,
+                                                           int* cnt) {
   extern __shared__ float sel_q[];  // [d][KT_QB] queries rounded down, then rounded up
   float* qlo = sel_q;
   float* qhi = sel_q + (size_t)d * KT_QB;
@@ -1073,13 +1106,19 @@ __global__ void __launch_bounds__(KT_QB) knn_select_kernel(const double* Xp, con
   // absent rows get a negative threshold, which no bound meets
   tq_s[tid] = tid < tl.qn ? __double2float_ru(tau[tl.q0 + tid] * (1.0 + 1e-9)) : -1.0f;
   __syncthreads();
+  const int fg = first_grp[tl.prob];
   for (int c0 = 0; c0 < nt; c0 += KT_QB) {
     const int t = c0 + tid;
     bool c = false;
-    if (t < nt) {
+    // the warp's SEL_GROUP tiles first as one group: a group box beyond T (every
+    // lane computes the same bound from broadcast loads) rejects them all, as each
+    // tile's own bound, rounded the same way, is at least the group's
+    const bool grp_live = c0 + 32 * w < nt &&
+                          !(box_lower_bound(bq, sbox + (size_t)(fg + ((c0 + 32 * w) / SEL_GROUP)) * 2 * d, d) > T);
+    if (t < nt && grp_live) {
       bool seeded = false;
       for (int r = 0; r < ns; ++r) seeded = seeded || sd[r] == t;
-      c = !seeded && !(box_lower_bound(bq, box + (size_t)(ft + t) * 2 * d, d) > T);
+      c = !seeded && !(box_lower_bound_T(bq, boxT, NT, ft + t, d) > T);
     }
     cand[tid] = c ? 1 : 0;
     __syncthreads();
@@ -1273,14 +1312,30 @@ int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* kn
   IA_LAUNCH_CHECK();
   center_points_kernel<<<nt, KT_QB, 0, st>>>(Xp, d, padded_dim(d), b.tiles, b.mean, b.Xc, b.qn, b.rmax);
   IA_LAUNCH_CHECK();
-  tile_box_kernel<<<nt, 64, 0, st>>>(Xp, d, b.tiles, box);
+  float* boxT = s.boxT.ensure_n<float>((size_t)nt * 2 * d);
+  tile_box_kernel<<<nt, 64, 0, st>>>(Xp, d, b.tiles, nt, box, boxT);
+  IA_LAUNCH_CHECK();
+  // groups of SEL_GROUP consecutive tiles of each problem and their boxes
+  std::vector<int2> grp;
+  std::vector<int> fgrp(np, 0);
+  for (int q = 0; q < np; ++q) {
+    fgrp[q] = (int)grp.size();
+    const int ntq = (problems[q].second + KT_RB - 1) / KT_RB;
+    for (int j = 0; j < ntq; j += SEL_GROUP) grp.push_back(make_int2(first[q] + j, std::min(SEL_GROUP, ntq - j)));
+  }
+  int2* grp_d = s.grps.ensure_n<int2>(grp.size());
+  int* fgrp_d = s.fgrp.ensure_n<int>(np);
+  float* sbox = s.sbox.ensure_n<float>(grp.size() * 2 * d);
+  h2d(grp_d, grp.data(), grp.size(), st);
+  h2d(fgrp_d, fgrp.data(), np, st);
+  super_box_kernel<<<(unsigned)grp.size(), 64, 0, st>>>(box, d, grp_d, sbox);
   IA_LAUNCH_CHECK();
   const int Dp = padded_dim(d);
   uint32_t* rec = s.rec.ensure_n<uint32_t>((size_t)nt * 2 * KT_RB * Dp);
   float* tn = s.tnorm.ensure_n<float>((size_t)nt * KT_RB);
   records_dispatch(Dp, b.Xc, b.qn, b.tiles, nt, rec, tn, st);
   // 1. seed tiles: the nearest boxes
-  knn_seed_pick_kernel<<<nt, KT_QB, 0, st>>>(b.tiles, first_d, box, d, soff_d, seeds_d);
+  knn_seed_pick_kernel<<<nt, KT_QB, 0, st>>>(b.tiles, first_d, box, boxT, nt, d, soff_d, seeds_d);
   IA_LAUNCH_CHECK();
   auto prefilter = [&](TileList list) {
     if (KP == 16) prefilter2_dispatch<16>(Dp, rec, tn, b.tiles, first_d, nt, b.cd, b.ci, b.status, st, list);
@@ -1308,8 +1363,8 @@ int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* kn
   for (const auto& pr : problems) max_nt = std::max(max_nt, (pr.second + KT_RB - 1) / KT_RB);
   const size_t mstride = (size_t)(max_nt + 31) / 32 + 4;  // words per block, padded to the last chunk
   unsigned* bits = s.bits.ensure_n<unsigned>((size_t)nt * mstride);
-  knn_select_kernel<<<nt, KT_QB, sel_smem, st>>>(Xp, b.tiles, soff_d, seeds_d, first_d, box, d, Tq, tau, mstride,
-                                                 bits, cnt);
+  knn_select_kernel<<<nt, KT_QB, sel_smem, st>>>(Xp, b.tiles, soff_d, seeds_d, first_d, box, boxT, nt, sbox,
+                                                 fgrp_d, d, Tq, tau, mstride, bits, cnt);
   IA_LAUNCH_CHECK();
   std::vector<int> hc(nt), ho(nt + 1, 0);
   d2h(hc.data(), cnt, nt, st);
