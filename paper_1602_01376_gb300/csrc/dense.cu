@@ -1689,9 +1689,10 @@ __device__ __forceinline__ void mma_tf32_16x8x8(float (&d)[4], const uint32_t (&
 // step is issued before its values are used: the block's 32 L (or U) values of a row
 // are loaded together, and the next step's inverse block is fetched during this one.
 constexpr int RI_NC = 16;
+constexpr int RI_LD = RI_NC + 4;  // X row stride: consecutive rows in distinct shared-memory banks
 __global__ void __launch_bounds__(RS_THREADS, 2) getrs_inv_kernel(const LuSolveDescT<float>* descs) {
   extern __shared__ __align__(16) unsigned char ri_sh[];
-  float* X = reinterpret_cast<float*>(ri_sh);  // n x RI_NC, row-major
+  float* X = reinterpret_cast<float*>(ri_sh);  // n x RI_NC, row-major, stride RI_LD
   __shared__ __align__(16) float Dv[32][33];
   const LuSolveDescT<float> D = descs[blockIdx.y];
   const int c0 = blockIdx.x * RI_NC;
@@ -1702,7 +1703,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) getrs_inv_kernel(const LuSolveD
   const int tid = threadIdx.x;
   for (int t = tid; t < n * RI_NC; t += RS_THREADS) {
     const int i = t % n, c = t / n;
-    X[(size_t)i * RI_NC + c] = c < nc ? D.B[(size_t)perm[i] + (size_t)(c0 + c) * D.ldb] : 0.0f;
+    X[(size_t)i * RI_LD + c] = c < nc ? D.B[(size_t)perm[i] + (size_t)(c0 + c) * D.ldb] : 0.0f;
   }
   const int di = tid >> 3, dc = (tid & 7) * 2;  // diagonal product: row di, columns dc, dc + 1
   constexpr int DV_PER = 1024 / RS_THREADS;     // inverse entries staged per thread
@@ -1734,14 +1735,14 @@ __global__ void __launch_bounds__(RS_THREADS, 2) getrs_inv_kernel(const LuSolveD
         for (int k = 0; k < 32; ++k) {
           if (k < bs) {
             const float a = Dv[di][k];
-            const float2 xv = *reinterpret_cast<const float2*>(&X[(size_t)(b0 + k) * RI_NC + dc]);
+            const float2 xv = *reinterpret_cast<const float2*>(&X[(size_t)(b0 + k) * RI_LD + dc]);
             o0 = fmaf(a, xv.x, o0);
             o1 = fmaf(a, xv.y, o1);
           }
         }
       }
       __syncthreads();
-      if (di < bs) *reinterpret_cast<float2*>(&X[(size_t)(b0 + di) * RI_NC + dc]) = make_float2(o0, o1);
+      if (di < bs) *reinterpret_cast<float2*>(&X[(size_t)(b0 + di) * RI_LD + dc]) = make_float2(o0, o1);
       __syncthreads();
       // rows to update: below the block (L) or above it (U).  X_r -= L_rb X_b as
       // 16 x 16 x 32 products on the tensor cores (mma.sync m16n8k8 TF32, three
@@ -1757,7 +1758,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) getrs_inv_kernel(const LuSolveD
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
             const int k = kt * 8 + tq + 4 * q;
-            const float x = k < bs ? X[(size_t)(b0 + k) * RI_NC + nt * 8 + gq] : 0.0f;
+            const float x = k < bs ? X[(size_t)(b0 + k) * RI_LD + nt * 8 + gq] : 0.0f;
             bh[kt][nt][q] = tc::to_tf32(x);
             bl[kt][nt][q] = tc::to_tf32(x - __uint_as_float(bh[kt][nt][q]));
           }
@@ -1807,12 +1808,12 @@ __global__ void __launch_bounds__(RS_THREADS, 2) getrs_inv_kernel(const LuSolveD
         for (int nt = 0; nt < 2; ++nt) {
           const int c = nt * 8 + 2 * tq;
           if (va) {
-            float2* xa = reinterpret_cast<float2*>(&X[(size_t)ra * RI_NC + c]);
+            float2* xa = reinterpret_cast<float2*>(&X[(size_t)ra * RI_LD + c]);
             const float2 t = *xa;
             *xa = make_float2(t.x - acc[nt][0], t.y - acc[nt][1]);
           }
           if (vb) {
-            float2* xb = reinterpret_cast<float2*>(&X[(size_t)rb * RI_NC + c]);
+            float2* xb = reinterpret_cast<float2*>(&X[(size_t)rb * RI_LD + c]);
             const float2 t = *xb;
             *xb = make_float2(t.x - acc[nt][2], t.y - acc[nt][3]);
           }
@@ -1827,7 +1828,7 @@ __global__ void __launch_bounds__(RS_THREADS, 2) getrs_inv_kernel(const LuSolveD
   __syncthreads();
   for (int t = tid; t < n * nc; t += RS_THREADS) {
     const int i = t % n, c = t / n;
-    D.B[(size_t)i + (size_t)(c0 + c) * D.ldb] = X[(size_t)i * RI_NC + c];
+    D.B[(size_t)i + (size_t)(c0 + c) * D.ldb] = X[(size_t)i * RI_LD + c];
   }
 }
 
@@ -2193,7 +2194,7 @@ void getrs_batched(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int m
     }
   }
   if (std::is_same<T, float>::value && inv) {
-    const size_t smem = (size_t)max_n * RI_NC * sizeof(float);
+    const size_t smem = (size_t)max_n * RI_LD * sizeof(float);
     if (smem > 200 * 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "LU block too large");
     if (smem > 48 * 1024)
       IA_CUDA(cudaFuncSetAttribute(getrs_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
