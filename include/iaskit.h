@@ -325,8 +325,9 @@ int iaskit_get_P(int level, int index, double* P, int64_t cap);
  *           blocks); returned as hi + lo
  *   form 2  FP32, difference form (the mixed form's sampled blocks)
  *   form 3  FP64 Gram form with the dot products on the BF16 tensor cores from 8-digit
- *           slices of the coordinates (the mixed form's FP64 operator blocks under
- *           "op_slices"); Gaussian kernel and d <= 64 only (else IASKIT_ERR_UNSUPPORTED)
+ *           slices of the coordinates and a table-driven FP64 exp (about 1 ulp) (the mixed
+ *           form's FP64 operator blocks under "op_slices"); Gaussian kernel and d <= 64
+ *           only (else IASKIT_ERR_UNSUPPORTED)
  * With option "kernel" = 1 the block is the polynomial kernel's, (x_i . x_j / h^2 +
  * "poly_c")^"poly_p", from the dot product in the first three precisions.
  * points: HOST N x d row-major; rows[nr], cols[nc]: HOST point indices in [0, N);

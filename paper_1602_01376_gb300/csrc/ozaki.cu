@@ -30,6 +30,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 
 #include "kernels.cuh"
 #include "tc.cuh"
@@ -361,6 +363,31 @@ __device__ __forceinline__ double oz_pow2(int e) {
   return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
 }
 
+// exp(x) for x <= 0 by Tang's table-driven method (ACM TOMS 15(2), 1989): x = (64 m + j)
+// ln2 / 64 + r with |r| <= ln2 / 128 (Cody and Waite's two-part reduction: L_hi has its
+// 17 low bits clear, so that n L_hi is exact for |n| < 2^17), exp(x) = 2^m 2^(j/64)
+// (1 + p(r)), p the Taylor polynomial of e^r - 1 to degree 5 (truncation r^6 / 720 <
+// 2^-54 relative).  The 64 values 2^(j/64), rounded to FP64 from extended precision, and
+// the constants come from the host (OzExp).  About 1 ulp in all; arguments below -708
+// (results near the subnormal range) take the library's exp.
+struct OzExp {
+  double T[64];
+  double inv_l, l_hi, l_lo;  // 64 / ln2, and ln2 / 64 = l_hi + l_lo
+};
+__device__ __forceinline__ double oz_exp_neg(double x, const double* T, double inv_l, double l_hi, double l_lo) {
+  if (x < -708.0) return exp(x);
+  const double nf = rint(x * inv_l);
+  const int n = (int)nf;
+  double r = fma(-nf, l_hi, x);
+  r = fma(-nf, l_lo, r);
+  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  q = fma(r, q, 1.0 / 6.0);
+  q = fma(r, q, 0.5);
+  const double p = fma(r * r, q, r);
+  const double t = T[n & 63];
+  return fma(t, p, t) * __longlong_as_double((long long)((n >> 6) + 1023) << 52);
+}
+
 // One block per 128-row tile of a descriptor (rows row0 + i, consecutive points): the
 // tile's digits stay in shared memory (A: OZ_S operands of 128 x DP); per tile of 32
 // columns the columns' digits are gathered (B: OZ_S * 32 rows, digit j of column c at row
@@ -368,7 +395,8 @@ __device__ __forceinline__ double oz_pow2(int e) {
 // accumulators, so that the MMAs of tile c + 1 run while all threads finish tile c.
 template <int DP>
 __global__ void __launch_bounds__(OZK_THREADS, 1) oz_kblock_kernel(const uint16_t* XD, const int* XE, const double* xn,
-                                                                   const OzKDesc* descs, int nd, int* status) {
+                                                                   const OzKDesc* descs, int nd, int* status,
+                                                                   const OzExp ex) {
   extern __shared__ __align__(1024) unsigned char ok_sh[];
   constexpr int ABYTES = OZ_TM * DP * 2;  // one digit operand of the row tile
   constexpr int BROWS = OZ_S * OZK_TC;
@@ -381,7 +409,9 @@ __global__ void __launch_bounds__(OZK_THREADS, 1) oz_kblock_kernel(const uint16_
   __shared__ double nj_s[2][OZK_TC];
   __shared__ uint64_t mbar[2], fin;
   __shared__ uint32_t tslot;
+  __shared__ double exp_tab[64];
   const int tid = (int)threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid < 64) exp_tab[tid] = ex.T[tid];  // read after the barriers below
   const OzKDesc D = descs[oz_find(descs, nd, (int)blockIdx.x)];
   const int i0 = ((int)blockIdx.x - D.tile0) * OZ_TM;
   const int nct = (D.ncols + OZK_TC - 1) / OZK_TC;
@@ -481,7 +511,7 @@ __global__ void __launch_bounds__(OZK_THREADS, 1) oz_kblock_kernel(const uint16_
         const int e = Ei + ej_s[b][cc] - 14 - 8 * (OZ_HI - 1);
         const double dot = fma((double)lo[c], OZ_LO_SCALE, (double)hi[c]) * oz_pow2(e);
         const double d2 = fmax((ni + nj_s[b][cc]) - 2.0 * dot, 0.0);
-        double kv = exp(d2 * D.scale);
+        double kv = oz_exp_neg(d2 * D.scale, exp_tab, ex.inv_l, ex.l_hi, ex.l_lo);
         if (idi == idj_s[b][cc]) kv += D.diag;
         D.out[(size_t)i + (size_t)j * D.ld] = kv;
       }
@@ -515,6 +545,25 @@ void oz_points(const double* X, int N, int d, uint16_t* XD, int* XE, cudaStream_
   IA_LAUNCH_CHECK();
 }
 
+// The table and constants of oz_exp_neg, in long double (then rounded to FP64) once.
+static const OzExp& oz_exp_table() {
+  static const OzExp tab = [] {
+    OzExp e{};
+    for (int j = 0; j < 64; ++j) e.T[j] = (double)exp2l((long double)j / 64.0L);
+    const long double L = logl(2.0L) / 64.0L;
+    e.inv_l = (double)(1.0L / L);
+    double hi = (double)L;
+    unsigned long long b;
+    std::memcpy(&b, &hi, sizeof b);
+    b &= ~((1ull << 17) - 1);
+    std::memcpy(&hi, &b, sizeof b);
+    e.l_hi = hi;
+    e.l_lo = (double)(L - (long double)hi);
+    return e;
+  }();
+  return tab;
+}
+
 template <int DP>
 static void launch_kblock(const uint16_t* XD, const int* XE, const double* xn, const OzKDesc* descs_dev, int ndesc,
                           int ntiles, int* status, cudaStream_t st) {
@@ -525,7 +574,7 @@ static void launch_kblock(const uint16_t* XD, const int* XE, const double* xn, c
     IA_CUDA(cudaFuncSetAttribute(oz_kblock_kernel<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     attr = true;
   }
-  oz_kblock_kernel<DP><<<ntiles, OZK_THREADS, smem, st>>>(XD, XE, xn, descs_dev, ndesc, status);
+  oz_kblock_kernel<DP><<<ntiles, OZK_THREADS, smem, st>>>(XD, XE, xn, descs_dev, ndesc, status, oz_exp_table());
   IA_LAUNCH_CHECK();
 }
 
