@@ -380,153 +380,186 @@ __global__ void knn_records_kernel(const float* Xc, const float* qnorm, const Kn
 // The prefilter of knn_prefilter_kernel (same lists, same arithmetic) over tile records:
 // the query block is the record of its own tile; the point tile of step t (local index
 // tlist[..] or t, record first_tile[prob] + local) arrives by bulk copy into one of two
-// operand buffers, its norms into one of three slots.  Per step: wait for MMA t; thread
-// 0 starts the copy of tile t + 2 into the buffer MMA t has released, waits for tile
-// t + 1's copy and issues MMA t + 1 into the other accumulator; every thread scans
-// accumulator t; one barrier.  Waits are bounded; a wait that gives up sets DEV_TIMEOUT,
-// and the block stops issuing, waits (bounded) for its copies in flight and returns.
+// operand buffers, its norms into one of PF_NSLOT slots.  Warp 16 (one thread) issues
+// the copies and the MMAs: tile t's products go to accumulator t % NACC (NACC = 4 TMEM
+// accumulators of 128 columns for D >= 32, else 2) as soon as its operands have arrived
+// and every warp has finished scanning the tile that used that accumulator before
+// (mbarrier arrivals, one per warp), and tile t + 2's copy starts once MMA t has read
+// its operand buffer.  Warps 0-15 scan accumulator after accumulator at their own pace:
+// no block barrier per tile, so a warp whose list insertions run long no longer holds up
+// the others, and the products run up to NACC - 1 tiles ahead of the slowest warp.
+// Waits are bounded; a wait that gives up sets DEV_TIMEOUT, the block stops issuing,
+// waits (bounded) for its MMAs and copies in flight, frees its TMEM and returns.
+constexpr int PF_NSLOT = 8;  // norm slots: refilled only after every warp scanned their tile
+template <int D>
+constexpr int pf_nacc() { return D >= 32 ? 4 : 2; }
 template <int D>
 constexpr size_t prefilter2_smem() {
-  return (size_t)3 * rec_bytes<D>() + 3 * KT_RB * 4 + 8 * 8 + 64;
+  return (size_t)3 * rec_bytes<D>() + (size_t)PF_NSLOT * KT_RB * 4 + 64;
 }
+static_assert(PF_NSLOT - 2 >= 4, "a norm slot is refilled after the scans of its tile");
 
 template <int D, int KP>
-__global__ void __launch_bounds__(KT_NTH) knn_prefilter2_kernel(const uint32_t* rec, const float* tnorm,
-                                                                const KnnTile* tiles, const int* first_tile,
-                                                                const int* tlist, const int* toff, int load_init,
-                                                                float* cand_d, int* cand_i, int* status) {
+__global__ void __launch_bounds__(KT_NTH + 32) knn_prefilter2_kernel(const uint32_t* rec, const float* tnorm,
+                                                                     const KnnTile* tiles, const int* first_tile,
+                                                                     const int* tlist, const int* toff,
+                                                                     int load_init, float* cand_d, int* cand_i,
+                                                                     int* status) {
   extern __shared__ __align__(1024) unsigned char kt_sh[];
   constexpr uint32_t RB = rec_bytes<D>();
   constexpr int OPW = KT_QB * D;  // 32-bit words of one operand (hi or lo)
+  constexpr int NACC = pf_nacc<D>();
   uint32_t* Ah = reinterpret_cast<uint32_t*>(kt_sh);
   uint32_t* Al = Ah + OPW;
   uint32_t* B0 = Al + OPW;  // operand buffer b at B0 + 2 b OPW: hi, then lo
-  float* rn3 = reinterpret_cast<float*>(Al + OPW + 4 * OPW);     // [3][KT_RB]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(rn3 + 3 * KT_RB);  // A, B0, B1, M0, M1
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 8);
-  __shared__ int abort_s;
+  float* rns = reinterpret_cast<float*>(Al + OPW + 4 * OPW);  // [PF_NSLOT][KT_RB]
+  __shared__ uint64_t qbar, full[2], opfree[2], nfull[PF_NSLOT], mmadone[NACC], accfree[NACC], fin;
+  __shared__ uint32_t tslot;
+  __shared__ volatile int abort_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int lq = warp & 3, cq = warp >> 2;
+  const int lq = warp & 3, cq = (warp >> 2) & 3;
   const int qi = lq * 32 + lane;
   const KnnTile tl = tiles[blockIdx.x];
   const int my_q = tl.q0 + qi;
-  const bool active = qi < tl.qn;
+  const bool scanner = warp < 16;
+  const bool active = scanner && qi < tl.qn;
   const int rend = tl.rb + tl.rn;
   const int lbeg = tlist ? toff[blockIdx.x] : 0;
   const int ntile = tlist ? toff[blockIdx.x + 1] - lbeg : (tl.rn + KT_RB - 1) / KT_RB;
   if (ntile == 0) return;  // block-uniform: nothing to scan, the lists stay as they are
   const int ft = first_tile[tl.prob];
   auto local = [&](int t) { return tlist ? tlist[lbeg + t] : t; };
-  auto load = [&](int t, int b) {  // thread 0: tile t into operand buffer b, norms into slot t % 3
-    const int r = ft + local(t);
-    tc::mbar_expect_tx(&bar[1 + b], RB + KT_RB * 4);
-    tc::bulk_g2s(B0 + 2 * b * OPW, rec + (size_t)r * (RB / 4), RB, &bar[1 + b]);
-    tc::bulk_g2s(rn3 + (t % 3) * KT_RB, tnorm + (size_t)r * KT_RB, KT_RB * 4, &bar[1 + b]);
-  };
-  if (warp == 0) tc::tmem_alloc(tslot, 2 * KT_RB);
+  if (warp == 0) tc::tmem_alloc(&tslot, NACC * KT_RB);
   if (tid == 0) {
-    for (int i = 0; i < 5; ++i) tc::mbar_init(&bar[i], 1);
+    tc::mbar_init(&qbar, 1);
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&full[i], 1);
+      tc::mbar_init(&opfree[i], 1);
+    }
+    for (int i = 0; i < PF_NSLOT; ++i) tc::mbar_init(&nfull[i], 1);
+    for (int i = 0; i < NACC; ++i) {
+      tc::mbar_init(&mmadone[i], 1);
+      tc::mbar_init(&accfree[i], 16);
+    }
+    tc::mbar_init(&fin, 1);
     abort_s = 0;
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  const uint32_t tmem = *tslot;
-  // thread 0: copies started into / seen complete in each operand buffer
-  int issued0 = 0, issued1 = 0, waited0 = 0, waited1 = 0;
-  constexpr uint32_t idesc = tc::idesc_tf32(KT_QB, KT_RB);
-  constexpr uint32_t SBO = (D / 4) * 128;
-  auto issue = [&](int b) {
-    const uint32_t dt = tmem + (uint32_t)(b * KT_RB);
-#pragma unroll 1
-    for (int ks = 0; ks < D / 8; ++ks) {
-      const uint32_t ko = (uint32_t)ks * 256;
-      const uint64_t ah = tc::smem_desc(tc::smem_addr(Ah) + ko, 128, SBO);
-      const uint64_t al = tc::smem_desc(tc::smem_addr(Al) + ko, 128, SBO);
-      const uint64_t bh = tc::smem_desc(tc::smem_addr(B0 + 2 * b * OPW) + ko, 128, SBO);
-      const uint64_t bl = tc::smem_desc(tc::smem_addr(B0 + 2 * b * OPW + OPW) + ko, 128, SBO);
-      tc::mma_tf32(dt, al, bh, idesc, ks > 0);
-      tc::mma_tf32(dt, ah, bl, idesc, true);
-      tc::mma_tf32(dt, ah, bh, idesc, true);
-    }
-    tc::mma_commit(&bar[3 + b]);
-  };
-  if (tid == 0) {
-    tc::mbar_expect_tx(&bar[0], RB);
-    tc::bulk_g2s(Ah, rec + (size_t)blockIdx.x * (RB / 4), RB, &bar[0]);
-    load(0, 0);
-    issued0 = 1;
-    if (ntile > 1) {
-      load(1, 1);
-      issued1 = 1;
-    }
-    bool ok = tc::mbar_wait(&bar[0], 0, KT_WAIT) && tc::mbar_wait(&bar[1], 0, KT_WAIT);
-    if (ok) {
-      waited0 = 1;
-      tc::fence_after_sync();
-      issue(0);
-    } else {
-      atomicOr(status, DEV_TIMEOUT);
-      abort_s = 1;
-    }
-  }
+  const uint32_t tmem = tslot;
   float bd[KP];
   int bi[KP];
-#pragma unroll
-  for (int u = 0; u < KP; ++u) {
-    bd[u] = FLT_MAX;
-    bi[u] = INT_MAX;
-  }
-  if (load_init && active) {
-    const size_t o = (size_t)my_q * (KT_SUB * KP) + (size_t)cq * KP;
-#pragma unroll
-    for (int u = 0; u < KP; ++u) {
-      bd[u] = cand_d[o + u];
-      bi[u] = cand_i[o + u];
-    }
-  }
-  const float qv = active ? tnorm[(size_t)blockIdx.x * KT_RB + qi] : 0.0f;
-  __syncthreads();  // abort_s of the first issue
-  for (int t = 0; t < ntile; ++t) {
-    const int b = t & 1;
-    const bool stop = abort_s != 0;
-    bool got = false;
-    if (!stop) {
-      got = tc::mbar_wait(&bar[3 + b], (uint32_t)((t >> 1) & 1), KT_WAIT);
-      if (!got) {
-        atomicOr(status, DEV_TIMEOUT);
-        abort_s = 1;
+  if (warp == 16) {
+    if (lane == 0) {
+      // tile t: operands into buffer t & 1 (full), norms into slot t % PF_NSLOT (nfull)
+      auto load = [&](int t) {
+        const int b = t & 1, r = ft + local(t);
+        tc::mbar_expect_tx(&full[b], RB);
+        tc::bulk_g2s(B0 + 2 * b * OPW, rec + (size_t)r * (RB / 4), RB, &full[b]);
+        tc::mbar_expect_tx(&nfull[t % PF_NSLOT], KT_RB * 4);
+        tc::bulk_g2s(rns + (t % PF_NSLOT) * KT_RB, tnorm + (size_t)r * KT_RB, KT_RB * 4, &nfull[t % PF_NSLOT]);
+      };
+      auto wait = [&](uint64_t* bar, uint32_t par) {
+        for (long it = 0; it < KT_WAIT; it += 64) {
+          if (tc::mbar_wait(bar, par, 64)) return true;
+          if (abort_s) return false;
+        }
+        return false;
+      };
+      constexpr uint32_t idesc = tc::idesc_tf32(KT_QB, KT_RB);
+      constexpr uint32_t SBO = (D / 4) * 128;
+      tc::mbar_expect_tx(&qbar, RB);
+      tc::bulk_g2s(Ah, rec + (size_t)blockIdx.x * (RB / 4), RB, &qbar);
+      int loaded = 0, issued = 0;
+      load(0);
+      loaded = 1;
+      if (ntile > 1) {
+        load(1);
+        loaded = 2;
       }
-    }
-    tc::fence_after_sync();
-    if (tid == 0 && got) {
-      if (t + 2 < ntile) {  // MMA t has released operand buffer b
-        load(t + 2, b);
-        if (b) ++issued1;
-        else ++issued0;
+      bool ok = wait(&qbar, 0);
+      for (int t = 0; t < ntile && ok; ++t) {
+        const int b = t & 1, a = t % NACC;
+        ok = wait(&full[b], (uint32_t)((t >> 1) & 1));
+        // the accumulator's previous tile (t - NACC) has been scanned by every warp; that
+        // also frees the norm slot of tile t + 2 (PF_NSLOT - 2 >= NACC)
+        if (ok && t >= NACC) ok = wait(&accfree[a], (uint32_t)((t / NACC - 1) & 1));
+        if (!ok) break;
+        tc::fence_after_sync();
+        const uint32_t dt = tmem + (uint32_t)(a * KT_RB);
+#pragma unroll 1
+        for (int ks = 0; ks < D / 8; ++ks) {
+          const uint32_t ko = (uint32_t)ks * 256;
+          const uint64_t ah = tc::smem_desc(tc::smem_addr(Ah) + ko, 128, SBO);
+          const uint64_t al = tc::smem_desc(tc::smem_addr(Al) + ko, 128, SBO);
+          const uint64_t bh = tc::smem_desc(tc::smem_addr(B0 + 2 * b * OPW) + ko, 128, SBO);
+          const uint64_t bl = tc::smem_desc(tc::smem_addr(B0 + 2 * b * OPW + OPW) + ko, 128, SBO);
+          tc::mma_tf32(dt, al, bh, idesc, ks > 0);
+          tc::mma_tf32(dt, ah, bl, idesc, true);
+          tc::mma_tf32(dt, ah, bh, idesc, true);
+        }
+        tc::mma_commit(&mmadone[a]);
+        tc::mma_commit(&opfree[b]);
+        issued = t + 1;
+        if (t + 2 < ntile) {  // MMA t releases operand buffer b for tile t + 2
+          ok = wait(&opfree[b], (uint32_t)((t >> 1) & 1));
+          if (!ok) break;
+          load(t + 2);
+          loaded = t + 3;
+        }
       }
-      if (t + 1 < ntile) {
-        const int b1 = b ^ 1;
-        if (tc::mbar_wait(&bar[1 + b1], (uint32_t)(((t + 1) >> 1) & 1), KT_WAIT)) {
-          if (b1) ++waited1;
-          else ++waited0;
-          tc::fence_after_sync();
-          issue(b1);
-        } else {
+      if (!ok) {
+        if (!abort_s) {
           atomicOr(status, DEV_TIMEOUT);
           abort_s = 1;
         }
+        tc::mma_commit(&fin);  // every MMA issued so far, then the copies that may be in flight:
+        tc::mbar_wait(&fin, 0, KT_WAIT);  // operands not yet consumed, norms of the last slots
+        for (int u = issued; u < loaded; ++u)
+          if (!tc::mbar_wait(&full[u & 1], (uint32_t)((u >> 1) & 1), KT_WAIT)) break;
+        for (int u = max(0, loaded - PF_NSLOT); u < loaded; ++u)
+          if (!tc::mbar_wait(&nfull[u % PF_NSLOT], (uint32_t)((u / PF_NSLOT) & 1), KT_WAIT)) break;
       }
     }
-    const int r0 = tl.rb + local(t) * KT_RB, nt = min(KT_RB, rend - r0);
-    const bool use = __all_sync(0xffffffffu, got);  // tcgen05.ld needs the whole warp
-    if (use) {
-      const float* rn_t = rn3 + (t % 3) * KT_RB;
+  } else {
+#pragma unroll
+    for (int u = 0; u < KP; ++u) {
+      bd[u] = FLT_MAX;
+      bi[u] = INT_MAX;
+    }
+    if (load_init && active) {
+      const size_t o = (size_t)my_q * (KT_SUB * KP) + (size_t)cq * KP;
+#pragma unroll
+      for (int u = 0; u < KP; ++u) {
+        bd[u] = cand_d[o + u];
+        bi[u] = cand_i[o + u];
+      }
+    }
+    const float qv = active ? tnorm[(size_t)blockIdx.x * KT_RB + qi] : 0.0f;
+    for (int t = 0; t < ntile; ++t) {
+      const int a = t % NACC, slot = t % PF_NSLOT;
+      bool got = false;
+      for (long it = 0; it < KT_WAIT && !got; it += 64) {
+        got = tc::mbar_wait(&mmadone[a], (uint32_t)((t / NACC) & 1), 64) &&
+              tc::mbar_wait(&nfull[slot], (uint32_t)((t / PF_NSLOT) & 1), 64);
+        if (abort_s) break;
+      }
+      if (!__all_sync(0xffffffffu, got)) {  // tcgen05.ld needs the whole warp
+        if (lane == 0 && !abort_s) {
+          atomicOr(status, DEV_TIMEOUT);
+          abort_s = 1;
+        }
+        break;
+      }
+      tc::fence_after_sync();
+      const int r0 = tl.rb + local(t) * KT_RB, nt = min(KT_RB, rend - r0);
+      const float* rn_t = rns + slot * KT_RB;
 #pragma unroll 1
       for (int h = 0; h < 2; ++h) {
         const int c0 = cq * 32 + h * 16;
         float v[16];
-        tc::tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(b * KT_RB + c0), v);
+        tc::tmem_ld16(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(a * KT_RB + c0), v);
         unsigned ok = !active || c0 >= nt ? 0u : (nt - c0 >= 16 ? 0xFFFFu : (1u << (nt - c0)) - 1u);
         const int self = my_q - (r0 + c0);
         if (self >= 0 && self < 16) ok &= ~(1u << self);
@@ -565,21 +598,15 @@ __global__ void __launch_bounds__(KT_NTH) knn_prefilter2_kernel(const uint32_t* 
           }
         }
       }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&accfree[a]);  // this warp is done with accumulator a and slot
     }
-    tc::fence_before_sync();
-    __syncthreads();  // accumulator b and norm slot t % 3 are reused by later steps
-    if (abort_s) break;
-  }
-  if (tid == 0) {  // copies still in flight after an abort
-    for (; waited0 < issued0; ++waited0)
-      if (!tc::mbar_wait(&bar[1], (uint32_t)(waited0 & 1), KT_WAIT)) break;
-    for (; waited1 < issued1; ++waited1)
-      if (!tc::mbar_wait(&bar[2], (uint32_t)(waited1 & 1), KT_WAIT)) break;
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 0) tc::tmem_free(tmem, 2 * KT_RB);
+  if (warp == 0) tc::tmem_free(tmem, NACC * KT_RB);
   if (active) {
     const size_t o = (size_t)my_q * (KT_SUB * KP) + (size_t)cq * KP;
 #pragma unroll
@@ -778,9 +805,10 @@ void prefilter_dispatch(const float* Xc, const float* qn, int d, const KnnTile* 
 template <int D, int KP>
 void launch_prefilter2(const uint32_t* rec, const float* tn, const KnnTile* tiles, const int* first, int ntiles,
                        float* cd, int* ci, int* status, cudaStream_t st, TileList tl) {
-  const size_t smem = std::max<size_t>(prefilter2_smem<D>(), 80 * 1024);
+  // with 4 accumulators (512 TMEM columns) a block must hold its SM alone: at least 116 KB
+  const size_t smem = std::max<size_t>(prefilter2_smem<D>(), pf_nacc<D>() > 2 ? 116 * 1024 : 80 * 1024);
   IA_CUDA(cudaFuncSetAttribute(knn_prefilter2_kernel<D, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  knn_prefilter2_kernel<D, KP><<<ntiles, KT_NTH, smem, st>>>(rec, tn, tiles, first, tl.tlist, tl.toff, tl.load_init,
+  knn_prefilter2_kernel<D, KP><<<ntiles, KT_NTH + 32, smem, st>>>(rec, tn, tiles, first, tl.tlist, tl.toff, tl.load_init,
                                                               cd, ci, status);
   IA_LAUNCH_CHECK();
 }
