@@ -1032,27 +1032,28 @@ __global__ void knn_seed_pick_kernel(const KnnTile* tiles, const int* first_tile
   }
 }
 
-// tau[i] = the kappa-th smallest exact FP64 distance among the candidates of the seed
-// pass (an upper bound on the true kappa-th distance; DBL_MAX when fewer than kappa),
-// and Tq[g] = the largest tau of block g.
+// tau[i] = an upper bound on the kappa-th smallest exact FP64 distance among the
+// candidates of the seed pass (so on the true kappa-th distance; DBL_MAX when fewer than
+// kappa), and Tq[g] = the largest tau of block g.  It needs no FP64 distance: by the
+// prefilter's rounding bound every candidate's exact distance is at most
+// D + E, E = (8 K + 32) 2^-23 (|a|^2 + |b|^2) (K = Kdim, the norms those of the centred
+// FP32 rows), so the kappa-th smallest D + E bounds the kappa-th smallest exact distance
+// (a factor 1 + 1e-12 covers the FP64 distances' own rounding).  A larger tau only scans
+// a few more tiles; the re-rank certifies every list against it as before.
 template <int KP, int KAP>
-__global__ void knn_seed_bound_kernel(const double* X, int d, int kappa, const KnnTile* tiles,
-                                      const float* cand_d, const int* cand_i, const int* ids, double* tau,
-                                      double* Tq) {
+__global__ void knn_seed_bound_kernel(const float* qnorm, int Kdim, int kappa, const KnnTile* tiles,
+                                      const float* cand_d, const int* cand_i, double* tau, double* Tq) {
   __shared__ double red[KT_QB];
   const KnnTile tl = tiles[blockIdx.x];
   const int t = threadIdx.x;
+  const double ef = (8.0 * Kdim + 32.0) * 0x1p-23;
   double bound = 0.0;
   if (t < tl.qn) {
     const int i = tl.q0 + t;
+    const double a2 = (double)qnorm[i];
     double dd[KAP];
-    int ii[KAP];
 #pragma unroll
-    for (int u = 0; u < KAP; ++u) {
-      dd[u] = DBL_MAX;
-      ii[u] = INT_MAX;
-    }
-    const double* xi = X + (size_t)i * d;
+    for (int u = 0; u < KAP; ++u) dd[u] = DBL_MAX;
     const size_t o = (size_t)i * (KT_SUB * KP);
     int found = 0;
     for (int q = 0; q < KT_SUB; ++q)
@@ -1060,23 +1061,19 @@ __global__ void knn_seed_bound_kernel(const double* X, int d, int kappa, const K
         const int j = cand_i[o + (size_t)q * KP + u];
         if (j == INT_MAX) break;
         ++found;
-        double v = exact_sqdist(xi, X + (size_t)j * d, d);
-        int jj = ids[j];
-        if (!pair_less(v, jj, dd[kappa - 1], ii[kappa - 1])) continue;
+        double v = (double)cand_d[o + (size_t)q * KP + u] + ef * (a2 + (double)qnorm[j]);
+        if (!(v < dd[kappa - 1])) continue;
 #pragma unroll
         for (int w = 0; w < KAP; ++w) {
           if (w >= kappa) break;
-          if (pair_less(v, jj, dd[w], ii[w])) {
+          if (v < dd[w]) {
             const double tv = dd[w];
-            const int tj = ii[w];
             dd[w] = v;
-            ii[w] = jj;
             v = tv;
-            jj = tj;
           }
         }
       }
-    bound = found >= kappa ? dd[kappa - 1] : DBL_MAX;
+    bound = found >= kappa ? dd[kappa - 1] * (1.0 + 1e-12) : DBL_MAX;
     tau[i] = bound;
   }
   red[t] = bound;
@@ -1134,6 +1131,26 @@ __global__ void __launch_bounds__(KT_QB) knn_select_kernel(const double* Xp, con
   // absent rows get a negative threshold, which no bound meets
   tq_s[tid] = tid < tl.qn ? __double2float_ru(tau[tl.q0 + tid] * (1.0 + 1e-9)) : -1.0f;
   __syncthreads();
+  // the four sub-blocks of 32 queries (lane + 32 j: queries consecutive in tree order):
+  // their boxes and largest thresholds
+  __shared__ float sub_lo[4][64], sub_hi[4][64], Tj_s[4];
+  {
+    const int j = tid >> 5;
+    for (int k = lane; k < d; k += 32) {
+      float lo = FLT_MAX, hi = -FLT_MAX;
+      for (int q = 32 * j; q < min(32 * j + 32, tl.qn); ++q) {
+        lo = fminf(lo, qlo[(size_t)k * KT_QB + q]);
+        hi = fmaxf(hi, qhi[(size_t)k * KT_QB + q]);
+      }
+      sub_lo[j][k] = lo;
+      sub_hi[j][k] = hi;
+    }
+    float tm = tq_s[tid];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) tm = fmaxf(tm, __shfl_xor_sync(0xffffffffu, tm, o));
+    if (lane == 0) Tj_s[j] = tm;
+  }
+  __syncthreads();
   const int fg = first_grp[tl.prob];
   for (int c0 = 0; c0 < nt; c0 += KT_QB) {
     const int t = c0 + tid;
@@ -1156,20 +1173,41 @@ __global__ void __launch_bounds__(KT_QB) knn_select_kernel(const double* Xp, con
         continue;
       }
       const float* bt = box + (size_t)(ft + c0 + i) * 2 * d;
-      float lb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      for (int k = 0; k < d; ++k) {
+      // a sub-block whose box lies beyond its largest threshold has no query that can
+      // reach the tile (its lower bound, rounded down in any order, bounds every one of
+      // its queries' true distances from below): the lanes share its dimensions
+      float ps[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      for (int k = lane; k < d; k += 32) {
         const float lo = bt[k], hi = bt[d + k];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const int q = lane + 32 * j;
-          const float gap =
-              fmaxf(0.0f, fmaxf(__fsub_rd(lo, qhi[(size_t)k * KT_QB + q]), __fsub_rd(qlo[(size_t)k * KT_QB + q], hi)));
-          lb[j] = __fadd_rd(lb[j], __fmul_rd(gap, gap));
+          const float gap = fmaxf(0.0f, fmaxf(__fsub_rd(lo, sub_hi[j][k]), __fsub_rd(sub_lo[j][k], hi)));
+          ps[j] = __fadd_rd(ps[j], __fmul_rd(gap, gap));
         }
       }
+      bool live[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) ps[j] = __fadd_rd(ps[j], __shfl_xor_sync(0xffffffffu, ps[j], o));
+        live[j] = ps[j] <= Tj_s[j];  // the same in every lane (symmetric butterfly)
+      }
+      float lb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      if (live[0] || live[1] || live[2] || live[3])
+        for (int k = 0; k < d; ++k) {
+          const float lo = bt[k], hi = bt[d + k];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (!live[j]) continue;  // warp-uniform
+            const int q = lane + 32 * j;
+            const float gap =
+                fmaxf(0.0f, fmaxf(__fsub_rd(lo, qhi[(size_t)k * KT_QB + q]), __fsub_rd(qlo[(size_t)k * KT_QB + q], hi)));
+            lb[j] = __fadd_rd(lb[j], __fmul_rd(gap, gap));
+          }
+        }
       bool hit = false;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) hit = hit || lb[j] <= tq_s[lane + 32 * j];
+      for (int j = 0; j < 4; ++j) hit = hit || (live[j] && lb[j] <= tq_s[lane + 32 * j]);
       const bool any = __any_sync(0xffffffffu, hit);
       if (lane == 0) keep[i] = any ? 1 : 0;
     }
@@ -1374,7 +1412,7 @@ int knn_tree(const double* Xp, const int* perm, int N, int d, int kappa, int* kn
   // 2. bounds and the tiles left to scan
   auto seed_bound = [&](auto kp_tag, auto kap_tag) {
     constexpr int kp = decltype(kp_tag)::value, kap = decltype(kap_tag)::value;
-    knn_seed_bound_kernel<kp, kap><<<nt, KT_QB, 0, st>>>(Xp, d, kappa, b.tiles, b.cd, b.ci, perm, tau, Tq);
+    knn_seed_bound_kernel<kp, kap><<<nt, KT_QB, 0, st>>>(b.qn, padded_dim(d), kappa, b.tiles, b.cd, b.ci, tau, Tq);
   };
   using I16 = std::integral_constant<int, 16>;
   using I32 = std::integral_constant<int, 32>;
