@@ -660,8 +660,15 @@ __global__ void knn_rerank_kernel(const double* X, int d, int kappa, int Kdim, c
   }
   const double* xi = X + (size_t)i * d;
   const size_t o = (size_t)i * (KT_SUB * KP);
+  const double c = (8.0 * Kdim + 32.0) * 1.1920928955078125e-07;  // (8K + 32) 2^-23
+  const double a2 = (double)qnorm[i];
+  // pass 1: every candidate's exact distance lies within D +- E_j, E_j = c (|a|^2 + |b_j|^2);
+  // U = the kappa-th smallest D + E_j bounds the kappa-th smallest exact distance
   float cut = FLT_MAX;
   int found = 0;
+  double ub[KAP];
+#pragma unroll
+  for (int u = 0; u < KAP; ++u) ub[u] = DBL_MAX;
   for (int q = 0; q < KT_SUB; ++q) {
     cut = fminf(cut, cand_d[o + (size_t)q * KP + KP - 1]);
     for (int u = 0; u < KP; ++u) {
@@ -673,6 +680,28 @@ __global__ void knn_rerank_kernel(const double* X, int d, int kappa, int Kdim, c
         return;
       }
       ++found;
+      double v = (double)cand_d[o + (size_t)q * KP + u] + c * (a2 + (double)qnorm[j]);
+      if (!(v < ub[kappa - 1])) continue;
+#pragma unroll
+      for (int w = 0; w < KAP; ++w) {
+        if (w >= kappa) break;
+        if (v < ub[w]) {
+          const double tv = ub[w];
+          ub[w] = v;
+          v = tv;
+        }
+      }
+    }
+  }
+  const double U = found >= kappa ? ub[kappa - 1] * (1.0 + 1e-12) : DBL_MAX;
+  // pass 2: exact distances of the candidates that can be among the kappa nearest; one
+  // whose D - E_j exceeds U is strictly farther than the kappa-th (no tie with it)
+  for (int q = 0; q < KT_SUB; ++q) {
+    for (int u = 0; u < KP; ++u) {
+      const int j = cand_i[o + (size_t)q * KP + u];
+      if (j == INT_MAX) break;
+      const double lbj = ((double)cand_d[o + (size_t)q * KP + u] - c * (a2 + (double)qnorm[j])) * (1.0 - 1e-12);
+      if (lbj > U) continue;
       double v = exact_sqdist(xi, X + (size_t)j * d, d);
       int jj = ids ? ids[j] : j;
       if (!pair_less(v, jj, dd[kappa - 1], ii[kappa - 1])) continue;
@@ -690,7 +719,6 @@ __global__ void knn_rerank_kernel(const double* X, int d, int kappa, int Kdim, c
       }
     }
   }
-  const double c = (8.0 * Kdim + 32.0) * 1.1920928955078125e-07;  // (8K + 32) 2^-23
   const double E = c * ((double)qnorm[i] + (double)__uint_as_float(rmax_bits[tl.prob]));
   const bool all_in = found >= N - 1;  // every other point was a candidate
   const double lo = ((double)cut - E) * (1.0 - 1e-12);
