@@ -298,7 +298,7 @@ def config_of(w):
 # ------------------------------------------------------------------- GPU leg
 FP32_LANES_PER_SM = 128              # GB300: FP32 FMA lanes per SM
 PEAK_CLASS = {                       # kernel classes whose arithmetic is FP32
-    "kernel_blocks_f32", "cpqr_id_f32", "getrf_f32", "getrs_f32"}
+    "kernel_blocks_f32", "cpqr_id_f32", "getrf_f32", "getrs_f32", "getri_f32"}
 PAIR_INSTR_PER_MAC = 12              # FP32 instructions of one FP32-pair multiply-add
 FP64_EQUIV_NOTE = {                  # classes whose flops count FP64 work done partly elsewhere
     "kernel_blocks_sliced": "FP64-equivalent flops (2d + 3 per entry, the FP64 Gram form's); the dot "

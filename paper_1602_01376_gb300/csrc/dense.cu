@@ -1688,8 +1688,14 @@ __device__ __forceinline__ void mma_tf32_16x8x8(float (&d)[4], const uint32_t (&
 // upwards with U.  No step is a sequential substitution, and every global load of a
 // step is issued before its values are used: the block's 32 L (or U) values of a row
 // are loaded together, and the next step's inverse block is fetched during this one.
+// INV (GETRI): the right-hand sides are the identity's columns and the result is the
+// matrix's inverse.  With P A = L U, A^-1 = U^-1 L^-1 P: chunk c0 solves for the
+// identity's columns c0 .. c0 + 15, whose rows above c0 stay zero through the forward
+// pass (its first c0 / 32 steps are skipped), and column c of U^-1 L^-1 is column
+// perm[c] of A^-1, where the chunk writes it.
 constexpr int RI_NC = 16;
 constexpr int RI_LD = RI_NC + 4;  // X row stride: consecutive rows in distinct shared-memory banks
+template <bool INV>
 __global__ void __launch_bounds__(RS_THREADS, 2) getrs_inv_kernel(const LuSolveDescT<float>* descs) {
   extern __shared__ __align__(16) unsigned char ri_sh[];
   float* X = reinterpret_cast<float*>(ri_sh);  // n x RI_NC, row-major, stride RI_LD
@@ -1703,8 +1709,10 @@ __global__ void __launch_bounds__(RS_THREADS, 2) getrs_inv_kernel(const LuSolveD
   const int tid = threadIdx.x;
   for (int t = tid; t < n * RI_NC; t += RS_THREADS) {
     const int i = t % n, c = t / n;
-    X[(size_t)i * RI_LD + c] = c < nc ? D.B[(size_t)perm[i] + (size_t)(c0 + c) * D.ldb] : 0.0f;
+    if constexpr (INV) X[(size_t)i * RI_LD + c] = (c < nc && i == c0 + c) ? 1.0f : 0.0f;
+    else X[(size_t)i * RI_LD + c] = c < nc ? D.B[(size_t)perm[i] + (size_t)(c0 + c) * D.ldb] : 0.0f;
   }
+  const int s0 = INV ? (c0 >> 5) : 0;          // first forward step with a nonzero row
   const int di = tid >> 3, dc = (tid & 7) * 2;  // diagonal product: row di, columns dc, dc + 1
   constexpr int DV_PER = 1024 / RS_THREADS;     // inverse entries staged per thread
   float dnext[DV_PER];
@@ -1714,9 +1722,9 @@ __global__ void __launch_bounds__(RS_THREADS, 2) getrs_inv_kernel(const LuSolveD
 #pragma unroll
     for (int u = 0; u < DV_PER; ++u) dnext[u] = inv[tid + u * RS_THREADS];
   };
-  fetch_inv(0, 0);
+  fetch_inv(0, s0);
   for (int pass = 0; pass < 2; ++pass) {  // 0: L downwards, 1: U upwards
-    for (int step = 0; step < nb; ++step) {
+    for (int step = pass == 0 ? s0 : 0; step < nb; ++step) {
       const int blk = pass == 0 ? step : nb - 1 - step;
       const int b0 = 32 * blk, bs = min(32, n - b0);
       __syncthreads();  // X rows of the previous step are final; Dv is free
@@ -1828,7 +1836,8 @@ __global__ void __launch_bounds__(RS_THREADS, 2) getrs_inv_kernel(const LuSolveD
   __syncthreads();
   for (int t = tid; t < n * nc; t += RS_THREADS) {
     const int i = t % n, c = t / n;
-    D.B[(size_t)i + (size_t)(c0 + c) * D.ldb] = X[(size_t)i * RI_LD + c];
+    const int oc = INV ? perm[c0 + c] : c0 + c;
+    D.B[(size_t)i + (size_t)oc * D.ldb] = X[(size_t)i * RI_LD + c];
   }
 }
 
@@ -2197,14 +2206,27 @@ void getrs_batched(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int m
     const size_t smem = (size_t)max_n * RI_LD * sizeof(float);
     if (smem > 200 * 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "LU block too large");
     if (smem > 48 * 1024)
-      IA_CUDA(cudaFuncSetAttribute(getrs_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      IA_CUDA(cudaFuncSetAttribute(getrs_inv_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (ndesc > 65535) throw Error(IASKIT_ERR_UNSUPPORTED, "more than 65535 LU solves in one launch");
     dim3 grid(ceil_div(max_cols, RI_NC), ndesc);
-    getrs_inv_kernel<<<grid, RS_THREADS, smem, st>>>(reinterpret_cast<const LuSolveDescT<float>*>(descs_dev));
+    getrs_inv_kernel<false><<<grid, RS_THREADS, smem, st>>>(reinterpret_cast<const LuSolveDescT<float>*>(descs_dev));
     IA_LAUNCH_CHECK();
     return;
   }
   solve_dispatch<T, false>(descs_dev, ndesc, max_n, max_cols, st);
+}
+
+void getri_batched(const LuSolveDescT<float>* descs_dev, int ndesc, int max_n, cudaStream_t st) {
+  if (ndesc <= 0 || max_n <= 0) return;
+  ProfScope _ps(PK_GETRI32, st);
+  const size_t smem = (size_t)max_n * RI_LD * sizeof(float);
+  if (smem > 200 * 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "LU block too large");
+  if (smem > 48 * 1024)
+    IA_CUDA(cudaFuncSetAttribute(getrs_inv_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (ndesc > 65535) throw Error(IASKIT_ERR_UNSUPPORTED, "more than 65535 LU inverses in one launch");
+  dim3 grid(ceil_div(max_n, RI_NC), ndesc);
+  getrs_inv_kernel<true><<<grid, RS_THREADS, smem, st>>>(descs_dev);
+  IA_LAUNCH_CHECK();
 }
 
 template <typename T>

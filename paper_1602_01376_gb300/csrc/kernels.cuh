@@ -225,6 +225,10 @@ struct LuSolveDescT {
 template <typename T>
 void getrs_batched(const LuSolveDescT<T>* descs_dev, int ndesc, int max_n, int max_cols,
                    cudaStream_t st, bool inv = false, bool pair = false);
+// GETRI of FP32 LUs factored with their dinv areas: B (n x n, ldb) <- A^-1 for each
+// descriptor (ncols is n; B must not overlap the LU).  Singular U gives non-finite
+// entries, as the solve would.
+void getri_batched(const LuSolveDescT<float>* descs_dev, int ndesc, int max_n, cudaStream_t st);
 // B <- U^{-1} B with U the upper triangle of the n x n block at LU (ipiv unused): the
 // ID's T = R11^{-1} R12 after cpqr_id.  A zero diagonal entry gives a zero row.
 template <typename T>

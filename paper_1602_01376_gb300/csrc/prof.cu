@@ -10,7 +10,8 @@ const char* prof_name(int k) {
                                         "getrs_f32", "gemm_f32", "learned_sampling", "mlp_bf16",
                                         "id_judge", "gemm_pair",
                                         "kernel_blocks_pair", "near_field", "predict",
-                                        "operator_slices", "slice_split", "kernel_blocks_sliced"};
+                                        "operator_slices", "slice_split", "kernel_blocks_sliced",
+                                        "getri_f32"};
   return (k >= 0 && k < PK_COUNT) ? names[k] : "?";
 }
 

@@ -38,6 +38,7 @@ enum ProfKind {
   PK_OZ,           // FP64 operator products by exact BF16 slices (tensor cores)
   PK_OZ_SPLIT,     // splitting FP64 blocks and right-hand sides into BF16 digits
   PK_KBLOCK_OZ,    // FP64 kernel blocks with the dot products on the tensor cores
+  PK_GETRI32,      // explicit inverses of the FP32 LUs (leaf blocks, reduced systems)
   PK_COUNT
 };
 

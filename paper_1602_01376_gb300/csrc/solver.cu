@@ -89,6 +89,11 @@ struct Options {
   double learned_temp = 0.0;  // Gumbel temperature of the learned selection (0: top scores)
   int gemm_tc = 1;            // FP32 products with more than 16 columns on the tensor cores (3xTF32)
   int cpqr_cluster = 1;       // FP32 IDs of up to 512 x 512 on a cluster of blocks per node
+  // FP32 LUs inverted once and applied as products: 1 the leaf blocks, 2 the leaf blocks
+  // and the reduced systems; 0 none (LU solves).  Products by the inverse of a reduced
+  // system raised the refinement's iterations on the manifold in d 64 (9 -> 16; leaf
+  // blocks alone: 10)
+  int lu_inverse = 1;
   // mixed form: problems whose condition estimate exceeds this keep their operator
   // blocks in FP64 from the start; any other problem whose refinement stops at the
   // FP32-pair operator's rounding floor is upgraded to FP64 and refined again.  Measured
@@ -194,6 +199,12 @@ template <typename T>
 double getrs_flops(const std::vector<LuSolveDescT<T>>& v) {
   double f = 0;
   for (const auto& d : v) f += 2.0 * d.n * (double)d.n * d.ncols;
+  return f;
+}
+// GETRI from the LU: 4/3 n^3 (LAPACK's count)
+double getri_flops(const std::vector<LuSolveDescT<float>>& v) {
+  double f = 0;
+  for (const auto& d : v) f += 4.0 / 3.0 * d.n * (double)d.n * d.n;
   return f;
 }
 template <typename T>
@@ -442,6 +453,9 @@ class Solver {
   DevBuf Ppair;   // mixed form: P as FP32 pairs for the operator (Kleaf, Ustore hold pairs too)
   DevBuf Xpair;   // mixed form: permuted coordinates as FP32 pairs
   DevBuf DInv32;  // FP32 LUs: inverses of their 32 x 32 diagonal blocks and pivot permutations
+  DevBuf LUi32, Zi32;  // explicit inverses of the FP32 leaf LUs and reduced systems (lu_inverse)
+  DevBuf fsS;          // forest solves with inverses: the right-hand sides' copy
+  bool inv_leaf = false, inv_z = false;  // this factorization's FP32 leaf LUs / Zs have inverses
   DevBuf rhs_keep;  // mixed form: the right-hand side, for a refinement after an operator upgrade
   DevBuf pred_part, pred_io;  // kernel sums at test points: chunk partials; host-call staging
   DevBuf kperm, kiperm, Xk;   // kNN search order (tree of 128-point leaves) and its points
@@ -598,7 +612,7 @@ class Solver {
   // Applies (lambda I + K~_cc)^{-1} to the block of every root c, in place, with the
   // factorization stored in precision T.  Writes P_c v_c to roots[].t_out when given.
   template <typename T>
-  void forest_solve(const std::vector<RootBlock<T>>& roots) {
+  void forest_solve(const std::vector<RootBlock<T>>& roots, bool with_inverses) {
     const bool need_t = !roots.empty() && roots[0].t_out != nullptr;
     std::vector<int> root_of(nd.size(), -1);
     std::vector<T*> Vp(nd.size(), nullptr);
@@ -645,15 +659,43 @@ class Solver {
       }
     };
 
+    // FP32 LUs with inverses: the leaf solves and the reduced systems are products
+    const bool fp32 = std::is_same<T, float>::value;
+    const bool inv = fp32 && inv_leaf && with_inverses, invz = fp32 && inv_z && with_inverses;
     // 1. leaf LU solves; leaf t = P v
     {
       std::vector<LuSolveDescT<T>> ds;
-      std::vector<GemmDescT<T>> g;
+      std::vector<GemmDescT<T>> g, gl;
+      std::vector<CopyDescT<T>> cps;
+      std::vector<int64_t> soff(roots.size(), 0);
+      int64_t max_cp = 0;
+      T* S = nullptr;
+      if (inv) {  // every root's right-hand sides to the scratch, read there by the products
+        int64_t so = 0;
+        for (size_t q = 0; q < roots.size(); ++q) {
+          soff[q] = so;
+          so += (int64_t)nd[roots[q].gid].size * roots[q].nc;
+        }
+        S = fsS.ensure_n<T>(std::max<int64_t>(so, 1));
+        for (size_t q = 0; q < roots.size(); ++q) {
+          const int rows = nd[roots[q].gid].size;
+          cps.push_back(CopyDescT<T>{roots[q].V, S + soff[q], rows, roots[q].nc, roots[q].ld, rows});
+          max_cp = std::max<int64_t>(max_cp, (int64_t)rows * roots[q].nc);
+        }
+      }
       for (int u : by_height[0]) {
         if (root_of[u] < 0) continue;
-        ds.push_back(LuSolveDescT<T>{luP<T>() + nd[u].LU_off,
-                                     LUpiv.as<int>() + (int64_t)nd[u].leaf * m_max, Vp[u],
-                                     nd[u].size, nd[u].size, ldV(u), ncV(u), dinvP<T>(u)});
+        if (inv) {
+          const RootBlock<T>& R = roots[root_of[u]];
+          const int rows = nd[R.gid].size;
+          add_gemm<T>(gl, (const T*)LUi32.as<float>() + nd[u].LU_off, nd[u].size,
+                      S + soff[root_of[u]] + (nd[u].off - nd[R.gid].off), rows, Vp[u], ldV(u), nd[u].size, ncV(u),
+                      nd[u].size, 1.0, 0.0);
+        } else {
+          ds.push_back(LuSolveDescT<T>{luP<T>() + nd[u].LU_off,
+                                       LUpiv.as<int>() + (int64_t)nd[u].leaf * m_max, Vp[u],
+                                       nd[u].size, nd[u].size, ldV(u), ncV(u), dinvP<T>(u)});
+        }
         const bool top_root = roots[root_of[u]].gid == u;
         if (!top_root || need_t) {
           T* dst;
@@ -664,29 +706,42 @@ class Solver {
         }
       }
       arena.clear();
-      size_t o = arena.push(ds);
-      char* base = upload_arena();
-      prof().flops[pk_of<T>(PK_GETRS)] += getrs_flops(ds);
-      getrs_batched((const LuSolveDescT<T>*)(base + o), (int)ds.size(), m_max, max_nc, st,
-                    std::is_same<T, float>::value, pair_products<T>());
+      if (inv) {
+        size_t o = arena.push(cps);
+        char* base = upload_arena();
+        copy_batched((const CopyDescT<T>*)(base + o), (int)cps.size(), max_cp, st);
+        run_gemms(gl);
+      } else {
+        size_t o = arena.push(ds);
+        char* base = upload_arena();
+        prof().flops[pk_of<T>(PK_GETRS)] += getrs_flops(ds);
+        getrs_batched((const LuSolveDescT<T>*)(base + o), (int)ds.size(), m_max, max_nc, st,
+                      std::is_same<T, float>::value, pair_products<T>());
+      }
       run_gemms(g);
     }
     // 2. heights 1 .. top
     for (int hh = 1; hh <= top; ++hh) {
       std::vector<CopyDescT<T>> cp;
       std::vector<LuSolveDescT<T>> zs;
-      std::vector<GemmDescT<T>> g1, g2;
+      std::vector<GemmDescT<T>> g1, g2, gz;
       int64_t max_cp = 0;
-      int max_n2 = 0;
+      int max_n2 = 0, nodes_here = 0;
       for (int b : by_height[hh]) {
         if (root_of[b] < 0) continue;
+        ++nodes_here;
         const int a = left(b), c = right(b);  // children: a left, c right
         const int sa = nd[a].s, sc = nd[c].s, nb2 = sa + sc, nc = ncV(b);
         max_n2 = std::max(max_n2, nb2);
         max_cp = std::max<int64_t>(max_cp, (int64_t)nb2 * nc);
-        cp.push_back(CopyDescT<T>{Tp(b), Yp(b), nb2, nc, nb2, nb2});
-        zs.push_back(LuSolveDescT<T>{zP<T>() + nd[b].Z_off, Zpiv.as<int>() + nd[b].Zpiv_off, Yp(b),
-                                     nb2, nb2, nb2, nc, dinvP<T>(b)});
+        if (invz) {  // y = Z^-1 t
+          add_gemm<T>(gz, (const T*)Zi32.as<float>() + nd[b].Z_off, nb2, Tp(b), nb2, Yp(b), nb2, nb2, nc, nb2,
+                      1.0, 0.0);
+        } else {
+          cp.push_back(CopyDescT<T>{Tp(b), Yp(b), nb2, nc, nb2, nb2});
+          zs.push_back(LuSolveDescT<T>{zP<T>() + nd[b].Z_off, Zpiv.as<int>() + nd[b].Zpiv_off, Yp(b),
+                                       nb2, nb2, nb2, nc, dinvP<T>(b)});
+        }
         const T* W = wP<T>();
         // v_a -= W_{a c~} y1 (y1 = Y[sa : nb2]);  v_c -= W_{c a~} y2 (y2 = Y[0 : sa])
         add_gemm<T>(g1, W + nd[a].W_off, nd[a].size, Yp(b) + sa, nb2, Vp[a], ldV(b), nd[a].size, nc,
@@ -705,19 +760,25 @@ class Solver {
                       0.0);
         }
       }
-      if (cp.empty()) continue;
-      std::vector<GemmTile> t1, t2;
+      if (nodes_here == 0) continue;
+      std::vector<GemmTile> t1, t2, tz;
       const GemmShape sh1 = make_tiles(g1, t1, opt.gemm_tc != 0, !pair_products<T>()),
-                      sh2 = make_tiles(g2, t2, opt.gemm_tc != 0, !pair_products<T>());
+                      sh2 = make_tiles(g2, t2, opt.gemm_tc != 0, !pair_products<T>()),
+                      shz = make_tiles(gz, tz, opt.gemm_tc != 0, !pair_products<T>());
       arena.clear();
       size_t ocp = arena.push(cp), ozs = arena.push(zs), og1 = arena.push(g1), ot1 = arena.push(t1),
-             og2 = arena.push(g2), ot2 = arena.push(t2);
+             og2 = arena.push(g2), ot2 = arena.push(t2), ogz = arena.push(gz), otz = arena.push(tz);
       char* base = upload_arena();
       prof().flops[pk_of<T>(PK_GETRS)] += getrs_flops(zs);
-      prof().flops[pair_products<T>() ? PK_GEMM_PAIR : pk_of<T>(PK_GEMM)] += gemm_flops(g1) + gemm_flops(g2);
-      copy_batched((const CopyDescT<T>*)(base + ocp), (int)cp.size(), max_cp, st);
-      getrs_batched((const LuSolveDescT<T>*)(base + ozs), (int)zs.size(), max_n2, max_nc, st,
-                    std::is_same<T, float>::value, pair_products<T>());
+      prof().flops[pair_products<T>() ? PK_GEMM_PAIR : pk_of<T>(PK_GEMM)] +=
+          gemm_flops(g1) + gemm_flops(g2) + gemm_flops(gz);
+      if (invz) {
+        launch_gemms((const GemmDescT<T>*)(base + ogz), (const GemmTile*)(base + otz), (int)tz.size(), shz);
+      } else {
+        copy_batched((const CopyDescT<T>*)(base + ocp), (int)cp.size(), max_cp, st);
+        getrs_batched((const LuSolveDescT<T>*)(base + ozs), (int)zs.size(), max_n2, max_nc, st,
+                      std::is_same<T, float>::value, pair_products<T>());
+      }
       launch_gemms((const GemmDescT<T>*)(base + og1), (const GemmTile*)(base + ot1), (int)t1.size(), sh1);
       launch_gemms((const GemmDescT<T>*)(base + og2), (const GemmTile*)(base + ot2), (int)t2.size(), sh2);
     }
@@ -1928,6 +1989,26 @@ class Solver {
       prof().flops[PK_GETRF] += getrf_flops(l64);
       getrf_batched<double>((const LuDesc*)(base + o64), (int)l64.size(), m_max, status.as<int>(), st);
     }
+    // the FP32 LUs' inverses (lu_inverse), after the launches above that read the
+    // previous descriptor upload
+    inv_leaf = mixed && opt.lu_inverse >= 1;
+    inv_z = mixed && opt.lu_inverse == 2;
+    if (inv_leaf && !l32.empty()) {
+      float* li = LUi32.ensure_n<float>(tot_t[0]);
+      std::vector<LuSolveDescT<float>> ri;
+      for (int g : by_height[0]) {
+        if (f64(g)) continue;
+        const Node& n = nd[g];
+        ri.push_back(LuSolveDescT<float>{lu32 + n.LU_off, lp + (int64_t)n.leaf * m_max, li + n.LU_off, n.size,
+                                         n.size, n.size, n.size, dinvP<float>(g)});
+      }
+      arena.clear();
+      size_t oi = arena.push(ri);
+      char* bi = upload_arena();
+      prof().flops[PK_GETRI32] += getri_flops(ri);
+      getri_batched((const LuSolveDescT<float>*)(bi + oi), (int)ri.size(), m_max, st);
+      stats.bytes_LU += tot_t[0] * 4;
+    }
   }
 
   // a7 + a8: W and Z, heights 1 .. Hmax, each problem's factorization in its own
@@ -1961,12 +2042,13 @@ class Solver {
         n.CR_off = csz[t];
         csz[t] += (int64_t)sb * sa;
       }
-    const double bytes = (double)(wsz[0] + zsz[0] + csz[0]) * 4 + (double)(wsz[1] + zsz[1] + csz[1]) * 8 +
-                         (mixed ? (double)usz * 8 : 0.0);
+    const double bytes = (double)(wsz[0] + zsz[0] * (inv_z ? 2 : 1) + csz[0]) * 4 +
+                         (double)(wsz[1] + zsz[1] + csz[1]) * 8 + (mixed ? (double)usz * 8 : 0.0);
     if (opt.mem_cap_gb > 0 && bytes > opt.mem_cap_gb * 1e9)
       throw Error(IASKIT_ERR_NOMEM, "factorization exceeds mem_cap_gb");
     if (wsz[0]) Wb32.ensure_n<float>(wsz[0]);
     if (zsz[0]) Zb32.ensure_n<float>(zsz[0]);
+    if (zsz[0] && inv_z) Zi32.ensure_n<float>(zsz[0]);
     if (csz[0]) Cb32.ensure_n<float>(csz[0]);
     if (wsz[1]) Wb.ensure_n<double>(wsz[1]);
     if (zsz[1]) Zb.ensure_n<double>(zsz[1]);
@@ -1976,6 +2058,7 @@ class Solver {
     double* U64 = mixed ? Ustore.ensure_n<double>(std::max<int64_t>(usz, 1))
                         : Wb.ensure_n<double>(std::max<int64_t>(wsz[1], 1));
     stats.bytes_W = wsz[0] * 4 + wsz[1] * 8;
+    if (inv_z) stats.bytes_LU += zsz[0] * 4;
     if (mixed) stats.bytes_operator += usz * 8;
     int* sk = skel.as<int>();
     for (int hh = 1; hh <= Hmax; ++hh) {
@@ -2046,7 +2129,7 @@ class Solver {
         T* tout = C + ((n.uid & 1) == 0 ? nd[g].CL_off : nd[g].CR_off);
         rb.push_back(RootBlock<T>{c, W + n.W_off, n.size, nd[sib].s, tout, n.s});
       }
-    forest_solve<T>(rb);
+    forest_solve<T>(rb, true);
     std::vector<ZDescT<T>> zd;
     std::vector<LuDescT<T>> ld;
     int64_t max_z = 0;
@@ -2066,6 +2149,19 @@ class Solver {
     prof().flops[pk_of<T>(PK_GETRF)] += getrf_flops(ld);
     getrf_batched<T>((const LuDescT<T>*)(base + ol), (int)ld.size(), max_n, status.as<int>(), st,
                      std::is_same<T, float>::value);
+    if (std::is_same<T, float>::value && inv_z) {
+      std::vector<LuSolveDescT<float>> ri;
+      for (int g : nodes) {
+        const int n2g = n2(g);
+        ri.push_back(LuSolveDescT<float>{Zb32.as<float>() + nd[g].Z_off, Zpiv.as<int>() + nd[g].Zpiv_off,
+                                         Zi32.as<float>() + nd[g].Z_off, n2g, n2g, n2g, n2g, dinvP<float>(g)});
+      }
+      arena.clear();
+      size_t oi = arena.push(ri);
+      char* bi = upload_arena();
+      prof().flops[PK_GETRI32] += getri_flops(ri);
+      getri_batched((const LuSolveDescT<float>*)(bi + oi), (int)ri.size(), max_n, st);
+    }
   }
 
   // ------------------------------------------------------------------ solve
@@ -2153,10 +2249,10 @@ class Solver {
     }
     if (!r32.empty()) {
       conv_segs<double, float>(V, V32, back);
-      forest_solve<float>(r32);
+      forest_solve<float>(r32, true);
       conv_segs<float, double>(V32, V, back);
     }
-    if (!r64.empty()) forest_solve<double>(r64);
+    if (!r64.empty()) forest_solve<double>(r64, false);
     gather(V, out, nrhs, blocks, true);
   }
 
@@ -2800,7 +2896,7 @@ class Solver {
     DevBuf* all[] = {&X, &Xp, &perm, &iperm, &pid, &knn, &knn_pos, &samp, &ranks, &skel,
                      &piv_ws, &A_ws, &status, &arena_dev, &step_dev, &tbuf, &vbuf, &vbuf32,
                      &ubuf, &rbuf, &wt, &io, &normbuf, &redpart, &blocks_dev, &LU, &LUpiv, &Wb, &Zb, &Zpiv,
-                     &Cb, &LU32, &Wb32, &Zb32, &Cb32, &tbuf32, &Kleaf, &Ustore, &Pd, &Pf, &Ppair, &Xpair, &DInv32, &rhs_keep,
+                     &Cb, &LU32, &Wb32, &Zb32, &Cb32, &tbuf32, &Kleaf, &Ustore, &Pd, &Pf, &Ppair, &Xpair, &DInv32, &LUi32, &Zi32, &fsS, &rhs_keep,
                      &gseg_dev, &kryl, &kzb, &coefbuf, &cseg_dev, &rowsum, &l_cand, &l_hits,
                      &l_feat, &l_score, &l_linfo, &l_samp, &l_rk, &l_Ptmp, &l_sktmp, &l_hold, &l_err,
                      &l_cols, &l_gram, &l_dense, &mlp_master, &mlp_m, &mlp_v, &mlp_grad, &mlp_b16,
@@ -3140,6 +3236,8 @@ int iaskit_set_option(const char* key, double value) {
       o.gemm_tc = as_int(0, 1);
     } else if (k == "cpqr_cluster") {
       o.cpqr_cluster = as_int(0, 1);
+    } else if (k == "lu_inverse") {
+      o.lu_inverse = as_int(0, 2);
     } else if (k == "pair_cond_max") {
       if (!(value >= 1.0)) throw Error(IASKIT_ERR_ARG, "invalid pair_cond_max");
       o.pair_cond_max = value;
@@ -3191,6 +3289,7 @@ int iaskit_get_option(const char* key, double* value) {
     else if (k == "learned_temp") *value = o.learned_temp;
     else if (k == "gemm_tc") *value = o.gemm_tc;
     else if (k == "cpqr_cluster") *value = o.cpqr_cluster;
+    else if (k == "lu_inverse") *value = o.lu_inverse;
     else if (k == "pair_cond_max") *value = o.pair_cond_max;
     else if (k == "near_field") *value = o.near_field;
     else if (k == "inject_status") *value = o.inject_status;

@@ -145,6 +145,53 @@ def test_tensor_core_products_match_cuda_core_products(gpu_lib):
     assert 0.25 < h1[0] / h0[0] < 4.0
 
 
+def test_inverse_products_match_lu_solves(gpu_lib):
+    """The FP32 leaf blocks (lu_inverse 1), and the reduced systems as well (2), applied
+    through their explicit inverses (GETRI, then products) give the factorization to
+    FP32 accuracy as the LU solves do (0): the same skeletons, first-sweep residuals of
+    the same size, and refinement to 1e-10 against the FP64 operator with a similar
+    number of GMRES iterations and the same solution."""
+    ia = gpu_lib
+    w = workload("C2", N=6000)
+    X = make_points(w)
+    u = np.random.default_rng(43).standard_normal((6000, 20))   # > 16 columns: tensor-core tiles
+    ia.iaskit_set_option("precision", 1)
+    out = {}
+    try:
+        for inv in (0, 1, 2):
+            ia.iaskit_set_option("lu_inverse", inv)
+            ia.iaskit_factor(X, 1.0, 1e-2, 256, 128, 1e-5)
+            U = ia.iaskit_get_skeleton(1, 0)
+            ia.iaskit_set_option("refine", 1)
+            ia.iaskit_set_option("refine_tol", 1e-300)
+            with pytest.raises(ia.IaskitError):
+                ia.iaskit_solve(u)
+            first = ia.iaskit_stats()["refine_history"][0]
+            ia.iaskit_set_option("refine", 200)
+            ia.iaskit_set_option("refine_tol", 1e-10)
+            sol = ia.iaskit_solve(u)
+            st = ia.iaskit_stats()
+            out[inv] = (U, first, st["refine_history"][-1], st["refine_iters"], sol)
+    finally:
+        ia.iaskit_set_option("lu_inverse", 1)
+        ia.iaskit_set_option("refine", 0)
+        ia.iaskit_set_option("refine_tol", 1e-10)
+        ia.iaskit_set_option("precision", 0)
+    s0, f0, r0, i0, w0 = out[0]
+    print("first sweep: LU solves", f0, "inverses", [out[k][1] for k in (1, 2)],
+          "; iterations", i0, [out[k][3] for k in (1, 2)])
+    assert f0 < 1e-3 and r0 <= 1e-10
+    for k in (1, 2):
+        s1, f1, r1, i1, w1 = out[k]
+        assert np.array_equal(s0, s1)          # the ID does not use the solves
+        assert f1 < 1e-3
+        assert 0.1 < f1 / f0 < 10.0
+        assert r1 <= 1e-10
+        assert i1 <= i0 + 3
+        # the refined solutions agree to the refinement's accuracy (times the conditioning)
+        assert np.linalg.norm(w1 - w0) <= 1e-6 * np.linalg.norm(w0)
+
+
 def test_cluster_cpqr_matches_single_block_cpqr(gpu_lib):
     """The FP32 ID on a cluster of blocks (columns held in registers) takes the same
     arithmetic steps as the one-block kernel: the same ranks, skeletons and P (up to
