@@ -1203,8 +1203,12 @@ __device__ void lu_diag_inverses(const LuDescT<T>& D) {
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* descs, int* status, int pld) {
+// PSH: the launch gave room for the panel (rows x NB) in shared memory; else it is
+// factored in place.  The trailing update's next tile (operands) and this tile's C
+// values are loaded into registers while the current tile's products run.
+template <typename T, bool PSH>
+__global__ void __launch_bounds__(LU_THREADS, sizeof(T) == 4 ? 2 : 1)
+    getrf_kernel(const LuDescT<T>* descs, int* status, int pld) {
   __shared__ T rv[LU_THREADS / 32];
   __shared__ int ri[LU_THREADS / 32];
   __shared__ T L11[LU_NB][LU_NB + 1];
@@ -1221,11 +1225,11 @@ __global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* des
   for (int k0 = 0; k0 < n; k0 += LU_NB) {
     const int nb = min(LU_NB, n - k0);
     // 1. panel factorization: rows k0.. of the panel's columns, in shared memory when
-    //    the launch gave room for them (pld > 0), else in place
-    T* pb = pld > 0 ? reinterpret_cast<T*>(lu_sh) : A + (size_t)k0 * ld;
-    const int pl = pld > 0 ? pld : ld, roff = pld > 0 ? k0 : 0;
+    //    the launch gave room for them (PSH), else in place
+    T* pb = PSH ? reinterpret_cast<T*>(lu_sh) : A + (size_t)k0 * ld;
+    const int pl = PSH ? pld : ld, roff = PSH ? k0 : 0;
     auto pn = [&](int i, int c) -> T& { return pb[(size_t)(i - roff) + (size_t)c * pl]; };
-    if (pld > 0) {
+    if (PSH) {
       for (int e = tid; e < (n - k0) * nb; e += LU_THREADS) {
         const int i = k0 + e % (n - k0), c = e / (n - k0);
         pn(i, c) = at(i, k0 + c);
@@ -1275,15 +1279,24 @@ __global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* des
         continue;
       }
       // scaling and rank-1 update of the panel's remaining columns: a thread per row,
-      // the pivot row's entries broadcast from the panel
+      // the pivot row's entries in registers, each row's entries loaded before any of
+      // them is stored
+      T prow[LU_NB];
+#pragma unroll
+      for (int c = 0; c < LU_NB; ++c) prow[c] = (c > j && c < nb) ? pn(k, c) : (T)0;
       for (int i = k + 1 + tid; i < n; i += LU_THREADS) {
+        T row[LU_NB];
+#pragma unroll
+        for (int c = 0; c < LU_NB; ++c) row[c] = (c > j && c < nb) ? pn(i, c) : (T)0;
         const T l = pn(i, j) / piv;
         pn(i, j) = l;
-        for (int c = j + 1; c < nb; ++c) pn(i, c) -= l * pn(k, c);
+#pragma unroll
+        for (int c = 0; c < LU_NB; ++c)
+          if (c > j && c < nb) pn(i, c) = row[c] - l * prow[c];
       }
       __syncthreads();
     }
-    if (pld > 0) {
+    if (PSH) {
       for (int e = tid; e < (n - k0) * nb; e += LU_THREADS) {
         const int i = k0 + e % (n - k0), c = e / (n - k0);
         at(i, k0 + c) = pn(i, c);
@@ -1360,46 +1373,75 @@ __global__ void __launch_bounds__(LU_THREADS) getrf_kernel(const LuDescT<T>* des
         if (r < nb) at(k0 + r, c) = x[r];
     }
     __syncthreads();
-    // 4. A22 -= L21 U12, tiles of LU_TM x LU_TN, 4 x 4 per thread
+    // 4. A22 -= L21 U12, tiles of LU_TM x LU_TN, 4 x 4 per thread; tile t + 1's operands
+    //    are in flight during tile t's products
     const int m2 = n - c0;
     const int tx = tid & 15, ty = tid >> 4;
-    for (int tm = 0; tm < m2; tm += LU_TM)
-      for (int tn = 0; tn < m2; tn += LU_TN) {
-        for (int e = tid; e < LU_NB * LU_TM; e += LU_THREADS) {
-          const int r = e % LU_TM, q = e / LU_TM;
-          As[q][r] = (q < nb && tm + r < m2) ? at(c0 + tm + r, k0 + q) : (T)0;
-        }
-        for (int e = tid; e < LU_NB * LU_TN; e += LU_THREADS) {
-          const int q = e % LU_NB, cc = e / LU_NB;
-          Bs[q][cc] = (q < nb && tn + cc < m2) ? at(k0 + q, c0 + tn + cc) : (T)0;
-        }
-        __syncthreads();
-        T acc[4][4];
+    const int ntm = (m2 + LU_TM - 1) / LU_TM, ntiles = ntm * ((m2 + LU_TN - 1) / LU_TN);
+    constexpr int AV = LU_NB * LU_TM / LU_THREADS, BV = LU_NB * LU_TN / LU_THREADS;
+    T an[AV], bn[BV];
+    auto fetch = [&](int t) {
+      const int tm = (t % ntm) * LU_TM, tn = (t / ntm) * LU_TN;
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) acc[a][b] = 0;
-#pragma unroll 8
-        for (int q = 0; q < LU_NB; ++q) {
-          T av[4], bv[4];
-#pragma unroll
-          for (int a = 0; a < 4; ++a) av[a] = As[q][tx + 16 * a];
-#pragma unroll
-          for (int b = 0; b < 4; ++b) bv[b] = Bs[q][ty + 16 * b];
-#pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
-        }
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int r = tm + tx + 16 * a, cc = tn + ty + 16 * b;
-            if (r < m2 && cc < m2) at(c0 + r, c0 + cc) -= acc[a][b];
-          }
-        __syncthreads();
+      for (int u = 0; u < AV; ++u) {
+        const int e = tid + u * LU_THREADS, r = e % LU_TM, q = e / LU_TM;
+        an[u] = (q < nb && tm + r < m2) ? at(c0 + tm + r, k0 + q) : (T)0;
       }
+#pragma unroll
+      for (int u = 0; u < BV; ++u) {
+        const int e = tid + u * LU_THREADS, q = e % LU_NB, cc = e / LU_NB;
+        bn[u] = (q < nb && tn + cc < m2) ? at(k0 + q, c0 + tn + cc) : (T)0;
+      }
+    };
+    if (ntiles > 0) fetch(0);
+    for (int t = 0; t < ntiles; ++t) {
+      const int tm = (t % ntm) * LU_TM, tn = (t / ntm) * LU_TN;
+#pragma unroll
+      for (int u = 0; u < AV; ++u) {
+        const int e = tid + u * LU_THREADS;
+        As[e / LU_TM][e % LU_TM] = an[u];
+      }
+#pragma unroll
+      for (int u = 0; u < BV; ++u) {
+        const int e = tid + u * LU_THREADS;
+        Bs[e % LU_NB][e / LU_NB] = bn[u];
+      }
+      __syncthreads();
+      if (t + 1 < ntiles) fetch(t + 1);
+      T cv[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int r = tm + tx + 16 * a, cc = tn + ty + 16 * b;
+          cv[a][b] = (r < m2 && cc < m2) ? at(c0 + r, c0 + cc) : (T)0;
+        }
+      T acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+#pragma unroll 8
+      for (int q = 0; q < LU_NB; ++q) {
+        T av[4], bv[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) av[a] = As[q][tx + 16 * a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bv[b] = Bs[q][ty + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int r = tm + tx + 16 * a, cc = tn + ty + 16 * b;
+          if (r < m2 && cc < m2) at(c0 + r, c0 + cc) = cv[a][b] - acc[a][b];
+        }
+      __syncthreads();
+    }
   }
 }
 
@@ -2181,8 +2223,12 @@ void getrf_batched(const LuDescT<T>* descs_dev, int ndesc, int max_n, int* dev_s
   const bool fits = smem <= 160 * 1024;
   if (!fits) smem = 0;
   // (the kernel's static tiles take up to 42 KB: the opt-in is needed for any panel)
-  IA_CUDA(cudaFuncSetAttribute(getrf_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  getrf_kernel<T><<<ndesc, LU_THREADS, smem, st>>>(descs_dev, dev_status, fits ? pld : 0);
+  if (fits) {
+    IA_CUDA(cudaFuncSetAttribute(getrf_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    getrf_kernel<T, true><<<ndesc, LU_THREADS, smem, st>>>(descs_dev, dev_status, pld);
+  } else {
+    getrf_kernel<T, false><<<ndesc, LU_THREADS, 0, st>>>(descs_dev, dev_status, 0);
+  }
   IA_LAUNCH_CHECK();
   if (std::is_same<T, float>::value && inv) {
     if (max_n > 1024) throw Error(IASKIT_ERR_UNSUPPORTED, "LU block too large for its inverse blocks");
