@@ -363,29 +363,33 @@ __device__ __forceinline__ double oz_pow2(int e) {
   return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
 }
 
-// exp(x) for x <= 0 by Tang's table-driven method (ACM TOMS 15(2), 1989): x = (64 m + j)
-// ln2 / 64 + r with |r| <= ln2 / 128 (Cody and Waite's two-part reduction: L_hi has its
-// 17 low bits clear, so that n L_hi is exact for |n| < 2^17), exp(x) = 2^m 2^(j/64)
-// (1 + p(r)), p the Taylor polynomial of e^r - 1 to degree 5 (truncation r^6 / 720 <
-// 2^-54 relative).  The 64 values 2^(j/64), rounded to FP64 from extended precision, and
-// the constants come from the host (OzExp).  About 1 ulp in all; arguments below -708
+// exp(x) for x <= 0 by Tang's table-driven method (ACM TOMS 15(2), 1989): x = (256 m + j)
+// ln2 / 256 + r with |r| <= ln2 / 512 (Cody and Waite's two-part reduction: L_hi has its
+// 18 low bits clear, so that n L_hi is exact for |n| < 2^18), exp(x) = 2^m 2^(j/256)
+// (1 + p(r)), p the Taylor polynomial of e^r - 1 to degree 4 (truncation r^5 / 120 <
+// 2^-54 relative).  n is rounded by adding 1.5 * 2^52 (the sum's low bits hold n in two's
+// complement), which takes the place of a multiply, a rounding and a conversion on the
+// FP64 pipe.  The 256 values 2^(j/256), rounded to FP64 from extended precision, and the
+// constants come from the host (OzExp).  About 1 ulp in all; arguments below -708
 // (results near the subnormal range) take the library's exp.
+constexpr int OZ_EXP_J = 256;
 struct OzExp {
-  double T[64];
-  double inv_l, l_hi, l_lo;  // 64 / ln2, and ln2 / 64 = l_hi + l_lo
+  double T[OZ_EXP_J];
+  double inv_l, l_hi, l_lo;  // 256 / ln2, and ln2 / 256 = l_hi + l_lo
 };
 __device__ __forceinline__ double oz_exp_neg(double x, const double* T, double inv_l, double l_hi, double l_lo) {
   if (x < -708.0) return exp(x);
-  const double nf = rint(x * inv_l);
-  const int n = (int)nf;
+  constexpr double SHIFT = 6755399441055744.0;  // 1.5 * 2^52
+  const double ts = fma(x, inv_l, SHIFT);      // n = nearest integer to x / (ln2 / 256)
+  const int n = __double2loint(ts);
+  const double nf = ts - SHIFT;
   double r = fma(-nf, l_hi, x);
   r = fma(-nf, l_lo, r);
-  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-  q = fma(r, q, 1.0 / 6.0);
+  double q = fma(r, 1.0 / 24.0, 1.0 / 6.0);
   q = fma(r, q, 0.5);
   const double p = fma(r * r, q, r);
-  const double t = T[n & 63];
-  return fma(t, p, t) * __longlong_as_double((long long)((n >> 6) + 1023) << 52);
+  const double t = T[n & (OZ_EXP_J - 1)];
+  return fma(t, p, t) * __longlong_as_double((long long)((n >> 8) + 1023) << 52);
 }
 
 // One block per 128-row tile of a descriptor (rows row0 + i, consecutive points): the
@@ -409,9 +413,9 @@ __global__ void __launch_bounds__(OZK_THREADS, 1) oz_kblock_kernel(const uint16_
   __shared__ double nj_s[2][OZK_TC];
   __shared__ uint64_t mbar[2], fin;
   __shared__ uint32_t tslot;
-  __shared__ double exp_tab[64];
+  __shared__ double exp_tab[OZ_EXP_J];
   const int tid = (int)threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  if (tid < 64) exp_tab[tid] = ex.T[tid];  // read after the barriers below
+  for (int e = tid; e < OZ_EXP_J; e += (int)blockDim.x) exp_tab[e] = ex.T[e];  // read after the barriers below
   const OzKDesc D = descs[oz_find(descs, nd, (int)blockIdx.x)];
   const int i0 = ((int)blockIdx.x - D.tile0) * OZ_TM;
   const int nct = (D.ncols + OZK_TC - 1) / OZK_TC;
@@ -549,13 +553,13 @@ void oz_points(const double* X, int N, int d, uint16_t* XD, int* XE, cudaStream_
 static const OzExp& oz_exp_table() {
   static const OzExp tab = [] {
     OzExp e{};
-    for (int j = 0; j < 64; ++j) e.T[j] = (double)exp2l((long double)j / 64.0L);
-    const long double L = logl(2.0L) / 64.0L;
+    for (int j = 0; j < OZ_EXP_J; ++j) e.T[j] = (double)exp2l((long double)j / (long double)OZ_EXP_J);
+    const long double L = logl(2.0L) / (long double)OZ_EXP_J;
     e.inv_l = (double)(1.0L / L);
     double hi = (double)L;
     unsigned long long b;
     std::memcpy(&b, &hi, sizeof b);
-    b &= ~((1ull << 17) - 1);
+    b &= ~((1ull << 18) - 1);
     std::memcpy(&hi, &b, sizeof b);
     e.l_hi = hi;
     e.l_lo = (double)(L - (long double)hi);
