@@ -222,15 +222,18 @@ int iaskit_predict_device(const double* d_test, int64_t M, const double* d_w, in
  *   "cpqr_cluster" 1: FP32 IDs of blocks up to 512 x 512 run on a cluster of up to 8
  *                  thread blocks per node, the columns held in registers (default);
  *                  0: one thread block per node.  Same arithmetic either way.
- *   "lu_inverse"   mixed precision: 1: every FP32 leaf LU (lambda I + K_aa) is inverted
- *                  once after it is factored (GETRI, A^-1 = U^-1 L^-1 P), and the leaf
- *                  solves of Alg. "Solve" (in W = D^-1 U and in iaskit_solve) multiply by
- *                  the inverses: FP32 products on the tensor cores instead of triangular
- *                  solves; 4 more bytes per leaf-block entry (default).  2: the reduced
- *                  systems Z as well (faster factorization; the products by the inverses
- *                  of Z weaken the preconditioner: 16 refinement iterations instead of 9
- *                  on the manifold in d 64).  0: LU solves throughout.  All are FP32
- *                  solves whose error the refinement removes [before iaskit_factor]
+ *   "lu_inverse"   mixed precision: FP32 LUs inverted once after they are factored
+ *                  (GETRI, A^-1 = U^-1 L^-1 P), their solves in Alg. "Solve" (in W =
+ *                  D^-1 U and in iaskit_solve) then multiply by the inverses: FP32
+ *                  products on the tensor cores instead of triangular solves, 4 more
+ *                  bytes per inverted entry.  2: the leaf blocks lambda I + K_aa and the
+ *                  reduced systems Z up to height "lu_inverse_zh" (default); 1: the leaf
+ *                  blocks only; 0: LU solves throughout.  Products by an FP32 inverse
+ *                  are not backward stable: inverses of the Zs above height 1 raised the
+ *                  refinement's iterations (10 -> 16 on the manifold in d 64).  All are
+ *                  FP32 solves whose error the refinement removes [before iaskit_factor]
+ *   "lu_inverse_zh" with lu_inverse 2: the greatest height whose reduced systems are
+ *                  inverted (1; leaves are height 0) [before iaskit_factor]
  *   "near_field"   1: the operator is the kNN-separated lambda I + K~ + S of eq. (askit)
  *                  (Sec. II-B): for each target i, a node that the Evaluate step reaches
  *                  for i (the sibling of an ancestor of i's leaf) and that holds one of

@@ -90,10 +90,11 @@ struct Options {
   int gemm_tc = 1;            // FP32 products with more than 16 columns on the tensor cores (3xTF32)
   int cpqr_cluster = 1;       // FP32 IDs of up to 512 x 512 on a cluster of blocks per node
   // FP32 LUs inverted once and applied as products: 1 the leaf blocks, 2 the leaf blocks
-  // and the reduced systems; 0 none (LU solves).  Products by the inverse of a reduced
-  // system raised the refinement's iterations on the manifold in d 64 (9 -> 16; leaf
-  // blocks alone: 10)
-  int lu_inverse = 1;
+  // and the reduced systems up to height lu_inverse_zh; 0 none (LU solves).  Inverses of
+  // the reduced systems above height 1 raised the refinement's GMRES iterations on the
+  // manifold in d 64 (10 -> 16); those of height 1 did not
+  int lu_inverse = 2;
+  int lu_inverse_zh = 1;
   // mixed form: problems whose condition estimate exceeds this keep their operator
   // blocks in FP64 from the start; any other problem whose refinement stops at the
   // FP32-pair operator's rounding floor is upgraded to FP64 and refined again.  Measured
@@ -456,6 +457,7 @@ class Solver {
   DevBuf LUi32, Zi32;  // explicit inverses of the FP32 leaf LUs and reduced systems (lu_inverse)
   DevBuf fsS;          // forest solves with inverses: the right-hand sides' copy
   bool inv_leaf = false, inv_z = false;  // this factorization's FP32 leaf LUs / Zs have inverses
+  int inv_zh = 0;                         // the Zs up to this height (inv_z)
   DevBuf rhs_keep;  // mixed form: the right-hand side, for a refinement after an operator upgrade
   DevBuf pred_part, pred_io;  // kernel sums at test points: chunk partials; host-call staging
   DevBuf kperm, kiperm, Xk;   // kNN search order (tree of 128-point leaves) and its points
@@ -722,6 +724,7 @@ class Solver {
     }
     // 2. heights 1 .. top
     for (int hh = 1; hh <= top; ++hh) {
+      const bool invzh = invz && hh <= inv_zh;
       std::vector<CopyDescT<T>> cp;
       std::vector<LuSolveDescT<T>> zs;
       std::vector<GemmDescT<T>> g1, g2, gz;
@@ -734,7 +737,7 @@ class Solver {
         const int sa = nd[a].s, sc = nd[c].s, nb2 = sa + sc, nc = ncV(b);
         max_n2 = std::max(max_n2, nb2);
         max_cp = std::max<int64_t>(max_cp, (int64_t)nb2 * nc);
-        if (invz) {  // y = Z^-1 t
+        if (invzh) {  // y = Z^-1 t
           add_gemm<T>(gz, (const T*)Zi32.as<float>() + nd[b].Z_off, nb2, Tp(b), nb2, Yp(b), nb2, nb2, nc, nb2,
                       1.0, 0.0);
         } else {
@@ -772,7 +775,7 @@ class Solver {
       prof().flops[pk_of<T>(PK_GETRS)] += getrs_flops(zs);
       prof().flops[pair_products<T>() ? PK_GEMM_PAIR : pk_of<T>(PK_GEMM)] +=
           gemm_flops(g1) + gemm_flops(g2) + gemm_flops(gz);
-      if (invz) {
+      if (invzh) {
         launch_gemms((const GemmDescT<T>*)(base + ogz), (const GemmTile*)(base + otz), (int)tz.size(), shz);
       } else {
         copy_batched((const CopyDescT<T>*)(base + ocp), (int)cp.size(), max_cp, st);
@@ -1993,6 +1996,7 @@ class Solver {
     // previous descriptor upload
     inv_leaf = mixed && opt.lu_inverse >= 1;
     inv_z = mixed && opt.lu_inverse == 2;
+    inv_zh = opt.lu_inverse_zh;
     if (inv_leaf && !l32.empty()) {
       float* li = LUi32.ensure_n<float>(tot_t[0]);
       std::vector<LuSolveDescT<float>> ri;
@@ -2149,7 +2153,7 @@ class Solver {
     prof().flops[pk_of<T>(PK_GETRF)] += getrf_flops(ld);
     getrf_batched<T>((const LuDescT<T>*)(base + ol), (int)ld.size(), max_n, status.as<int>(), st,
                      std::is_same<T, float>::value);
-    if (std::is_same<T, float>::value && inv_z) {
+    if (std::is_same<T, float>::value && inv_z && height(nodes[0]) <= inv_zh) {
       std::vector<LuSolveDescT<float>> ri;
       for (int g : nodes) {
         const int n2g = n2(g);
@@ -3238,6 +3242,8 @@ int iaskit_set_option(const char* key, double value) {
       o.cpqr_cluster = as_int(0, 1);
     } else if (k == "lu_inverse") {
       o.lu_inverse = as_int(0, 2);
+    } else if (k == "lu_inverse_zh") {
+      o.lu_inverse_zh = as_int(0, 1 << 20);
     } else if (k == "pair_cond_max") {
       if (!(value >= 1.0)) throw Error(IASKIT_ERR_ARG, "invalid pair_cond_max");
       o.pair_cond_max = value;
@@ -3290,6 +3296,7 @@ int iaskit_get_option(const char* key, double* value) {
     else if (k == "gemm_tc") *value = o.gemm_tc;
     else if (k == "cpqr_cluster") *value = o.cpqr_cluster;
     else if (k == "lu_inverse") *value = o.lu_inverse;
+    else if (k == "lu_inverse_zh") *value = o.lu_inverse_zh;
     else if (k == "pair_cond_max") *value = o.pair_cond_max;
     else if (k == "near_field") *value = o.near_field;
     else if (k == "inject_status") *value = o.inject_status;

@@ -146,11 +146,11 @@ def test_tensor_core_products_match_cuda_core_products(gpu_lib):
 
 
 def test_inverse_products_match_lu_solves(gpu_lib):
-    """The FP32 leaf blocks (lu_inverse 1), and the reduced systems as well (2), applied
-    through their explicit inverses (GETRI, then products) give the factorization to
-    FP32 accuracy as the LU solves do (0): the same skeletons, first-sweep residuals of
-    the same size, and refinement to 1e-10 against the FP64 operator with a similar
-    number of GMRES iterations and the same solution."""
+    """The FP32 leaf blocks (lu_inverse 1), and the reduced systems as well (2, up to
+    height 1 or at every height), applied through their explicit inverses (GETRI, then
+    products) give the factorization to FP32 accuracy as the LU solves do (0): the same
+    skeletons, first-sweep residuals of the same size, and refinement to 1e-10 against
+    the FP64 operator with a similar number of GMRES iterations and the same solution."""
     ia = gpu_lib
     w = workload("C2", N=6000)
     X = make_points(w)
@@ -158,8 +158,9 @@ def test_inverse_products_match_lu_solves(gpu_lib):
     ia.iaskit_set_option("precision", 1)
     out = {}
     try:
-        for inv in (0, 1, 2):
+        for key, (inv, zh) in enumerate(((0, 1), (1, 1), (2, 1), (2, 1 << 20))):
             ia.iaskit_set_option("lu_inverse", inv)
+            ia.iaskit_set_option("lu_inverse_zh", zh)
             ia.iaskit_factor(X, 1.0, 1e-2, 256, 128, 1e-5)
             U = ia.iaskit_get_skeleton(1, 0)
             ia.iaskit_set_option("refine", 1)
@@ -171,17 +172,18 @@ def test_inverse_products_match_lu_solves(gpu_lib):
             ia.iaskit_set_option("refine_tol", 1e-10)
             sol = ia.iaskit_solve(u)
             st = ia.iaskit_stats()
-            out[inv] = (U, first, st["refine_history"][-1], st["refine_iters"], sol)
+            out[key] = (U, first, st["refine_history"][-1], st["refine_iters"], sol)
     finally:
-        ia.iaskit_set_option("lu_inverse", 1)
+        ia.iaskit_set_option("lu_inverse", 2)
+        ia.iaskit_set_option("lu_inverse_zh", 1)
         ia.iaskit_set_option("refine", 0)
         ia.iaskit_set_option("refine_tol", 1e-10)
         ia.iaskit_set_option("precision", 0)
     s0, f0, r0, i0, w0 = out[0]
-    print("first sweep: LU solves", f0, "inverses", [out[k][1] for k in (1, 2)],
-          "; iterations", i0, [out[k][3] for k in (1, 2)])
+    print("first sweep: LU solves", f0, "inverses", [out[k][1] for k in (1, 2, 3)],
+          "; iterations", i0, [out[k][3] for k in (1, 2, 3)])
     assert f0 < 1e-3 and r0 <= 1e-10
-    for k in (1, 2):
+    for k in (1, 2, 3):
         s1, f1, r1, i1, w1 = out[k]
         assert np.array_equal(s0, s1)          # the ID does not use the solves
         assert f1 < 1e-3
