@@ -614,7 +614,7 @@ class Solver {
   // Applies (lambda I + K~_cc)^{-1} to the block of every root c, in place, with the
   // factorization stored in precision T.  Writes P_c v_c to roots[].t_out when given.
   template <typename T>
-  void forest_solve(const std::vector<RootBlock<T>>& roots, bool with_inverses) {
+  void forest_solve(const std::vector<RootBlock<T>>& roots) {
     const bool need_t = !roots.empty() && roots[0].t_out != nullptr;
     std::vector<int> root_of(nd.size(), -1);
     std::vector<T*> Vp(nd.size(), nullptr);
@@ -663,7 +663,7 @@ class Solver {
 
     // FP32 LUs with inverses: the leaf solves and the reduced systems are products
     const bool fp32 = std::is_same<T, float>::value;
-    const bool inv = fp32 && inv_leaf && with_inverses, invz = fp32 && inv_z && with_inverses;
+    const bool inv = fp32 && inv_leaf, invz = fp32 && inv_z;
     // 1. leaf LU solves; leaf t = P v
     {
       std::vector<LuSolveDescT<T>> ds;
@@ -2032,7 +2032,8 @@ class Solver {
         n.W_off = wsz[f64(g)];
         wsz[f64(g)] += e;
       }
-    for (int hh = 1; hh <= Hmax; ++hh)
+    int64_t zinv = 0;  // FP32 Zs of heights <= inv_zh, inverted: a prefix of the FP32 Z pool
+    for (int hh = 1; hh <= Hmax; ++hh) {
       for (int g : by_height[hh]) {
         Node& n = nd[g];
         const int t = f64(g);
@@ -2046,13 +2047,15 @@ class Solver {
         n.CR_off = csz[t];
         csz[t] += (int64_t)sb * sa;
       }
-    const double bytes = (double)(wsz[0] + zsz[0] * (inv_z ? 2 : 1) + csz[0]) * 4 +
+      if (inv_z && hh <= inv_zh) zinv = zsz[0];
+    }
+    const double bytes = (double)(wsz[0] + zsz[0] + zinv + csz[0]) * 4 +
                          (double)(wsz[1] + zsz[1] + csz[1]) * 8 + (mixed ? (double)usz * 8 : 0.0);
     if (opt.mem_cap_gb > 0 && bytes > opt.mem_cap_gb * 1e9)
       throw Error(IASKIT_ERR_NOMEM, "factorization exceeds mem_cap_gb");
     if (wsz[0]) Wb32.ensure_n<float>(wsz[0]);
     if (zsz[0]) Zb32.ensure_n<float>(zsz[0]);
-    if (zsz[0] && inv_z) Zi32.ensure_n<float>(zsz[0]);
+    if (zinv) Zi32.ensure_n<float>(zinv);
     if (csz[0]) Cb32.ensure_n<float>(csz[0]);
     if (wsz[1]) Wb.ensure_n<double>(wsz[1]);
     if (zsz[1]) Zb.ensure_n<double>(zsz[1]);
@@ -2062,7 +2065,7 @@ class Solver {
     double* U64 = mixed ? Ustore.ensure_n<double>(std::max<int64_t>(usz, 1))
                         : Wb.ensure_n<double>(std::max<int64_t>(wsz[1], 1));
     stats.bytes_W = wsz[0] * 4 + wsz[1] * 8;
-    if (inv_z) stats.bytes_LU += zsz[0] * 4;
+    stats.bytes_LU += zinv * 4;
     if (mixed) stats.bytes_operator += usz * 8;
     int* sk = skel.as<int>();
     for (int hh = 1; hh <= Hmax; ++hh) {
@@ -2133,7 +2136,7 @@ class Solver {
         T* tout = C + ((n.uid & 1) == 0 ? nd[g].CL_off : nd[g].CR_off);
         rb.push_back(RootBlock<T>{c, W + n.W_off, n.size, nd[sib].s, tout, n.s});
       }
-    forest_solve<T>(rb, true);
+    forest_solve<T>(rb);
     std::vector<ZDescT<T>> zd;
     std::vector<LuDescT<T>> ld;
     int64_t max_z = 0;
@@ -2253,10 +2256,10 @@ class Solver {
     }
     if (!r32.empty()) {
       conv_segs<double, float>(V, V32, back);
-      forest_solve<float>(r32, true);
+      forest_solve<float>(r32);
       conv_segs<float, double>(V32, V, back);
     }
-    if (!r64.empty()) forest_solve<double>(r64, false);
+    if (!r64.empty()) forest_solve<double>(r64);
     gather(V, out, nrhs, blocks, true);
   }
 
